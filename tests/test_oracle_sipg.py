@@ -1,0 +1,144 @@
+"""Pins of the oracle's SIPG operator and block-Jacobi smoother.
+
+The assembled route (quadrature of the weak form, facet by facet) and the
+matrix-free facet route (Alg. 2 stages) share only the 1D reference element,
+which is pinned separately; their agreement, symmetry, positivity, polynomial
+consistency and the smoother's fixed point pin the operator (Sec. 2.3, 4.1)."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse.linalg as spla
+
+from oracle import sipg
+
+CASES = [((3, 3), 1), ((3, 4), 2), ((3, 3), 3), ((2, 3), 5), ((2, 2, 2), 1), ((2, 3, 2), 2), ((2, 2, 2), 3)]
+
+
+def _kappa(mesh, kind, seed=0):
+    if kind == "one":
+        return None
+    return np.exp(np.random.default_rng(seed).normal(size=mesh.ncell))
+
+
+@pytest.mark.parametrize("n,p", CASES)
+@pytest.mark.parametrize("kind", ["one", "lognormal"])
+def test_assembled_equals_facet_route(n, p, kind):
+    mesh = sipg.Mesh(n, p)
+    kap = _kappa(mesh, kind)
+    A = sipg.assemble(mesh, kap)
+    u = np.random.default_rng(1).normal(size=mesh.ndof)
+    y1, y2 = A @ u, sipg.apply(mesh, u, kap)
+    assert np.abs(y1 - y2).max() <= 1e-13 * np.abs(y1).max()
+
+
+@pytest.mark.parametrize("n,p", CASES)
+@pytest.mark.parametrize("kind", ["one", "lognormal"])
+def test_symmetric_positive_definite(n, p, kind):
+    mesh = sipg.Mesh(n, p)
+    Ad = sipg.assemble(mesh, _kappa(mesh, kind)).toarray()
+    assert np.abs(Ad - Ad.T).max() <= 1e-14 * np.abs(Ad).max()
+    assert np.linalg.eigvalsh(0.5 * (Ad + Ad.T))[0] > 0.0
+
+
+@pytest.mark.parametrize("n,p", CASES)
+@pytest.mark.parametrize("kind", ["one", "lognormal"])
+def test_block_diagonal_is_diagonal_of_assembled(n, p, kind):
+    mesh = sipg.Mesh(n, p)
+    kap = _kappa(mesh, kind)
+    Ad = sipg.assemble(mesh, kap).toarray()
+    B = sipg.block_diagonal(mesh, kap)
+    nl = mesh.nloc
+    for c in range(mesh.ncell):
+        blk = Ad[c * nl:(c + 1) * nl, c * nl:(c + 1) * nl]
+        assert np.abs(B[c] - blk).max() <= 1e-13 * np.abs(blk).max()
+
+
+@pytest.mark.parametrize("d,p", [(2, 1), (2, 2), (2, 3), (2, 4), (3, 1), (3, 2), (3, 3)])
+def test_polynomial_consistency(d, p):
+    """For constant kappa and a global polynomial u of degree <= p per axis, the
+    SIPG residual on cells away from the boundary equals the L2 projection of
+    -kappa Lap u: (A u)_K = kappa M_K (-Lap u)_K (consistency of the method)."""
+    n = (4,) * d
+    mesh = sipg.Mesh(n, p)
+    kap = 2.5
+    rng = np.random.default_rng(d * 10 + p)
+    C = rng.normal(size=(p + 1,) * d)                       # coefficients of x^a y^b z^c
+
+    def poly(X, deriv=None):
+        val = np.zeros(X.shape[0])
+        for idx in np.ndindex(C.shape):
+            term = np.full(X.shape[0], C[idx])
+            for a in range(d):
+                e = idx[a]
+                if deriv == a:
+                    term = term * (e * (e - 1) * X[:, a] ** max(e - 2, 0) if e >= 2 else 0.0)
+                else:
+                    term = term * X[:, a] ** e
+            val += term
+        return val
+
+    X = mesh.node_coords()
+    u = poly(X)
+    lap = sum(poly(X, deriv=a) for a in range(d))
+    Au = sipg.apply(mesh, u, np.full(mesh.ncell, kap))
+    L = mesh.grid(-kap * lap)
+    for a in range(d):
+        L = sipg.apply_1d(mesh.M[a], L, mesh.node_axis(a))
+    Mlap = mesh.flat(L)
+    Au = Au.reshape(mesh.ncell, mesh.nloc)
+    cells = np.indices(n[::-1]).reshape(d, -1)[::-1]
+    inner = np.all([(cells[a] > 0) & (cells[a] < n[a] - 1) for a in range(d)], axis=0)
+    scale = np.abs(Au).max()
+    assert np.abs(Au[inner] - Mlap[inner]).max() <= 1e-11 * scale
+
+
+@pytest.mark.parametrize("n,p", [((3, 4), 2), ((2, 2, 2), 2), ((3, 3), 4)])
+@pytest.mark.parametrize("kind", ["one", "lognormal"])
+def test_smoother_fixed_point_and_orders(n, p, kind):
+    mesh = sipg.Mesh(n, p)
+    kap = _kappa(mesh, kind)
+    A = sipg.assemble(mesh, kap)
+    rng = np.random.default_rng(3)
+    b = rng.normal(size=mesh.ndof)
+    xs = spla.spsolve(A.tocsc(), b)
+    bj = sipg.BlockJacobi(mesh, kap)
+    x1 = bj.step_alg2(xs, b, 0.8, 1)
+    assert np.abs(x1 - xs).max() <= 1e-12 * np.abs(xs).max()
+    # Alg. 4 (fused) == Alg. 2 (three sweeps) == dense u + omega D^-1 (b - A u)
+    Ad = A.toarray()
+    nl = mesh.nloc
+    D = sla.block_diag(*[Ad[c * nl:(c + 1) * nl, c * nl:(c + 1) * nl] for c in range(mesh.ncell)])
+    u0 = rng.normal(size=mesh.ndof)
+    ud = u0.copy()
+    for _ in range(3):
+        ud = ud + 0.8 * np.linalg.solve(D, b - Ad @ ud)
+    u2 = bj.step_alg2(u0, b, 0.8, 3)
+    u4, proj = bj.step_alg4(u0, b, 0.8, 3)
+    sc = np.abs(ud).max()
+    assert np.abs(u2 - ud).max() <= 1e-12 * sc
+    assert np.abs(u4 - ud).max() <= 1e-12 * sc
+    # the returned projections are those of the returned iterate
+    ref = sipg.project(mesh, mesh.grid(u4))
+    for a in range(mesh.d):
+        for f1, f2 in zip(proj[a], ref[a]):
+            assert np.array_equal(f1, f2)
+
+
+def test_load_vector_and_l2_error_closed_forms():
+    for n, p in [((3, 2), 2), ((2, 2, 3), 3)]:
+        mesh = sipg.Mesh(n, p)
+        d = mesh.d
+        one = lambda *X: np.ones_like(X[0])
+        b = sipg.load_vector(mesh, one)
+        assert abs(b.sum() - 1.0) < 1e-13                 # sum_i (1, phi_i) = |Omega|
+        # polynomial f of degree <= p per axis: b = M f_nodal exactly
+        f = lambda *X: sum((a + 1) * X[a] ** p for a in range(d)) + X[0] * X[-1]
+        X = mesh.node_coords()
+        F = mesh.grid(f(*[X[:, a] for a in range(d)]))
+        for a in range(d):
+            F = sipg.apply_1d(mesh.M[a], F, mesh.node_axis(a))
+        assert np.allclose(sipg.load_vector(mesh, f), mesh.flat(F).reshape(-1), atol=1e-14)
+        # interpolant of a degree-p polynomial has zero L2 error; ||0 - 1|| = 1
+        u = f(*[X[:, a] for a in range(d)])
+        assert sipg.l2_error(mesh, u, f) < 1e-13
+        assert abs(sipg.l2_error(mesh, np.zeros(mesh.ndof), one) - 1.0) < 1e-13
