@@ -1,0 +1,236 @@
+/*
+ * dgmg.h -- C ABI of libdgmg: matrix-free SIPG discontinuous Galerkin with
+ * hp-multigrid on one NVIDIA GB300 GPU (sm_103a).
+ *
+ * Method: Baccas, Belozerov, Mueller, Weinzierl, "Implementation techniques for
+ * multigrid solvers for high-order Discontinuous Galerkin methods" (arXiv
+ * 2510.00998). Section / algorithm / equation numbers below refer to that paper.
+ *
+ * Problem: -div(kappa grad u) = f on the unit box [0,1]^d (d = 2 or 3),
+ * homogeneous Dirichlet, uniform mesh of n[0] x n[1] (x n[2]) cells,
+ * tensor-product GLL Lagrange basis of degree p per axis (q = p+1 nodes per
+ * axis, q^d DoFs per cell), cellwise-constant kappa > 0. Bilinear form: Eq.
+ * weak_form_IP (Sec. 2.3.1) with theta = -1 (symmetric interior penalty),
+ * penalty gamma_F = 2 p (p+1) / h on every facet, every interior facet term
+ * scaled by the harmonic mean 2 k- k+ / (k- + k+), boundary facet terms and
+ * the volume term by the cell's kappa.
+ *
+ * Vector layout (every DG vector argument): double[ncell * q^d], cell-major,
+ * cell = ix + n0 * (iy + n1 * iz), node = i + q * (j + q * k) within the cell
+ * (x fastest), nodes at the GLL points of the cell. CG (Q1) vectors live on the
+ * interior vertices, (vx-1) + (n0-1) * ((vy-1) + (n1-1) * (vz-1)).
+ *
+ * Memory: unless stated otherwise, vector arguments are DEVICE pointers owned by
+ * the caller; the library keeps no reference to them after the call returns its
+ * work to the stream. All device work of a call is queued on `stream` (a
+ * cudaStream_t passed as void*, NULL = the legacy default stream); calls return
+ * without a host synchronisation unless stated. The library owns everything
+ * inside a dgmg_ctx. A ctx may be used from one host thread at a time.
+ *
+ * Errors: every int-returning call returns DGMG_OK (0) or a negative code; the
+ * thread-local message of the last failure is returned by dgmg_last_error().
+ * Arguments are validated before any device work is queued.
+ */
+#ifndef DGMG_H
+#define DGMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DGMG_OK 0
+#define DGMG_EINVAL (-1)          /* invalid argument (message says which)            */
+#define DGMG_ENOMEM (-2)          /* device or host allocation failed                 */
+#define DGMG_EBUDGET (-3)         /* request cannot fit the server's HBM budget       */
+#define DGMG_ENOTCONVERGED (-4)   /* maxit reached; x holds the last iterate          */
+#define DGMG_ENONFINITE (-5)      /* a NaN/Inf was detected in an input or residual   */
+#define DGMG_ECUDA (-6)           /* a CUDA runtime call failed                       */
+
+/* precision of the V-cycle used as preconditioner */
+#define DGMG_FP64 0               /* every stage in FP64                               */
+#define DGMG_MIXED_FP32 1         /* V-cycle in FP32 inside FP64 CG (Sec. 5 cycle,     */
+                                  /* outer residual/update/coarsest solve in FP64)     */
+
+/* block inverse used by the block-Jacobi smoother (Eq. block-Jacobi-IP) */
+#define DGMG_BLOCK_EXACT 0        /* exact diagonal block A_KK of every cell           */
+#define DGMG_BLOCK_INTERIOR_ONLY 1/* Technique 4: the block of an interior cell, with  */
+                                  /* the cell's own kappa, for every cell              */
+
+typedef struct {
+    int dim;                      /* 2 or 3                                            */
+    int n[3];                     /* cells per axis, each >= 1 (n[2] ignored for d=2)  */
+} dgmg_mesh;
+
+typedef struct {
+    double omega_dg;              /* block-Jacobi damping, 0 < omega < 2 (default 0.8) */
+    double omega_cg;              /* point-Jacobi damping on Q1 levels (default 0.8)   */
+    int nu_pre, nu_post;          /* smoothing steps per level (default 2, 2)          */
+    int precision;                /* DGMG_FP64 (default) or DGMG_MIXED_FP32            */
+    int block_inverse;            /* DGMG_BLOCK_EXACT (default) | _INTERIOR_ONLY       */
+    int coarsening;               /* h-coarsening factor 2 (default) or 3              */
+    double rtol;                  /* dgmg_solve: stop at ||b-Ax||_2 <= rtol ||b||_2    */
+                                  /* (default 1e-10)                                   */
+    int maxit;                    /* dgmg_solve iteration cap (default 200)            */
+} dgmg_opts;
+
+typedef struct {
+    int dim, p, q;                /* dimension, degree, nodes per axis                 */
+    int n[3];                     /* cells per axis                                    */
+    int64_t ncell, ndof;          /* cells, DG unknowns                                */
+    int nlevels_cg;               /* Q1 levels below the DG level (>= 1)               */
+    int64_t nvert0;               /* unknowns of the first Q1 level                    */
+    int64_t ncoarse;              /* unknowns of the coarsest level (dense solve)      */
+    double omega_dg, omega_cg;    /* damping actually used                             */
+    int nu_pre, nu_post, precision, block_inverse, coarsening;
+    size_t device_bytes;          /* device memory held by the ctx                     */
+} dgmg_info_t;
+
+typedef struct {
+    int iterations;               /* outer CG iterations                               */
+    double rel_residual;          /* ||b - A x||_2 / ||b||_2 of the returned x, recomputed */
+    double rel_residual_recursive;/* the CG recurrence's last estimate                 */
+    double prec_residual;         /* ||z||_2 / ||z_0||_2 of the last preconditioned    */
+                                  /* residual z = V(r) (Eq. preconditioned_residual)   */
+    double seconds;               /* wall time of the call                             */
+} dgmg_stats;
+
+typedef struct dgmg_ctx dgmg_ctx;
+
+/* Library version string. */
+const char *dgmg_version(void);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char *dgmg_last_error(void);
+
+/* Fill *opts with the defaults listed in dgmg_opts. */
+void dgmg_default_opts(dgmg_opts *opts);
+
+/*
+ * Build the hierarchy for `mesh`, degree p (1..6) and kappa (HOST array of
+ * ncell positive finite doubles, cell-major; NULL = kappa 1 everywhere):
+ * 1D reference matrices (Sec. 2.2), per-cell fast-diagonalisation factors of
+ * the exact diagonal blocks A_KK (Sec. 4.1, Technique 3), the Q1 operator
+ * P^T A P (Sec. 2.4) and its Galerkin coarsenings (Sec. 5.2), the dense inverse
+ * of the coarsest operator, and all device work buffers. opts NULL = defaults.
+ * Synchronous. On failure *out is NULL and nothing is leaked.
+ */
+int dgmg_create(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_opts *opts,
+                dgmg_ctx **out);
+
+/* Free every resource of ctx (waits for its device work). NULL is accepted. */
+int dgmg_destroy(dgmg_ctx *ctx);
+
+/* Describe ctx (host struct, filled synchronously). */
+int dgmg_info(const dgmg_ctx *ctx, dgmg_info_t *info);
+
+/* Number of nodes per cell q^d and the GLL node coordinates on [-1,1]
+ * (HOST array of q doubles) of ctx's basis. */
+int dgmg_gll_nodes(const dgmg_ctx *ctx, double *nodes_host);
+
+/*
+ * y = A u (the SIPG operator, Eq. matrix_form_IP), FP64, DG layout. Runs the
+ * warm-up projection (Alg. 4 preamble) and the cell equation of Alg. 2 stage 3
+ * on the stored projections. u and y must not overlap.
+ */
+int dgmg_apply(dgmg_ctx *ctx, const double *u, double *y, void *stream);
+
+/* r = b - A u, FP64 (Alg. 6 residual without the restriction). */
+int dgmg_residual(dgmg_ctx *ctx, const double *u, const double *b, double *r, void *stream);
+
+/*
+ * nsteps >= 0 damped block-Jacobi steps u <- u + omega_dg A_KK^{-1} (b - A u)
+ * in the single-touch order of Alg. 4 (one warm-up projection, then one fused
+ * traversal per step reading the neighbours' stored projections, updating the
+ * cell, re-projecting it). FP64, u in/out, b input.
+ */
+int dgmg_smooth(dgmg_ctx *ctx, double *u, const double *b, int nsteps, void *stream);
+
+/*
+ * e = V(r): one hp V(nu_pre, nu_post) cycle with zero initial guess (Alg. 6 /
+ * Alg. 7 building blocks, Sec. 5.2): nu_pre smoothing steps, residual and
+ * p-restriction to Q1, the h-multigrid V-cycle with point Jacobi on the Q1
+ * levels and the dense coarsest solve, p-prolongation fused into the next
+ * projection, nu_post smoothing steps. In DGMG_MIXED_FP32 precision the cycle
+ * runs in FP32 (r rounded on entry, e widened on exit); the coarsest solve is
+ * FP64 in both. r and e are FP64 and must not overlap.
+ */
+int dgmg_vcycle(dgmg_ctx *ctx, const double *r, double *e, void *stream);
+
+/*
+ * Solve A x = b with conjugate gradients preconditioned by dgmg_vcycle (flexible
+ * Polak-Ribiere form in mixed precision), FP64 outer residual, update and dot
+ * products, starting from the x passed in. Stops when the recursively updated
+ * residual satisfies ||r||_2 <= rtol ||b||_2, then recomputes b - A x and
+ * reports it in stats (HOST struct, may be NULL). Blocks until done (it reads
+ * one scalar per iteration). Returns DGMG_ENOTCONVERGED after maxit
+ * iterations, DGMG_ENONFINITE if a residual norm is not finite.
+ */
+int dgmg_solve(dgmg_ctx *ctx, const double *b, double *x, dgmg_stats *stats, void *stream);
+
+/*
+ * dgmg_solve with HOST vectors: copies b and x (initial guess) to the ctx's
+ * device buffers, solves, copies x back. b_host, x_host: ndof doubles each
+ * (pinned memory gives the fastest copies). Blocks until x_host is written.
+ */
+int dgmg_solve_host(dgmg_ctx *ctx, const double *b_host, double *x_host, dgmg_stats *stats,
+                    void *stream);
+
+/*
+ * b_i = (f, phi_i) (Sec. 2.3.1 right-hand side) from f sampled at the (p+2)^d
+ * Gauss-Legendre points of every cell: fq is a DEVICE array [ncell][(p+2)^d]
+ * (x fastest within a cell), b a DEVICE DG vector. dgmg_quad_points writes the
+ * physical coordinates of those points, DEVICE array [ncell][(p+2)^d][dim].
+ */
+int dgmg_quad_points(dgmg_ctx *ctx, double *xq, void *stream);
+int dgmg_load_vector(dgmg_ctx *ctx, const double *fq, double *b, void *stream);
+
+/* ---- stage entry points: the individual steps of the path, for testing ---- */
+
+/*
+ * Warm-up projection (Alg. 4 preamble, Eq. solution_projection /
+ * gradient_projection), optionally fused with the p-prolongation u += P e
+ * (Eq. prolongation, Sec. 5.1 "Prolongation"): e is a DEVICE Q1 vector of
+ * level 0 or NULL; u (in/out when e != NULL). traces: DEVICE output
+ * [ncell][2d faces][2][q^(d-1)] doubles, face = 2*axis + (0 low, 1 high end),
+ * component 0 = value, 1 = derivative along +axis; face node index = the
+ * remaining axes, lowest axis fastest. FP64.
+ */
+int dgmg_project(dgmg_ctx *ctx, double *u, const double *e, double *traces, void *stream);
+
+/*
+ * Residual r = b - A u and p-restriction rc = P^T r (Alg. 6, the restriction
+ * fused into the residual traversal), given the projections `traces` of u
+ * (layout of dgmg_project). r may be NULL (not written); rc (DEVICE Q1 vector
+ * of level 0) may be NULL. FP64.
+ */
+int dgmg_residual_restrict(dgmg_ctx *ctx, const double *u, const double *b,
+                           const double *traces, double *r, double *rc, void *stream);
+
+/* Q1 level `level` (0 = first Q1 level): `nsteps` damped point-Jacobi steps
+ * u <- u + omega_cg D^{-1}(b - A_l u) (Sec. 2.4), FP64, u in/out. */
+int dgmg_cg_smooth(dgmg_ctx *ctx, int level, double *u, const double *b, int nsteps,
+                   void *stream);
+
+/* Q1 level `level`: r = b - A_l u. */
+int dgmg_cg_residual(dgmg_ctx *ctx, int level, const double *u, const double *b, double *r,
+                     void *stream);
+
+/* h-restriction rc = P_h^T rf from level `level` to level+1 (Sec. 5.2). */
+int dgmg_h_restrict(dgmg_ctx *ctx, int level, const double *rf, double *rc, void *stream);
+
+/* h-prolongation uf += P_h ec from level+1 to level `level`. */
+int dgmg_h_prolong(dgmg_ctx *ctx, int level, const double *ec, double *uf, void *stream);
+
+/* Coarsest-level solve e = A_c^{-1} r (dense, FP64; Alg. 6 coarse solve). */
+int dgmg_coarse_solve(dgmg_ctx *ctx, const double *r, double *e, void *stream);
+
+/* Unknowns of Q1 level `level` (HOST query). */
+int64_t dgmg_cg_size(const dgmg_ctx *ctx, int level);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DGMG_H */

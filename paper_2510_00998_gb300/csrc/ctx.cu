@@ -1,0 +1,1122 @@
+// libdgmg context: hierarchy set-up on the host, device buffers, the stage
+// entry points, the hp V-cycle and the FP64 preconditioned CG solve.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "internal.h"
+
+namespace dgmg {
+
+// ------------------------------------------------------------------- errors
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+int fail(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    g_last_error = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+    return DGMG_ECUDA;
+}
+
+// ---------------------------------------------------------- host threading
+template <typename F>
+static void parallel_for(int64_t n, F f) {
+    unsigned nt = std::thread::hardware_concurrency();
+    nt = std::max(1u, std::min(nt, 64u));
+    if (n < 4096 || nt == 1) {
+        for (int64_t i = 0; i < n; ++i) f(i);
+        return;
+    }
+    std::vector<std::thread> th;
+    const int64_t chunk = (n + nt - 1) / nt;
+    for (unsigned k = 0; k < nt; ++k) {
+        const int64_t a = k * chunk, b = std::min(n, a + chunk);
+        if (a >= b) break;
+        th.emplace_back([=, &f]() {
+            for (int64_t i = a; i < b; ++i) f(i);
+        });
+    }
+    for (auto &t : th) t.join();
+}
+
+// --------------------------------------------------------------- Q1 levels
+// One continuous Q1 level on the host: stencils (SoA [3^d][nv]) and the
+// per-axis transfer tables to the next coarser level.
+struct CGLevelHost {
+    int n[3] = {1, 1, 1};   // cells per axis
+    int m[3] = {1, 1, 1};   // interior vertices per axis
+    int64_t nv = 0;
+    std::vector<double> st;
+    // transfer to the next level (empty on the coarsest)
+    int mc[3] = {1, 1, 1};
+    std::vector<int> pl_lo[3], pl_hi[3], rs_start[3], rs_cnt[3];
+    std::vector<double> pl_wlo[3], pl_whi[3], rs_w[3];
+};
+
+static std::vector<int> coarse_positions(int n, int f) {
+    std::vector<int> pos;
+    for (int i = 0; i < n; i += f) pos.push_back(i);
+    pos.push_back(n);
+    return pos;
+}
+
+static bool can_coarsen(int n, int f) { return n > f; }
+
+// Per-axis nested Q1 interpolation tables between n fine cells and the coarse
+// axis (coarse vertices at fine indices 0, f, 2f, ..., n).
+static void axis_tables(int n, int f, CGLevelHost &L, int a, int &nc) {
+    const int mf = n - 1;
+    L.pl_lo[a].assign(mf, -1);
+    L.pl_hi[a].assign(mf, -1);
+    L.pl_wlo[a].assign(mf, 0.0);
+    L.pl_whi[a].assign(mf, 0.0);
+    if (!can_coarsen(n, f)) {
+        nc = n;
+        for (int i = 0; i < mf; ++i) {
+            L.pl_lo[a][i] = i;
+            L.pl_wlo[a][i] = 1.0;
+        }
+        L.rs_start[a].resize(mf);
+        L.rs_cnt[a].assign(mf, 1);
+        L.rs_w[a].assign(mf * 5, 0.0);
+        for (int i = 0; i < mf; ++i) {
+            L.rs_start[a][i] = i;
+            L.rs_w[a][i * 5] = 1.0;
+        }
+        return;
+    }
+    const std::vector<int> pos = coarse_positions(n, f);
+    nc = (int)pos.size() - 1;
+    for (int i = 1; i < n; ++i) {           // fine interior vertex i
+        int j = 0;
+        while (!(pos[j] <= i && i < pos[j + 1])) ++j;
+        const double wlo = double(pos[j + 1] - i) / double(pos[j + 1] - pos[j]);
+        const double whi = double(i - pos[j]) / double(pos[j + 1] - pos[j]);
+        if (j >= 1 && wlo != 0.0) {
+            L.pl_lo[a][i - 1] = j - 1;
+            L.pl_wlo[a][i - 1] = wlo;
+        }
+        if (j + 1 <= nc - 1 && whi != 0.0) {
+            L.pl_hi[a][i - 1] = j;               // coarse vertex j+1 -> interior index j
+            L.pl_whi[a][i - 1] = whi;
+        }
+    }
+    const int mcv = nc - 1;
+    L.rs_start[a].assign(mcv, 0);
+    L.rs_cnt[a].assign(mcv, 0);
+    L.rs_w[a].assign(mcv * 5, 0.0);
+    for (int J = 1; J < nc; ++J) {
+        const int lo = pos[J - 1], mid = pos[J], hi = pos[J + 1];
+        L.rs_start[a][J - 1] = lo;              // fine vertex lo+1 -> interior index lo
+        int k = 0;
+        for (int i = lo + 1; i < hi; ++i, ++k) {
+            const double w = i <= mid ? double(i - lo) / double(mid - lo) : double(hi - i) / double(hi - mid);
+            L.rs_w[a][(J - 1) * 5 + k] = w;
+        }
+        L.rs_cnt[a][J - 1] = k;
+    }
+}
+
+static int stencil_size(int dim) { return dim == 3 ? 27 : 9; }
+
+// Level 0: the kappa-weighted Q1 stiffness on the interior vertices, which equals
+// P^T A P for the SIPG operator A (all facet terms vanish on continuous functions
+// that are zero on the boundary, Sec. 2.4). Element matrix per cell:
+// sum over axes of K1 (x) M1 (x) M1 with K1 = (1/h)[1 -1; -1 1], M1 = (h/6)[2 1; 1 2].
+static void build_level0(int dim, const int *n, const std::vector<double> &kappa, CGLevelHost &L) {
+    const int NS = stencil_size(dim);
+    for (int a = 0; a < 3; ++a) {
+        L.n[a] = a < dim ? n[a] : 1;
+        L.m[a] = a < dim ? n[a] - 1 : 1;
+    }
+    L.nv = (int64_t)L.m[0] * L.m[1] * L.m[2];
+    L.st.assign((size_t)NS * L.nv, 0.0);
+    const int nc = 1 << dim;
+    double h[3] = {1.0 / n[0], 1.0 / n[1], dim == 3 ? 1.0 / n[2] : 1.0};
+    std::vector<double> Ke(nc * nc, 0.0);
+    for (int A = 0; A < nc; ++A)
+        for (int B = 0; B < nc; ++B) {
+            double s = 0.0;
+            for (int k = 0; k < dim; ++k) {
+                double t = 1.0;
+                for (int a = 0; a < dim; ++a) {
+                    const int ia = (A >> a) & 1, ib = (B >> a) & 1;
+                    if (a == k)
+                        t *= (ia == ib ? 1.0 : -1.0) / h[a];
+                    else
+                        t *= (ia == ib ? 2.0 : 1.0) * h[a] / 6.0;
+                }
+                s += t;
+            }
+            Ke[A * nc + B] = s;
+        }
+    // gather per vertex (no races): vertex v collects from its 2^d cells
+    parallel_for(L.nv, [&](int64_t v) {
+        int c[3] = {(int)(v % L.m[0]), (int)((v / L.m[0]) % L.m[1]), (int)(v / ((int64_t)L.m[0] * L.m[1]))};
+        int vv[3] = {c[0] + 1, c[1] + 1, c[2] + 1};   // vertex index per axis
+        for (int a = 0; a < nc; ++a) {
+            // cell with lower corner vv - 1 + a; the vertex is its corner A = ~a
+            int cc[3] = {0, 0, 0};
+            for (int d = 0; d < dim; ++d) cc[d] = vv[d] - 1 + ((a >> d) & 1);
+            const int64_t cell = cc[0] + (int64_t)n[0] * (cc[1] + (dim == 3 ? (int64_t)n[1] * cc[2] : 0));
+            const int A = (~a) & (nc - 1);
+            for (int B = 0; B < nc; ++B) {
+                int w[3] = {1, 1, 1}, off[3] = {0, 0, 0};
+                bool inside = true;
+                for (int d = 0; d < dim; ++d) {
+                    w[d] = cc[d] + ((B >> d) & 1);
+                    off[d] = w[d] - vv[d];
+                    inside = inside && w[d] >= 1 && w[d] <= n[d] - 1;
+                }
+                if (!inside) continue;
+                const int k = (off[0] + 1) + 3 * (off[1] + 1) + (dim == 3 ? 9 * (off[2] + 1) : 0);
+                L.st[(size_t)k * L.nv + v] += kappa[cell] * Ke[A * nc + B];
+            }
+        }
+    });
+}
+
+// Galerkin coarsening A_c = P_h^T A_f P_h on stencils (row I of A_c gathered
+// from the fine children of I; the coarse stencil stays 3^d-point).
+static void build_coarse(int dim, CGLevelHost &F, CGLevelHost &C) {
+    const int NS = stencil_size(dim);
+    for (int a = 0; a < 3; ++a) {
+        C.n[a] = a < dim ? F.mc[a] : 1;
+        C.m[a] = a < dim ? F.mc[a] - 1 : 1;
+    }
+    C.nv = (int64_t)C.m[0] * C.m[1] * C.m[2];
+    C.st.assign((size_t)NS * C.nv, 0.0);
+    parallel_for(C.nv, [&](int64_t I) {
+        int Ic[3] = {(int)(I % C.m[0]), (int)((I / C.m[0]) % C.m[1]), (int)(I / ((int64_t)C.m[0] * C.m[1]))};
+        int st0[3], cnt[3];
+        for (int a = 0; a < 3; ++a) {
+            if (a < dim) {
+                st0[a] = F.rs_start[a][Ic[a]];
+                cnt[a] = F.rs_cnt[a][Ic[a]];
+            } else {
+                st0[a] = 0;
+                cnt[a] = 1;
+            }
+        }
+        double acc[27] = {0};
+        for (int kz = 0; kz < cnt[2]; ++kz)
+            for (int ky = 0; ky < cnt[1]; ++ky)
+                for (int kx = 0; kx < cnt[0]; ++kx) {
+                    const int fi[3] = {st0[0] + kx, st0[1] + ky, st0[2] + kz};
+                    double wi = F.rs_w[0][Ic[0] * 5 + kx] * F.rs_w[1][Ic[1] * 5 + ky];
+                    if (dim == 3) wi *= F.rs_w[2][Ic[2] * 5 + kz];
+                    const int64_t iv = fi[0] + (int64_t)F.m[0] * (fi[1] + (int64_t)F.m[1] * fi[2]);
+                    for (int s = 0; s < NS; ++s) {
+                        const int so[3] = {s % 3 - 1, (s / 3) % 3 - 1, dim == 3 ? s / 9 - 1 : 0};
+                        int fj[3];
+                        bool inside = true;
+                        for (int a = 0; a < 3; ++a) {
+                            fj[a] = fi[a] + so[a];
+                            if (a < dim) inside = inside && fj[a] >= 0 && fj[a] < F.m[a];
+                        }
+                        if (!inside) continue;
+                        const double Aij = F.st[(size_t)s * F.nv + iv];
+                        if (Aij == 0.0) continue;
+                        // coarse parents of fine vertex j
+                        int par[3][2];
+                        double pw[3][2];
+                        for (int a = 0; a < 3; ++a) {
+                            if (a < dim) {
+                                par[a][0] = F.pl_lo[a][fj[a]];
+                                pw[a][0] = F.pl_wlo[a][fj[a]];
+                                par[a][1] = F.pl_hi[a][fj[a]];
+                                pw[a][1] = F.pl_whi[a][fj[a]];
+                            } else {
+                                par[a][0] = 0;
+                                pw[a][0] = 1.0;
+                                par[a][1] = -1;
+                                pw[a][1] = 0.0;
+                            }
+                        }
+                        for (int z = 0; z < 2; ++z) {
+                            if (par[2][z] < 0) continue;
+                            for (int y = 0; y < 2; ++y) {
+                                if (par[1][y] < 0) continue;
+                                for (int x = 0; x < 2; ++x) {
+                                    if (par[0][x] < 0) continue;
+                                    const int o[3] = {par[0][x] - Ic[0], par[1][y] - Ic[1], par[2][z] - Ic[2]};
+                                    const int k = (o[0] + 1) + 3 * (o[1] + 1) + (dim == 3 ? 9 * (o[2] + 1) : 0);
+                                    acc[k] += wi * Aij * pw[0][x] * pw[1][y] * pw[2][z];
+                                }
+                            }
+                        }
+                    }
+                }
+        for (int s = 0; s < NS; ++s) C.st[(size_t)s * C.nv + I] = acc[s];
+    });
+}
+
+}  // namespace dgmg
+
+using namespace dgmg;
+
+// ---------------------------------------------------------------- context
+template <typename T>
+struct DGDev {
+    DGConst<T> c;
+    T *kappa = nullptr, *fd = nullptr, *tr[2] = {nullptr, nullptr}, *corners = nullptr;
+};
+
+template <typename T>
+struct CGDev {
+    CGLevelDev<T> L;
+    T *st = nullptr;
+    T *u[2] = {nullptr, nullptr}, *b = nullptr, *r = nullptr;
+    int *itab = nullptr;
+    T *wtab = nullptr;
+};
+
+struct dgmg_ctx {
+    int dim = 0, p = 0, q = 0;
+    int n[3] = {1, 1, 1};
+    int64_t ncell = 0, ndof = 0, nloc = 0;
+    dgmg_opts opts;
+    RefElem1D re;
+    int cpb = 8;
+    std::vector<CGLevelHost> lv;
+    int64_t ncoarse = 0;
+    double *coarse_inv = nullptr;
+    DGDev<double> d64;
+    DGDev<float> d32;
+    std::vector<CGDev<double>> cg64;
+    std::vector<CGDev<float>> cg32;
+    // work vectors
+    float *r32 = nullptr, *z32 = nullptr;
+    double *w_r = nullptr, *w_z = nullptr, *w_p = nullptr, *w_q = nullptr, *w_rold = nullptr;
+    double *w_b = nullptr, *w_x = nullptr;        // dgmg_solve_host staging
+    double *scal = nullptr, *partials = nullptr;  // device scalars
+    double *host_scal = nullptr;                  // pinned
+    double *quad_x1 = nullptr, *quad_V = nullptr, *quad_w = nullptr;
+    std::vector<void *> allocs;
+    size_t bytes = 0;
+
+    template <typename T>
+    int alloc(T **ptr, size_t count) {
+        *ptr = nullptr;
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMalloc((void **)ptr, count * sizeof(T));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(DGMG_ENOMEM, std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) +
+                                         " bytes failed: " + cudaGetErrorString(e));
+        }
+        allocs.push_back(*ptr);
+        bytes += count * sizeof(T);
+        return DGMG_OK;
+    }
+    template <typename T>
+    int upload(T **ptr, const std::vector<T> &h) {
+        int rc = alloc(ptr, h.size());
+        if (rc) return rc;
+        if (!h.empty()) DG_CUDA(cudaMemcpy(*ptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+        return DGMG_OK;
+    }
+    ~dgmg_ctx() {
+        for (void *p : allocs) cudaFree(p);
+        if (host_scal) cudaFreeHost(host_scal);
+    }
+};
+
+// slots of ctx->scal
+enum { S_RZ = 0, S_PQ = 1, S_BETA = 2, S_RR = 3, S_RZN = 4, S_RZO = 5, S_BB = 6, S_ZZ = 7, S_NSCAL = 16 };
+
+namespace {
+
+#define RC(x)                        \
+    do {                             \
+        int rc_ = (x);               \
+        if (rc_ != DGMG_OK) return rc_; \
+    } while (0)
+
+#define LC(x)                                             \
+    do {                                                  \
+        cudaError_t e_ = (x);                             \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #x);  \
+    } while (0)
+
+template <typename T>
+void fill_const(const dgmg_ctx &C, DGConst<T> &c) {
+    std::memset(&c, 0, sizeof(c));
+    const int q = C.q;
+    for (int a = 0; a < 3; ++a) c.n[a] = C.n[a];
+    c.ncell = C.ncell;
+    for (int a = 0; a < C.dim; ++a) {
+        const double h = 1.0 / C.n[a];
+        for (int i = 0; i < q * q; ++i) {
+            c.M[a][i] = (T)(C.re.M[i] * h / 2.0);
+            c.K[a][i] = (T)(C.re.K[i] * 2.0 / h);
+        }
+        for (int i = 0; i < q; ++i) {
+            c.d0[a][i] = (T)(C.re.d0[i] * 2.0 / h);
+            c.dp[a][i] = (T)(C.re.dp[i] * 2.0 / h);
+        }
+        c.gamma[a] = (T)(2.0 * C.p * (C.p + 1) / h);
+    }
+    for (int i = 0; i < q; ++i) {
+        c.hat[0][i] = (T)((1.0 - C.re.nodes[i]) / 2.0);
+        c.hat[1][i] = (T)((1.0 + C.re.nodes[i]) / 2.0);
+    }
+    c.omega = (T)C.opts.omega_dg;
+}
+
+// Per-cell fast-diagonalisation factors of the exact diagonal block:
+// Kt_a = kappa_K K_a + low-face and high-face own terms (Sec. 4.1 Schur block),
+// Kt_a S = M_a S diag(lambda), S^T M_a S = I.
+void fast_diag_factors(const dgmg_ctx &C, const std::vector<double> &kappa, std::vector<double> &fd) {
+    const int q = C.q, dim = C.dim, fds = q * q + q;
+    fd.assign((size_t)C.ncell * dim * fds, 0.0);
+    double Linv[3][QMAX * QMAX];
+    double Mh[3][QMAX * QMAX], Kh[3][QMAX * QMAX], d0[3][QMAX], dp[3][QMAX], gam[3];
+    for (int a = 0; a < dim; ++a) {
+        const double h = 1.0 / C.n[a];
+        for (int i = 0; i < q * q; ++i) {
+            Mh[a][i] = C.re.M[i] * h / 2.0;
+            Kh[a][i] = C.re.K[i] * 2.0 / h;
+        }
+        for (int i = 0; i < q; ++i) {
+            d0[a][i] = C.re.d0[i] * 2.0 / h;
+            dp[a][i] = C.re.dp[i] * 2.0 / h;
+        }
+        gam[a] = 2.0 * C.p * (C.p + 1) / h;
+        cholesky_inverse_lower(q, Mh[a], Linv[a]);
+    }
+    const bool interior_only = C.opts.block_inverse == DGMG_BLOCK_INTERIOR_ONLY;
+    bool uniform = true;
+    for (int64_t i = 1; i < C.ncell; ++i)
+        if (kappa[i] != kappa[0]) {
+            uniform = false;
+            break;
+        }
+    auto factor = [&](int a, double kK, double kL, double wL, double kR, double wR, double *out) {
+        double Kt[QMAX * QMAX];
+        for (int i = 0; i < q; ++i)
+            for (int j = 0; j < q; ++j) {
+                const double e0i = i == 0, e0j = j == 0, epi = i == q - 1, epj = j == q - 1;
+                double v = kK * Kh[a][i * q + j];
+                v += kL * (wL * (e0i * d0[a][j] + d0[a][i] * e0j) + gam[a] * e0i * e0j);
+                v += kR * (-wR * (epi * dp[a][j] + dp[a][i] * epj) + gam[a] * epi * epj);
+                Kt[i * q + j] = v;
+            }
+        gen_eig_sym(q, Kt, Linv[a], out, out + q * q);
+    };
+    auto cell_factors = [&](int64_t cell, double *dst) {
+        int ci[3] = {(int)(cell % C.n[0]), (int)((cell / C.n[0]) % C.n[1]),
+                     (int)(cell / ((int64_t)C.n[0] * C.n[1]))};
+        const double kK = kappa[cell];
+        for (int a = 0; a < dim; ++a) {
+            const int64_t stride = a == 0 ? 1 : (a == 1 ? C.n[0] : (int64_t)C.n[0] * C.n[1]);
+            double kL, wL, kR, wR;
+            if (interior_only) {
+                kL = kR = kK;
+                wL = wR = 0.5;
+            } else {
+                if (ci[a] > 0) {
+                    const double kN = kappa[cell - stride];
+                    kL = 2.0 * kK * kN / (kK + kN);
+                    wL = 0.5;
+                } else {
+                    kL = kK;
+                    wL = 1.0;
+                }
+                if (ci[a] < C.n[a] - 1) {
+                    const double kN = kappa[cell + stride];
+                    kR = 2.0 * kK * kN / (kK + kN);
+                    wR = 0.5;
+                } else {
+                    kR = kK;
+                    wR = 1.0;
+                }
+            }
+            factor(a, kK, kL, wL, kR, wR, dst + a * fds);
+        }
+    };
+    if (uniform) {
+        // at most four distinct 1D blocks per axis: interior, low boundary, high
+        // boundary, both (one cell along the axis)
+        std::vector<double> tab((size_t)dim * 4 * fds);
+        const double k = kappa[0];
+        for (int a = 0; a < dim; ++a)
+            for (int cls = 0; cls < 4; ++cls) {
+                const bool lo = (cls & 1) && !interior_only, hi = (cls & 2) && !interior_only;
+                factor(a, k, k, lo ? 1.0 : 0.5, k, hi ? 1.0 : 0.5, &tab[((size_t)a * 4 + cls) * fds]);
+            }
+        parallel_for(C.ncell, [&](int64_t cell) {
+            int ci[3] = {(int)(cell % C.n[0]), (int)((cell / C.n[0]) % C.n[1]),
+                         (int)(cell / ((int64_t)C.n[0] * C.n[1]))};
+            for (int a = 0; a < dim; ++a) {
+                const int cls = (ci[a] == 0 ? 1 : 0) | (ci[a] == C.n[a] - 1 ? 2 : 0);
+                std::memcpy(&fd[((size_t)cell * dim + a) * fds], &tab[((size_t)a * 4 + cls) * fds],
+                            sizeof(double) * fds);
+            }
+        });
+    } else {
+        parallel_for(C.ncell, [&](int64_t cell) { cell_factors(cell, &fd[(size_t)cell * dim * fds]); });
+    }
+}
+
+template <typename T>
+std::vector<T> convert(const std::vector<double> &v) {
+    return std::vector<T>(v.begin(), v.end());
+}
+
+template <typename T>
+int setup_dg(dgmg_ctx &C, DGDev<T> &D, const std::vector<double> &kappa, const std::vector<double> &fd) {
+    fill_const(C, D.c);
+    RC(C.upload(&D.kappa, convert<T>(kappa)));
+    RC(C.upload(&D.fd, convert<T>(fd)));
+    const int64_t tr = C.ncell * 2 * C.dim * 2 * (C.nloc / C.q);
+    RC(C.alloc(&D.tr[0], tr));
+    RC(C.alloc(&D.tr[1], tr));
+    RC(C.alloc(&D.corners, C.ncell * (1 << C.dim)));
+    return DGMG_OK;
+}
+
+template <typename T>
+int setup_cg(dgmg_ctx &C, std::vector<CGDev<T>> &out) {
+    const int nl = (int)C.lv.size();
+    out.resize(nl);
+    for (int l = 0; l < nl; ++l) {
+        CGLevelHost &H = C.lv[l];
+        CGDev<T> &D = out[l];
+        std::memset(&D.L, 0, sizeof(D.L));
+        for (int a = 0; a < 3; ++a) {
+            D.L.m[a] = H.m[a];
+            D.L.mc[a] = H.mc[a] > 0 ? H.mc[a] - 1 : 0;
+        }
+        D.L.nv = H.nv;
+        RC(C.upload(&D.st, convert<T>(H.st)));
+        D.L.st = D.st;
+        RC(C.alloc(&D.u[0], H.nv));
+        RC(C.alloc(&D.u[1], H.nv));
+        RC(C.alloc(&D.b, H.nv));
+        RC(C.alloc(&D.r, H.nv));
+        if (l + 1 < nl) {
+            std::vector<int> it;
+            std::vector<double> wt;
+            size_t off_i[3][4], off_w[3][3];
+            for (int a = 0; a < C.dim; ++a) {
+                off_i[a][0] = it.size();
+                it.insert(it.end(), H.pl_lo[a].begin(), H.pl_lo[a].end());
+                off_i[a][1] = it.size();
+                it.insert(it.end(), H.pl_hi[a].begin(), H.pl_hi[a].end());
+                off_i[a][2] = it.size();
+                it.insert(it.end(), H.rs_start[a].begin(), H.rs_start[a].end());
+                off_i[a][3] = it.size();
+                it.insert(it.end(), H.rs_cnt[a].begin(), H.rs_cnt[a].end());
+                off_w[a][0] = wt.size();
+                wt.insert(wt.end(), H.pl_wlo[a].begin(), H.pl_wlo[a].end());
+                off_w[a][1] = wt.size();
+                wt.insert(wt.end(), H.pl_whi[a].begin(), H.pl_whi[a].end());
+                off_w[a][2] = wt.size();
+                wt.insert(wt.end(), H.rs_w[a].begin(), H.rs_w[a].end());
+            }
+            RC(C.upload(&D.itab, it));
+            RC(C.upload(&D.wtab, convert<T>(wt)));
+            for (int a = 0; a < C.dim; ++a) {
+                D.L.pl_lo[a] = D.itab + off_i[a][0];
+                D.L.pl_hi[a] = D.itab + off_i[a][1];
+                D.L.rs_start[a] = D.itab + off_i[a][2];
+                D.L.rs_cnt[a] = D.itab + off_i[a][3];
+                D.L.pl_wlo[a] = D.wtab + off_w[a][0];
+                D.L.pl_whi[a] = D.wtab + off_w[a][1];
+                D.L.rs_w[a] = D.wtab + off_w[a][2];
+            }
+            for (int a = 0; a < 3; ++a) D.L.mc[a] = a < C.dim ? H.mc[a] - 1 : 1;
+        }
+    }
+    return DGMG_OK;
+}
+
+// dense inverse of the coarsest operator via Cholesky (FP64, host)
+int coarse_inverse(dgmg_ctx &C) {
+    const CGLevelHost &L = C.lv.back();
+    const int64_t nc = L.nv;
+    if (nc > 4096) return fail(DGMG_EINVAL, "coarsest level has more than 4096 unknowns");
+    C.ncoarse = nc;
+    std::vector<double> A((size_t)nc * nc, 0.0);
+    const int NS = stencil_size(C.dim);
+    for (int64_t v = 0; v < nc; ++v) {
+        int c[3] = {(int)(v % L.m[0]), (int)((v / L.m[0]) % L.m[1]), (int)(v / ((int64_t)L.m[0] * L.m[1]))};
+        for (int s = 0; s < NS; ++s) {
+            const int o[3] = {s % 3 - 1, (s / 3) % 3 - 1, C.dim == 3 ? s / 9 - 1 : 0};
+            int w[3];
+            bool inside = true;
+            for (int a = 0; a < 3; ++a) {
+                w[a] = c[a] + o[a];
+                inside = inside && w[a] >= 0 && w[a] < L.m[a];
+            }
+            if (!inside) continue;
+            const int64_t wi = w[0] + (int64_t)L.m[0] * (w[1] + (int64_t)L.m[1] * w[2]);
+            A[v * nc + wi] += L.st[(size_t)s * L.nv + v];
+        }
+    }
+    // Cholesky A = L L^T in place (lower)
+    std::vector<double> Lc((size_t)nc * nc, 0.0);
+    for (int64_t j = 0; j < nc; ++j) {
+        double s = A[j * nc + j];
+        for (int64_t k = 0; k < j; ++k) s -= Lc[j * nc + k] * Lc[j * nc + k];
+        if (!(s > 0.0)) return fail(DGMG_EINVAL, "coarsest operator is not positive definite");
+        Lc[j * nc + j] = std::sqrt(s);
+        for (int64_t i = j + 1; i < nc; ++i) {
+            double t = A[i * nc + j];
+            for (int64_t k = 0; k < j; ++k) t -= Lc[i * nc + k] * Lc[j * nc + k];
+            Lc[i * nc + j] = t / Lc[j * nc + j];
+        }
+    }
+    // inverse column by column: solve L y = e_c, L^T x = y
+    std::vector<double> inv((size_t)nc * nc, 0.0), y(nc);
+    for (int64_t c = 0; c < nc; ++c) {
+        for (int64_t i = 0; i < nc; ++i) {
+            double s = (i == c) ? 1.0 : 0.0;
+            for (int64_t k = 0; k < i; ++k) s -= Lc[i * nc + k] * y[k];
+            y[i] = s / Lc[i * nc + i];
+        }
+        for (int64_t i = nc - 1; i >= 0; --i) {
+            double s = y[i];
+            for (int64_t k = i + 1; k < nc; ++k) s -= Lc[k * nc + i] * inv[k * nc + c];
+            inv[i * nc + c] = s / Lc[i * nc + i];
+        }
+    }
+    return C.upload(&C.coarse_inv, inv);
+}
+
+// ------------------------------------------------------------ V-cycle
+template <typename T>
+DGDev<T> &dg(dgmg_ctx &C);
+template <>
+DGDev<double> &dg<double>(dgmg_ctx &C) { return C.d64; }
+template <>
+DGDev<float> &dg<float>(dgmg_ctx &C) { return C.d32; }
+template <typename T>
+std::vector<CGDev<T>> &cgl(dgmg_ctx &C);
+template <>
+std::vector<CGDev<double>> &cgl<double>(dgmg_ctx &C) { return C.cg64; }
+template <>
+std::vector<CGDev<float>> &cgl<float>(dgmg_ctx &C) { return C.cg32; }
+
+// h-multigrid V-cycle on Q1 level l with zero initial guess; RHS in cg[l].b.
+// Returns the buffer holding the result.
+template <typename T>
+int cg_vcycle(dgmg_ctx &C, int l, cudaStream_t s, T **result) {
+    auto &lv = cgl<T>(C);
+    CGDev<T> &L = lv[l];
+    const T om = (T)C.opts.omega_cg;
+    if (l == (int)lv.size() - 1) {
+        LC(launch_coarse_solve<T>(L.L.nv, C.coarse_inv, L.b, L.u[0], s));
+        *result = L.u[0];
+        return DGMG_OK;
+    }
+    int cur = 0;
+    bool zero = true;
+    for (int k = 0; k < C.opts.nu_pre; ++k) {
+        LC(launch_cg_jacobi<T>(C.dim, L.L, L.u[cur], L.b, L.u[cur ^ 1], om, zero, s));
+        zero = false;
+        cur ^= 1;
+    }
+    if (zero) {
+        LC(cudaMemsetAsync(L.u[cur], 0, sizeof(T) * L.L.nv, s));
+        zero = false;
+    }
+    LC(launch_cg_residual<T>(C.dim, L.L, L.u[cur], L.b, L.r, s));
+    LC(launch_h_restrict<T>(C.dim, L.L, L.r, lv[l + 1].b, s));
+    T *ec = nullptr;
+    RC(cg_vcycle<T>(C, l + 1, s, &ec));
+    LC(launch_h_prolong<T>(C.dim, L.L, ec, L.u[cur], s));
+    for (int k = 0; k < C.opts.nu_post; ++k) {
+        LC(launch_cg_jacobi<T>(C.dim, L.L, L.u[cur], L.b, L.u[cur ^ 1], om, false, s));
+        cur ^= 1;
+    }
+    *result = L.u[cur];
+    return DGMG_OK;
+}
+
+// z = V(r) on the DG level in precision T (zero initial guess).
+template <typename T>
+int dg_vcycle(dgmg_ctx &C, const T *r, T *z, cudaStream_t s) {
+    DGDev<T> &D = dg<T>(C);
+    const int64_t trn = C.ncell * 2 * C.dim * 2 * (C.nloc / C.q);
+    LC(cudaMemsetAsync(z, 0, sizeof(T) * C.ndof, s));
+    LC(cudaMemsetAsync(D.tr[0], 0, sizeof(T) * trn, s));   // projections of z = 0
+    int cur = 0;
+    for (int k = 0; k < C.opts.nu_pre; ++k) {
+        LC(launch_smooth<T>(C.dim, C.q, D.c, C.cpb, z, r, D.kappa, D.fd, D.tr[cur], D.tr[cur ^ 1], s));
+        cur ^= 1;
+    }
+    LC(launch_residual<T>(C.dim, C.q, D.c, C.cpb, RES_HAS_B | RES_CORNERS, z, r, D.kappa, D.tr[cur], nullptr,
+                          D.corners, s));
+    auto &lv = cgl<T>(C);
+    LC(launch_corner_gather<T>(C.dim, C.n, D.corners, lv[0].b, s));
+    T *e0 = nullptr;
+    RC(cg_vcycle<T>(C, 0, s, &e0));
+    LC(launch_project<T>(C.dim, C.q, D.c, C.cpb, z, e0, D.tr[0], s));   // z += P e0, projections
+    cur = 0;
+    for (int k = 0; k < C.opts.nu_post; ++k) {
+        LC(launch_smooth<T>(C.dim, C.q, D.c, C.cpb, z, r, D.kappa, D.fd, D.tr[cur], D.tr[cur ^ 1], s));
+        cur ^= 1;
+    }
+    return DGMG_OK;
+}
+
+int vcycle64(dgmg_ctx &C, const double *r, double *z, cudaStream_t s) {
+    if (C.opts.precision == DGMG_MIXED_FP32) {
+        LC(launch_cast_d2f(C.ndof, r, C.r32, s));
+        RC(dg_vcycle<float>(C, C.r32, C.z32, s));
+        LC(launch_cast_f2d(C.ndof, C.z32, z, s));
+        return DGMG_OK;
+    }
+    return dg_vcycle<double>(C, r, z, s);
+}
+
+// y = A u (negate = false) or r = b - A u, FP64
+int apply64(dgmg_ctx &C, const double *u, const double *b, double *out, cudaStream_t s) {
+    DGDev<double> &D = C.d64;
+    LC(launch_project<double>(C.dim, C.q, D.c, C.cpb, const_cast<double *>(u), nullptr, D.tr[0], s));
+    const int mode = b ? (RES_HAS_B | RES_WRITE_R) : (RES_WRITE_R | RES_NEGATE);
+    LC(launch_residual<double>(C.dim, C.q, D.c, C.cpb, mode, u, b, D.kappa, D.tr[0], out, nullptr, s));
+    return DGMG_OK;
+}
+
+// beta of the CG direction update (Fletcher-Reeves, or Polak-Ribiere for the
+// flexible variant) and the shift of <r,z>, on the device
+__global__ void k_scalar_beta(double *scal, int flexible) {
+    const double rzn = scal[S_RZN];
+    scal[S_BETA] = flexible ? (rzn - scal[S_RZO]) / scal[S_RZ] : rzn / scal[S_RZ];
+    scal[S_RZ] = rzn;
+}
+
+int check_ctx(const dgmg_ctx *C) {
+    if (!C) return fail(DGMG_EINVAL, "ctx is NULL");
+    return DGMG_OK;
+}
+
+}  // namespace
+
+// ============================================================== C ABI
+extern "C" {
+
+const char *dgmg_version(void) { return "libdgmg 0.1 (sm_103a)"; }
+
+const char *dgmg_last_error(void) { return g_last_error.c_str(); }
+
+void dgmg_default_opts(dgmg_opts *o) {
+    if (!o) return;
+    o->omega_dg = 0.8;
+    o->omega_cg = 0.8;
+    o->nu_pre = 2;
+    o->nu_post = 2;
+    o->precision = DGMG_FP64;
+    o->block_inverse = DGMG_BLOCK_EXACT;
+    o->coarsening = 2;
+    o->rtol = 1e-10;
+    o->maxit = 200;
+}
+
+int dgmg_create(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_opts *opts, dgmg_ctx **out) {
+    if (!out) return fail(DGMG_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!mesh) return fail(DGMG_EINVAL, "mesh is NULL");
+    if (mesh->dim != 2 && mesh->dim != 3) return fail(DGMG_EINVAL, "mesh->dim must be 2 or 3");
+    if (p < 1 || p > PMAX) return fail(DGMG_EINVAL, "p must be in 1..6");
+    for (int a = 0; a < mesh->dim; ++a)
+        if (mesh->n[a] < 2 || mesh->n[a] > (1 << 20))
+            return fail(DGMG_EINVAL, "every mesh->n[a] must be in 2..2^20");
+    dgmg_opts o;
+    dgmg_default_opts(&o);
+    if (opts) o = *opts;
+    if (!(o.omega_dg > 0 && o.omega_dg < 2) || !(o.omega_cg > 0 && o.omega_cg < 2))
+        return fail(DGMG_EINVAL, "omega_dg and omega_cg must be in (0, 2)");
+    if (o.nu_pre < 0 || o.nu_post < 0 || o.nu_pre > 64 || o.nu_post > 64)
+        return fail(DGMG_EINVAL, "nu_pre, nu_post must be in 0..64");
+    if (o.precision != DGMG_FP64 && o.precision != DGMG_MIXED_FP32) return fail(DGMG_EINVAL, "unknown precision");
+    if (o.block_inverse != DGMG_BLOCK_EXACT && o.block_inverse != DGMG_BLOCK_INTERIOR_ONLY)
+        return fail(DGMG_EINVAL, "unknown block_inverse");
+    if (o.coarsening != 2 && o.coarsening != 3) return fail(DGMG_EINVAL, "coarsening must be 2 or 3");
+    if (!(o.rtol > 0 && o.rtol < 1)) return fail(DGMG_EINVAL, "rtol must be in (0, 1)");
+    if (o.maxit < 1) return fail(DGMG_EINVAL, "maxit must be >= 1");
+
+    std::unique_ptr<dgmg_ctx> C(new dgmg_ctx());
+    C->dim = mesh->dim;
+    C->p = p;
+    C->q = p + 1;
+    for (int a = 0; a < 3; ++a) C->n[a] = a < mesh->dim ? mesh->n[a] : 1;
+    C->ncell = (int64_t)C->n[0] * C->n[1] * C->n[2];
+    C->nloc = C->dim == 3 ? (int64_t)C->q * C->q * C->q : (int64_t)C->q * C->q;
+    C->ndof = C->ncell * C->nloc;
+    C->opts = o;
+    const int nf = (int)(C->nloc / C->q);
+    C->cpb = std::max(1, 128 / nf);
+    while (C->cpb * nf > 256) --C->cpb;
+
+    std::vector<double> kap(C->ncell, 1.0);
+    if (kappa) {
+        for (int64_t i = 0; i < C->ncell; ++i) {
+            if (!(kappa[i] > 0.0) || !std::isfinite(kappa[i]))
+                return fail(DGMG_EINVAL, "kappa must be positive and finite (cell " + std::to_string(i) + ")");
+            kap[i] = kappa[i];
+        }
+    }
+    C->re = make_refelem(p);
+
+    // Q1 hierarchy
+    C->lv.emplace_back();
+    build_level0(C->dim, C->n, kap, C->lv[0]);
+    const int f = o.coarsening;
+    for (;;) {
+        CGLevelHost &F = C->lv.back();
+        bool any = false;
+        for (int a = 0; a < C->dim; ++a) any = any || can_coarsen(F.n[a], f);
+        if (!any) break;
+        for (int a = 0; a < C->dim; ++a) {
+            int nc = 0;
+            axis_tables(F.n[a], f, F, a, nc);
+            F.mc[a] = nc;
+        }
+        CGLevelHost Cl;
+        build_coarse(C->dim, F, Cl);
+        C->lv.push_back(std::move(Cl));
+    }
+    RC(coarse_inverse(*C));
+
+    std::vector<double> fd;
+    fast_diag_factors(*C, kap, fd);
+    RC(setup_dg<double>(*C, C->d64, kap, fd));
+    RC(setup_cg<double>(*C, C->cg64));
+    if (o.precision == DGMG_MIXED_FP32) {
+        RC(setup_dg<float>(*C, C->d32, kap, fd));
+        RC(setup_cg<float>(*C, C->cg32));
+        RC(C->alloc(&C->r32, C->ndof));
+        RC(C->alloc(&C->z32, C->ndof));
+    }
+    RC(C->alloc(&C->w_r, C->ndof));
+    RC(C->alloc(&C->w_z, C->ndof));
+    RC(C->alloc(&C->w_p, C->ndof));
+    RC(C->alloc(&C->w_q, C->ndof));
+    RC(C->alloc(&C->w_rold, C->ndof));
+    RC(C->alloc(&C->scal, S_NSCAL));
+    RC(C->alloc(&C->partials, 2 * DOT_BLOCKS));
+    {
+        cudaError_t e = cudaMallocHost((void **)&C->host_scal, sizeof(double) * S_NSCAL);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
+    }
+    // quadrature tables for the load vector: (p+2) Gauss points per axis
+    {
+        const int mq = p + 2;
+        std::vector<double> xg, wg;
+        gauss_legendre(mq, xg, wg);
+        std::vector<double> V((size_t)C->q * mq), W((size_t)3 * mq);
+        std::vector<double> val(C->q);
+        for (int g = 0; g < mq; ++g) {
+            lagrange_at(C->re.nodes, xg[g], val.data(), nullptr);
+            for (int i = 0; i < C->q; ++i) V[(size_t)i * mq + g] = val[i];
+        }
+        for (int a = 0; a < 3; ++a)
+            for (int g = 0; g < mq; ++g) W[(size_t)a * mq + g] = wg[g] * 0.5 / C->n[a];
+        RC(C->upload(&C->quad_x1, xg));
+        RC(C->upload(&C->quad_V, V));
+        RC(C->upload(&C->quad_w, W));
+    }
+    DG_CUDA(cudaDeviceSynchronize());
+    *out = C.release();
+    return DGMG_OK;
+}
+
+int dgmg_destroy(dgmg_ctx *ctx) {
+    if (!ctx) return DGMG_OK;
+    cudaDeviceSynchronize();
+    delete ctx;
+    return DGMG_OK;
+}
+
+int dgmg_info(const dgmg_ctx *C, dgmg_info_t *info) {
+    RC(check_ctx(C));
+    if (!info) return fail(DGMG_EINVAL, "info is NULL");
+    std::memset(info, 0, sizeof(*info));
+    info->dim = C->dim;
+    info->p = C->p;
+    info->q = C->q;
+    for (int a = 0; a < 3; ++a) info->n[a] = C->n[a];
+    info->ncell = C->ncell;
+    info->ndof = C->ndof;
+    info->nlevels_cg = (int)C->lv.size();
+    info->nvert0 = C->lv[0].nv;
+    info->ncoarse = C->ncoarse;
+    info->omega_dg = C->opts.omega_dg;
+    info->omega_cg = C->opts.omega_cg;
+    info->nu_pre = C->opts.nu_pre;
+    info->nu_post = C->opts.nu_post;
+    info->precision = C->opts.precision;
+    info->block_inverse = C->opts.block_inverse;
+    info->coarsening = C->opts.coarsening;
+    info->device_bytes = C->bytes;
+    return DGMG_OK;
+}
+
+int dgmg_gll_nodes(const dgmg_ctx *C, double *nodes) {
+    RC(check_ctx(C));
+    if (!nodes) return fail(DGMG_EINVAL, "nodes is NULL");
+    for (int i = 0; i < C->q; ++i) nodes[i] = C->re.nodes[i];
+    return DGMG_OK;
+}
+
+int64_t dgmg_cg_size(const dgmg_ctx *C, int level) {
+    if (!C || level < 0 || level >= (int)C->lv.size()) return -1;
+    return C->lv[level].nv;
+}
+
+#define NEED(ptr) \
+    if (!(ptr)) return fail(DGMG_EINVAL, #ptr " is NULL")
+
+int dgmg_apply(dgmg_ctx *C, const double *u, double *y, void *stream) {
+    RC(check_ctx(C));
+    NEED(u);
+    NEED(y);
+    if (u == y) return fail(DGMG_EINVAL, "u and y must not overlap");
+    return apply64(*C, u, nullptr, y, (cudaStream_t)stream);
+}
+
+int dgmg_residual(dgmg_ctx *C, const double *u, const double *b, double *r, void *stream) {
+    RC(check_ctx(C));
+    NEED(u);
+    NEED(b);
+    NEED(r);
+    if (u == r) return fail(DGMG_EINVAL, "u and r must not overlap");
+    return apply64(*C, u, b, r, (cudaStream_t)stream);
+}
+
+int dgmg_smooth(dgmg_ctx *C, double *u, const double *b, int nsteps, void *stream) {
+    RC(check_ctx(C));
+    NEED(u);
+    NEED(b);
+    if (nsteps < 0) return fail(DGMG_EINVAL, "nsteps must be >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    DGDev<double> &D = C->d64;
+    LC(launch_project<double>(C->dim, C->q, D.c, C->cpb, u, nullptr, D.tr[0], s));
+    int cur = 0;
+    for (int k = 0; k < nsteps; ++k) {
+        LC(launch_smooth<double>(C->dim, C->q, D.c, C->cpb, u, b, D.kappa, D.fd, D.tr[cur], D.tr[cur ^ 1], s));
+        cur ^= 1;
+    }
+    return DGMG_OK;
+}
+
+int dgmg_vcycle(dgmg_ctx *C, const double *r, double *e, void *stream) {
+    RC(check_ctx(C));
+    NEED(r);
+    NEED(e);
+    if (r == e) return fail(DGMG_EINVAL, "r and e must not overlap");
+    return vcycle64(*C, r, e, (cudaStream_t)stream);
+}
+
+int dgmg_project(dgmg_ctx *C, double *u, const double *e, double *traces, void *stream) {
+    RC(check_ctx(C));
+    NEED(u);
+    NEED(traces);
+    LC(launch_project<double>(C->dim, C->q, C->d64.c, C->cpb, u, e, traces, (cudaStream_t)stream));
+    return DGMG_OK;
+}
+
+int dgmg_residual_restrict(dgmg_ctx *C, const double *u, const double *b, const double *traces, double *r,
+                           double *rc, void *stream) {
+    RC(check_ctx(C));
+    NEED(u);
+    NEED(b);
+    NEED(traces);
+    cudaStream_t s = (cudaStream_t)stream;
+    int mode = RES_HAS_B;
+    if (r) mode |= RES_WRITE_R;
+    if (rc) mode |= RES_CORNERS;
+    LC(launch_residual<double>(C->dim, C->q, C->d64.c, C->cpb, mode, u, b, C->d64.kappa, traces, r,
+                               C->d64.corners, s));
+    if (rc) LC(launch_corner_gather<double>(C->dim, C->n, C->d64.corners, rc, s));
+    return DGMG_OK;
+}
+
+static int check_level(dgmg_ctx *C, int level, bool need_next) {
+    RC(check_ctx(C));
+    if (level < 0 || level >= (int)C->lv.size() - (need_next ? 1 : 0))
+        return fail(DGMG_EINVAL, "level out of range");
+    return DGMG_OK;
+}
+
+int dgmg_cg_smooth(dgmg_ctx *C, int level, double *u, const double *b, int nsteps, void *stream) {
+    RC(check_level(C, level, false));
+    NEED(u);
+    NEED(b);
+    cudaStream_t s = (cudaStream_t)stream;
+    CGDev<double> &L = C->cg64[level];
+    for (int k = 0; k < nsteps; ++k) {
+        LC(launch_cg_jacobi<double>(C->dim, L.L, u, b, L.u[0], C->opts.omega_cg, false, s));
+        LC(cudaMemcpyAsync(u, L.u[0], sizeof(double) * L.L.nv, cudaMemcpyDeviceToDevice, s));
+    }
+    return DGMG_OK;
+}
+
+int dgmg_cg_residual(dgmg_ctx *C, int level, const double *u, const double *b, double *r, void *stream) {
+    RC(check_level(C, level, false));
+    NEED(u);
+    NEED(b);
+    NEED(r);
+    LC(launch_cg_residual<double>(C->dim, C->cg64[level].L, u, b, r, (cudaStream_t)stream));
+    return DGMG_OK;
+}
+
+int dgmg_h_restrict(dgmg_ctx *C, int level, const double *rf, double *rc, void *stream) {
+    RC(check_level(C, level, true));
+    NEED(rf);
+    NEED(rc);
+    LC(launch_h_restrict<double>(C->dim, C->cg64[level].L, rf, rc, (cudaStream_t)stream));
+    return DGMG_OK;
+}
+
+int dgmg_h_prolong(dgmg_ctx *C, int level, const double *ec, double *uf, void *stream) {
+    RC(check_level(C, level, true));
+    NEED(ec);
+    NEED(uf);
+    LC(launch_h_prolong<double>(C->dim, C->cg64[level].L, ec, uf, (cudaStream_t)stream));
+    return DGMG_OK;
+}
+
+int dgmg_coarse_solve(dgmg_ctx *C, const double *r, double *e, void *stream) {
+    RC(check_ctx(C));
+    NEED(r);
+    NEED(e);
+    LC(launch_coarse_solve<double>(C->ncoarse, C->coarse_inv, r, e, (cudaStream_t)stream));
+    return DGMG_OK;
+}
+
+int dgmg_quad_points(dgmg_ctx *C, double *xq, void *stream) {
+    RC(check_ctx(C));
+    NEED(xq);
+    LC(launch_quad_points(C->dim, C->q, C->n, C->p + 2, C->quad_x1, xq, C->ncell, (cudaStream_t)stream));
+    return DGMG_OK;
+}
+
+int dgmg_load_vector(dgmg_ctx *C, const double *fq, double *b, void *stream) {
+    RC(check_ctx(C));
+    NEED(fq);
+    NEED(b);
+    LC(launch_load_vector(C->dim, C->q, C->p + 2, C->ncell, C->quad_V, C->quad_w, fq, b, (cudaStream_t)stream));
+    return DGMG_OK;
+}
+
+// ----------------------------------------------------------------- solve
+static int read_scalar(dgmg_ctx *C, int slot, double *v, cudaStream_t s) {
+    LC(cudaMemcpyAsync(C->host_scal + slot, C->scal + slot, sizeof(double), cudaMemcpyDeviceToHost, s));
+    LC(cudaStreamSynchronize(s));
+    *v = C->host_scal[slot];
+    return DGMG_OK;
+}
+
+int dgmg_solve(dgmg_ctx *C, const double *b, double *x, dgmg_stats *stats, void *stream) {
+    RC(check_ctx(C));
+    NEED(b);
+    NEED(x);
+    if (b == x) return fail(DGMG_EINVAL, "b and x must not overlap");
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = C->ndof;
+    const bool flexible = C->opts.precision == DGMG_MIXED_FP32;
+    double *r = C->w_r, *z = C->w_z, *p = C->w_p, *q = C->w_q, *rold = C->w_rold;
+    double bb = 0.0, rr = 0.0, zz0 = 0.0, zz = 0.0;
+    RC(apply64(*C, x, b, r, s));                                 // r = b - A x
+    LC(launch_dot(n, b, b, C->partials, C->scal + S_BB, s));
+    RC(read_scalar(C, S_BB, &bb, s));
+    if (!std::isfinite(bb)) return fail(DGMG_ENONFINITE, "||b|| is not finite");
+    LC(launch_dot(n, r, r, C->partials, C->scal + S_RR, s));
+    RC(read_scalar(C, S_RR, &rr, s));
+    if (!std::isfinite(rr)) return fail(DGMG_ENONFINITE, "initial residual is not finite");
+    const double bn = std::sqrt(bb) > 0 ? std::sqrt(bb) : 1.0;
+    const double rtol = C->opts.rtol;
+    int it = 0;
+    int status = DGMG_OK;
+    double relrec = std::sqrt(rr) / bn;
+    if (relrec > rtol) {
+        RC(vcycle64(*C, r, z, s));
+        LC(launch_dot(n, r, z, C->partials, C->scal + S_RZ, s));
+        LC(launch_dot(n, z, z, C->partials, C->scal + S_ZZ, s));
+        RC(read_scalar(C, S_ZZ, &zz0, s));
+        LC(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        zz = zz0;
+        for (it = 1; it <= C->opts.maxit; ++it) {
+            RC(apply64(*C, p, nullptr, q, s));                   // q = A p
+            LC(launch_dot(n, p, q, C->partials, C->scal + S_PQ, s));
+            if (flexible) LC(cudaMemcpyAsync(rold, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+            LC(launch_pcg_update_xr(n, x, r, p, q, C->scal, s));   // alpha = rz / pq
+            LC(launch_dot(n, r, r, C->partials, C->scal + S_RR, s));
+            RC(read_scalar(C, S_RR, &rr, s));
+            if (!std::isfinite(rr)) {
+                status = fail(DGMG_ENONFINITE, "residual norm is not finite");
+                break;
+            }
+            relrec = std::sqrt(rr) / bn;
+            if (relrec <= rtol) break;
+            if (it == C->opts.maxit) {
+                status = fail(DGMG_ENOTCONVERGED, "maxit reached");
+                break;
+            }
+            RC(vcycle64(*C, r, z, s));
+            if (flexible)
+                LC(launch_dot2(n, r, z, rold, C->partials, C->scal + S_RZN, C->scal + S_RZO, s));
+            else
+                LC(launch_dot(n, r, z, C->partials, C->scal + S_RZN, s));
+            k_scalar_beta<<<1, 1, 0, s>>>(C->scal, flexible ? 1 : 0);
+            LC(cudaGetLastError());
+            LC(launch_pcg_update_p(n, p, z, C->scal, s));
+        }
+        if (it > C->opts.maxit) it = C->opts.maxit;
+        LC(launch_dot(n, z, z, C->partials, C->scal + S_ZZ, s));
+        RC(read_scalar(C, S_ZZ, &zz, s));
+    }
+    // true residual of the returned x
+    RC(apply64(*C, x, b, r, s));
+    LC(launch_dot(n, r, r, C->partials, C->scal + S_RR, s));
+    double rtrue = 0.0;
+    RC(read_scalar(C, S_RR, &rtrue, s));
+    if (stats) {
+        stats->iterations = it;
+        stats->rel_residual = std::sqrt(rtrue) / bn;
+        stats->rel_residual_recursive = relrec;
+        stats->prec_residual = zz0 > 0 ? std::sqrt(zz / zz0) : 0.0;
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return status;
+}
+
+int dgmg_solve_host(dgmg_ctx *C, const double *b_host, double *x_host, dgmg_stats *stats, void *stream) {
+    RC(check_ctx(C));
+    NEED(b_host);
+    NEED(x_host);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!C->w_b) {
+        RC(C->alloc(&C->w_b, C->ndof));
+        RC(C->alloc(&C->w_x, C->ndof));
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    LC(cudaMemcpyAsync(C->w_b, b_host, sizeof(double) * C->ndof, cudaMemcpyHostToDevice, s));
+    LC(cudaMemcpyAsync(C->w_x, x_host, sizeof(double) * C->ndof, cudaMemcpyHostToDevice, s));
+    const int rc = dgmg_solve(C, C->w_b, C->w_x, stats, stream);
+    if (rc != DGMG_OK && rc != DGMG_ENOTCONVERGED) return rc;
+    LC(cudaMemcpyAsync(x_host, C->w_x, sizeof(double) * C->ndof, cudaMemcpyDeviceToHost, s));
+    LC(cudaStreamSynchronize(s));
+    if (stats)
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,707 @@
+// DG-level kernels of the SIPG hp-multigrid path: warm-up projection (with the
+// fused p-prolongation), the single-touch block-Jacobi smoothing step and the
+// residual (with the fused p-restriction). Templated on dimension, nodes per
+// axis and arithmetic type; instantiated in dg_fp64.cu and dg_fp32.cu.
+//
+// Work decomposition. A CTA owns `cpb` consecutive cells; each cell is served
+// by q^(d-1) threads. In a "pass along axis a" thread t of a cell owns the
+// pencil of q nodes along axis a through the tangential position t (t = lower
+// remaining axis + q * upper remaining axis), loads it from shared memory into
+// registers, applies a q x q matrix and stores it back; a CTA barrier separates
+// passes along different axes. Face node t of the two faces normal to axis a
+// is the end of pencil t, so facet work maps onto the same threads.
+//
+// Trace layout (the projection variables of the paper's Technique 1, stored
+// per cell): tr[cell][face][comp][t], face = 2*axis + side (side 0 = low end,
+// 1 = high end), comp 0 = value u, comp 1 = derivative along +axis.
+#pragma once
+
+#include "internal.h"
+
+namespace dgmg {
+
+template <int DIM, int Q>
+struct Geo {
+    static constexpr int NL = DIM == 3 ? Q * Q * Q : Q * Q;   // nodes per cell
+    static constexpr int NF = NL / Q;                          // nodes per face = threads per cell
+    static constexpr int NFACE = 2 * DIM;
+    static constexpr int TR = NFACE * 2 * NF;                  // trace values per cell
+    static constexpr int NC = 1 << DIM;                        // corners per cell
+    static constexpr int FDS = Q * Q + Q;                      // fast-diag factors per axis
+    // volume index of node i of the pencil along `dir` at tangential position t
+    static __device__ __forceinline__ int vidx(int dir, int t, int i) {
+        if (DIM == 2) return dir == 0 ? i + Q * t : t + Q * i;
+        if (dir == 0) return i + Q * t;
+        if (dir == 1) return (t % Q) + Q * (i + Q * (t / Q));
+        return t + Q * Q * i;
+    }
+};
+
+template <int DIM>
+__device__ __forceinline__ void cell_coords(int64_t cell, const int *n, int *ci) {
+    ci[0] = (int)(cell % n[0]);
+    int64_t r = cell / n[0];
+    if (DIM == 3) {
+        ci[1] = (int)(r % n[1]);
+        ci[2] = (int)(r / n[1]);
+    } else {
+        ci[1] = (int)r;
+    }
+}
+
+template <int DIM>
+__device__ __forceinline__ int64_t axis_stride(const int *n, int dir) {
+    return dir == 0 ? 1 : (dir == 1 ? (int64_t)n[0] : (int64_t)n[0] * n[1]);
+}
+
+// Cooperative copy of `count` contiguous elements (all threads of the CTA).
+template <typename T>
+__device__ __forceinline__ void block_copy(T *__restrict__ dst, const T *__restrict__ src, int64_t count) {
+    for (int64_t i = threadIdx.x; i < count; i += blockDim.x) dst[i] = src[i];
+}
+
+// Load the neighbours' traces of the faces of one cell into sF[face][comp][t]
+// and the facet coefficient kF[face] (harmonic mean of kappa; 0 on the boundary,
+// where the facet has no neighbour contribution).
+template <int DIM, int Q, typename T>
+__device__ __forceinline__ void load_neighbour_traces(const DGConst<T> &c, int64_t cell, const int *ci, int t,
+                                                      const T *__restrict__ tr, const T *__restrict__ kappa,
+                                                      T *sF, T *sKF, T *sKappa) {
+    using G = Geo<DIM, Q>;
+    const T kK = kappa[cell];
+#pragma unroll
+    for (int f = 0; f < G::NFACE; ++f) {
+        const int dir = f >> 1, side = f & 1;
+        const int cn = ci[dir] + (side ? 1 : -1);
+        const bool inside = cn >= 0 && cn < c.n[dir];
+        T g = T(0), h = T(0);
+        if (inside) {
+            const int64_t nb = cell + (side ? axis_stride<DIM>(c.n, dir) : -axis_stride<DIM>(c.n, dir));
+            const T *src = tr + nb * G::TR + (f ^ 1) * 2 * G::NF;
+            g = src[t];
+            h = src[G::NF + t];
+            if (t == 0) {
+                const T kN = kappa[nb];
+                sKF[f] = T(2) * kK * kN / (kK + kN);
+            }
+        } else if (t == 0) {
+            sKF[f] = T(0);
+        }
+        sF[(f * 2 + 0) * G::NF + t] = g;
+        sF[(f * 2 + 1) * G::NF + t] = h;
+    }
+    if (t == 0) *sKappa = kK;
+}
+
+// Apply the facet mass matrix (tensor product of the tangential 1D masses) to
+// both components of every interior face of the cell, in place. Needs all
+// threads of the CTA (contains barriers); `active` threads do the arithmetic.
+template <int DIM, int Q, typename T>
+__device__ __forceinline__ void facet_mass(const DGConst<T> &c, bool active, int t, T *sF, const T *sKF) {
+    using G = Geo<DIM, Q>;
+    constexpr int NPASS = DIM - 1;
+#pragma unroll
+    for (int pass = 0; pass < NPASS; ++pass) {
+        T out[G::NFACE][2];
+        if (active) {
+            const int ia = t % Q, ib = t / Q;
+#pragma unroll
+            for (int f = 0; f < G::NFACE; ++f) {
+                const int dir = f >> 1;
+                // tangential axes: ta (lower), tb (upper)
+                const int ta = dir == 0 ? 1 : 0;
+                const int tb = dir == 2 ? 1 : 2;
+#pragma unroll
+                for (int comp = 0; comp < 2; ++comp) {
+                    const T *fld = sF + (f * 2 + comp) * G::NF;
+                    T s = T(0);
+                    if (sKF[f] != T(0)) {
+                        if (DIM == 2) {
+#pragma unroll
+                            for (int m = 0; m < Q; ++m) s += c.M[ta][t * Q + m] * fld[m];
+                        } else if (pass == 0) {
+#pragma unroll
+                            for (int m = 0; m < Q; ++m) s += c.M[ta][ia * Q + m] * fld[m + Q * ib];
+                        } else {
+#pragma unroll
+                            for (int m = 0; m < Q; ++m) s += c.M[tb][ib * Q + m] * fld[ia + Q * m];
+                        }
+                    }
+                    out[f][comp] = s;
+                }
+            }
+        }
+        __syncthreads();
+        if (active) {
+#pragma unroll
+            for (int f = 0; f < G::NFACE; ++f)
+#pragma unroll
+                for (int comp = 0; comp < 2; ++comp) sF[(f * 2 + comp) * G::NF + t] = out[f][comp];
+        }
+        __syncthreads();
+    }
+}
+
+// r -= N u_nb: the neighbours' part of the facet terms of the cell equation
+// (all terms of Eq. weak_form_IP_facet_spaces that involve the neighbour's
+// projections), lifted into the cell. sF holds the mass-applied neighbour
+// fields G = M_t g, H = M_t h. For the low face (cell = K^+):
+//   N = kF [ e_0 (x) (H/2 - gamma G) - d_0 (x) G/2 ],
+// for the high face (cell = K^-):
+//   N = kF [ e_p (x) (-H/2 - gamma G) + d_p (x) G/2 ].
+template <int DIM, int Q, typename T>
+__device__ __forceinline__ void lift_neighbours(const DGConst<T> &c, bool active, int t, T *sR, const T *sF,
+                                                const T *sKF) {
+    using G = Geo<DIM, Q>;
+#pragma unroll
+    for (int dir = 0; dir < DIM; ++dir) {
+        if (active) {
+            T x[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) x[i] = sR[G::vidx(dir, t, i)];
+            const T half = T(0.5);
+            const T kL = sKF[2 * dir], kR = sKF[2 * dir + 1];
+            if (kL != T(0)) {
+                const T Gv = sF[((2 * dir) * 2 + 0) * G::NF + t];
+                const T Hv = sF[((2 * dir) * 2 + 1) * G::NF + t];
+                x[0] -= kL * (half * Hv - c.gamma[dir] * Gv);
+                const T a = kL * half * Gv;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) x[i] += a * c.d0[dir][i];
+            }
+            if (kR != T(0)) {
+                const T Gv = sF[((2 * dir + 1) * 2 + 0) * G::NF + t];
+                const T Hv = sF[((2 * dir + 1) * 2 + 1) * G::NF + t];
+                x[Q - 1] -= kR * (-half * Hv - c.gamma[dir] * Gv);
+                const T a = kR * half * Gv;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) x[i] -= a * c.dp[dir][i];
+            }
+#pragma unroll
+            for (int i = 0; i < Q; ++i) sR[G::vidx(dir, t, i)] = x[i];
+        }
+        __syncthreads();
+    }
+}
+
+// Value and +axis derivative of a pencil at both ends, written to the trace array.
+template <int DIM, int Q, typename T>
+__device__ __forceinline__ void write_pencil_traces(const DGConst<T> &c, int dir, int t, const T *x,
+                                                    T *__restrict__ trc) {
+    using G = Geo<DIM, Q>;
+    T dlo = T(0), dhi = T(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        dlo += c.d0[dir][i] * x[i];
+        dhi += c.dp[dir][i] * x[i];
+    }
+    T *lo = trc + (2 * dir) * 2 * G::NF;
+    T *hi = trc + (2 * dir + 1) * 2 * G::NF;
+    lo[t] = x[0];
+    lo[G::NF + t] = dlo;
+    hi[t] = x[Q - 1];
+    hi[G::NF + t] = dhi;
+}
+
+// ---------------------------------------------------------------------------
+// Warm-up projection (Alg. 4 preamble), optionally preceded by u += P e
+// (the p-prolongation fused into the projection, Sec. 5.1 "Prolongation").
+// ---------------------------------------------------------------------------
+template <int DIM, int Q, typename T>
+__global__ void __launch_bounds__(256) k_project(DGConst<T> c, int cpb, T *__restrict__ u,
+                                                  const T *__restrict__ e0, T *__restrict__ tr) {
+    using G = Geo<DIM, Q>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sU = reinterpret_cast<T *>(smem_raw);
+    T *sE = sU + cpb * G::NL;
+    const int lc = threadIdx.x / G::NF, t = threadIdx.x - lc * G::NF;
+    const int64_t cell0 = (int64_t)blockIdx.x * cpb;
+    const int ncl = (int)min((int64_t)cpb, c.ncell - cell0);
+    const bool active = lc < ncl;
+    const int64_t cell = cell0 + lc;
+    int ci[3] = {0, 0, 0};
+    if (active) cell_coords<DIM>(cell, c.n, ci);
+    block_copy(sU, u + cell0 * G::NL, (int64_t)ncl * G::NL);
+    if (e0 != nullptr && active) {
+        for (int k = t; k < G::NC; k += G::NF) {
+            bool interior = true;
+            int64_t vid = 0, stride = 1;
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) {
+                const int v = ci[a] + ((k >> a) & 1);
+                interior = interior && v >= 1 && v <= c.n[a] - 1;
+                vid += (int64_t)(v - 1) * stride;
+                stride *= (c.n[a] - 1);
+            }
+            sE[lc * G::NC + k] = interior ? e0[vid] : T(0);
+        }
+    }
+    __syncthreads();
+    T *trc = tr + cell * G::TR;
+    // pass along x: prolongation and x-face traces
+    if (active) {
+        T x[Q];
+        T *pu = sU + lc * G::NL;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) x[i] = pu[G::vidx(0, t, i)];
+        if (e0 != nullptr) {
+            const T *e = sE + lc * G::NC;
+            T A0, A1;
+            if (DIM == 2) {
+                A0 = e[0] * c.hat[0][t] + e[2] * c.hat[1][t];
+                A1 = e[1] * c.hat[0][t] + e[3] * c.hat[1][t];
+            } else {
+                const int a = t % Q, b = t / Q;
+                const T w00 = c.hat[0][a] * c.hat[0][b], w10 = c.hat[1][a] * c.hat[0][b];
+                const T w01 = c.hat[0][a] * c.hat[1][b], w11 = c.hat[1][a] * c.hat[1][b];
+                A0 = e[0] * w00 + e[2] * w10 + e[4] * w01 + e[6] * w11;
+                A1 = e[1] * w00 + e[3] * w10 + e[5] * w01 + e[7] * w11;
+            }
+#pragma unroll
+            for (int i = 0; i < Q; ++i) x[i] += A0 * c.hat[0][i] + A1 * c.hat[1][i];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) pu[G::vidx(0, t, i)] = x[i];
+        }
+        write_pencil_traces<DIM, Q, T>(c, 0, t, x, trc);
+    }
+    if (e0 != nullptr) __syncthreads();
+    if (active) {
+#pragma unroll
+        for (int dir = 1; dir < DIM; ++dir) {
+            T x[Q];
+            const T *pu = sU + lc * G::NL;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) x[i] = pu[G::vidx(dir, t, i)];
+            write_pencil_traces<DIM, Q, T>(c, dir, t, x, trc);
+        }
+    }
+    if (e0 != nullptr) {
+        __syncthreads();
+        block_copy(u + cell0 * G::NL, sU, (int64_t)ncl * G::NL);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Single-touch block-Jacobi smoothing step (Alg. 4 fused loop body, Technique 5):
+//   u_K <- u_K + omega A_KK^{-1} (b - A u)_K
+// evaluated as u_K <- (1 - omega) u_K + omega A_KK^{-1} (b_K - N_K u_nb), where
+// N_K u_nb are the facet terms that involve the neighbours' stored projections
+// (A u = A_KK u_K + N_K u_nb, so both forms are the same update). A_KK^{-1} by
+// fast diagonalisation: A_KK = sum over axes of Kt_a (x) M (x) M with the
+// generalized eigen-decomposition Kt_a S_a = M S_a Lambda_a, S_a^T M S_a = I,
+// so A_KK^{-1} = (S_x (x) S_y (x) S_z) (Lambda_x + Lambda_y + Lambda_z)^{-1} (...)^T.
+// Reads the neighbours' traces from tr_in, writes the cell's new traces to
+// tr_out (ping-pong: every cell reads projections of the same iterate).
+// ---------------------------------------------------------------------------
+template <int DIM, int Q, typename T>
+__global__ void __launch_bounds__(256) k_smooth(DGConst<T> c, int cpb, T *__restrict__ u, const T *__restrict__ b,
+                                                 const T *__restrict__ kappa, const T *__restrict__ fd,
+                                                 const T *__restrict__ tr_in, T *__restrict__ tr_out) {
+    using G = Geo<DIM, Q>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sU = reinterpret_cast<T *>(smem_raw);
+    T *sR = sU + cpb * G::NL;
+    T *sF = sR + cpb * G::NL;
+    T *sFD = sF + cpb * G::NFACE * 2 * G::NF;
+    T *sK = sFD + cpb * DIM * G::FDS;          // [cpb][NFACE + 1]
+    const int lc = threadIdx.x / G::NF, t = threadIdx.x - lc * G::NF;
+    const int64_t cell0 = (int64_t)blockIdx.x * cpb;
+    const int ncl = (int)min((int64_t)cpb, c.ncell - cell0);
+    const bool active = lc < ncl;
+    const int64_t cell = cell0 + lc;
+    int ci[3] = {0, 0, 0};
+    block_copy(sU, u + cell0 * G::NL, (int64_t)ncl * G::NL);
+    block_copy(sR, b + cell0 * G::NL, (int64_t)ncl * G::NL);
+    block_copy(sFD, fd + cell0 * DIM * G::FDS, (int64_t)ncl * DIM * G::FDS);
+    T *myF = sF + lc * G::NFACE * 2 * G::NF;
+    T *myK = sK + lc * (G::NFACE + 1);
+    if (active) {
+        cell_coords<DIM>(cell, c.n, ci);
+        load_neighbour_traces<DIM, Q, T>(c, cell, ci, t, tr_in, kappa, myF, myK, myK + G::NFACE);
+    }
+    __syncthreads();
+    facet_mass<DIM, Q, T>(c, active, t, myF, myK);
+    T *myR = sR + lc * G::NL;
+    T *myU = sU + lc * G::NL;
+    lift_neighbours<DIM, Q, T>(c, active, t, myR, myF, myK);
+    const T *myS = sFD + lc * DIM * G::FDS;      // S_a at a*FDS, lambda_a at a*FDS + Q*Q
+    // S^T along the axes 0..DIM-2
+#pragma unroll
+    for (int dir = 0; dir < DIM - 1; ++dir) {
+        if (active) {
+            T x[Q], y[Q];
+            const T *S = myS + dir * G::FDS;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) x[i] = myR[G::vidx(dir, t, i)];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                T s = T(0);
+#pragma unroll
+                for (int m = 0; m < Q; ++m) s += S[m * Q + i] * x[m];
+                y[i] = s;
+            }
+#pragma unroll
+            for (int i = 0; i < Q; ++i) myR[G::vidx(dir, t, i)] = y[i];
+        }
+        __syncthreads();
+    }
+    // last axis: S^T, divide by the eigenvalue sums, S
+    {
+        constexpr int D = DIM - 1;
+        if (active) {
+            T x[Q], y[Q];
+            const T *S = myS + D * G::FDS;
+            const T *lam = S + Q * Q;
+            T lt;
+            if (DIM == 2) {
+                lt = myS[0 * G::FDS + Q * Q + t];
+            } else {
+                lt = myS[0 * G::FDS + Q * Q + (t % Q)] + myS[1 * G::FDS + Q * Q + (t / Q)];
+            }
+#pragma unroll
+            for (int i = 0; i < Q; ++i) x[i] = myR[G::vidx(D, t, i)];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                T s = T(0);
+#pragma unroll
+                for (int m = 0; m < Q; ++m) s += S[m * Q + i] * x[m];
+                y[i] = s / (lt + lam[i]);
+            }
+#pragma unroll
+            for (int m = 0; m < Q; ++m) {
+                T s = T(0);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) s += S[m * Q + i] * y[i];
+                x[m] = s;
+            }
+#pragma unroll
+            for (int i = 0; i < Q; ++i) myR[G::vidx(D, t, i)] = x[i];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int dir = DIM - 2; dir >= 1; --dir) {
+        if (active) {
+            T x[Q], y[Q];
+            const T *S = myS + dir * G::FDS;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) x[i] = myR[G::vidx(dir, t, i)];
+#pragma unroll
+            for (int m = 0; m < Q; ++m) {
+                T s = T(0);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) s += S[m * Q + i] * x[i];
+                y[m] = s;
+            }
+#pragma unroll
+            for (int i = 0; i < Q; ++i) myR[G::vidx(dir, t, i)] = y[i];
+        }
+        __syncthreads();
+    }
+    // axis 0: S, damped update, x-face traces
+    T *trc = tr_out + cell * G::TR;
+    if (active) {
+        T x[Q], un[Q];
+        const T *S = myS;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) x[i] = myR[G::vidx(0, t, i)];
+        const T om = c.omega;
+#pragma unroll
+        for (int m = 0; m < Q; ++m) {
+            T s = T(0);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) s += S[m * Q + i] * x[i];
+            un[m] = (T(1) - om) * myU[G::vidx(0, t, m)] + om * s;
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) myU[G::vidx(0, t, i)] = un[i];
+        write_pencil_traces<DIM, Q, T>(c, 0, t, un, trc);
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+        for (int dir = 1; dir < DIM; ++dir) {
+            T x[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) x[i] = myU[G::vidx(dir, t, i)];
+            write_pencil_traces<DIM, Q, T>(c, dir, t, x, trc);
+        }
+    }
+    block_copy(u + cell0 * G::NL, sU, (int64_t)ncl * G::NL);
+}
+
+// ---------------------------------------------------------------------------
+// Residual r = b - A u (Alg. 2 stage 3 / Alg. 6 residual traversal) from u and
+// the stored projections of u, with A u = A_KK u_K + N_K u_nb and
+// A_KK u = sum_a Kt_a (x) M (x) M u (sum factorised), optional fused
+// p-restriction: per cell and corner, sum_i hat_corner(x_i) r_i, gathered per
+// vertex afterwards in a fixed order.
+// ---------------------------------------------------------------------------
+template <int DIM, int Q, typename T>
+__global__ void __launch_bounds__(256) k_residual(DGConst<T> c, int cpb, int mode, const T *__restrict__ u,
+                                                   const T *__restrict__ b, const T *__restrict__ kappa,
+                                                   const T *__restrict__ tr, T *__restrict__ rout,
+                                                   T *__restrict__ corners) {
+    using G = Geo<DIM, Q>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sU = reinterpret_cast<T *>(smem_raw);
+    T *sR = sU + cpb * G::NL;
+    T *sA = sR + cpb * G::NL;
+    T *sB = sA + cpb * G::NL;
+    T *sF = sB + cpb * G::NL;
+    T *sKT = sF + cpb * G::NFACE * 2 * G::NF;   // [cpb][DIM][Q*Q]
+    T *sK = sKT + cpb * DIM * Q * Q;            // [cpb][NFACE + 1]
+    const int lc = threadIdx.x / G::NF, t = threadIdx.x - lc * G::NF;
+    const int64_t cell0 = (int64_t)blockIdx.x * cpb;
+    const int ncl = (int)min((int64_t)cpb, c.ncell - cell0);
+    const bool active = lc < ncl;
+    const int64_t cell = cell0 + lc;
+    int ci[3] = {0, 0, 0};
+    block_copy(sU, u + cell0 * G::NL, (int64_t)ncl * G::NL);
+    if (mode & RES_HAS_B) {
+        block_copy(sR, b + cell0 * G::NL, (int64_t)ncl * G::NL);
+    } else {
+        for (int64_t i = threadIdx.x; i < (int64_t)ncl * G::NL; i += blockDim.x) sR[i] = T(0);
+    }
+    T *myF = sF + lc * G::NFACE * 2 * G::NF;
+    T *myK = sK + lc * (G::NFACE + 1);
+    if (active) {
+        cell_coords<DIM>(cell, c.n, ci);
+        load_neighbour_traces<DIM, Q, T>(c, cell, ci, t, tr, kappa, myF, myK, myK + G::NFACE);
+    }
+    __syncthreads();
+    // Kt_a = kappa_K K_a + own facet terms of the two faces normal to axis a:
+    // low face  kF_L ( w_L (e0 d0^T + d0 e0^T) + gamma e0 e0^T ),
+    // high face kF_R (-w_R (ep dp^T + dp ep^T) + gamma ep ep^T ),
+    // kF = harmonic mean and w = 1/2 inside, kF = kappa_K and w = 1 on the boundary.
+    T *myKT = sKT + lc * DIM * Q * Q;
+    if (active) {
+        const T kK = myK[G::NFACE];
+        for (int e = t; e < DIM * Q * Q; e += G::NF) {
+            const int a = e / (Q * Q), i = (e / Q) % Q, j = e % Q;
+            const bool inL = myK[2 * a] != T(0), inR = myK[2 * a + 1] != T(0);
+            const T kL = inL ? myK[2 * a] : kK, wL = inL ? T(0.5) : T(1);
+            const T kR = inR ? myK[2 * a + 1] : kK, wR = inR ? T(0.5) : T(1);
+            T v = kK * c.K[a][i * Q + j];
+            const T e0i = i == 0 ? T(1) : T(0), e0j = j == 0 ? T(1) : T(0);
+            const T epi = i == Q - 1 ? T(1) : T(0), epj = j == Q - 1 ? T(1) : T(0);
+            v += kL * (wL * (e0i * c.d0[a][j] + c.d0[a][i] * e0j) + c.gamma[a] * e0i * e0j);
+            v += kR * (-wR * (epi * c.dp[a][j] + c.dp[a][i] * epj) + c.gamma[a] * epi * epj);
+            myKT[e] = v;
+        }
+    }
+    facet_mass<DIM, Q, T>(c, active, t, myF, myK);   // contains barriers
+    T *myR = sR + lc * G::NL;
+    T *myU = sU + lc * G::NL;
+    T *myA = sA + lc * G::NL;
+    T *myB = sB + lc * G::NL;
+    lift_neighbours<DIM, Q, T>(c, active, t, myR, myF, myK);
+    // A_KK u by sum factorisation
+    if (DIM == 3) {
+        if (active) {   // axis z: a = M_z u, bb = Kt_z u
+            T x[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) x[i] = myU[G::vidx(2, t, i)];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                T sa = T(0), sb = T(0);
+#pragma unroll
+                for (int m = 0; m < Q; ++m) {
+                    sa += c.M[2][i * Q + m] * x[m];
+                    sb += myKT[2 * Q * Q + i * Q + m] * x[m];
+                }
+                myA[G::vidx(2, t, i)] = sa;
+                myB[G::vidx(2, t, i)] = sb;
+            }
+        }
+        __syncthreads();
+        if (active) {   // axis y: c = M_y a, e = Kt_y a + M_y bb
+            T xa[Q], xb[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                xa[i] = myA[G::vidx(1, t, i)];
+                xb[i] = myB[G::vidx(1, t, i)];
+            }
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                T sc = T(0), se = T(0);
+#pragma unroll
+                for (int m = 0; m < Q; ++m) {
+                    sc += c.M[1][i * Q + m] * xa[m];
+                    se += myKT[1 * Q * Q + i * Q + m] * xa[m] + c.M[1][i * Q + m] * xb[m];
+                }
+                myA[G::vidx(1, t, i)] = sc;
+                myB[G::vidx(1, t, i)] = se;
+            }
+        }
+        __syncthreads();
+    } else {
+        if (active) {   // axis y: a = M_y u, bb = Kt_y u
+            T x[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) x[i] = myU[G::vidx(1, t, i)];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                T sa = T(0), sb = T(0);
+#pragma unroll
+                for (int m = 0; m < Q; ++m) {
+                    sa += c.M[1][i * Q + m] * x[m];
+                    sb += myKT[1 * Q * Q + i * Q + m] * x[m];
+                }
+                myA[G::vidx(1, t, i)] = sa;
+                myB[G::vidx(1, t, i)] = sb;
+            }
+        }
+        __syncthreads();
+    }
+    // axis x: y = Kt_x a + M_x bb; r = R - y
+    T rr[Q];
+    if (active) {
+        T xa[Q], xb[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            xa[i] = myA[G::vidx(0, t, i)];
+            xb[i] = myB[G::vidx(0, t, i)];
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            T s = T(0);
+#pragma unroll
+            for (int m = 0; m < Q; ++m) s += myKT[i * Q + m] * xa[m] + c.M[0][i * Q + m] * xb[m];
+            rr[i] = myR[G::vidx(0, t, i)] - s;
+            if (mode & RES_NEGATE) rr[i] = -rr[i];
+        }
+        if (mode & RES_WRITE_R) {
+            T *dst = rout + cell * G::NL;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) dst[G::vidx(0, t, i)] = rr[i];
+        }
+    }
+    if (mode & RES_CORNERS) {
+        // partial sums over x of hat_cx(x_i) r_i, then over the tangential axes
+        T *px = sF;                     // reuse: [cpb][2][NF]
+        __syncthreads();
+        if (active) {
+            T p0 = T(0), p1 = T(0);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                p0 += c.hat[0][i] * rr[i];
+                p1 += c.hat[1][i] * rr[i];
+            }
+            px[(lc * 2 + 0) * G::NF + t] = p0;
+            px[(lc * 2 + 1) * G::NF + t] = p1;
+        }
+        __syncthreads();
+        if (active) {
+            for (int k = t; k < G::NC; k += G::NF) {
+                const int cx = k & 1, cy = (k >> 1) & 1, cz = (k >> 2) & 1;
+                const T *src = px + (lc * 2 + cx) * G::NF;
+                T s = T(0);
+                if (DIM == 2) {
+                    for (int a = 0; a < Q; ++a) s += c.hat[cy][a] * src[a];
+                } else {
+                    for (int bb = 0; bb < Q; ++bb) {
+                        T sa = T(0);
+                        for (int a = 0; a < Q; ++a) sa += c.hat[cy][a] * src[a + Q * bb];
+                        s += c.hat[cz][bb] * sa;
+                    }
+                }
+                corners[cell * G::NC + k] = s;
+            }
+        }
+    }
+}
+
+// Shared-memory bytes per CTA of each kernel.
+template <int DIM, int Q, typename T>
+constexpr size_t smem_project(int cpb) {
+    return (size_t)cpb * (Geo<DIM, Q>::NL + Geo<DIM, Q>::NC) * sizeof(T);
+}
+template <int DIM, int Q, typename T>
+constexpr size_t smem_smooth(int cpb) {
+    using G = Geo<DIM, Q>;
+    return (size_t)cpb * (2 * G::NL + G::NFACE * 2 * G::NF + DIM * G::FDS + G::NFACE + 1) * sizeof(T);
+}
+template <int DIM, int Q, typename T>
+constexpr size_t smem_residual(int cpb) {
+    using G = Geo<DIM, Q>;
+    return (size_t)cpb * (4 * G::NL + G::NFACE * 2 * G::NF + DIM * Q * Q + G::NFACE + 1) * sizeof(T);
+}
+
+template <int DIM, int Q, typename T>
+struct DGLaunch {
+    using G = Geo<DIM, Q>;
+    static cudaError_t project(const DGConst<T> &c, int cpb, T *u, const T *e0, T *tr, cudaStream_t s) {
+        const size_t sm = smem_project<DIM, Q, T>(cpb);
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_project<DIM, Q, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            attr = true;
+        }
+        const int64_t grid = (c.ncell + cpb - 1) / cpb;
+        if (grid == 0) return cudaSuccess;
+        k_project<DIM, Q, T><<<(unsigned)grid, cpb * G::NF, sm, s>>>(c, cpb, u, e0, tr);
+        return cudaGetLastError();
+    }
+    static cudaError_t smooth(const DGConst<T> &c, int cpb, T *u, const T *b, const T *kappa, const T *fd,
+                              const T *tri, T *tro, cudaStream_t s) {
+        const size_t sm = smem_smooth<DIM, Q, T>(cpb);
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_smooth<DIM, Q, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            attr = true;
+        }
+        const int64_t grid = (c.ncell + cpb - 1) / cpb;
+        if (grid == 0) return cudaSuccess;
+        k_smooth<DIM, Q, T><<<(unsigned)grid, cpb * G::NF, sm, s>>>(c, cpb, u, b, kappa, fd, tri, tro);
+        return cudaGetLastError();
+    }
+    static cudaError_t residual(const DGConst<T> &c, int cpb, int mode, const T *u, const T *b, const T *kappa,
+                                const T *tr, T *r, T *corners, cudaStream_t s) {
+        const size_t sm = smem_residual<DIM, Q, T>(cpb);
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_residual<DIM, Q, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            attr = true;
+        }
+        const int64_t grid = (c.ncell + cpb - 1) / cpb;
+        if (grid == 0) return cudaSuccess;
+        k_residual<DIM, Q, T><<<(unsigned)grid, cpb * G::NF, sm, s>>>(c, cpb, mode, u, b, kappa, tr, r, corners);
+        return cudaGetLastError();
+    }
+};
+
+#define DGMG_DISPATCH(dim, q, CALL)                      \
+    switch ((dim) * 16 + (q)) {                          \
+        case 2 * 16 + 2: return DGLaunch<2, 2, T>::CALL; \
+        case 2 * 16 + 3: return DGLaunch<2, 3, T>::CALL; \
+        case 2 * 16 + 4: return DGLaunch<2, 4, T>::CALL; \
+        case 2 * 16 + 5: return DGLaunch<2, 5, T>::CALL; \
+        case 2 * 16 + 6: return DGLaunch<2, 6, T>::CALL; \
+        case 2 * 16 + 7: return DGLaunch<2, 7, T>::CALL; \
+        case 3 * 16 + 2: return DGLaunch<3, 2, T>::CALL; \
+        case 3 * 16 + 3: return DGLaunch<3, 3, T>::CALL; \
+        case 3 * 16 + 4: return DGLaunch<3, 4, T>::CALL; \
+        case 3 * 16 + 5: return DGLaunch<3, 5, T>::CALL; \
+        case 3 * 16 + 6: return DGLaunch<3, 6, T>::CALL; \
+        case 3 * 16 + 7: return DGLaunch<3, 7, T>::CALL; \
+        default: return cudaErrorInvalidValue;           \
+    }
+
+template <typename T>
+cudaError_t launch_project_impl(int dim, int q, const DGConst<T> &c, int cpb, T *u, const T *e0, T *tr,
+                                cudaStream_t s) {
+    DGMG_DISPATCH(dim, q, project(c, cpb, u, e0, tr, s))
+}
+template <typename T>
+cudaError_t launch_smooth_impl(int dim, int q, const DGConst<T> &c, int cpb, T *u, const T *b, const T *kappa,
+                               const T *fd, const T *tri, T *tro, cudaStream_t s) {
+    DGMG_DISPATCH(dim, q, smooth(c, cpb, u, b, kappa, fd, tri, tro, s))
+}
+template <typename T>
+cudaError_t launch_residual_impl(int dim, int q, const DGConst<T> &c, int cpb, int mode, const T *u, const T *b,
+                                 const T *kappa, const T *tr, T *r, T *corners, cudaStream_t s) {
+    DGMG_DISPATCH(dim, q, residual(c, cpb, mode, u, b, kappa, tr, r, corners, s))
+}
+
+}  // namespace dgmg

@@ -1,0 +1,136 @@
+// Internal declarations of libdgmg (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "dgmg.h"
+
+namespace dgmg {
+
+constexpr int QMAX = 7;     // p <= 6
+constexpr int PMAX = QMAX - 1;
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define DG_CUDA(call)                                         \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return ::dgmg::cuda_fail(e_, #call); \
+    } while (0)
+
+// ------------------------------------------------------- reference element
+// 1D GLL Lagrange element of degree p on [-1,1] (paper Sec. 2.2), computed
+// on the host in double precision.
+struct RefElem1D {
+    int p = 0, q = 0;
+    std::vector<double> nodes;            // q GLL nodes
+    std::vector<double> M, K;             // q x q exact mass / stiffness on [-1,1], row-major
+    std::vector<double> d0, dp;           // l_j'(-1), l_j'(+1)
+};
+RefElem1D make_refelem(int p);
+void gauss_legendre(int m, std::vector<double> &x, std::vector<double> &w);
+// values and derivatives of the Lagrange basis on `nodes` at x
+void lagrange_at(const std::vector<double> &nodes, double x, double *val, double *der);
+
+// Symmetric generalized eigenproblem Kt S = M S diag(lam), S^T M S = I, by
+// Cholesky of M and cyclic Jacobi rotations. Kt, M: q x q row-major.
+void gen_eig_sym(int q, const double *Kt, const double *Lchol_inv, double *S, double *lam);
+// lower Cholesky factor inverse of the SPD q x q matrix M (row-major)
+bool cholesky_inverse_lower(int q, const double *M, double *Linv);
+
+// ------------------------------------------------------------ kernels API
+// Constant data of one DG level, passed to kernels by value.
+template <typename T>
+struct DGConst {
+    int n[3];
+    int64_t ncell;
+    T M[3][QMAX * QMAX];
+    T K[3][QMAX * QMAX];
+    T d0[3][QMAX];
+    T dp[3][QMAX];
+    T gamma[3];
+    T hat[2][QMAX];
+    T omega;
+};
+
+// Q1 level description for the CG kernels.
+template <typename T>
+struct CGLevelDev {
+    int m[3];              // interior vertices per axis
+    int64_t nv;
+    const T *st;           // [nv][3^d] stencil, offset (sx+1) + 3 (sy+1) + 9 (sz+1)
+    // transfer to the next coarser level (per axis tables); null on the coarsest
+    const int *pl_lo[3];   // fine vertex -> lower coarse parent (-1 if none)
+    const int *pl_hi[3];   // fine vertex -> upper coarse parent (-1 if none)
+    const T *pl_wlo[3], *pl_whi[3];
+    const int *rs_start[3];  // coarse vertex -> first fine child
+    const int *rs_cnt[3];    // number of fine children (<= 2f-1)
+    const T *rs_w[3];        // [nc][5] weights
+    int mc[3];               // interior vertices per axis of the coarser level
+};
+
+struct DGBuffers {
+    const void *kappa;     // [ncell] T
+    const void *fd;        // [ncell][d][q*q+q] T: S (row m, col i) then lambda
+};
+
+// Launch wrappers (implemented per precision in dg_fp64.cu / dg_fp32.cu).
+// All return cudaError_t of the launch.
+template <typename T>
+cudaError_t launch_project(int dim, int q, const DGConst<T> &c, int cpb, T *u, const T *e0,
+                           T *tr, cudaStream_t s);
+template <typename T>
+cudaError_t launch_smooth(int dim, int q, const DGConst<T> &c, int cpb, T *u, const T *b,
+                          const T *kappa, const T *fd, const T *tr_in, T *tr_out, cudaStream_t s);
+// mode bits for launch_residual
+enum { RES_HAS_B = 1, RES_WRITE_R = 2, RES_CORNERS = 4, RES_NEGATE = 8 };
+template <typename T>
+cudaError_t launch_residual(int dim, int q, const DGConst<T> &c, int cpb, int mode, const T *u,
+                            const T *b, const T *kappa, const T *tr, T *r, T *corners,
+                            cudaStream_t s);
+
+// CG kernels (cg.cu)
+template <typename T>
+cudaError_t launch_corner_gather(int dim, const int *n, const T *corners, T *b0, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cg_jacobi(int dim, const CGLevelDev<T> &L, const T *u_in, const T *b, T *u_out,
+                             T omega, bool zero_guess, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cg_residual(int dim, const CGLevelDev<T> &L, const T *u, const T *b, T *r,
+                               cudaStream_t s);
+template <typename T>
+cudaError_t launch_h_restrict(int dim, const CGLevelDev<T> &L, const T *rf, T *rc, cudaStream_t s);
+template <typename T>
+cudaError_t launch_h_prolong(int dim, const CGLevelDev<T> &L, const T *ec, T *uf, cudaStream_t s);
+template <typename T>
+cudaError_t launch_coarse_solve(int64_t nc, const double *Ainv, const T *r, T *e, cudaStream_t s);
+
+// BLAS-1 and helpers (blas.cu)
+cudaError_t launch_dot(int64_t n, const double *x, const double *y, double *partials,
+                       double *out, cudaStream_t s);
+cudaError_t launch_dot2(int64_t n, const double *x, const double *y, const double *z,
+                        double *partials, double *out_xy, double *out_zy, cudaStream_t s);
+cudaError_t launch_cast_d2f(int64_t n, const double *x, float *y, cudaStream_t s);
+cudaError_t launch_cast_f2d(int64_t n, const float *x, double *y, cudaStream_t s);
+cudaError_t launch_pcg_update_xr(int64_t n, double *x, double *r, const double *p,
+                                 const double *q, const double *scal, cudaStream_t s);
+cudaError_t launch_pcg_update_p(int64_t n, double *p, const double *z, const double *scal,
+                                cudaStream_t s);
+cudaError_t launch_sub(int64_t n, const double *a, const double *b, double *out, cudaStream_t s);
+cudaError_t launch_copy_scalar(const double *src, double *dst, cudaStream_t s);
+cudaError_t launch_quad_points(int dim, int q, const int *n, int mq, const double *xq1,
+                               double *xq, int64_t ncell, cudaStream_t s);
+cudaError_t launch_load_vector(int dim, int q, int mq, int64_t ncell, const double *V,
+                               const double *wq, const double *fq, double *b, cudaStream_t s);
+
+constexpr int DOT_BLOCKS = 304;     // 2 x 152 SMs
+constexpr int DOT_THREADS = 256;
+
+}  // namespace dgmg

@@ -1,0 +1,253 @@
+"""Python binding of libdgmg (ctypes): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts torch tensors
+to device pointers and raises ``DGMGError`` on any non-zero return code. There
+is no fallback: if ``libdgmg.so`` is missing the import fails loudly.
+"""
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libdgmg.so")
+
+DGMG_OK = 0
+DGMG_EINVAL = -1
+DGMG_ENOMEM = -2
+DGMG_EBUDGET = -3
+DGMG_ENOTCONVERGED = -4
+DGMG_ENONFINITE = -5
+DGMG_ECUDA = -6
+DGMG_FP64 = 0
+DGMG_MIXED_FP32 = 1
+DGMG_BLOCK_EXACT = 0
+DGMG_BLOCK_INTERIOR_ONLY = 1
+
+
+class DGMGError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"dgmg error {code}: {msg}")
+        self.code = code
+
+
+class Mesh(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("omega_dg", ctypes.c_double), ("omega_cg", ctypes.c_double),
+                ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int), ("precision", ctypes.c_int),
+                ("block_inverse", ctypes.c_int), ("coarsening", ctypes.c_int),
+                ("rtol", ctypes.c_double), ("maxit", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("p", ctypes.c_int), ("q", ctypes.c_int), ("n", ctypes.c_int * 3),
+                ("ncell", ctypes.c_int64), ("ndof", ctypes.c_int64), ("nlevels_cg", ctypes.c_int),
+                ("nvert0", ctypes.c_int64), ("ncoarse", ctypes.c_int64),
+                ("omega_dg", ctypes.c_double), ("omega_cg", ctypes.c_double),
+                ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int), ("precision", ctypes.c_int),
+                ("block_inverse", ctypes.c_int), ("coarsening", ctypes.c_int),
+                ("device_bytes", ctypes.c_size_t)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("rel_residual_recursive", ctypes.c_double), ("prec_residual", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_SIGS = {
+    "dgmg_version": (ctypes.c_char_p, []),
+    "dgmg_last_error": (ctypes.c_char_p, []),
+    "dgmg_default_opts": (None, [ctypes.POINTER(Opts)]),
+    "dgmg_create": (_I, [ctypes.POINTER(Mesh), _I, _P, ctypes.POINTER(Opts), ctypes.POINTER(_P)]),
+    "dgmg_destroy": (_I, [_P]),
+    "dgmg_info": (_I, [_P, ctypes.POINTER(Info)]),
+    "dgmg_gll_nodes": (_I, [_P, _P]),
+    "dgmg_apply": (_I, [_P, _P, _P, _P]),
+    "dgmg_residual": (_I, [_P, _P, _P, _P, _P]),
+    "dgmg_smooth": (_I, [_P, _P, _P, _I, _P]),
+    "dgmg_vcycle": (_I, [_P, _P, _P, _P]),
+    "dgmg_solve": (_I, [_P, _P, _P, ctypes.POINTER(Stats), _P]),
+    "dgmg_solve_host": (_I, [_P, _P, _P, ctypes.POINTER(Stats), _P]),
+    "dgmg_quad_points": (_I, [_P, _P, _P]),
+    "dgmg_load_vector": (_I, [_P, _P, _P, _P]),
+    "dgmg_project": (_I, [_P, _P, _P, _P, _P]),
+    "dgmg_residual_restrict": (_I, [_P, _P, _P, _P, _P, _P, _P]),
+    "dgmg_cg_smooth": (_I, [_P, _I, _P, _P, _I, _P]),
+    "dgmg_cg_residual": (_I, [_P, _I, _P, _P, _P, _P]),
+    "dgmg_h_restrict": (_I, [_P, _I, _P, _P, _P]),
+    "dgmg_h_prolong": (_I, [_P, _I, _P, _P, _P]),
+    "dgmg_coarse_solve": (_I, [_P, _P, _P, _P]),
+    "dgmg_cg_size": (ctypes.c_int64, [_P, _I]),
+}
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load libdgmg.so (raises OSError if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"libdgmg.so not found at {path}; build it with __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc, allow=()):
+    if rc != DGMG_OK and rc not in allow:
+        raise DGMGError(rc, load().dgmg_last_error().decode())
+    return rc
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch.Tensor")
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("tensor must be a contiguous CUDA tensor")
+    if t.dtype != torch.float64:
+        raise ValueError("tensor must be float64")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def default_opts():
+    o = Opts()
+    load().dgmg_default_opts(ctypes.byref(o))
+    return o
+
+
+class Context:
+    """A dgmg_ctx: the hierarchy for one mesh, degree and kappa field."""
+
+    def __init__(self, n, p, kappa=None, **opts):
+        lib = load()
+        self.lib = lib
+        m = Mesh()
+        m.dim = len(n)
+        for a in range(3):
+            m.n[a] = int(n[a]) if a < len(n) else 1
+        o = default_opts()
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(o, k, v)
+        self.opts = o
+        kap_ptr = None
+        self._kappa_keep = None
+        if kappa is not None:
+            import numpy as np
+            k = np.ascontiguousarray(np.asarray(kappa, dtype=np.float64).reshape(-1))
+            self._kappa_keep = k
+            kap_ptr = k.ctypes.data_as(ctypes.c_void_p)
+        h = ctypes.c_void_p()
+        _check(lib.dgmg_create(ctypes.byref(m), int(p), kap_ptr, ctypes.byref(o), ctypes.byref(h)))
+        self.h = h
+        self.info = self.get_info()
+        self.n = tuple(int(v) for v in n)
+        self.p = int(p)
+        self.ndof = int(self.info.ndof)
+
+    def get_info(self):
+        inf = Info()
+        _check(self.lib.dgmg_info(self.h, ctypes.byref(inf)))
+        return inf
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dgmg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def gll_nodes(self):
+        import numpy as np
+        x = np.zeros(self.info.q)
+        _check(self.lib.dgmg_gll_nodes(self.h, x.ctypes.data_as(ctypes.c_void_p)))
+        return x
+
+    def cg_size(self, level):
+        return int(self.lib.dgmg_cg_size(self.h, int(level)))
+
+    def apply(self, u, y, stream=None):
+        _check(self.lib.dgmg_apply(self.h, _ptr(u), _ptr(y), _stream(stream)))
+
+    def residual(self, u, b, r, stream=None):
+        _check(self.lib.dgmg_residual(self.h, _ptr(u), _ptr(b), _ptr(r), _stream(stream)))
+
+    def smooth(self, u, b, nsteps, stream=None):
+        _check(self.lib.dgmg_smooth(self.h, _ptr(u), _ptr(b), int(nsteps), _stream(stream)))
+
+    def vcycle(self, r, e, stream=None):
+        _check(self.lib.dgmg_vcycle(self.h, _ptr(r), _ptr(e), _stream(stream)))
+
+    def solve(self, b, x, stream=None, allow_notconverged=False):
+        st = Stats()
+        allow = (DGMG_ENOTCONVERGED,) if allow_notconverged else ()
+        rc = _check(self.lib.dgmg_solve(self.h, _ptr(b), _ptr(x), ctypes.byref(st), _stream(stream)), allow)
+        return st, rc
+
+    def solve_host(self, b_host, x_host, stream=None):
+        """b_host, x_host: CPU float64 torch tensors (pinned for best speed)."""
+        import torch
+        for t in (b_host, x_host):
+            if t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+                raise ValueError("host tensors must be contiguous CPU float64")
+        st = Stats()
+        _check(self.lib.dgmg_solve_host(self.h, ctypes.c_void_p(b_host.data_ptr()),
+                                        ctypes.c_void_p(x_host.data_ptr()), ctypes.byref(st), _stream(stream)))
+        return st
+
+    def quad_points(self, xq, stream=None):
+        _check(self.lib.dgmg_quad_points(self.h, _ptr(xq), _stream(stream)))
+
+    def load_vector(self, fq, b, stream=None):
+        _check(self.lib.dgmg_load_vector(self.h, _ptr(fq), _ptr(b), _stream(stream)))
+
+    def project(self, u, e, traces, stream=None):
+        _check(self.lib.dgmg_project(self.h, _ptr(u), _ptr(e), _ptr(traces), _stream(stream)))
+
+    def residual_restrict(self, u, b, traces, r, rc, stream=None):
+        _check(self.lib.dgmg_residual_restrict(self.h, _ptr(u), _ptr(b), _ptr(traces), _ptr(r), _ptr(rc),
+                                               _stream(stream)))
+
+    def cg_smooth(self, level, u, b, nsteps, stream=None):
+        _check(self.lib.dgmg_cg_smooth(self.h, int(level), _ptr(u), _ptr(b), int(nsteps), _stream(stream)))
+
+    def cg_residual(self, level, u, b, r, stream=None):
+        _check(self.lib.dgmg_cg_residual(self.h, int(level), _ptr(u), _ptr(b), _ptr(r), _stream(stream)))
+
+    def h_restrict(self, level, rf, rc, stream=None):
+        _check(self.lib.dgmg_h_restrict(self.h, int(level), _ptr(rf), _ptr(rc), _stream(stream)))
+
+    def h_prolong(self, level, ec, uf, stream=None):
+        _check(self.lib.dgmg_h_prolong(self.h, int(level), _ptr(ec), _ptr(uf), _stream(stream)))
+
+    def coarse_solve(self, r, e, stream=None):
+        _check(self.lib.dgmg_coarse_solve(self.h, _ptr(r), _ptr(e), _stream(stream)))
+
+    def trace_size(self):
+        d, q = self.info.dim, self.info.q
+        return int(self.info.ncell) * 2 * d * 2 * q ** (d - 1)
