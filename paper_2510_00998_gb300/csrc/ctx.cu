@@ -350,6 +350,8 @@ namespace {
         if (e_ != cudaSuccess) return cuda_fail(e_, #x);  \
     } while (0)
 
+int exact_block(const dgmg_ctx &C) { return C.opts.block_inverse == DGMG_BLOCK_EXACT ? 1 : 0; }
+
 template <typename T>
 void fill_const(const dgmg_ctx &C, DGConst<T> &c) {
     std::memset(&c, 0, sizeof(c));
@@ -655,7 +657,7 @@ int dg_vcycle(dgmg_ctx &C, const T *r, T *z, cudaStream_t s) {
     LC(cudaMemsetAsync(D.tr[0], 0, sizeof(T) * trn, s));   // projections of z = 0
     int cur = 0;
     for (int k = 0; k < C.opts.nu_pre; ++k) {
-        LC(launch_smooth<T>(C.dim, C.q, D.c, C.cpb, z, r, D.kappa, D.fd, D.tr[cur], D.tr[cur ^ 1], s));
+        LC(launch_smooth<T>(C.dim, C.q, D.c, C.cpb, exact_block(C), z, r, D.kappa, D.fd, D.tr[cur], D.tr[cur ^ 1], s));
         cur ^= 1;
     }
     LC(launch_residual<T>(C.dim, C.q, D.c, C.cpb, RES_HAS_B | RES_CORNERS, z, r, D.kappa, D.tr[cur], nullptr,
@@ -667,7 +669,7 @@ int dg_vcycle(dgmg_ctx &C, const T *r, T *z, cudaStream_t s) {
     LC(launch_project<T>(C.dim, C.q, D.c, C.cpb, z, e0, D.tr[0], s));   // z += P e0, projections
     cur = 0;
     for (int k = 0; k < C.opts.nu_post; ++k) {
-        LC(launch_smooth<T>(C.dim, C.q, D.c, C.cpb, z, r, D.kappa, D.fd, D.tr[cur], D.tr[cur ^ 1], s));
+        LC(launch_smooth<T>(C.dim, C.q, D.c, C.cpb, exact_block(C), z, r, D.kappa, D.fd, D.tr[cur], D.tr[cur ^ 1], s));
         cur ^= 1;
     }
     return DGMG_OK;
@@ -909,7 +911,7 @@ int dgmg_smooth(dgmg_ctx *C, double *u, const double *b, int nsteps, void *strea
     LC(launch_project<double>(C->dim, C->q, D.c, C->cpb, u, nullptr, D.tr[0], s));
     int cur = 0;
     for (int k = 0; k < nsteps; ++k) {
-        LC(launch_smooth<double>(C->dim, C->q, D.c, C->cpb, u, b, D.kappa, D.fd, D.tr[cur], D.tr[cur ^ 1], s));
+        LC(launch_smooth<double>(C->dim, C->q, D.c, C->cpb, exact_block(*C), u, b, D.kappa, D.fd, D.tr[cur], D.tr[cur ^ 1], s));
         cur ^= 1;
     }
     return DGMG_OK;

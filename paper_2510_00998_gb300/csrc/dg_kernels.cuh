@@ -184,6 +184,94 @@ __device__ __forceinline__ void lift_neighbours(const DGConst<T> &c, bool active
     }
 }
 
+// Kt_a = kappa_K K_a + own facet terms of the two faces normal to axis a:
+// low face  kF_L ( w_L (e0 d0^T + d0 e0^T) + gamma e0 e0^T ),
+// high face kF_R (-w_R (ep dp^T + dp ep^T) + gamma ep ep^T ),
+// kF = harmonic mean and w = 1/2 inside, kF = kappa_K and w = 1 on the boundary.
+template <int DIM, int Q, typename T>
+__device__ __forceinline__ void build_block_1d(const DGConst<T> &c, bool active, int t, const T *myK, T *myKT) {
+    using G = Geo<DIM, Q>;
+    if (!active) return;
+    const T kK = myK[G::NFACE];
+    for (int e = t; e < DIM * Q * Q; e += G::NF) {
+        const int a = e / (Q * Q), i = (e / Q) % Q, j = e % Q;
+        const bool inL = myK[2 * a] != T(0), inR = myK[2 * a + 1] != T(0);
+        const T kL = inL ? myK[2 * a] : kK, wL = inL ? T(0.5) : T(1);
+        const T kR = inR ? myK[2 * a + 1] : kK, wR = inR ? T(0.5) : T(1);
+        T v = kK * c.K[a][i * Q + j];
+        const T e0i = i == 0 ? T(1) : T(0), e0j = j == 0 ? T(1) : T(0);
+        const T epi = i == Q - 1 ? T(1) : T(0), epj = j == Q - 1 ? T(1) : T(0);
+        v += kL * (wL * (e0i * c.d0[a][j] + c.d0[a][i] * e0j) + c.gamma[a] * e0i * e0j);
+        v += kR * (-wR * (epi * c.dp[a][j] + c.dp[a][i] * epj) + c.gamma[a] * epi * epj);
+        myKT[e] = v;
+    }
+}
+
+// R -= A_KK U with A_KK = sum_a Kt_a (x) M (x) M by sum factorisation:
+// 3D: a = M_z u, bb = Kt_z u; c = M_y a, e = Kt_y a + M_y bb; y = Kt_x c + M_x e.
+// 2D: a = M_y u, bb = Kt_y u; y = Kt_x a + M_x bb. Contains barriers.
+template <int DIM, int Q, typename T>
+__device__ __forceinline__ void subtract_block_apply(const DGConst<T> &c, bool active, int t, const T *myU, T *myR,
+                                                     T *myA, T *myB, const T *myKT) {
+    using G = Geo<DIM, Q>;
+    constexpr int D = DIM - 1;   // first pass along the highest axis
+    if (active) {
+        T x[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) x[i] = myU[G::vidx(D, t, i)];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            T sa = T(0), sb = T(0);
+#pragma unroll
+            for (int m = 0; m < Q; ++m) {
+                sa += c.M[D][i * Q + m] * x[m];
+                sb += myKT[D * Q * Q + i * Q + m] * x[m];
+            }
+            myA[G::vidx(D, t, i)] = sa;
+            myB[G::vidx(D, t, i)] = sb;
+        }
+    }
+    __syncthreads();
+    if (DIM == 3) {
+        if (active) {
+            T xa[Q], xb[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                xa[i] = myA[G::vidx(1, t, i)];
+                xb[i] = myB[G::vidx(1, t, i)];
+            }
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                T sc = T(0), se = T(0);
+#pragma unroll
+                for (int m = 0; m < Q; ++m) {
+                    sc += c.M[1][i * Q + m] * xa[m];
+                    se += myKT[1 * Q * Q + i * Q + m] * xa[m] + c.M[1][i * Q + m] * xb[m];
+                }
+                myA[G::vidx(1, t, i)] = sc;
+                myB[G::vidx(1, t, i)] = se;
+            }
+        }
+        __syncthreads();
+    }
+    if (active) {
+        T xa[Q], xb[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            xa[i] = myA[G::vidx(0, t, i)];
+            xb[i] = myB[G::vidx(0, t, i)];
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            T s = T(0);
+#pragma unroll
+            for (int m = 0; m < Q; ++m) s += myKT[i * Q + m] * xa[m] + c.M[0][i * Q + m] * xb[m];
+            myR[G::vidx(0, t, i)] -= s;
+        }
+    }
+    __syncthreads();
+}
+
 // Value and +axis derivative of a pencil at both ends, written to the trace array.
 template <int DIM, int Q, typename T>
 __device__ __forceinline__ void write_pencil_traces(const DGConst<T> &c, int dir, int t, const T *x,
@@ -283,20 +371,25 @@ __global__ void __launch_bounds__(256) k_project(DGConst<T> c, int cpb, T *__res
 
 // ---------------------------------------------------------------------------
 // Single-touch block-Jacobi smoothing step (Alg. 4 fused loop body, Technique 5):
-//   u_K <- u_K + omega A_KK^{-1} (b - A u)_K
-// evaluated as u_K <- (1 - omega) u_K + omega A_KK^{-1} (b_K - N_K u_nb), where
-// N_K u_nb are the facet terms that involve the neighbours' stored projections
-// (A u = A_KK u_K + N_K u_nb, so both forms are the same update). A_KK^{-1} by
-// fast diagonalisation: A_KK = sum over axes of Kt_a (x) M (x) M with the
-// generalized eigen-decomposition Kt_a S_a = M S_a Lambda_a, S_a^T M S_a = I,
-// so A_KK^{-1} = (S_x (x) S_y (x) S_z) (Lambda_x + Lambda_y + Lambda_z)^{-1} (...)^T.
-// Reads the neighbours' traces from tr_in, writes the cell's new traces to
+//   u_K <- u_K + omega B_K^{-1} (b - A u)_K,   B_K = A_KK (exact) or the block of
+//   an interior cell (Technique 4).
+// With the exact block the update is evaluated as
+//   u_K <- (1 - omega) u_K + omega A_KK^{-1} (b_K - N_K u_nb),
+// where N_K u_nb are the facet terms that involve the neighbours' stored
+// projections (A u = A_KK u_K + N_K u_nb, so both forms are the same update
+// and the volume operator is never applied). With the interior-only block the
+// full residual b - N_K u_nb - A_KK u_K is formed first (c.exact == 0).
+// B^{-1} by fast diagonalisation: B = sum over axes of Kt_a (x) M (x) M with
+// Kt_a S_a = M S_a Lambda_a, S_a^T M S_a = I, so
+// B^{-1} = (S_x (x) S_y (x) S_z) (Lambda_x + Lambda_y + Lambda_z)^{-1} (...)^T.
+// Reads the neighbours' traces from tr_in and writes the cell's new traces to
 // tr_out (ping-pong: every cell reads projections of the same iterate).
 // ---------------------------------------------------------------------------
 template <int DIM, int Q, typename T>
-__global__ void __launch_bounds__(256) k_smooth(DGConst<T> c, int cpb, T *__restrict__ u, const T *__restrict__ b,
-                                                 const T *__restrict__ kappa, const T *__restrict__ fd,
-                                                 const T *__restrict__ tr_in, T *__restrict__ tr_out) {
+__global__ void __launch_bounds__(256) k_smooth(DGConst<T> c, int cpb, int exact, T *__restrict__ u,
+                                                const T *__restrict__ b, const T *__restrict__ kappa,
+                                                const T *__restrict__ fd, const T *__restrict__ tr_in,
+                                                T *__restrict__ tr_out) {
     using G = Geo<DIM, Q>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sU = reinterpret_cast<T *>(smem_raw);
@@ -304,6 +397,9 @@ __global__ void __launch_bounds__(256) k_smooth(DGConst<T> c, int cpb, T *__rest
     T *sF = sR + cpb * G::NL;
     T *sFD = sF + cpb * G::NFACE * 2 * G::NF;
     T *sK = sFD + cpb * DIM * G::FDS;          // [cpb][NFACE + 1]
+    T *sA = sK + cpb * (G::NFACE + 1);         // inexact block only: [cpb][NL] x 2, [cpb][DIM*Q*Q]
+    T *sB = sA + cpb * G::NL;
+    T *sKT = sB + cpb * G::NL;
     const int lc = threadIdx.x / G::NF, t = threadIdx.x - lc * G::NF;
     const int64_t cell0 = (int64_t)blockIdx.x * cpb;
     const int ncl = (int)min((int64_t)cpb, c.ncell - cell0);
@@ -320,10 +416,14 @@ __global__ void __launch_bounds__(256) k_smooth(DGConst<T> c, int cpb, T *__rest
         load_neighbour_traces<DIM, Q, T>(c, cell, ci, t, tr_in, kappa, myF, myK, myK + G::NFACE);
     }
     __syncthreads();
-    facet_mass<DIM, Q, T>(c, active, t, myF, myK);
     T *myR = sR + lc * G::NL;
     T *myU = sU + lc * G::NL;
+    if (!exact) build_block_1d<DIM, Q, T>(c, active, t, myK, sKT + lc * DIM * Q * Q);
+    facet_mass<DIM, Q, T>(c, active, t, myF, myK);
     lift_neighbours<DIM, Q, T>(c, active, t, myR, myF, myK);
+    if (!exact)
+        subtract_block_apply<DIM, Q, T>(c, active, t, myU, myR, sA + lc * G::NL, sB + lc * G::NL,
+                                        sKT + lc * DIM * Q * Q);
     const T *myS = sFD + lc * DIM * G::FDS;      // S_a at a*FDS, lambda_a at a*FDS + Q*Q
     // S^T along the axes 0..DIM-2
 #pragma unroll
@@ -406,12 +506,13 @@ __global__ void __launch_bounds__(256) k_smooth(DGConst<T> c, int cpb, T *__rest
 #pragma unroll
         for (int i = 0; i < Q; ++i) x[i] = myR[G::vidx(0, t, i)];
         const T om = c.omega;
+        const T keep = exact ? T(1) - om : T(1);
 #pragma unroll
         for (int m = 0; m < Q; ++m) {
             T s = T(0);
 #pragma unroll
             for (int i = 0; i < Q; ++i) s += S[m * Q + i] * x[i];
-            un[m] = (T(1) - om) * myU[G::vidx(0, t, m)] + om * s;
+            un[m] = keep * myU[G::vidx(0, t, m)] + om * s;
         }
 #pragma unroll
         for (int i = 0; i < Q; ++i) myU[G::vidx(0, t, i)] = un[i];
@@ -432,16 +533,15 @@ __global__ void __launch_bounds__(256) k_smooth(DGConst<T> c, int cpb, T *__rest
 
 // ---------------------------------------------------------------------------
 // Residual r = b - A u (Alg. 2 stage 3 / Alg. 6 residual traversal) from u and
-// the stored projections of u, with A u = A_KK u_K + N_K u_nb and
-// A_KK u = sum_a Kt_a (x) M (x) M u (sum factorised), optional fused
-// p-restriction: per cell and corner, sum_i hat_corner(x_i) r_i, gathered per
-// vertex afterwards in a fixed order.
+// the stored projections of u, with A u = A_KK u_K + N_K u_nb, and the optional
+// fused p-restriction: per cell and corner, sum_i hat_corner(x_i) r_i, gathered
+// per vertex afterwards in a fixed order.
 // ---------------------------------------------------------------------------
 template <int DIM, int Q, typename T>
 __global__ void __launch_bounds__(256) k_residual(DGConst<T> c, int cpb, int mode, const T *__restrict__ u,
-                                                   const T *__restrict__ b, const T *__restrict__ kappa,
-                                                   const T *__restrict__ tr, T *__restrict__ rout,
-                                                   T *__restrict__ corners) {
+                                                  const T *__restrict__ b, const T *__restrict__ kappa,
+                                                  const T *__restrict__ tr, T *__restrict__ rout,
+                                                  T *__restrict__ corners) {
     using G = Geo<DIM, Q>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sU = reinterpret_cast<T *>(smem_raw);
@@ -470,105 +570,18 @@ __global__ void __launch_bounds__(256) k_residual(DGConst<T> c, int cpb, int mod
         load_neighbour_traces<DIM, Q, T>(c, cell, ci, t, tr, kappa, myF, myK, myK + G::NFACE);
     }
     __syncthreads();
-    // Kt_a = kappa_K K_a + own facet terms of the two faces normal to axis a:
-    // low face  kF_L ( w_L (e0 d0^T + d0 e0^T) + gamma e0 e0^T ),
-    // high face kF_R (-w_R (ep dp^T + dp ep^T) + gamma ep ep^T ),
-    // kF = harmonic mean and w = 1/2 inside, kF = kappa_K and w = 1 on the boundary.
     T *myKT = sKT + lc * DIM * Q * Q;
-    if (active) {
-        const T kK = myK[G::NFACE];
-        for (int e = t; e < DIM * Q * Q; e += G::NF) {
-            const int a = e / (Q * Q), i = (e / Q) % Q, j = e % Q;
-            const bool inL = myK[2 * a] != T(0), inR = myK[2 * a + 1] != T(0);
-            const T kL = inL ? myK[2 * a] : kK, wL = inL ? T(0.5) : T(1);
-            const T kR = inR ? myK[2 * a + 1] : kK, wR = inR ? T(0.5) : T(1);
-            T v = kK * c.K[a][i * Q + j];
-            const T e0i = i == 0 ? T(1) : T(0), e0j = j == 0 ? T(1) : T(0);
-            const T epi = i == Q - 1 ? T(1) : T(0), epj = j == Q - 1 ? T(1) : T(0);
-            v += kL * (wL * (e0i * c.d0[a][j] + c.d0[a][i] * e0j) + c.gamma[a] * e0i * e0j);
-            v += kR * (-wR * (epi * c.dp[a][j] + c.dp[a][i] * epj) + c.gamma[a] * epi * epj);
-            myKT[e] = v;
-        }
-    }
+    build_block_1d<DIM, Q, T>(c, active, t, myK, myKT);
     facet_mass<DIM, Q, T>(c, active, t, myF, myK);   // contains barriers
     T *myR = sR + lc * G::NL;
     T *myU = sU + lc * G::NL;
-    T *myA = sA + lc * G::NL;
-    T *myB = sB + lc * G::NL;
     lift_neighbours<DIM, Q, T>(c, active, t, myR, myF, myK);
-    // A_KK u by sum factorisation
-    if (DIM == 3) {
-        if (active) {   // axis z: a = M_z u, bb = Kt_z u
-            T x[Q];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) x[i] = myU[G::vidx(2, t, i)];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                T sa = T(0), sb = T(0);
-#pragma unroll
-                for (int m = 0; m < Q; ++m) {
-                    sa += c.M[2][i * Q + m] * x[m];
-                    sb += myKT[2 * Q * Q + i * Q + m] * x[m];
-                }
-                myA[G::vidx(2, t, i)] = sa;
-                myB[G::vidx(2, t, i)] = sb;
-            }
-        }
-        __syncthreads();
-        if (active) {   // axis y: c = M_y a, e = Kt_y a + M_y bb
-            T xa[Q], xb[Q];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                xa[i] = myA[G::vidx(1, t, i)];
-                xb[i] = myB[G::vidx(1, t, i)];
-            }
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                T sc = T(0), se = T(0);
-#pragma unroll
-                for (int m = 0; m < Q; ++m) {
-                    sc += c.M[1][i * Q + m] * xa[m];
-                    se += myKT[1 * Q * Q + i * Q + m] * xa[m] + c.M[1][i * Q + m] * xb[m];
-                }
-                myA[G::vidx(1, t, i)] = sc;
-                myB[G::vidx(1, t, i)] = se;
-            }
-        }
-        __syncthreads();
-    } else {
-        if (active) {   // axis y: a = M_y u, bb = Kt_y u
-            T x[Q];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) x[i] = myU[G::vidx(1, t, i)];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                T sa = T(0), sb = T(0);
-#pragma unroll
-                for (int m = 0; m < Q; ++m) {
-                    sa += c.M[1][i * Q + m] * x[m];
-                    sb += myKT[1 * Q * Q + i * Q + m] * x[m];
-                }
-                myA[G::vidx(1, t, i)] = sa;
-                myB[G::vidx(1, t, i)] = sb;
-            }
-        }
-        __syncthreads();
-    }
-    // axis x: y = Kt_x a + M_x bb; r = R - y
+    subtract_block_apply<DIM, Q, T>(c, active, t, myU, myR, sA + lc * G::NL, sB + lc * G::NL, myKT);
     T rr[Q];
     if (active) {
-        T xa[Q], xb[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            xa[i] = myA[G::vidx(0, t, i)];
-            xb[i] = myB[G::vidx(0, t, i)];
-        }
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            T s = T(0);
-#pragma unroll
-            for (int m = 0; m < Q; ++m) s += myKT[i * Q + m] * xa[m] + c.M[0][i * Q + m] * xb[m];
-            rr[i] = myR[G::vidx(0, t, i)] - s;
+            rr[i] = myR[G::vidx(0, t, i)];
             if (mode & RES_NEGATE) rr[i] = -rr[i];
         }
         if (mode & RES_WRITE_R) {
@@ -580,7 +593,6 @@ __global__ void __launch_bounds__(256) k_residual(DGConst<T> c, int cpb, int mod
     if (mode & RES_CORNERS) {
         // partial sums over x of hat_cx(x_i) r_i, then over the tangential axes
         T *px = sF;                     // reuse: [cpb][2][NF]
-        __syncthreads();
         if (active) {
             T p0 = T(0), p1 = T(0);
 #pragma unroll
@@ -618,9 +630,11 @@ constexpr size_t smem_project(int cpb) {
     return (size_t)cpb * (Geo<DIM, Q>::NL + Geo<DIM, Q>::NC) * sizeof(T);
 }
 template <int DIM, int Q, typename T>
-constexpr size_t smem_smooth(int cpb) {
+constexpr size_t smem_smooth(int cpb, bool exact) {
     using G = Geo<DIM, Q>;
-    return (size_t)cpb * (2 * G::NL + G::NFACE * 2 * G::NF + DIM * G::FDS + G::NFACE + 1) * sizeof(T);
+    return (size_t)cpb *
+           (2 * G::NL + G::NFACE * 2 * G::NF + DIM * G::FDS + G::NFACE + 1 + (exact ? 0 : 2 * G::NL + DIM * Q * Q)) *
+           sizeof(T);
 }
 template <int DIM, int Q, typename T>
 constexpr size_t smem_residual(int cpb) {
@@ -643,9 +657,9 @@ struct DGLaunch {
         k_project<DIM, Q, T><<<(unsigned)grid, cpb * G::NF, sm, s>>>(c, cpb, u, e0, tr);
         return cudaGetLastError();
     }
-    static cudaError_t smooth(const DGConst<T> &c, int cpb, T *u, const T *b, const T *kappa, const T *fd,
-                              const T *tri, T *tro, cudaStream_t s) {
-        const size_t sm = smem_smooth<DIM, Q, T>(cpb);
+    static cudaError_t smooth(const DGConst<T> &c, int cpb, int exact, T *u, const T *b, const T *kappa,
+                              const T *fd, const T *tri, T *tro, cudaStream_t s) {
+        const size_t sm = smem_smooth<DIM, Q, T>(cpb, exact != 0);
         static bool attr = false;
         if (!attr) {
             cudaFuncSetAttribute(k_smooth<DIM, Q, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -653,7 +667,7 @@ struct DGLaunch {
         }
         const int64_t grid = (c.ncell + cpb - 1) / cpb;
         if (grid == 0) return cudaSuccess;
-        k_smooth<DIM, Q, T><<<(unsigned)grid, cpb * G::NF, sm, s>>>(c, cpb, u, b, kappa, fd, tri, tro);
+        k_smooth<DIM, Q, T><<<(unsigned)grid, cpb * G::NF, sm, s>>>(c, cpb, exact, u, b, kappa, fd, tri, tro);
         return cudaGetLastError();
     }
     static cudaError_t residual(const DGConst<T> &c, int cpb, int mode, const T *u, const T *b, const T *kappa,
@@ -694,9 +708,9 @@ cudaError_t launch_project_impl(int dim, int q, const DGConst<T> &c, int cpb, T 
     DGMG_DISPATCH(dim, q, project(c, cpb, u, e0, tr, s))
 }
 template <typename T>
-cudaError_t launch_smooth_impl(int dim, int q, const DGConst<T> &c, int cpb, T *u, const T *b, const T *kappa,
-                               const T *fd, const T *tri, T *tro, cudaStream_t s) {
-    DGMG_DISPATCH(dim, q, smooth(c, cpb, u, b, kappa, fd, tri, tro, s))
+cudaError_t launch_smooth_impl(int dim, int q, const DGConst<T> &c, int cpb, int exact, T *u, const T *b,
+                               const T *kappa, const T *fd, const T *tri, T *tro, cudaStream_t s) {
+    DGMG_DISPATCH(dim, q, smooth(c, cpb, exact, u, b, kappa, fd, tri, tro, s))
 }
 template <typename T>
 cudaError_t launch_residual_impl(int dim, int q, const DGConst<T> &c, int cpb, int mode, const T *u, const T *b,

@@ -65,7 +65,7 @@ template <typename T>
 struct CGLevelDev {
     int m[3];              // interior vertices per axis
     int64_t nv;
-    const T *st;           // [nv][3^d] stencil, offset (sx+1) + 3 (sy+1) + 9 (sz+1)
+    const T *st;           // [3^d][nv] stencil, offset (sx+1) + 3 (sy+1) + 9 (sz+1)
     // transfer to the next coarser level (per axis tables); null on the coarsest
     const int *pl_lo[3];   // fine vertex -> lower coarse parent (-1 if none)
     const int *pl_hi[3];   // fine vertex -> upper coarse parent (-1 if none)
@@ -76,18 +76,13 @@ struct CGLevelDev {
     int mc[3];               // interior vertices per axis of the coarser level
 };
 
-struct DGBuffers {
-    const void *kappa;     // [ncell] T
-    const void *fd;        // [ncell][d][q*q+q] T: S (row m, col i) then lambda
-};
-
 // Launch wrappers (implemented per precision in dg_fp64.cu / dg_fp32.cu).
 // All return cudaError_t of the launch.
 template <typename T>
 cudaError_t launch_project(int dim, int q, const DGConst<T> &c, int cpb, T *u, const T *e0,
                            T *tr, cudaStream_t s);
 template <typename T>
-cudaError_t launch_smooth(int dim, int q, const DGConst<T> &c, int cpb, T *u, const T *b,
+cudaError_t launch_smooth(int dim, int q, const DGConst<T> &c, int cpb, int exact, T *u, const T *b,
                           const T *kappa, const T *fd, const T *tr_in, T *tr_out, cudaStream_t s);
 // mode bits for launch_residual
 enum { RES_HAS_B = 1, RES_WRITE_R = 2, RES_CORNERS = 4, RES_NEGATE = 8 };
