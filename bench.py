@@ -1,0 +1,330 @@
+"""Benchmark of the SIPG hp-multigrid hot path on GB300 (one JSON line on stdout).
+
+Workload: 3D unit cube, 32^3 hexahedra, GLL degree p = 3 (64 DoF per cell,
+2,097,152 DoF), kappa = 1, f = 3 pi^2 prod_i sin(pi x_i); FP64 PCG with the
+hp V(2,2) cycle as preconditioner, solved from x = 0 to ||b - A x|| <= 1e-10 ||b||.
+One bench step is one complete solve: every stage of the path (warm-up
+projections, single-touch smoothing steps, residual + p-restriction, Q1
+levels, coarsest solve, p-prolongation, FP64 apply and CG vector work) runs
+in it. The metric is GDoF/s per smoothing step: DoF x (fine-level
+smoothing steps executed in the step) / step time, so everything else the
+solve does counts against it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+--impl reference times the plain CPU oracle on the host cores (the same
+metric and unit, on a bounded sample of the workload). Under torchrun (N > 1)
+every rank solves its own replica of the workload (weak scaling, no
+collective on the data path); rank 0 prints.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_CELLS = (32, 32, 32)
+DEGREE = 3
+RTOL = 1e-10
+WORKLOAD = "sipg_3d_32^3_p3_kappa1_fp64_pcg_vcycle22"
+SAMPLE_CELLS = (16, 16, 16)      # bounded CPU sample: same p, 1/8 of the DoFs
+SAMPLE_STEPS = 60
+FP64_PEAK_TFLOPS = 1.25          # nominal GB300 dense FP64 (no FP64 entry in the measured peaks)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reduce_max_sum(values, world, device):
+    """Max of values[0] and sum of values[1] over ranks (identity for one rank)."""
+    if world == 1:
+        return values[0], values[1]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([values[0]], dtype=torch.float64, device=device)
+    s = torch.tensor([values[1]], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(s, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(s.item())
+
+
+# ---------------------------------------------------------------- flop model
+def smooth_flops(n, q):
+    """Floating-point operations of one launch of the fused smoothing kernel as
+    implemented (an FMA counts 2, a division 1): facet mass on the two
+    neighbour fields of every interior face side, lifting, S^T / Lambda^-1 / S
+    along every axis, damped update, new traces of every face."""
+    d = len(n)
+    ncell = 1
+    for v in n:
+        ncell *= v
+    nf = q ** (d - 1)
+    nl = q ** d
+    sides = 0                       # interior face sides (each interior facet has two)
+    for a in range(d):
+        other = ncell // n[a]
+        sides += 2 * (n[a] - 1) * other
+    facet_mass = sides * 2 * (d - 1) * nf * q * 2
+    lift = sides * nf * (q * 2 + 4)
+    per_cell = 2 * d * nl * q * 2 + nl * 3 + nl * 3 + d * nf * 2 * q * 2
+    return facet_mass + lift + ncell * per_cell
+
+
+def smooth_bytes_per_cell(d, q, s=8):
+    """Algorithmic HBM bytes of one cell of the smoothing step: read u, b, write u;
+    read the 2d neighbour traces (value + derivative) and write the cell's own;
+    read the per-cell fast-diagonalisation factors d (q^2 + q) and kappa of the
+    cell and its neighbours."""
+    nl = q ** d
+    nf = q ** (d - 1)
+    return s * (3 * nl + 2 * (2 * d * 2 * nf) + d * (q * q + q) + (2 * d + 1))
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            if len(r) < 9:
+                continue
+            for k, nm in enumerate(names):
+                if r[5 + k].strip().lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- CPU oracle
+def cpu_oracle_chunks(chunks, steps_per_chunk):
+    """Run the oracle's Alg. 4 smoothing steps on the bounded sample in a
+    single-threaded subprocess: one block-inverse set-up, then `chunks` timed
+    chunks of `steps_per_chunk` steps. Returns (ndof, [seconds per chunk])."""
+    code = f"""
+import json, os, sys, time
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+from oracle import sipg
+m = sipg.Mesh({SAMPLE_CELLS!r}, {DEGREE})
+bj = sipg.BlockJacobi(m)
+rng = np.random.default_rng(0)
+u, b = rng.normal(size=m.ndof), rng.normal(size=m.ndof)
+secs = []
+for _ in range({chunks}):
+    t = time.perf_counter()
+    u, _ = bj.step_alg4(u, b, 0.8, {steps_per_chunk})
+    secs.append(time.perf_counter() - t)
+print(json.dumps({{"ndof": m.ndof, "seconds": secs}}))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    return r["ndof"], r["seconds"]
+
+
+def cpu_oracle_rate(steps):
+    ndof, secs = cpu_oracle_chunks(1, steps)
+    return ndof * steps / secs[0] / 1e9, secs[0], ndof
+
+
+def sample_text(steps):
+    return (f"oracle Alg. 4 smoothing steps on {SAMPLE_CELLS[0]}x{SAMPLE_CELLS[1]}x{SAMPLE_CELLS[2]} cells, p={DEGREE} "
+            f"(1/8 of the workload's DoF, same degree), {steps} steps after the block-inverse set-up, "
+            f"one thread, FP64")
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    steps_per = 10
+    ndof, allsecs = cpu_oracle_chunks(args.warmup + args.steps, steps_per)
+    secs = allsecs[args.warmup:]
+    value = ndof * steps_per * len(secs) / sum(secs) / 1e9
+    line = {
+        "impl": "reference", "metric": "GDoF/s per smoothing step", "value": value, "unit": "GDoF/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(secs) / len(secs), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": sample_text(steps_per)},
+        "cpu_baseline": {"value": value, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+                         "sample": sample_text(steps_per)},
+        "e2e": {"value": value, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gb300(args):
+    import numpy as np
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2510_00998_gb300 import dgmg
+
+    ctx = dgmg.Context(N_CELLS, DEGREE, rtol=RTOL)
+    ndof = ctx.ndof
+    d, q = 3, DEGREE + 1
+    # right-hand side b_i = (f, phi_i) from f at the library's quadrature points
+    mq = DEGREE + 2
+    xq = torch.empty(ctx.info.ncell * mq ** 3 * 3, dtype=torch.float64, device=dev)
+    ctx.quad_points(xq)
+    X = xq.view(-1, 3)
+    fq = (3 * np.pi ** 2) * torch.sin(np.pi * X[:, 0]) * torch.sin(np.pi * X[:, 1]) * torch.sin(np.pi * X[:, 2])
+    b = torch.empty(ndof, dtype=torch.float64, device=dev)
+    ctx.load_vector(fq.contiguous(), b)
+    x = torch.zeros_like(b)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def one_solve():
+        x.zero_()
+        st, _ = ctx.solve(b, x)
+        return st
+
+    for _ in range(args.warmup):
+        one_solve()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    ctx.profile(True)
+    launches0 = dgmg.kernel_launches()
+    total_ms, iters, relres = 0.0, [], []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        st = one_solve()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        iters.append(st.iterations)
+        relres.append(st.rel_residual)
+    launches = dgmg.kernel_launches() - launches0
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    smooth_steps_total = prof["smooth"][1]
+    units_local = float(ndof) * smooth_steps_total
+    t_max, units = reduce_max_sum((total_ms, units_local), world, dev)
+    value = units / (t_max * 1e-3) / 1e9
+    # roofline of the dominant kernel (the fused smoothing step)
+    sm_ms, sm_n = prof["smooth"]
+    avg_ms = sm_ms / max(sm_n, 1)
+    flops = smooth_flops(N_CELLS, q)
+    achieved = flops / (avg_ms * 1e-3) / 1e12
+    shares = {k: round(v[0] / max(sum(w[0] for w in prof.values()), 1e-30), 4) for k, v in prof.items()}
+
+    # end to end through the host-buffer entry point
+    bh = b.cpu().pin_memory()
+    xh = torch.zeros(ndof, dtype=torch.float64).pin_memory()
+    e2e_ms = 0.0
+    e2e_units = 0.0
+    for k in range(args.warmup + args.steps):
+        xh.zero_()
+        t = time.perf_counter()
+        st = ctx.solve_host(bh, xh)
+        dt = time.perf_counter() - t
+        if k >= args.warmup:
+            e2e_ms += 1e3 * dt
+            e2e_units += float(ndof) * st.iterations * (ctx.opts.nu_pre + ctx.opts.nu_post)
+    e2e_t, e2e_u = reduce_max_sum((e2e_ms, e2e_units), world, dev)
+
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            v, s, _ = cpu_oracle_rate(SAMPLE_STEPS)
+            cpu = {"value": v, "unit": "GDoF/s", "cores": 1, "kind": "oracle", "sample": sample_text(SAMPLE_STEPS)}
+        line = {
+            "metric": "GDoF/s per smoothing step", "value": value, "unit": "GDoF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": list(N_CELLS), "p": DEGREE, "ndof": ndof,
+                       "kappa": "1", "rhs": "3 pi^2 prod sin(pi x_i)", "rtol": RTOL, "cycle": "V(2,2)",
+                       "outer": "FP64 PCG", "step": "one full solve from x=0",
+                       "l2": "flushed (256 MB write) before every timed step, outside the step's events",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                         "kernel": "k_smooth<3,4,double>", "avg_launch_ms": avg_ms,
+                         "flops_per_launch": flops,
+                         "hbm_bytes_per_launch": smooth_bytes_per_cell(d, q) * ctx.info.ncell,
+                         "peak_note": "nominal FP64 1.25 TFLOP/s (FMA loop measured 1.257 on this pool)"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_u / (e2e_t * 1e-3) / 1e9, "unit": "GDoF/s",
+                    "h2d_bytes_per_step": 2 * 8 * ndof, "d2h_bytes_per_step": 8 * ndof},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "solves_per_s": args.steps / (t_max * 1e-3),
+            "iterations": statistics.median(iters), "rel_residual_max": max(relres),
+            "smoothing_steps": smooth_steps_total, "stage_share": shares,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -227,8 +227,28 @@ int dgmg_h_prolong(dgmg_ctx *ctx, int level, const double *ec, double *uf, void 
 /* Coarsest-level solve e = A_c^{-1} r (dense, FP64; Alg. 6 coarse solve). */
 int dgmg_coarse_solve(dgmg_ctx *ctx, const double *r, double *e, void *stream);
 
-/* Unknowns of Q1 level `level` (HOST query). */
+/* Unknowns of Q1 level `level` (HOST query); -1 if out of range. */
 int64_t dgmg_cg_size(const dgmg_ctx *ctx, int level);
+
+/* ---- instrumentation ---- */
+
+/*
+ * Per-stage device time: while enabled, every stage launch of ctx is bracketed
+ * by CUDA events recorded on the launching stream. Stages (index into the
+ * arrays of dgmg_profile_read): 0 projection, 1 smoothing step, 2 residual
+ * (apply / residual / residual+restriction), 3 Q1 levels (vertex gather,
+ * h-cycle, coarsest solve), 4 vector kernels of the outer CG loop.
+ * dgmg_profile(ctx, on) enables or disables it and clears the accumulators.
+ */
+int dgmg_profile(dgmg_ctx *ctx, int enable);
+
+/* Waits for the recorded events and writes, for the first nstage stages, the
+ * summed milliseconds and the number of timed launches since the last read
+ * (HOST arrays); then clears the accumulators. */
+int dgmg_profile_read(dgmg_ctx *ctx, double *ms, long long *launches, int nstage);
+
+/* Number of CUDA kernels this library has launched in this process. */
+long long dgmg_kernel_launches(void);
 
 #ifdef __cplusplus
 }

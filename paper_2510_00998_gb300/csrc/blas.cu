@@ -135,6 +135,7 @@ inline unsigned grid_for(int64_t n) {
 }  // namespace
 
 cudaError_t launch_dot(int64_t n, const double *x, const double *y, double *partials, double *out, cudaStream_t s) {
+    count_launches(2);
     k_dot_partial<<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(n, x, y, partials);
     k_reduce<<<1, 512, 0, s>>>(DOT_BLOCKS, partials, out);
     return cudaGetLastError();
@@ -142,6 +143,7 @@ cudaError_t launch_dot(int64_t n, const double *x, const double *y, double *part
 
 cudaError_t launch_dot2(int64_t n, const double *x, const double *y, const double *z, double *partials,
                         double *out_xy, double *out_zy, cudaStream_t s) {
+    count_launches(3);
     k_dot2_partial<<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(n, x, y, z, partials);
     k_reduce<<<1, 512, 0, s>>>(DOT_BLOCKS, partials, out_xy);
     k_reduce<<<1, 512, 0, s>>>(DOT_BLOCKS, partials + DOT_BLOCKS, out_zy);
@@ -149,32 +151,38 @@ cudaError_t launch_dot2(int64_t n, const double *x, const double *y, const doubl
 }
 
 cudaError_t launch_cast_d2f(int64_t n, const double *x, float *y, cudaStream_t s) {
+    count_launches(1);
     k_d2f<<<grid_for(n), 256, 0, s>>>(n, x, y);
     return cudaGetLastError();
 }
 
 cudaError_t launch_cast_f2d(int64_t n, const float *x, double *y, cudaStream_t s) {
+    count_launches(1);
     k_f2d<<<grid_for(n), 256, 0, s>>>(n, x, y);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_update_xr(int64_t n, double *x, double *r, const double *p, const double *q,
                                  const double *scal, cudaStream_t s) {
+    count_launches(1);
     k_update_xr<<<grid_for(n), 256, 0, s>>>(n, x, r, p, q, scal);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_update_p(int64_t n, double *p, const double *z, const double *scal, cudaStream_t s) {
+    count_launches(1);
     k_update_p<<<grid_for(n), 256, 0, s>>>(n, p, z, scal);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sub(int64_t n, const double *a, const double *b, double *out, cudaStream_t s) {
+    count_launches(1);
     k_sub<<<grid_for(n), 256, 0, s>>>(n, a, b, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_copy_scalar(const double *src, double *dst, cudaStream_t s) {
+    count_launches(1);
     k_copy_scalar<<<1, 1, 0, s>>>(src, dst);
     return cudaGetLastError();
 }
@@ -185,6 +193,7 @@ cudaError_t launch_quad_points(int dim, int q, const int *n, int mq, const doubl
     const int64_t npc = dim == 3 ? (int64_t)mq * mq * mq : (int64_t)mq * mq;
     const int64_t tot = ncell * npc;
     if (tot == 0) return cudaSuccess;
+    count_launches(1);
     k_quad_points<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(dim, n[0], n[1], dim == 3 ? n[2] : 1, mq, xq1, xq,
                                                                  ncell);
     return cudaGetLastError();
@@ -195,6 +204,7 @@ cudaError_t launch_load_vector(int dim, int q, int mq, int64_t ncell, const doub
     const int64_t nl = dim == 3 ? (int64_t)q * q * q : (int64_t)q * q;
     const int64_t tot = ncell * nl;
     if (tot == 0) return cudaSuccess;
+    count_launches(1);
     k_load_vector<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(dim, q, mq, ncell, V, wq, fq, b);
     return cudaGetLastError();
 }

@@ -167,6 +167,7 @@ template <typename T>
 cudaError_t launch_corner_gather(int dim, const int *n, const T *corners, T *b0, cudaStream_t s) {
     const int64_t nv = dim == 3 ? (int64_t)(n[0] - 1) * (n[1] - 1) * (n[2] - 1) : (int64_t)(n[0] - 1) * (n[1] - 1);
     if (nv <= 0) return cudaSuccess;
+    count_launches(1);
     if (dim == 3)
         k_corner_gather<3, T><<<blocks_for(nv), TPB, 0, s>>>(n[0], n[1], n[2], corners, b0);
     else
@@ -178,6 +179,7 @@ template <typename T>
 cudaError_t launch_cg_jacobi(int dim, const CGLevelDev<T> &L, const T *u_in, const T *b, T *u_out, T omega,
                              bool zero_guess, cudaStream_t s) {
     if (L.nv <= 0) return cudaSuccess;
+    count_launches(1);
     if (dim == 3)
         k_cg_jacobi<3, T><<<blocks_for(L.nv), TPB, 0, s>>>(L, u_in, b, u_out, omega, zero_guess ? 1 : 0);
     else
@@ -188,6 +190,7 @@ cudaError_t launch_cg_jacobi(int dim, const CGLevelDev<T> &L, const T *u_in, con
 template <typename T>
 cudaError_t launch_cg_residual(int dim, const CGLevelDev<T> &L, const T *u, const T *b, T *r, cudaStream_t s) {
     if (L.nv <= 0) return cudaSuccess;
+    count_launches(1);
     if (dim == 3)
         k_cg_residual<3, T><<<blocks_for(L.nv), TPB, 0, s>>>(L, u, b, r);
     else
@@ -199,6 +202,7 @@ template <typename T>
 cudaError_t launch_h_restrict(int dim, const CGLevelDev<T> &L, const T *rf, T *rc, cudaStream_t s) {
     const int64_t ncv = dim == 3 ? (int64_t)L.mc[0] * L.mc[1] * L.mc[2] : (int64_t)L.mc[0] * L.mc[1];
     if (ncv <= 0) return cudaSuccess;
+    count_launches(1);
     if (dim == 3)
         k_h_restrict<3, T><<<blocks_for(ncv), TPB, 0, s>>>(L, rf, rc);
     else
@@ -209,6 +213,7 @@ cudaError_t launch_h_restrict(int dim, const CGLevelDev<T> &L, const T *rf, T *r
 template <typename T>
 cudaError_t launch_h_prolong(int dim, const CGLevelDev<T> &L, const T *ec, T *uf, cudaStream_t s) {
     if (L.nv <= 0) return cudaSuccess;
+    count_launches(1);
     if (dim == 3)
         k_h_prolong<3, T><<<blocks_for(L.nv), TPB, 0, s>>>(L, ec, uf);
     else
@@ -219,6 +224,7 @@ cudaError_t launch_h_prolong(int dim, const CGLevelDev<T> &L, const T *ec, T *uf
 template <typename T>
 cudaError_t launch_coarse_solve(int64_t nc, const double *Ainv, const T *r, T *e, cudaStream_t s) {
     if (nc <= 0) return cudaSuccess;
+    count_launches(1);
     k_coarse_solve<T><<<blocks_for(nc), TPB, 0, s>>>(nc, Ainv, r, e);
     return cudaGetLastError();
 }

@@ -14,6 +14,8 @@
 
 namespace dgmg {
 
+std::atomic<long long> g_kernel_launches{0};
+
 // ------------------------------------------------------------------- errors
 static thread_local std::string g_last_error;
 
@@ -282,6 +284,59 @@ struct CGDev {
     T *wtab = nullptr;
 };
 
+// Per-stage device time, recorded with CUDA events on the launching stream
+// around every stage launch while profiling is on (dgmg_profile).
+enum { ST_PROJECT = 0, ST_SMOOTH = 1, ST_RESIDUAL = 2, ST_CG = 3, ST_VECTOR = 4, ST_N = 5 };
+struct StageProfiler {
+    bool on = false;
+    std::vector<cudaEvent_t> ev;        // pairs: 2k start, 2k+1 stop
+    std::vector<int> stage;
+    size_t used = 0;
+    double ms[ST_N] = {0};
+    long long cnt[ST_N] = {0};
+    int open_stage = -1;
+    void begin(int st, cudaStream_t s) {
+        if (!on) return;
+        if (2 * used + 2 > ev.size()) {
+            cudaEvent_t a, b;
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            ev.push_back(a);
+            ev.push_back(b);
+            stage.push_back(st);
+        }
+        stage[used] = st;
+        cudaEventRecord(ev[2 * used], s);
+        open_stage = st;
+    }
+    void end(cudaStream_t s) {
+        if (!on || open_stage < 0) return;
+        cudaEventRecord(ev[2 * used + 1], s);
+        ++used;
+        open_stage = -1;
+    }
+    void collect() {
+        for (size_t k = 0; k < used; ++k) {
+            cudaEventSynchronize(ev[2 * k + 1]);
+            float m = 0.f;
+            cudaEventElapsedTime(&m, ev[2 * k], ev[2 * k + 1]);
+            ms[stage[k]] += m;
+            cnt[stage[k]] += 1;
+        }
+        used = 0;
+    }
+    void reset() {
+        collect();
+        for (int i = 0; i < ST_N; ++i) {
+            ms[i] = 0;
+            cnt[i] = 0;
+        }
+    }
+    ~StageProfiler() {
+        for (auto e : ev) cudaEventDestroy(e);
+    }
+};
+
 struct dgmg_ctx {
     int dim = 0, p = 0, q = 0;
     int n[3] = {1, 1, 1};
@@ -305,6 +360,7 @@ struct dgmg_ctx {
     double *quad_x1 = nullptr, *quad_V = nullptr, *quad_w = nullptr;
     std::vector<void *> allocs;
     size_t bytes = 0;
+    StageProfiler prof;
 
     template <typename T>
     int alloc(T **ptr, size_t count) {
@@ -657,19 +713,29 @@ int dg_vcycle(dgmg_ctx &C, const T *r, T *z, cudaStream_t s) {
     LC(cudaMemsetAsync(D.tr[0], 0, sizeof(T) * trn, s));   // projections of z = 0
     int cur = 0;
     for (int k = 0; k < C.opts.nu_pre; ++k) {
+        C.prof.begin(ST_SMOOTH, s);
         LC(launch_smooth<T>(C.dim, C.q, D.c, C.cpb, exact_block(C), z, r, D.kappa, D.fd, D.tr[cur], D.tr[cur ^ 1], s));
+        C.prof.end(s);
         cur ^= 1;
     }
+    C.prof.begin(ST_RESIDUAL, s);
     LC(launch_residual<T>(C.dim, C.q, D.c, C.cpb, RES_HAS_B | RES_CORNERS, z, r, D.kappa, D.tr[cur], nullptr,
                           D.corners, s));
+    C.prof.end(s);
     auto &lv = cgl<T>(C);
+    C.prof.begin(ST_CG, s);
     LC(launch_corner_gather<T>(C.dim, C.n, D.corners, lv[0].b, s));
     T *e0 = nullptr;
     RC(cg_vcycle<T>(C, 0, s, &e0));
+    C.prof.end(s);
+    C.prof.begin(ST_PROJECT, s);
     LC(launch_project<T>(C.dim, C.q, D.c, C.cpb, z, e0, D.tr[0], s));   // z += P e0, projections
+    C.prof.end(s);
     cur = 0;
     for (int k = 0; k < C.opts.nu_post; ++k) {
+        C.prof.begin(ST_SMOOTH, s);
         LC(launch_smooth<T>(C.dim, C.q, D.c, C.cpb, exact_block(C), z, r, D.kappa, D.fd, D.tr[cur], D.tr[cur ^ 1], s));
+        C.prof.end(s);
         cur ^= 1;
     }
     return DGMG_OK;
@@ -677,9 +743,13 @@ int dg_vcycle(dgmg_ctx &C, const T *r, T *z, cudaStream_t s) {
 
 int vcycle64(dgmg_ctx &C, const double *r, double *z, cudaStream_t s) {
     if (C.opts.precision == DGMG_MIXED_FP32) {
+        C.prof.begin(ST_VECTOR, s);
         LC(launch_cast_d2f(C.ndof, r, C.r32, s));
+        C.prof.end(s);
         RC(dg_vcycle<float>(C, C.r32, C.z32, s));
+        C.prof.begin(ST_VECTOR, s);
         LC(launch_cast_f2d(C.ndof, C.z32, z, s));
+        C.prof.end(s);
         return DGMG_OK;
     }
     return dg_vcycle<double>(C, r, z, s);
@@ -688,9 +758,13 @@ int vcycle64(dgmg_ctx &C, const double *r, double *z, cudaStream_t s) {
 // y = A u (negate = false) or r = b - A u, FP64
 int apply64(dgmg_ctx &C, const double *u, const double *b, double *out, cudaStream_t s) {
     DGDev<double> &D = C.d64;
+    C.prof.begin(ST_PROJECT, s);
     LC(launch_project<double>(C.dim, C.q, D.c, C.cpb, const_cast<double *>(u), nullptr, D.tr[0], s));
+    C.prof.end(s);
     const int mode = b ? (RES_HAS_B | RES_WRITE_R) : (RES_WRITE_R | RES_NEGATE);
+    C.prof.begin(ST_RESIDUAL, s);
     LC(launch_residual<double>(C.dim, C.q, D.c, C.cpb, mode, u, b, D.kappa, D.tr[0], out, nullptr, s));
+    C.prof.end(s);
     return DGMG_OK;
 }
 
@@ -908,10 +982,15 @@ int dgmg_smooth(dgmg_ctx *C, double *u, const double *b, int nsteps, void *strea
     if (nsteps < 0) return fail(DGMG_EINVAL, "nsteps must be >= 0");
     cudaStream_t s = (cudaStream_t)stream;
     DGDev<double> &D = C->d64;
+    C->prof.begin(ST_PROJECT, s);
     LC(launch_project<double>(C->dim, C->q, D.c, C->cpb, u, nullptr, D.tr[0], s));
+    C->prof.end(s);
     int cur = 0;
     for (int k = 0; k < nsteps; ++k) {
-        LC(launch_smooth<double>(C->dim, C->q, D.c, C->cpb, exact_block(*C), u, b, D.kappa, D.fd, D.tr[cur], D.tr[cur ^ 1], s));
+        C->prof.begin(ST_SMOOTH, s);
+        LC(launch_smooth<double>(C->dim, C->q, D.c, C->cpb, exact_block(*C), u, b, D.kappa, D.fd, D.tr[cur],
+                                 D.tr[cur ^ 1], s));
+        C->prof.end(s);
         cur ^= 1;
     }
     return DGMG_OK;
@@ -1057,10 +1136,12 @@ int dgmg_solve(dgmg_ctx *C, const double *b, double *x, dgmg_stats *stats, void 
         zz = zz0;
         for (it = 1; it <= C->opts.maxit; ++it) {
             RC(apply64(*C, p, nullptr, q, s));                   // q = A p
+            C->prof.begin(ST_VECTOR, s);
             LC(launch_dot(n, p, q, C->partials, C->scal + S_PQ, s));
             if (flexible) LC(cudaMemcpyAsync(rold, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
             LC(launch_pcg_update_xr(n, x, r, p, q, C->scal, s));   // alpha = rz / pq
             LC(launch_dot(n, r, r, C->partials, C->scal + S_RR, s));
+            C->prof.end(s);
             RC(read_scalar(C, S_RR, &rr, s));
             if (!std::isfinite(rr)) {
                 status = fail(DGMG_ENONFINITE, "residual norm is not finite");
@@ -1073,13 +1154,16 @@ int dgmg_solve(dgmg_ctx *C, const double *b, double *x, dgmg_stats *stats, void 
                 break;
             }
             RC(vcycle64(*C, r, z, s));
+            C->prof.begin(ST_VECTOR, s);
             if (flexible)
                 LC(launch_dot2(n, r, z, rold, C->partials, C->scal + S_RZN, C->scal + S_RZO, s));
             else
                 LC(launch_dot(n, r, z, C->partials, C->scal + S_RZN, s));
+            count_launches(1);
             k_scalar_beta<<<1, 1, 0, s>>>(C->scal, flexible ? 1 : 0);
             LC(cudaGetLastError());
             LC(launch_pcg_update_p(n, p, z, C->scal, s));
+            C->prof.end(s);
         }
         if (it > C->opts.maxit) it = C->opts.maxit;
         LC(launch_dot(n, z, z, C->partials, C->scal + S_ZZ, s));
@@ -1120,5 +1204,29 @@ int dgmg_solve_host(dgmg_ctx *C, const double *b_host, double *x_host, dgmg_stat
         stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return rc;
 }
+
+int dgmg_profile(dgmg_ctx *C, int enable) {
+    RC(check_ctx(C));
+    C->prof.reset();
+    C->prof.on = enable != 0;
+    return DGMG_OK;
+}
+
+int dgmg_profile_read(dgmg_ctx *C, double *ms, long long *launches, int nstage) {
+    RC(check_ctx(C));
+    if (nstage < 0 || (nstage > 0 && (!ms || !launches))) return fail(DGMG_EINVAL, "bad output arrays");
+    C->prof.collect();
+    for (int i = 0; i < nstage && i < ST_N; ++i) {
+        ms[i] = C->prof.ms[i];
+        launches[i] = C->prof.cnt[i];
+    }
+    for (int i = 0; i < ST_N; ++i) {
+        C->prof.ms[i] = 0;
+        C->prof.cnt[i] = 0;
+    }
+    return DGMG_OK;
+}
+
+long long dgmg_kernel_launches(void) { return g_kernel_launches.load(); }
 
 }  // extern "C"

@@ -654,6 +654,7 @@ struct DGLaunch {
         }
         const int64_t grid = (c.ncell + cpb - 1) / cpb;
         if (grid == 0) return cudaSuccess;
+        count_launches(1);
         k_project<DIM, Q, T><<<(unsigned)grid, cpb * G::NF, sm, s>>>(c, cpb, u, e0, tr);
         return cudaGetLastError();
     }
@@ -667,6 +668,7 @@ struct DGLaunch {
         }
         const int64_t grid = (c.ncell + cpb - 1) / cpb;
         if (grid == 0) return cudaSuccess;
+        count_launches(1);
         k_smooth<DIM, Q, T><<<(unsigned)grid, cpb * G::NF, sm, s>>>(c, cpb, exact, u, b, kappa, fd, tri, tro);
         return cudaGetLastError();
     }
@@ -680,6 +682,7 @@ struct DGLaunch {
         }
         const int64_t grid = (c.ncell + cpb - 1) / cpb;
         if (grid == 0) return cudaSuccess;
+        count_launches(1);
         k_residual<DIM, Q, T><<<(unsigned)grid, cpb * G::NF, sm, s>>>(c, cpb, mode, u, b, kappa, tr, r, corners);
         return cudaGetLastError();
     }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -24,6 +25,10 @@ int cuda_fail(cudaError_t e, const char *what);
         cudaError_t e_ = (call);                              \
         if (e_ != cudaSuccess) return ::dgmg::cuda_fail(e_, #call); \
     } while (0)
+
+// Process-wide count of kernels launched by the library (dgmg_kernel_launches).
+extern std::atomic<long long> g_kernel_launches;
+inline void count_launches(int k) { g_kernel_launches.fetch_add(k, std::memory_order_relaxed); }
 
 // ------------------------------------------------------- reference element
 // 1D GLL Lagrange element of degree p on [-1,1] (paper Sec. 2.2), computed

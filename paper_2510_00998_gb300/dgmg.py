@@ -83,7 +83,17 @@ _SIGS = {
     "dgmg_h_prolong": (_I, [_P, _I, _P, _P, _P]),
     "dgmg_coarse_solve": (_I, [_P, _P, _P, _P]),
     "dgmg_cg_size": (ctypes.c_int64, [_P, _I]),
+    "dgmg_profile": (_I, [_P, _I]),
+    "dgmg_profile_read": (_I, [_P, _P, _P, _I]),
+    "dgmg_kernel_launches": (ctypes.c_longlong, []),
 }
+
+STAGES = ("project", "smooth", "residual", "cg_levels", "vector")
+
+
+def kernel_launches():
+    """Kernels launched by libdgmg in this process."""
+    return int(load().dgmg_kernel_launches())
 
 _lib = None
 
@@ -247,6 +257,18 @@ class Context:
 
     def coarse_solve(self, r, e, stream=None):
         _check(self.lib.dgmg_coarse_solve(self.h, _ptr(r), _ptr(e), _stream(stream)))
+
+    def profile(self, enable=True):
+        _check(self.lib.dgmg_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{stage: (milliseconds, launches)} since the last read."""
+        import numpy as np
+        ms = np.zeros(len(STAGES))
+        cnt = np.zeros(len(STAGES), dtype=np.int64)
+        _check(self.lib.dgmg_profile_read(self.h, ms.ctypes.data_as(ctypes.c_void_p),
+                                          cnt.ctypes.data_as(ctypes.c_void_p), len(STAGES)))
+        return {s: (float(ms[i]), int(cnt[i])) for i, s in enumerate(STAGES)}
 
     def trace_size(self):
         d, q = self.info.dim, self.info.q
