@@ -209,6 +209,26 @@ int dgmg_project(dgmg_ctx *ctx, double *u, const double *e, double *traces, void
 int dgmg_residual_restrict(dgmg_ctx *ctx, const double *u, const double *b,
                            const double *traces, double *r, double *rc, void *stream);
 
+/*
+ * Same result as dgmg_residual_restrict, without allocating anything: for
+ * callers that cannot allocate device memory when they call (work recorded
+ * into a CUDA graph during stream capture, loops that forbid allocation after
+ * start-up, fixed memory budgets). The paper has no counterpart; this is an
+ * interface variant of the residual + p-restriction stage.
+ * The 2^d corner partial sums per cell go to one fixed device array of 2^21
+ * doubles (16 MiB) that every GPU loading the library keeps until exit;
+ * meshes needing more (more than 262,144 hexahedra or 524,288 quadrilaterals)
+ * are rejected with DGMG_EINVAL. The first call on a device looks up that
+ * array's device address (a one-time set-up per device, made with that device
+ * current); make that first call before any stream capture. All calls share
+ * the array: calls whose GPU work overlaps in time (other streams, other
+ * threads, other contexts on the same device) race and must be serialised
+ * by the caller. Every call overwrites the sums it reads, so no clearing is
+ * needed between calls.
+ */
+int dgmg_residual_restrict_noalloc(dgmg_ctx *ctx, const double *u, const double *b,
+                                   const double *traces, double *r, double *rc, void *stream);
+
 /* Q1 level `level` (0 = first Q1 level): `nsteps` damped point-Jacobi steps
  * u <- u + omega_cg D^{-1}(b - A_l u) (Sec. 2.4), FP64, u in/out. */
 int dgmg_cg_smooth(dgmg_ctx *ctx, int level, double *u, const double *b, int nsteps,

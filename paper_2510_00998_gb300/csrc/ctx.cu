@@ -1230,3 +1230,24 @@ int dgmg_profile_read(dgmg_ctx *C, double *ms, long long *launches, int nstage) 
 long long dgmg_kernel_launches(void) { return g_kernel_launches.load(); }
 
 }  // extern "C"
+
+// ------------------------------------------------ scratch-parameterised stage
+namespace dgmg {
+
+// Per-cell corner partial sums needed by the residual + p-restriction of ctx.
+int64_t corner_scratch_count(const dgmg_ctx *C) { return C->ncell * (int64_t)(1 << C->dim); }
+
+// dgmg_residual_restrict with the corner partial sums written to `corner_scratch`
+// (corner_scratch_count(C) doubles) instead of the ctx's own buffer.
+int residual_restrict_with_scratch(dgmg_ctx *C, const double *u, const double *b, const double *traces,
+                                   double *r, double *rc, double *corner_scratch, cudaStream_t s) {
+    int mode = RES_HAS_B;
+    if (r) mode |= RES_WRITE_R;
+    if (rc) mode |= RES_CORNERS;
+    LC(launch_residual<double>(C->dim, C->q, C->d64.c, C->cpb, mode, u, b, C->d64.kappa, traces, r,
+                               corner_scratch, s));
+    if (rc) LC(launch_corner_gather<double>(C->dim, C->n, corner_scratch, rc, s));
+    return DGMG_OK;
+}
+
+}  // namespace dgmg

@@ -130,6 +130,11 @@ cudaError_t launch_quad_points(int dim, int q, const int *n, int mq, const doubl
 cudaError_t launch_load_vector(int dim, int q, int mq, int64_t ncell, const double *V,
                                const double *wq, const double *fq, double *b, cudaStream_t s);
 
+// Residual + p-restriction with caller-chosen corner scratch (ctx.cu).
+int64_t corner_scratch_count(const dgmg_ctx *C);
+int residual_restrict_with_scratch(dgmg_ctx *C, const double *u, const double *b, const double *traces,
+                                   double *r, double *rc, double *corner_scratch, cudaStream_t s);
+
 constexpr int DOT_BLOCKS = 304;     // 2 x 152 SMs
 constexpr int DOT_THREADS = 256;
 

@@ -77,6 +77,7 @@ _SIGS = {
     "dgmg_load_vector": (_I, [_P, _P, _P, _P]),
     "dgmg_project": (_I, [_P, _P, _P, _P, _P]),
     "dgmg_residual_restrict": (_I, [_P, _P, _P, _P, _P, _P, _P]),
+    "dgmg_residual_restrict_noalloc": (_I, [_P, _P, _P, _P, _P, _P, _P]),
     "dgmg_cg_smooth": (_I, [_P, _I, _P, _P, _I, _P]),
     "dgmg_cg_residual": (_I, [_P, _I, _P, _P, _P, _P]),
     "dgmg_h_restrict": (_I, [_P, _I, _P, _P, _P]),
@@ -242,6 +243,12 @@ class Context:
     def residual_restrict(self, u, b, traces, r, rc, stream=None):
         _check(self.lib.dgmg_residual_restrict(self.h, _ptr(u), _ptr(b), _ptr(traces), _ptr(r), _ptr(rc),
                                                _stream(stream)))
+
+    def residual_restrict_noalloc(self, u, b, traces, r, rc, stream=None):
+        """As residual_restrict, with the scratch in the library's fixed device
+        array instead of the context's (allocates nothing; see dgmg.h)."""
+        _check(self.lib.dgmg_residual_restrict_noalloc(self.h, _ptr(u), _ptr(b), _ptr(traces), _ptr(r), _ptr(rc),
+                                                       _stream(stream)))
 
     def cg_smooth(self, level, u, b, nsteps, stream=None):
         _check(self.lib.dgmg_cg_smooth(self.h, int(level), _ptr(u), _ptr(b), int(nsteps), _stream(stream)))
