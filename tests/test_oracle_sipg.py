@@ -142,3 +142,12 @@ def test_load_vector_and_l2_error_closed_forms():
         u = f(*[X[:, a] for a in range(d)])
         assert sipg.l2_error(mesh, u, f) < 1e-13
         assert abs(sipg.l2_error(mesh, np.zeros(mesh.ndof), one) - 1.0) < 1e-13
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_harmonic_kappa_reading_stays_definite_at_high_contrast(p):
+    """The kappa extension (every interior facet term scaled by the harmonic mean)
+    keeps the operator positive definite at neighbour contrast 1000."""
+    mesh = sipg.Mesh((4, 4), p)
+    kap = np.array([1000.0 if (i + j) % 2 else 1.0 for j in range(4) for i in range(4)])
+    assert np.linalg.eigvalsh(sipg.assemble(mesh, kap).toarray())[0] > 0.0
