@@ -54,6 +54,16 @@ extern "C" {
 #define DGMG_MIXED_FP32 1         /* V-cycle in FP32 inside FP64 CG (Sec. 5 cycle,     */
                                   /* outer residual/update/coarsest solve in FP64)     */
 
+/* outer iteration of dgmg_solve */
+#define DGMG_OUTER_AUTO 0         /* RELIABLE with DGMG_MIXED_FP32, PCG with DGMG_FP64  */
+#define DGMG_OUTER_PCG 1          /* FP64 CG: one FP64 apply per iteration (flexible   */
+                                  /* Polak-Ribiere form with the FP32 V-cycle)         */
+#define DGMG_OUTER_RELIABLE 2     /* DGMG_MIXED_FP32 only: CG in FP32 (FP32 apply and  */
+                                  /* V-cycle, FP64-accumulated dot products), solution */
+                                  /* accumulated in FP64, true residual recomputed in  */
+                                  /* FP64 whenever the FP32 residual fell by `delta`   */
+                                  /* (reliable updates) and for the stopping test      */
+
 /* block inverse used by the block-Jacobi smoother (Eq. block-Jacobi-IP) */
 #define DGMG_BLOCK_EXACT 0        /* exact diagonal block A_KK of every cell           */
 #define DGMG_BLOCK_INTERIOR_ONLY 1/* Technique 4: the block of an interior cell, with  */
@@ -74,6 +84,8 @@ typedef struct {
     double rtol;                  /* dgmg_solve: stop at ||b-Ax||_2 <= rtol ||b||_2    */
                                   /* (default 1e-10)                                   */
     int maxit;                    /* dgmg_solve iteration cap (default 200)            */
+    int outer;                    /* DGMG_OUTER_* (default AUTO)                       */
+    double delta;                 /* reliable-update factor, 0 < delta < 1 (0.1)       */
 } dgmg_opts;
 
 typedef struct {
@@ -86,6 +98,7 @@ typedef struct {
     double omega_dg, omega_cg;    /* damping actually used                             */
     int nu_pre, nu_post, precision, block_inverse, coarsening;
     size_t device_bytes;          /* device memory held by the ctx                     */
+    int outer;                    /* DGMG_OUTER_PCG or DGMG_OUTER_RELIABLE in use      */
 } dgmg_info_t;
 
 typedef struct {
@@ -95,6 +108,8 @@ typedef struct {
     double prec_residual;         /* ||z||_2 / ||z_0||_2 of the last preconditioned    */
                                   /* residual z = V(r) (Eq. preconditioned_residual)   */
     double seconds;               /* wall time of the call                             */
+    int fp64_applies;             /* FP64 applications of A (residuals b - A x and, in */
+                                  /* DGMG_OUTER_PCG, the products A p)                 */
 } dgmg_stats;
 
 typedef struct dgmg_ctx dgmg_ctx;
@@ -160,13 +175,18 @@ int dgmg_smooth(dgmg_ctx *ctx, double *u, const double *b, int nsteps, void *str
 int dgmg_vcycle(dgmg_ctx *ctx, const double *r, double *e, void *stream);
 
 /*
- * Solve A x = b with conjugate gradients preconditioned by dgmg_vcycle (flexible
- * Polak-Ribiere form in mixed precision), FP64 outer residual, update and dot
- * products, starting from the x passed in. Stops when the recursively updated
- * residual satisfies ||r||_2 <= rtol ||b||_2, then recomputes b - A x and
- * reports it in stats (HOST struct, may be NULL). Blocks until done (it reads
- * one scalar per iteration). Returns DGMG_ENOTCONVERGED after maxit
- * iterations, DGMG_ENONFINITE if a residual norm is not finite.
+ * Solve A x = b with conjugate gradients preconditioned by dgmg_vcycle,
+ * starting from the x passed in. DGMG_OUTER_PCG: FP64 residual, update and dot
+ * products every iteration (flexible Polak-Ribiere form with the FP32 V-cycle).
+ * DGMG_OUTER_RELIABLE (mixed precision): the CG recurrences run in FP32 with
+ * FP64-accumulated dot products; the solution is accumulated in FP64 and the
+ * true residual b - A x is recomputed in FP64 whenever the FP32 residual has
+ * dropped by `delta` and before stopping (outer residual, solution update and
+ * coarsest solve stay FP64). Stops when ||b - A x||_2 <= rtol ||b||_2 (PCG: on
+ * the recursive residual, then verified), reports the recomputed residual in
+ * stats (HOST struct, may be NULL). Blocks until done (it reads one scalar per
+ * iteration). Returns DGMG_ENOTCONVERGED after maxit iterations,
+ * DGMG_ENONFINITE if a residual norm is not finite.
  */
 int dgmg_solve(dgmg_ctx *ctx, const double *b, double *x, dgmg_stats *stats, void *stream);
 

@@ -91,6 +91,64 @@ __global__ void k_f2d(int64_t n, const float *__restrict__ x, double *__restrict
 
 __global__ void k_copy_scalar(const double *src, double *dst) { *dst = *src; }
 
+// FP32 vectors with FP64 accumulation (the inner loop of the mixed solver)
+__global__ void k_dotf_partial(int64_t n, const float *__restrict__ x, const float *__restrict__ y,
+                               double *__restrict__ partials) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s += (double)x[i] * (double)y[i];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void k_dot2f_partial(int64_t n, const float *__restrict__ x, const float *__restrict__ y,
+                                const float *__restrict__ z, double *__restrict__ partials) {
+    __shared__ double sh[32];
+    double s = 0.0, t = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double yi = y[i];
+        s += (double)x[i] * yi;
+        t += (double)z[i] * yi;
+    }
+    s = block_sum(s, sh);
+    __syncthreads();
+    t = block_sum(t, sh);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = s;
+        partials[gridDim.x + blockIdx.x] = t;
+    }
+}
+
+// xs += alpha p, r -= alpha q, rold = old r (when given), alpha = scal[0] / scal[1]
+__global__ void k_update_xr_f(int64_t n, float *__restrict__ xs, float *__restrict__ r, float *__restrict__ rold,
+                              const float *__restrict__ p, const float *__restrict__ q,
+                              const double *__restrict__ scal) {
+    const float alpha = (float)(scal[0] / scal[1]);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float ri = r[i];
+        if (rold) rold[i] = ri;
+        xs[i] += alpha * p[i];
+        r[i] = ri - alpha * q[i];
+    }
+}
+
+__global__ void k_update_p_f(int64_t n, float *__restrict__ p, const float *__restrict__ z,
+                             const double *__restrict__ scal) {
+    const float beta = (float)scal[2];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = z[i] + beta * p[i];
+}
+
+// x += xs (FP64 accumulation of the FP32 correction), xs = 0
+__global__ void k_accumulate_f2d(int64_t n, double *__restrict__ x, float *__restrict__ xs) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        x[i] += (double)xs[i];
+        xs[i] = 0.0f;
+    }
+}
+
+
 // physical coordinates of the mq^d Gauss points of every cell
 __global__ void k_quad_points(int dim, int n0, int n1, int n2, int mq, const double *__restrict__ xq1,
                               double *__restrict__ xq, int64_t ncell) {
@@ -206,6 +264,41 @@ cudaError_t launch_load_vector(int dim, int q, int mq, int64_t ncell, const doub
     if (tot == 0) return cudaSuccess;
     count_launches(1);
     k_load_vector<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(dim, q, mq, ncell, V, wq, fq, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dotf(int64_t n, const float *x, const float *y, double *partials, double *out, cudaStream_t s) {
+    count_launches(2);
+    k_dotf_partial<<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(n, x, y, partials);
+    k_reduce<<<1, 512, 0, s>>>(DOT_BLOCKS, partials, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dot2f(int64_t n, const float *x, const float *y, const float *z, double *partials,
+                         double *out_xy, double *out_zy, cudaStream_t s) {
+    count_launches(3);
+    k_dot2f_partial<<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(n, x, y, z, partials);
+    k_reduce<<<1, 512, 0, s>>>(DOT_BLOCKS, partials, out_xy);
+    k_reduce<<<1, 512, 0, s>>>(DOT_BLOCKS, partials + DOT_BLOCKS, out_zy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_xr_f(int64_t n, float *xs, float *r, float *rold, const float *p, const float *q,
+                               const double *scal, cudaStream_t s) {
+    count_launches(1);
+    k_update_xr_f<<<grid_for(n), 256, 0, s>>>(n, xs, r, rold, p, q, scal);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_p_f(int64_t n, float *p, const float *z, const double *scal, cudaStream_t s) {
+    count_launches(1);
+    k_update_p_f<<<grid_for(n), 256, 0, s>>>(n, p, z, scal);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_accumulate_f2d(int64_t n, double *x, float *xs, cudaStream_t s) {
+    count_launches(1);
+    k_accumulate_f2d<<<grid_for(n), 256, 0, s>>>(n, x, xs);
     return cudaGetLastError();
 }
 

@@ -273,6 +273,7 @@ template <typename T>
 struct DGDev {
     DGConst<T> c;
     T *kappa = nullptr, *fd = nullptr, *tr[2] = {nullptr, nullptr}, *corners = nullptr;
+    T *linv = nullptr;   // per-node 1 / (sum of the cell's eigenvalues); FP64 only
 };
 
 template <typename T>
@@ -352,7 +353,7 @@ struct dgmg_ctx {
     std::vector<CGDev<double>> cg64;
     std::vector<CGDev<float>> cg32;
     // work vectors
-    float *r32 = nullptr, *z32 = nullptr;
+    float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *xs32 = nullptr, *rold32 = nullptr;
     double *w_r = nullptr, *w_z = nullptr, *w_p = nullptr, *w_q = nullptr, *w_rold = nullptr;
     double *w_b = nullptr, *w_x = nullptr;        // dgmg_solve_host staging
     double *scal = nullptr, *partials = nullptr;  // device scalars
@@ -533,11 +534,35 @@ std::vector<T> convert(const std::vector<double> &v) {
     return std::vector<T>(v.begin(), v.end());
 }
 
+// 1 / (lambda_x[i] + lambda_y[j] (+ lambda_z[k])) for every node of every cell,
+// from the fast-diagonalisation factors (the FP64 smoother multiplies by it
+// instead of dividing: FP64 division is a multi-instruction sequence on the
+// FP64 pipe, which bounds that kernel; the table costs one extra read per DoF).
+static void inverse_eigen_sums(const dgmg_ctx &C, const std::vector<double> &fd, std::vector<double> &linv) {
+    const int q = C.q, dim = C.dim, fds = q * q + q;
+    linv.assign((size_t)C.ndof, 0.0);
+    parallel_for(C.ncell, [&](int64_t cell) {
+        const double *lam0 = &fd[((size_t)cell * dim + 0) * fds + q * q];
+        const double *lam1 = &fd[((size_t)cell * dim + 1) * fds + q * q];
+        const double *lam2 = dim == 3 ? &fd[((size_t)cell * dim + 2) * fds + q * q] : nullptr;
+        double *out = &linv[(size_t)cell * C.nloc];
+        for (int64_t node = 0; node < C.nloc; ++node) {
+            const int i = (int)(node % q), j = (int)((node / q) % q), k = (int)(node / (q * q));
+            out[node] = 1.0 / (lam0[i] + lam1[j] + (lam2 ? lam2[k] : 0.0));
+        }
+    });
+}
+
 template <typename T>
 int setup_dg(dgmg_ctx &C, DGDev<T> &D, const std::vector<double> &kappa, const std::vector<double> &fd) {
     fill_const(C, D.c);
     RC(C.upload(&D.kappa, convert<T>(kappa)));
     RC(C.upload(&D.fd, convert<T>(fd)));
+    if (sizeof(T) == sizeof(double)) {
+        std::vector<double> linv;
+        inverse_eigen_sums(C, fd, linv);
+        RC(C.upload(&D.linv, convert<T>(linv)));
+    }
     const int64_t tr = C.ncell * 2 * C.dim * 2 * (C.nloc / C.q);
     RC(C.alloc(&D.tr[0], tr));
     RC(C.alloc(&D.tr[1], tr));
@@ -714,7 +739,8 @@ int dg_vcycle(dgmg_ctx &C, const T *r, T *z, cudaStream_t s) {
     int cur = 0;
     for (int k = 0; k < C.opts.nu_pre; ++k) {
         C.prof.begin(ST_SMOOTH, s);
-        LC(launch_smooth<T>(C.dim, C.q, D.c, C.cpb, exact_block(C), z, r, D.kappa, D.fd, D.tr[cur], D.tr[cur ^ 1], s));
+        LC(launch_smooth<T>(C.dim, C.q, D.c, C.cpb, exact_block(C), z, r, D.kappa, D.fd, D.linv, D.tr[cur],
+                            D.tr[cur ^ 1], s));
         C.prof.end(s);
         cur ^= 1;
     }
@@ -734,7 +760,8 @@ int dg_vcycle(dgmg_ctx &C, const T *r, T *z, cudaStream_t s) {
     cur = 0;
     for (int k = 0; k < C.opts.nu_post; ++k) {
         C.prof.begin(ST_SMOOTH, s);
-        LC(launch_smooth<T>(C.dim, C.q, D.c, C.cpb, exact_block(C), z, r, D.kappa, D.fd, D.tr[cur], D.tr[cur ^ 1], s));
+        LC(launch_smooth<T>(C.dim, C.q, D.c, C.cpb, exact_block(C), z, r, D.kappa, D.fd, D.linv, D.tr[cur],
+                            D.tr[cur ^ 1], s));
         C.prof.end(s);
         cur ^= 1;
     }
@@ -801,6 +828,8 @@ void dgmg_default_opts(dgmg_opts *o) {
     o->coarsening = 2;
     o->rtol = 1e-10;
     o->maxit = 200;
+    o->outer = DGMG_OUTER_AUTO;
+    o->delta = 0.1;
 }
 
 int dgmg_create(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_opts *opts, dgmg_ctx **out) {
@@ -825,6 +854,12 @@ int dgmg_create(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_op
     if (o.coarsening != 2 && o.coarsening != 3) return fail(DGMG_EINVAL, "coarsening must be 2 or 3");
     if (!(o.rtol > 0 && o.rtol < 1)) return fail(DGMG_EINVAL, "rtol must be in (0, 1)");
     if (o.maxit < 1) return fail(DGMG_EINVAL, "maxit must be >= 1");
+    if (o.outer != DGMG_OUTER_AUTO && o.outer != DGMG_OUTER_PCG && o.outer != DGMG_OUTER_RELIABLE)
+        return fail(DGMG_EINVAL, "unknown outer iteration");
+    if (o.outer == DGMG_OUTER_RELIABLE && o.precision != DGMG_MIXED_FP32)
+        return fail(DGMG_EINVAL, "DGMG_OUTER_RELIABLE needs DGMG_MIXED_FP32");
+    if (!(o.delta > 0 && o.delta < 1)) return fail(DGMG_EINVAL, "delta must be in (0, 1)");
+    if (o.outer == DGMG_OUTER_AUTO) o.outer = o.precision == DGMG_MIXED_FP32 ? DGMG_OUTER_RELIABLE : DGMG_OUTER_PCG;
 
     std::unique_ptr<dgmg_ctx> C(new dgmg_ctx());
     C->dim = mesh->dim;
@@ -878,6 +913,12 @@ int dgmg_create(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_op
         RC(setup_cg<float>(*C, C->cg32));
         RC(C->alloc(&C->r32, C->ndof));
         RC(C->alloc(&C->z32, C->ndof));
+        if (o.outer == DGMG_OUTER_RELIABLE) {
+            RC(C->alloc(&C->p32, C->ndof));
+            RC(C->alloc(&C->q32, C->ndof));
+            RC(C->alloc(&C->xs32, C->ndof));
+            RC(C->alloc(&C->rold32, C->ndof));
+        }
     }
     RC(C->alloc(&C->w_r, C->ndof));
     RC(C->alloc(&C->w_z, C->ndof));
@@ -940,6 +981,7 @@ int dgmg_info(const dgmg_ctx *C, dgmg_info_t *info) {
     info->block_inverse = C->opts.block_inverse;
     info->coarsening = C->opts.coarsening;
     info->device_bytes = C->bytes;
+    info->outer = C->opts.outer;
     return DGMG_OK;
 }
 
@@ -988,8 +1030,8 @@ int dgmg_smooth(dgmg_ctx *C, double *u, const double *b, int nsteps, void *strea
     int cur = 0;
     for (int k = 0; k < nsteps; ++k) {
         C->prof.begin(ST_SMOOTH, s);
-        LC(launch_smooth<double>(C->dim, C->q, D.c, C->cpb, exact_block(*C), u, b, D.kappa, D.fd, D.tr[cur],
-                                 D.tr[cur ^ 1], s));
+        LC(launch_smooth<double>(C->dim, C->q, D.c, C->cpb, exact_block(*C), u, b, D.kappa, D.fd, D.linv,
+                                 D.tr[cur], D.tr[cur ^ 1], s));
         C->prof.end(s);
         cur ^= 1;
     }
@@ -1104,6 +1146,122 @@ static int read_scalar(dgmg_ctx *C, int slot, double *v, cudaStream_t s) {
     return DGMG_OK;
 }
 
+// y = A u in FP32 (warm-up projection + cell equation on the FP32 hierarchy)
+static int apply32(dgmg_ctx *C, const float *u, float *y, cudaStream_t s) {
+    DGDev<float> &D = C->d32;
+    C->prof.begin(ST_PROJECT, s);
+    LC(launch_project<float>(C->dim, C->q, D.c, C->cpb, const_cast<float *>(u), nullptr, D.tr[0], s));
+    C->prof.end(s);
+    C->prof.begin(ST_RESIDUAL, s);
+    LC(launch_residual<float>(C->dim, C->q, D.c, C->cpb, RES_WRITE_R | RES_NEGATE, u, nullptr, D.kappa, D.tr[0], y,
+                              nullptr, s));
+    C->prof.end(s);
+    return DGMG_OK;
+}
+
+// Mixed-precision CG with reliable updates: FP32 recurrences (apply, V-cycle,
+// vector updates; dot products accumulated in FP64), FP64 solution and FP64
+// true residual whenever the FP32 residual fell below delta times its value at
+// the last FP64 evaluation, and for the stopping test.
+static int solve_reliable(dgmg_ctx *C, const double *b, double *x, dgmg_stats *stats, cudaStream_t s,
+                          std::chrono::steady_clock::time_point t0) {
+    const int64_t n = C->ndof;
+    double *r64 = C->w_r;
+    float *r = C->r32, *z = C->z32, *p = C->p32, *q = C->q32, *xs = C->xs32, *rold = C->rold32;
+    double bb = 0.0, rr = 0.0, zz0 = 0.0, zz = 0.0;
+    int nres = 0;
+    LC(launch_dot(n, b, b, C->partials, C->scal + S_BB, s));
+    RC(read_scalar(C, S_BB, &bb, s));
+    if (!std::isfinite(bb)) return fail(DGMG_ENONFINITE, "||b|| is not finite");
+    const double bn = std::sqrt(bb) > 0 ? std::sqrt(bb) : 1.0;
+    const double rtol = C->opts.rtol;
+    auto true_residual = [&](double *out_rr) -> int {
+        RC(apply64(*C, x, b, r64, s));
+        C->prof.begin(ST_VECTOR, s);
+        LC(launch_dot(n, r64, r64, C->partials, C->scal + S_RR, s));
+        LC(launch_cast_d2f(n, r64, r, s));
+        C->prof.end(s);
+        ++nres;
+        return read_scalar(C, S_RR, out_rr, s);
+    };
+    RC(true_residual(&rr));
+    if (!std::isfinite(rr)) return fail(DGMG_ENONFINITE, "initial residual is not finite");
+    double rel_true = std::sqrt(rr) / bn, relrec = rel_true;
+    double rnorm_at_update = std::sqrt(rr);
+    int it = 0, status = DGMG_OK;
+    if (rel_true > rtol) {
+        LC(cudaMemsetAsync(xs, 0, sizeof(float) * n, s));
+        RC(dg_vcycle<float>(*C, r, z, s));
+        C->prof.begin(ST_VECTOR, s);
+        LC(launch_dotf(n, r, z, C->partials, C->scal + S_RZ, s));
+        LC(launch_dotf(n, z, z, C->partials, C->scal + S_ZZ, s));
+        LC(cudaMemcpyAsync(p, z, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+        C->prof.end(s);
+        RC(read_scalar(C, S_ZZ, &zz0, s));
+        zz = zz0;
+        for (it = 1; it <= C->opts.maxit; ++it) {
+            RC(apply32(C, p, q, s));
+            C->prof.begin(ST_VECTOR, s);
+            LC(launch_dotf(n, p, q, C->partials, C->scal + S_PQ, s));
+            LC(launch_update_xr_f(n, xs, r, rold, p, q, C->scal, s));
+            LC(launch_dotf(n, r, r, C->partials, C->scal + S_RR, s));
+            C->prof.end(s);
+            double rr32 = 0.0;
+            RC(read_scalar(C, S_RR, &rr32, s));
+            if (!std::isfinite(rr32)) {
+                status = fail(DGMG_ENONFINITE, "residual norm is not finite");
+                break;
+            }
+            relrec = std::sqrt(rr32) / bn;
+            if (relrec <= rtol || std::sqrt(rr32) < C->opts.delta * rnorm_at_update) {
+                // reliable update: fold the FP32 correction into x, true FP64 residual
+                C->prof.begin(ST_VECTOR, s);
+                LC(launch_accumulate_f2d(n, x, xs, s));
+                C->prof.end(s);
+                RC(true_residual(&rr));
+                if (!std::isfinite(rr)) {
+                    status = fail(DGMG_ENONFINITE, "residual norm is not finite");
+                    break;
+                }
+                rel_true = std::sqrt(rr) / bn;
+                rnorm_at_update = std::sqrt(rr);
+                if (rel_true <= rtol) break;
+            }
+            if (it == C->opts.maxit) {
+                status = fail(DGMG_ENOTCONVERGED, "maxit reached");
+                break;
+            }
+            RC(dg_vcycle<float>(*C, r, z, s));
+            C->prof.begin(ST_VECTOR, s);
+            LC(launch_dot2f(n, r, z, rold, C->partials, C->scal + S_RZN, C->scal + S_RZO, s));
+            count_launches(1);
+            k_scalar_beta<<<1, 1, 0, s>>>(C->scal, 1);
+            LC(cudaGetLastError());
+            LC(launch_update_p_f(n, p, z, C->scal, s));
+            C->prof.end(s);
+        }
+        if (it > C->opts.maxit) it = C->opts.maxit;
+        if (status != DGMG_OK) {
+            C->prof.begin(ST_VECTOR, s);
+            LC(launch_accumulate_f2d(n, x, xs, s));
+            C->prof.end(s);
+            RC(true_residual(&rr));
+            rel_true = std::sqrt(rr) / bn;
+        }
+        LC(launch_dotf(n, z, z, C->partials, C->scal + S_ZZ, s));
+        RC(read_scalar(C, S_ZZ, &zz, s));
+    }
+    if (stats) {
+        stats->iterations = it;
+        stats->rel_residual = rel_true;
+        stats->rel_residual_recursive = relrec;
+        stats->prec_residual = zz0 > 0 ? std::sqrt(zz / zz0) : 0.0;
+        stats->fp64_applies = nres;
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return status;
+}
+
 int dgmg_solve(dgmg_ctx *C, const double *b, double *x, dgmg_stats *stats, void *stream) {
     RC(check_ctx(C));
     NEED(b);
@@ -1111,11 +1269,14 @@ int dgmg_solve(dgmg_ctx *C, const double *b, double *x, dgmg_stats *stats, void 
     if (b == x) return fail(DGMG_EINVAL, "b and x must not overlap");
     const auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = (cudaStream_t)stream;
+    if (C->opts.outer == DGMG_OUTER_RELIABLE) return solve_reliable(C, b, x, stats, s, t0);
     const int64_t n = C->ndof;
     const bool flexible = C->opts.precision == DGMG_MIXED_FP32;
+    int nres = 0;
     double *r = C->w_r, *z = C->w_z, *p = C->w_p, *q = C->w_q, *rold = C->w_rold;
     double bb = 0.0, rr = 0.0, zz0 = 0.0, zz = 0.0;
     RC(apply64(*C, x, b, r, s));                                 // r = b - A x
+    ++nres;
     LC(launch_dot(n, b, b, C->partials, C->scal + S_BB, s));
     RC(read_scalar(C, S_BB, &bb, s));
     if (!std::isfinite(bb)) return fail(DGMG_ENONFINITE, "||b|| is not finite");
@@ -1171,6 +1332,7 @@ int dgmg_solve(dgmg_ctx *C, const double *b, double *x, dgmg_stats *stats, void 
     }
     // true residual of the returned x
     RC(apply64(*C, x, b, r, s));
+    ++nres;
     LC(launch_dot(n, r, r, C->partials, C->scal + S_RR, s));
     double rtrue = 0.0;
     RC(read_scalar(C, S_RR, &rtrue, s));
@@ -1179,6 +1341,7 @@ int dgmg_solve(dgmg_ctx *C, const double *b, double *x, dgmg_stats *stats, void 
         stats->rel_residual = std::sqrt(rtrue) / bn;
         stats->rel_residual_recursive = relrec;
         stats->prec_residual = zz0 > 0 ? std::sqrt(zz / zz0) : 0.0;
+        stats->fp64_applies = nres + it;
         stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
     return status;

@@ -12,9 +12,9 @@ cudaError_t launch_project<float>(int dim, int q, const DGConst<float> &c, int c
 template <>
 cudaError_t launch_smooth<float>(int dim, int q, const DGConst<float> &c, int cpb, int exact, float *u,
                                 const float *b,
-                                const float *kappa, const float *fd, const float *tr_in, float *tr_out,
+                                const float *kappa, const float *fd, const float *linv, const float *tr_in, float *tr_out,
                                 cudaStream_t s) {
-    return launch_smooth_impl<float>(dim, q, c, cpb, exact, u, b, kappa, fd, tr_in, tr_out, s);
+    return launch_smooth_impl<float>(dim, q, c, cpb, exact, u, b, kappa, fd, linv, tr_in, tr_out, s);
 }
 
 template <>

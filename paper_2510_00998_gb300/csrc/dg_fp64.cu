@@ -12,9 +12,9 @@ cudaError_t launch_project<double>(int dim, int q, const DGConst<double> &c, int
 template <>
 cudaError_t launch_smooth<double>(int dim, int q, const DGConst<double> &c, int cpb, int exact, double *u,
                                 const double *b,
-                                const double *kappa, const double *fd, const double *tr_in, double *tr_out,
+                                const double *kappa, const double *fd, const double *linv, const double *tr_in, double *tr_out,
                                 cudaStream_t s) {
-    return launch_smooth_impl<double>(dim, q, c, cpb, exact, u, b, kappa, fd, tr_in, tr_out, s);
+    return launch_smooth_impl<double>(dim, q, c, cpb, exact, u, b, kappa, fd, linv, tr_in, tr_out, s);
 }
 
 template <>

@@ -60,6 +60,35 @@ __device__ __forceinline__ void block_copy(T *__restrict__ dst, const T *__restr
     for (int64_t i = threadIdx.x; i < count; i += blockDim.x) dst[i] = src[i];
 }
 
+// Copy the 1D mass matrices of all axes into shared memory (all threads).
+template <int DIM, int Q, typename T>
+__device__ __forceinline__ void stage_masses(const DGConst<T> &c, T *sM) {
+    for (int e = threadIdx.x; e < DIM * Q * Q; e += blockDim.x) sM[e] = c.M[e / (Q * Q)][e % (Q * Q)];
+}
+
+// 1D tables read with thread-dependent indices by build_block_1d, staged in
+// shared memory: K [axis][q*q], then d0 [axis][q], then dp [axis][q].
+template <int DIM, int Q, typename T>
+__device__ __forceinline__ void stage_block_tables(const DGConst<T> &c, T *sT) {
+    for (int e = threadIdx.x; e < DIM * Q * Q; e += blockDim.x) sT[e] = c.K[e / (Q * Q)][e % (Q * Q)];
+    for (int e = threadIdx.x; e < DIM * Q; e += blockDim.x) {
+        sT[DIM * Q * Q + e] = c.d0[e / Q][e % Q];
+        sT[DIM * Q * Q + DIM * Q + e] = c.dp[e / Q][e % Q];
+    }
+}
+
+// Bit f set when face f (= 2*axis + side) of the cell has a neighbour.
+template <int DIM>
+__device__ __forceinline__ int interior_mask(const int *ci, const int *n) {
+    int m = 0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        if (ci[a] > 0) m |= 1 << (2 * a);
+        if (ci[a] < n[a] - 1) m |= 1 << (2 * a + 1);
+    }
+    return m;
+}
+
 // Load the neighbours' traces of the faces of one cell into sF[face][comp][t]
 // and the facet coefficient kF[face] (harmonic mean of kappa; 0 on the boundary,
 // where the facet has no neighbour contribution).
@@ -96,8 +125,10 @@ __device__ __forceinline__ void load_neighbour_traces(const DGConst<T> &c, int64
 // Apply the facet mass matrix (tensor product of the tangential 1D masses) to
 // both components of every interior face of the cell, in place. Needs all
 // threads of the CTA (contains barriers); `active` threads do the arithmetic.
+// sM: shared-memory copy of the 1D masses, [axis][q*q] (the row read depends
+// on the thread, which would serialise reads from kernel-parameter space).
 template <int DIM, int Q, typename T>
-__device__ __forceinline__ void facet_mass(const DGConst<T> &c, bool active, int t, T *sF, const T *sKF) {
+__device__ __forceinline__ void facet_mass(const T *sM, bool active, int t, T *sF, int mask) {
     using G = Geo<DIM, Q>;
     constexpr int NPASS = DIM - 1;
 #pragma unroll
@@ -115,16 +146,16 @@ __device__ __forceinline__ void facet_mass(const DGConst<T> &c, bool active, int
                 for (int comp = 0; comp < 2; ++comp) {
                     const T *fld = sF + (f * 2 + comp) * G::NF;
                     T s = T(0);
-                    if (sKF[f] != T(0)) {
+                    if (mask & (1 << f)) {
                         if (DIM == 2) {
 #pragma unroll
-                            for (int m = 0; m < Q; ++m) s += c.M[ta][t * Q + m] * fld[m];
+                            for (int m = 0; m < Q; ++m) s += sM[ta * Q * Q + t * Q + m] * fld[m];
                         } else if (pass == 0) {
 #pragma unroll
-                            for (int m = 0; m < Q; ++m) s += c.M[ta][ia * Q + m] * fld[m + Q * ib];
+                            for (int m = 0; m < Q; ++m) s += sM[ta * Q * Q + ia * Q + m] * fld[m + Q * ib];
                         } else {
 #pragma unroll
-                            for (int m = 0; m < Q; ++m) s += c.M[tb][ib * Q + m] * fld[ia + Q * m];
+                            for (int m = 0; m < Q; ++m) s += sM[tb * Q * Q + ib * Q + m] * fld[ia + Q * m];
                         }
                     }
                     out[f][comp] = s;
@@ -151,7 +182,7 @@ __device__ __forceinline__ void facet_mass(const DGConst<T> &c, bool active, int
 //   N = kF [ e_p (x) (-H/2 - gamma G) + d_p (x) G/2 ].
 template <int DIM, int Q, typename T>
 __device__ __forceinline__ void lift_neighbours(const DGConst<T> &c, bool active, int t, T *sR, const T *sF,
-                                                const T *sKF) {
+                                                const T *sKF, int mask) {
     using G = Geo<DIM, Q>;
 #pragma unroll
     for (int dir = 0; dir < DIM; ++dir) {
@@ -161,7 +192,7 @@ __device__ __forceinline__ void lift_neighbours(const DGConst<T> &c, bool active
             for (int i = 0; i < Q; ++i) x[i] = sR[G::vidx(dir, t, i)];
             const T half = T(0.5);
             const T kL = sKF[2 * dir], kR = sKF[2 * dir + 1];
-            if (kL != T(0)) {
+            if (mask & (1 << (2 * dir))) {
                 const T Gv = sF[((2 * dir) * 2 + 0) * G::NF + t];
                 const T Hv = sF[((2 * dir) * 2 + 1) * G::NF + t];
                 x[0] -= kL * (half * Hv - c.gamma[dir] * Gv);
@@ -169,7 +200,7 @@ __device__ __forceinline__ void lift_neighbours(const DGConst<T> &c, bool active
 #pragma unroll
                 for (int i = 0; i < Q; ++i) x[i] += a * c.d0[dir][i];
             }
-            if (kR != T(0)) {
+            if (mask & (1 << (2 * dir + 1))) {
                 const T Gv = sF[((2 * dir + 1) * 2 + 0) * G::NF + t];
                 const T Hv = sF[((2 * dir + 1) * 2 + 1) * G::NF + t];
                 x[Q - 1] -= kR * (-half * Hv - c.gamma[dir] * Gv);
@@ -189,20 +220,33 @@ __device__ __forceinline__ void lift_neighbours(const DGConst<T> &c, bool active
 // high face kF_R (-w_R (ep dp^T + dp ep^T) + gamma ep ep^T ),
 // kF = harmonic mean and w = 1/2 inside, kF = kappa_K and w = 1 on the boundary.
 template <int DIM, int Q, typename T>
-__device__ __forceinline__ void build_block_1d(const DGConst<T> &c, bool active, int t, const T *myK, T *myKT) {
+__device__ __forceinline__ void build_block_1d(const DGConst<T> &c, const T *sT, bool active, int t, const T *myK,
+                                               int mask, T *myKT) {
     using G = Geo<DIM, Q>;
     if (!active) return;
+    const T *K = sT, *d0 = sT + DIM * Q * Q, *dp = d0 + DIM * Q;
     const T kK = myK[G::NFACE];
     for (int e = t; e < DIM * Q * Q; e += G::NF) {
         const int a = e / (Q * Q), i = (e / Q) % Q, j = e % Q;
-        const bool inL = myK[2 * a] != T(0), inR = myK[2 * a + 1] != T(0);
-        const T kL = inL ? myK[2 * a] : kK, wL = inL ? T(0.5) : T(1);
-        const T kR = inR ? myK[2 * a + 1] : kK, wR = inR ? T(0.5) : T(1);
-        T v = kK * c.K[a][i * Q + j];
-        const T e0i = i == 0 ? T(1) : T(0), e0j = j == 0 ? T(1) : T(0);
-        const T epi = i == Q - 1 ? T(1) : T(0), epj = j == Q - 1 ? T(1) : T(0);
-        v += kL * (wL * (e0i * c.d0[a][j] + c.d0[a][i] * e0j) + c.gamma[a] * e0i * e0j);
-        v += kR * (-wR * (epi * c.dp[a][j] + c.dp[a][i] * epj) + c.gamma[a] * epi * epj);
+        T v = kK * K[e];
+        if (i == 0 || j == 0) {               // low-face terms live in row / column 0
+            const bool in = mask & (1 << (2 * a));
+            const T kL = in ? myK[2 * a] : kK;
+            const T w = in ? T(0.5) : T(1);
+            if (i == 0 && j == 0)
+                v += kL * (T(2) * w * d0[a * Q] + c.gamma[a]);
+            else
+                v += kL * w * d0[a * Q + (i == 0 ? j : i)];
+        }
+        if (i == Q - 1 || j == Q - 1) {       // high-face terms live in row / column q-1
+            const bool in = mask & (1 << (2 * a + 1));
+            const T kR = in ? myK[2 * a + 1] : kK;
+            const T w = in ? T(0.5) : T(1);
+            if (i == Q - 1 && j == Q - 1)
+                v += kR * (c.gamma[a] - T(2) * w * dp[a * Q + Q - 1]);
+            else
+                v -= kR * w * dp[a * Q + (i == Q - 1 ? j : i)];
+        }
         myKT[e] = v;
     }
 }
@@ -388,8 +432,8 @@ __global__ void __launch_bounds__(256) k_project(DGConst<T> c, int cpb, T *__res
 template <int DIM, int Q, typename T>
 __global__ void __launch_bounds__(256) k_smooth(DGConst<T> c, int cpb, int exact, T *__restrict__ u,
                                                 const T *__restrict__ b, const T *__restrict__ kappa,
-                                                const T *__restrict__ fd, const T *__restrict__ tr_in,
-                                                T *__restrict__ tr_out) {
+                                                const T *__restrict__ fd, const T *__restrict__ linv,
+                                                const T *__restrict__ tr_in, T *__restrict__ tr_out) {
     using G = Geo<DIM, Q>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sU = reinterpret_cast<T *>(smem_raw);
@@ -406,6 +450,10 @@ __global__ void __launch_bounds__(256) k_smooth(DGConst<T> c, int cpb, int exact
     const bool active = lc < ncl;
     const int64_t cell = cell0 + lc;
     int ci[3] = {0, 0, 0};
+    __shared__ T sM[DIM * Q * Q];
+    __shared__ T sT[DIM * Q * Q + 2 * DIM * Q];
+    stage_masses<DIM, Q, T>(c, sM);
+    if (!exact) stage_block_tables<DIM, Q, T>(c, sT);
     block_copy(sU, u + cell0 * G::NL, (int64_t)ncl * G::NL);
     block_copy(sR, b + cell0 * G::NL, (int64_t)ncl * G::NL);
     block_copy(sFD, fd + cell0 * DIM * G::FDS, (int64_t)ncl * DIM * G::FDS);
@@ -418,9 +466,10 @@ __global__ void __launch_bounds__(256) k_smooth(DGConst<T> c, int cpb, int exact
     __syncthreads();
     T *myR = sR + lc * G::NL;
     T *myU = sU + lc * G::NL;
-    if (!exact) build_block_1d<DIM, Q, T>(c, active, t, myK, sKT + lc * DIM * Q * Q);
-    facet_mass<DIM, Q, T>(c, active, t, myF, myK);
-    lift_neighbours<DIM, Q, T>(c, active, t, myR, myF, myK);
+    const int mask = active ? interior_mask<DIM>(ci, c.n) : 0;
+    if (!exact) build_block_1d<DIM, Q, T>(c, sT, active, t, myK, mask, sKT + lc * DIM * Q * Q);
+    facet_mass<DIM, Q, T>(sM, active, t, myF, mask);
+    lift_neighbours<DIM, Q, T>(c, active, t, myR, myF, myK, mask);
     if (!exact)
         subtract_block_apply<DIM, Q, T>(c, active, t, myU, myR, sA + lc * G::NL, sB + lc * G::NL,
                                         sKT + lc * DIM * Q * Q);
@@ -460,12 +509,15 @@ __global__ void __launch_bounds__(256) k_smooth(DGConst<T> c, int cpb, int exact
             }
 #pragma unroll
             for (int i = 0; i < Q; ++i) x[i] = myR[G::vidx(D, t, i)];
+            // 1 / (lambda_x + lambda_y + lambda_z): from the per-node table when
+            // one is given (saves a division per node), else divided here
+            const T *li = linv ? linv + cell * G::NL : nullptr;
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 T s = T(0);
 #pragma unroll
                 for (int m = 0; m < Q; ++m) s += S[m * Q + i] * x[m];
-                y[i] = s / (lt + lam[i]);
+                y[i] = li ? s * li[G::vidx(D, t, i)] : s / (lt + lam[i]);
             }
 #pragma unroll
             for (int m = 0; m < Q; ++m) {
@@ -557,6 +609,10 @@ __global__ void __launch_bounds__(256) k_residual(DGConst<T> c, int cpb, int mod
     const bool active = lc < ncl;
     const int64_t cell = cell0 + lc;
     int ci[3] = {0, 0, 0};
+    __shared__ T sM[DIM * Q * Q];
+    __shared__ T sT[DIM * Q * Q + 2 * DIM * Q];
+    stage_masses<DIM, Q, T>(c, sM);
+    stage_block_tables<DIM, Q, T>(c, sT);
     block_copy(sU, u + cell0 * G::NL, (int64_t)ncl * G::NL);
     if (mode & RES_HAS_B) {
         block_copy(sR, b + cell0 * G::NL, (int64_t)ncl * G::NL);
@@ -571,11 +627,12 @@ __global__ void __launch_bounds__(256) k_residual(DGConst<T> c, int cpb, int mod
     }
     __syncthreads();
     T *myKT = sKT + lc * DIM * Q * Q;
-    build_block_1d<DIM, Q, T>(c, active, t, myK, myKT);
-    facet_mass<DIM, Q, T>(c, active, t, myF, myK);   // contains barriers
+    const int mask = active ? interior_mask<DIM>(ci, c.n) : 0;
+    build_block_1d<DIM, Q, T>(c, sT, active, t, myK, mask, myKT);
+    facet_mass<DIM, Q, T>(sM, active, t, myF, mask);   // contains barriers
     T *myR = sR + lc * G::NL;
     T *myU = sU + lc * G::NL;
-    lift_neighbours<DIM, Q, T>(c, active, t, myR, myF, myK);
+    lift_neighbours<DIM, Q, T>(c, active, t, myR, myF, myK, mask);
     subtract_block_apply<DIM, Q, T>(c, active, t, myU, myR, sA + lc * G::NL, sB + lc * G::NL, myKT);
     T rr[Q];
     if (active) {
@@ -659,7 +716,7 @@ struct DGLaunch {
         return cudaGetLastError();
     }
     static cudaError_t smooth(const DGConst<T> &c, int cpb, int exact, T *u, const T *b, const T *kappa,
-                              const T *fd, const T *tri, T *tro, cudaStream_t s) {
+                              const T *fd, const T *linv, const T *tri, T *tro, cudaStream_t s) {
         const size_t sm = smem_smooth<DIM, Q, T>(cpb, exact != 0);
         static bool attr = false;
         if (!attr) {
@@ -669,7 +726,7 @@ struct DGLaunch {
         const int64_t grid = (c.ncell + cpb - 1) / cpb;
         if (grid == 0) return cudaSuccess;
         count_launches(1);
-        k_smooth<DIM, Q, T><<<(unsigned)grid, cpb * G::NF, sm, s>>>(c, cpb, exact, u, b, kappa, fd, tri, tro);
+        k_smooth<DIM, Q, T><<<(unsigned)grid, cpb * G::NF, sm, s>>>(c, cpb, exact, u, b, kappa, fd, linv, tri, tro);
         return cudaGetLastError();
     }
     static cudaError_t residual(const DGConst<T> &c, int cpb, int mode, const T *u, const T *b, const T *kappa,
@@ -712,8 +769,8 @@ cudaError_t launch_project_impl(int dim, int q, const DGConst<T> &c, int cpb, T 
 }
 template <typename T>
 cudaError_t launch_smooth_impl(int dim, int q, const DGConst<T> &c, int cpb, int exact, T *u, const T *b,
-                               const T *kappa, const T *fd, const T *tri, T *tro, cudaStream_t s) {
-    DGMG_DISPATCH(dim, q, smooth(c, cpb, exact, u, b, kappa, fd, tri, tro, s))
+                               const T *kappa, const T *fd, const T *linv, const T *tri, T *tro, cudaStream_t s) {
+    DGMG_DISPATCH(dim, q, smooth(c, cpb, exact, u, b, kappa, fd, linv, tri, tro, s))
 }
 template <typename T>
 cudaError_t launch_residual_impl(int dim, int q, const DGConst<T> &c, int cpb, int mode, const T *u, const T *b,

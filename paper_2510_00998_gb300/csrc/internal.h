@@ -88,7 +88,7 @@ cudaError_t launch_project(int dim, int q, const DGConst<T> &c, int cpb, T *u, c
                            T *tr, cudaStream_t s);
 template <typename T>
 cudaError_t launch_smooth(int dim, int q, const DGConst<T> &c, int cpb, int exact, T *u, const T *b,
-                          const T *kappa, const T *fd, const T *tr_in, T *tr_out, cudaStream_t s);
+                          const T *kappa, const T *fd, const T *linv, const T *tr_in, T *tr_out, cudaStream_t s);
 // mode bits for launch_residual
 enum { RES_HAS_B = 1, RES_WRITE_R = 2, RES_CORNERS = 4, RES_NEGATE = 8 };
 template <typename T>
@@ -125,6 +125,14 @@ cudaError_t launch_pcg_update_p(int64_t n, double *p, const double *z, const dou
                                 cudaStream_t s);
 cudaError_t launch_sub(int64_t n, const double *a, const double *b, double *out, cudaStream_t s);
 cudaError_t launch_copy_scalar(const double *src, double *dst, cudaStream_t s);
+cudaError_t launch_dotf(int64_t n, const float *x, const float *y, double *partials, double *out,
+                        cudaStream_t s);
+cudaError_t launch_dot2f(int64_t n, const float *x, const float *y, const float *z, double *partials,
+                         double *out_xy, double *out_zy, cudaStream_t s);
+cudaError_t launch_update_xr_f(int64_t n, float *xs, float *r, float *rold, const float *p, const float *q,
+                               const double *scal, cudaStream_t s);
+cudaError_t launch_update_p_f(int64_t n, float *p, const float *z, const double *scal, cudaStream_t s);
+cudaError_t launch_accumulate_f2d(int64_t n, double *x, float *xs, cudaStream_t s);
 cudaError_t launch_quad_points(int dim, int q, const int *n, int mq, const double *xq1,
                                double *xq, int64_t ncell, cudaStream_t s);
 cudaError_t launch_load_vector(int dim, int q, int mq, int64_t ncell, const double *V,

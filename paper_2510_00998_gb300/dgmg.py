@@ -19,6 +19,9 @@ DGMG_ENONFINITE = -5
 DGMG_ECUDA = -6
 DGMG_FP64 = 0
 DGMG_MIXED_FP32 = 1
+DGMG_OUTER_AUTO = 0
+DGMG_OUTER_PCG = 1
+DGMG_OUTER_RELIABLE = 2
 DGMG_BLOCK_EXACT = 0
 DGMG_BLOCK_INTERIOR_ONLY = 1
 
@@ -37,7 +40,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("omega_dg", ctypes.c_double), ("omega_cg", ctypes.c_double),
                 ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int), ("precision", ctypes.c_int),
                 ("block_inverse", ctypes.c_int), ("coarsening", ctypes.c_int),
-                ("rtol", ctypes.c_double), ("maxit", ctypes.c_int)]
+                ("rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("outer", ctypes.c_int),
+                ("delta", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
@@ -47,13 +51,13 @@ class Info(ctypes.Structure):
                 ("omega_dg", ctypes.c_double), ("omega_cg", ctypes.c_double),
                 ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int), ("precision", ctypes.c_int),
                 ("block_inverse", ctypes.c_int), ("coarsening", ctypes.c_int),
-                ("device_bytes", ctypes.c_size_t)]
+                ("device_bytes", ctypes.c_size_t), ("outer", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("rel_residual", ctypes.c_double),
                 ("rel_residual_recursive", ctypes.c_double), ("prec_residual", ctypes.c_double),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("fp64_applies", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

@@ -207,13 +207,17 @@ def test_vcycle_mixed_fp32(dgmg, n, p):
     assert _rel(_np(e), hier.vcycle(r)) <= 2e-5
 
 
-@pytest.mark.parametrize("n,p,kind,prec", [((16, 16), 2, "one", 0), ((8, 8, 8), 2, "lognormal", 0),
-                                           ((6, 5, 4), 3, "lognormal", 0), ((8, 8, 8), 3, "lognormal", 1),
-                                           ((12, 10), 4, "lognormal", 1)])
-def test_solve_matches_oracle(dgmg, n, p, kind, prec):
+@pytest.mark.parametrize("n,p,kind,prec,outer", [((16, 16), 2, "one", 0, 0), ((8, 8, 8), 2, "lognormal", 0, 0),
+                                                 ((6, 5, 4), 3, "lognormal", 0, 0),
+                                                 ((8, 8, 8), 3, "lognormal", 1, 0), ((12, 10), 4, "lognormal", 1, 0),
+                                                 ((8, 8, 8), 3, "lognormal", 1, 1), ((12, 10), 4, "lognormal", 1, 1),
+                                                 ((10, 9, 8), 4, "lognormal", 1, 2)])
+def test_solve_matches_oracle(dgmg, n, p, kind, prec, outer):
+    """FP64 PCG, mixed precision with FP64 PCG around the FP32 V-cycle, and the
+    reliable-update FP32 CG (outer 0 = the precision's default)."""
     kap = _kappa(n, kind)
     mesh = sipg.Mesh(n, p)
-    ctx = dgmg.Context(n, p, kap, precision=prec)
+    ctx = dgmg.Context(n, p, kap, precision=prec, outer=outer)
     b = np.random.default_rng(12).normal(size=mesh.ndof)
     x = torch.zeros(mesh.ndof, dtype=torch.float64, device=DEV)
     st, _ = ctx.solve(_t(b), x)
