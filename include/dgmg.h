@@ -110,9 +110,26 @@ typedef struct {
     double seconds;               /* wall time of the call                             */
     int fp64_applies;             /* FP64 applications of A (residuals b - A x and, in */
                                   /* DGMG_OUTER_PCG, the products A p)                 */
+    double queue_seconds;         /* served requests: submit -> admission (else 0);   */
+                                  /* `seconds` is then submit -> completion            */
 } dgmg_stats;
 
 typedef struct dgmg_ctx dgmg_ctx;
+typedef struct dgmg_server dgmg_server;
+
+/* request states reported by dgmg_poll */
+#define DGMG_PENDING 0            /* queued, not yet admitted                          */
+#define DGMG_RUNNING 1            /* admitted, solve in progress on the GPU            */
+#define DGMG_DONE 2               /* converged; x holds the solution                   */
+#define DGMG_FAILED 3             /* see dgmg_poll's return code and dgmg_last_error   */
+
+typedef struct {
+    int pending, active;          /* queued / admitted requests                        */
+    long long done, failed, admitted;
+    int cache_entries;            /* resident hierarchies (busy or idle)               */
+    long long cache_hits, cache_misses, evictions;
+    size_t bytes_in_use, budget;  /* device bytes held by resident hierarchies         */
+} dgmg_server_info_t;
 
 /* Library version string. */
 const char *dgmg_version(void);
@@ -206,6 +223,49 @@ int dgmg_solve_host(dgmg_ctx *ctx, const double *b_host, double *x_host, dgmg_st
  */
 int dgmg_quad_points(dgmg_ctx *ctx, double *xq, void *stream);
 int dgmg_load_vector(dgmg_ctx *ctx, const double *fq, double *b, void *stream);
+
+/*
+ * Device bytes dgmg_create would hold for this problem (exact byte count of its
+ * allocations, before allocator rounding). HOST output.
+ */
+int dgmg_estimate_bytes(const dgmg_mesh *mesh, int p, const dgmg_opts *opts, size_t *bytes);
+
+/* ---- serving: continuous batching of independent solves ---- */
+
+/*
+ * Start a solve server on the current device: at most `max_active` solves run
+ * at once (each on its own stream, advanced one CG iteration at a time by a
+ * scheduler thread, so their kernels overlap), and the hierarchies it keeps
+ * resident (busy or idle, reused for repeated problems, least recently used
+ * idle ones evicted first) never exceed `hbm_budget_bytes`. opts (NULL =
+ * defaults) apply to every request.
+ */
+int dgmg_server_create(size_t hbm_budget_bytes, int max_active, const dgmg_opts *opts, dgmg_server **out);
+
+/*
+ * Queue a solve of A x = b for (mesh, p, kappa_host) and return at once with a
+ * ticket. kappa_host (HOST, ncell values, NULL = 1) is copied. b_dev, x_dev:
+ * caller-owned DEVICE vectors (x_dev holds the initial guess and receives the
+ * solution); they must be ready when dgmg_submit is called and stay alive
+ * until dgmg_poll reports DGMG_DONE or DGMG_FAILED. Requests that can never
+ * fit the budget fail with DGMG_EBUDGET. Thread-safe.
+ */
+int dgmg_submit(dgmg_server *server, const dgmg_mesh *mesh, int p, const double *kappa_host,
+                const double *b_dev, double *x_dev, uint64_t *ticket);
+
+/*
+ * State of a ticket (DGMG_PENDING / RUNNING / DONE / FAILED) and, once finished,
+ * its stats (HOST, may be NULL; `seconds` = submit to completion, `queue_seconds`
+ * = submit to admission). Returns the request's error code when it FAILED.
+ * Thread-safe.
+ */
+int dgmg_poll(dgmg_server *server, uint64_t ticket, int *status, dgmg_stats *stats);
+
+/* Counters of the server (HOST struct). */
+int dgmg_server_info(dgmg_server *server, dgmg_server_info_t *info);
+
+/* Fail the queued requests, finish the running ones, free everything. */
+int dgmg_server_destroy(dgmg_server *server);
 
 /* ---- stage entry points: the individual steps of the path, for testing ---- */
 

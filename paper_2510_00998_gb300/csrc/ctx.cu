@@ -10,7 +10,7 @@
 #include <thread>
 #include <vector>
 
-#include "internal.h"
+#include "ctx.h"
 
 namespace dgmg {
 
@@ -53,19 +53,6 @@ static void parallel_for(int64_t n, F f) {
 }
 
 // --------------------------------------------------------------- Q1 levels
-// One continuous Q1 level on the host: stencils (SoA [3^d][nv]) and the
-// per-axis transfer tables to the next coarser level.
-struct CGLevelHost {
-    int n[3] = {1, 1, 1};   // cells per axis
-    int m[3] = {1, 1, 1};   // interior vertices per axis
-    int64_t nv = 0;
-    std::vector<double> st;
-    // transfer to the next level (empty on the coarsest)
-    int mc[3] = {1, 1, 1};
-    std::vector<int> pl_lo[3], pl_hi[3], rs_start[3], rs_cnt[3];
-    std::vector<double> pl_wlo[3], pl_whi[3], rs_w[3];
-};
-
 static std::vector<int> coarse_positions(int n, int f) {
     std::vector<int> pos;
     for (int i = 0; i < n; i += f) pos.push_back(i);
@@ -266,146 +253,7 @@ static void build_coarse(int dim, CGLevelHost &F, CGLevelHost &C) {
 
 }  // namespace dgmg
 
-using namespace dgmg;
-
-// ---------------------------------------------------------------- context
-template <typename T>
-struct DGDev {
-    DGConst<T> c;
-    T *kappa = nullptr, *fd = nullptr, *tr[2] = {nullptr, nullptr}, *corners = nullptr;
-    T *linv = nullptr;   // per-node 1 / (sum of the cell's eigenvalues); FP64 only
-};
-
-template <typename T>
-struct CGDev {
-    CGLevelDev<T> L;
-    T *st = nullptr;
-    T *u[2] = {nullptr, nullptr}, *b = nullptr, *r = nullptr;
-    int *itab = nullptr;
-    T *wtab = nullptr;
-};
-
-// Per-stage device time, recorded with CUDA events on the launching stream
-// around every stage launch while profiling is on (dgmg_profile).
-enum { ST_PROJECT = 0, ST_SMOOTH = 1, ST_RESIDUAL = 2, ST_CG = 3, ST_VECTOR = 4, ST_N = 5 };
-struct StageProfiler {
-    bool on = false;
-    std::vector<cudaEvent_t> ev;        // pairs: 2k start, 2k+1 stop
-    std::vector<int> stage;
-    size_t used = 0;
-    double ms[ST_N] = {0};
-    long long cnt[ST_N] = {0};
-    int open_stage = -1;
-    void begin(int st, cudaStream_t s) {
-        if (!on) return;
-        if (2 * used + 2 > ev.size()) {
-            cudaEvent_t a, b;
-            cudaEventCreate(&a);
-            cudaEventCreate(&b);
-            ev.push_back(a);
-            ev.push_back(b);
-            stage.push_back(st);
-        }
-        stage[used] = st;
-        cudaEventRecord(ev[2 * used], s);
-        open_stage = st;
-    }
-    void end(cudaStream_t s) {
-        if (!on || open_stage < 0) return;
-        cudaEventRecord(ev[2 * used + 1], s);
-        ++used;
-        open_stage = -1;
-    }
-    void collect() {
-        for (size_t k = 0; k < used; ++k) {
-            cudaEventSynchronize(ev[2 * k + 1]);
-            float m = 0.f;
-            cudaEventElapsedTime(&m, ev[2 * k], ev[2 * k + 1]);
-            ms[stage[k]] += m;
-            cnt[stage[k]] += 1;
-        }
-        used = 0;
-    }
-    void reset() {
-        collect();
-        for (int i = 0; i < ST_N; ++i) {
-            ms[i] = 0;
-            cnt[i] = 0;
-        }
-    }
-    ~StageProfiler() {
-        for (auto e : ev) cudaEventDestroy(e);
-    }
-};
-
-struct dgmg_ctx {
-    int dim = 0, p = 0, q = 0;
-    int n[3] = {1, 1, 1};
-    int64_t ncell = 0, ndof = 0, nloc = 0;
-    dgmg_opts opts;
-    RefElem1D re;
-    int cpb = 8;
-    std::vector<CGLevelHost> lv;
-    int64_t ncoarse = 0;
-    double *coarse_inv = nullptr;
-    DGDev<double> d64;
-    DGDev<float> d32;
-    std::vector<CGDev<double>> cg64;
-    std::vector<CGDev<float>> cg32;
-    // work vectors
-    float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *xs32 = nullptr, *rold32 = nullptr;
-    double *w_r = nullptr, *w_z = nullptr, *w_p = nullptr, *w_q = nullptr, *w_rold = nullptr;
-    double *w_b = nullptr, *w_x = nullptr;        // dgmg_solve_host staging
-    double *scal = nullptr, *partials = nullptr;  // device scalars
-    double *host_scal = nullptr;                  // pinned
-    double *quad_x1 = nullptr, *quad_V = nullptr, *quad_w = nullptr;
-    std::vector<void *> allocs;
-    size_t bytes = 0;
-    StageProfiler prof;
-
-    template <typename T>
-    int alloc(T **ptr, size_t count) {
-        *ptr = nullptr;
-        if (count == 0) count = 1;
-        cudaError_t e = cudaMalloc((void **)ptr, count * sizeof(T));
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return fail(DGMG_ENOMEM, std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) +
-                                         " bytes failed: " + cudaGetErrorString(e));
-        }
-        allocs.push_back(*ptr);
-        bytes += count * sizeof(T);
-        return DGMG_OK;
-    }
-    template <typename T>
-    int upload(T **ptr, const std::vector<T> &h) {
-        int rc = alloc(ptr, h.size());
-        if (rc) return rc;
-        if (!h.empty()) DG_CUDA(cudaMemcpy(*ptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
-        return DGMG_OK;
-    }
-    ~dgmg_ctx() {
-        for (void *p : allocs) cudaFree(p);
-        if (host_scal) cudaFreeHost(host_scal);
-    }
-};
-
-// slots of ctx->scal
-enum { S_RZ = 0, S_PQ = 1, S_BETA = 2, S_RR = 3, S_RZN = 4, S_RZO = 5, S_BB = 6, S_ZZ = 7, S_NSCAL = 16 };
-
-namespace {
-
-#define RC(x)                        \
-    do {                             \
-        int rc_ = (x);               \
-        if (rc_ != DGMG_OK) return rc_; \
-    } while (0)
-
-#define LC(x)                                             \
-    do {                                                  \
-        cudaError_t e_ = (x);                             \
-        if (e_ != cudaSuccess) return cuda_fail(e_, #x);  \
-    } while (0)
+namespace dgmg {
 
 int exact_block(const dgmg_ctx &C) { return C.opts.block_inverse == DGMG_BLOCK_EXACT ? 1 : 0; }
 
@@ -795,20 +643,15 @@ int apply64(dgmg_ctx &C, const double *u, const double *b, double *out, cudaStre
     return DGMG_OK;
 }
 
-// beta of the CG direction update (Fletcher-Reeves, or Polak-Ribiere for the
-// flexible variant) and the shift of <r,z>, on the device
-__global__ void k_scalar_beta(double *scal, int flexible) {
-    const double rzn = scal[S_RZN];
-    scal[S_BETA] = flexible ? (rzn - scal[S_RZO]) / scal[S_RZ] : rzn / scal[S_RZ];
-    scal[S_RZ] = rzn;
-}
-
 int check_ctx(const dgmg_ctx *C) {
     if (!C) return fail(DGMG_EINVAL, "ctx is NULL");
     return DGMG_OK;
 }
 
-}  // namespace
+template int dg_vcycle<double>(dgmg_ctx &, const double *, double *, cudaStream_t);
+template int dg_vcycle<float>(dgmg_ctx &, const float *, float *, cudaStream_t);
+
+}  // namespace dgmg
 
 // ============================================================== C ABI
 extern "C" {
@@ -930,6 +773,8 @@ int dgmg_create(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_op
     {
         cudaError_t e = cudaMallocHost((void **)&C->host_scal, sizeof(double) * S_NSCAL);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
+        e = cudaEventCreateWithFlags(&C->ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
     }
     // quadrature tables for the load vector: (p+2) Gauss points per axis
     {
@@ -1138,235 +983,57 @@ int dgmg_load_vector(dgmg_ctx *C, const double *fq, double *b, void *stream) {
     return DGMG_OK;
 }
 
-// ----------------------------------------------------------------- solve
-static int read_scalar(dgmg_ctx *C, int slot, double *v, cudaStream_t s) {
-    LC(cudaMemcpyAsync(C->host_scal + slot, C->scal + slot, sizeof(double), cudaMemcpyDeviceToHost, s));
-    LC(cudaStreamSynchronize(s));
-    *v = C->host_scal[slot];
+int dgmg_estimate_bytes(const dgmg_mesh *mesh, int p, const dgmg_opts *opts, size_t *bytes) {
+    if (!mesh || !bytes) return fail(DGMG_EINVAL, "mesh and bytes must not be NULL");
+    if (mesh->dim != 2 && mesh->dim != 3) return fail(DGMG_EINVAL, "mesh->dim must be 2 or 3");
+    if (p < 1 || p > PMAX) return fail(DGMG_EINVAL, "p must be in 1..6");
+    for (int a = 0; a < mesh->dim; ++a)
+        if (mesh->n[a] < 2 || mesh->n[a] > (1 << 20)) return fail(DGMG_EINVAL, "every mesh->n[a] must be in 2..2^20");
+    dgmg_opts o;
+    dgmg_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.coarsening != 2 && o.coarsening != 3) return fail(DGMG_EINVAL, "coarsening must be 2 or 3");
+    const int dim = mesh->dim, q = p + 1, f = o.coarsening;
+    const bool mixed = o.precision == DGMG_MIXED_FP32;
+    const bool reliable = mixed && o.outer != DGMG_OUTER_PCG;
+    int n[3] = {1, 1, 1};
+    for (int a = 0; a < dim; ++a) n[a] = mesh->n[a];
+    const int64_t ncell = (int64_t)n[0] * n[1] * n[2];
+    const int64_t nloc = dim == 3 ? (int64_t)q * q * q : (int64_t)q * q, ndof = ncell * nloc;
+    const int64_t nf = nloc / q, tr = ncell * 2 * dim * 2 * nf, ns = dim == 3 ? 27 : 9;
+    auto sz = [](int64_t count, size_t elem) { return (size_t)std::max<int64_t>(count, 1) * elem; };
+    size_t dg64 = sz(ncell, 8) + sz(ncell * dim * (q * q + q), 8) + sz(ndof, 8) + 2 * sz(tr, 8) + sz(ncell << dim, 8);
+    size_t dg32 = sz(ncell, 4) + sz(ncell * dim * (q * q + q), 4) + 2 * sz(tr, 4) + sz(ncell << dim, 4);
+    size_t cg64 = 0, cg32 = 0;
+    int cur[3] = {n[0], n[1], n[2]};
+    int64_t nv = 1;
+    for (;;) {
+        nv = (int64_t)(cur[0] - 1) * (dim >= 2 ? cur[1] - 1 : 1) * (dim == 3 ? cur[2] - 1 : 1);
+        cg64 += sz(ns * nv, 8) + 4 * sz(nv, 8);
+        cg32 += sz(ns * nv, 4) + 4 * sz(nv, 4);
+        bool any = false;
+        for (int a = 0; a < dim; ++a) any = any || can_coarsen(cur[a], f);
+        if (!any) break;
+        int64_t ints = 0, dbl = 0;
+        int nxt[3] = {cur[0], cur[1], cur[2]};
+        for (int a = 0; a < dim; ++a) {
+            const int mf = cur[a] - 1;
+            const int nc = can_coarsen(cur[a], f) ? (int)coarse_positions(cur[a], f).size() - 1 : cur[a];
+            ints += 2 * mf + 2 * (nc - 1);
+            dbl += 2 * mf + 5 * (nc - 1);
+            nxt[a] = nc;
+        }
+        cg64 += sz(ints, 4) + sz(dbl, 8);
+        cg32 += sz(ints, 4) + sz(dbl, 4);
+        for (int a = 0; a < 3; ++a) cur[a] = nxt[a];
+    }
+    size_t total = sz(nv * nv, 8) + dg64 + cg64 + 5 * sz(ndof, 8) + sz(S_NSCAL, 8) + sz(2 * DOT_BLOCKS, 8) +
+                   sz(p + 2, 8) + sz((int64_t)q * (p + 2), 8) + sz(3 * (p + 2), 8);
+    if (mixed) total += dg32 + cg32 + 2 * sz(ndof, 4) + (reliable ? 4 * sz(ndof, 4) : 0);
+    *bytes = total;
     return DGMG_OK;
 }
 
-// y = A u in FP32 (warm-up projection + cell equation on the FP32 hierarchy)
-static int apply32(dgmg_ctx *C, const float *u, float *y, cudaStream_t s) {
-    DGDev<float> &D = C->d32;
-    C->prof.begin(ST_PROJECT, s);
-    LC(launch_project<float>(C->dim, C->q, D.c, C->cpb, const_cast<float *>(u), nullptr, D.tr[0], s));
-    C->prof.end(s);
-    C->prof.begin(ST_RESIDUAL, s);
-    LC(launch_residual<float>(C->dim, C->q, D.c, C->cpb, RES_WRITE_R | RES_NEGATE, u, nullptr, D.kappa, D.tr[0], y,
-                              nullptr, s));
-    C->prof.end(s);
-    return DGMG_OK;
-}
-
-// Mixed-precision CG with reliable updates: FP32 recurrences (apply, V-cycle,
-// vector updates; dot products accumulated in FP64), FP64 solution and FP64
-// true residual whenever the FP32 residual fell below delta times its value at
-// the last FP64 evaluation, and for the stopping test.
-static int solve_reliable(dgmg_ctx *C, const double *b, double *x, dgmg_stats *stats, cudaStream_t s,
-                          std::chrono::steady_clock::time_point t0) {
-    const int64_t n = C->ndof;
-    double *r64 = C->w_r;
-    float *r = C->r32, *z = C->z32, *p = C->p32, *q = C->q32, *xs = C->xs32, *rold = C->rold32;
-    double bb = 0.0, rr = 0.0, zz0 = 0.0, zz = 0.0;
-    int nres = 0;
-    LC(launch_dot(n, b, b, C->partials, C->scal + S_BB, s));
-    RC(read_scalar(C, S_BB, &bb, s));
-    if (!std::isfinite(bb)) return fail(DGMG_ENONFINITE, "||b|| is not finite");
-    const double bn = std::sqrt(bb) > 0 ? std::sqrt(bb) : 1.0;
-    const double rtol = C->opts.rtol;
-    auto true_residual = [&](double *out_rr) -> int {
-        RC(apply64(*C, x, b, r64, s));
-        C->prof.begin(ST_VECTOR, s);
-        LC(launch_dot(n, r64, r64, C->partials, C->scal + S_RR, s));
-        LC(launch_cast_d2f(n, r64, r, s));
-        C->prof.end(s);
-        ++nres;
-        return read_scalar(C, S_RR, out_rr, s);
-    };
-    RC(true_residual(&rr));
-    if (!std::isfinite(rr)) return fail(DGMG_ENONFINITE, "initial residual is not finite");
-    double rel_true = std::sqrt(rr) / bn, relrec = rel_true;
-    double rnorm_at_update = std::sqrt(rr);
-    int it = 0, status = DGMG_OK;
-    if (rel_true > rtol) {
-        LC(cudaMemsetAsync(xs, 0, sizeof(float) * n, s));
-        RC(dg_vcycle<float>(*C, r, z, s));
-        C->prof.begin(ST_VECTOR, s);
-        LC(launch_dotf(n, r, z, C->partials, C->scal + S_RZ, s));
-        LC(launch_dotf(n, z, z, C->partials, C->scal + S_ZZ, s));
-        LC(cudaMemcpyAsync(p, z, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
-        C->prof.end(s);
-        RC(read_scalar(C, S_ZZ, &zz0, s));
-        zz = zz0;
-        for (it = 1; it <= C->opts.maxit; ++it) {
-            RC(apply32(C, p, q, s));
-            C->prof.begin(ST_VECTOR, s);
-            LC(launch_dotf(n, p, q, C->partials, C->scal + S_PQ, s));
-            LC(launch_update_xr_f(n, xs, r, rold, p, q, C->scal, s));
-            LC(launch_dotf(n, r, r, C->partials, C->scal + S_RR, s));
-            C->prof.end(s);
-            double rr32 = 0.0;
-            RC(read_scalar(C, S_RR, &rr32, s));
-            if (!std::isfinite(rr32)) {
-                status = fail(DGMG_ENONFINITE, "residual norm is not finite");
-                break;
-            }
-            relrec = std::sqrt(rr32) / bn;
-            if (relrec <= rtol || std::sqrt(rr32) < C->opts.delta * rnorm_at_update) {
-                // reliable update: fold the FP32 correction into x, true FP64 residual
-                C->prof.begin(ST_VECTOR, s);
-                LC(launch_accumulate_f2d(n, x, xs, s));
-                C->prof.end(s);
-                RC(true_residual(&rr));
-                if (!std::isfinite(rr)) {
-                    status = fail(DGMG_ENONFINITE, "residual norm is not finite");
-                    break;
-                }
-                rel_true = std::sqrt(rr) / bn;
-                rnorm_at_update = std::sqrt(rr);
-                if (rel_true <= rtol) break;
-            }
-            if (it == C->opts.maxit) {
-                status = fail(DGMG_ENOTCONVERGED, "maxit reached");
-                break;
-            }
-            RC(dg_vcycle<float>(*C, r, z, s));
-            C->prof.begin(ST_VECTOR, s);
-            LC(launch_dot2f(n, r, z, rold, C->partials, C->scal + S_RZN, C->scal + S_RZO, s));
-            count_launches(1);
-            k_scalar_beta<<<1, 1, 0, s>>>(C->scal, 1);
-            LC(cudaGetLastError());
-            LC(launch_update_p_f(n, p, z, C->scal, s));
-            C->prof.end(s);
-        }
-        if (it > C->opts.maxit) it = C->opts.maxit;
-        if (status != DGMG_OK) {
-            C->prof.begin(ST_VECTOR, s);
-            LC(launch_accumulate_f2d(n, x, xs, s));
-            C->prof.end(s);
-            RC(true_residual(&rr));
-            rel_true = std::sqrt(rr) / bn;
-        }
-        LC(launch_dotf(n, z, z, C->partials, C->scal + S_ZZ, s));
-        RC(read_scalar(C, S_ZZ, &zz, s));
-    }
-    if (stats) {
-        stats->iterations = it;
-        stats->rel_residual = rel_true;
-        stats->rel_residual_recursive = relrec;
-        stats->prec_residual = zz0 > 0 ? std::sqrt(zz / zz0) : 0.0;
-        stats->fp64_applies = nres;
-        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    }
-    return status;
-}
-
-int dgmg_solve(dgmg_ctx *C, const double *b, double *x, dgmg_stats *stats, void *stream) {
-    RC(check_ctx(C));
-    NEED(b);
-    NEED(x);
-    if (b == x) return fail(DGMG_EINVAL, "b and x must not overlap");
-    const auto t0 = std::chrono::steady_clock::now();
-    cudaStream_t s = (cudaStream_t)stream;
-    if (C->opts.outer == DGMG_OUTER_RELIABLE) return solve_reliable(C, b, x, stats, s, t0);
-    const int64_t n = C->ndof;
-    const bool flexible = C->opts.precision == DGMG_MIXED_FP32;
-    int nres = 0;
-    double *r = C->w_r, *z = C->w_z, *p = C->w_p, *q = C->w_q, *rold = C->w_rold;
-    double bb = 0.0, rr = 0.0, zz0 = 0.0, zz = 0.0;
-    RC(apply64(*C, x, b, r, s));                                 // r = b - A x
-    ++nres;
-    LC(launch_dot(n, b, b, C->partials, C->scal + S_BB, s));
-    RC(read_scalar(C, S_BB, &bb, s));
-    if (!std::isfinite(bb)) return fail(DGMG_ENONFINITE, "||b|| is not finite");
-    LC(launch_dot(n, r, r, C->partials, C->scal + S_RR, s));
-    RC(read_scalar(C, S_RR, &rr, s));
-    if (!std::isfinite(rr)) return fail(DGMG_ENONFINITE, "initial residual is not finite");
-    const double bn = std::sqrt(bb) > 0 ? std::sqrt(bb) : 1.0;
-    const double rtol = C->opts.rtol;
-    int it = 0;
-    int status = DGMG_OK;
-    double relrec = std::sqrt(rr) / bn;
-    if (relrec > rtol) {
-        RC(vcycle64(*C, r, z, s));
-        LC(launch_dot(n, r, z, C->partials, C->scal + S_RZ, s));
-        LC(launch_dot(n, z, z, C->partials, C->scal + S_ZZ, s));
-        RC(read_scalar(C, S_ZZ, &zz0, s));
-        LC(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-        zz = zz0;
-        for (it = 1; it <= C->opts.maxit; ++it) {
-            RC(apply64(*C, p, nullptr, q, s));                   // q = A p
-            C->prof.begin(ST_VECTOR, s);
-            LC(launch_dot(n, p, q, C->partials, C->scal + S_PQ, s));
-            if (flexible) LC(cudaMemcpyAsync(rold, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-            LC(launch_pcg_update_xr(n, x, r, p, q, C->scal, s));   // alpha = rz / pq
-            LC(launch_dot(n, r, r, C->partials, C->scal + S_RR, s));
-            C->prof.end(s);
-            RC(read_scalar(C, S_RR, &rr, s));
-            if (!std::isfinite(rr)) {
-                status = fail(DGMG_ENONFINITE, "residual norm is not finite");
-                break;
-            }
-            relrec = std::sqrt(rr) / bn;
-            if (relrec <= rtol) break;
-            if (it == C->opts.maxit) {
-                status = fail(DGMG_ENOTCONVERGED, "maxit reached");
-                break;
-            }
-            RC(vcycle64(*C, r, z, s));
-            C->prof.begin(ST_VECTOR, s);
-            if (flexible)
-                LC(launch_dot2(n, r, z, rold, C->partials, C->scal + S_RZN, C->scal + S_RZO, s));
-            else
-                LC(launch_dot(n, r, z, C->partials, C->scal + S_RZN, s));
-            count_launches(1);
-            k_scalar_beta<<<1, 1, 0, s>>>(C->scal, flexible ? 1 : 0);
-            LC(cudaGetLastError());
-            LC(launch_pcg_update_p(n, p, z, C->scal, s));
-            C->prof.end(s);
-        }
-        if (it > C->opts.maxit) it = C->opts.maxit;
-        LC(launch_dot(n, z, z, C->partials, C->scal + S_ZZ, s));
-        RC(read_scalar(C, S_ZZ, &zz, s));
-    }
-    // true residual of the returned x
-    RC(apply64(*C, x, b, r, s));
-    ++nres;
-    LC(launch_dot(n, r, r, C->partials, C->scal + S_RR, s));
-    double rtrue = 0.0;
-    RC(read_scalar(C, S_RR, &rtrue, s));
-    if (stats) {
-        stats->iterations = it;
-        stats->rel_residual = std::sqrt(rtrue) / bn;
-        stats->rel_residual_recursive = relrec;
-        stats->prec_residual = zz0 > 0 ? std::sqrt(zz / zz0) : 0.0;
-        stats->fp64_applies = nres + it;
-        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    }
-    return status;
-}
-
-int dgmg_solve_host(dgmg_ctx *C, const double *b_host, double *x_host, dgmg_stats *stats, void *stream) {
-    RC(check_ctx(C));
-    NEED(b_host);
-    NEED(x_host);
-    cudaStream_t s = (cudaStream_t)stream;
-    if (!C->w_b) {
-        RC(C->alloc(&C->w_b, C->ndof));
-        RC(C->alloc(&C->w_x, C->ndof));
-    }
-    const auto t0 = std::chrono::steady_clock::now();
-    LC(cudaMemcpyAsync(C->w_b, b_host, sizeof(double) * C->ndof, cudaMemcpyHostToDevice, s));
-    LC(cudaMemcpyAsync(C->w_x, x_host, sizeof(double) * C->ndof, cudaMemcpyHostToDevice, s));
-    const int rc = dgmg_solve(C, C->w_b, C->w_x, stats, stream);
-    if (rc != DGMG_OK && rc != DGMG_ENOTCONVERGED) return rc;
-    LC(cudaMemcpyAsync(x_host, C->w_x, sizeof(double) * C->ndof, cudaMemcpyDeviceToHost, s));
-    LC(cudaStreamSynchronize(s));
-    if (stats)
-        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    return rc;
-}
 
 int dgmg_profile(dgmg_ctx *C, int enable) {
     RC(check_ctx(C));
@@ -1393,6 +1060,7 @@ int dgmg_profile_read(dgmg_ctx *C, double *ms, long long *launches, int nstage) 
 long long dgmg_kernel_launches(void) { return g_kernel_launches.load(); }
 
 }  // extern "C"
+
 
 // ------------------------------------------------ scratch-parameterised stage
 namespace dgmg {

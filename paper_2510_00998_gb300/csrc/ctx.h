@@ -1,0 +1,204 @@
+// Internal definition of the libdgmg context (shared by ctx.cu, solver.cu and
+// server.cu; not part of the C ABI).
+#pragma once
+
+#include <chrono>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace dgmg {
+
+// --------------------------------------------------------------- Q1 levels
+// One continuous Q1 level on the host: stencils (SoA [3^d][nv]) and the
+// per-axis transfer tables to the next coarser level.
+struct CGLevelHost {
+    int n[3] = {1, 1, 1};   // cells per axis
+    int m[3] = {1, 1, 1};   // interior vertices per axis
+    int64_t nv = 0;
+    std::vector<double> st;
+    // transfer to the next level (empty on the coarsest)
+    int mc[3] = {1, 1, 1};
+    std::vector<int> pl_lo[3], pl_hi[3], rs_start[3], rs_cnt[3];
+    std::vector<double> pl_wlo[3], pl_whi[3], rs_w[3];
+};
+
+
+}  // namespace dgmg
+
+using namespace dgmg;
+
+// ---------------------------------------------------------------- context
+template <typename T>
+struct DGDev {
+    DGConst<T> c;
+    T *kappa = nullptr, *fd = nullptr, *tr[2] = {nullptr, nullptr}, *corners = nullptr;
+    T *linv = nullptr;   // per-node 1 / (sum of the cell's eigenvalues); FP64 only
+};
+
+template <typename T>
+struct CGDev {
+    CGLevelDev<T> L;
+    T *st = nullptr;
+    T *u[2] = {nullptr, nullptr}, *b = nullptr, *r = nullptr;
+    int *itab = nullptr;
+    T *wtab = nullptr;
+};
+
+// Per-stage device time, recorded with CUDA events on the launching stream
+// around every stage launch while profiling is on (dgmg_profile).
+enum { ST_PROJECT = 0, ST_SMOOTH = 1, ST_RESIDUAL = 2, ST_CG = 3, ST_VECTOR = 4, ST_N = 5 };
+struct StageProfiler {
+    bool on = false;
+    std::vector<cudaEvent_t> ev;        // pairs: 2k start, 2k+1 stop
+    std::vector<int> stage;
+    size_t used = 0;
+    double ms[ST_N] = {0};
+    long long cnt[ST_N] = {0};
+    int open_stage = -1;
+    void begin(int st, cudaStream_t s) {
+        if (!on) return;
+        if (2 * used + 2 > ev.size()) {
+            cudaEvent_t a, b;
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            ev.push_back(a);
+            ev.push_back(b);
+            stage.push_back(st);
+        }
+        stage[used] = st;
+        cudaEventRecord(ev[2 * used], s);
+        open_stage = st;
+    }
+    void end(cudaStream_t s) {
+        if (!on || open_stage < 0) return;
+        cudaEventRecord(ev[2 * used + 1], s);
+        ++used;
+        open_stage = -1;
+    }
+    void collect() {
+        for (size_t k = 0; k < used; ++k) {
+            cudaEventSynchronize(ev[2 * k + 1]);
+            float m = 0.f;
+            cudaEventElapsedTime(&m, ev[2 * k], ev[2 * k + 1]);
+            ms[stage[k]] += m;
+            cnt[stage[k]] += 1;
+        }
+        used = 0;
+    }
+    void reset() {
+        collect();
+        for (int i = 0; i < ST_N; ++i) {
+            ms[i] = 0;
+            cnt[i] = 0;
+        }
+    }
+    ~StageProfiler() {
+        for (auto e : ev) cudaEventDestroy(e);
+    }
+};
+
+struct dgmg_ctx {
+    int dim = 0, p = 0, q = 0;
+    int n[3] = {1, 1, 1};
+    int64_t ncell = 0, ndof = 0, nloc = 0;
+    dgmg_opts opts;
+    RefElem1D re;
+    int cpb = 8;
+    std::vector<CGLevelHost> lv;
+    int64_t ncoarse = 0;
+    double *coarse_inv = nullptr;
+    DGDev<double> d64;
+    DGDev<float> d32;
+    std::vector<CGDev<double>> cg64;
+    std::vector<CGDev<float>> cg32;
+    // work vectors
+    float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *xs32 = nullptr, *rold32 = nullptr;
+    double *w_r = nullptr, *w_z = nullptr, *w_p = nullptr, *w_q = nullptr, *w_rold = nullptr;
+    double *w_b = nullptr, *w_x = nullptr;        // dgmg_solve_host staging
+    double *scal = nullptr, *partials = nullptr;  // device scalars
+    double *host_scal = nullptr;                  // pinned
+    double *quad_x1 = nullptr, *quad_V = nullptr, *quad_w = nullptr;
+    std::vector<void *> allocs;
+    size_t bytes = 0;
+    StageProfiler prof;
+    cudaEvent_t ev = nullptr;                     // completion of the scalars copied to host_scal
+
+    template <typename T>
+    int alloc(T **ptr, size_t count) {
+        *ptr = nullptr;
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMalloc((void **)ptr, count * sizeof(T));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(DGMG_ENOMEM, std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) +
+                                         " bytes failed: " + cudaGetErrorString(e));
+        }
+        allocs.push_back(*ptr);
+        bytes += count * sizeof(T);
+        return DGMG_OK;
+    }
+    template <typename T>
+    int upload(T **ptr, const std::vector<T> &h) {
+        int rc = alloc(ptr, h.size());
+        if (rc) return rc;
+        if (!h.empty()) DG_CUDA(cudaMemcpy(*ptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+        return DGMG_OK;
+    }
+    ~dgmg_ctx() {
+        for (void *p : allocs) cudaFree(p);
+        if (host_scal) cudaFreeHost(host_scal);
+        if (ev) cudaEventDestroy(ev);
+    }
+};
+
+// slots of ctx->scal
+enum { S_RZ = 0, S_PQ = 1, S_BETA = 2, S_RR = 3, S_RZN = 4, S_RZO = 5, S_BB = 6, S_ZZ = 7, S_ZZ0 = 8, S_NSCAL = 16 };
+
+
+#define RC(x)                           \
+    do {                                \
+        int rc_ = (x);                  \
+        if (rc_ != DGMG_OK) return rc_; \
+    } while (0)
+
+#define LC(x)                                            \
+    do {                                                 \
+        cudaError_t e_ = (x);                            \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #x); \
+    } while (0)
+
+namespace dgmg {
+
+int check_ctx(const dgmg_ctx *C);
+int exact_block(const dgmg_ctx &C);
+// y = A u (b == NULL) or out = b - A u, FP64
+int apply64(dgmg_ctx &C, const double *u, const double *b, double *out, cudaStream_t s);
+// y = A u in FP32
+int apply32(dgmg_ctx &C, const float *u, float *y, cudaStream_t s);
+// z = V(r): FP64 interface (FP32 cycle inside in mixed precision)
+int vcycle64(dgmg_ctx &C, const double *r, double *z, cudaStream_t s);
+// z = V(r) on the DG level in precision T (zero initial guess)
+template <typename T>
+int dg_vcycle(dgmg_ctx &C, const T *r, T *z, cudaStream_t s);
+
+// One solve as a non-blocking state machine (solver.cu). advance() queues the
+// next stretch of device work on the run's stream and returns without waiting;
+// it returns 1 once the solve has finished (status and stats final), 0 while it
+// waits for device scalars or has more work to queue.
+struct SolveRun {
+    dgmg_ctx *C = nullptr;
+    const double *b = nullptr;
+    double *x = nullptr;
+    cudaStream_t s = nullptr;
+    int state = 0, it = 0, status = DGMG_OK, nres = 0;
+    double bb = 0, bn = 1, rr = 0, relrec = 0, rel_true = 0, rnorm_upd = 0, zz0 = 0, zz = 0;
+    bool need_accumulate = false;
+    std::chrono::steady_clock::time_point t0;
+    dgmg_stats stats{};
+    void start(dgmg_ctx *ctx, const double *b_, double *x_, cudaStream_t s_);
+    int advance(bool blocking);
+};
+
+}  // namespace dgmg

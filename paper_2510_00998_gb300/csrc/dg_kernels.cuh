@@ -16,18 +16,23 @@
 // 1 = high end), comp 0 = value u, comp 1 = derivative along +axis.
 #pragma once
 
+#include <type_traits>
+
 #include "internal.h"
 
 namespace dgmg {
 
-template <int DIM, int Q>
+template <int DIM, int Q, typename T = float>
 struct Geo {
     static constexpr int NL = DIM == 3 ? Q * Q * Q : Q * Q;   // nodes per cell
     static constexpr int NF = NL / Q;                          // nodes per face = threads per cell
     static constexpr int NFACE = 2 * DIM;
     static constexpr int TR = NFACE * 2 * NF;                  // trace values per cell
     static constexpr int NC = 1 << DIM;                        // corners per cell
-    static constexpr int FDS = Q * Q + Q;                      // fast-diag factors per axis
+    static constexpr int FDS = Q * Q + Q;                      // fast-diag factors per axis (global)
+    static constexpr int VEC = 16 / (int)sizeof(T);            // elements per 16-byte vector
+    static constexpr int FDSP = (FDS + VEC - 1) / VEC * VEC;   // per axis in shared memory (padded)
+    static constexpr int QQV = (Q * Q + VEC - 1) / VEC;        // 16-byte vectors covering S
     // volume index of node i of the pencil along `dir` at tangential position t
     static __device__ __forceinline__ int vidx(int dir, int t, int i) {
         if (DIM == 2) return dir == 0 ? i + Q * t : t + Q * i;
@@ -66,6 +71,17 @@ __device__ __forceinline__ void stage_masses(const DGConst<T> &c, T *sM) {
     for (int e = threadIdx.x; e < DIM * Q * Q; e += blockDim.x) sM[e] = c.M[e / (Q * Q)][e % (Q * Q)];
 }
 
+// Load one q x q factor matrix (16-byte aligned in shared memory) into
+// registers with 16-byte vector loads.
+template <int DIM, int Q, typename T>
+__device__ __forceinline__ void load_factor(const T *src, T *dst) {
+    using G = Geo<DIM, Q, T>;
+    using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    const V *s = reinterpret_cast<const V *>(src);
+#pragma unroll
+    for (int k = 0; k < G::QQV; ++k) reinterpret_cast<V *>(dst)[k] = s[k];
+}
+
 // 1D tables read with thread-dependent indices by build_block_1d, staged in
 // shared memory: K [axis][q*q], then d0 [axis][q], then dp [axis][q].
 template <int DIM, int Q, typename T>
@@ -96,7 +112,7 @@ template <int DIM, int Q, typename T>
 __device__ __forceinline__ void load_neighbour_traces(const DGConst<T> &c, int64_t cell, const int *ci, int t,
                                                       const T *__restrict__ tr, const T *__restrict__ kappa,
                                                       T *sF, T *sKF, T *sKappa) {
-    using G = Geo<DIM, Q>;
+    using G = Geo<DIM, Q, T>;
     const T kK = kappa[cell];
 #pragma unroll
     for (int f = 0; f < G::NFACE; ++f) {
@@ -125,21 +141,31 @@ __device__ __forceinline__ void load_neighbour_traces(const DGConst<T> &c, int64
 // Apply the facet mass matrix (tensor product of the tangential 1D masses) to
 // both components of every interior face of the cell, in place. Needs all
 // threads of the CTA (contains barriers); `active` threads do the arithmetic.
-// sM: shared-memory copy of the 1D masses, [axis][q*q] (the row read depends
-// on the thread, which would serialise reads from kernel-parameter space).
+// Each thread keeps the rows of the (h-scaled) 1D masses it needs in registers:
+// its first tangential index ia with the masses of axes 0 and 1 (first pass),
+// its second index ib with the masses of axes 1 and 2 (second pass). sM: the
+// per-axis masses staged in shared memory, [axis][q*q].
 template <int DIM, int Q, typename T>
 __device__ __forceinline__ void facet_mass(const T *sM, bool active, int t, T *sF, int mask) {
-    using G = Geo<DIM, Q>;
+    using G = Geo<DIM, Q, T>;
     constexpr int NPASS = DIM - 1;
+    const int ia = t % Q, ib = t / Q;
+    T ra[2][Q], rb[2][Q];
+#pragma unroll
+    for (int m = 0; m < Q; ++m) {
+        ra[0][m] = sM[0 * Q * Q + ia * Q + m];
+        ra[1][m] = sM[1 * Q * Q + ia * Q + m];
+        rb[0][m] = DIM == 3 ? sM[1 * Q * Q + ib * Q + m] : T(0);
+        rb[1][m] = DIM == 3 ? sM[2 * Q * Q + ib * Q + m] : T(0);
+    }
 #pragma unroll
     for (int pass = 0; pass < NPASS; ++pass) {
         T out[G::NFACE][2];
         if (active) {
-            const int ia = t % Q, ib = t / Q;
 #pragma unroll
             for (int f = 0; f < G::NFACE; ++f) {
                 const int dir = f >> 1;
-                // tangential axes: ta (lower), tb (upper)
+                // tangential axes: ta (lower) in {0, 1}, tb (upper) in {1, 2}
                 const int ta = dir == 0 ? 1 : 0;
                 const int tb = dir == 2 ? 1 : 2;
 #pragma unroll
@@ -149,13 +175,13 @@ __device__ __forceinline__ void facet_mass(const T *sM, bool active, int t, T *s
                     if (mask & (1 << f)) {
                         if (DIM == 2) {
 #pragma unroll
-                            for (int m = 0; m < Q; ++m) s += sM[ta * Q * Q + t * Q + m] * fld[m];
+                            for (int m = 0; m < Q; ++m) s += ra[ta][m] * fld[m];
                         } else if (pass == 0) {
 #pragma unroll
-                            for (int m = 0; m < Q; ++m) s += sM[ta * Q * Q + ia * Q + m] * fld[m + Q * ib];
+                            for (int m = 0; m < Q; ++m) s += ra[ta][m] * fld[m + Q * ib];
                         } else {
 #pragma unroll
-                            for (int m = 0; m < Q; ++m) s += sM[tb * Q * Q + ib * Q + m] * fld[ia + Q * m];
+                            for (int m = 0; m < Q; ++m) s += rb[tb - 1][m] * fld[ia + Q * m];
                         }
                     }
                     out[f][comp] = s;
@@ -183,7 +209,7 @@ __device__ __forceinline__ void facet_mass(const T *sM, bool active, int t, T *s
 template <int DIM, int Q, typename T>
 __device__ __forceinline__ void lift_neighbours(const DGConst<T> &c, bool active, int t, T *sR, const T *sF,
                                                 const T *sKF, int mask) {
-    using G = Geo<DIM, Q>;
+    using G = Geo<DIM, Q, T>;
 #pragma unroll
     for (int dir = 0; dir < DIM; ++dir) {
         if (active) {
@@ -222,7 +248,7 @@ __device__ __forceinline__ void lift_neighbours(const DGConst<T> &c, bool active
 template <int DIM, int Q, typename T>
 __device__ __forceinline__ void build_block_1d(const DGConst<T> &c, const T *sT, bool active, int t, const T *myK,
                                                int mask, T *myKT) {
-    using G = Geo<DIM, Q>;
+    using G = Geo<DIM, Q, T>;
     if (!active) return;
     const T *K = sT, *d0 = sT + DIM * Q * Q, *dp = d0 + DIM * Q;
     const T kK = myK[G::NFACE];
@@ -257,7 +283,7 @@ __device__ __forceinline__ void build_block_1d(const DGConst<T> &c, const T *sT,
 template <int DIM, int Q, typename T>
 __device__ __forceinline__ void subtract_block_apply(const DGConst<T> &c, bool active, int t, const T *myU, T *myR,
                                                      T *myA, T *myB, const T *myKT) {
-    using G = Geo<DIM, Q>;
+    using G = Geo<DIM, Q, T>;
     constexpr int D = DIM - 1;   // first pass along the highest axis
     if (active) {
         T x[Q];
@@ -320,7 +346,7 @@ __device__ __forceinline__ void subtract_block_apply(const DGConst<T> &c, bool a
 template <int DIM, int Q, typename T>
 __device__ __forceinline__ void write_pencil_traces(const DGConst<T> &c, int dir, int t, const T *x,
                                                     T *__restrict__ trc) {
-    using G = Geo<DIM, Q>;
+    using G = Geo<DIM, Q, T>;
     T dlo = T(0), dhi = T(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -342,7 +368,7 @@ __device__ __forceinline__ void write_pencil_traces(const DGConst<T> &c, int dir
 template <int DIM, int Q, typename T>
 __global__ void __launch_bounds__(256) k_project(DGConst<T> c, int cpb, T *__restrict__ u,
                                                   const T *__restrict__ e0, T *__restrict__ tr) {
-    using G = Geo<DIM, Q>;
+    using G = Geo<DIM, Q, T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sU = reinterpret_cast<T *>(smem_raw);
     T *sE = sU + cpb * G::NL;
@@ -434,13 +460,13 @@ __global__ void __launch_bounds__(256) k_smooth(DGConst<T> c, int cpb, int exact
                                                 const T *__restrict__ b, const T *__restrict__ kappa,
                                                 const T *__restrict__ fd, const T *__restrict__ linv,
                                                 const T *__restrict__ tr_in, T *__restrict__ tr_out) {
-    using G = Geo<DIM, Q>;
+    using G = Geo<DIM, Q, T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sU = reinterpret_cast<T *>(smem_raw);
+    T *sFD = reinterpret_cast<T *>(smem_raw);   // [cpb][DIM][FDSP], 16-byte aligned blocks
+    T *sU = sFD + cpb * DIM * G::FDSP;
     T *sR = sU + cpb * G::NL;
     T *sF = sR + cpb * G::NL;
-    T *sFD = sF + cpb * G::NFACE * 2 * G::NF;
-    T *sK = sFD + cpb * DIM * G::FDS;          // [cpb][NFACE + 1]
+    T *sK = sF + cpb * G::NFACE * 2 * G::NF;   // [cpb][NFACE + 1]
     T *sA = sK + cpb * (G::NFACE + 1);         // inexact block only: [cpb][NL] x 2, [cpb][DIM*Q*Q]
     T *sB = sA + cpb * G::NL;
     T *sKT = sB + cpb * G::NL;
@@ -456,7 +482,8 @@ __global__ void __launch_bounds__(256) k_smooth(DGConst<T> c, int cpb, int exact
     if (!exact) stage_block_tables<DIM, Q, T>(c, sT);
     block_copy(sU, u + cell0 * G::NL, (int64_t)ncl * G::NL);
     block_copy(sR, b + cell0 * G::NL, (int64_t)ncl * G::NL);
-    block_copy(sFD, fd + cell0 * DIM * G::FDS, (int64_t)ncl * DIM * G::FDS);
+    for (int64_t i = threadIdx.x; i < (int64_t)ncl * DIM * G::FDS; i += blockDim.x)
+        sFD[(i / G::FDS) * G::FDSP + i % G::FDS] = fd[cell0 * DIM * G::FDS + i];
     T *myF = sF + lc * G::NFACE * 2 * G::NF;
     T *myK = sK + lc * (G::NFACE + 1);
     if (active) {
@@ -473,13 +500,14 @@ __global__ void __launch_bounds__(256) k_smooth(DGConst<T> c, int cpb, int exact
     if (!exact)
         subtract_block_apply<DIM, Q, T>(c, active, t, myU, myR, sA + lc * G::NL, sB + lc * G::NL,
                                         sKT + lc * DIM * Q * Q);
-    const T *myS = sFD + lc * DIM * G::FDS;      // S_a at a*FDS, lambda_a at a*FDS + Q*Q
+    const T *myS = sFD + lc * DIM * G::FDSP;     // S_a at a*FDSP, lambda_a at a*FDSP + Q*Q
     // S^T along the axes 0..DIM-2
 #pragma unroll
     for (int dir = 0; dir < DIM - 1; ++dir) {
         if (active) {
             T x[Q], y[Q];
-            const T *S = myS + dir * G::FDS;
+            __align__(16) T S[G::QQV * G::VEC];
+            load_factor<DIM, Q, T>(myS + dir * G::FDSP, S);
 #pragma unroll
             for (int i = 0; i < Q; ++i) x[i] = myR[G::vidx(dir, t, i)];
 #pragma unroll
@@ -499,13 +527,14 @@ __global__ void __launch_bounds__(256) k_smooth(DGConst<T> c, int cpb, int exact
         constexpr int D = DIM - 1;
         if (active) {
             T x[Q], y[Q];
-            const T *S = myS + D * G::FDS;
-            const T *lam = S + Q * Q;
+            __align__(16) T S[G::QQV * G::VEC];
+            load_factor<DIM, Q, T>(myS + D * G::FDSP, S);
+            const T *lam = myS + D * G::FDSP + Q * Q;
             T lt;
             if (DIM == 2) {
-                lt = myS[0 * G::FDS + Q * Q + t];
+                lt = myS[0 * G::FDSP + Q * Q + t];
             } else {
-                lt = myS[0 * G::FDS + Q * Q + (t % Q)] + myS[1 * G::FDS + Q * Q + (t / Q)];
+                lt = myS[0 * G::FDSP + Q * Q + (t % Q)] + myS[1 * G::FDSP + Q * Q + (t / Q)];
             }
 #pragma unroll
             for (int i = 0; i < Q; ++i) x[i] = myR[G::vidx(D, t, i)];
@@ -535,7 +564,8 @@ __global__ void __launch_bounds__(256) k_smooth(DGConst<T> c, int cpb, int exact
     for (int dir = DIM - 2; dir >= 1; --dir) {
         if (active) {
             T x[Q], y[Q];
-            const T *S = myS + dir * G::FDS;
+            __align__(16) T S[G::QQV * G::VEC];
+            load_factor<DIM, Q, T>(myS + dir * G::FDSP, S);
 #pragma unroll
             for (int i = 0; i < Q; ++i) x[i] = myR[G::vidx(dir, t, i)];
 #pragma unroll
@@ -554,7 +584,8 @@ __global__ void __launch_bounds__(256) k_smooth(DGConst<T> c, int cpb, int exact
     T *trc = tr_out + cell * G::TR;
     if (active) {
         T x[Q], un[Q];
-        const T *S = myS;
+        __align__(16) T S[G::QQV * G::VEC];
+        load_factor<DIM, Q, T>(myS, S);
 #pragma unroll
         for (int i = 0; i < Q; ++i) x[i] = myR[G::vidx(0, t, i)];
         const T om = c.omega;
@@ -594,7 +625,7 @@ __global__ void __launch_bounds__(256) k_residual(DGConst<T> c, int cpb, int mod
                                                   const T *__restrict__ b, const T *__restrict__ kappa,
                                                   const T *__restrict__ tr, T *__restrict__ rout,
                                                   T *__restrict__ corners) {
-    using G = Geo<DIM, Q>;
+    using G = Geo<DIM, Q, T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sU = reinterpret_cast<T *>(smem_raw);
     T *sR = sU + cpb * G::NL;
@@ -684,24 +715,24 @@ __global__ void __launch_bounds__(256) k_residual(DGConst<T> c, int cpb, int mod
 // Shared-memory bytes per CTA of each kernel.
 template <int DIM, int Q, typename T>
 constexpr size_t smem_project(int cpb) {
-    return (size_t)cpb * (Geo<DIM, Q>::NL + Geo<DIM, Q>::NC) * sizeof(T);
+    return (size_t)cpb * (Geo<DIM, Q, T>::NL + Geo<DIM, Q, T>::NC) * sizeof(T);
 }
 template <int DIM, int Q, typename T>
 constexpr size_t smem_smooth(int cpb, bool exact) {
-    using G = Geo<DIM, Q>;
+    using G = Geo<DIM, Q, T>;
     return (size_t)cpb *
-           (2 * G::NL + G::NFACE * 2 * G::NF + DIM * G::FDS + G::NFACE + 1 + (exact ? 0 : 2 * G::NL + DIM * Q * Q)) *
+           (DIM * G::FDSP + 2 * G::NL + G::NFACE * 2 * G::NF + G::NFACE + 1 + (exact ? 0 : 2 * G::NL + DIM * Q * Q)) *
            sizeof(T);
 }
 template <int DIM, int Q, typename T>
 constexpr size_t smem_residual(int cpb) {
-    using G = Geo<DIM, Q>;
+    using G = Geo<DIM, Q, T>;
     return (size_t)cpb * (4 * G::NL + G::NFACE * 2 * G::NF + DIM * Q * Q + G::NFACE + 1) * sizeof(T);
 }
 
 template <int DIM, int Q, typename T>
 struct DGLaunch {
-    using G = Geo<DIM, Q>;
+    using G = Geo<DIM, Q, T>;
     static cudaError_t project(const DGConst<T> &c, int cpb, T *u, const T *e0, T *tr, cudaStream_t s) {
         const size_t sm = smem_project<DIM, Q, T>(cpb);
         static bool attr = false;

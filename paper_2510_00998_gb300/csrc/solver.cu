@@ -1,0 +1,403 @@
+// The outer iterations of dgmg_solve as a non-blocking state machine:
+//
+//  * FP64 preconditioned CG (DGMG_OUTER_PCG): one FP64 apply per iteration, the
+//    V-cycle (FP64 or FP32) as preconditioner, flexible Polak-Ribiere form when
+//    the V-cycle runs in FP32.
+//  * Reliable-update CG (DGMG_OUTER_RELIABLE, mixed precision): the
+//    recurrences in FP32 (FP32 apply and V-cycle, dot products accumulated in
+//    FP64), the solution accumulated in FP64, and the true residual b - A x
+//    recomputed in FP64 whenever the FP32 residual has fallen by `delta`
+//    since the last FP64 evaluation, and before stopping.
+//
+// Device work is queued on the run's stream; the scalars the host decides on
+// (residual norms) come back through pinned memory and an event, so a
+// scheduler can advance many runs on different streams without blocking.
+#include <cmath>
+
+#include "ctx.h"
+
+namespace dgmg {
+
+namespace {
+
+// beta of the CG direction update (Fletcher-Reeves, or Polak-Ribiere for the
+// flexible variant) and the shift of <r,z>, on the device
+__global__ void k_scalar_beta(double *scal, int flexible) {
+    const double rzn = scal[S_RZN];
+    scal[S_BETA] = flexible ? (rzn - scal[S_RZO]) / scal[S_RZ] : rzn / scal[S_RZ];
+    scal[S_RZ] = rzn;
+}
+
+int launch_beta(dgmg_ctx *C, int flexible, cudaStream_t s) {
+    count_launches(1);
+    k_scalar_beta<<<1, 1, 0, s>>>(C->scal, flexible);
+    LC(cudaGetLastError());
+    return DGMG_OK;
+}
+
+// queue the copy of the whole scalar block to pinned host memory + the event
+int post_scalars(dgmg_ctx *C, cudaStream_t s) {
+    LC(cudaMemcpyAsync(C->host_scal, C->scal, sizeof(double) * S_NSCAL, cudaMemcpyDeviceToHost, s));
+    LC(cudaEventRecord(C->ev, s));
+    return DGMG_OK;
+}
+
+// 1 if the posted scalars have arrived, 0 if not yet; <0 on error
+int scalars_ready(dgmg_ctx *C, bool blocking) {
+    cudaError_t e = blocking ? cudaEventSynchronize(C->ev) : cudaEventQuery(C->ev);
+    if (e == cudaSuccess) return 1;
+    if (e == cudaErrorNotReady) return 0;
+    return cuda_fail(e, "cudaEventQuery");
+}
+
+enum {
+    P_START, P_WAIT0, P_WAIT1, P_ITER, P_WAIT_RR, P_FINAL, P_WAIT_FINAL,   // FP64 PCG
+    R_START, R_WAIT0, R_ITER, R_WAIT_RR, R_WAIT_UPD, R_CONT, R_FINAL, R_WAIT_FIN,   // reliable updates
+    S_DONE
+};
+
+}  // namespace
+
+// y = A u in FP32 (warm-up projection + cell equation on the FP32 hierarchy)
+int apply32(dgmg_ctx &C, const float *u, float *y, cudaStream_t s) {
+    DGDev<float> &D = C.d32;
+    C.prof.begin(ST_PROJECT, s);
+    LC(launch_project<float>(C.dim, C.q, D.c, C.cpb, const_cast<float *>(u), nullptr, D.tr[0], s));
+    C.prof.end(s);
+    C.prof.begin(ST_RESIDUAL, s);
+    LC(launch_residual<float>(C.dim, C.q, D.c, C.cpb, RES_WRITE_R | RES_NEGATE, u, nullptr, D.kappa, D.tr[0], y,
+                              nullptr, s));
+    C.prof.end(s);
+    return DGMG_OK;
+}
+
+void SolveRun::start(dgmg_ctx *ctx, const double *b_, double *x_, cudaStream_t s_) {
+    C = ctx;
+    b = b_;
+    x = x_;
+    s = s_;
+    it = 0;
+    status = DGMG_OK;
+    nres = 0;
+    need_accumulate = false;
+    zz0 = zz = 0;
+    t0 = std::chrono::steady_clock::now();
+    state = C->opts.outer == DGMG_OUTER_RELIABLE ? R_START : P_START;
+}
+
+#define ADV_FAIL(code, msg)               \
+    do {                                  \
+        status = fail(code, msg);         \
+        state = S_DONE;                   \
+        return 1;                         \
+    } while (0)
+
+#define ADV(x)                            \
+    do {                                  \
+        int rc_ = (x);                    \
+        if (rc_ != DGMG_OK) {             \
+            status = rc_;                 \
+            state = S_DONE;               \
+            return 1;                     \
+        }                                 \
+    } while (0)
+
+#define ADV_CUDA(x)                                          \
+    do {                                                     \
+        cudaError_t e_ = (x);                                \
+        if (e_ != cudaSuccess) ADV(cuda_fail(e_, #x));      \
+    } while (0)
+
+int SolveRun::advance(bool blocking) {
+    const int64_t n = C->ndof;
+    const double rtol = C->opts.rtol;
+    const bool flexible = C->opts.precision == DGMG_MIXED_FP32;
+    double *r = C->w_r, *z = C->w_z, *p = C->w_p, *q = C->w_q, *rold = C->w_rold;
+    float *r32 = C->r32, *z32 = C->z32, *p32 = C->p32, *q32 = C->q32, *xs = C->xs32, *rold32 = C->rold32;
+    for (;;) {
+        switch (state) {
+            // ------------------------------------------------ FP64 PCG
+            case P_START:
+                ADV(apply64(*C, x, b, r, s));          // r = b - A x
+                ++nres;
+                ADV_CUDA(launch_dot(n, b, b, C->partials, C->scal + S_BB, s));
+                ADV_CUDA(launch_dot(n, r, r, C->partials, C->scal + S_RR, s));
+                ADV(post_scalars(C, s));
+                state = P_WAIT0;
+                break;
+            case P_WAIT0: {
+                const int rdy = scalars_ready(C, blocking);
+                if (rdy < 0) ADV(rdy);
+                if (!rdy) return 0;
+                bb = C->host_scal[S_BB];
+                rr = C->host_scal[S_RR];
+                if (!std::isfinite(bb)) ADV_FAIL(DGMG_ENONFINITE, "||b|| is not finite");
+                if (!std::isfinite(rr)) ADV_FAIL(DGMG_ENONFINITE, "initial residual is not finite");
+                bn = std::sqrt(bb) > 0 ? std::sqrt(bb) : 1.0;
+                relrec = std::sqrt(rr) / bn;
+                if (relrec <= rtol) {
+                    state = P_FINAL;
+                    break;
+                }
+                ADV(vcycle64(*C, r, z, s));
+                ADV_CUDA(launch_dot(n, r, z, C->partials, C->scal + S_RZ, s));
+                ADV_CUDA(launch_dot(n, z, z, C->partials, C->scal + S_ZZ0, s));
+                ADV_CUDA(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+                it = 1;
+                state = P_ITER;
+                break;
+            }
+            case P_ITER:
+                ADV(apply64(*C, p, nullptr, q, s));    // q = A p
+                C->prof.begin(ST_VECTOR, s);
+                ADV_CUDA(launch_dot(n, p, q, C->partials, C->scal + S_PQ, s));
+                if (flexible) ADV_CUDA(cudaMemcpyAsync(rold, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+                ADV_CUDA(launch_pcg_update_xr(n, x, r, p, q, C->scal, s));   // alpha = rz / pq
+                ADV_CUDA(launch_dot(n, r, r, C->partials, C->scal + S_RR, s));
+                C->prof.end(s);
+                ADV(post_scalars(C, s));
+                state = P_WAIT_RR;
+                break;
+            case P_WAIT_RR: {
+                const int rdy = scalars_ready(C, blocking);
+                if (rdy < 0) ADV(rdy);
+                if (!rdy) return 0;
+                rr = C->host_scal[S_RR];
+                if (!std::isfinite(rr)) {
+                    status = fail(DGMG_ENONFINITE, "residual norm is not finite");
+                    state = P_FINAL;
+                    break;
+                }
+                relrec = std::sqrt(rr) / bn;
+                if (relrec <= rtol) {
+                    state = P_FINAL;
+                    break;
+                }
+                if (it >= C->opts.maxit) {
+                    status = fail(DGMG_ENOTCONVERGED, "maxit reached");
+                    state = P_FINAL;
+                    break;
+                }
+                ADV(vcycle64(*C, r, z, s));
+                C->prof.begin(ST_VECTOR, s);
+                if (flexible)
+                    ADV_CUDA(launch_dot2(n, r, z, rold, C->partials, C->scal + S_RZN, C->scal + S_RZO, s));
+                else
+                    ADV_CUDA(launch_dot(n, r, z, C->partials, C->scal + S_RZN, s));
+                ADV(launch_beta(C, flexible ? 1 : 0, s));
+                ADV_CUDA(launch_pcg_update_p(n, p, z, C->scal, s));
+                C->prof.end(s);
+                ++it;
+                state = P_ITER;
+                break;
+            }
+            case P_FINAL:
+                ADV_CUDA(launch_dot(n, z, z, C->partials, C->scal + S_ZZ, s));
+                ADV(apply64(*C, x, b, r, s));          // true residual of the returned x
+                ++nres;
+                ADV_CUDA(launch_dot(n, r, r, C->partials, C->scal + S_RR, s));
+                ADV(post_scalars(C, s));
+                state = P_WAIT_FINAL;
+                break;
+            case P_WAIT_FINAL: {
+                const int rdy = scalars_ready(C, blocking);
+                if (rdy < 0) ADV(rdy);
+                if (!rdy) return 0;
+                zz = C->host_scal[S_ZZ];
+                zz0 = it > 0 ? C->host_scal[S_ZZ0] : 0.0;
+                rel_true = std::sqrt(C->host_scal[S_RR]) / bn;
+                stats.iterations = it;
+                stats.rel_residual = rel_true;
+                stats.rel_residual_recursive = relrec;
+                stats.prec_residual = zz0 > 0 ? std::sqrt(zz / zz0) : 0.0;
+                stats.fp64_applies = nres + it;
+                stats.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+                state = S_DONE;
+                return 1;
+            }
+            // ------------------------------------------------ reliable updates
+            case R_START:
+                ADV_CUDA(launch_dot(n, b, b, C->partials, C->scal + S_BB, s));
+                ADV(apply64(*C, x, b, r, s));
+                ++nres;
+                C->prof.begin(ST_VECTOR, s);
+                ADV_CUDA(launch_dot(n, r, r, C->partials, C->scal + S_RR, s));
+                ADV_CUDA(launch_cast_d2f(n, r, r32, s));
+                C->prof.end(s);
+                ADV(post_scalars(C, s));
+                state = R_WAIT0;
+                break;
+            case R_WAIT0: {
+                const int rdy = scalars_ready(C, blocking);
+                if (rdy < 0) ADV(rdy);
+                if (!rdy) return 0;
+                bb = C->host_scal[S_BB];
+                rr = C->host_scal[S_RR];
+                if (!std::isfinite(bb)) ADV_FAIL(DGMG_ENONFINITE, "||b|| is not finite");
+                if (!std::isfinite(rr)) ADV_FAIL(DGMG_ENONFINITE, "initial residual is not finite");
+                bn = std::sqrt(bb) > 0 ? std::sqrt(bb) : 1.0;
+                rel_true = relrec = std::sqrt(rr) / bn;
+                rnorm_upd = std::sqrt(rr);
+                if (rel_true <= rtol) {
+                    state = R_FINAL;
+                    break;
+                }
+                ADV_CUDA(cudaMemsetAsync(xs, 0, sizeof(float) * n, s));
+                ADV(dg_vcycle<float>(*C, r32, z32, s));
+                C->prof.begin(ST_VECTOR, s);
+                ADV_CUDA(launch_dotf(n, r32, z32, C->partials, C->scal + S_RZ, s));
+                ADV_CUDA(launch_dotf(n, z32, z32, C->partials, C->scal + S_ZZ0, s));
+                ADV_CUDA(cudaMemcpyAsync(p32, z32, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+                C->prof.end(s);
+                it = 1;
+                state = R_ITER;
+                break;
+            }
+            case R_ITER:
+                ADV(apply32(*C, p32, q32, s));
+                C->prof.begin(ST_VECTOR, s);
+                ADV_CUDA(launch_dotf(n, p32, q32, C->partials, C->scal + S_PQ, s));
+                ADV_CUDA(launch_update_xr_f(n, xs, r32, rold32, p32, q32, C->scal, s));
+                ADV_CUDA(launch_dotf(n, r32, r32, C->partials, C->scal + S_RR, s));
+                C->prof.end(s);
+                need_accumulate = true;
+                ADV(post_scalars(C, s));
+                state = R_WAIT_RR;
+                break;
+            case R_WAIT_RR: {
+                const int rdy = scalars_ready(C, blocking);
+                if (rdy < 0) ADV(rdy);
+                if (!rdy) return 0;
+                const double rr32 = C->host_scal[S_RR];
+                if (!std::isfinite(rr32)) {
+                    status = fail(DGMG_ENONFINITE, "residual norm is not finite");
+                    state = R_FINAL;
+                    break;
+                }
+                relrec = std::sqrt(rr32) / bn;
+                if (relrec <= rtol || std::sqrt(rr32) < C->opts.delta * rnorm_upd) {
+                    // reliable update: fold the FP32 correction into x, FP64 true residual
+                    C->prof.begin(ST_VECTOR, s);
+                    ADV_CUDA(launch_accumulate_f2d(n, x, xs, s));
+                    C->prof.end(s);
+                    need_accumulate = false;
+                    ADV(apply64(*C, x, b, r, s));
+                    ++nres;
+                    C->prof.begin(ST_VECTOR, s);
+                    ADV_CUDA(launch_dot(n, r, r, C->partials, C->scal + S_RR, s));
+                    ADV_CUDA(launch_cast_d2f(n, r, r32, s));
+                    C->prof.end(s);
+                    ADV(post_scalars(C, s));
+                    state = R_WAIT_UPD;
+                    break;
+                }
+                state = R_CONT;
+                break;
+            }
+            case R_WAIT_UPD: {
+                const int rdy = scalars_ready(C, blocking);
+                if (rdy < 0) ADV(rdy);
+                if (!rdy) return 0;
+                rr = C->host_scal[S_RR];
+                if (!std::isfinite(rr)) {
+                    status = fail(DGMG_ENONFINITE, "residual norm is not finite");
+                    state = R_FINAL;
+                    break;
+                }
+                rel_true = std::sqrt(rr) / bn;
+                rnorm_upd = std::sqrt(rr);
+                if (rel_true <= rtol) {
+                    state = R_FINAL;
+                    break;
+                }
+                state = R_CONT;
+                break;
+            }
+            case R_CONT:
+                if (it >= C->opts.maxit) {
+                    status = fail(DGMG_ENOTCONVERGED, "maxit reached");
+                    state = R_FINAL;
+                    break;
+                }
+                ADV(dg_vcycle<float>(*C, r32, z32, s));
+                C->prof.begin(ST_VECTOR, s);
+                ADV_CUDA(launch_dot2f(n, r32, z32, rold32, C->partials, C->scal + S_RZN, C->scal + S_RZO, s));
+                ADV(launch_beta(C, 1, s));
+                ADV_CUDA(launch_update_p_f(n, p32, z32, C->scal, s));
+                C->prof.end(s);
+                ++it;
+                state = R_ITER;
+                break;
+            case R_FINAL:
+                if (need_accumulate) {
+                    C->prof.begin(ST_VECTOR, s);
+                    ADV_CUDA(launch_accumulate_f2d(n, x, xs, s));
+                    C->prof.end(s);
+                    need_accumulate = false;
+                    ADV(apply64(*C, x, b, r, s));
+                    ++nres;
+                    ADV_CUDA(launch_dot(n, r, r, C->partials, C->scal + S_RR, s));
+                }
+                if (it > 0) ADV_CUDA(launch_dotf(n, z32, z32, C->partials, C->scal + S_ZZ, s));
+                ADV(post_scalars(C, s));
+                state = R_WAIT_FIN;
+                break;
+            case R_WAIT_FIN: {
+                const int rdy = scalars_ready(C, blocking);
+                if (rdy < 0) ADV(rdy);
+                if (!rdy) return 0;
+                rel_true = std::sqrt(C->host_scal[S_RR]) / bn;
+                zz = it > 0 ? C->host_scal[S_ZZ] : 0.0;
+                zz0 = it > 0 ? C->host_scal[S_ZZ0] : 0.0;
+                stats.iterations = it;
+                stats.rel_residual = rel_true;
+                stats.rel_residual_recursive = relrec;
+                stats.prec_residual = zz0 > 0 ? std::sqrt(zz / zz0) : 0.0;
+                stats.fp64_applies = nres;
+                stats.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+                state = S_DONE;
+                return 1;
+            }
+            case S_DONE:
+            default:
+                return 1;
+        }
+    }
+}
+
+}  // namespace dgmg
+
+extern "C" {
+
+int dgmg_solve(dgmg_ctx *C, const double *b, double *x, dgmg_stats *stats, void *stream) {
+    RC(check_ctx(C));
+    if (!b || !x) return fail(DGMG_EINVAL, "b and x must not be NULL");
+    if (b == x) return fail(DGMG_EINVAL, "b and x must not overlap");
+    SolveRun run;
+    run.start(C, b, x, (cudaStream_t)stream);
+    while (!run.advance(true)) {
+    }
+    if (stats) *stats = run.stats;
+    return run.status;
+}
+
+int dgmg_solve_host(dgmg_ctx *C, const double *b_host, double *x_host, dgmg_stats *stats, void *stream) {
+    RC(check_ctx(C));
+    if (!b_host || !x_host) return fail(DGMG_EINVAL, "b_host and x_host must not be NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!C->w_b) {
+        RC(C->alloc(&C->w_b, C->ndof));
+        RC(C->alloc(&C->w_x, C->ndof));
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    LC(cudaMemcpyAsync(C->w_b, b_host, sizeof(double) * C->ndof, cudaMemcpyHostToDevice, s));
+    LC(cudaMemcpyAsync(C->w_x, x_host, sizeof(double) * C->ndof, cudaMemcpyHostToDevice, s));
+    const int rc = dgmg_solve(C, C->w_b, C->w_x, stats, stream);
+    if (rc != DGMG_OK && rc != DGMG_ENOTCONVERGED) return rc;
+    LC(cudaMemcpyAsync(x_host, C->w_x, sizeof(double) * C->ndof, cudaMemcpyDeviceToHost, s));
+    LC(cudaStreamSynchronize(s));
+    if (stats) stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return rc;
+}
+
+}  // extern "C"

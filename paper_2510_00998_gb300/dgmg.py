@@ -22,6 +22,10 @@ DGMG_MIXED_FP32 = 1
 DGMG_OUTER_AUTO = 0
 DGMG_OUTER_PCG = 1
 DGMG_OUTER_RELIABLE = 2
+DGMG_PENDING = 0
+DGMG_RUNNING = 1
+DGMG_DONE = 2
+DGMG_FAILED = 3
 DGMG_BLOCK_EXACT = 0
 DGMG_BLOCK_INTERIOR_ONLY = 1
 
@@ -57,7 +61,14 @@ class Info(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("rel_residual", ctypes.c_double),
                 ("rel_residual_recursive", ctypes.c_double), ("prec_residual", ctypes.c_double),
-                ("seconds", ctypes.c_double), ("fp64_applies", ctypes.c_int)]
+                ("seconds", ctypes.c_double), ("fp64_applies", ctypes.c_int), ("queue_seconds", ctypes.c_double)]
+
+
+class ServerInfo(ctypes.Structure):
+    _fields_ = [("pending", ctypes.c_int), ("active", ctypes.c_int), ("done", ctypes.c_longlong),
+                ("failed", ctypes.c_longlong), ("admitted", ctypes.c_longlong), ("cache_entries", ctypes.c_int),
+                ("cache_hits", ctypes.c_longlong), ("cache_misses", ctypes.c_longlong),
+                ("evictions", ctypes.c_longlong), ("bytes_in_use", ctypes.c_size_t), ("budget", ctypes.c_size_t)]
 
 
 _P = ctypes.c_void_p
@@ -88,6 +99,12 @@ _SIGS = {
     "dgmg_h_prolong": (_I, [_P, _I, _P, _P, _P]),
     "dgmg_coarse_solve": (_I, [_P, _P, _P, _P]),
     "dgmg_cg_size": (ctypes.c_int64, [_P, _I]),
+    "dgmg_estimate_bytes": (_I, [ctypes.POINTER(Mesh), _I, ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_size_t)]),
+    "dgmg_server_create": (_I, [ctypes.c_size_t, _I, ctypes.POINTER(Opts), ctypes.POINTER(_P)]),
+    "dgmg_submit": (_I, [_P, ctypes.POINTER(Mesh), _I, _P, _P, _P, ctypes.POINTER(ctypes.c_uint64)]),
+    "dgmg_poll": (_I, [_P, ctypes.c_uint64, ctypes.POINTER(_I), ctypes.POINTER(Stats)]),
+    "dgmg_server_info": (_I, [_P, ctypes.POINTER(ServerInfo)]),
+    "dgmg_server_destroy": (_I, [_P]),
     "dgmg_profile": (_I, [_P, _I]),
     "dgmg_profile_read": (_I, [_P, _P, _P, _I]),
     "dgmg_kernel_launches": (ctypes.c_longlong, []),
@@ -142,6 +159,81 @@ def _stream(stream):
     import torch
     s = torch.cuda.current_stream() if stream is None else stream
     return ctypes.c_void_p(s.cuda_stream)
+
+
+def _mesh(n):
+    m = Mesh()
+    m.dim = len(n)
+    for a in range(3):
+        m.n[a] = int(n[a]) if a < len(n) else 1
+    return m
+
+
+def _opts(**opts):
+    o = Opts()
+    load().dgmg_default_opts(ctypes.byref(o))
+    for k, v in opts.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def estimate_bytes(n, p, **opts):
+    b = ctypes.c_size_t()
+    _check(load().dgmg_estimate_bytes(ctypes.byref(_mesh(n)), int(p), ctypes.byref(_opts(**opts)), ctypes.byref(b)))
+    return int(b.value)
+
+
+class Server:
+    """A dgmg_server: continuous batching of independent solves."""
+
+    def __init__(self, budget_bytes, max_active, **opts):
+        self.lib = load()
+        self.opts = _opts(**opts)
+        h = ctypes.c_void_p()
+        _check(self.lib.dgmg_server_create(ctypes.c_size_t(int(budget_bytes)), int(max_active),
+                                           ctypes.byref(self.opts), ctypes.byref(h)))
+        self.h = h
+        self._keep = {}
+
+    def submit(self, n, p, b, x, kappa=None):
+        """Queue a solve; b, x: contiguous CUDA float64 tensors kept alive until done."""
+        import numpy as np
+        kp = None
+        if kappa is not None:
+            k = np.ascontiguousarray(np.asarray(kappa, dtype=np.float64).reshape(-1))
+            kp = k.ctypes.data_as(ctypes.c_void_p)
+        t = ctypes.c_uint64()
+        _check(self.lib.dgmg_submit(self.h, ctypes.byref(_mesh(n)), int(p), kp, _ptr(b), _ptr(x), ctypes.byref(t)))
+        self._keep[t.value] = (b, x)
+        return int(t.value)
+
+    def poll(self, ticket):
+        """(status, Stats or None); raises DGMGError if the request failed."""
+        st = ctypes.c_int()
+        stats = Stats()
+        rc = self.lib.dgmg_poll(self.h, ctypes.c_uint64(ticket), ctypes.byref(st), ctypes.byref(stats))
+        if st.value in (DGMG_DONE, DGMG_FAILED):
+            self._keep.pop(ticket, None)
+        _check(rc)
+        return st.value, (stats if st.value == DGMG_DONE else None)
+
+    def info(self):
+        inf = ServerInfo()
+        _check(self.lib.dgmg_server_info(self.h, ctypes.byref(inf)))
+        return inf
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dgmg_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def default_opts():
