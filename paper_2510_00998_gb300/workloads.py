@@ -10,6 +10,12 @@ Workloads (every input seeded and synthetic):
   3d64_p4_mixed  3D unit cube, 64^3 cells, p = 4, kappa_K = exp(N(0,1)) from
                  numpy default_rng(3), f as above, FP32 V-cycle in FP64 CG
   3d64_p4_fp64   the same problem with the FP64 V-cycle
+  batch          256 independent 3D solves (n in [8,24], p in 2..4, lognormal
+                 kappa, 8 random Fourier modes, default_rng(4)) through the
+                 solve server vs plain FP64 one-at-a-time
+  serve          Poisson arrivals (default_rng(5)) of requests with n in [8,48],
+                 p in 2..5, kappa in {1, lognormal, two-phase 1/100}, at
+                 multiples of the FP64 one-at-a-time capacity; p50/p99 latency
 """
 import argparse
 import json
@@ -87,11 +93,211 @@ def run(name, solves=3, warmup=1):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("name", choices=sorted(WORKLOADS))
+    ap.add_argument("name", choices=sorted(WORKLOADS) + ["batch", "serve"])
     ap.add_argument("--solves", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=1)
+    ap.add_argument("--count", type=int, default=0)
+    ap.add_argument("--max-active", type=int, default=0)
     a = ap.parse_args()
-    print(json.dumps(run(a.name, a.solves, a.warmup)))
+    if a.name == "batch":
+        kw = {}
+        if a.count:
+            kw["count"] = a.count
+        if a.max_active:
+            kw["max_active"] = a.max_active
+        print(json.dumps(run_batch(**kw)))
+    elif a.name == "serve":
+        kw = {}
+        if a.count:
+            kw["count"] = a.count
+        if a.max_active:
+            kw["max_active"] = a.max_active
+        print(json.dumps(run_serve(**kw)))
+    else:
+        print(json.dumps(run(a.name, a.solves, a.warmup)))
+
+
+
+# ------------------------------------------------------------------ many solves
+def fourier_rhs_values(X, coeffs, waves):
+    """f = sum_m a_m prod_i sin(k_{m,i} pi x_i) at points X (torch, [npts, d])."""
+    import torch
+    f = torch.zeros(X.shape[0], dtype=torch.float64, device=X.device)
+    for a, k in zip(coeffs, waves):
+        term = torch.full_like(f, float(a))
+        for i in range(X.shape[1]):
+            term = term * torch.sin(float(k[i]) * math.pi * X[:, i])
+        f += term
+    return f
+
+
+def two_phase_kappa(n, rng):
+    """kappa in {1, 100}: 100 on the side of a random plane through the cube."""
+    d = len(n)
+    normal = rng.normal(size=d)
+    normal /= np.linalg.norm(normal)
+    centres = [(np.arange(v) + 0.5) / v for v in n]
+    grids = np.meshgrid(*centres[::-1], indexing="ij")[::-1]      # x fastest when flattened
+    s = sum(normal[a] * (grids[a] - 0.5) for a in range(d)) + rng.uniform(-0.2, 0.2)
+    return np.where(s.reshape(-1) > 0, 100.0, 1.0)
+
+
+def request_stream(kind, count, seed):
+    """Seeded problem list. kind 'batch': n in [8,24], p in {2,3,4}, lognormal kappa,
+    8 random Fourier modes; kind 'serve': n in [8,48], p in 2..5, kappa one of
+    {1, lognormal, two-phase 1/100}, same RHS family."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        if kind == "batch":
+            nn = int(rng.integers(8, 25))
+            p = int(rng.integers(2, 5))
+            kk = "lognormal"
+        else:
+            nn = int(rng.integers(8, 49))
+            p = int(rng.integers(2, 6))
+            kk = ["one", "lognormal", "two-phase"][int(rng.integers(0, 3))]
+        n = (nn, nn, nn)
+        ncell = nn ** 3
+        if kk == "one":
+            kappa = None
+        elif kk == "lognormal":
+            kappa = np.exp(rng.normal(size=ncell))
+        else:
+            kappa = two_phase_kappa(n, rng)
+        coeffs = rng.normal(size=8)
+        waves = rng.integers(1, 5, size=(8, 3))
+        out.append(dict(n=n, p=p, kappa=kappa, kappa_kind=kk, coeffs=coeffs, waves=waves))
+    return out
+
+
+def build_rhs(reqs, device="cuda"):
+    """b for every request, through the library's quadrature (one kappa = 1
+    context per distinct mesh and degree, freed afterwards)."""
+    import torch
+    from . import dgmg
+    cache = {}
+    for r in reqs:
+        key = (r["n"], r["p"])
+        if key not in cache:
+            ctx = dgmg.Context(r["n"], r["p"])
+            mq = r["p"] + 2
+            xq = torch.empty(int(ctx.info.ncell) * mq ** 3 * 3, dtype=torch.float64, device=device)
+            ctx.quad_points(xq)
+            cache[key] = (ctx, xq.view(-1, 3))
+        ctx, X = cache[key]
+        b = torch.empty(ctx.ndof, dtype=torch.float64, device=device)
+        ctx.load_vector(fourier_rhs_values(X, r["coeffs"], r["waves"]).contiguous(), b)
+        r["b"] = b
+    torch.cuda.synchronize()
+    for ctx, _ in cache.values():
+        ctx.close()
+
+
+def one_at_a_time(reqs, precision=0):
+    """Solve every request alone in order (create, solve, destroy); returns the
+    per-request service times in seconds (set-up included)."""
+    import torch
+    from . import dgmg
+    times = []
+    for r in reqs:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        ctx = dgmg.Context(r["n"], r["p"], r["kappa"], precision=precision)
+        x = torch.zeros_like(r["b"])
+        st, _ = ctx.solve(r["b"], x)
+        ctx.close()
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t)
+        assert st.rel_residual <= 1e-10, st.rel_residual
+    return times
+
+
+def fifo_latencies(arrivals, service):
+    """Latencies of a one-at-a-time FIFO server with the given service times."""
+    t, out = 0.0, []
+    for a, s in zip(arrivals, service):
+        t = max(t, a) + s
+        out.append(t - a)
+    return out
+
+
+def serve_trace(reqs, arrivals, budget, max_active, precision=1):
+    """Submit each request at its arrival time to a server; returns
+    (latencies, makespan, stats list)."""
+    import torch
+    from . import dgmg
+    srv = dgmg.Server(budget, max_active, precision=precision)
+    xs = [torch.zeros_like(r["b"]) for r in reqs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tickets, sub_t = [None] * len(reqs), [0.0] * len(reqs)
+    done = {}
+    k = 0
+    while len(done) < len(reqs):
+        now = time.perf_counter() - t0
+        while k < len(reqs) and arrivals[k] <= now:
+            r = reqs[k]
+            tickets[k] = srv.submit(r["n"], r["p"], r["b"], xs[k], r["kappa"])
+            sub_t[k] = arrivals[k]
+            k += 1
+        for i in range(k):
+            if i in done:
+                continue
+            st, stats = srv.poll(tickets[i])
+            if st == dgmg.DGMG_DONE:
+                done[i] = (time.perf_counter() - t0, stats)
+        time.sleep(0.0002)
+    makespan = time.perf_counter() - t0
+    lat = [done[i][0] - sub_t[i] for i in range(len(reqs))]
+    stats = [done[i][1] for i in range(len(reqs))]
+    info = srv.info()
+    srv.close()
+    return lat, makespan, stats, info
+
+
+def pct(v, q):
+    return float(np.percentile(np.asarray(v), q))
+
+
+def run_batch(count=256, seed=4, max_active=32, budget_gb=64):
+    """All requests submitted at once to a mixed-precision server vs plain FP64
+    one-at-a-time. solves/s for both (set-up included in both)."""
+    reqs = request_stream("batch", count, seed)
+    build_rhs(reqs)
+    t_alone = one_at_a_time(reqs, precision=0)
+    lat, makespan, stats, info = serve_trace(reqs, [0.0] * count, budget_gb << 30, max_active)
+    return {"workload": f"batch of {count} 3D solves, n in [8,24], p in 2..4, lognormal kappa, Fourier RHS",
+            "fp64_one_at_a_time_solves_per_s": count / sum(t_alone),
+            "served_mixed_solves_per_s": count / makespan,
+            "served_p50_s": pct(lat, 50), "served_p99_s": pct(lat, 99),
+            "max_rel_residual": max(s.rel_residual for s in stats),
+            "cache_misses": info.cache_misses, "max_active": max_active}
+
+
+def run_serve(count=64, seed=5, rates=(0.25, 0.5, 1.0, 2.0, 4.0), max_active=16, budget_gb=96):
+    """Poisson arrivals at multiples of the plain FP64 one-at-a-time capacity."""
+    reqs = request_stream("serve", count, seed)
+    build_rhs(reqs)
+    service = one_at_a_time(reqs, precision=0)
+    capacity = len(service) / sum(service)
+    rng = np.random.default_rng(seed + 1000)
+    gaps = rng.exponential(size=count)
+    out = {"workload": f"{count} requests, n in [8,48], p in 2..5, kappa in {{1, lognormal, two-phase}}",
+           "fp64_capacity_solves_per_s": capacity, "rates": []}
+    for m in rates:
+        lam = m * capacity
+        arrivals = list(np.cumsum(gaps / lam))
+        fifo = fifo_latencies(arrivals, service)
+        lat, makespan, stats, info = serve_trace(reqs, arrivals, budget_gb << 30, max_active)
+        out["rates"].append({"rate_x_capacity": m, "rate_per_s": lam,
+                             "served": {"solves_per_s": count / makespan, "p50_s": pct(lat, 50),
+                                        "p99_s": pct(lat, 99)},
+                             "fp64_one_at_a_time": {
+                                 "solves_per_s": count / max(a + l for a, l in zip(arrivals, fifo)),
+                                 "p50_s": pct(fifo, 50), "p99_s": pct(fifo, 99)},
+                             "max_rel_residual": max(s.rel_residual for s in stats)})
+    return out
 
 
 if __name__ == "__main__":
