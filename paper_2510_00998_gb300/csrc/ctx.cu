@@ -705,6 +705,12 @@ int dgmg_create(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_op
     if (o.outer == DGMG_OUTER_AUTO) o.outer = o.precision == DGMG_MIXED_FP32 ? DGMG_OUTER_RELIABLE : DGMG_OUTER_PCG;
 
     std::unique_ptr<dgmg_ctx> C(new dgmg_ctx());
+    {
+        cudaError_t e = cudaStreamCreateWithFlags(&C->setup_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+        e = cudaStreamCreateWithFlags(&C->capture_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+    }
     C->dim = mesh->dim;
     C->p = p;
     C->q = p + 1;
@@ -793,7 +799,7 @@ int dgmg_create(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_op
         RC(C->upload(&C->quad_V, V));
         RC(C->upload(&C->quad_w, W));
     }
-    DG_CUDA(cudaDeviceSynchronize());
+    DG_CUDA(cudaStreamSynchronize(C->setup_stream));   // uploads done before any use
     *out = C.release();
     return DGMG_OK;
 }

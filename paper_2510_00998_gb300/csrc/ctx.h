@@ -124,12 +124,26 @@ struct dgmg_ctx {
     size_t bytes = 0;
     StageProfiler prof;
     cudaEvent_t ev = nullptr;                     // completion of the scalars copied to host_scal
+    cudaStream_t setup_stream = nullptr;          // allocations, uploads and frees of this ctx
+    // CUDA graphs of the CG iteration chunks (captured on capture_stream at the
+    // second use, replayed with one launch; not used while profiling)
+    struct Graph {
+        cudaGraphExec_t exec = nullptr;
+        const void *key = nullptr;                // user pointer the captured work depends on
+        long long kernels = 0;                    // kernels inside (for the launch counter)
+        int uses = 0;
+    };
+    Graph g_iter, g_body;
+    cudaStream_t capture_stream = nullptr;
+    bool use_graphs = true;
 
     template <typename T>
     int alloc(T **ptr, size_t count) {
         *ptr = nullptr;
         if (count == 0) count = 1;
-        cudaError_t e = cudaMalloc((void **)ptr, count * sizeof(T));
+        // stream-ordered allocation on the context's own stream: no device-wide
+        // synchronisation with solves running on other streams
+        cudaError_t e = cudaMallocAsync((void **)ptr, count * sizeof(T), setup_stream);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return fail(DGMG_ENOMEM, std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) +
@@ -143,11 +157,19 @@ struct dgmg_ctx {
     int upload(T **ptr, const std::vector<T> &h) {
         int rc = alloc(ptr, h.size());
         if (rc) return rc;
-        if (!h.empty()) DG_CUDA(cudaMemcpy(*ptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+        if (!h.empty())
+            DG_CUDA(cudaMemcpyAsync(*ptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, setup_stream));
         return DGMG_OK;
     }
     ~dgmg_ctx() {
-        for (void *p : allocs) cudaFree(p);
+        for (Graph *g : {&g_iter, &g_body})
+            if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (capture_stream) cudaStreamDestroy(capture_stream);
+        for (void *p : allocs) cudaFreeAsync(p, setup_stream);
+        if (setup_stream) {
+            cudaStreamSynchronize(setup_stream);
+            cudaStreamDestroy(setup_stream);
+        }
         if (host_scal) cudaFreeHost(host_scal);
         if (ev) cudaEventDestroy(ev);
     }
@@ -199,6 +221,8 @@ struct SolveRun {
     dgmg_stats stats{};
     void start(dgmg_ctx *ctx, const double *b_, double *x_, cudaStream_t s_);
     int advance(bool blocking);
+    int pcg_chunk(bool update_dir, cudaStream_t st);
+    int reliable_chunk(bool update_dir, cudaStream_t st);
 };
 
 }  // namespace dgmg

@@ -90,9 +90,80 @@ struct dgmg_server {
     uint64_t next_id = 1, tick = 0;
     std::vector<cudaStream_t> streams;
     std::vector<bool> slot_busy;
+    std::deque<std::pair<Request *, size_t>> to_setup;   // admitted, hierarchy not built yet (bytes reserved)
+    int setting_up = 0;
     bool stop = false;
     long long n_done = 0, n_failed = 0, hits = 0, misses = 0, admitted = 0, evictions = 0;
     std::thread worker;
+    std::vector<std::thread> setup_workers;
+
+    int take_slot() {
+        int slot = 0;
+        while (slot_busy[slot]) ++slot;
+        slot_busy[slot] = true;
+        return slot;
+    }
+
+    void activate(Request *r, CacheEntry *e) {
+        e->busy = true;
+        r->entry = e;
+        r->t_admit = Clock::now();
+        r->status = DGMG_RUNNING;
+        r->run.start(e->ctx, r->b, r->x, streams[r->slot]);
+        active.push_back(r);
+        ++admitted;
+    }
+
+    // Builds hierarchies for admitted requests off the scheduler thread, so
+    // running solves keep being advanced meanwhile.
+    void setup_loop() {
+        cudaSetDevice(device);
+        std::unique_lock<std::mutex> lk(mu);
+        for (;;) {
+            cv.wait(lk, [&] { return stop_setup || !to_setup.empty(); });
+            if (to_setup.empty()) {
+                if (stop_setup) return;
+                continue;
+            }
+            Request *r = to_setup.front().first;
+            const size_t reserved = to_setup.front().second;
+            to_setup.pop_front();
+            const double *kp = r->has_kappa ? r->kappa.data() : nullptr;
+            lk.unlock();
+            dgmg_ctx *ctx = nullptr;
+            const int rc = dgmg_create(&r->mesh, r->p, kp, &opts, &ctx);
+            const std::string err = rc == DGMG_OK ? "" : dgmg_last_error();
+            size_t actual = 0;
+            if (rc == DGMG_OK) {
+                dgmg_info_t inf;
+                dgmg_info(ctx, &inf);
+                actual = inf.device_bytes;
+            }
+            lk.lock();
+            --setting_up;
+            bytes -= reserved;
+            if (rc != DGMG_OK) {
+                slot_busy[r->slot] = false;
+                finish(r, DGMG_FAILED, rc, err);
+            } else {
+                cache.emplace_back();
+                CacheEntry *e = &cache.back();
+                e->mesh = r->mesh;
+                e->p = r->p;
+                e->has_kappa = r->has_kappa;
+                e->khash = r->khash;
+                e->kappa = r->kappa;
+                e->ctx = ctx;
+                e->bytes = actual;
+                bytes += actual;
+                r->kappa.clear();
+                r->kappa.shrink_to_fit();
+                activate(r, e);
+            }
+            cv.notify_all();
+        }
+    }
+    bool stop_setup = false;
 
     void finish(Request *r, int status, int rc, const std::string &err) {
         r->status = status;
@@ -107,8 +178,11 @@ struct dgmg_server {
     }
 
     // Admit queued requests while slots and memory allow (scheduler thread only).
-    void admit(std::unique_lock<std::mutex> &lk) {
-        while (!pending.empty() && (int)active.size() < max_active) {
+    // A resident hierarchy of the same problem is reused at once; otherwise the
+    // bytes are reserved (evicting least recently used idle hierarchies as
+    // needed) and the build is handed to the set-up workers.
+    void admit() {
+        while (!pending.empty() && (int)active.size() + setting_up < max_active) {
             Request *r = pending.front();
             CacheEntry *e = nullptr;
             for (auto &c : cache)
@@ -118,78 +192,56 @@ struct dgmg_server {
                 }
             if (e) {
                 ++hits;
-            } else {
-                size_t est = 0;
-                if (dgmg_estimate_bytes(&r->mesh, r->p, &opts, &est) != DGMG_OK) {
-                    pending.pop_front();
-                    finish(r, DGMG_FAILED, DGMG_EINVAL, dgmg_last_error());
-                    continue;
-                }
-                if (est > budget) {
-                    pending.pop_front();
-                    finish(r, DGMG_FAILED, DGMG_EBUDGET,
-                           "request needs " + std::to_string(est) + " bytes, budget " + std::to_string(budget));
-                    continue;
-                }
-                while (bytes + est > budget) {   // evict least recently used idle hierarchies
-                    auto victim = cache.end();
-                    for (auto it = cache.begin(); it != cache.end(); ++it)
-                        if (!it->busy && (victim == cache.end() || it->last_use < victim->last_use)) victim = it;
-                    if (victim == cache.end()) break;
-                    bytes -= victim->bytes;
-                    dgmg_destroy(victim->ctx);
-                    cache.erase(victim);
-                    ++evictions;
-                }
-                if (bytes + est > budget) return;   // wait for running solves to release memory
-                ++misses;
-                const double *kp = r->has_kappa ? r->kappa.data() : nullptr;
-                dgmg_ctx *ctx = nullptr;
-                lk.unlock();
-                const int rc = dgmg_create(&r->mesh, r->p, kp, &opts, &ctx);
-                const std::string err = rc == DGMG_OK ? "" : dgmg_last_error();
-                lk.lock();
-                if (rc != DGMG_OK) {
-                    pending.pop_front();
-                    finish(r, DGMG_FAILED, rc, err);
-                    continue;
-                }
-                cache.emplace_back();
-                e = &cache.back();
-                e->mesh = r->mesh;
-                e->p = r->p;
-                e->has_kappa = r->has_kappa;
-                e->khash = r->khash;
-                e->kappa = r->kappa;
-                e->ctx = ctx;
-                dgmg_info_t inf;
-                dgmg_info(ctx, &inf);
-                e->bytes = inf.device_bytes;
-                bytes += e->bytes;
+                pending.pop_front();
+                r->slot = take_slot();
+                r->kappa.clear();
+                r->kappa.shrink_to_fit();
+                activate(r, e);
+                continue;
             }
+            size_t est = 0;
+            if (dgmg_estimate_bytes(&r->mesh, r->p, &opts, &est) != DGMG_OK) {
+                pending.pop_front();
+                finish(r, DGMG_FAILED, DGMG_EINVAL, dgmg_last_error());
+                continue;
+            }
+            if (est > budget) {
+                pending.pop_front();
+                finish(r, DGMG_FAILED, DGMG_EBUDGET,
+                       "request needs " + std::to_string(est) + " bytes, budget " + std::to_string(budget));
+                continue;
+            }
+            while (bytes + est > budget) {   // evict least recently used idle hierarchies
+                auto victim = cache.end();
+                for (auto it = cache.begin(); it != cache.end(); ++it)
+                    if (!it->busy && (victim == cache.end() || it->last_use < victim->last_use)) victim = it;
+                if (victim == cache.end()) break;
+                bytes -= victim->bytes;
+                destroy_idle(victim->ctx);
+                cache.erase(victim);
+                ++evictions;
+            }
+            if (bytes + est > budget) return;   // wait for running solves to release memory
+            ++misses;
             pending.pop_front();
-            e->busy = true;
-            int slot = 0;
-            while (slot_busy[slot]) ++slot;
-            slot_busy[slot] = true;
-            r->entry = e;
-            r->slot = slot;
-            r->t_admit = Clock::now();
-            r->status = DGMG_RUNNING;
-            r->kappa.clear();
-            r->kappa.shrink_to_fit();
-            r->run.start(e->ctx, r->b, r->x, streams[slot]);
-            active.push_back(r);
-            ++admitted;
+            bytes += est;
+            r->slot = take_slot();
+            ++setting_up;
+            to_setup.emplace_back(r, est);
+            cv.notify_all();
         }
     }
+
+    // An idle hierarchy: its last solve has completed (the run's final event),
+    // so it is freed without a device-wide synchronisation.
+    static void destroy_idle(dgmg_ctx *ctx) { delete ctx; }
 
     void loop() {
         cudaSetDevice(device);
         std::unique_lock<std::mutex> lk(mu);
         for (;;) {
-            if (stop && active.empty() && pending.empty()) break;
-            admit(lk);
+            if (stop && active.empty() && pending.empty() && setting_up == 0) break;
+            admit();
             std::vector<Request *> work = active;
             lk.unlock();
             std::vector<Request *> finished;
@@ -241,6 +293,7 @@ int dgmg_server_create(size_t hbm_budget_bytes, int max_active, const dgmg_opts 
     }
     dgmg_server *raw = S.get();
     S->worker = std::thread([raw]() { raw->loop(); });
+    for (int i = 0; i < 2; ++i) S->setup_workers.emplace_back([raw]() { raw->setup_loop(); });
     *out = S.release();
     return DGMG_OK;
 }
@@ -316,7 +369,13 @@ int dgmg_server_destroy(dgmg_server *S) {
         S->cv.notify_all();
     }
     if (S->worker.joinable()) S->worker.join();
-    for (auto &c : S->cache) dgmg_destroy(c.ctx);
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop_setup = true;
+        S->cv.notify_all();
+    }
+    for (auto &w : S->setup_workers) w.join();
+    for (auto &c : S->cache) dgmg_server::destroy_idle(c.ctx);
     for (cudaStream_t s : S->streams) cudaStreamDestroy(s);
     delete S;
     return DGMG_OK;

@@ -36,9 +36,51 @@ int launch_beta(dgmg_ctx *C, int flexible, cudaStream_t s) {
 }
 
 // queue the copy of the whole scalar block to pinned host memory + the event
-int post_scalars(dgmg_ctx *C, cudaStream_t s) {
+int copy_scalars(dgmg_ctx *C, cudaStream_t s) {
     LC(cudaMemcpyAsync(C->host_scal, C->scal, sizeof(double) * S_NSCAL, cudaMemcpyDeviceToHost, s));
+    return DGMG_OK;
+}
+
+int post_scalars(dgmg_ctx *C, cudaStream_t s) {
+    RC(copy_scalars(C, s));
     LC(cudaEventRecord(C->ev, s));
+    return DGMG_OK;
+}
+
+// Queue the work of `enqueue(stream)` on s. With graphs enabled (and profiling
+// off) the work is captured once into a CUDA graph at its second use and then
+// replayed with a single launch; `key` is the user pointer the work depends
+// on (a different key re-captures).
+template <typename F>
+int run_chunk(dgmg_ctx *C, dgmg_ctx::Graph &g, const void *key, cudaStream_t s, F enqueue) {
+    if (!C->use_graphs || C->prof.on || g.uses++ == 0) return enqueue(s);
+    if (!g.exec || g.key != key) {
+        if (g.exec) {
+            cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+        }
+        const long long before = g_kernel_launches.load();
+        LC(cudaStreamBeginCapture(C->capture_stream, cudaStreamCaptureModeRelaxed));
+        const int rc = enqueue(C->capture_stream);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(C->capture_stream, &graph);
+        g.kernels = g_kernel_launches.load() - before;
+        g_kernel_launches.fetch_sub(g.kernels);   // capturing launched nothing
+        if (rc != DGMG_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            g.exec = nullptr;
+            return cuda_fail(ei, "cudaGraphInstantiate");
+        }
+        g.key = key;
+    }
+    LC(cudaGraphLaunch(g.exec, s));
+    count_launches((int)g.kernels);
     return DGMG_OK;
 }
 
@@ -108,12 +150,61 @@ void SolveRun::start(dgmg_ctx *ctx, const double *b_, double *x_, cudaStream_t s
         if (e_ != cudaSuccess) ADV(cuda_fail(e_, #x));      \
     } while (0)
 
+// One PCG iteration's device work: (when `update_dir`) z = V(r), beta, p = z + beta p;
+// then q = A p, alpha, x += alpha p, r -= alpha q, ||r||^2, scalars to the host.
+int SolveRun::pcg_chunk(bool update_dir, cudaStream_t st) {
+    const int64_t n = C->ndof;
+    const bool flexible = C->opts.precision == DGMG_MIXED_FP32;
+    double *r = C->w_r, *z = C->w_z, *p = C->w_p, *q = C->w_q, *rold = C->w_rold;
+    if (update_dir) {
+        RC(vcycle64(*C, r, z, st));
+        C->prof.begin(ST_VECTOR, st);
+        if (flexible)
+            LC(launch_dot2(n, r, z, rold, C->partials, C->scal + S_RZN, C->scal + S_RZO, st));
+        else
+            LC(launch_dot(n, r, z, C->partials, C->scal + S_RZN, st));
+        RC(launch_beta(C, flexible ? 1 : 0, st));
+        LC(launch_pcg_update_p(n, p, z, C->scal, st));
+        C->prof.end(st);
+    }
+    RC(apply64(*C, p, nullptr, q, st));                         // q = A p
+    C->prof.begin(ST_VECTOR, st);
+    LC(launch_dot(n, p, q, C->partials, C->scal + S_PQ, st));
+    if (flexible) LC(cudaMemcpyAsync(rold, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    LC(launch_pcg_update_xr(n, x, r, p, q, C->scal, st));      // alpha = rz / pq
+    LC(launch_dot(n, r, r, C->partials, C->scal + S_RR, st));
+    C->prof.end(st);
+    return copy_scalars(C, st);
+}
+
+// One reliable-update CG iteration's FP32 work: (when `update_dir`) z = V(r),
+// beta, p = z + beta p; then q = A p, alpha, xs += alpha p, r -= alpha q,
+// ||r||^2, scalars to the host.
+int SolveRun::reliable_chunk(bool update_dir, cudaStream_t st) {
+    const int64_t n = C->ndof;
+    float *r32 = C->r32, *z32 = C->z32, *p32 = C->p32, *q32 = C->q32, *xs = C->xs32, *rold32 = C->rold32;
+    if (update_dir) {
+        RC(dg_vcycle<float>(*C, r32, z32, st));
+        C->prof.begin(ST_VECTOR, st);
+        LC(launch_dot2f(n, r32, z32, rold32, C->partials, C->scal + S_RZN, C->scal + S_RZO, st));
+        RC(launch_beta(C, 1, st));
+        LC(launch_update_p_f(n, p32, z32, C->scal, st));
+        C->prof.end(st);
+    }
+    RC(apply32(*C, p32, q32, st));
+    C->prof.begin(ST_VECTOR, st);
+    LC(launch_dotf(n, p32, q32, C->partials, C->scal + S_PQ, st));
+    LC(launch_update_xr_f(n, xs, r32, rold32, p32, q32, C->scal, st));
+    LC(launch_dotf(n, r32, r32, C->partials, C->scal + S_RR, st));
+    C->prof.end(st);
+    return copy_scalars(C, st);
+}
+
 int SolveRun::advance(bool blocking) {
     const int64_t n = C->ndof;
     const double rtol = C->opts.rtol;
-    const bool flexible = C->opts.precision == DGMG_MIXED_FP32;
-    double *r = C->w_r, *z = C->w_z, *p = C->w_p, *q = C->w_q, *rold = C->w_rold;
-    float *r32 = C->r32, *z32 = C->z32, *p32 = C->p32, *q32 = C->q32, *xs = C->xs32, *rold32 = C->rold32;
+    double *r = C->w_r, *z = C->w_z, *p = C->w_p;
+    float *r32 = C->r32, *z32 = C->z32, *p32 = C->p32, *xs = C->xs32;
     for (;;) {
         switch (state) {
             // ------------------------------------------------ FP64 PCG
@@ -148,14 +239,10 @@ int SolveRun::advance(bool blocking) {
                 break;
             }
             case P_ITER:
-                ADV(apply64(*C, p, nullptr, q, s));    // q = A p
-                C->prof.begin(ST_VECTOR, s);
-                ADV_CUDA(launch_dot(n, p, q, C->partials, C->scal + S_PQ, s));
-                if (flexible) ADV_CUDA(cudaMemcpyAsync(rold, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-                ADV_CUDA(launch_pcg_update_xr(n, x, r, p, q, C->scal, s));   // alpha = rz / pq
-                ADV_CUDA(launch_dot(n, r, r, C->partials, C->scal + S_RR, s));
-                C->prof.end(s);
-                ADV(post_scalars(C, s));
+                ADV(run_chunk(C, it == 1 ? C->g_iter : C->g_body, x, s, [&](cudaStream_t st) -> int {
+                    return pcg_chunk(it > 1, st);
+                }));
+                ADV_CUDA(cudaEventRecord(C->ev, s));
                 state = P_WAIT_RR;
                 break;
             case P_WAIT_RR: {
@@ -178,16 +265,7 @@ int SolveRun::advance(bool blocking) {
                     state = P_FINAL;
                     break;
                 }
-                ADV(vcycle64(*C, r, z, s));
-                C->prof.begin(ST_VECTOR, s);
-                if (flexible)
-                    ADV_CUDA(launch_dot2(n, r, z, rold, C->partials, C->scal + S_RZN, C->scal + S_RZO, s));
-                else
-                    ADV_CUDA(launch_dot(n, r, z, C->partials, C->scal + S_RZN, s));
-                ADV(launch_beta(C, flexible ? 1 : 0, s));
-                ADV_CUDA(launch_pcg_update_p(n, p, z, C->scal, s));
-                C->prof.end(s);
-                ++it;
+                ++it;                                  // next chunk starts with V-cycle and direction update
                 state = P_ITER;
                 break;
             }
@@ -254,14 +332,11 @@ int SolveRun::advance(bool blocking) {
                 break;
             }
             case R_ITER:
-                ADV(apply32(*C, p32, q32, s));
-                C->prof.begin(ST_VECTOR, s);
-                ADV_CUDA(launch_dotf(n, p32, q32, C->partials, C->scal + S_PQ, s));
-                ADV_CUDA(launch_update_xr_f(n, xs, r32, rold32, p32, q32, C->scal, s));
-                ADV_CUDA(launch_dotf(n, r32, r32, C->partials, C->scal + S_RR, s));
-                C->prof.end(s);
+                ADV(run_chunk(C, it == 1 ? C->g_iter : C->g_body, nullptr, s, [&](cudaStream_t st) -> int {
+                    return reliable_chunk(it > 1, st);
+                }));
+                ADV_CUDA(cudaEventRecord(C->ev, s));
                 need_accumulate = true;
-                ADV(post_scalars(C, s));
                 state = R_WAIT_RR;
                 break;
             case R_WAIT_RR: {
@@ -319,13 +394,7 @@ int SolveRun::advance(bool blocking) {
                     state = R_FINAL;
                     break;
                 }
-                ADV(dg_vcycle<float>(*C, r32, z32, s));
-                C->prof.begin(ST_VECTOR, s);
-                ADV_CUDA(launch_dot2f(n, r32, z32, rold32, C->partials, C->scal + S_RZN, C->scal + S_RZO, s));
-                ADV(launch_beta(C, 1, s));
-                ADV_CUDA(launch_update_p_f(n, p32, z32, C->scal, s));
-                C->prof.end(s);
-                ++it;
+                ++it;                                  // next chunk starts with V-cycle and direction update
                 state = R_ITER;
                 break;
             case R_FINAL:
@@ -388,6 +457,7 @@ int dgmg_solve_host(dgmg_ctx *C, const double *b_host, double *x_host, dgmg_stat
     if (!C->w_b) {
         RC(C->alloc(&C->w_b, C->ndof));
         RC(C->alloc(&C->w_x, C->ndof));
+        LC(cudaStreamSynchronize(C->setup_stream));
     }
     const auto t0 = std::chrono::steady_clock::now();
     LC(cudaMemcpyAsync(C->w_b, b_host, sizeof(double) * C->ndof, cudaMemcpyHostToDevice, s));
