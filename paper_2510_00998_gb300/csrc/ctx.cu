@@ -4,6 +4,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -31,12 +32,28 @@ int cuda_fail(cudaError_t e, const char *what) {
     return DGMG_ECUDA;
 }
 
+// ------------------------------------------------------------ set-up trace
+// With the environment variable DGMG_TRACE_SETUP set, dgmg_create prints the
+// wall time of each set-up phase to stderr.
+struct SetupTrace {
+    bool on = std::getenv("DGMG_TRACE_SETUP") != nullptr;
+    std::chrono::steady_clock::time_point t = std::chrono::steady_clock::now();
+    void mark(const char *what) {
+        if (!on) return;
+        const auto now = std::chrono::steady_clock::now();
+        std::fprintf(stderr, "dgmg setup %-14s %8.3f ms\n", what,
+                     std::chrono::duration<double, std::milli>(now - t).count());
+        t = now;
+    }
+};
+
 // ---------------------------------------------------------- host threading
 template <typename F>
 static void parallel_for(int64_t n, F f) {
     unsigned nt = std::thread::hardware_concurrency();
-    nt = std::max(1u, std::min(nt, 64u));
-    if (n < 4096 || nt == 1) {
+    // about 2048 items per thread: thread start-up costs tens of microseconds
+    nt = (unsigned)std::max<int64_t>(1, std::min<int64_t>({(int64_t)nt, 64, n / 2048}));
+    if (nt == 1) {
         for (int64_t i = 0; i < n; ++i) f(i);
         return;
     }
@@ -731,7 +748,9 @@ int dgmg_create(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_op
             kap[i] = kappa[i];
         }
     }
+    SetupTrace trace;
     C->re = make_refelem(p);
+    trace.mark("refelem");
 
     // Q1 hierarchy
     C->lv.emplace_back();
@@ -751,12 +770,17 @@ int dgmg_create(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_op
         build_coarse(C->dim, F, Cl);
         C->lv.push_back(std::move(Cl));
     }
+    trace.mark("q1 levels");
     RC(coarse_inverse(*C));
+    trace.mark("coarse inverse");
 
     std::vector<double> fd;
     fast_diag_factors(*C, kap, fd);
+    trace.mark("fast-diag");
     RC(setup_dg<double>(*C, C->d64, kap, fd));
+    trace.mark("dg upload");
     RC(setup_cg<double>(*C, C->cg64));
+    trace.mark("cg upload");
     if (o.precision == DGMG_MIXED_FP32) {
         RC(setup_dg<float>(*C, C->d32, kap, fd));
         RC(setup_cg<float>(*C, C->cg32));
@@ -799,7 +823,9 @@ int dgmg_create(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_op
         RC(C->upload(&C->quad_V, V));
         RC(C->upload(&C->quad_w, W));
     }
+    trace.mark("rest");
     DG_CUDA(cudaStreamSynchronize(C->setup_stream));   // uploads done before any use
+    trace.mark("sync");
     *out = C.release();
     return DGMG_OK;
 }

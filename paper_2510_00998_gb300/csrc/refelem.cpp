@@ -157,11 +157,17 @@ static void jacobi_eig(int n, double *A, double *V, double *lam) {
                 tot += A[i * n + j] * A[i * n + j];
                 if (i != j) off += A[i * n + j] * A[i * n + j];
             }
-        if (off <= 1e-34 * tot) break;
+        // converged once the off-diagonal part is at the rounding level
+        if (off <= 1e-30 * tot) break;
+        int rotations = 0;
         for (int p = 0; p < n - 1; ++p)
             for (int r = p + 1; r < n; ++r) {
                 const double apr = A[p * n + r];
-                if (std::fabs(apr) < 1e-300) continue;
+                // an element negligible against its diagonal pair is left alone
+                if (std::fabs(apr) <= 1e-18 * std::sqrt(std::fabs(A[p * n + p] * A[r * n + r])) ||
+                    std::fabs(apr) < 1e-300)
+                    continue;
+                ++rotations;
                 const double theta = (A[r * n + r] - A[p * n + p]) / (2.0 * apr);
                 const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
                 const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
@@ -181,6 +187,7 @@ static void jacobi_eig(int n, double *A, double *V, double *lam) {
                     V[k * n + r] = s * vkp + c * vkr;
                 }
             }
+        if (rotations == 0) break;
     }
     for (int i = 0; i < n; ++i) lam[i] = A[i * n + i];
 }

@@ -293,7 +293,7 @@ int dgmg_server_create(size_t hbm_budget_bytes, int max_active, const dgmg_opts 
     }
     dgmg_server *raw = S.get();
     S->worker = std::thread([raw]() { raw->loop(); });
-    for (int i = 0; i < 2; ++i) S->setup_workers.emplace_back([raw]() { raw->setup_loop(); });
+    for (int i = 0; i < 6; ++i) S->setup_workers.emplace_back([raw]() { raw->setup_loop(); });
     *out = S.release();
     return DGMG_OK;
 }
