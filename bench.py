@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     return ap.parse_args()
 
 
@@ -197,6 +198,36 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- serving
+SERVE_REQUESTS = 24
+SERVE_RATE = 2.0      # arrival rate as a multiple of the FP64 one-at-a-time capacity
+
+
+def serving_run():
+    """Solves/s and p50/p99 latency (arrival to completion, rel. residual 1e-10)
+    of the mixed-precision solve server against plain FP64 one-at-a-time solving,
+    for Poisson arrivals of requests with n in [8,48]^3 cells, p in 2..5 and
+    kappa in {1, lognormal, two-phase} at SERVE_RATE x the FP64 capacity."""
+    import numpy as np
+    from paper_2510_00998_gb300 import workloads as wl
+    reqs = wl.request_stream("serve", SERVE_REQUESTS, 5)
+    wl.build_rhs(reqs)
+    service = wl.one_at_a_time(reqs, precision=0)
+    capacity = len(service) / sum(service)
+    gaps = np.random.default_rng(1005).exponential(size=len(reqs))
+    arrivals = list(np.cumsum(gaps / (SERVE_RATE * capacity)))
+    fifo = wl.fifo_latencies(arrivals, service)
+    lat, makespan, stats, info = wl.serve_trace(reqs, arrivals, 96 << 30, 16)
+    return {"requests": len(reqs), "rate_per_s": SERVE_RATE * capacity,
+            "rate_x_fp64_capacity": SERVE_RATE,
+            "served_mixed": {"solves_per_s": len(reqs) / makespan, "p50_s": wl.pct(lat, 50),
+                             "p99_s": wl.pct(lat, 99), "max_rel_residual": max(s.rel_residual for s in stats)},
+            "fp64_one_at_a_time": {"solves_per_s": len(reqs) / max(a + l for a, l in zip(arrivals, fifo)),
+                                   "p50_s": wl.pct(fifo, 50), "p99_s": wl.pct(fifo, 99)},
+            "workload": "Poisson arrivals, n in [8,48]^3, p in 2..5, kappa in {1, lognormal, two-phase 1/100}, "
+                        "8 random Fourier modes (seeds 5, 1005)"}
+
+
 # ---------------------------------------------------------------- GPU arm
 def run_gb300(args):
     import numpy as np
@@ -283,6 +314,10 @@ def run_gb300(args):
             e2e_units += float(ndof) * st.iterations * (ctx.opts.nu_pre + ctx.opts.nu_post)
     e2e_t, e2e_u = reduce_max_sum((e2e_ms, e2e_units), world, dev)
 
+    serving = None
+    if rank == 0 and not args.no_serving:
+        serving = serving_run()
+
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
@@ -312,6 +347,7 @@ def run_gb300(args):
             "solves_per_s": args.steps / (t_max * 1e-3),
             "iterations": statistics.median(iters), "rel_residual_max": max(relres),
             "smoothing_steps": smooth_steps_total, "stage_share": shares,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
