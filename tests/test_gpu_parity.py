@@ -285,3 +285,54 @@ def test_nonfinite_rhs_reported(dgmg):
     with pytest.raises(dgmg.DGMGError) as ei:
         ctx.solve(b, x)
     assert ei.value.code == dgmg.DGMG_ENONFINITE
+
+
+@pytest.mark.parametrize("n,p", [((2, 2), 1), ((2, 2), 6), ((2, 3), 3), ((2, 2, 2), 1), ((2, 2, 2), 4),
+                                 ((2, 3, 2), 6)])
+def test_minimum_meshes_and_degree_extremes(dgmg, n, p):
+    """Smallest meshes (two cells per axis, one Q1 unknown per axis) and the
+    lowest and highest supported degrees: apply, smoothing, V-cycle, solve."""
+    kap = _kappa(n, "lognormal", 9)
+    mesh = sipg.Mesh(n, p)
+    ctx = dgmg.Context(n, p, kap)
+    rng = np.random.default_rng(14)
+    u, b = rng.normal(size=mesh.ndof), rng.normal(size=mesh.ndof)
+    y = torch.empty(mesh.ndof, dtype=torch.float64, device=DEV)
+    ctx.apply(_t(u), y)
+    assert _rel(_np(y), sipg.apply(mesh, u, kap)) <= 1e-12
+    ut = _t(u)
+    ctx.smooth(ut, _t(b), 2)
+    ref, _ = sipg.BlockJacobi(mesh, kap).step_alg4(u, b, 0.8, 2)
+    assert _rel(_np(ut), ref) <= 1e-11
+    hier = hpmg.Hierarchy(mesh, kap)
+    e = torch.empty_like(y)
+    ctx.vcycle(_t(b), e)
+    assert _rel(_np(e), hier.vcycle(b)) <= 1e-11
+    x = torch.zeros_like(y)
+    st, _ = ctx.solve(_t(b), x)
+    assert st.rel_residual <= 1e-10
+
+
+def test_zero_rhs_returns_zero(dgmg):
+    ctx = dgmg.Context((4, 5, 3), 2)
+    b = torch.zeros(ctx.ndof, dtype=torch.float64, device=DEV)
+    x = torch.zeros_like(b)
+    st, _ = ctx.solve(b, x)
+    assert st.iterations == 0 and float(x.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_maxit_exhaustion_reports_not_converged(dgmg, prec):
+    """maxit reached: DGMG_ENOTCONVERGED, x holds a finite last iterate whose
+    residual is below the initial one."""
+    n, p = (8, 8, 8), 3
+    ctx = dgmg.Context(n, p, _kappa(n, "lognormal", 2), precision=prec, maxit=3)
+    b = torch.tensor(np.random.default_rng(15).normal(size=ctx.ndof), device=DEV)
+    x = torch.zeros_like(b)
+    with pytest.raises(dgmg.DGMGError) as ei:
+        ctx.solve(b, x)
+    assert ei.value.code == dgmg.DGMG_ENOTCONVERGED
+    assert bool(torch.isfinite(x).all())
+    r = torch.empty_like(b)
+    ctx.residual(x, b, r)
+    assert float(r.norm()) < float(b.norm())
