@@ -350,6 +350,15 @@ int dgmg_profile_read(dgmg_ctx *ctx, double *ms, long long *launches, int nstage
 /* Number of CUDA kernels this library has launched in this process. */
 long long dgmg_kernel_launches(void);
 
+/* Bounded device-side waits (mbarrier phases of the bulk copies in the FP32
+ * smoothing kernel) that ran out of iterations on the CURRENT device since the
+ * library was loaded; 0 in every healthy run. A kernel whose wait runs out
+ * abandons its cells for that launch (their u and traces keep the old values),
+ * so a nonzero count means the results of that run are not to be trusted.
+ * Synchronous (reads device memory); *count (HOST) receives the number.
+ * Returns DGMG_EINVAL for a NULL pointer, DGMG_ECUDA if the read fails. */
+int dgmg_wait_timeouts(unsigned long long *count);
+
 #ifdef __cplusplus
 }
 #endif

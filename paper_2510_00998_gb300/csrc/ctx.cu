@@ -1091,6 +1091,16 @@ int dgmg_profile_read(dgmg_ctx *C, double *ms, long long *launches, int nstage) 
 
 long long dgmg_kernel_launches(void) { return g_kernel_launches.load(); }
 
+int dgmg_wait_timeouts(unsigned long long *count) {
+    if (!count) return fail(DGMG_EINVAL, "dgmg_wait_timeouts: count is NULL");
+    unsigned long long a = 0, b = 0;
+    cudaError_t e = wait_timeouts_fp32(&a);
+    if (e == cudaSuccess) e = wait_timeouts_fp64(&b);
+    if (e != cudaSuccess) return cuda_fail(e, "dgmg_wait_timeouts");
+    *count = a + b;
+    return DGMG_OK;
+}
+
 }  // extern "C"
 
 

@@ -24,4 +24,6 @@ cudaError_t launch_residual<float>(int dim, int q, const DGConst<float> &c, int 
     return launch_residual_impl<float>(dim, q, c, cpb, mode, u, b, kappa, tr, r, corners, s);
 }
 
+cudaError_t wait_timeouts_fp32(unsigned long long *count) { return read_wait_timeouts(count); }
+
 }  // namespace dgmg

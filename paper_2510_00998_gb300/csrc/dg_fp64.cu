@@ -24,4 +24,6 @@ cudaError_t launch_residual<double>(int dim, int q, const DGConst<double> &c, in
     return launch_residual_impl<double>(dim, q, c, cpb, mode, u, b, kappa, tr, r, corners, s);
 }
 
+cudaError_t wait_timeouts_fp64(unsigned long long *count) { return read_wait_timeouts(count); }
+
 }  // namespace dgmg

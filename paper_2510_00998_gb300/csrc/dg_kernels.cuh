@@ -16,6 +16,7 @@
 // 1 = high end), comp 0 = value u, comp 1 = derivative along +axis.
 #pragma once
 
+#include <algorithm>
 #include <type_traits>
 
 #include "internal.h"
@@ -712,6 +713,13 @@ __global__ void __launch_bounds__(256) k_residual(DGConst<T> c, int cpb, int mod
     }
 }
 
+
+}  // namespace dgmg
+
+#include "smooth_cells.cuh"
+
+namespace dgmg {
+
 // Shared-memory bytes per CTA of each kernel.
 template <int DIM, int Q, typename T>
 constexpr size_t smem_project(int cpb) {
@@ -748,6 +756,13 @@ struct DGLaunch {
     }
     static cudaError_t smooth(const DGConst<T> &c, int cpb, int exact, T *u, const T *b, const T *kappa,
                               const T *fd, const T *linv, const T *tri, T *tro, cudaStream_t s) {
+        if constexpr (std::is_same<T, float>::value && DIM == 3 && Q <= 5) {
+            // bulk copies want 16-byte aligned vectors and factors, cp.async 8-byte aligned traces
+            const bool aligned = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(b) |
+                                   reinterpret_cast<uintptr_t>(fd)) & 15) == 0 &&
+                                 ((reinterpret_cast<uintptr_t>(tri) | reinterpret_cast<uintptr_t>(tro)) & 7) == 0;
+            if (exact && aligned) return smooth_cells(c, u, b, kappa, fd, tri, tro, s);
+        }
         const size_t sm = smem_smooth<DIM, Q, T>(cpb, exact != 0);
         static bool attr = false;
         if (!attr) {
@@ -759,6 +774,25 @@ struct DGLaunch {
         count_launches(1);
         k_smooth<DIM, Q, T><<<(unsigned)grid, cpb * G::NF, sm, s>>>(c, cpb, exact, u, b, kappa, fd, linv, tri, tro);
         return cudaGetLastError();
+    }
+    // FP32 3D exact-block smoothing step with one thread per cell (k_smooth_cells)
+    static cudaError_t smooth_cells(const DGConst<T> &c, T *u, const T *b, const T *kappa, const T *fd,
+                                    const T *tri, T *tro, cudaStream_t s) {
+        if constexpr (std::is_same<T, float>::value && DIM == 3 && Q <= 5) {
+            using CG = CellGeo<Q>;
+            static bool attr = false;
+            if (!attr) {
+                cudaFuncSetAttribute(k_smooth_cells<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CG::BYTES);
+                attr = true;
+            }
+            const int64_t grid = (c.ncell + CG::W - 1) / CG::W;
+            if (grid == 0) return cudaSuccess;
+            count_launches(1);
+            k_smooth_cells<Q><<<(unsigned)grid, CG::W, CG::BYTES, s>>>(c, u, b, kappa, fd, tri, tro);
+            return cudaGetLastError();
+        } else {
+            return cudaErrorInvalidValue;
+        }
     }
     static cudaError_t residual(const DGConst<T> &c, int cpb, int mode, const T *u, const T *b, const T *kappa,
                                 const T *tr, T *r, T *corners, cudaStream_t s) {

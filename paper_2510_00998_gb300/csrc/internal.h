@@ -29,6 +29,9 @@ int cuda_fail(cudaError_t e, const char *what);
 // Process-wide count of kernels launched by the library (dgmg_kernel_launches).
 extern std::atomic<long long> g_kernel_launches;
 inline void count_launches(int k) { g_kernel_launches.fetch_add(k, std::memory_order_relaxed); }
+// Bounded waits that ran out in the kernels of the float / double translation unit.
+cudaError_t wait_timeouts_fp32(unsigned long long *count);
+cudaError_t wait_timeouts_fp64(unsigned long long *count);
 
 // ------------------------------------------------------- reference element
 // 1D GLL Lagrange element of degree p on [-1,1] (paper Sec. 2.2), computed

@@ -1,0 +1,493 @@
+// FP32 single-touch smoothing step (Algorithm 4, exact diagonal blocks) with one
+// thread per cell, for 3D and q <= 5 nodes per axis.
+//
+// Each thread keeps its whole cell (q^3 values) in registers, so the six
+// tensor passes of the fast-diagonalisation inverse need no transposes through
+// shared memory. A CTA is one warp serving 32 consecutive cells. Its inputs are
+// staged in shared memory in the order they are consumed:
+//   - b and the fast-diagonalisation factors: one bulk (TMA) copy each,
+//     completing on an mbarrier;
+//   - the neighbours' traces, face by face through two slots, with cp.async
+//     (8-byte pieces: a face of one cell is 2 q^2 floats, which is not a
+//     multiple of 16 bytes for odd q);
+//   - u of the previous iterate: a bulk copy into b's buffer once b is read,
+//     overlapping the facet work.
+// The new u leaves through a bulk store; the new traces through the face slots
+// with coalesced stores. A lane reads its own cell with stride q^3 (odd for odd
+// q, so a warp's 32 loads hit 32 banks).
+//
+// The split update of the exact block (u <- (1 - w) u + w A_KK^{-1}(b - N u_nb))
+// needs only the neighbours' traces and b before the inverse, so u itself is
+// read once, at the end.
+#pragma once
+
+#include <cstdint>
+
+namespace dgmg {
+
+// Waits in the kernels below that gave up (an mbarrier phase that did not
+// complete within the iteration limit). Zero in every healthy run.
+static __device__ unsigned long long g_wait_timeouts;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile(
+        "{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(smem_addr(bar)),
+        "r"(bytes)
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// Bounded wait on phase `parity`; false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity) {
+    for (int it = 0; it < (1 << 20); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void bulk_store(void *dst, const void *src, unsigned bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst), "r"(smem_addr(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+
+// Lane 0 waits for `bar`; the verdict is shared with the warp. A wait that runs
+// out is counted, then waited for once more (the copies must land before the
+// CTA's shared memory is released).
+__device__ __forceinline__ bool warp_wait_copies(uint64_t *bar, int lane) {
+    int ok = 1;
+    if (lane == 0) {
+        if (!mbar_wait_bounded(bar, 0)) {
+            atomicAdd(&g_wait_timeouts, 1ull);
+            mbar_wait_bounded(bar, 0);
+            ok = 0;
+        }
+    }
+    __syncwarp();
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+template <int Q>
+struct CellGeo {
+    static constexpr int NL = Q * Q * Q, NF = Q * Q, TR = 12 * NF, FDS = Q * Q + Q;
+    static constexpr int W = 32;                       // cells per CTA (one per lane)
+    // shared memory (floats), per cell: area A holds b, then the factors, then
+    // the new u; area B holds two neighbour-face slots, then the previous u, then
+    // two faces of new traces
+    static constexpr int PA = NL > 3 * FDS ? NL : 3 * FDS;
+    static constexpr int PB = NL > 4 * NF ? NL : 4 * NF;
+    static constexpr size_t OFF_B = (size_t)W * PA;
+    static constexpr size_t OFF_K = OFF_B + (size_t)W * PB;   // kF [6][W]
+    static constexpr size_t OFF_NB = OFF_K + 6 * W;          // neighbour cell [6][W] (int)
+    static constexpr size_t BYTES = (OFF_NB + 6 * W) * sizeof(float);
+};
+
+// Stage face f of the neighbours of the CTA's cells (their face f^1) into a slot.
+template <int Q>
+__device__ __forceinline__ void stage_face(int f, int ncl, int lane, const int *sNb, const float *__restrict__ tr,
+                                           float *slot) {
+    using G = CellGeo<Q>;
+    constexpr int PIECES = G::NF;                      // 8-byte pieces per face of one cell
+    for (int idx = lane; idx < ncl * PIECES; idx += G::W) {
+        const int j = idx / PIECES, part = idx - j * PIECES;
+        const int nb = sNb[f * G::W + j];
+        if (nb >= 0)
+            cp_async8(slot + j * 2 * G::NF + 2 * part, tr + (int64_t)nb * G::TR + (f ^ 1) * 2 * G::NF + 2 * part);
+    }
+    cp_async_commit();
+}
+
+// The cell tensor R[x + q y + q^2 z] is kept in registers and only ever worked
+// on along its first index; the other axes are brought there by rotating the
+// tensor (one code path for all three axes, which keeps the kernel small
+// enough for the instruction cache).
+// rotate: new (x, y, z) = old (y, z, x).
+template <int Q>
+__device__ __forceinline__ void rotate(float *R) {
+    float T[Q * Q * Q];
+#pragma unroll
+    for (int e = 0; e < Q * Q * Q; ++e) T[e] = R[e];
+#pragma unroll
+    for (int k = 0; k < Q; ++k)
+#pragma unroll
+        for (int j = 0; j < Q; ++j)
+#pragma unroll
+            for (int i = 0; i < Q; ++i) R[j + Q * k + Q * Q * i] = T[i + Q * j + Q * Q * k];
+}
+// rotate_back: new (x, y, z) = old (z, x, y).
+template <int Q>
+__device__ __forceinline__ void rotate_back(float *R) {
+    float T[Q * Q * Q];
+#pragma unroll
+    for (int e = 0; e < Q * Q * Q; ++e) T[e] = R[e];
+#pragma unroll
+    for (int k = 0; k < Q; ++k)
+#pragma unroll
+        for (int j = 0; j < Q; ++j)
+#pragma unroll
+            for (int i = 0; i < Q; ++i) R[k + Q * i + Q * Q * j] = T[i + Q * j + Q * Q * k];
+}
+
+// Load a q x q matrix (row-major, 8-byte aligned in shared memory) into
+// registers, transposed if asked.
+template <int Q, bool TRANSPOSE>
+__device__ __forceinline__ void load_matrix(const float *src, float *S) {
+    float v[Q * Q];
+#pragma unroll
+    for (int e = 0; e < (Q * Q) / 2; ++e) {
+        const float2 w = reinterpret_cast<const float2 *>(src)[e];
+        v[2 * e] = w.x;
+        v[2 * e + 1] = w.y;
+    }
+    if ((Q * Q) & 1) v[Q * Q - 1] = src[Q * Q - 1];
+#pragma unroll
+    for (int m = 0; m < Q; ++m)
+#pragma unroll
+        for (int n = 0; n < Q; ++n) S[m * Q + n] = TRANSPOSE ? v[n * Q + m] : v[m * Q + n];
+}
+
+// Along x: R[., a, b] <- A R[., a, b] for every pencil (A row-major q x q).
+template <int Q>
+__device__ __forceinline__ void pass_x(const float *A, float *R) {
+#pragma unroll
+    for (int t = 0; t < Q * Q; ++t) {
+        float x[Q];
+#pragma unroll
+        for (int n = 0; n < Q; ++n) x[n] = R[n + Q * t];
+#pragma unroll
+        for (int m = 0; m < Q; ++m) {
+            float s = 0.f;
+#pragma unroll
+            for (int n = 0; n < Q; ++n) s += A[m * Q + n] * x[n];
+            R[m + Q * t] = s;
+        }
+    }
+}
+
+// r -= N u_nb for the face normal to the current x axis on side `side`, whose
+// neighbour fields fld = [g | h] (q^2 each) are indexed sa * a + sb * b at the
+// current tangential position (a, b) = (y, z). With G, H the fields after the
+// tangential mass M_a (x) M_b (Ma, Mb: the 1D masses of the original axes now
+// at y and z):
+//   low face:  N = kF [e_0 (x) (H/2 - gamma G) - d_0 (x) G/2],
+//   high face: N = kF [e_p (x) (-H/2 - gamma G) + d_p (x) G/2].
+template <int Q>
+__device__ __forceinline__ void lift_x_face(int side, const float *fld, int sa, int sb, const float *Ma,
+                                            const float *Mb, const float *dv, float gam, float kF, float *R) {
+    constexpr int NF = Q * Q;
+    const float g2 = kF * gam, wv = 0.5f * kF, sgn = side ? -1.f : 1.f;
+    // value field: end layer += kF gamma G; all layers += sgn kF/2 G d
+    // derivative field: end layer -= sgn kF/2 H
+#pragma unroll
+    for (int comp = 0; comp < 2; ++comp) {
+        const float *f = fld + comp * NF;
+        float t1[NF];                                  // t1[a + q b] = sum_b' Mb[b][b'] f(a, b')
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            float col[Q];
+#pragma unroll
+            for (int bb = 0; bb < Q; ++bb) col[bb] = f[sa * a + sb * bb];
+#pragma unroll
+            for (int b = 0; b < Q; ++b) {
+                float s = 0.f;
+#pragma unroll
+                for (int bb = 0; bb < Q; ++bb) s += Mb[b * Q + bb] * col[bb];
+                t1[a + Q * b] = s;
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < Q; ++b)
+#pragma unroll
+            for (int a = 0; a < Q; ++a) {
+                float v = 0.f;
+#pragma unroll
+                for (int aa = 0; aa < Q; ++aa) v += Ma[a * Q + aa] * t1[aa + Q * b];
+                float *pen = R + Q * (a + Q * b);          // the pencil along x at (a, b)
+                if (comp == 0) {
+                    const float w = sgn * wv * v;
+                    if (side) pen[Q - 1] += g2 * v; else pen[0] += g2 * v;
+#pragma unroll
+                    for (int n = 0; n < Q; ++n) pen[n] += w * dv[n];
+                } else {
+                    if (side) pen[Q - 1] += wv * v; else pen[0] -= wv * v;
+                }
+            }
+    }
+}
+
+// Traces of the face normal to the current x axis on side `side` into dst
+// ([value q^2 | derivative q^2], indexed sa * a + sb * b).
+template <int Q>
+__device__ __forceinline__ void x_face_traces(int side, const float *R, const float *dv, int sa, int sb,
+                                              float *dst) {
+    constexpr int NF = Q * Q;
+#pragma unroll
+    for (int b = 0; b < Q; ++b)
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const float *pen = R + Q * (a + Q * b);
+            float d = 0.f;
+#pragma unroll
+            for (int n = 0; n < Q; ++n) d += dv[n] * pen[n];
+            dst[sa * a + sb * b] = side ? pen[Q - 1] : pen[0];
+            dst[NF + sa * a + sb * b] = d;
+        }
+}
+
+template <int Q>
+__global__ void __launch_bounds__(32) k_smooth_cells(const __grid_constant__ DGConst<float> c, float *__restrict__ u,
+                                                     const float *__restrict__ b, const float *__restrict__ kappa,
+                                                     const float *__restrict__ fd, const float *__restrict__ tr_in,
+                                                     float *__restrict__ tr_out) {
+    using G = CellGeo<Q>;
+    constexpr int W = G::W, NL = G::NL, NF = G::NF, FDS = G::FDS, TR = G::TR;
+    extern __shared__ __align__(128) float smem_f[];
+    float *sA = smem_f;                                  // b -> factors -> new u
+    float *sB = smem_f + G::OFF_B;                       // face slots -> previous u -> new traces
+    // face slot s (0, 1) of area B: sB + s * W * 2 NF
+    float *sK = smem_f + G::OFF_K;
+    int *sNb = reinterpret_cast<int *>(smem_f + G::OFF_NB);
+    __shared__ __align__(8) uint64_t bars[3];
+    __shared__ float sM[3][Q * Q];
+    const int lane = threadIdx.x;
+    const int64_t cell0 = (int64_t)blockIdx.x * W;
+    const int ncl = (int)min((int64_t)W, c.ncell - cell0);
+    const bool full = ncl == W;                          // bulk copies need whole 32-cell blocks
+    const bool active = lane < ncl;
+    const int64_t cell = cell0 + lane;
+
+    for (int e = lane; e < 3 * Q * Q; e += W) sM[e / (Q * Q)][e % (Q * Q)] = c.M[e / (Q * Q)][e % (Q * Q)];
+    if (full) {
+        if (lane == 0) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) mbar_init(&bars[i], 1);
+            fence_mbar_init();
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&bars[0], (unsigned)(W * NL * sizeof(float)));
+            bulk_load(sA, b + cell0 * NL, (unsigned)(W * NL * sizeof(float)), &bars[0]);
+        }
+    } else {
+        for (int e = lane; e < ncl * NL; e += W) sA[e] = b[cell0 * NL + e];
+    }
+    // neighbours and facet coefficients of this lane's cell
+    int mask = 0;
+    {
+        float kK = 1.f;
+        if (active) {
+            int ci[3];
+            cell_coords<3>(cell, c.n, ci);
+            mask = interior_mask<3>(ci, c.n);
+            kK = kappa[cell];
+        }
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            int nb = -1;
+            float kF = 0.f;
+            if (mask & (1 << f)) {
+                const int64_t s = axis_stride<3>(c.n, f >> 1);
+                nb = (int)((f & 1) ? cell + s : cell - s);
+                const float kN = kappa[nb];
+                kF = 2.f * kK * kN / (kK + kN);
+            }
+            sNb[f * W + lane] = nb;
+            sK[f * W + lane] = kF;
+        }
+    }
+    __syncwarp();
+    stage_face<Q>(0, ncl, lane, sNb, tr_in, sB);
+    stage_face<Q>(1, ncl, lane, sNb, tr_in, sB + W * 2 * NF);
+
+    // r = b
+    if (full) {
+        if (!warp_wait_copies(&bars[0], lane)) {
+            cp_async_wait<0>();
+            return;
+        }
+    } else {
+        __syncwarp();
+    }
+    float R[NL];
+#pragma unroll
+    for (int e = 0; e < NL; ++e) R[e] = active ? sA[lane * NL + e] : 0.f;
+    // the factors into the same area, behind the facet work
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (full) {
+        if (lane == 0) {
+            mbar_arrive_expect_tx(&bars[1], (unsigned)(W * 3 * FDS * sizeof(float)));
+            bulk_load(sA, fd + cell0 * 3 * FDS, (unsigned)(W * 3 * FDS * sizeof(float)), &bars[1]);
+        }
+    } else {
+        for (int e = lane; e < ncl * 3 * FDS; e += W) sA[e] = fd[cell0 * 3 * FDS + e];
+    }
+
+    // r -= N u_nb: the two faces normal to axis p, then rotate the next axis to x
+#pragma unroll 1
+    for (int p = 0; p < 3; ++p) {
+        float Ma[Q * Q], Mb[Q * Q], dv[Q];
+        const int ta = p == 2 ? 0 : p + 1, tb = p == 0 ? 2 : p - 1;
+        const int sa = p == 1 ? Q : 1, sb = p == 1 ? 1 : Q;   // the y faces are stored transposed
+#pragma unroll
+        for (int e = 0; e < Q * Q; ++e) {
+            Ma[e] = sM[ta][e];
+            Mb[e] = sM[tb][e];
+        }
+        const float gam = c.gamma[p];
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const int f = 2 * p + side;
+            if (f < 5)
+                cp_async_wait<1>();
+            else
+                cp_async_wait<0>();
+            __syncwarp();
+            if (active && (mask & (1 << f))) {
+#pragma unroll
+                for (int n = 0; n < Q; ++n) dv[n] = side ? c.dp[p][n] : c.d0[p][n];
+                lift_x_face<Q>(side, sB + side * W * 2 * NF + lane * 2 * NF, sa, sb, Ma, Mb, dv, gam, sK[f * W + lane], R);
+            }
+            __syncwarp();
+            if (f + 2 < 6) stage_face<Q>(f + 2, ncl, lane, sNb, tr_in, sB + side * W * 2 * NF);
+        }
+        rotate<Q>(R);
+    }
+    // the previous iterate into area B (the face slots are free now)
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (full) {
+        if (lane == 0) {
+            mbar_arrive_expect_tx(&bars[2], (unsigned)(W * NL * sizeof(float)));
+            bulk_load(sB, u + cell0 * NL, (unsigned)(W * NL * sizeof(float)), &bars[2]);
+        }
+    } else {
+        for (int e = lane; e < ncl * NL; e += W) sB[e] = u[cell0 * NL + e];
+    }
+
+    // A_KK^{-1} by fast diagonalisation: S^T along x, y, z; divide by the
+    // eigenvalue sums; S along z, y, x
+    if (full) {
+        if (!warp_wait_copies(&bars[1], lane)) {
+            warp_wait_copies(&bars[2], lane);
+            return;
+        }
+    } else {
+        __syncwarp();
+    }
+    const float *myFD = sA + lane * 3 * FDS;
+    if (active) {
+#pragma unroll 1
+        for (int p = 0; p < 3; ++p) {
+            float S[Q * Q];
+            load_matrix<Q, true>(myFD + p * FDS, S);
+            pass_x<Q>(S, R);
+            rotate<Q>(R);
+        }
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            const float lz = myFD[2 * FDS + Q * Q + k];
+#pragma unroll
+            for (int j = 0; j < Q; ++j) {
+                const float lyz = myFD[1 * FDS + Q * Q + j] + lz;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const int e = i + Q * (j + Q * k);
+                    R[e] = __fdividef(R[e], myFD[Q * Q + i] + lyz);
+                }
+            }
+        }
+#pragma unroll 1
+        for (int p = 2; p >= 0; --p) {
+            float S[Q * Q];
+            rotate_back<Q>(R);
+            load_matrix<Q, false>(myFD + p * FDS, S);
+            pass_x<Q>(S, R);
+        }
+    }
+
+    // u <- (1 - w) u + w y, stored through area A
+    if (full) {
+        if (!warp_wait_copies(&bars[2], lane)) return;
+    } else {
+        __syncwarp();
+    }
+    float *myU = sA + lane * NL;                        // overlaps other lanes' factors: after the barrier
+    if (active) {
+        const float om = c.omega, keep = 1.f - om;
+#pragma unroll
+        for (int e = 0; e < NL; ++e) R[e] = keep * sB[lane * NL + e] + om * R[e];
+#pragma unroll
+        for (int e = 0; e < NL; ++e) myU[e] = R[e];
+    }
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (full) {
+        if (lane == 0) {
+            bulk_store(u + cell0 * NL, sA, (unsigned)(W * NL * sizeof(float)));
+            bulk_commit();
+        }
+    } else {
+        for (int e = lane; e < ncl * NL; e += W) u[cell0 * NL + e] = sA[e];
+    }
+
+    // traces of the new iterate: the faces normal to axis p through area B, then
+    // rotate; copied out to tr[cell][face][2][q^2]
+#pragma unroll 1
+    for (int p = 0; p < 3; ++p) {
+        const int sa = p == 1 ? Q : 1, sb = p == 1 ? 1 : Q;
+        if (active) {
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                float dv[Q];
+#pragma unroll
+                for (int n = 0; n < Q; ++n) dv[n] = side ? c.dp[p][n] : c.d0[p][n];
+                x_face_traces<Q>(side, R, dv, sa, sb, sB + side * W * 2 * NF + lane * 2 * NF);
+            }
+        }
+        __syncwarp();
+        for (int idx = lane; idx < ncl * 2 * NF; idx += W) {   // 2 faces x [W][2 NF] -> [cell][face 2p + side]
+            const int side = idx / (ncl * NF), r = idx - side * (ncl * NF);
+            const int j = r / NF, part = r - j * NF;
+            const float2 v = reinterpret_cast<const float2 *>(sB + side * W * 2 * NF + j * 2 * NF)[part];
+            reinterpret_cast<float2 *>(tr_out + (cell0 + j) * TR + (2 * p + side) * 2 * NF)[part] = v;
+        }
+        __syncwarp();
+        rotate<Q>(R);
+    }
+    if (full && lane == 0) bulk_wait_read_all();
+}
+
+// Host-side read of the timeout counter of this translation unit.
+static inline cudaError_t read_wait_timeouts(unsigned long long *v) {
+    return cudaMemcpyFromSymbol(v, g_wait_timeouts, sizeof(*v));
+}
+
+}  // namespace dgmg

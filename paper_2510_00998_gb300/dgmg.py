@@ -108,6 +108,7 @@ _SIGS = {
     "dgmg_profile": (_I, [_P, _I]),
     "dgmg_profile_read": (_I, [_P, _P, _P, _I]),
     "dgmg_kernel_launches": (ctypes.c_longlong, []),
+    "dgmg_wait_timeouts": (_I, [ctypes.POINTER(ctypes.c_ulonglong)]),
 }
 
 STAGES = ("project", "smooth", "residual", "cg_levels", "vector")
@@ -116,6 +117,13 @@ STAGES = ("project", "smooth", "residual", "cg_levels", "vector")
 def kernel_launches():
     """Kernels launched by libdgmg in this process."""
     return int(load().dgmg_kernel_launches())
+
+
+def wait_timeouts():
+    """Device-side bounded waits that ran out on the current device (0 when healthy)."""
+    v = ctypes.c_ulonglong(0)
+    _check(load().dgmg_wait_timeouts(ctypes.byref(v)))
+    return int(v.value)
 
 _lib = None
 

@@ -192,7 +192,8 @@ def test_vcycle_fp64(dgmg, n, p, kind):
     assert _rel(_np(e), hier.vcycle(r)) <= 1e-11
 
 
-@pytest.mark.parametrize("n,p", [((16, 16), 2), ((6, 5, 7), 2), ((4, 4, 4), 4)])
+@pytest.mark.parametrize("n,p", [((16, 16), 2), ((6, 5, 7), 2), ((4, 4, 4), 4), ((5, 6, 7), 3), ((7, 6, 5), 4),
+                                 ((5, 4, 3), 1), ((4, 3, 5), 5), ((9, 8, 7), 4)])
 def test_vcycle_mixed_fp32(dgmg, n, p):
     """FP32 V-cycle: every stage in FP32 except the FP64 coarsest solve; bound on
     the relative max error derived from FP32 rounding through ~10 stages of
@@ -205,6 +206,7 @@ def test_vcycle_mixed_fp32(dgmg, n, p):
     e = torch.empty(mesh.ndof, dtype=torch.float64, device=DEV)
     ctx.vcycle(_t(r), e)
     assert _rel(_np(e), hier.vcycle(r)) <= 2e-5
+    assert dgmg.wait_timeouts() == 0
 
 
 @pytest.mark.parametrize("n,p,kind,prec,outer", [((16, 16), 2, "one", 0, 0), ((8, 8, 8), 2, "lognormal", 0, 0),
