@@ -242,7 +242,7 @@ def run_gb300(args):
     __graft_entry__.build()
     from paper_2510_00998_gb300 import dgmg
 
-    ctx = dgmg.Context(N_CELLS, DEGREE, rtol=RTOL)
+    ctx = dgmg.Context(N_CELLS, DEGREE, rtol=RTOL, autotune=1)
     ndof = ctx.ndof
     d, q = 3, DEGREE + 1
     # right-hand side b_i = (f, phi_i) from f at the library's quadrature points

@@ -86,6 +86,10 @@ typedef struct {
     int maxit;                    /* dgmg_solve iteration cap (default 200)            */
     int outer;                    /* DGMG_OUTER_* (default AUTO)                       */
     double delta;                 /* reliable-update factor, 0 < delta < 1 (0.1)       */
+    int autotune;                 /* 1: dgmg_create times the candidate tile shapes of */
+                                  /* the DG-level kernels on this mesh and keeps the   */
+                                  /* fastest (cached per mesh shape in the process);   */
+                                  /* 0 (default): fixed heuristic                      */
 } dgmg_opts;
 
 typedef struct {
@@ -99,6 +103,10 @@ typedef struct {
     int nu_pre, nu_post, precision, block_inverse, coarsening;
     size_t device_bytes;          /* device memory held by the ctx                     */
     int outer;                    /* DGMG_OUTER_PCG or DGMG_OUTER_RELIABLE in use      */
+    int tiles[6];                 /* cells per CTA of the DG-level kernels in use:     */
+                                  /* FP64 projection, smoothing, residual, then FP32   */
+                                  /* (mixed precision only, else 0); a smoothing entry */
+                                  /* of 0 = the one-thread-per-cell FP32 kernel        */
 } dgmg_info_t;
 
 typedef struct {
@@ -239,6 +247,11 @@ int dgmg_estimate_bytes(const dgmg_mesh *mesh, int p, const dgmg_opts *opts, siz
  * resident (busy or idle, reused for repeated problems, least recently used
  * idle ones evicted first) never exceed `hbm_budget_bytes`. opts (NULL =
  * defaults) apply to every request.
+ * The scheduler captures repeated CG iterations into CUDA graphs on its own
+ * streams. Meanwhile other threads of the process should synchronise streams
+ * or events, not the whole device: a device-wide synchronisation during a
+ * capture fails in the caller (cudaErrorStreamCaptureUnsupported); the server
+ * then finishes the affected solves without graphs, with the same results.
  */
 int dgmg_server_create(size_t hbm_budget_bytes, int max_active, const dgmg_opts *opts, dgmg_server **out);
 

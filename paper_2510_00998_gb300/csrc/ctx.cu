@@ -1,11 +1,13 @@
 // libdgmg context: hierarchy set-up on the host, device buffers, the stage
 // entry points, the hp V-cycle and the FP64 preconditioned CG solve.
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <thread>
@@ -604,14 +606,14 @@ int dg_vcycle(dgmg_ctx &C, const T *r, T *z, cudaStream_t s) {
     int cur = 0;
     for (int k = 0; k < C.opts.nu_pre; ++k) {
         C.prof.begin(ST_SMOOTH, s);
-        LC(launch_smooth<T>(C.dim, C.q, D.c, C.cpb, exact_block(C), z, r, D.kappa, D.fd, D.linv, D.tr[cur],
-                            D.tr[cur ^ 1], s));
+        LC(launch_smooth<T>(C.dim, C.q, D.c, C.tile_of<T>(TILE_SMOOTH), exact_block(C), z, r, D.kappa, D.fd,
+                            D.linv, D.tr[cur], D.tr[cur ^ 1], s));
         C.prof.end(s);
         cur ^= 1;
     }
     C.prof.begin(ST_RESIDUAL, s);
-    LC(launch_residual<T>(C.dim, C.q, D.c, C.cpb, RES_HAS_B | RES_CORNERS, z, r, D.kappa, D.tr[cur], nullptr,
-                          D.corners, s));
+    LC(launch_residual<T>(C.dim, C.q, D.c, C.tile_of<T>(TILE_RESIDUAL), RES_HAS_B | RES_CORNERS, z, r, D.kappa,
+                          D.tr[cur], nullptr, D.corners, s));
     C.prof.end(s);
     auto &lv = cgl<T>(C);
     C.prof.begin(ST_CG, s);
@@ -620,13 +622,13 @@ int dg_vcycle(dgmg_ctx &C, const T *r, T *z, cudaStream_t s) {
     RC(cg_vcycle<T>(C, 0, s, &e0));
     C.prof.end(s);
     C.prof.begin(ST_PROJECT, s);
-    LC(launch_project<T>(C.dim, C.q, D.c, C.cpb, z, e0, D.tr[0], s));   // z += P e0, projections
+    LC(launch_project<T>(C.dim, C.q, D.c, C.tile_of<T>(TILE_PROJECT), z, e0, D.tr[0], s));   // z += P e0
     C.prof.end(s);
     cur = 0;
     for (int k = 0; k < C.opts.nu_post; ++k) {
         C.prof.begin(ST_SMOOTH, s);
-        LC(launch_smooth<T>(C.dim, C.q, D.c, C.cpb, exact_block(C), z, r, D.kappa, D.fd, D.linv, D.tr[cur],
-                            D.tr[cur ^ 1], s));
+        LC(launch_smooth<T>(C.dim, C.q, D.c, C.tile_of<T>(TILE_SMOOTH), exact_block(C), z, r, D.kappa, D.fd,
+                            D.linv, D.tr[cur], D.tr[cur ^ 1], s));
         C.prof.end(s);
         cur ^= 1;
     }
@@ -651,12 +653,119 @@ int vcycle64(dgmg_ctx &C, const double *r, double *z, cudaStream_t s) {
 int apply64(dgmg_ctx &C, const double *u, const double *b, double *out, cudaStream_t s) {
     DGDev<double> &D = C.d64;
     C.prof.begin(ST_PROJECT, s);
-    LC(launch_project<double>(C.dim, C.q, D.c, C.cpb, const_cast<double *>(u), nullptr, D.tr[0], s));
+    LC(launch_project<double>(C.dim, C.q, D.c, C.tile[0][TILE_PROJECT], const_cast<double *>(u), nullptr, D.tr[0],
+                              s));
     C.prof.end(s);
     const int mode = b ? (RES_HAS_B | RES_WRITE_R) : (RES_WRITE_R | RES_NEGATE);
     C.prof.begin(ST_RESIDUAL, s);
-    LC(launch_residual<double>(C.dim, C.q, D.c, C.cpb, mode, u, b, D.kappa, D.tr[0], out, nullptr, s));
+    LC(launch_residual<double>(C.dim, C.q, D.c, C.tile[0][TILE_RESIDUAL], mode, u, b, D.kappa, D.tr[0], out,
+                               nullptr, s));
     C.prof.end(s);
+    return DGMG_OK;
+}
+
+// ------------------------------------------------------------ tile autotuner
+// For each DG-level kernel (projection, smoothing step, residual + restriction)
+// and each precision the ctx runs, time the candidate cells-per-CTA values on
+// the ctx's own buffers (one warm-up and three timed launches each, CUDA events
+// on the set-up stream) and keep the fastest; for the FP32 smoothing step the
+// one-thread-per-cell kernel (tile 0) competes with the pencil tiles. Results
+// are cached per (dimension, degree, mesh, precision, block inverse) for the
+// process, so a repeated shape is tuned once.
+struct TileKey {
+    int v[7];
+    bool operator<(const TileKey &o) const { return std::lexicographical_compare(v, v + 7, o.v, o.v + 7); }
+};
+static std::mutex g_tile_mu;
+static std::map<TileKey, std::array<int, 6>> g_tile_cache;
+
+template <typename T>
+static int tune_tiles(dgmg_ctx &C, T *u, T *b, int *tile, bool trace) {
+    DGDev<T> &D = dg<T>(C);
+    cudaStream_t s = C.setup_stream;
+    const int nf = (int)(C.nloc / C.q);
+    const int64_t trn = C.ncell * 2 * C.dim * 2 * nf;
+    std::vector<int> cand;
+    for (int c = 1; c <= 64; c *= 2)
+        if (c * nf >= 32 && c * nf <= 256) cand.push_back(c);
+    if (cand.empty()) cand.push_back(C.cpb);
+    DG_CUDA(cudaMemsetAsync(u, 0, sizeof(T) * C.ndof, s));
+    DG_CUDA(cudaMemsetAsync(b, 0, sizeof(T) * C.ndof, s));
+    DG_CUDA(cudaMemsetAsync(D.tr[0], 0, sizeof(T) * trn, s));
+    DG_CUDA(cudaMemsetAsync(D.tr[1], 0, sizeof(T) * trn, s));
+    cudaEvent_t e0, e1;
+    DG_CUDA(cudaEventCreate(&e0));
+    DG_CUDA(cudaEventCreate(&e1));
+    const float INF = 1e30f;
+    // milliseconds of three launches, INF if the shape cannot launch
+    auto time_it = [&](auto launch) -> float {
+        if (launch() != cudaSuccess) {
+            cudaGetLastError();
+            return INF;
+        }
+        cudaEventRecord(e0, s);
+        for (int k = 0; k < 3; ++k)
+            if (launch() != cudaSuccess) {
+                cudaGetLastError();
+                return INF;
+            }
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) return INF;
+        float ms = INF;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms;
+    };
+    const char *tname = sizeof(T) == 8 ? "fp64" : "fp32";
+    auto pick = [&](const char *stage, std::vector<int> cs, auto launch_with) {
+        int best = cs[0];
+        float best_ms = INF;
+        for (int c : cs) {
+            const float ms = time_it([&] { return launch_with(c); });
+            if (trace) std::fprintf(stderr, "dgmg autotune %s %-9s tile %2d: %8.4f ms\n", tname, stage, c, ms / 3);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+        return best;
+    };
+    tile[TILE_PROJECT] = pick("project", cand, [&](int c) {
+        return launch_project<T>(C.dim, C.q, D.c, c, u, nullptr, D.tr[0], s);
+    });
+    std::vector<int> cs = cand;
+    if (std::is_same<T, float>::value && C.dim == 3 && C.q <= 5 && exact_block(C)) cs.insert(cs.begin(), 0);
+    tile[TILE_SMOOTH] = pick("smooth", cs, [&](int c) {
+        return launch_smooth<T>(C.dim, C.q, D.c, c, exact_block(C), u, b, D.kappa, D.fd, D.linv, D.tr[0],
+                                D.tr[1], s);
+    });
+    tile[TILE_RESIDUAL] = pick("residual", cand, [&](int c) {
+        return launch_residual<T>(C.dim, C.q, D.c, c, RES_HAS_B | RES_CORNERS, u, b, D.kappa, D.tr[0], nullptr,
+                                  D.corners, s);
+    });
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    DG_CUDA(cudaStreamSynchronize(s));
+    return DGMG_OK;
+}
+
+static int autotune_tiles(dgmg_ctx &C) {
+    const bool mixed = C.opts.precision == DGMG_MIXED_FP32;
+    const TileKey key{{C.dim, C.q, C.n[0], C.n[1], C.n[2], C.opts.precision, C.opts.block_inverse}};
+    {
+        std::lock_guard<std::mutex> lk(g_tile_mu);
+        auto it = g_tile_cache.find(key);
+        if (it != g_tile_cache.end()) {
+            for (int k = 0; k < 6; ++k) C.tile[k / 3][k % 3] = it->second[k];
+            return DGMG_OK;
+        }
+    }
+    const bool trace = std::getenv("DGMG_TRACE_SETUP") != nullptr;
+    RC(tune_tiles<double>(C, C.w_z, C.w_r, C.tile[0], trace));
+    if (mixed) RC(tune_tiles<float>(C, C.z32, C.r32, C.tile[1], trace));
+    std::array<int, 6> v;
+    for (int k = 0; k < 6; ++k) v[k] = C.tile[k / 3][k % 3];
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    g_tile_cache[key] = v;
     return DGMG_OK;
 }
 
@@ -690,6 +799,7 @@ void dgmg_default_opts(dgmg_opts *o) {
     o->maxit = 200;
     o->outer = DGMG_OUTER_AUTO;
     o->delta = 0.1;
+    o->autotune = 0;
 }
 
 int dgmg_create(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_opts *opts, dgmg_ctx **out) {
@@ -739,6 +849,9 @@ int dgmg_create(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_op
     const int nf = (int)(C->nloc / C->q);
     C->cpb = std::max(1, 128 / nf);
     while (C->cpb * nf > 256) --C->cpb;
+    for (int k = 0; k < 2; ++k)
+        for (int st = 0; st < 3; ++st) C->tile[k][st] = C->cpb;
+    C->tile[1][TILE_SMOOTH] = 0;   // FP32: the one-thread-per-cell smoother where it applies
 
     std::vector<double> kap(C->ncell, 1.0);
     if (kappa) {
@@ -826,6 +939,10 @@ int dgmg_create(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_op
     trace.mark("rest");
     DG_CUDA(cudaStreamSynchronize(C->setup_stream));   // uploads done before any use
     trace.mark("sync");
+    if (o.autotune) {
+        RC(autotune_tiles(*C));
+        trace.mark("autotune");
+    }
     *out = C.release();
     return DGMG_OK;
 }
@@ -859,6 +976,8 @@ int dgmg_info(const dgmg_ctx *C, dgmg_info_t *info) {
     info->coarsening = C->opts.coarsening;
     info->device_bytes = C->bytes;
     info->outer = C->opts.outer;
+    const bool mixed = C->opts.precision == DGMG_MIXED_FP32;
+    for (int k = 0; k < 6; ++k) info->tiles[k] = (k < 3 || mixed) ? C->tile[k / 3][k % 3] : 0;
     return DGMG_OK;
 }
 
@@ -902,12 +1021,12 @@ int dgmg_smooth(dgmg_ctx *C, double *u, const double *b, int nsteps, void *strea
     cudaStream_t s = (cudaStream_t)stream;
     DGDev<double> &D = C->d64;
     C->prof.begin(ST_PROJECT, s);
-    LC(launch_project<double>(C->dim, C->q, D.c, C->cpb, u, nullptr, D.tr[0], s));
+    LC(launch_project<double>(C->dim, C->q, D.c, C->tile[0][TILE_PROJECT], u, nullptr, D.tr[0], s));
     C->prof.end(s);
     int cur = 0;
     for (int k = 0; k < nsteps; ++k) {
         C->prof.begin(ST_SMOOTH, s);
-        LC(launch_smooth<double>(C->dim, C->q, D.c, C->cpb, exact_block(*C), u, b, D.kappa, D.fd, D.linv,
+        LC(launch_smooth<double>(C->dim, C->q, D.c, C->tile[0][TILE_SMOOTH], exact_block(*C), u, b, D.kappa, D.fd, D.linv,
                                  D.tr[cur], D.tr[cur ^ 1], s));
         C->prof.end(s);
         cur ^= 1;
@@ -927,7 +1046,7 @@ int dgmg_project(dgmg_ctx *C, double *u, const double *e, double *traces, void *
     RC(check_ctx(C));
     NEED(u);
     NEED(traces);
-    LC(launch_project<double>(C->dim, C->q, C->d64.c, C->cpb, u, e, traces, (cudaStream_t)stream));
+    LC(launch_project<double>(C->dim, C->q, C->d64.c, C->tile[0][TILE_PROJECT], u, e, traces, (cudaStream_t)stream));
     return DGMG_OK;
 }
 
@@ -941,7 +1060,7 @@ int dgmg_residual_restrict(dgmg_ctx *C, const double *u, const double *b, const 
     int mode = RES_HAS_B;
     if (r) mode |= RES_WRITE_R;
     if (rc) mode |= RES_CORNERS;
-    LC(launch_residual<double>(C->dim, C->q, C->d64.c, C->cpb, mode, u, b, C->d64.kappa, traces, r,
+    LC(launch_residual<double>(C->dim, C->q, C->d64.c, C->tile[0][TILE_RESIDUAL], mode, u, b, C->d64.kappa, traces, r,
                                C->d64.corners, s));
     if (rc) LC(launch_corner_gather<double>(C->dim, C->n, C->d64.corners, rc, s));
     return DGMG_OK;
@@ -1117,7 +1236,7 @@ int residual_restrict_with_scratch(dgmg_ctx *C, const double *u, const double *b
     int mode = RES_HAS_B;
     if (r) mode |= RES_WRITE_R;
     if (rc) mode |= RES_CORNERS;
-    LC(launch_residual<double>(C->dim, C->q, C->d64.c, C->cpb, mode, u, b, C->d64.kappa, traces, r,
+    LC(launch_residual<double>(C->dim, C->q, C->d64.c, C->tile[0][TILE_RESIDUAL], mode, u, b, C->d64.kappa, traces, r,
                                corner_scratch, s));
     if (rc) LC(launch_corner_gather<double>(C->dim, C->n, corner_scratch, rc, s));
     return DGMG_OK;

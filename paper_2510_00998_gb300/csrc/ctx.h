@@ -4,6 +4,7 @@
 
 #include <chrono>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -49,6 +50,7 @@ struct CGDev {
 // Per-stage device time, recorded with CUDA events on the launching stream
 // around every stage launch while profiling is on (dgmg_profile).
 enum { ST_PROJECT = 0, ST_SMOOTH = 1, ST_RESIDUAL = 2, ST_CG = 3, ST_VECTOR = 4, ST_N = 5 };
+enum { TILE_PROJECT = 0, TILE_SMOOTH = 1, TILE_RESIDUAL = 2 };
 struct StageProfiler {
     bool on = false;
     std::vector<cudaEvent_t> ev;        // pairs: 2k start, 2k+1 stop
@@ -105,7 +107,14 @@ struct dgmg_ctx {
     int64_t ncell = 0, ndof = 0, nloc = 0;
     dgmg_opts opts;
     RefElem1D re;
-    int cpb = 8;
+    int cpb = 8;                                  // heuristic cells per CTA
+    // cells per CTA in use, [FP64, FP32][TILE_PROJECT, TILE_SMOOTH, TILE_RESIDUAL];
+    // 0 = the launcher's own choice (the one-thread-per-cell FP32 smoother where it applies)
+    int tile[2][3] = {{8, 8, 8}, {8, 8, 8}};
+    template <typename T>
+    int tile_of(int stage) const {
+        return tile[std::is_same<T, float>::value ? 1 : 0][stage];
+    }
     std::vector<CGLevelHost> lv;
     int64_t ncoarse = 0;
     double *coarse_inv = nullptr;

@@ -741,7 +741,14 @@ constexpr size_t smem_residual(int cpb) {
 template <int DIM, int Q, typename T>
 struct DGLaunch {
     using G = Geo<DIM, Q, T>;
+    // cells per CTA when the caller leaves the choice (cpb <= 0): about 128 threads
+    static int default_cpb() {
+        int c = std::max(1, 128 / G::NF);
+        while (c > 1 && c * G::NF > 256) --c;
+        return c;
+    }
     static cudaError_t project(const DGConst<T> &c, int cpb, T *u, const T *e0, T *tr, cudaStream_t s) {
+        if (cpb <= 0) cpb = default_cpb();
         const size_t sm = smem_project<DIM, Q, T>(cpb);
         static bool attr = false;
         if (!attr) {
@@ -761,8 +768,9 @@ struct DGLaunch {
             const bool aligned = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(b) |
                                    reinterpret_cast<uintptr_t>(fd)) & 15) == 0 &&
                                  ((reinterpret_cast<uintptr_t>(tri) | reinterpret_cast<uintptr_t>(tro)) & 7) == 0;
-            if (exact && aligned) return smooth_cells(c, u, b, kappa, fd, tri, tro, s);
+            if (cpb <= 0 && exact && aligned) return smooth_cells(c, u, b, kappa, fd, tri, tro, s);
         }
+        if (cpb <= 0) cpb = default_cpb();
         const size_t sm = smem_smooth<DIM, Q, T>(cpb, exact != 0);
         static bool attr = false;
         if (!attr) {
@@ -796,6 +804,7 @@ struct DGLaunch {
     }
     static cudaError_t residual(const DGConst<T> &c, int cpb, int mode, const T *u, const T *b, const T *kappa,
                                 const T *tr, T *r, T *corners, cudaStream_t s) {
+        if (cpb <= 0) cpb = default_cpb();
         const size_t sm = smem_residual<DIM, Q, T>(cpb);
         static bool attr = false;
         if (!attr) {

@@ -59,23 +59,34 @@ int run_chunk(dgmg_ctx *C, dgmg_ctx::Graph &g, const void *key, cudaStream_t s, 
             cudaGraphExecDestroy(g.exec);
             g.exec = nullptr;
         }
+        // A capture can be invalidated from outside (another thread of the
+        // process synchronising the whole device while it runs): then nothing
+        // was queued, so this ctx stops using graphs and queues the work eagerly.
+        auto eager = [&]() {
+            cudaGetLastError();
+            C->use_graphs = false;
+            return enqueue(s);
+        };
         const long long before = g_kernel_launches.load();
-        LC(cudaStreamBeginCapture(C->capture_stream, cudaStreamCaptureModeRelaxed));
+        if (cudaStreamBeginCapture(C->capture_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) return eager();
         const int rc = enqueue(C->capture_stream);
         cudaGraph_t graph = nullptr;
         const cudaError_t e = cudaStreamEndCapture(C->capture_stream, &graph);
         g.kernels = g_kernel_launches.load() - before;
         g_kernel_launches.fetch_sub(g.kernels);   // capturing launched nothing
-        if (rc != DGMG_OK) {
+        if (rc != DGMG_OK || e != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
-            return rc;
+            if (e == cudaErrorStreamCaptureInvalidated || e == cudaErrorStreamCaptureUnsupported ||
+                e == cudaErrorStreamCaptureImplicit || (rc != DGMG_OK && e != cudaSuccess))
+                return eager();
+            if (rc != DGMG_OK) return rc;
+            return cuda_fail(e, "cudaStreamEndCapture");
         }
-        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
         const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
         cudaGraphDestroy(graph);
         if (ei != cudaSuccess) {
             g.exec = nullptr;
-            return cuda_fail(ei, "cudaGraphInstantiate");
+            return eager();
         }
         g.key = key;
     }
@@ -104,10 +115,10 @@ enum {
 int apply32(dgmg_ctx &C, const float *u, float *y, cudaStream_t s) {
     DGDev<float> &D = C.d32;
     C.prof.begin(ST_PROJECT, s);
-    LC(launch_project<float>(C.dim, C.q, D.c, C.cpb, const_cast<float *>(u), nullptr, D.tr[0], s));
+    LC(launch_project<float>(C.dim, C.q, D.c, C.tile[1][TILE_PROJECT], const_cast<float *>(u), nullptr, D.tr[0], s));
     C.prof.end(s);
     C.prof.begin(ST_RESIDUAL, s);
-    LC(launch_residual<float>(C.dim, C.q, D.c, C.cpb, RES_WRITE_R | RES_NEGATE, u, nullptr, D.kappa, D.tr[0], y,
+    LC(launch_residual<float>(C.dim, C.q, D.c, C.tile[1][TILE_RESIDUAL], RES_WRITE_R | RES_NEGATE, u, nullptr, D.kappa, D.tr[0], y,
                               nullptr, s));
     C.prof.end(s);
     return DGMG_OK;

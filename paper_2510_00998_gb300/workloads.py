@@ -61,7 +61,7 @@ def make(name, device="cuda", **overrides):
     from . import dgmg
     w = dict(WORKLOADS[name])
     w.update(overrides)
-    ctx = dgmg.Context(w["n"], w["p"], kappa_field(w["kappa"], w["n"]), precision=w["precision"])
+    ctx = dgmg.Context(w["n"], w["p"], kappa_field(w["kappa"], w["n"]), precision=w["precision"], autotune=1)
     return ctx, sine_rhs(ctx, device)
 
 
@@ -88,7 +88,7 @@ def run(name, solves=3, warmup=1):
     ctx.profile(False)
     return {"workload": name, "ndof": ctx.ndof, "solve_ms": 1e3 * dt, "iterations": its,
             "rel_residual": max(res), "stages_ms_launches": prof,
-            "launches": dgmg.kernel_launches()}
+            "launches": dgmg.kernel_launches(), "tiles": list(ctx.info.tiles)}
 
 
 def main():

@@ -72,7 +72,9 @@ def test_results_in_the_mix_equal_results_alone(dgmg, precision):
     xs, tickets = [], []
     for k, (n, p, (kappa, b)) in enumerate(probs):
         x = torch.zeros_like(b)
-        torch.cuda.synchronize()
+        # stream (not device-wide) synchronisation: the server may be capturing
+        # a CUDA graph on another stream meanwhile
+        torch.cuda.current_stream().synchronize()
         tickets.append(srv.submit(n, p, b, x, kappa))
         xs.append(x)
         if k % 3 == 2:
@@ -98,7 +100,9 @@ def test_budget_bounds_admission_and_evicts(dgmg):
     xs, tickets = [], []
     for kappa, b in probs:
         x = torch.zeros_like(b)
-        torch.cuda.synchronize()
+        # stream (not device-wide) synchronisation: the server may be capturing
+        # a CUDA graph on another stream meanwhile
+        torch.cuda.current_stream().synchronize()
         tickets.append(srv.submit(n, p, b, x, kappa))
         xs.append(x)
     res, seen_active = _wait(srv, tickets)
