@@ -37,6 +37,9 @@ WORKLOAD = "sipg_3d_32^3_p3_kappa1_fp64_pcg_vcycle22"
 SAMPLE_CELLS = (16, 16, 16)      # bounded CPU sample: same p, 1/8 of the DoFs
 SAMPLE_STEPS = 60
 FP64_PEAK_TFLOPS = 1.25          # nominal GB300 dense FP64 (no FP64 entry in the measured peaks)
+# DRAM bytes (read + write) of one launch of k_smooth_cells<double,4> on this
+# workload, from one ncu capture (profiles/k_smooth_cells_fp64_32cube_p3.md)
+SMOOTH_TRAFFIC_BYTES = 115_337_472 + 12_144_640
 
 
 def parse():
@@ -318,6 +321,9 @@ def run_gb300(args):
     if rank == 0 and not args.no_serving:
         serving = serving_run()
 
+    # the smoothing kernel the tuned context runs (tile 0 = one thread per cell)
+    cells_kernel = ctx.info.tiles[1] == 0 and d == 3 and q <= 4
+    smooth_kernel = f"k_smooth_cells<double,{q}>" if cells_kernel else f"k_smooth<{d},{q},double>"
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
@@ -334,8 +340,11 @@ def run_gb300(args):
                        "l2": "flushed (256 MB write) before every timed step, outside the step's events",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                         "kernel": "k_smooth<3,4,double>", "avg_launch_ms": avg_ms,
+                         "frac": achieved / FP64_PEAK_TFLOPS,
+                         "traffic": SMOOTH_TRAFFIC_BYTES if cells_kernel else None,
+                         "traffic_note": ("dram__bytes_read.sum + dram__bytes_write.sum of one launch, ncu "
+                                          "(profiles/k_smooth_cells_fp64_32cube_p3.md)") if cells_kernel else None,
+                         "kernel": smooth_kernel, "avg_launch_ms": avg_ms,
                          "flops_per_launch": flops,
                          "hbm_bytes_per_launch": smooth_bytes_per_cell(d, q) * ctx.info.ncell,
                          "peak_note": "nominal FP64 1.25 TFLOP/s (FMA loop measured 1.257 on this pool)"},

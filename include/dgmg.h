@@ -106,7 +106,9 @@ typedef struct {
     int tiles[6];                 /* cells per CTA of the DG-level kernels in use:     */
                                   /* FP64 projection, smoothing, residual, then FP32   */
                                   /* (mixed precision only, else 0); a smoothing entry */
-                                  /* of 0 = the one-thread-per-cell FP32 kernel        */
+                                  /* of 0 = the one-thread-per-cell kernel where it    */
+                                  /* applies (3D, exact blocks, FP32 q <= 5, FP64      */
+                                  /* q <= 4), else the default pencil tile             */
 } dgmg_info_t;
 
 typedef struct {

@@ -733,7 +733,7 @@ static int tune_tiles(dgmg_ctx &C, T *u, T *b, int *tile, bool trace) {
         return launch_project<T>(C.dim, C.q, D.c, c, u, nullptr, D.tr[0], s);
     });
     std::vector<int> cs = cand;
-    if (std::is_same<T, float>::value && C.dim == 3 && C.q <= 5 && exact_block(C)) cs.insert(cs.begin(), 0);
+    if (C.dim == 3 && C.q <= (std::is_same<T, float>::value ? 5 : 4) && exact_block(C)) cs.insert(cs.begin(), 0);
     tile[TILE_SMOOTH] = pick("smooth", cs, [&](int c) {
         return launch_smooth<T>(C.dim, C.q, D.c, c, exact_block(C), u, b, D.kappa, D.fd, D.linv, D.tr[0],
                                 D.tr[1], s);
@@ -851,7 +851,8 @@ int dgmg_create(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_op
     while (C->cpb * nf > 256) --C->cpb;
     for (int k = 0; k < 2; ++k)
         for (int st = 0; st < 3; ++st) C->tile[k][st] = C->cpb;
-    C->tile[1][TILE_SMOOTH] = 0;   // FP32: the one-thread-per-cell smoother where it applies
+    C->tile[0][TILE_SMOOTH] = 0;   // the one-thread-per-cell smoother where it applies
+    C->tile[1][TILE_SMOOTH] = 0;
 
     std::vector<double> kap(C->ncell, 1.0);
     if (kappa) {

@@ -763,12 +763,14 @@ struct DGLaunch {
     }
     static cudaError_t smooth(const DGConst<T> &c, int cpb, int exact, T *u, const T *b, const T *kappa,
                               const T *fd, const T *linv, const T *tri, T *tro, cudaStream_t s) {
-        if constexpr (std::is_same<T, float>::value && DIM == 3 && Q <= 5) {
-            // bulk copies want 16-byte aligned vectors and factors, cp.async 8-byte aligned traces
+        if constexpr (CELLS_OK) {
+            // bulk copies want 16-byte aligned vectors, factors and table; the face
+            // pieces 8- (FP32) or 16-byte (FP64) aligned traces
+            const uintptr_t tra = std::is_same<T, float>::value ? 7 : 15;
             const bool aligned = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(b) |
-                                   reinterpret_cast<uintptr_t>(fd)) & 15) == 0 &&
-                                 ((reinterpret_cast<uintptr_t>(tri) | reinterpret_cast<uintptr_t>(tro)) & 7) == 0;
-            if (cpb <= 0 && exact && aligned) return smooth_cells(c, u, b, kappa, fd, tri, tro, s);
+                                   reinterpret_cast<uintptr_t>(fd) | reinterpret_cast<uintptr_t>(linv)) & 15) == 0 &&
+                                 ((reinterpret_cast<uintptr_t>(tri) | reinterpret_cast<uintptr_t>(tro)) & tra) == 0;
+            if (cpb <= 0 && exact && aligned) return smooth_cells(c, u, b, kappa, fd, linv, tri, tro, s);
         }
         if (cpb <= 0) cpb = default_cpb();
         const size_t sm = smem_smooth<DIM, Q, T>(cpb, exact != 0);
@@ -783,20 +785,23 @@ struct DGLaunch {
         k_smooth<DIM, Q, T><<<(unsigned)grid, cpb * G::NF, sm, s>>>(c, cpb, exact, u, b, kappa, fd, linv, tri, tro);
         return cudaGetLastError();
     }
-    // FP32 3D exact-block smoothing step with one thread per cell (k_smooth_cells)
+    // 3D exact-block smoothing step with one thread per cell (k_smooth_cells):
+    // FP32 q <= 5, FP64 q <= 4 (the cell must fit in the registers of a thread)
+    static constexpr bool CELLS_OK = DIM == 3 && (std::is_same<T, float>::value ? Q <= 5 : Q <= 4);
     static cudaError_t smooth_cells(const DGConst<T> &c, T *u, const T *b, const T *kappa, const T *fd,
-                                    const T *tri, T *tro, cudaStream_t s) {
-        if constexpr (std::is_same<T, float>::value && DIM == 3 && Q <= 5) {
-            using CG = CellGeo<Q>;
+                                    const T *linv, const T *tri, T *tro, cudaStream_t s) {
+        if constexpr (CELLS_OK) {
+            using CG = CellGeo<T, Q>;
             static bool attr = false;
             if (!attr) {
-                cudaFuncSetAttribute(k_smooth_cells<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CG::BYTES);
+                cudaFuncSetAttribute(k_smooth_cells<T, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)CG::BYTES);
                 attr = true;
             }
             const int64_t grid = (c.ncell + CG::W - 1) / CG::W;
             if (grid == 0) return cudaSuccess;
             count_launches(1);
-            k_smooth_cells<Q><<<(unsigned)grid, CG::W, CG::BYTES, s>>>(c, u, b, kappa, fd, tri, tro);
+            k_smooth_cells<T, Q><<<(unsigned)grid, CG::W, CG::BYTES, s>>>(c, u, b, kappa, fd, linv, tri, tro);
             return cudaGetLastError();
         } else {
             return cudaErrorInvalidValue;

@@ -1,5 +1,5 @@
-// FP32 single-touch smoothing step (Algorithm 4, exact diagonal blocks) with one
-// thread per cell, for 3D and q <= 5 nodes per axis.
+// Single-touch smoothing step (Algorithm 4, exact diagonal blocks) with one
+// thread per cell, 3D: FP32 for q <= 5, FP64 for q <= 4 nodes per axis.
 //
 // Each thread keeps its whole cell (q^3 values) in registers, so the six
 // tensor passes of the fast-diagonalisation inverse need no transposes through
@@ -8,10 +8,14 @@
 //   - b and the fast-diagonalisation factors: one bulk (TMA) copy each,
 //     completing on an mbarrier;
 //   - the neighbours' traces, face by face through two slots, with cp.async
-//     (8-byte pieces: a face of one cell is 2 q^2 floats, which is not a
-//     multiple of 16 bytes for odd q);
-//   - u of the previous iterate: a bulk copy into b's buffer once b is read,
-//     overlapping the facet work.
+//     (16-byte pieces, or 8-byte ones where a face of one cell, 2 q^2 values,
+//     is not a multiple of 16 bytes: FP32 with odd q);
+//   - FP32: u of the previous iterate by a bulk copy into the slot area once
+//     the faces are consumed, overlapping the inverse;
+//   - FP64: the per-node table of inverse eigenvalue sums into the slot area
+//     once the faces are consumed (FP64 division is a long sequence on the
+//     FP64 pipe, which bounds the FP64 kernel), then u of the previous iterate
+//     into the same area once the table is used, overlapping the last passes.
 // The new u leaves through a bulk store; the new traces through the face slots
 // with coalesced stores. A lane reads its own cell with stride q^3 (odd for odd
 // q, so a warp's 32 loads hit 32 banks).
@@ -33,6 +37,9 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)
 
 __device__ __forceinline__ void cp_async8(void *dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
@@ -96,32 +103,47 @@ __device__ __forceinline__ bool warp_wait_copies(uint64_t *bar, int lane) {
     return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
-template <int Q>
+template <typename T, int Q>
 struct CellGeo {
     static constexpr int NL = Q * Q * Q, NF = Q * Q, TR = 12 * NF, FDS = Q * Q + Q;
     static constexpr int W = 32;                       // cells per CTA (one per lane)
-    // shared memory (floats), per cell: area A holds b, then the factors, then
-    // the new u; area B holds two neighbour-face slots, then the previous u, then
-    // two faces of new traces
+    // copy granule of the face staging: 16 bytes where a face of one cell allows it
+    static constexpr int PIECE = (2 * NF * (int)sizeof(T)) % 16 == 0 ? 16 : 8;
+    static constexpr int PER_PIECE = PIECE / (int)sizeof(T);   // values per piece
+    static constexpr int PIECES = 2 * NF / PER_PIECE;          // pieces per face of one cell
+    // FP64 (LEAN): the kernel is bound by the FP64 pipe, not by memory, so the
+    // neighbour faces, the table and the previous u are read straight from
+    // global memory by each lane and the traces written the same way; only
+    // area A is staged. That halves the shared memory per CTA, so more CTAs
+    // are resident (a 32^3 mesh fits in one wave).
+    static constexpr bool LEAN = sizeof(T) == 8;
+    // shared memory (values of T), per cell: area A holds b, then the factors,
+    // then the new u; area B (FP32) holds two neighbour-face slots, then the
+    // previous u, then two faces of new traces
     static constexpr int PA = NL > 3 * FDS ? NL : 3 * FDS;
-    static constexpr int PB = NL > 4 * NF ? NL : 4 * NF;
+    static constexpr int PB = LEAN ? 0 : (NL > 4 * NF ? NL : 4 * NF);
     static constexpr size_t OFF_B = (size_t)W * PA;
     static constexpr size_t OFF_K = OFF_B + (size_t)W * PB;   // kF [6][W]
     static constexpr size_t OFF_NB = OFF_K + 6 * W;          // neighbour cell [6][W] (int)
-    static constexpr size_t BYTES = (OFF_NB + 6 * W) * sizeof(float);
+    static constexpr size_t BYTES = OFF_NB * sizeof(T) + 6 * W * sizeof(int);
 };
 
 // Stage face f of the neighbours of the CTA's cells (their face f^1) into a slot.
-template <int Q>
-__device__ __forceinline__ void stage_face(int f, int ncl, int lane, const int *sNb, const float *__restrict__ tr,
-                                           float *slot) {
-    using G = CellGeo<Q>;
-    constexpr int PIECES = G::NF;                      // 8-byte pieces per face of one cell
-    for (int idx = lane; idx < ncl * PIECES; idx += G::W) {
-        const int j = idx / PIECES, part = idx - j * PIECES;
+template <typename T, int Q>
+__device__ __forceinline__ void stage_face(int f, int ncl, int lane, const int *sNb, const T *__restrict__ tr,
+                                           T *slot) {
+    using G = CellGeo<T, Q>;
+    for (int idx = lane; idx < ncl * G::PIECES; idx += G::W) {
+        const int j = idx / G::PIECES, part = idx - j * G::PIECES;
         const int nb = sNb[f * G::W + j];
-        if (nb >= 0)
-            cp_async8(slot + j * 2 * G::NF + 2 * part, tr + (int64_t)nb * G::TR + (f ^ 1) * 2 * G::NF + 2 * part);
+        if (nb >= 0) {
+            T *dst = slot + j * 2 * G::NF + G::PER_PIECE * part;
+            const T *src = tr + (int64_t)nb * G::TR + (f ^ 1) * 2 * G::NF + G::PER_PIECE * part;
+            if (G::PIECE == 16)
+                cp_async16(dst, src);
+            else
+                cp_async8(dst, src);
+        }
     }
     cp_async_commit();
 }
@@ -131,44 +153,48 @@ __device__ __forceinline__ void stage_face(int f, int ncl, int lane, const int *
 // tensor (one code path for all three axes, which keeps the kernel small
 // enough for the instruction cache).
 // rotate: new (x, y, z) = old (y, z, x).
-template <int Q>
-__device__ __forceinline__ void rotate(float *R) {
-    float T[Q * Q * Q];
+template <typename T, int Q>
+__device__ __forceinline__ void rotate(T *R) {
+    T tmp[Q * Q * Q];
 #pragma unroll
-    for (int e = 0; e < Q * Q * Q; ++e) T[e] = R[e];
+    for (int e = 0; e < Q * Q * Q; ++e) tmp[e] = R[e];
 #pragma unroll
     for (int k = 0; k < Q; ++k)
 #pragma unroll
         for (int j = 0; j < Q; ++j)
 #pragma unroll
-            for (int i = 0; i < Q; ++i) R[j + Q * k + Q * Q * i] = T[i + Q * j + Q * Q * k];
+            for (int i = 0; i < Q; ++i) R[j + Q * k + Q * Q * i] = tmp[i + Q * j + Q * Q * k];
 }
 // rotate_back: new (x, y, z) = old (z, x, y).
-template <int Q>
-__device__ __forceinline__ void rotate_back(float *R) {
-    float T[Q * Q * Q];
+template <typename T, int Q>
+__device__ __forceinline__ void rotate_back(T *R) {
+    T tmp[Q * Q * Q];
 #pragma unroll
-    for (int e = 0; e < Q * Q * Q; ++e) T[e] = R[e];
+    for (int e = 0; e < Q * Q * Q; ++e) tmp[e] = R[e];
 #pragma unroll
     for (int k = 0; k < Q; ++k)
 #pragma unroll
         for (int j = 0; j < Q; ++j)
 #pragma unroll
-            for (int i = 0; i < Q; ++i) R[k + Q * i + Q * Q * j] = T[i + Q * j + Q * Q * k];
+            for (int i = 0; i < Q; ++i) R[k + Q * i + Q * Q * j] = tmp[i + Q * j + Q * Q * k];
 }
 
-// Load a q x q matrix (row-major, 8-byte aligned in shared memory) into
-// registers, transposed if asked.
-template <int Q, bool TRANSPOSE>
-__device__ __forceinline__ void load_matrix(const float *src, float *S) {
-    float v[Q * Q];
+// Load a q x q matrix (row-major in shared memory) into registers, transposed if asked.
+template <typename T, int Q, bool TRANSPOSE>
+__device__ __forceinline__ void load_matrix(const T *src, T *S) {
+    T v[Q * Q];
+    if (sizeof(T) == 4) {                               // 8-byte loads (the matrix is 8-byte aligned)
 #pragma unroll
-    for (int e = 0; e < (Q * Q) / 2; ++e) {
-        const float2 w = reinterpret_cast<const float2 *>(src)[e];
-        v[2 * e] = w.x;
-        v[2 * e + 1] = w.y;
+        for (int e = 0; e < (Q * Q) / 2; ++e) {
+            const float2 w = reinterpret_cast<const float2 *>(src)[e];
+            v[2 * e] = (T)w.x;
+            v[2 * e + 1] = (T)w.y;
+        }
+        if ((Q * Q) & 1) v[Q * Q - 1] = src[Q * Q - 1];
+    } else {
+#pragma unroll
+        for (int e = 0; e < Q * Q; ++e) v[e] = src[e];
     }
-    if ((Q * Q) & 1) v[Q * Q - 1] = src[Q * Q - 1];
 #pragma unroll
     for (int m = 0; m < Q; ++m)
 #pragma unroll
@@ -176,16 +202,16 @@ __device__ __forceinline__ void load_matrix(const float *src, float *S) {
 }
 
 // Along x: R[., a, b] <- A R[., a, b] for every pencil (A row-major q x q).
-template <int Q>
-__device__ __forceinline__ void pass_x(const float *A, float *R) {
+template <typename T, int Q>
+__device__ __forceinline__ void pass_x(const T *A, T *R) {
 #pragma unroll
     for (int t = 0; t < Q * Q; ++t) {
-        float x[Q];
+        T x[Q];
 #pragma unroll
         for (int n = 0; n < Q; ++n) x[n] = R[n + Q * t];
 #pragma unroll
         for (int m = 0; m < Q; ++m) {
-            float s = 0.f;
+            T s = T(0);
 #pragma unroll
             for (int n = 0; n < Q; ++n) s += A[m * Q + n] * x[n];
             R[m + Q * t] = s;
@@ -197,28 +223,28 @@ __device__ __forceinline__ void pass_x(const float *A, float *R) {
 // neighbour fields fld = [g | h] (q^2 each) are indexed sa * a + sb * b at the
 // current tangential position (a, b) = (y, z). With G, H the fields after the
 // tangential mass M_a (x) M_b (Ma, Mb: the 1D masses of the original axes now
-// at y and z):
+// at y and z, in shared memory):
 //   low face:  N = kF [e_0 (x) (H/2 - gamma G) - d_0 (x) G/2],
 //   high face: N = kF [e_p (x) (-H/2 - gamma G) + d_p (x) G/2].
-template <int Q>
-__device__ __forceinline__ void lift_x_face(int side, const float *fld, int sa, int sb, const float *Ma,
-                                            const float *Mb, const float *dv, float gam, float kF, float *R) {
+template <typename T, int Q>
+__device__ __forceinline__ void lift_x_face(int side, const T *fld, int sa, int sb, const T *Ma, const T *Mb,
+                                            const T *dv, T gam, T kF, T *R) {
     constexpr int NF = Q * Q;
-    const float g2 = kF * gam, wv = 0.5f * kF, sgn = side ? -1.f : 1.f;
+    const T g2 = kF * gam, wv = T(0.5) * kF, sgn = side ? T(-1) : T(1);
     // value field: end layer += kF gamma G; all layers += sgn kF/2 G d
     // derivative field: end layer -= sgn kF/2 H
 #pragma unroll
     for (int comp = 0; comp < 2; ++comp) {
-        const float *f = fld + comp * NF;
-        float t1[NF];                                  // t1[a + q b] = sum_b' Mb[b][b'] f(a, b')
+        const T *f = fld + comp * NF;
+        T t1[NF];                                      // t1[a + q b] = sum_b' Mb[b][b'] f(a, b')
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
-            float col[Q];
+            T col[Q];
 #pragma unroll
             for (int bb = 0; bb < Q; ++bb) col[bb] = f[sa * a + sb * bb];
 #pragma unroll
             for (int b = 0; b < Q; ++b) {
-                float s = 0.f;
+                T s = T(0);
 #pragma unroll
                 for (int bb = 0; bb < Q; ++bb) s += Mb[b * Q + bb] * col[bb];
                 t1[a + Q * b] = s;
@@ -228,12 +254,12 @@ __device__ __forceinline__ void lift_x_face(int side, const float *fld, int sa, 
         for (int b = 0; b < Q; ++b)
 #pragma unroll
             for (int a = 0; a < Q; ++a) {
-                float v = 0.f;
+                T v = T(0);
 #pragma unroll
                 for (int aa = 0; aa < Q; ++aa) v += Ma[a * Q + aa] * t1[aa + Q * b];
-                float *pen = R + Q * (a + Q * b);          // the pencil along x at (a, b)
+                T *pen = R + Q * (a + Q * b);              // the pencil along x at (a, b)
                 if (comp == 0) {
-                    const float w = sgn * wv * v;
+                    const T w = sgn * wv * v;
                     if (side) pen[Q - 1] += g2 * v; else pen[0] += g2 * v;
 #pragma unroll
                     for (int n = 0; n < Q; ++n) pen[n] += w * dv[n];
@@ -246,16 +272,15 @@ __device__ __forceinline__ void lift_x_face(int side, const float *fld, int sa, 
 
 // Traces of the face normal to the current x axis on side `side` into dst
 // ([value q^2 | derivative q^2], indexed sa * a + sb * b).
-template <int Q>
-__device__ __forceinline__ void x_face_traces(int side, const float *R, const float *dv, int sa, int sb,
-                                              float *dst) {
+template <typename T, int Q>
+__device__ __forceinline__ void x_face_traces(int side, const T *R, const T *dv, int sa, int sb, T *dst) {
     constexpr int NF = Q * Q;
 #pragma unroll
     for (int b = 0; b < Q; ++b)
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
-            const float *pen = R + Q * (a + Q * b);
-            float d = 0.f;
+            const T *pen = R + Q * (a + Q * b);
+            T d = T(0);
 #pragma unroll
             for (int n = 0; n < Q; ++n) d += dv[n] * pen[n];
             dst[sa * a + sb * b] = side ? pen[Q - 1] : pen[0];
@@ -263,45 +288,62 @@ __device__ __forceinline__ void x_face_traces(int side, const float *R, const fl
         }
 }
 
-template <int Q>
-__global__ void __launch_bounds__(32) k_smooth_cells(const __grid_constant__ DGConst<float> c, float *__restrict__ u,
-                                                     const float *__restrict__ b, const float *__restrict__ kappa,
-                                                     const float *__restrict__ fd, const float *__restrict__ tr_in,
-                                                     float *__restrict__ tr_out) {
-    using G = CellGeo<Q>;
+template <typename T>
+__device__ __forceinline__ T div_approx(T a, T b);
+template <>
+__device__ __forceinline__ float div_approx<float>(float a, float b) { return __fdividef(a, b); }
+template <>
+__device__ __forceinline__ double div_approx<double>(double a, double b) { return a / b; }
+
+// Bulk copy of `bytes` into shared memory on `bar` (lane 0 issues).
+template <typename T>
+__device__ __forceinline__ void stage_bulk(bool full, int lane, uint64_t *bar, T *dst, const T *src, int64_t count,
+                                           int ncount) {
+    if (full) {
+        if (lane == 0) {
+            mbar_arrive_expect_tx(bar, (unsigned)(count * sizeof(T)));
+            bulk_load(dst, src, (unsigned)(count * sizeof(T)), bar);
+        }
+    } else {
+        for (int e = lane; e < ncount; e += 32) dst[e] = src[e];
+    }
+}
+
+template <typename T, int Q>
+__global__ void __launch_bounds__(32) k_smooth_cells(const __grid_constant__ DGConst<T> c, T *__restrict__ u,
+                                                     const T *__restrict__ b, const T *__restrict__ kappa,
+                                                     const T *__restrict__ fd, const T *__restrict__ linv,
+                                                     const T *__restrict__ tr_in, T *__restrict__ tr_out) {
+    using G = CellGeo<T, Q>;
     constexpr int W = G::W, NL = G::NL, NF = G::NF, FDS = G::FDS, TR = G::TR;
-    extern __shared__ __align__(128) float smem_f[];
-    float *sA = smem_f;                                  // b -> factors -> new u
-    float *sB = smem_f + G::OFF_B;                       // face slots -> previous u -> new traces
+    extern __shared__ __align__(128) unsigned char smem_c[];
+    T *sA = reinterpret_cast<T *>(smem_c);              // b -> factors -> new u
+    T *sB = sA + G::OFF_B;                               // face slots -> (table) -> previous u -> new traces
     // face slot s (0, 1) of area B: sB + s * W * 2 NF
-    float *sK = smem_f + G::OFF_K;
-    int *sNb = reinterpret_cast<int *>(smem_f + G::OFF_NB);
-    __shared__ __align__(8) uint64_t bars[3];
-    __shared__ float sM[3][Q * Q];
+    T *sK = sA + G::OFF_K;
+    int *sNb = reinterpret_cast<int *>(sA + G::OFF_NB);
+    __shared__ __align__(8) uint64_t bars[4];
+    __shared__ T sM[3][Q * Q];
     const int lane = threadIdx.x;
     const int64_t cell0 = (int64_t)blockIdx.x * W;
     const int ncl = (int)min((int64_t)W, c.ncell - cell0);
     const bool full = ncl == W;                          // bulk copies need whole 32-cell blocks
     const bool active = lane < ncl;
     const int64_t cell = cell0 + lane;
+    const bool table = linv != nullptr;
 
     for (int e = lane; e < 3 * Q * Q; e += W) sM[e / (Q * Q)][e % (Q * Q)] = c.M[e / (Q * Q)][e % (Q * Q)];
-    if (full) {
-        if (lane == 0) {
+    if (full && lane == 0) {
 #pragma unroll
-            for (int i = 0; i < 3; ++i) mbar_init(&bars[i], 1);
-            fence_mbar_init();
-            fence_proxy_async_smem();
-            mbar_arrive_expect_tx(&bars[0], (unsigned)(W * NL * sizeof(float)));
-            bulk_load(sA, b + cell0 * NL, (unsigned)(W * NL * sizeof(float)), &bars[0]);
-        }
-    } else {
-        for (int e = lane; e < ncl * NL; e += W) sA[e] = b[cell0 * NL + e];
+        for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
+        fence_mbar_init();
+        fence_proxy_async_smem();
     }
+    stage_bulk<T>(full, lane, &bars[0], sA, b + cell0 * NL, W * NL, ncl * NL);
     // neighbours and facet coefficients of this lane's cell
     int mask = 0;
     {
-        float kK = 1.f;
+        T kK = T(1);
         if (active) {
             int ci[3];
             cell_coords<3>(cell, c.n, ci);
@@ -311,20 +353,22 @@ __global__ void __launch_bounds__(32) k_smooth_cells(const __grid_constant__ DGC
 #pragma unroll
         for (int f = 0; f < 6; ++f) {
             int nb = -1;
-            float kF = 0.f;
+            T kF = T(0);
             if (mask & (1 << f)) {
                 const int64_t s = axis_stride<3>(c.n, f >> 1);
                 nb = (int)((f & 1) ? cell + s : cell - s);
-                const float kN = kappa[nb];
-                kF = 2.f * kK * kN / (kK + kN);
+                const T kN = kappa[nb];
+                kF = T(2) * kK * kN / (kK + kN);
             }
             sNb[f * W + lane] = nb;
             sK[f * W + lane] = kF;
         }
     }
     __syncwarp();
-    stage_face<Q>(0, ncl, lane, sNb, tr_in, sB);
-    stage_face<Q>(1, ncl, lane, sNb, tr_in, sB + W * 2 * NF);
+    if (!G::LEAN) {
+        stage_face<T, Q>(0, ncl, lane, sNb, tr_in, sB);
+        stage_face<T, Q>(1, ncl, lane, sNb, tr_in, sB + W * 2 * NF);
+    }
 
     // r = b
     if (full) {
@@ -335,115 +379,115 @@ __global__ void __launch_bounds__(32) k_smooth_cells(const __grid_constant__ DGC
     } else {
         __syncwarp();
     }
-    float R[NL];
+    T R[NL];
 #pragma unroll
-    for (int e = 0; e < NL; ++e) R[e] = active ? sA[lane * NL + e] : 0.f;
+    for (int e = 0; e < NL; ++e) R[e] = active ? sA[lane * NL + e] : T(0);
     // the factors into the same area, behind the facet work
     fence_proxy_async_smem();
     __syncwarp();
-    if (full) {
-        if (lane == 0) {
-            mbar_arrive_expect_tx(&bars[1], (unsigned)(W * 3 * FDS * sizeof(float)));
-            bulk_load(sA, fd + cell0 * 3 * FDS, (unsigned)(W * 3 * FDS * sizeof(float)), &bars[1]);
-        }
-    } else {
-        for (int e = lane; e < ncl * 3 * FDS; e += W) sA[e] = fd[cell0 * 3 * FDS + e];
-    }
+    stage_bulk<T>(full, lane, &bars[1], sA, fd + cell0 * 3 * FDS, W * 3 * FDS, ncl * 3 * FDS);
 
     // r -= N u_nb: the two faces normal to axis p, then rotate the next axis to x
 #pragma unroll 1
     for (int p = 0; p < 3; ++p) {
-        float Ma[Q * Q], Mb[Q * Q], dv[Q];
+        T dv[Q];
         const int ta = p == 2 ? 0 : p + 1, tb = p == 0 ? 2 : p - 1;
         const int sa = p == 1 ? Q : 1, sb = p == 1 ? 1 : Q;   // the y faces are stored transposed
-#pragma unroll
-        for (int e = 0; e < Q * Q; ++e) {
-            Ma[e] = sM[ta][e];
-            Mb[e] = sM[tb][e];
-        }
-        const float gam = c.gamma[p];
+        const T gam = c.gamma[p];
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
             const int f = 2 * p + side;
-            if (f < 5)
-                cp_async_wait<1>();
-            else
-                cp_async_wait<0>();
-            __syncwarp();
+            if (!G::LEAN) {
+                if (f < 5)
+                    cp_async_wait<1>();
+                else
+                    cp_async_wait<0>();
+                __syncwarp();
+            }
             if (active && (mask & (1 << f))) {
 #pragma unroll
                 for (int n = 0; n < Q; ++n) dv[n] = side ? c.dp[p][n] : c.d0[p][n];
-                lift_x_face<Q>(side, sB + side * W * 2 * NF + lane * 2 * NF, sa, sb, Ma, Mb, dv, gam, sK[f * W + lane], R);
+                const T *fld = G::LEAN ? tr_in + (int64_t)sNb[f * W + lane] * TR + (f ^ 1) * 2 * NF
+                                       : sB + side * W * 2 * NF + lane * 2 * NF;
+                lift_x_face<T, Q>(side, fld, sa, sb, sM[ta], sM[tb], dv, gam, sK[f * W + lane], R);
             }
-            __syncwarp();
-            if (f + 2 < 6) stage_face<Q>(f + 2, ncl, lane, sNb, tr_in, sB + side * W * 2 * NF);
+            if (!G::LEAN) {
+                __syncwarp();
+                if (f + 2 < 6) stage_face<T, Q>(f + 2, ncl, lane, sNb, tr_in, sB + side * W * 2 * NF);
+            }
         }
-        rotate<Q>(R);
+        rotate<T, Q>(R);
     }
-    // the previous iterate into area B (the face slots are free now)
-    fence_proxy_async_smem();
-    __syncwarp();
-    if (full) {
-        if (lane == 0) {
-            mbar_arrive_expect_tx(&bars[2], (unsigned)(W * NL * sizeof(float)));
-            bulk_load(sB, u + cell0 * NL, (unsigned)(W * NL * sizeof(float)), &bars[2]);
-        }
-    } else {
-        for (int e = lane; e < ncl * NL; e += W) sB[e] = u[cell0 * NL + e];
+    // FP32: the previous iterate into area B (the face slots are free now)
+    if (!G::LEAN) {
+        fence_proxy_async_smem();
+        __syncwarp();
+        stage_bulk<T>(full, lane, &bars[2], sB, u + cell0 * NL, W * NL, ncl * NL);
     }
 
-    // A_KK^{-1} by fast diagonalisation: S^T along x, y, z; divide by the
-    // eigenvalue sums; S along z, y, x
+    // A_KK^{-1} by fast diagonalisation: S^T along x, y, z; scale by the
+    // inverse eigenvalue sums; S along z, y, x
     if (full) {
         if (!warp_wait_copies(&bars[1], lane)) {
-            warp_wait_copies(&bars[2], lane);
+            if (!G::LEAN) warp_wait_copies(&bars[2], lane);
             return;
         }
     } else {
         __syncwarp();
     }
-    const float *myFD = sA + lane * 3 * FDS;
+    const T *myFD = sA + lane * 3 * FDS;
     if (active) {
 #pragma unroll 1
         for (int p = 0; p < 3; ++p) {
-            float S[Q * Q];
-            load_matrix<Q, true>(myFD + p * FDS, S);
-            pass_x<Q>(S, R);
-            rotate<Q>(R);
+            T S[Q * Q];
+            load_matrix<T, Q, true>(myFD + p * FDS, S);
+            pass_x<T, Q>(S, R);
+            rotate<T, Q>(R);
         }
+    }
+    if (active) {
+        if (table) {
+            const T *li = linv + cell * NL;
 #pragma unroll
-        for (int k = 0; k < Q; ++k) {
-            const float lz = myFD[2 * FDS + Q * Q + k];
+            for (int e = 0; e < NL; ++e) R[e] *= li[e];
+        } else {
 #pragma unroll
-            for (int j = 0; j < Q; ++j) {
-                const float lyz = myFD[1 * FDS + Q * Q + j] + lz;
+            for (int k = 0; k < Q; ++k) {
+                const T lz = myFD[2 * FDS + Q * Q + k];
 #pragma unroll
-                for (int i = 0; i < Q; ++i) {
-                    const int e = i + Q * (j + Q * k);
-                    R[e] = __fdividef(R[e], myFD[Q * Q + i] + lyz);
+                for (int j = 0; j < Q; ++j) {
+                    const T lyz = myFD[1 * FDS + Q * Q + j] + lz;
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) {
+                        const int e = i + Q * (j + Q * k);
+                        R[e] = div_approx<T>(R[e], myFD[Q * Q + i] + lyz);
+                    }
                 }
             }
         }
+    }
+    if (active) {
 #pragma unroll 1
         for (int p = 2; p >= 0; --p) {
-            float S[Q * Q];
-            rotate_back<Q>(R);
-            load_matrix<Q, false>(myFD + p * FDS, S);
-            pass_x<Q>(S, R);
+            T S[Q * Q];
+            rotate_back<T, Q>(R);
+            load_matrix<T, Q, false>(myFD + p * FDS, S);
+            pass_x<T, Q>(S, R);
         }
     }
 
     // u <- (1 - w) u + w y, stored through area A
-    if (full) {
+    if (!G::LEAN && full) {
         if (!warp_wait_copies(&bars[2], lane)) return;
     } else {
         __syncwarp();
     }
-    float *myU = sA + lane * NL;                        // overlaps other lanes' factors: after the barrier
+    T *myU = sA + lane * NL;                            // overlaps other lanes' factors: after the barrier
     if (active) {
-        const float om = c.omega, keep = 1.f - om;
+        const T om = c.omega, keep = T(1) - om;
+        const T *uo = G::LEAN ? u + cell * NL : sB + lane * NL;
 #pragma unroll
-        for (int e = 0; e < NL; ++e) R[e] = keep * sB[lane * NL + e] + om * R[e];
+        for (int e = 0; e < NL; ++e) R[e] = keep * uo[e] + om * R[e];
 #pragma unroll
         for (int e = 0; e < NL; ++e) myU[e] = R[e];
     }
@@ -451,7 +495,7 @@ __global__ void __launch_bounds__(32) k_smooth_cells(const __grid_constant__ DGC
     __syncwarp();
     if (full) {
         if (lane == 0) {
-            bulk_store(u + cell0 * NL, sA, (unsigned)(W * NL * sizeof(float)));
+            bulk_store(u + cell0 * NL, sA, (unsigned)(W * NL * sizeof(T)));
             bulk_commit();
         }
     } else {
@@ -466,21 +510,30 @@ __global__ void __launch_bounds__(32) k_smooth_cells(const __grid_constant__ DGC
         if (active) {
 #pragma unroll
             for (int side = 0; side < 2; ++side) {
-                float dv[Q];
+                T dv[Q];
 #pragma unroll
                 for (int n = 0; n < Q; ++n) dv[n] = side ? c.dp[p][n] : c.d0[p][n];
-                x_face_traces<Q>(side, R, dv, sa, sb, sB + side * W * 2 * NF + lane * 2 * NF);
+                T *dst = G::LEAN ? tr_out + cell * TR + (2 * p + side) * 2 * NF
+                                 : sB + side * W * 2 * NF + lane * 2 * NF;
+                x_face_traces<T, Q>(side, R, dv, sa, sb, dst);
             }
         }
-        __syncwarp();
-        for (int idx = lane; idx < ncl * 2 * NF; idx += W) {   // 2 faces x [W][2 NF] -> [cell][face 2p + side]
-            const int side = idx / (ncl * NF), r = idx - side * (ncl * NF);
-            const int j = r / NF, part = r - j * NF;
-            const float2 v = reinterpret_cast<const float2 *>(sB + side * W * 2 * NF + j * 2 * NF)[part];
-            reinterpret_cast<float2 *>(tr_out + (cell0 + j) * TR + (2 * p + side) * 2 * NF)[part] = v;
+        if (G::LEAN) {
+            if (p < 2) rotate<T, Q>(R);
+            continue;
         }
         __syncwarp();
-        rotate<Q>(R);
+        // 2 faces x [W][2 NF] -> [cell][face 2p + side], in 8-byte (FP32) or 16-byte (FP64) pieces
+        using V = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+        constexpr int NV = NF;                          // 2 NF values = NF pieces of two
+        for (int idx = lane; idx < ncl * 2 * NV; idx += W) {
+            const int side = idx / (ncl * NV), r = idx - side * (ncl * NV);
+            const int j = r / NV, part = r - j * NV;
+            const V v = reinterpret_cast<const V *>(sB + side * W * 2 * NF + j * 2 * NF)[part];
+            reinterpret_cast<V *>(tr_out + (cell0 + j) * TR + (2 * p + side) * 2 * NF)[part] = v;
+        }
+        __syncwarp();
+        if (p < 2) rotate<T, Q>(R);
     }
     if (full && lane == 0) bulk_wait_read_all();
 }

@@ -342,9 +342,10 @@ def test_maxit_exhaustion_reports_not_converged(dgmg, prec):
 
 @pytest.mark.parametrize("n,p,prec", [((8, 8, 8), 3, 0), ((9, 8, 7), 4, 1), ((12, 10), 4, 0)])
 def test_autotuned_tiles(dgmg, n, p, prec):
-    """The tile autotuner only changes how cells are grouped into CTAs: FP64
-    results are bit-identical to the default tiles; mixed-precision solves
-    still meet the oracle bound. The chosen tiles are reported by dgmg_info."""
+    """The tile autotuner only changes how cells are grouped into CTAs (and which
+    of two smoothing kernels with different summation orders runs): FP64
+    results agree with the default tiles to rounding; every solve meets the
+    oracle bound. The chosen tiles are reported by dgmg_info."""
     kap = _kappa(n, "lognormal")
     mesh = sipg.Mesh(n, p)
     b = np.random.default_rng(21).normal(size=mesh.ndof)
@@ -352,7 +353,7 @@ def test_autotuned_tiles(dgmg, n, p, prec):
     for tune in (0, 1):
         ctx = dgmg.Context(n, p, kap, precision=prec, autotune=tune)
         tiles = list(ctx.info.tiles)
-        assert all(t >= 0 for t in tiles) and all(t > 0 for t in tiles[:3])
+        assert all(t >= 0 for t in tiles) and tiles[0] > 0 and tiles[2] > 0
         if prec == 0:
             assert tiles[3:] == [0, 0, 0]
         x = torch.zeros(mesh.ndof, dtype=torch.float64, device=DEV)
@@ -360,7 +361,7 @@ def test_autotuned_tiles(dgmg, n, p, prec):
         assert st.rel_residual <= 1e-10
         xs.append(_np(x))
     if prec == 0:
-        assert np.array_equal(xs[0], xs[1])
+        assert np.abs(xs[0] - xs[1]).max() <= 1e-12 * np.abs(xs[0]).max()
     x_ref, _, _ = hpmg.pcg(hpmg.Hierarchy(mesh, kap), b, rtol=1e-13)
     for x in xs:
         assert np.linalg.norm(x - x_ref) <= 1e-9 * np.linalg.norm(x_ref)
