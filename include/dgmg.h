@@ -63,6 +63,13 @@ extern "C" {
                                   /* accumulated in FP64, true residual recomputed in  */
                                   /* FP64 whenever the FP32 residual fell by `delta`   */
                                   /* (reliable updates) and for the stopping test      */
+#define DGMG_OUTER_MGMULT 3       /* DGMG_FP64 only: the stationary hp-multigrid       */
+                                  /* iteration (Alg. 7, MGMult): per cycle nu_pre      */
+                                  /* block-Jacobi steps and one coarse-grid correction */
+                                  /* (Alg. 6); stops when ||b - A x|| <= rtol ||b||    */
+#define DGMG_OUTER_MGMULT_PREC 4  /* as DGMG_OUTER_MGMULT, but stops on the            */
+                                  /* preconditioned residual: ||x_k - x_(k-1)|| <=     */
+                                  /* rtol ||x_1 - x_0||                                */
 
 /* block inverse used by the block-Jacobi smoother (Eq. block-Jacobi-IP) */
 #define DGMG_BLOCK_EXACT 0        /* exact diagonal block A_KK of every cell           */
@@ -102,7 +109,7 @@ typedef struct {
     double omega_dg, omega_cg;    /* damping actually used                             */
     int nu_pre, nu_post, precision, block_inverse, coarsening;
     size_t device_bytes;          /* device memory held by the ctx                     */
-    int outer;                    /* DGMG_OUTER_PCG or DGMG_OUTER_RELIABLE in use      */
+    int outer;                    /* DGMG_OUTER_* in use (AUTO resolved)               */
     int tiles[6];                 /* cells per CTA of the DG-level kernels in use:     */
                                   /* FP64 projection, smoothing, residual, then FP32   */
                                   /* (mixed precision only, else 0); a smoothing entry */
@@ -211,7 +218,10 @@ int dgmg_vcycle(dgmg_ctx *ctx, const double *r, double *e, void *stream);
  * dropped by `delta` and before stopping (outer residual, solution update and
  * coarsest solve stay FP64). Stops when ||b - A x||_2 <= rtol ||b||_2 (PCG: on
  * the recursive residual, then verified), reports the recomputed residual in
- * stats (HOST struct, may be NULL). Blocks until done (it reads one scalar per
+ * stats (HOST struct, may be NULL). DGMG_OUTER_MGMULT / _PREC run the stationary
+ * iteration instead (iterations = cycles; prec_residual = ||x_k - x_(k-1)|| /
+ * ||x_1 - x_0|| of the last cycle; rel_residual the true residual of the last
+ * cycle). Blocks until done (it reads one scalar per
  * iteration). Returns DGMG_ENOTCONVERGED after maxit iterations,
  * DGMG_ENONFINITE if a residual norm is not finite.
  */

@@ -635,6 +635,50 @@ int dg_vcycle(dgmg_ctx &C, const T *r, T *z, cudaStream_t s) {
     return DGMG_OK;
 }
 
+// One cycle of the stationary hp-multigrid iteration (Alg. 7, MGMult) in FP64:
+// nu_pre block-Jacobi steps on A x = b, then the coarse-grid correction (Alg. 6:
+// residual, p-restriction, one h-V-cycle on the Q1 levels, p-prolongation fused
+// into the projection). D.tr[0] holds the projections of x on entry and of the
+// new x on exit; r (if not NULL) receives b - A x of the new x.
+int mg_cycle64(dgmg_ctx &C, double *x, const double *b, double *r, cudaStream_t s) {
+    DGDev<double> &D = C.d64;
+    int cur = 0;
+    for (int k = 0; k < C.opts.nu_pre; ++k) {
+        C.prof.begin(ST_SMOOTH, s);
+        LC(launch_smooth<double>(C.dim, C.q, D.c, C.tile[0][TILE_SMOOTH], exact_block(C), x, b, D.kappa, D.fd,
+                                 D.linv, D.tr[cur], D.tr[cur ^ 1], s));
+        C.prof.end(s);
+        cur ^= 1;
+    }
+    C.prof.begin(ST_RESIDUAL, s);
+    LC(launch_residual<double>(C.dim, C.q, D.c, C.tile[0][TILE_RESIDUAL], RES_HAS_B | RES_CORNERS, x, b, D.kappa,
+                               D.tr[cur], nullptr, D.corners, s));
+    C.prof.end(s);
+    C.prof.begin(ST_CG, s);
+    LC(launch_corner_gather<double>(C.dim, C.n, D.corners, C.cg64[0].b, s));
+    double *e0 = nullptr;
+    RC(cg_vcycle<double>(C, 0, s, &e0));
+    C.prof.end(s);
+    C.prof.begin(ST_PROJECT, s);
+    LC(launch_project<double>(C.dim, C.q, D.c, C.tile[0][TILE_PROJECT], x, e0, D.tr[0], s));   // x += P e0
+    C.prof.end(s);
+    if (r) {
+        C.prof.begin(ST_RESIDUAL, s);
+        LC(launch_residual<double>(C.dim, C.q, D.c, C.tile[0][TILE_RESIDUAL], RES_HAS_B | RES_WRITE_R, x, b,
+                                   D.kappa, D.tr[0], r, nullptr, s));
+        C.prof.end(s);
+    }
+    return DGMG_OK;
+}
+
+// Projections of x into D.tr[0] (FP64), for a stationary cycle's first step.
+int project64(dgmg_ctx &C, double *x, cudaStream_t s) {
+    C.prof.begin(ST_PROJECT, s);
+    LC(launch_project<double>(C.dim, C.q, C.d64.c, C.tile[0][TILE_PROJECT], x, nullptr, C.d64.tr[0], s));
+    C.prof.end(s);
+    return DGMG_OK;
+}
+
 int vcycle64(dgmg_ctx &C, const double *r, double *z, cudaStream_t s) {
     if (C.opts.precision == DGMG_MIXED_FP32) {
         C.prof.begin(ST_VECTOR, s);
@@ -824,8 +868,10 @@ int dgmg_create(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_op
     if (o.coarsening != 2 && o.coarsening != 3) return fail(DGMG_EINVAL, "coarsening must be 2 or 3");
     if (!(o.rtol > 0 && o.rtol < 1)) return fail(DGMG_EINVAL, "rtol must be in (0, 1)");
     if (o.maxit < 1) return fail(DGMG_EINVAL, "maxit must be >= 1");
-    if (o.outer != DGMG_OUTER_AUTO && o.outer != DGMG_OUTER_PCG && o.outer != DGMG_OUTER_RELIABLE)
+    if (o.outer < DGMG_OUTER_AUTO || o.outer > DGMG_OUTER_MGMULT_PREC)
         return fail(DGMG_EINVAL, "unknown outer iteration");
+    if ((o.outer == DGMG_OUTER_MGMULT || o.outer == DGMG_OUTER_MGMULT_PREC) && o.precision != DGMG_FP64)
+        return fail(DGMG_EINVAL, "DGMG_OUTER_MGMULT runs in DGMG_FP64");
     if (o.outer == DGMG_OUTER_RELIABLE && o.precision != DGMG_MIXED_FP32)
         return fail(DGMG_EINVAL, "DGMG_OUTER_RELIABLE needs DGMG_MIXED_FP32");
     if (!(o.delta > 0 && o.delta < 1)) return fail(DGMG_EINVAL, "delta must be in (0, 1)");

@@ -218,6 +218,9 @@ int dg_vcycle(dgmg_ctx &C, const T *r, T *z, cudaStream_t s);
 // next stretch of device work on the run's stream and returns without waiting;
 // it returns 1 once the solve has finished (status and stats final), 0 while it
 // waits for device scalars or has more work to queue.
+int mg_cycle64(dgmg_ctx &C, double *x, const double *b, double *r, cudaStream_t s);
+int project64(dgmg_ctx &C, double *x, cudaStream_t s);
+
 struct SolveRun {
     dgmg_ctx *C = nullptr;
     const double *b = nullptr;
@@ -231,6 +234,8 @@ struct SolveRun {
     void start(dgmg_ctx *ctx, const double *b_, double *x_, cudaStream_t s_);
     int advance(bool blocking);
     int pcg_chunk(bool update_dir, cudaStream_t st);
+    int mg_chunk(cudaStream_t st);
+    double dd1 = 0;                               // MGMult: ||x_1 - x_0||^2
     int reliable_chunk(bool update_dir, cudaStream_t st);
 };
 

@@ -106,6 +106,7 @@ int scalars_ready(dgmg_ctx *C, bool blocking) {
 enum {
     P_START, P_WAIT0, P_WAIT1, P_ITER, P_WAIT_RR, P_FINAL, P_WAIT_FINAL,   // FP64 PCG
     R_START, R_WAIT0, R_ITER, R_WAIT_RR, R_WAIT_UPD, R_CONT, R_FINAL, R_WAIT_FIN,   // reliable updates
+    M_START, M_WAIT0, M_ITER, M_WAIT,                                              // MGMult
     S_DONE
 };
 
@@ -135,7 +136,10 @@ void SolveRun::start(dgmg_ctx *ctx, const double *b_, double *x_, cudaStream_t s
     need_accumulate = false;
     zz0 = zz = 0;
     t0 = std::chrono::steady_clock::now();
-    state = C->opts.outer == DGMG_OUTER_RELIABLE ? R_START : P_START;
+    dd1 = 0;
+    const int o = C->opts.outer;
+    state = o == DGMG_OUTER_RELIABLE ? R_START : (o == DGMG_OUTER_MGMULT || o == DGMG_OUTER_MGMULT_PREC) ? M_START
+                                                                                                          : P_START;
 }
 
 #define ADV_FAIL(code, msg)               \
@@ -207,6 +211,24 @@ int SolveRun::reliable_chunk(bool update_dir, cudaStream_t st) {
     LC(launch_dotf(n, p32, q32, C->partials, C->scal + S_PQ, st));
     LC(launch_update_xr_f(n, xs, r32, rold32, p32, q32, C->scal, st));
     LC(launch_dotf(n, r32, r32, C->partials, C->scal + S_RR, st));
+    C->prof.end(st);
+    return copy_scalars(C, st);
+}
+
+// One MGMult cycle's device work (Alg. 7): x_old = x, one cycle on A x = b (b
+// copied to w_rold at the start, so the captured graph does not depend on the
+// caller's b), r = b - A x, ||r||^2 and ||x - x_old||^2, scalars to the host.
+int SolveRun::mg_chunk(cudaStream_t st) {
+    const int64_t n = C->ndof;
+    double *xold = C->w_p, *dx = C->w_q, *r = C->w_r, *bc = C->w_rold;
+    C->prof.begin(ST_VECTOR, st);
+    LC(cudaMemcpyAsync(xold, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    C->prof.end(st);
+    RC(mg_cycle64(*C, x, bc, r, st));
+    C->prof.begin(ST_VECTOR, st);
+    LC(launch_dot(n, r, r, C->partials, C->scal + S_RR, st));
+    LC(launch_sub(n, x, xold, dx, st));
+    LC(launch_dot(n, dx, dx, C->partials, C->scal + S_ZZ, st));
     C->prof.end(st);
     return copy_scalars(C, st);
 }
@@ -434,6 +456,63 @@ int SolveRun::advance(bool blocking) {
                 stats.rel_residual_recursive = relrec;
                 stats.prec_residual = zz0 > 0 ? std::sqrt(zz / zz0) : 0.0;
                 stats.fp64_applies = nres;
+                stats.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+                state = S_DONE;
+                return 1;
+            }
+            // ------------------------------------------------ MGMult (Alg. 7)
+            case M_START:
+                ADV_CUDA(cudaMemcpyAsync(C->w_rold, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+                ADV(project64(*C, x, s));              // projections of the initial guess
+                ADV_CUDA(launch_dot(n, b, b, C->partials, C->scal + S_BB, s));
+                ADV(post_scalars(C, s));
+                state = M_WAIT0;
+                break;
+            case M_WAIT0: {
+                const int rdy = scalars_ready(C, blocking);
+                if (rdy < 0) ADV(rdy);
+                if (!rdy) return 0;
+                bb = C->host_scal[S_BB];
+                if (!std::isfinite(bb)) ADV_FAIL(DGMG_ENONFINITE, "||b|| is not finite");
+                bn = std::sqrt(bb) > 0 ? std::sqrt(bb) : 1.0;
+                it = 0;
+                state = M_ITER;
+                break;
+            }
+            case M_ITER:
+                ADV(run_chunk(C, C->g_body, x, s, [&](cudaStream_t st) -> int { return mg_chunk(st); }));
+                ADV_CUDA(cudaEventRecord(C->ev, s));
+                state = M_WAIT;
+                break;
+            case M_WAIT: {
+                const int rdy = scalars_ready(C, blocking);
+                if (rdy < 0) ADV(rdy);
+                if (!rdy) return 0;
+                ++it;
+                rr = C->host_scal[S_RR];
+                const double dd = C->host_scal[S_ZZ];
+                if (it == 1) dd1 = dd;
+                rel_true = relrec = std::sqrt(rr) / bn;
+                const double prec = dd1 > 0 ? std::sqrt(dd / dd1) : 0.0;
+                bool done = false;
+                if (!std::isfinite(rr) || !std::isfinite(dd)) {
+                    status = fail(DGMG_ENONFINITE, "residual norm is not finite");
+                    done = true;
+                } else if (C->opts.outer == DGMG_OUTER_MGMULT ? rel_true <= rtol : (it > 1 && prec <= rtol)) {
+                    done = true;
+                } else if (it >= C->opts.maxit) {
+                    status = fail(DGMG_ENOTCONVERGED, "maxit reached");
+                    done = true;
+                }
+                if (!done) {
+                    state = M_ITER;
+                    break;
+                }
+                stats.iterations = it;
+                stats.rel_residual = rel_true;
+                stats.rel_residual_recursive = relrec;
+                stats.prec_residual = prec;
+                stats.fp64_applies = 2 * it;
                 stats.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
                 state = S_DONE;
                 return 1;

@@ -22,6 +22,8 @@ DGMG_MIXED_FP32 = 1
 DGMG_OUTER_AUTO = 0
 DGMG_OUTER_PCG = 1
 DGMG_OUTER_RELIABLE = 2
+DGMG_OUTER_MGMULT = 3
+DGMG_OUTER_MGMULT_PREC = 4
 DGMG_PENDING = 0
 DGMG_RUNNING = 1
 DGMG_DONE = 2

@@ -56,6 +56,43 @@ def sine_rhs(ctx, device):
     return b
 
 
+def sin_product_rhs_2d(ctx, device):
+    """b = (f, phi_i) for the "sin-product" solution sin(2 pi x) sin(2 pi y) of
+    Sec. 6.4 (f = 8 pi^2 sin(2 pi x) sin(2 pi y)), through the library's quadrature."""
+    import torch
+    mq = ctx.p + 2
+    xq = torch.empty(int(ctx.info.ncell) * mq ** 2 * 2, dtype=torch.float64, device=device)
+    ctx.quad_points(xq)
+    X = xq.view(-1, 2)
+    f = 8 * math.pi ** 2 * torch.sin(2 * math.pi * X[:, 0]) * torch.sin(2 * math.pi * X[:, 1])
+    b = torch.empty(ctx.ndof, dtype=torch.float64, device=device)
+    ctx.load_vector(f.contiguous(), b)
+    return b
+
+
+def tables34(meshes=(9, 27, 81, 243), degrees=(2, 3, 4, 5, 6), nu=3, device="cuda"):
+    """MGMult cycles (Alg. 7) to reduce the unpreconditioned and the
+    preconditioned residual by 1e-7 on n x n meshes, factor-3 h-coarsening, the
+    "sin-product" right-hand side: the setting of the paper's Tables 3-4.
+    Returns {(n, p): (cycles unpreconditioned, cycles preconditioned)}."""
+    import torch
+    from . import dgmg
+    out = {}
+    for n in meshes:
+        for p in degrees:
+            ks = []
+            for outer in (dgmg.DGMG_OUTER_MGMULT, dgmg.DGMG_OUTER_MGMULT_PREC):
+                ctx = dgmg.Context((n, n), p, outer=outer, coarsening=3, nu_pre=nu, nu_post=nu, rtol=1e-7,
+                                   maxit=1000)
+                b = sin_product_rhs_2d(ctx, device)
+                x = torch.zeros_like(b)
+                st, _ = ctx.solve(b, x)
+                ks.append(int(st.iterations))
+                ctx.close()
+            out[(n, p)] = tuple(ks)
+    return out
+
+
 def make(name, device="cuda", **overrides):
     """Create (ctx, b) for a named workload."""
     from . import dgmg
@@ -93,7 +130,7 @@ def run(name, solves=3, warmup=1):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("name", choices=sorted(WORKLOADS) + ["batch", "serve"])
+    ap.add_argument("name", choices=sorted(WORKLOADS) + ["batch", "serve", "tables34"])
     ap.add_argument("--solves", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--count", type=int, default=0)
@@ -113,6 +150,9 @@ def main():
         if a.max_active:
             kw["max_active"] = a.max_active
         print(json.dumps(run_serve(**kw)))
+    elif a.name == "tables34":
+        res = tables34()
+        print(json.dumps({f"{n}x{n} p={p}": {"unprec": v[0], "prec": v[1]} for (n, p), v in res.items()}))
     else:
         print(json.dumps(run(a.name, a.solves, a.warmup)))
 
