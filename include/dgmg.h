@@ -292,6 +292,52 @@ int dgmg_server_info(dgmg_server *server, dgmg_server_info_t *info);
 /* Fail the queued requests, finish the running ones, free everything. */
 int dgmg_server_destroy(dgmg_server *server);
 
+/* ---- batched solves: independent problems sharing one launch per stage ---- */
+
+typedef struct dgmg_batch dgmg_batch;
+
+typedef struct {
+    int count;                    /* problems in the batch                             */
+    int groups;                   /* DG launch groups (one per polynomial degree)      */
+    int64_t ndof;                 /* length of the batch vectors (with padding)        */
+    size_t device_bytes;          /* device memory of the problems' hierarchies        */
+    int max_levels;               /* deepest Q1 hierarchy of the batch                 */
+    long long kernels_per_iteration; /* kernels in one CG iteration of the whole batch */
+                                  /* (0 before the first solve); independent of count  */
+} dgmg_batch_info_t;
+
+/*
+ * Build `count` independent problems (meshes[i], degree p[i] in 1..6,
+ * kappa[i]: HOST array of the mesh's ncell positive values or NULL = 1; kappa
+ * itself may be NULL) for batched solving: each problem gets its own hierarchy
+ * (as dgmg_create), and the problems of equal degree share one launch per
+ * DG-level stage (projection, smoothing step, residual + p-restriction), all
+ * problems share one launch per Q1-level stage (point Jacobi, residual,
+ * h-restriction, h-prolongation, vertex gather, dense coarsest solve). All
+ * meshes have the same dimension. opts (NULL = defaults) apply to every
+ * problem; precision must be DGMG_FP64 and nu_pre >= 1 (DGMG_EINVAL
+ * otherwise). Synchronous.
+ */
+int dgmg_batch_create(int count, const dgmg_mesh *meshes, const int *p, const double *const *kappa,
+                      const dgmg_opts *opts, dgmg_batch **out);
+
+int dgmg_batch_info(const dgmg_batch *batch, dgmg_batch_info_t *info);
+
+/*
+ * Solve A_i x_i = b_i for every problem: FP64 conjugate gradients on the
+ * direct sum of the problems, preconditioned by the batched V-cycle (a
+ * block-diagonal preconditioner: each problem's own hp V-cycle), stopping when
+ * every problem satisfies ||b_i - A_i x_i||_2 <= rtol ||b_i||_2. b[i], x[i]:
+ * DEVICE vectors of problem i (x[i] holds the initial guess and receives the
+ * solution). stats: HOST array of `count` (may be NULL); rel_residual is each
+ * problem's recomputed true residual, iterations the batch's. Blocks until
+ * done. DGMG_ENOTCONVERGED after maxit iterations.
+ */
+int dgmg_batch_solve(dgmg_batch *batch, const double *const *b, double *const *x, dgmg_stats *stats,
+                     void *stream);
+
+int dgmg_batch_destroy(dgmg_batch *batch);
+
 /* ---- stage entry points: the individual steps of the path, for testing ---- */
 
 /*

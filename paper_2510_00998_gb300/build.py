@@ -15,7 +15,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdgmg.so")
-SOURCES = ["dg_fp64.cu", "dg_fp32.cu", "ctx.cu", "solver.cu", "server.cu", "cg.cu", "blas.cu", "noalloc.cu", "refelem.cpp"]
+SOURCES = ["dg_fp64.cu", "dg_fp32.cu", "ctx.cu", "solver.cu", "server.cu", "batch.cu", "cg.cu", "blas.cu", "noalloc.cu",
+           "refelem.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,541 @@
+// Batched solves: many independent problems share one kernel launch per stage.
+//
+// dgmg_batch_create builds one ordinary hierarchy per problem (all of the
+// set-up is the single-problem code), then lays the problems out for batched
+// launches:
+//  * DG level: problems of equal degree form a group. Their DG vectors are
+//    concatenated (each problem starts at a multiple of 32 cells); every stage
+//    of the group (projection, smoothing step, residual + p-restriction) is one
+//    launch whose CTAs map, through a table, to (problem, first cell), and each
+//    CTA runs the single-problem kernel body on its problem's slice with that
+//    problem's constants and arrays.
+//  * Q1 levels: one launch per stage for all problems (all degrees); a
+//    problem's levels end at its own coarsest level, where the batched dense
+//    solve takes it, while deeper problems continue the h-cycle.
+// The outer iteration is FP64 conjugate gradients on the direct sum of the
+// problems (the batch vectors), preconditioned by the batched V-cycle; it stops
+// when every problem's residual satisfies ||b_i - A_i x_i|| <= rtol ||b_i||.
+// One iteration is captured in a CUDA graph at its second use and replayed.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <thread>
+#include <vector>
+
+#include "ctx.h"
+
+using namespace dgmg;
+
+namespace {
+
+constexpr int BATCH_ALIGN_CELLS = 32;   // one CTA of the one-thread-per-cell smoother
+
+// out[i] = sum of v[k]^2 over problem i's slice (one CTA per problem)
+__global__ void k_seg_norm2(const int64_t *__restrict__ off, const int64_t *__restrict__ len,
+                            const double *__restrict__ v, double *__restrict__ out) {
+    __shared__ double red[256];
+    const int64_t o = off[blockIdx.x], n = len[blockIdx.x];
+    double s = 0.0;
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) s += v[o + k] * v[o + k];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+}
+
+// beta = <r,z>_new / <r,z>_old; <r,z> <- <r,z>_new
+__global__ void k_batch_beta(double *scal) {
+    const double rzn = scal[S_RZN];
+    scal[S_BETA] = rzn / scal[S_RZ];
+    scal[S_RZ] = rzn;
+}
+
+}  // namespace
+
+struct dgmg_batch {
+    int count = 0, dim = 0;
+    dgmg_opts opts;
+    std::vector<dgmg_ctx *> inst;
+    std::vector<int> depth;                  // Q1 levels per problem
+    struct Group {
+        int q = 0;
+        std::vector<int> members;            // problem indices
+        int64_t cells = 0;                   // padded cells
+        int64_t dof0 = 0;                    // first DoF in the batch vectors
+        BatchDG<double> *D = nullptr;        // device, one per member
+        int tile[3] = {0, 0, 0};             // cells per CTA: projection, smoothing (0: one per thread), residual
+        BlockMap *map[3] = {nullptr, nullptr, nullptr};
+        int nblocks[3] = {0, 0, 0};
+    };
+    std::vector<Group> groups;
+    BatchCG<double> *C = nullptr;            // device, (problem, level) in order
+    struct LevelMaps {
+        VertMap *fine = nullptr, *next = nullptr, *coarse = nullptr;
+        int nfine = 0, nnext = 0, ncoarse = 0;
+    };
+    std::vector<LevelMaps> lm;
+    VertMap *gather = nullptr;
+    int ngather = 0, maxdepth = 0;
+    int64_t ndof = 0;
+    double *x = nullptr, *b = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+    std::vector<int64_t> dof_off, dof_len;
+    int64_t *d_off = nullptr, *d_len = nullptr;
+    double *d_norm = nullptr, *h_norm = nullptr;   // [count] device, pinned host
+    double *scal = nullptr, *partials = nullptr, *h_scal = nullptr;
+    cudaEvent_t ev = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long graph_kernels = 0;
+    int graph_uses = 0;
+    long long kernels_per_iteration = 0;
+    std::vector<void *> allocs;
+    size_t bytes = 0;
+
+    template <typename T>
+    int alloc(T **ptr, size_t n) {
+        *ptr = nullptr;
+        if (n == 0) n = 1;
+        cudaError_t e = cudaMalloc((void **)ptr, n * sizeof(T));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(DGMG_ENOMEM, "batch: cudaMalloc failed");
+        }
+        allocs.push_back(*ptr);
+        bytes += n * sizeof(T);
+        return DGMG_OK;
+    }
+    template <typename T>
+    int upload(T **ptr, const std::vector<T> &h) {
+        RC(alloc(ptr, h.size()));
+        if (!h.empty()) LC(cudaMemcpy(*ptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+        return DGMG_OK;
+    }
+    ~dgmg_batch() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (capture_stream) cudaStreamDestroy(capture_stream);
+        if (ev) cudaEventDestroy(ev);
+        if (h_norm) cudaFreeHost(h_norm);
+        if (h_scal) cudaFreeHost(h_scal);
+        for (void *ptr : allocs) cudaFree(ptr);
+        for (dgmg_ctx *c : inst)
+            if (c) dgmg_destroy(c);
+    }
+};
+
+namespace {
+
+// result vector of Q1 level l of problem i after its part of the h-cycle
+const double *level_result(const dgmg_batch &B, int i, int l) {
+    const CGDev<double> &L = B.inst[i]->cg64[l];
+    if (l == B.depth[i] - 1) return L.u[0];
+    return L.u[(B.opts.nu_pre + B.opts.nu_post) & 1];
+}
+
+int build_block_map(dgmg_batch &B, dgmg_batch::Group &g, int stage) {
+    const int nf = (int)(B.inst[g.members[0]]->nloc / g.q);
+    int tile = g.tile[stage];
+    if (tile <= 0) {
+        // the one-thread-per-cell smoother where it applies (3D, exact blocks, q <= 4), else ~128 threads
+        const bool cells = stage == TILE_SMOOTH && B.dim == 3 && g.q <= 4 &&
+                           B.opts.block_inverse == DGMG_BLOCK_EXACT;
+        if (cells) {
+            tile = BATCH_ALIGN_CELLS;
+        } else {
+            tile = std::max(1, 128 / nf);
+            while (tile > 1 && tile * nf > 256) --tile;
+            g.tile[stage] = tile;
+        }
+    }
+    std::vector<BlockMap> m;
+    for (size_t k = 0; k < g.members.size(); ++k) {
+        const int64_t nc = B.inst[g.members[k]]->ncell;
+        for (int64_t c0 = 0; c0 < nc; c0 += tile) m.push_back(BlockMap{(int)k, (int)c0});
+    }
+    g.nblocks[stage] = (int)m.size();
+    return B.upload(&g.map[stage], m);
+}
+
+void push_verts(std::vector<VertMap> &m, int desc, int64_t n) {
+    for (int64_t v0 = 0; v0 < n; v0 += BATCH_VERTS) m.push_back(VertMap{desc, (int)v0});
+}
+
+// ---- batched stages
+int batch_apply(dgmg_batch &B, const double *u, const double *bvec, double *out, cudaStream_t s) {
+    const int mode = bvec ? (RES_HAS_B | RES_WRITE_R) : (RES_WRITE_R | RES_NEGATE);
+    for (auto &g : B.groups) {
+        LC(launch_project_batch<double>(B.dim, g.q, g.D, g.map[TILE_PROJECT], g.nblocks[TILE_PROJECT],
+                                        g.tile[TILE_PROJECT], const_cast<double *>(u) + g.dof0, 0, s));
+        LC(launch_residual_batch<double>(B.dim, g.q, g.D, g.map[TILE_RESIDUAL], g.nblocks[TILE_RESIDUAL],
+                                         g.tile[TILE_RESIDUAL], mode, u + g.dof0, bvec ? bvec + g.dof0 : nullptr,
+                                         out + g.dof0, 0, s));
+    }
+    return DGMG_OK;
+}
+
+int batch_cg_cycle(dgmg_batch &B, int l, cudaStream_t s) {
+    const auto &m = B.lm[l];
+    const double om = B.opts.omega_cg;
+    LC(launch_coarse_solve_batch<double>(B.C, m.coarse, m.ncoarse, s));
+    if (m.nfine == 0) return DGMG_OK;
+    int cur = 0;
+    for (int k = 0; k < B.opts.nu_pre; ++k) {
+        LC(launch_cg_jacobi_batch<double>(B.dim, B.C, m.fine, m.nfine, om, k == 0, cur, s));
+        cur ^= 1;
+    }
+    LC(launch_cg_residual_batch<double>(B.dim, B.C, m.fine, m.nfine, cur, s));
+    LC(launch_h_restrict_batch<double>(B.dim, B.C, m.next, m.nnext, s));
+    RC(batch_cg_cycle(B, l + 1, s));
+    LC(launch_h_prolong_batch<double>(B.dim, B.C, m.fine, m.nfine, cur, s));
+    for (int k = 0; k < B.opts.nu_post; ++k) {
+        LC(launch_cg_jacobi_batch<double>(B.dim, B.C, m.fine, m.nfine, om, false, cur, s));
+        cur ^= 1;
+    }
+    return DGMG_OK;
+}
+
+// z = V(r) for every problem at once (zero initial guess)
+int batch_vcycle(dgmg_batch &B, const double *r, double *z, cudaStream_t s) {
+    const int exact = B.opts.block_inverse == DGMG_BLOCK_EXACT ? 1 : 0;
+    LC(cudaMemsetAsync(z, 0, sizeof(double) * B.ndof, s));
+    for (auto &g : B.groups) LC(launch_zero_traces_batch<double>(B.dim, g.q, g.D, (int)g.members.size(), s));
+    for (int k = 0; k < B.opts.nu_pre; ++k)
+        for (auto &g : B.groups)
+            LC(launch_smooth_batch<double>(B.dim, g.q, g.D, g.map[TILE_SMOOTH], g.nblocks[TILE_SMOOTH],
+                                           g.tile[TILE_SMOOTH], exact, z + g.dof0, r + g.dof0, k & 1, s));
+    for (auto &g : B.groups)
+        LC(launch_residual_batch<double>(B.dim, g.q, g.D, g.map[TILE_RESIDUAL], g.nblocks[TILE_RESIDUAL],
+                                         g.tile[TILE_RESIDUAL], RES_HAS_B | RES_CORNERS, z + g.dof0, r + g.dof0,
+                                         nullptr, B.opts.nu_pre & 1, s));
+    LC(launch_corner_gather_batch<double>(B.dim, B.C, B.gather, B.ngather, s));
+    RC(batch_cg_cycle(B, 0, s));
+    for (auto &g : B.groups)
+        LC(launch_project_batch<double>(B.dim, g.q, g.D, g.map[TILE_PROJECT], g.nblocks[TILE_PROJECT],
+                                        g.tile[TILE_PROJECT], z + g.dof0, 1, s));
+    for (int k = 0; k < B.opts.nu_post; ++k)
+        for (auto &g : B.groups)
+            LC(launch_smooth_batch<double>(B.dim, g.q, g.D, g.map[TILE_SMOOTH], g.nblocks[TILE_SMOOTH],
+                                           g.tile[TILE_SMOOTH], exact, z + g.dof0, r + g.dof0, k & 1, s));
+    return DGMG_OK;
+}
+
+int batch_norms(dgmg_batch &B, const double *v, cudaStream_t s) {
+    count_launches(1);
+    k_seg_norm2<<<B.count, 256, 0, s>>>(B.d_off, B.d_len, v, B.d_norm);
+    LC(cudaGetLastError());
+    LC(cudaMemcpyAsync(B.h_norm, B.d_norm, sizeof(double) * B.count, cudaMemcpyDeviceToHost, s));
+    return DGMG_OK;
+}
+
+// One CG iteration on the direct sum: (update_dir) z = V(r), beta, p = z + beta p;
+// q = A p, alpha, x += alpha p, r -= alpha q; per-problem ||r_i||^2 to the host.
+int batch_iteration(dgmg_batch &B, bool update_dir, cudaStream_t s) {
+    const int64_t n = B.ndof;
+    if (update_dir) {
+        RC(batch_vcycle(B, B.r, B.z, s));
+        LC(launch_dot(n, B.r, B.z, B.partials, B.scal + S_RZN, s));
+        count_launches(1);
+        k_batch_beta<<<1, 1, 0, s>>>(B.scal);
+        LC(cudaGetLastError());
+        LC(launch_pcg_update_p(n, B.p, B.z, B.scal, s));
+    }
+    RC(batch_apply(B, B.p, nullptr, B.q, s));
+    LC(launch_dot(n, B.p, B.q, B.partials, B.scal + S_PQ, s));
+    LC(launch_pcg_update_xr(n, B.x, B.r, B.p, B.q, B.scal, s));
+    return batch_norms(B, B.r, s);
+}
+
+// the steady-state iteration as one CUDA graph (captured at its second use)
+int run_iteration(dgmg_batch &B, cudaStream_t s) {
+    if (B.graph_uses++ == 0) {
+        const long long before = g_kernel_launches.load();
+        RC(batch_iteration(B, true, s));
+        B.kernels_per_iteration = g_kernel_launches.load() - before;
+        return DGMG_OK;
+    }
+    if (!B.exec) {
+        const long long before = g_kernel_launches.load();
+        LC(cudaStreamBeginCapture(B.capture_stream, cudaStreamCaptureModeRelaxed));
+        const int rc = batch_iteration(B, true, B.capture_stream);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(B.capture_stream, &graph);
+        B.graph_kernels = g_kernel_launches.load() - before;
+        g_kernel_launches.fetch_sub(B.graph_kernels);
+        if (rc != DGMG_OK || e != cudaSuccess || cudaGraphInstantiate(&B.exec, graph, 0) != cudaSuccess) {
+            // capture not possible now (e.g. invalidated from another thread): run eagerly
+            if (graph) cudaGraphDestroy(graph);
+            B.exec = nullptr;
+            cudaGetLastError();
+            B.graph_uses = 1;
+            return batch_iteration(B, true, s);
+        }
+        cudaGraphDestroy(graph);
+    }
+    LC(cudaGraphLaunch(B.exec, s));
+    count_launches((int)B.graph_kernels);
+    return DGMG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dgmg_batch_create(int count, const dgmg_mesh *meshes, const int *p, const double *const *kappa,
+                      const dgmg_opts *opts, dgmg_batch **out) {
+    if (!out) return fail(DGMG_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (count < 1) return fail(DGMG_EINVAL, "count must be >= 1");
+    if (!meshes || !p) return fail(DGMG_EINVAL, "meshes and p must not be NULL");
+    dgmg_opts o;
+    dgmg_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.precision != DGMG_FP64) return fail(DGMG_EINVAL, "batched solves run in DGMG_FP64");
+    if (o.nu_pre < 1) return fail(DGMG_EINVAL, "batched solves need nu_pre >= 1");
+    for (int i = 0; i < count; ++i)
+        if (meshes[i].dim != meshes[0].dim) return fail(DGMG_EINVAL, "all meshes of a batch have one dimension");
+    std::unique_ptr<dgmg_batch> B(new dgmg_batch());
+    B->count = count;
+    B->dim = meshes[0].dim;
+    dgmg_opts oi = o;
+    oi.outer = DGMG_OUTER_PCG;
+    oi.autotune = 0;
+    B->opts = oi;
+    // one ordinary hierarchy per problem, built on a few host threads
+    B->inst.assign(count, nullptr);
+    std::vector<int> rcs(count, DGMG_OK);
+    std::vector<std::string> errs(count);
+    {
+        const int nt = std::max(1, std::min(count, 8));
+        std::vector<std::thread> th;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        for (int t = 0; t < nt; ++t)
+            th.emplace_back([&, t]() {
+                cudaSetDevice(dev);
+                for (int i = t; i < count; i += nt) {
+                    rcs[i] = dgmg_create(&meshes[i], p[i], kappa ? kappa[i] : nullptr, &oi, &B->inst[i]);
+                    if (rcs[i] != DGMG_OK) errs[i] = dgmg_last_error();
+                }
+            });
+        for (auto &x : th) x.join();
+    }
+    for (int i = 0; i < count; ++i)
+        if (rcs[i] != DGMG_OK) return fail(rcs[i], "batch problem " + std::to_string(i) + ": " + errs[i]);
+    for (int i = 0; i < count; ++i) B->depth.push_back((int)B->inst[i]->cg64.size());
+
+    // DG groups by degree; each problem starts at a multiple of 32 cells
+    for (int i = 0; i < count; ++i) {
+        const int q = B->inst[i]->q;
+        auto it = std::find_if(B->groups.begin(), B->groups.end(), [q](const dgmg_batch::Group &g) { return g.q == q; });
+        if (it == B->groups.end()) {
+            B->groups.emplace_back();
+            B->groups.back().q = q;
+            it = B->groups.end() - 1;
+        }
+        it->members.push_back(i);
+    }
+    B->dof_off.assign(count, 0);
+    B->dof_len.assign(count, 0);
+    int64_t dof = 0;
+    for (auto &g : B->groups) {
+        g.dof0 = dof;
+        std::vector<BatchDG<double>> D;
+        int64_t cells = 0;
+        for (int i : g.members) {
+            dgmg_ctx *c = B->inst[i];
+            BatchDG<double> d{};
+            d.c = c->d64.c;
+            d.off = cells;
+            d.kappa = c->d64.kappa;
+            d.fd = c->d64.fd;
+            d.linv = c->d64.linv;
+            d.tr[0] = c->d64.tr[0];
+            d.tr[1] = c->d64.tr[1];
+            d.corners = c->d64.corners;
+            d.e0 = level_result(*B, i, 0);
+            D.push_back(d);
+            B->dof_off[i] = g.dof0 + cells * c->nloc;
+            B->dof_len[i] = c->ndof;
+            cells += (c->ncell + BATCH_ALIGN_CELLS - 1) / BATCH_ALIGN_CELLS * BATCH_ALIGN_CELLS;
+        }
+        g.cells = cells;
+        dof += cells * B->inst[g.members[0]]->nloc;
+        RC(B->upload(&g.D, D));
+        g.tile[TILE_SMOOTH] = 0;
+        for (int st = 0; st < 3; ++st) RC(build_block_map(*B, g, st));
+    }
+    B->ndof = dof;
+
+    // Q1 levels of all problems
+    std::vector<BatchCG<double>> C;
+    std::vector<std::vector<int>> desc(count);
+    for (int i = 0; i < count; ++i) {
+        dgmg_ctx *c = B->inst[i];
+        for (int l = 0; l < B->depth[i]; ++l) {
+            const CGDev<double> &L = c->cg64[l];
+            BatchCG<double> e{};
+            e.L = L.L;
+            e.u[0] = L.u[0];
+            e.u[1] = L.u[1];
+            e.b = L.b;
+            e.r = L.r;
+            const bool last = l == B->depth[i] - 1;
+            e.b_next = last ? nullptr : c->cg64[l + 1].b;
+            e.e_next = last ? nullptr : level_result(*B, i, l + 1);
+            e.Ainv = last ? c->coarse_inv : nullptr;
+            for (int a = 0; a < 3; ++a) e.n[a] = c->n[a];
+            e.corners = c->d64.corners;
+            desc[i].push_back((int)C.size());
+            C.push_back(e);
+        }
+        B->maxdepth = std::max(B->maxdepth, B->depth[i]);
+    }
+    RC(B->upload(&B->C, C));
+    {
+        std::vector<VertMap> gm;
+        for (int i = 0; i < count; ++i) push_verts(gm, desc[i][0], B->inst[i]->cg64[0].L.nv);
+        B->ngather = (int)gm.size();
+        RC(B->upload(&B->gather, gm));
+    }
+    B->lm.resize(B->maxdepth);
+    for (int l = 0; l < B->maxdepth; ++l) {
+        std::vector<VertMap> fine, next, coarse;
+        for (int i = 0; i < count; ++i) {
+            if (l >= B->depth[i]) continue;
+            const int64_t nv = B->inst[i]->cg64[l].L.nv;
+            if (l == B->depth[i] - 1) {
+                push_verts(coarse, desc[i][l], nv);
+            } else {
+                push_verts(fine, desc[i][l], nv);
+                push_verts(next, desc[i][l], B->inst[i]->cg64[l + 1].L.nv);
+            }
+        }
+        auto &m = B->lm[l];
+        m.nfine = (int)fine.size();
+        m.nnext = (int)next.size();
+        m.ncoarse = (int)coarse.size();
+        RC(B->upload(&m.fine, fine));
+        RC(B->upload(&m.next, next));
+        RC(B->upload(&m.coarse, coarse));
+    }
+
+    // batch vectors (padding stays zero), per-problem slices, scalars
+    for (double **v : {&B->x, &B->b, &B->r, &B->z, &B->p, &B->q}) {
+        RC(B->alloc(v, B->ndof));
+        LC(cudaMemset(*v, 0, sizeof(double) * B->ndof));
+    }
+    RC(B->upload(&B->d_off, B->dof_off));
+    RC(B->upload(&B->d_len, B->dof_len));
+    RC(B->alloc(&B->d_norm, count));
+    RC(B->alloc(&B->scal, S_NSCAL));
+    RC(B->alloc(&B->partials, 2 * DOT_BLOCKS));
+    LC(cudaMallocHost((void **)&B->h_norm, sizeof(double) * count));
+    LC(cudaMallocHost((void **)&B->h_scal, sizeof(double) * S_NSCAL));
+    LC(cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming));
+    LC(cudaStreamCreateWithFlags(&B->capture_stream, cudaStreamNonBlocking));
+    for (dgmg_ctx *c : B->inst) B->bytes += c->bytes;
+    LC(cudaDeviceSynchronize());
+    *out = B.release();
+    return DGMG_OK;
+}
+
+int dgmg_batch_info(const dgmg_batch *B, dgmg_batch_info_t *info) {
+    if (!B || !info) return fail(DGMG_EINVAL, "batch and info must not be NULL");
+    std::memset(info, 0, sizeof(*info));
+    info->count = B->count;
+    info->groups = (int)B->groups.size();
+    info->ndof = B->ndof;
+    info->device_bytes = B->bytes;
+    info->max_levels = B->maxdepth;
+    info->kernels_per_iteration = B->kernels_per_iteration;
+    return DGMG_OK;
+}
+
+int dgmg_batch_solve(dgmg_batch *B, const double *const *b, double *const *x, dgmg_stats *stats, void *stream) {
+    if (!B) return fail(DGMG_EINVAL, "batch is NULL");
+    if (!b || !x) return fail(DGMG_EINVAL, "b and x must not be NULL");
+    for (int i = 0; i < B->count; ++i)
+        if (!b[i] || !x[i]) return fail(DGMG_EINVAL, "b[i] and x[i] must not be NULL");
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = B->count;
+    for (int i = 0; i < n; ++i) {
+        LC(cudaMemcpyAsync(B->b + B->dof_off[i], b[i], sizeof(double) * B->dof_len[i], cudaMemcpyDeviceToDevice, s));
+        LC(cudaMemcpyAsync(B->x + B->dof_off[i], x[i], sizeof(double) * B->dof_len[i], cudaMemcpyDeviceToDevice, s));
+    }
+    std::vector<double> bn(n), rel(n);
+    RC(batch_norms(*B, B->b, s));
+    LC(cudaStreamSynchronize(s));
+    for (int i = 0; i < n; ++i) {
+        if (!std::isfinite(B->h_norm[i])) return fail(DGMG_ENONFINITE, "||b|| is not finite");
+        bn[i] = B->h_norm[i] > 0 ? std::sqrt(B->h_norm[i]) : 1.0;
+    }
+    auto converged = [&]() {
+        double worst = 0.0;
+        for (int i = 0; i < n; ++i) {
+            rel[i] = std::sqrt(B->h_norm[i]) / bn[i];
+            worst = std::max(worst, std::isfinite(rel[i]) ? rel[i] : INFINITY);
+        }
+        return worst;
+    };
+    RC(batch_apply(*B, B->x, B->b, B->r, s));   // r = b - A x
+    RC(batch_norms(*B, B->r, s));
+    LC(cudaStreamSynchronize(s));
+    double worst = converged();
+    int status = DGMG_OK, it = 0;
+    if (worst > B->opts.rtol) {
+        RC(batch_vcycle(*B, B->r, B->z, s));
+        LC(launch_dot(B->ndof, B->r, B->z, B->partials, B->scal + S_RZ, s));
+        LC(cudaMemcpyAsync(B->p, B->z, sizeof(double) * B->ndof, cudaMemcpyDeviceToDevice, s));
+        RC(batch_apply(*B, B->p, nullptr, B->q, s));
+        LC(launch_dot(B->ndof, B->p, B->q, B->partials, B->scal + S_PQ, s));
+        LC(launch_pcg_update_xr(B->ndof, B->x, B->r, B->p, B->q, B->scal, s));
+        RC(batch_norms(*B, B->r, s));
+        it = 1;
+        for (;;) {
+            LC(cudaEventRecord(B->ev, s));
+            LC(cudaEventSynchronize(B->ev));
+            worst = converged();
+            if (!std::isfinite(worst)) {
+                status = fail(DGMG_ENONFINITE, "residual norm is not finite");
+                break;
+            }
+            if (worst <= B->opts.rtol) break;
+            if (it >= B->opts.maxit) {
+                status = fail(DGMG_ENOTCONVERGED, "maxit reached");
+                break;
+            }
+            RC(run_iteration(*B, s));
+            ++it;
+        }
+    }
+    // true residuals of the returned iterates
+    RC(batch_apply(*B, B->x, B->b, B->r, s));
+    RC(batch_norms(*B, B->r, s));
+    for (int i = 0; i < n; ++i)
+        LC(cudaMemcpyAsync(x[i], B->x + B->dof_off[i], sizeof(double) * B->dof_len[i], cudaMemcpyDeviceToDevice, s));
+    LC(cudaStreamSynchronize(s));
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (stats)
+        for (int i = 0; i < n; ++i) {
+            const double recursive = rel[i];
+            std::memset(&stats[i], 0, sizeof(stats[i]));
+            stats[i].iterations = it;
+            stats[i].rel_residual = std::sqrt(B->h_norm[i]) / bn[i];
+            stats[i].rel_residual_recursive = recursive;
+            stats[i].seconds = secs;
+            stats[i].fp64_applies = it + 2;
+        }
+    return status;
+}
+
+int dgmg_batch_destroy(dgmg_batch *B) {
+    delete B;
+    return DGMG_OK;
+}
+
+}  // extern "C"

@@ -25,10 +25,10 @@ __device__ __forceinline__ void vcoords(int64_t v, const int *m, int *c) {
 // b0[v] = sum over the 2^d cells around interior vertex v of the cell's corner
 // partial sum for that vertex (fixed order: deterministic p-restriction).
 template <int DIM, typename T>
-__global__ void k_corner_gather(int n0, int n1, int n2, const T *__restrict__ corners, T *__restrict__ b0) {
+__device__ __forceinline__ void corner_gather_at(int n0, int n1, int n2, const T *__restrict__ corners,
+                                                 T *__restrict__ b0, int64_t v) {
     const int m[3] = {n0 - 1, n1 - 1, n2 - 1};
     const int64_t nv = DIM == 3 ? (int64_t)m[0] * m[1] * m[2] : (int64_t)m[0] * m[1];
-    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nv) return;
     int c[3];
     vcoords<DIM>(v, m, c);
@@ -43,6 +43,11 @@ __global__ void k_corner_gather(int n0, int n1, int n2, const T *__restrict__ co
         s += corners[cell * (1 << DIM) + corner];
     }
     b0[v] = s;
+}
+
+template <int DIM, typename T>
+__global__ void k_corner_gather(int n0, int n1, int n2, const T *__restrict__ corners, T *__restrict__ b0) {
+    corner_gather_at<DIM, T>(n0, n1, n2, corners, b0, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 template <int DIM, typename T>
@@ -63,10 +68,10 @@ __device__ __forceinline__ T stencil_apply(const CGLevelDev<T> &L, int64_t v, co
 }
 
 template <int DIM, typename T>
-__global__ void k_cg_jacobi(CGLevelDev<T> L, const T *__restrict__ u_in, const T *__restrict__ b,
-                            T *__restrict__ u_out, T omega, int zero_guess) {
+__device__ __forceinline__ void cg_jacobi_at(const CGLevelDev<T> &L, const T *__restrict__ u_in,
+                                             const T *__restrict__ b, T *__restrict__ u_out, T omega,
+                                             int zero_guess, int64_t v) {
     constexpr int NS = DIM == 3 ? 27 : 9;
-    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= L.nv) return;
     const T diag = L.st[(int64_t)(NS / 2) * L.nv + v];
     if (zero_guess) {
@@ -80,20 +85,31 @@ __global__ void k_cg_jacobi(CGLevelDev<T> L, const T *__restrict__ u_in, const T
 }
 
 template <int DIM, typename T>
-__global__ void k_cg_residual(CGLevelDev<T> L, const T *__restrict__ u, const T *__restrict__ b,
-                              T *__restrict__ r) {
-    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_cg_jacobi(CGLevelDev<T> L, const T *__restrict__ u_in, const T *__restrict__ b,
+                            T *__restrict__ u_out, T omega, int zero_guess) {
+    cg_jacobi_at<DIM, T>(L, u_in, b, u_out, omega, zero_guess, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+template <int DIM, typename T>
+__device__ __forceinline__ void cg_residual_at(const CGLevelDev<T> &L, const T *__restrict__ u,
+                                               const T *__restrict__ b, T *__restrict__ r, int64_t v) {
     if (v >= L.nv) return;
     int c[3] = {0, 0, 0};
     vcoords<DIM>(v, L.m, c);
     r[v] = b[v] - stencil_apply<DIM, T>(L, v, c, u);
 }
 
+template <int DIM, typename T>
+__global__ void k_cg_residual(CGLevelDev<T> L, const T *__restrict__ u, const T *__restrict__ b,
+                              T *__restrict__ r) {
+    cg_residual_at<DIM, T>(L, u, b, r, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // rc[V] = sum_i P_h[i][V] rf[i]: per axis, the fine children of coarse vertex V.
 template <int DIM, typename T>
-__global__ void k_h_restrict(CGLevelDev<T> L, const T *__restrict__ rf, T *__restrict__ rc) {
+__device__ __forceinline__ void h_restrict_at(const CGLevelDev<T> &L, const T *__restrict__ rf, T *__restrict__ rc,
+                                              int64_t V) {
     const int64_t ncv = DIM == 3 ? (int64_t)L.mc[0] * L.mc[1] * L.mc[2] : (int64_t)L.mc[0] * L.mc[1];
-    const int64_t V = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (V >= ncv) return;
     int C[3] = {0, 0, 0};
     vcoords<DIM>(V, L.mc, C);
@@ -112,10 +128,15 @@ __global__ void k_h_restrict(CGLevelDev<T> L, const T *__restrict__ rf, T *__res
     rc[V] = s;
 }
 
+template <int DIM, typename T>
+__global__ void k_h_restrict(CGLevelDev<T> L, const T *__restrict__ rf, T *__restrict__ rc) {
+    h_restrict_at<DIM, T>(L, rf, rc, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // uf[i] += sum_V P_h[i][V] ec[V]: per axis, the (at most two) coarse parents.
 template <int DIM, typename T>
-__global__ void k_h_prolong(CGLevelDev<T> L, const T *__restrict__ ec, T *__restrict__ uf) {
-    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void h_prolong_at(const CGLevelDev<T> &L, const T *__restrict__ ec, T *__restrict__ uf,
+                                             int64_t v) {
     if (v >= L.nv) return;
     int c[3] = {0, 0, 0};
     vcoords<DIM>(v, L.m, c);
@@ -148,15 +169,71 @@ __global__ void k_h_prolong(CGLevelDev<T> L, const T *__restrict__ ec, T *__rest
     uf[v] += s;
 }
 
+template <int DIM, typename T>
+__global__ void k_h_prolong(CGLevelDev<T> L, const T *__restrict__ ec, T *__restrict__ uf) {
+    h_prolong_at<DIM, T>(L, ec, uf, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // e = A_c^{-1} r with the explicit FP64 inverse of the coarsest operator.
 template <typename T>
-__global__ void k_coarse_solve(int64_t nc, const double *__restrict__ Ainv, const T *__restrict__ r,
-                               T *__restrict__ e) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void coarse_row(int64_t nc, const double *__restrict__ Ainv, const T *__restrict__ r,
+                                           T *__restrict__ e, int64_t i) {
     if (i >= nc) return;
     double s = 0.0;
     for (int64_t j = 0; j < nc; ++j) s += Ainv[i * nc + j] * (double)r[j];
     e[i] = (T)s;
+}
+
+template <typename T>
+__global__ void k_coarse_solve(int64_t nc, const double *__restrict__ Ainv, const T *__restrict__ r,
+                               T *__restrict__ e) {
+    coarse_row<T>(nc, Ainv, r, e, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// ---- batched forms: CTA k covers vertices [v0, v0 + BATCH_VERTS) of descriptor
+// map[k].desc (one level of one instance); all instances share the launch.
+template <int DIM, typename T>
+__global__ void __launch_bounds__(BATCH_VERTS) k_corner_gather_batch(const BatchCG<T> *__restrict__ D,
+                                                                     const VertMap *__restrict__ map) {
+    const VertMap m = map[blockIdx.x];
+    const BatchCG<T> &d = D[m.desc];
+    corner_gather_at<DIM, T>(d.n[0], d.n[1], d.n[2], d.corners, d.b, (int64_t)m.v0 + threadIdx.x);
+}
+template <int DIM, typename T>
+__global__ void __launch_bounds__(BATCH_VERTS) k_cg_jacobi_batch(const BatchCG<T> *__restrict__ D,
+                                                                 const VertMap *__restrict__ map, T omega,
+                                                                 int zero_guess, int cur) {
+    const VertMap m = map[blockIdx.x];
+    const BatchCG<T> &d = D[m.desc];
+    cg_jacobi_at<DIM, T>(d.L, d.u[cur], d.b, d.u[cur ^ 1], omega, zero_guess, (int64_t)m.v0 + threadIdx.x);
+}
+template <int DIM, typename T>
+__global__ void __launch_bounds__(BATCH_VERTS) k_cg_residual_batch(const BatchCG<T> *__restrict__ D,
+                                                                   const VertMap *__restrict__ map, int cur) {
+    const VertMap m = map[blockIdx.x];
+    const BatchCG<T> &d = D[m.desc];
+    cg_residual_at<DIM, T>(d.L, d.u[cur], d.b, d.r, (int64_t)m.v0 + threadIdx.x);
+}
+template <int DIM, typename T>
+__global__ void __launch_bounds__(BATCH_VERTS) k_h_restrict_batch(const BatchCG<T> *__restrict__ D,
+                                                                  const VertMap *__restrict__ map) {
+    const VertMap m = map[blockIdx.x];
+    const BatchCG<T> &d = D[m.desc];
+    h_restrict_at<DIM, T>(d.L, d.r, d.b_next, (int64_t)m.v0 + threadIdx.x);
+}
+template <int DIM, typename T>
+__global__ void __launch_bounds__(BATCH_VERTS) k_h_prolong_batch(const BatchCG<T> *__restrict__ D,
+                                                                 const VertMap *__restrict__ map, int cur) {
+    const VertMap m = map[blockIdx.x];
+    const BatchCG<T> &d = D[m.desc];
+    h_prolong_at<DIM, T>(d.L, d.e_next, d.u[cur], (int64_t)m.v0 + threadIdx.x);
+}
+template <typename T>
+__global__ void __launch_bounds__(BATCH_VERTS) k_coarse_solve_batch(const BatchCG<T> *__restrict__ D,
+                                                                    const VertMap *__restrict__ map) {
+    const VertMap m = map[blockIdx.x];
+    const BatchCG<T> &d = D[m.desc];
+    coarse_row<T>(d.L.nv, d.Ainv, d.b, d.u[0], (int64_t)m.v0 + threadIdx.x);
 }
 
 inline unsigned blocks_for(int64_t n) { return (unsigned)((n + TPB - 1) / TPB); }
@@ -229,6 +306,72 @@ cudaError_t launch_coarse_solve(int64_t nc, const double *Ainv, const T *r, T *e
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_corner_gather_batch(int dim, const BatchCG<T> *D, const VertMap *map, int nb, cudaStream_t s) {
+    if (nb <= 0) return cudaSuccess;
+    count_launches(1);
+    if (dim == 3)
+        k_corner_gather_batch<3, T><<<nb, BATCH_VERTS, 0, s>>>(D, map);
+    else
+        k_corner_gather_batch<2, T><<<nb, BATCH_VERTS, 0, s>>>(D, map);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cg_jacobi_batch(int dim, const BatchCG<T> *D, const VertMap *map, int nb, T omega,
+                                   bool zero_guess, int cur, cudaStream_t s) {
+    if (nb <= 0) return cudaSuccess;
+    count_launches(1);
+    if (dim == 3)
+        k_cg_jacobi_batch<3, T><<<nb, BATCH_VERTS, 0, s>>>(D, map, omega, zero_guess ? 1 : 0, cur);
+    else
+        k_cg_jacobi_batch<2, T><<<nb, BATCH_VERTS, 0, s>>>(D, map, omega, zero_guess ? 1 : 0, cur);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cg_residual_batch(int dim, const BatchCG<T> *D, const VertMap *map, int nb, int cur,
+                                     cudaStream_t s) {
+    if (nb <= 0) return cudaSuccess;
+    count_launches(1);
+    if (dim == 3)
+        k_cg_residual_batch<3, T><<<nb, BATCH_VERTS, 0, s>>>(D, map, cur);
+    else
+        k_cg_residual_batch<2, T><<<nb, BATCH_VERTS, 0, s>>>(D, map, cur);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_h_restrict_batch(int dim, const BatchCG<T> *D, const VertMap *map, int nb, cudaStream_t s) {
+    if (nb <= 0) return cudaSuccess;
+    count_launches(1);
+    if (dim == 3)
+        k_h_restrict_batch<3, T><<<nb, BATCH_VERTS, 0, s>>>(D, map);
+    else
+        k_h_restrict_batch<2, T><<<nb, BATCH_VERTS, 0, s>>>(D, map);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_h_prolong_batch(int dim, const BatchCG<T> *D, const VertMap *map, int nb, int cur,
+                                   cudaStream_t s) {
+    if (nb <= 0) return cudaSuccess;
+    count_launches(1);
+    if (dim == 3)
+        k_h_prolong_batch<3, T><<<nb, BATCH_VERTS, 0, s>>>(D, map, cur);
+    else
+        k_h_prolong_batch<2, T><<<nb, BATCH_VERTS, 0, s>>>(D, map, cur);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_coarse_solve_batch(const BatchCG<T> *D, const VertMap *map, int nb, cudaStream_t s) {
+    if (nb <= 0) return cudaSuccess;
+    count_launches(1);
+    k_coarse_solve_batch<T><<<nb, BATCH_VERTS, 0, s>>>(D, map);
+    return cudaGetLastError();
+}
+
 #define DGMG_CG_INST(T)                                                                                         \
     template cudaError_t launch_corner_gather<T>(int, const int *, const T *, T *, cudaStream_t);              \
     template cudaError_t launch_cg_jacobi<T>(int, const CGLevelDev<T> &, const T *, const T *, T *, T, bool,   \
@@ -237,7 +380,17 @@ cudaError_t launch_coarse_solve(int64_t nc, const double *Ainv, const T *r, T *e
                                                cudaStream_t);                                                  \
     template cudaError_t launch_h_restrict<T>(int, const CGLevelDev<T> &, const T *, T *, cudaStream_t);       \
     template cudaError_t launch_h_prolong<T>(int, const CGLevelDev<T> &, const T *, T *, cudaStream_t);        \
-    template cudaError_t launch_coarse_solve<T>(int64_t, const double *, const T *, T *, cudaStream_t);
+    template cudaError_t launch_coarse_solve<T>(int64_t, const double *, const T *, T *, cudaStream_t);        \
+    template cudaError_t launch_corner_gather_batch<T>(int, const BatchCG<T> *, const VertMap *, int,           \
+                                                       cudaStream_t);                                          \
+    template cudaError_t launch_cg_jacobi_batch<T>(int, const BatchCG<T> *, const VertMap *, int, T, bool, int, \
+                                                   cudaStream_t);                                              \
+    template cudaError_t launch_cg_residual_batch<T>(int, const BatchCG<T> *, const VertMap *, int, int,         \
+                                                     cudaStream_t);                                            \
+    template cudaError_t launch_h_restrict_batch<T>(int, const BatchCG<T> *, const VertMap *, int, cudaStream_t); \
+    template cudaError_t launch_h_prolong_batch<T>(int, const BatchCG<T> *, const VertMap *, int, int,          \
+                                                   cudaStream_t);                                              \
+    template cudaError_t launch_coarse_solve_batch<T>(const BatchCG<T> *, const VertMap *, int, cudaStream_t);
 
 DGMG_CG_INST(double)
 DGMG_CG_INST(float)

@@ -24,6 +24,27 @@ cudaError_t launch_residual<float>(int dim, int q, const DGConst<float> &c, int 
     return launch_residual_impl<float>(dim, q, c, cpb, mode, u, b, kappa, tr, r, corners, s);
 }
 
+template <>
+cudaError_t launch_project_batch<float>(int dim, int q, const BatchDG<float> *D, const BlockMap *map, int nblocks, int cpb,
+                                     float *u, int with_e0, cudaStream_t s) {
+    return launch_project_batch_impl<float>(dim, q, D, map, nblocks, cpb, u, with_e0, s);
+}
+template <>
+cudaError_t launch_smooth_batch<float>(int dim, int q, const BatchDG<float> *D, const BlockMap *map, int nblocks, int cpb,
+                                    int exact, float *u, const float *b, int cur, cudaStream_t s) {
+    return launch_smooth_batch_impl<float>(dim, q, D, map, nblocks, cpb, exact, u, b, cur, s);
+}
+template <>
+cudaError_t launch_residual_batch<float>(int dim, int q, const BatchDG<float> *D, const BlockMap *map, int nblocks,
+                                      int cpb, int mode, const float *u, const float *b, float *r, int cur,
+                                      cudaStream_t s) {
+    return launch_residual_batch_impl<float>(dim, q, D, map, nblocks, cpb, mode, u, b, r, cur, s);
+}
+template <>
+cudaError_t launch_zero_traces_batch<float>(int dim, int q, const BatchDG<float> *D, int count, cudaStream_t s) {
+    return launch_zero_traces_batch_impl<float>(dim, q, D, count, s);
+}
+
 cudaError_t wait_timeouts_fp32(unsigned long long *count) { return read_wait_timeouts(count); }
 
 }  // namespace dgmg

@@ -24,6 +24,27 @@ cudaError_t launch_residual<double>(int dim, int q, const DGConst<double> &c, in
     return launch_residual_impl<double>(dim, q, c, cpb, mode, u, b, kappa, tr, r, corners, s);
 }
 
+template <>
+cudaError_t launch_project_batch<double>(int dim, int q, const BatchDG<double> *D, const BlockMap *map, int nblocks, int cpb,
+                                     double *u, int with_e0, cudaStream_t s) {
+    return launch_project_batch_impl<double>(dim, q, D, map, nblocks, cpb, u, with_e0, s);
+}
+template <>
+cudaError_t launch_smooth_batch<double>(int dim, int q, const BatchDG<double> *D, const BlockMap *map, int nblocks, int cpb,
+                                    int exact, double *u, const double *b, int cur, cudaStream_t s) {
+    return launch_smooth_batch_impl<double>(dim, q, D, map, nblocks, cpb, exact, u, b, cur, s);
+}
+template <>
+cudaError_t launch_residual_batch<double>(int dim, int q, const BatchDG<double> *D, const BlockMap *map, int nblocks,
+                                      int cpb, int mode, const double *u, const double *b, double *r, int cur,
+                                      cudaStream_t s) {
+    return launch_residual_batch_impl<double>(dim, q, D, map, nblocks, cpb, mode, u, b, r, cur, s);
+}
+template <>
+cudaError_t launch_zero_traces_batch<double>(int dim, int q, const BatchDG<double> *D, int count, cudaStream_t s) {
+    return launch_zero_traces_batch_impl<double>(dim, q, D, count, s);
+}
+
 cudaError_t wait_timeouts_fp64(unsigned long long *count) { return read_wait_timeouts(count); }
 
 }  // namespace dgmg

@@ -367,14 +367,12 @@ __device__ __forceinline__ void write_pencil_traces(const DGConst<T> &c, int dir
 // (the p-prolongation fused into the projection, Sec. 5.1 "Prolongation").
 // ---------------------------------------------------------------------------
 template <int DIM, int Q, typename T>
-__global__ void __launch_bounds__(256) k_project(DGConst<T> c, int cpb, T *__restrict__ u,
-                                                  const T *__restrict__ e0, T *__restrict__ tr) {
+__device__ __forceinline__ void k_project_body(const DGConst<T> &c, int64_t cell0, int cpb, T *__restrict__ u, const T *__restrict__ e0, T *__restrict__ tr) {
     using G = Geo<DIM, Q, T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sU = reinterpret_cast<T *>(smem_raw);
     T *sE = sU + cpb * G::NL;
     const int lc = threadIdx.x / G::NF, t = threadIdx.x - lc * G::NF;
-    const int64_t cell0 = (int64_t)blockIdx.x * cpb;
     const int ncl = (int)min((int64_t)cpb, c.ncell - cell0);
     const bool active = lc < ncl;
     const int64_t cell = cell0 + lc;
@@ -440,6 +438,11 @@ __global__ void __launch_bounds__(256) k_project(DGConst<T> c, int cpb, T *__res
     }
 }
 
+template <int DIM, int Q, typename T>
+__global__ void __launch_bounds__(256) k_project(DGConst<T> c, int cpb, T *__restrict__ u, const T *__restrict__ e0, T *__restrict__ tr) {
+    k_project_body<DIM, Q, T>(c, (int64_t)blockIdx.x * cpb, cpb, u, e0, tr);
+}
+
 // ---------------------------------------------------------------------------
 // Single-touch block-Jacobi smoothing step (Alg. 4 fused loop body, Technique 5):
 //   u_K <- u_K + omega B_K^{-1} (b - A u)_K,   B_K = A_KK (exact) or the block of
@@ -457,10 +460,7 @@ __global__ void __launch_bounds__(256) k_project(DGConst<T> c, int cpb, T *__res
 // tr_out (ping-pong: every cell reads projections of the same iterate).
 // ---------------------------------------------------------------------------
 template <int DIM, int Q, typename T>
-__global__ void __launch_bounds__(256) k_smooth(DGConst<T> c, int cpb, int exact, T *__restrict__ u,
-                                                const T *__restrict__ b, const T *__restrict__ kappa,
-                                                const T *__restrict__ fd, const T *__restrict__ linv,
-                                                const T *__restrict__ tr_in, T *__restrict__ tr_out) {
+__device__ __forceinline__ void k_smooth_body(const DGConst<T> &c, int64_t cell0, int cpb, int exact, T *__restrict__ u, const T *__restrict__ b, const T *__restrict__ kappa, const T *__restrict__ fd, const T *__restrict__ linv, const T *__restrict__ tr_in, T *__restrict__ tr_out) {
     using G = Geo<DIM, Q, T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sFD = reinterpret_cast<T *>(smem_raw);   // [cpb][DIM][FDSP], 16-byte aligned blocks
@@ -472,7 +472,6 @@ __global__ void __launch_bounds__(256) k_smooth(DGConst<T> c, int cpb, int exact
     T *sB = sA + cpb * G::NL;
     T *sKT = sB + cpb * G::NL;
     const int lc = threadIdx.x / G::NF, t = threadIdx.x - lc * G::NF;
-    const int64_t cell0 = (int64_t)blockIdx.x * cpb;
     const int ncl = (int)min((int64_t)cpb, c.ncell - cell0);
     const bool active = lc < ncl;
     const int64_t cell = cell0 + lc;
@@ -615,6 +614,11 @@ __global__ void __launch_bounds__(256) k_smooth(DGConst<T> c, int cpb, int exact
     block_copy(u + cell0 * G::NL, sU, (int64_t)ncl * G::NL);
 }
 
+template <int DIM, int Q, typename T>
+__global__ void __launch_bounds__(256) k_smooth(DGConst<T> c, int cpb, int exact, T *__restrict__ u, const T *__restrict__ b, const T *__restrict__ kappa, const T *__restrict__ fd, const T *__restrict__ linv, const T *__restrict__ tr_in, T *__restrict__ tr_out) {
+    k_smooth_body<DIM, Q, T>(c, (int64_t)blockIdx.x * cpb, cpb, exact, u, b, kappa, fd, linv, tr_in, tr_out);
+}
+
 // ---------------------------------------------------------------------------
 // Residual r = b - A u (Alg. 2 stage 3 / Alg. 6 residual traversal) from u and
 // the stored projections of u, with A u = A_KK u_K + N_K u_nb, and the optional
@@ -622,10 +626,7 @@ __global__ void __launch_bounds__(256) k_smooth(DGConst<T> c, int cpb, int exact
 // per vertex afterwards in a fixed order.
 // ---------------------------------------------------------------------------
 template <int DIM, int Q, typename T>
-__global__ void __launch_bounds__(256) k_residual(DGConst<T> c, int cpb, int mode, const T *__restrict__ u,
-                                                  const T *__restrict__ b, const T *__restrict__ kappa,
-                                                  const T *__restrict__ tr, T *__restrict__ rout,
-                                                  T *__restrict__ corners) {
+__device__ __forceinline__ void k_residual_body(const DGConst<T> &c, int64_t cell0, int cpb, int mode, const T *__restrict__ u, const T *__restrict__ b, const T *__restrict__ kappa, const T *__restrict__ tr, T *__restrict__ rout, T *__restrict__ corners) {
     using G = Geo<DIM, Q, T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sU = reinterpret_cast<T *>(smem_raw);
@@ -636,7 +637,6 @@ __global__ void __launch_bounds__(256) k_residual(DGConst<T> c, int cpb, int mod
     T *sKT = sF + cpb * G::NFACE * 2 * G::NF;   // [cpb][DIM][Q*Q]
     T *sK = sKT + cpb * DIM * Q * Q;            // [cpb][NFACE + 1]
     const int lc = threadIdx.x / G::NF, t = threadIdx.x - lc * G::NF;
-    const int64_t cell0 = (int64_t)blockIdx.x * cpb;
     const int ncl = (int)min((int64_t)cpb, c.ncell - cell0);
     const bool active = lc < ncl;
     const int64_t cell = cell0 + lc;
@@ -713,12 +713,89 @@ __global__ void __launch_bounds__(256) k_residual(DGConst<T> c, int cpb, int mod
     }
 }
 
+template <int DIM, int Q, typename T>
+__global__ void __launch_bounds__(256) k_residual(DGConst<T> c, int cpb, int mode, const T *__restrict__ u, const T *__restrict__ b, const T *__restrict__ kappa, const T *__restrict__ tr, T *__restrict__ rout, T *__restrict__ corners) {
+    k_residual_body<DIM, Q, T>(c, (int64_t)blockIdx.x * cpb, cpb, mode, u, b, kappa, tr, rout, corners);
+}
+
 
 }  // namespace dgmg
 
 #include "smooth_cells.cuh"
 
 namespace dgmg {
+
+// ---------------------------------------------------------------------------
+// Batched launches: CTA k serves the cells [cell0, cell0 + tile) of instance
+// map[k].inst; it copies that instance's descriptor (constants and array
+// pointers) into shared memory and runs the same body as the single-instance
+// kernel on the instance's slice of the group vectors.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void load_batch_desc(const BatchDG<T> *__restrict__ src, BatchDG<T> *dst) {
+    static_assert(sizeof(BatchDG<T>) % 8 == 0, "descriptor copied in 8-byte words");
+    const unsigned long long *s = reinterpret_cast<const unsigned long long *>(src);
+    unsigned long long *d = reinterpret_cast<unsigned long long *>(dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(BatchDG<T>) / 8); i += blockDim.x) d[i] = s[i];
+    __syncthreads();
+}
+
+template <int DIM, int Q, typename T>
+__global__ void __launch_bounds__(256) k_project_batch(const BatchDG<T> *__restrict__ D,
+                                                        const BlockMap *__restrict__ map, int cpb, T *u,
+                                                        int with_e0) {
+    using G = Geo<DIM, Q, T>;
+    __shared__ __align__(16) BatchDG<T> sd;
+    const BlockMap m = map[blockIdx.x];
+    load_batch_desc(D + m.inst, &sd);
+    k_project_body<DIM, Q, T>(sd.c, m.cell0, cpb, u + sd.off * G::NL, with_e0 ? sd.e0 : nullptr, sd.tr[0]);
+}
+
+template <int DIM, int Q, typename T>
+__global__ void __launch_bounds__(256) k_smooth_batch(const BatchDG<T> *__restrict__ D,
+                                                       const BlockMap *__restrict__ map, int cpb, int exact, T *u,
+                                                       const T *b, int cur) {
+    using G = Geo<DIM, Q, T>;
+    __shared__ __align__(16) BatchDG<T> sd;
+    const BlockMap m = map[blockIdx.x];
+    load_batch_desc(D + m.inst, &sd);
+    k_smooth_body<DIM, Q, T>(sd.c, m.cell0, cpb, exact, u + sd.off * G::NL, b + sd.off * G::NL, sd.kappa, sd.fd,
+                             sd.linv, sd.tr[cur], sd.tr[cur ^ 1]);
+}
+
+template <typename T, int Q>
+__global__ void __launch_bounds__(32) k_smooth_cells_batch(const BatchDG<T> *__restrict__ D,
+                                                            const BlockMap *__restrict__ map, T *u, const T *b,
+                                                            int cur) {
+    constexpr int NL = Q * Q * Q;
+    __shared__ __align__(16) BatchDG<T> sd;
+    const BlockMap m = map[blockIdx.x];
+    load_batch_desc(D + m.inst, &sd);
+    smooth_cells_body<T, Q>(sd.c, m.cell0, u + sd.off * NL, b + sd.off * NL, sd.kappa, sd.fd, sd.linv,
+                            sd.tr[cur], sd.tr[cur ^ 1]);
+}
+
+template <int DIM, int Q, typename T>
+__global__ void __launch_bounds__(256) k_residual_batch(const BatchDG<T> *__restrict__ D,
+                                                         const BlockMap *__restrict__ map, int cpb, int mode,
+                                                         const T *u, const T *b, T *r, int cur) {
+    using G = Geo<DIM, Q, T>;
+    __shared__ __align__(16) BatchDG<T> sd;
+    const BlockMap m = map[blockIdx.x];
+    load_batch_desc(D + m.inst, &sd);
+    k_residual_body<DIM, Q, T>(sd.c, m.cell0, cpb, mode, u + sd.off * G::NL, b ? b + sd.off * G::NL : nullptr,
+                               sd.kappa, sd.tr[cur], r ? r + sd.off * G::NL : nullptr, sd.corners);
+}
+
+// tr[0] of instance blockIdx.x := 0 (projections of a zero iterate)
+template <int DIM, int Q, typename T>
+__global__ void k_zero_traces_batch(const BatchDG<T> *__restrict__ D) {
+    using G = Geo<DIM, Q, T>;
+    const BatchDG<T> &d = D[blockIdx.x];
+    const int64_t n = d.c.ncell * G::TR;
+    T *tr = d.tr[0];
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) tr[i] = T(0);
+}
 
 // Shared-memory bytes per CTA of each kernel.
 template <int DIM, int Q, typename T>
@@ -807,6 +884,70 @@ struct DGLaunch {
             return cudaErrorInvalidValue;
         }
     }
+    // ---- batched forms (map: one entry per CTA; cpb cells per CTA, 32 for the
+    // one-thread-per-cell smoother)
+    static cudaError_t project_batch(const BatchDG<T> *D, const BlockMap *map, int nblocks, int cpb, T *u,
+                                     int with_e0, cudaStream_t s) {
+        if (nblocks <= 0) return cudaSuccess;
+        if (cpb <= 0) cpb = default_cpb();
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_project_batch<DIM, Q, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+            attr = true;
+        }
+        count_launches(1);
+        k_project_batch<DIM, Q, T><<<nblocks, cpb * G::NF, smem_project<DIM, Q, T>(cpb), s>>>(D, map, cpb, u, with_e0);
+        return cudaGetLastError();
+    }
+    static cudaError_t smooth_batch(const BatchDG<T> *D, const BlockMap *map, int nblocks, int cpb, int exact, T *u,
+                                    const T *b, int cur, cudaStream_t s) {
+        if (nblocks <= 0) return cudaSuccess;
+        if constexpr (CELLS_OK) {
+            if (cpb <= 0 && exact) {
+                using CG = CellGeo<T, Q>;
+                static bool attr = false;
+                if (!attr) {
+                    cudaFuncSetAttribute(k_smooth_cells_batch<T, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)CG::BYTES);
+                    attr = true;
+                }
+                count_launches(1);
+                k_smooth_cells_batch<T, Q><<<nblocks, CG::W, CG::BYTES, s>>>(D, map, u, b, cur);
+                return cudaGetLastError();
+            }
+        }
+        if (cpb <= 0) return cudaErrorInvalidValue;   // the map was built for 32-cell blocks
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_smooth_batch<DIM, Q, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+            attr = true;
+        }
+        count_launches(1);
+        k_smooth_batch<DIM, Q, T><<<nblocks, cpb * G::NF, smem_smooth<DIM, Q, T>(cpb, exact != 0), s>>>(
+            D, map, cpb, exact, u, b, cur);
+        return cudaGetLastError();
+    }
+    static cudaError_t residual_batch(const BatchDG<T> *D, const BlockMap *map, int nblocks, int cpb, int mode,
+                                      const T *u, const T *b, T *r, int cur, cudaStream_t s) {
+        if (nblocks <= 0) return cudaSuccess;
+        if (cpb <= 0) cpb = default_cpb();
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_residual_batch<DIM, Q, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 160 * 1024);
+            attr = true;
+        }
+        count_launches(1);
+        k_residual_batch<DIM, Q, T><<<nblocks, cpb * G::NF, smem_residual<DIM, Q, T>(cpb), s>>>(D, map, cpb, mode, u,
+                                                                                                b, r, cur);
+        return cudaGetLastError();
+    }
+    static cudaError_t zero_traces_batch(const BatchDG<T> *D, int count, cudaStream_t s) {
+        if (count <= 0) return cudaSuccess;
+        count_launches(1);
+        k_zero_traces_batch<DIM, Q, T><<<count, 256, 0, s>>>(D);
+        return cudaGetLastError();
+    }
     static cudaError_t residual(const DGConst<T> &c, int cpb, int mode, const T *u, const T *b, const T *kappa,
                                 const T *tr, T *r, T *corners, cudaStream_t s) {
         if (cpb <= 0) cpb = default_cpb();
@@ -855,6 +996,25 @@ template <typename T>
 cudaError_t launch_residual_impl(int dim, int q, const DGConst<T> &c, int cpb, int mode, const T *u, const T *b,
                                  const T *kappa, const T *tr, T *r, T *corners, cudaStream_t s) {
     DGMG_DISPATCH(dim, q, residual(c, cpb, mode, u, b, kappa, tr, r, corners, s))
+}
+template <typename T>
+cudaError_t launch_project_batch_impl(int dim, int q, const BatchDG<T> *D, const BlockMap *map, int nblocks, int cpb,
+                                      T *u, int with_e0, cudaStream_t s) {
+    DGMG_DISPATCH(dim, q, project_batch(D, map, nblocks, cpb, u, with_e0, s))
+}
+template <typename T>
+cudaError_t launch_smooth_batch_impl(int dim, int q, const BatchDG<T> *D, const BlockMap *map, int nblocks, int cpb,
+                                     int exact, T *u, const T *b, int cur, cudaStream_t s) {
+    DGMG_DISPATCH(dim, q, smooth_batch(D, map, nblocks, cpb, exact, u, b, cur, s))
+}
+template <typename T>
+cudaError_t launch_residual_batch_impl(int dim, int q, const BatchDG<T> *D, const BlockMap *map, int nblocks,
+                                       int cpb, int mode, const T *u, const T *b, T *r, int cur, cudaStream_t s) {
+    DGMG_DISPATCH(dim, q, residual_batch(D, map, nblocks, cpb, mode, u, b, r, cur, s))
+}
+template <typename T>
+cudaError_t launch_zero_traces_batch_impl(int dim, int q, const BatchDG<T> *D, int count, cudaStream_t s) {
+    DGMG_DISPATCH(dim, q, zero_traces_batch(D, count, s))
 }
 
 }  // namespace dgmg

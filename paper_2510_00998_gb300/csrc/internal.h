@@ -84,6 +84,42 @@ struct CGLevelDev {
     int mc[3];               // interior vertices per axis of the coarser level
 };
 
+// ---- batched launches: many independent instances of one degree share a launch
+// Per instance (DG level): its constants (mesh, h-scaled 1D matrices), its first
+// cell in the group's concatenated vectors (a multiple of 32 cells, so every
+// instance's slice keeps the vectors' 16-byte alignment), and its own arrays.
+template <typename T>
+struct BatchDG {
+    DGConst<T> c;
+    int64_t off;
+    const T *kappa, *fd, *linv;
+    T *tr[2];
+    T *corners;
+    const T *e0;          // the instance's Q1 level-0 correction (p-prolongation source)
+};
+// CTA -> (instance, first cell of the CTA within the instance)
+struct BlockMap {
+    int inst, cell0;
+};
+// Per (instance, Q1 level): the level, its vectors, the next coarser level's
+// right-hand side and correction, the dense inverse on the coarsest level, and
+// (level 0) the DG mesh and cell corner sums of the p-restriction.
+template <typename T>
+struct BatchCG {
+    CGLevelDev<T> L;
+    T *u[2], *b, *r;
+    T *b_next;
+    const T *e_next;
+    const double *Ainv;
+    int n[3];
+    const T *corners;
+};
+// CTA -> (descriptor, first vertex (or row) of the CTA)
+struct VertMap {
+    int desc, v0;
+};
+constexpr int BATCH_VERTS = 256;   // vertices (rows) per CTA of the batched Q1 kernels
+
 // Launch wrappers (implemented per precision in dg_fp64.cu / dg_fp32.cu).
 // All return cudaError_t of the launch.
 template <typename T>
@@ -98,6 +134,20 @@ template <typename T>
 cudaError_t launch_residual(int dim, int q, const DGConst<T> &c, int cpb, int mode, const T *u,
                             const T *b, const T *kappa, const T *tr, T *r, T *corners,
                             cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_project_batch(int dim, int q, const BatchDG<T> *D, const BlockMap *map, int nblocks, int cpb,
+                                 T *u, int with_e0, cudaStream_t s);
+// cpb 0: the one-thread-per-cell smoother (32 cells per CTA)
+template <typename T>
+cudaError_t launch_smooth_batch(int dim, int q, const BatchDG<T> *D, const BlockMap *map, int nblocks, int cpb,
+                                int exact, T *u, const T *b, int cur, cudaStream_t s);
+template <typename T>
+cudaError_t launch_residual_batch(int dim, int q, const BatchDG<T> *D, const BlockMap *map, int nblocks, int cpb,
+                                  int mode, const T *u, const T *b, T *r, int cur, cudaStream_t s);
+// zero tr[0] of every instance (one CTA per instance)
+template <typename T>
+cudaError_t launch_zero_traces_batch(int dim, int q, const BatchDG<T> *D, int count, cudaStream_t s);
 
 // CG kernels (cg.cu)
 template <typename T>
@@ -114,6 +164,24 @@ template <typename T>
 cudaError_t launch_h_prolong(int dim, const CGLevelDev<T> &L, const T *ec, T *uf, cudaStream_t s);
 template <typename T>
 cudaError_t launch_coarse_solve(int64_t nc, const double *Ainv, const T *r, T *e, cudaStream_t s);
+// batched Q1 kernels: every CTA covers BATCH_VERTS vertices (rows) of one descriptor
+template <typename T>
+cudaError_t launch_corner_gather_batch(int dim, const BatchCG<T> *D, const VertMap *map, int nb, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cg_jacobi_batch(int dim, const BatchCG<T> *D, const VertMap *map, int nb, T omega,
+                                   bool zero_guess, int cur, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cg_residual_batch(int dim, const BatchCG<T> *D, const VertMap *map, int nb, int cur,
+                                     cudaStream_t s);
+// map over the vertices of the next coarser level
+template <typename T>
+cudaError_t launch_h_restrict_batch(int dim, const BatchCG<T> *D, const VertMap *map, int nb, cudaStream_t s);
+template <typename T>
+cudaError_t launch_h_prolong_batch(int dim, const BatchCG<T> *D, const VertMap *map, int nb, int cur,
+                                   cudaStream_t s);
+// e = u[0] = A_c^{-1} b on descriptors that are an instance's coarsest level
+template <typename T>
+cudaError_t launch_coarse_solve_batch(const BatchCG<T> *D, const VertMap *map, int nb, cudaStream_t s);
 
 // BLAS-1 and helpers (blas.cu)
 cudaError_t launch_dot(int64_t n, const double *x, const double *y, double *partials,

@@ -310,10 +310,7 @@ __device__ __forceinline__ void stage_bulk(bool full, int lane, uint64_t *bar, T
 }
 
 template <typename T, int Q>
-__global__ void __launch_bounds__(32) k_smooth_cells(const __grid_constant__ DGConst<T> c, T *__restrict__ u,
-                                                     const T *__restrict__ b, const T *__restrict__ kappa,
-                                                     const T *__restrict__ fd, const T *__restrict__ linv,
-                                                     const T *__restrict__ tr_in, T *__restrict__ tr_out) {
+__device__ __forceinline__ void smooth_cells_body(const DGConst<T> &c, int64_t cell0, T *__restrict__ u, const T *__restrict__ b, const T *__restrict__ kappa, const T *__restrict__ fd, const T *__restrict__ linv, const T *__restrict__ tr_in, T *__restrict__ tr_out) {
     using G = CellGeo<T, Q>;
     constexpr int W = G::W, NL = G::NL, NF = G::NF, FDS = G::FDS, TR = G::TR;
     extern __shared__ __align__(128) unsigned char smem_c[];
@@ -325,7 +322,6 @@ __global__ void __launch_bounds__(32) k_smooth_cells(const __grid_constant__ DGC
     __shared__ __align__(8) uint64_t bars[4];
     __shared__ T sM[3][Q * Q];
     const int lane = threadIdx.x;
-    const int64_t cell0 = (int64_t)blockIdx.x * W;
     const int ncl = (int)min((int64_t)W, c.ncell - cell0);
     const bool full = ncl == W;                          // bulk copies need whole 32-cell blocks
     const bool active = lane < ncl;
@@ -536,6 +532,14 @@ __global__ void __launch_bounds__(32) k_smooth_cells(const __grid_constant__ DGC
         if (p < 2) rotate<T, Q>(R);
     }
     if (full && lane == 0) bulk_wait_read_all();
+}
+
+template <typename T, int Q>
+__global__ void __launch_bounds__(32) k_smooth_cells(const __grid_constant__ DGConst<T> c, T *__restrict__ u,
+                                                     const T *__restrict__ b, const T *__restrict__ kappa,
+                                                     const T *__restrict__ fd, const T *__restrict__ linv,
+                                                     const T *__restrict__ tr_in, T *__restrict__ tr_out) {
+    smooth_cells_body<T, Q>(c, (int64_t)blockIdx.x * CellGeo<T, Q>::W, u, b, kappa, fd, linv, tr_in, tr_out);
 }
 
 // Host-side read of the timeout counter of this translation unit.

@@ -73,6 +73,12 @@ class ServerInfo(ctypes.Structure):
                 ("evictions", ctypes.c_longlong), ("bytes_in_use", ctypes.c_size_t), ("budget", ctypes.c_size_t)]
 
 
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int), ("groups", ctypes.c_int), ("ndof", ctypes.c_int64),
+                ("device_bytes", ctypes.c_size_t), ("max_levels", ctypes.c_int),
+                ("kernels_per_iteration", ctypes.c_longlong)]
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _D = ctypes.c_double
@@ -107,6 +113,10 @@ _SIGS = {
     "dgmg_poll": (_I, [_P, ctypes.c_uint64, ctypes.POINTER(_I), ctypes.POINTER(Stats)]),
     "dgmg_server_info": (_I, [_P, ctypes.POINTER(ServerInfo)]),
     "dgmg_server_destroy": (_I, [_P]),
+    "dgmg_batch_create": (_I, [_I, _P, _P, _P, ctypes.POINTER(Opts), ctypes.POINTER(_P)]),
+    "dgmg_batch_info": (_I, [_P, ctypes.POINTER(BatchInfo)]),
+    "dgmg_batch_solve": (_I, [_P, _P, _P, _P, _P]),
+    "dgmg_batch_destroy": (_I, [_P]),
     "dgmg_profile": (_I, [_P, _I]),
     "dgmg_profile_read": (_I, [_P, _P, _P, _I]),
     "dgmg_kernel_launches": (ctypes.c_longlong, []),
@@ -237,6 +247,63 @@ class Server:
     def close(self):
         if getattr(self, "h", None):
             self.lib.dgmg_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """A dgmg_batch: independent problems solved together, one launch per stage."""
+
+    def __init__(self, problems, **opts):
+        """problems: list of (n, p, kappa or None); all meshes of one dimension."""
+        import numpy as np
+        self.lib = load()
+        self.opts = _opts(**opts)
+        k = len(problems)
+        meshes = (Mesh * k)()
+        ps = (ctypes.c_int * k)()
+        kps = (ctypes.c_void_p * k)()
+        self._kappa_keep = []
+        for i, (n, p, kappa) in enumerate(problems):
+            meshes[i] = _mesh(n)
+            ps[i] = int(p)
+            if kappa is not None:
+                a = np.ascontiguousarray(np.asarray(kappa, dtype=np.float64).reshape(-1))
+                self._kappa_keep.append(a)
+                kps[i] = a.ctypes.data
+        h = ctypes.c_void_p()
+        _check(self.lib.dgmg_batch_create(k, ctypes.cast(meshes, _P), ctypes.cast(ps, _P), ctypes.cast(kps, _P),
+                                          ctypes.byref(self.opts), ctypes.byref(h)))
+        self.h = h
+        self.count = k
+
+    def info(self):
+        inf = BatchInfo()
+        _check(self.lib.dgmg_batch_info(self.h, ctypes.byref(inf)))
+        return inf
+
+    def solve(self, bs, xs, stream=None, allow_notconverged=False):
+        """bs, xs: lists of contiguous CUDA float64 tensors, one per problem.
+        Returns (list of Stats, return code)."""
+        k = self.count
+        if len(bs) != k or len(xs) != k:
+            raise ValueError("one b and one x per problem")
+        bp = (ctypes.c_void_p * k)(*[t.data_ptr() for t in bs])
+        xp = (ctypes.c_void_p * k)(*[t.data_ptr() for t in xs])
+        st = (Stats * k)()
+        allow = (DGMG_ENOTCONVERGED,) if allow_notconverged else ()
+        rc = _check(self.lib.dgmg_batch_solve(self.h, ctypes.cast(bp, _P), ctypes.cast(xp, _P), ctypes.cast(st, _P),
+                                              _stream(stream)), allow)
+        return list(st), rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dgmg_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):
