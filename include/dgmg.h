@@ -304,6 +304,9 @@ typedef struct {
     int max_levels;               /* deepest Q1 hierarchy of the batch                 */
     long long kernels_per_iteration; /* kernels in one CG iteration of the whole batch */
                                   /* (0 before the first solve); independent of count  */
+    int group_q[4];               /* nodes per axis of the first four groups           */
+    int group_tiles[4][3];        /* their cells per CTA: projection, smoothing (0 =   */
+                                  /* one thread per cell), residual                    */
 } dgmg_batch_info_t;
 
 /*
@@ -316,7 +319,8 @@ typedef struct {
  * h-restriction, h-prolongation, vertex gather, dense coarsest solve). All
  * meshes have the same dimension. opts (NULL = defaults) apply to every
  * problem; precision must be DGMG_FP64 and nu_pre >= 1 (DGMG_EINVAL
- * otherwise). Synchronous.
+ * otherwise). With opts->autotune the cells per CTA of each group's launches
+ * are timed and chosen on the batch itself. Synchronous.
  */
 int dgmg_batch_create(int count, const dgmg_mesh *meshes, const int *p, const double *const *kappa,
                       const dgmg_opts *opts, dgmg_batch **out);
@@ -324,14 +328,14 @@ int dgmg_batch_create(int count, const dgmg_mesh *meshes, const int *p, const do
 int dgmg_batch_info(const dgmg_batch *batch, dgmg_batch_info_t *info);
 
 /*
- * Solve A_i x_i = b_i for every problem: FP64 conjugate gradients on the
- * direct sum of the problems, preconditioned by the batched V-cycle (a
- * block-diagonal preconditioner: each problem's own hp V-cycle), stopping when
- * every problem satisfies ||b_i - A_i x_i||_2 <= rtol ||b_i||_2. b[i], x[i]:
- * DEVICE vectors of problem i (x[i] holds the initial guess and receives the
- * solution). stats: HOST array of `count` (may be NULL); rel_residual is each
- * problem's recomputed true residual, iterations the batch's. Blocks until
- * done. DGMG_ENOTCONVERGED after maxit iterations.
+ * Solve A_i x_i = b_i for every problem: FP64 preconditioned conjugate
+ * gradients with the problem's own hp V-cycle, one CG recurrence per problem
+ * (its own alpha and beta), all problems advanced by the same batched
+ * launches; a problem that met ||b_i - A_i x_i||_2 <= rtol ||b_i||_2 stops
+ * changing while the others continue. b[i], x[i]: DEVICE vectors of problem i
+ * (x[i] holds the initial guess and receives the solution). stats: HOST array
+ * of `count` (may be NULL): each problem's iterations and recomputed true
+ * residual. Blocks until done. DGMG_ENOTCONVERGED after maxit iterations.
  */
 int dgmg_batch_solve(dgmg_batch *batch, const double *const *b, double *const *x, dgmg_stats *stats,
                      void *stream);

@@ -12,10 +12,13 @@
 //  * Q1 levels: one launch per stage for all problems (all degrees); a
 //    problem's levels end at its own coarsest level, where the batched dense
 //    solve takes it, while deeper problems continue the h-cycle.
-// The outer iteration is FP64 conjugate gradients on the direct sum of the
-// problems (the batch vectors), preconditioned by the batched V-cycle; it stops
-// when every problem's residual satisfies ||b_i - A_i x_i|| <= rtol ||b_i||.
-// One iteration is captured in a CUDA graph at its second use and replayed.
+// The outer iteration is FP64 preconditioned conjugate gradients with the
+// batched V-cycle, one recurrence per problem (per-problem dot products, alpha
+// and beta, from segmented kernels over the batch vectors): every problem
+// follows exactly its own PCG, and a problem that met ||b_i - A_i x_i|| <=
+// rtol ||b_i|| is frozen on the device while the others continue. One
+// iteration of the whole batch is captured in a CUDA graph at its second use
+// and replayed.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -32,27 +35,86 @@ namespace {
 
 constexpr int BATCH_ALIGN_CELLS = 32;   // one CTA of the one-thread-per-cell smoother
 
-// out[i] = sum of v[k]^2 over problem i's slice (one CTA per problem)
-__global__ void k_seg_norm2(const int64_t *__restrict__ off, const int64_t *__restrict__ len,
-                            const double *__restrict__ v, double *__restrict__ out) {
+// Per-problem CG: every problem runs its own conjugate-gradient recurrence
+// (its own alpha and beta); a problem whose residual met its bound is frozen
+// (active = 0) and its x, r and p are left untouched.
+constexpr int SEG_BLOCKS = 16;   // CTAs per problem of the segmented kernels
+
+// part[i][blockIdx.x] = partial sum of a*b over problem i = blockIdx.y
+__global__ void k_seg_dot_partial(const int64_t *__restrict__ off, const int64_t *__restrict__ len,
+                                  const double *__restrict__ a, const double *__restrict__ b,
+                                  double *__restrict__ part) {
     __shared__ double red[256];
-    const int64_t o = off[blockIdx.x], n = len[blockIdx.x];
+    const int i = blockIdx.y;
+    const int64_t o = off[i], n = len[i];
     double s = 0.0;
-    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) s += v[o + k] * v[o + k];
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        s += a[o + k] * b[o + k];
     red[threadIdx.x] = s;
     __syncthreads();
     for (int w = 128; w > 0; w >>= 1) {
         if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+    if (threadIdx.x == 0) part[(int64_t)i * SEG_BLOCKS + blockIdx.x] = red[0];
 }
 
-// beta = <r,z>_new / <r,z>_old; <r,z> <- <r,z>_new
-__global__ void k_batch_beta(double *scal) {
-    const double rzn = scal[S_RZN];
-    scal[S_BETA] = rzn / scal[S_RZ];
-    scal[S_RZ] = rzn;
+// out[i] = sum of the SEG_BLOCKS partials of problem i (fixed order)
+__global__ void k_seg_dot_final(int count, const double *__restrict__ part, double *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    double s = 0.0;
+    for (int k = 0; k < SEG_BLOCKS; ++k) s += part[(int64_t)i * SEG_BLOCKS + k];
+    out[i] = s;
+}
+
+// active problems: beta = <r,z>_new / <r,z>; <r,z> <- <r,z>_new
+__global__ void k_seg_beta(int count, const int *__restrict__ active, double *__restrict__ rz,
+                           const double *__restrict__ rzn, double *__restrict__ beta) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    if (!active[i]) {
+        beta[i] = 0.0;
+        return;
+    }
+    beta[i] = rzn[i] / rz[i];
+    rz[i] = rzn[i];
+}
+
+// active problems: p = z + beta p
+__global__ void k_seg_update_p(const int64_t *__restrict__ off, const int64_t *__restrict__ len,
+                               const int *__restrict__ active, const double *__restrict__ beta, double *__restrict__ p,
+                               const double *__restrict__ z) {
+    const int i = blockIdx.y;
+    if (!active[i]) return;
+    const int64_t o = off[i], n = len[i];
+    const double bt = beta[i];
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        p[o + k] = z[o + k] + bt * p[o + k];
+}
+
+// active problems: alpha = <r,z> / <p,q>; x += alpha p; r -= alpha q
+__global__ void k_seg_update_xr(const int64_t *__restrict__ off, const int64_t *__restrict__ len,
+                                const int *__restrict__ active, const double *__restrict__ rz,
+                                const double *__restrict__ pq, double *__restrict__ x, double *__restrict__ r,
+                                const double *__restrict__ p, const double *__restrict__ q) {
+    const int i = blockIdx.y;
+    if (!active[i]) return;
+    const int64_t o = off[i], n = len[i];
+    const double alpha = rz[i] / pq[i];
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        x[o + k] += alpha * p[o + k];
+        r[o + k] -= alpha * q[o + k];
+    }
+}
+
+// active[i] = ||r_i||^2 > rtol^2 ||b_i||^2 (and finite)
+__global__ void k_seg_flags(int count, const double *__restrict__ rr, const double *__restrict__ bb, double rtol2,
+                            int *__restrict__ active) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const double v = rr[i];
+    active[i] = (v > rtol2 * bb[i] && v == v) ? 1 : 0;
 }
 
 }  // namespace
@@ -86,7 +148,9 @@ struct dgmg_batch {
     std::vector<int64_t> dof_off, dof_len;
     int64_t *d_off = nullptr, *d_len = nullptr;
     double *d_norm = nullptr, *h_norm = nullptr;   // [count] device, pinned host
-    double *scal = nullptr, *partials = nullptr, *h_scal = nullptr;
+    double *d_bb = nullptr;                        // ||b_i||^2 (zero b: 1)
+    double *rz = nullptr, *rzn = nullptr, *pq = nullptr, *beta = nullptr, *part = nullptr;
+    int *active = nullptr;
     cudaEvent_t ev = nullptr;
     cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -120,7 +184,6 @@ struct dgmg_batch {
         if (capture_stream) cudaStreamDestroy(capture_stream);
         if (ev) cudaEventDestroy(ev);
         if (h_norm) cudaFreeHost(h_norm);
-        if (h_scal) cudaFreeHost(h_scal);
         for (void *ptr : allocs) cudaFree(ptr);
         for (dgmg_ctx *c : inst)
             if (c) dgmg_destroy(c);
@@ -158,6 +221,61 @@ int build_block_map(dgmg_batch &B, dgmg_batch::Group &g, int stage) {
     }
     g.nblocks[stage] = (int)m.size();
     return B.upload(&g.map[stage], m);
+}
+
+// Tile autotuning of a group's DG-level launches (opts.autotune): every
+// candidate cells-per-CTA value (and, for the smoothing step, the
+// one-thread-per-cell kernel) is timed on the batch's own buffers, one warm-up
+// and three timed launches; the fastest is kept.
+int tune_group(dgmg_batch &B, dgmg_batch::Group &g, cudaStream_t s) {
+    const int nf = (int)(B.inst[g.members[0]]->nloc / g.q);
+    const int exact = B.opts.block_inverse == DGMG_BLOCK_EXACT ? 1 : 0;
+    std::vector<int> cand;
+    for (int c = 1; c <= 64; c *= 2)
+        if (c * nf >= 32 && c * nf <= 256) cand.push_back(c);
+    if (cand.empty()) cand.push_back(std::max(1, 128 / nf));
+    cudaEvent_t e0, e1;
+    LC(cudaEventCreate(&e0));
+    LC(cudaEventCreate(&e1));
+    double *u = B.z + g.dof0, *bv = B.r + g.dof0;
+    for (int st = 0; st < 3; ++st) {
+        std::vector<int> cs = cand;
+        if (st == TILE_SMOOTH && B.dim == 3 && g.q <= 4 && exact) cs.insert(cs.begin(), 0);
+        int best = cs[0];
+        float best_ms = 1e30f;
+        for (int c : cs) {
+            g.tile[st] = c;
+            RC(build_block_map(B, g, st));
+            auto launch = [&]() -> cudaError_t {
+                if (st == TILE_PROJECT)
+                    return launch_project_batch<double>(B.dim, g.q, g.D, g.map[st], g.nblocks[st], g.tile[st], u, 0, s);
+                if (st == TILE_SMOOTH)
+                    return launch_smooth_batch<double>(B.dim, g.q, g.D, g.map[st], g.nblocks[st], g.tile[st], exact,
+                                                       u, bv, 0, s);
+                return launch_residual_batch<double>(B.dim, g.q, g.D, g.map[st], g.nblocks[st], g.tile[st],
+                                                     RES_HAS_B | RES_CORNERS, u, bv, nullptr, 0, s);
+            };
+            float ms = 1e30f;
+            if (launch() == cudaSuccess) {
+                cudaEventRecord(e0, s);
+                bool ok = true;
+                for (int k = 0; k < 3 && ok; ++k) ok = launch() == cudaSuccess;
+                cudaEventRecord(e1, s);
+                if (ok && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+            }
+            cudaGetLastError();
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+        g.tile[st] = best;
+        RC(build_block_map(B, g, st));
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    LC(cudaStreamSynchronize(s));
+    return DGMG_OK;
 }
 
 void push_verts(std::vector<VertMap> &m, int desc, int64_t n) {
@@ -223,44 +341,63 @@ int batch_vcycle(dgmg_batch &B, const double *r, double *z, cudaStream_t s) {
     return DGMG_OK;
 }
 
+unsigned small_grid(int count) { return (unsigned)((count + 127) / 128); }
+
+// out[i] = <a_i, b_i> for every problem (deterministic: fixed partial order)
+int seg_dot(dgmg_batch &B, const double *a, const double *b, double *out, cudaStream_t s) {
+    count_launches(2);
+    k_seg_dot_partial<<<dim3(SEG_BLOCKS, B.count), 256, 0, s>>>(B.d_off, B.d_len, a, b, B.part);
+    k_seg_dot_final<<<small_grid(B.count), 128, 0, s>>>(B.count, B.part, out);
+    LC(cudaGetLastError());
+    return DGMG_OK;
+}
+
+// ||v_i||^2 of every problem to the host (pinned) and the active flags
 int batch_norms(dgmg_batch &B, const double *v, cudaStream_t s) {
+    RC(seg_dot(B, v, v, B.d_norm, s));
     count_launches(1);
-    k_seg_norm2<<<B.count, 256, 0, s>>>(B.d_off, B.d_len, v, B.d_norm);
+    k_seg_flags<<<small_grid(B.count), 128, 0, s>>>(B.count, B.d_norm, B.d_bb, B.opts.rtol * B.opts.rtol, B.active);
     LC(cudaGetLastError());
     LC(cudaMemcpyAsync(B.h_norm, B.d_norm, sizeof(double) * B.count, cudaMemcpyDeviceToHost, s));
     return DGMG_OK;
 }
 
-// One CG iteration on the direct sum: (update_dir) z = V(r), beta, p = z + beta p;
-// q = A p, alpha, x += alpha p, r -= alpha q; per-problem ||r_i||^2 to the host.
-int batch_iteration(dgmg_batch &B, bool update_dir, cudaStream_t s) {
-    const int64_t n = B.ndof;
-    if (update_dir) {
-        RC(batch_vcycle(B, B.r, B.z, s));
-        LC(launch_dot(n, B.r, B.z, B.partials, B.scal + S_RZN, s));
-        count_launches(1);
-        k_batch_beta<<<1, 1, 0, s>>>(B.scal);
-        LC(cudaGetLastError());
-        LC(launch_pcg_update_p(n, B.p, B.z, B.scal, s));
-    }
+// alpha step of every active problem: q = A p, <p,q>, x += alpha p, r -= alpha q,
+// then ||r_i||^2 and the flags
+int alpha_step(dgmg_batch &B, cudaStream_t s) {
     RC(batch_apply(B, B.p, nullptr, B.q, s));
-    LC(launch_dot(n, B.p, B.q, B.partials, B.scal + S_PQ, s));
-    LC(launch_pcg_update_xr(n, B.x, B.r, B.p, B.q, B.scal, s));
+    RC(seg_dot(B, B.p, B.q, B.pq, s));
+    count_launches(1);
+    k_seg_update_xr<<<dim3(SEG_BLOCKS * 4, B.count), 256, 0, s>>>(B.d_off, B.d_len, B.active, B.rz, B.pq, B.x,
+                                                                    B.r, B.p, B.q);
+    LC(cudaGetLastError());
     return batch_norms(B, B.r, s);
+}
+
+// One CG iteration of every active problem: z = V(r), beta, p = z + beta p, then
+// the alpha step.
+int batch_iteration(dgmg_batch &B, cudaStream_t s) {
+    RC(batch_vcycle(B, B.r, B.z, s));
+    RC(seg_dot(B, B.r, B.z, B.rzn, s));
+    count_launches(2);
+    k_seg_beta<<<small_grid(B.count), 128, 0, s>>>(B.count, B.active, B.rz, B.rzn, B.beta);
+    k_seg_update_p<<<dim3(SEG_BLOCKS * 4, B.count), 256, 0, s>>>(B.d_off, B.d_len, B.active, B.beta, B.p, B.z);
+    LC(cudaGetLastError());
+    return alpha_step(B, s);
 }
 
 // the steady-state iteration as one CUDA graph (captured at its second use)
 int run_iteration(dgmg_batch &B, cudaStream_t s) {
     if (B.graph_uses++ == 0) {
         const long long before = g_kernel_launches.load();
-        RC(batch_iteration(B, true, s));
+        RC(batch_iteration(B, s));
         B.kernels_per_iteration = g_kernel_launches.load() - before;
         return DGMG_OK;
     }
     if (!B.exec) {
         const long long before = g_kernel_launches.load();
         LC(cudaStreamBeginCapture(B.capture_stream, cudaStreamCaptureModeRelaxed));
-        const int rc = batch_iteration(B, true, B.capture_stream);
+        const int rc = batch_iteration(B, B.capture_stream);
         cudaGraph_t graph = nullptr;
         const cudaError_t e = cudaStreamEndCapture(B.capture_stream, &graph);
         B.graph_kernels = g_kernel_launches.load() - before;
@@ -271,7 +408,7 @@ int run_iteration(dgmg_batch &B, cudaStream_t s) {
             B.exec = nullptr;
             cudaGetLastError();
             B.graph_uses = 1;
-            return batch_iteration(B, true, s);
+            return batch_iteration(B, s);
         }
         cudaGraphDestroy(graph);
     }
@@ -430,15 +567,16 @@ int dgmg_batch_create(int count, const dgmg_mesh *meshes, const int *p, const do
     }
     RC(B->upload(&B->d_off, B->dof_off));
     RC(B->upload(&B->d_len, B->dof_len));
-    RC(B->alloc(&B->d_norm, count));
-    RC(B->alloc(&B->scal, S_NSCAL));
-    RC(B->alloc(&B->partials, 2 * DOT_BLOCKS));
+    for (double **v : {&B->d_norm, &B->d_bb, &B->rz, &B->rzn, &B->pq, &B->beta}) RC(B->alloc(v, count));
+    RC(B->alloc(&B->part, (size_t)count * SEG_BLOCKS));
+    RC(B->alloc(&B->active, count));
     LC(cudaMallocHost((void **)&B->h_norm, sizeof(double) * count));
-    LC(cudaMallocHost((void **)&B->h_scal, sizeof(double) * S_NSCAL));
     LC(cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming));
     LC(cudaStreamCreateWithFlags(&B->capture_stream, cudaStreamNonBlocking));
     for (dgmg_ctx *c : B->inst) B->bytes += c->bytes;
     LC(cudaDeviceSynchronize());
+    if (o.autotune)
+        for (auto &g : B->groups) RC(tune_group(*B, g, B->capture_stream));
     *out = B.release();
     return DGMG_OK;
 }
@@ -452,6 +590,10 @@ int dgmg_batch_info(const dgmg_batch *B, dgmg_batch_info_t *info) {
     info->device_bytes = B->bytes;
     info->max_levels = B->maxdepth;
     info->kernels_per_iteration = B->kernels_per_iteration;
+    for (size_t k = 0; k < B->groups.size() && k < 4; ++k) {
+        info->group_q[k] = B->groups[k].q;
+        for (int st = 0; st < 3; ++st) info->group_tiles[k][st] = B->groups[k].tile[st];
+    }
     return DGMG_OK;
 }
 
@@ -468,12 +610,16 @@ int dgmg_batch_solve(dgmg_batch *B, const double *const *b, double *const *x, dg
         LC(cudaMemcpyAsync(B->x + B->dof_off[i], x[i], sizeof(double) * B->dof_len[i], cudaMemcpyDeviceToDevice, s));
     }
     std::vector<double> bn(n), rel(n);
-    RC(batch_norms(*B, B->b, s));
+    RC(seg_dot(*B, B->b, B->b, B->d_norm, s));
+    LC(cudaMemcpyAsync(B->h_norm, B->d_norm, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
     LC(cudaStreamSynchronize(s));
+    std::vector<double> bb(n);
     for (int i = 0; i < n; ++i) {
         if (!std::isfinite(B->h_norm[i])) return fail(DGMG_ENONFINITE, "||b|| is not finite");
         bn[i] = B->h_norm[i] > 0 ? std::sqrt(B->h_norm[i]) : 1.0;
+        bb[i] = bn[i] * bn[i];
     }
+    LC(cudaMemcpyAsync(B->d_bb, bb.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
     auto converged = [&]() {
         double worst = 0.0;
         for (int i = 0; i < n; ++i) {
@@ -487,19 +633,23 @@ int dgmg_batch_solve(dgmg_batch *B, const double *const *b, double *const *x, dg
     LC(cudaStreamSynchronize(s));
     double worst = converged();
     int status = DGMG_OK, it = 0;
+    std::vector<int> its(n, -1);              // iteration at which each problem met its bound
+    auto mark = [&]() {
+        for (int i = 0; i < n; ++i)
+            if (its[i] < 0 && rel[i] <= B->opts.rtol) its[i] = it;
+    };
+    mark();
     if (worst > B->opts.rtol) {
         RC(batch_vcycle(*B, B->r, B->z, s));
-        LC(launch_dot(B->ndof, B->r, B->z, B->partials, B->scal + S_RZ, s));
+        RC(seg_dot(*B, B->r, B->z, B->rz, s));
         LC(cudaMemcpyAsync(B->p, B->z, sizeof(double) * B->ndof, cudaMemcpyDeviceToDevice, s));
-        RC(batch_apply(*B, B->p, nullptr, B->q, s));
-        LC(launch_dot(B->ndof, B->p, B->q, B->partials, B->scal + S_PQ, s));
-        LC(launch_pcg_update_xr(B->ndof, B->x, B->r, B->p, B->q, B->scal, s));
-        RC(batch_norms(*B, B->r, s));
+        RC(alpha_step(*B, s));
         it = 1;
         for (;;) {
             LC(cudaEventRecord(B->ev, s));
             LC(cudaEventSynchronize(B->ev));
             worst = converged();
+            mark();
             if (!std::isfinite(worst)) {
                 status = fail(DGMG_ENONFINITE, "residual norm is not finite");
                 break;
@@ -524,7 +674,7 @@ int dgmg_batch_solve(dgmg_batch *B, const double *const *b, double *const *x, dg
         for (int i = 0; i < n; ++i) {
             const double recursive = rel[i];
             std::memset(&stats[i], 0, sizeof(stats[i]));
-            stats[i].iterations = it;
+            stats[i].iterations = its[i] >= 0 ? its[i] : it;
             stats[i].rel_residual = std::sqrt(B->h_norm[i]) / bn[i];
             stats[i].rel_residual_recursive = recursive;
             stats[i].seconds = secs;

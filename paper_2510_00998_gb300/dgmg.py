@@ -76,7 +76,8 @@ class ServerInfo(ctypes.Structure):
 class BatchInfo(ctypes.Structure):
     _fields_ = [("count", ctypes.c_int), ("groups", ctypes.c_int), ("ndof", ctypes.c_int64),
                 ("device_bytes", ctypes.c_size_t), ("max_levels", ctypes.c_int),
-                ("kernels_per_iteration", ctypes.c_longlong)]
+                ("kernels_per_iteration", ctypes.c_longlong), ("group_q", ctypes.c_int * 4),
+                ("group_tiles", (ctypes.c_int * 3) * 4)]
 
 
 _P = ctypes.c_void_p

@@ -234,9 +234,10 @@ def build_rhs(reqs, device="cuda"):
         ctx.close()
 
 
-def one_at_a_time(reqs, precision=0):
+def one_at_a_time(reqs, precision=0, solve_times=None):
     """Solve every request alone in order (create, solve, destroy); returns the
-    per-request service times in seconds (set-up included)."""
+    per-request service times in seconds (set-up included). With a list as
+    `solve_times`, the solve-only time of each request is appended to it."""
     import torch
     from . import dgmg
     times = []
@@ -245,12 +246,39 @@ def one_at_a_time(reqs, precision=0):
         t = time.perf_counter()
         ctx = dgmg.Context(r["n"], r["p"], r["kappa"], precision=precision)
         x = torch.zeros_like(r["b"])
+        ts = time.perf_counter()
         st, _ = ctx.solve(r["b"], x)
+        if solve_times is not None:
+            solve_times.append(time.perf_counter() - ts)
         ctx.close()
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t)
         assert st.rel_residual <= 1e-10, st.rel_residual
     return times
+
+
+def batched(reqs, solves=2):
+    """All requests as one dgmg_batch (FP64): set-up time, then `solves` batched
+    solves from x = 0 (the second and later replay the captured iteration).
+    Returns (setup_s, [solve_s], stats of the last solve, batch info)."""
+    import torch
+    from . import dgmg
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    batch = dgmg.Batch([(r["n"], r["p"], r["kappa"]) for r in reqs], autotune=1)
+    setup = time.perf_counter() - t
+    bs = [r["b"] for r in reqs]
+    times, stats = [], None
+    for _ in range(solves):
+        xs = [torch.zeros_like(b) for b in bs]
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        stats, _ = batch.solve(bs, xs)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t)
+    info = batch.info()
+    batch.close()
+    return setup, times, stats, info
 
 
 def fifo_latencies(arrivals, service):
@@ -305,10 +333,20 @@ def run_batch(count=256, seed=4, max_active=32, budget_gb=64):
     one-at-a-time. solves/s for both (set-up included in both)."""
     reqs = request_stream("batch", count, seed)
     build_rhs(reqs)
-    t_alone = one_at_a_time(reqs, precision=0)
+    solve_only = []
+    t_alone = one_at_a_time(reqs, precision=0, solve_times=solve_only)
+    setup, bt, bstats, binfo = batched(reqs)
     lat, makespan, stats, info = serve_trace(reqs, [0.0] * count, budget_gb << 30, max_active)
     return {"workload": f"batch of {count} 3D solves, n in [8,24], p in 2..4, lognormal kappa, Fourier RHS",
             "fp64_one_at_a_time_solves_per_s": count / sum(t_alone),
+            "fp64_one_at_a_time_solve_only_solves_per_s": count / sum(solve_only),
+            "batched_fp64": {"setup_s": setup, "solve_s": bt, "solves_per_s": count / (setup + bt[0]),
+                             "solve_only_solves_per_s": count / min(bt), "iterations": bstats[0].iterations,
+                             "max_rel_residual": max(s.rel_residual for s in bstats),
+                             "groups": binfo.groups, "kernels_per_iteration": binfo.kernels_per_iteration,
+                             "tiles": {f"q={binfo.group_q[k]}": list(binfo.group_tiles[k])
+                                       for k in range(min(binfo.groups, 4))},
+                             "ndof": binfo.ndof},
             "served_mixed_solves_per_s": count / makespan,
             "served_p50_s": pct(lat, 50), "served_p99_s": pct(lat, 99),
             "max_rel_residual": max(s.rel_residual for s in stats),

@@ -56,7 +56,8 @@ def test_batch_solutions_match_oracle(dgmg, mix):
 @pytest.mark.gpu
 def test_batch_single_problem_equals_context_solve(dgmg):
     """A batch of one problem runs the context's own algorithm: same iterations,
-    same solution to rounding."""
+    same solution to rounding. In a mixed batch every problem takes the
+    iterations it takes alone."""
     n, p = (7, 6, 5), 3
     mesh, kap, b = _problem(n, p, 3, "lognormal")
     bt = torch.tensor(b, device=DEV)
@@ -68,6 +69,16 @@ def test_batch_single_problem_equals_context_solve(dgmg):
     (st2,), _ = batch.solve([bt], [x2])
     assert st2.iterations == st1.iterations
     assert (x1 - x2).abs().max().item() <= 1e-11 * x1.abs().max().item()
+    spec = [((5, 6, 4), 2, "lognormal"), ((8, 8, 8), 1, "one"), ((6, 5, 7), 3, "lognormal")]
+    probs = [_problem(n, p, 60 + i, kind) for i, (n, p, kind) in enumerate(spec)]
+    bs = [torch.tensor(b, device=DEV) for _, _, b in probs]
+    alone = []
+    for (n, p, _), (_, kap, _), bt in zip(spec, probs, bs):
+        st, _ = dgmg.Context(n, p, kap).solve(bt, torch.zeros_like(bt))
+        alone.append(st.iterations)
+    batch = dgmg.Batch([(n, p, kap) for (n, p, _), (_, kap, _) in zip(spec, probs)])
+    stats, _ = batch.solve(bs, [torch.zeros_like(b) for b in bs])
+    assert [s.iterations for s in stats] == alone
 
 
 @pytest.mark.gpu
@@ -88,6 +99,26 @@ def test_batch_launches_do_not_grow_with_count(dgmg):
             assert max(s.rel_residual for s in stats) <= 1e-10
         kpi.append(batch.info().kernels_per_iteration)
     assert kpi[0] > 0 and kpi[0] == kpi[1]
+
+
+@pytest.mark.gpu
+def test_batch_autotuned_tiles_same_results(dgmg):
+    """Tuned tiles regroup cells into CTAs (and may switch the smoothing kernel):
+    the solutions agree with the default tiles to rounding."""
+    spec = [((6, 5, 4), 2, "lognormal"), ((5, 5, 5), 3, "one"), ((4, 5, 6), 4, "lognormal")]
+    probs = [_problem(n, p, 80 + i, kind) for i, (n, p, kind) in enumerate(spec)]
+    bs = [torch.tensor(b, device=DEV) for _, _, b in probs]
+    out = []
+    for tune in (0, 1):
+        batch = dgmg.Batch([(n, p, kap) for (n, p, _), (_, kap, _) in zip(spec, probs)], autotune=tune)
+        xs = [torch.zeros_like(b) for b in bs]
+        stats, _ = batch.solve(bs, xs)
+        assert max(s.rel_residual for s in stats) <= 1e-10
+        inf = batch.info()
+        assert all(inf.group_tiles[k][0] > 0 and inf.group_tiles[k][2] > 0 for k in range(inf.groups))
+        out.append([x.cpu().numpy() for x in xs])
+    for a, b in zip(*out):
+        assert np.abs(a - b).max() <= 1e-9 * np.abs(a).max()
 
 
 @pytest.mark.gpu
