@@ -318,9 +318,11 @@ typedef struct {
  * problems share one launch per Q1-level stage (point Jacobi, residual,
  * h-restriction, h-prolongation, vertex gather, dense coarsest solve). All
  * meshes have the same dimension. opts (NULL = defaults) apply to every
- * problem; precision must be DGMG_FP64 and nu_pre >= 1 (DGMG_EINVAL
- * otherwise). With opts->autotune the cells per CTA of each group's launches
- * are timed and chosen on the batch itself. Synchronous.
+ * problem; nu_pre >= 1 (DGMG_EINVAL otherwise). precision DGMG_FP64, or
+ * DGMG_MIXED_FP32: the V-cycle runs in FP32 (the dense coarsest solve stays
+ * FP64) inside FP64 CG recurrences with FP64 residuals (flexible
+ * Polak-Ribiere beta). With opts->autotune the cells per CTA of each group's
+ * launches are timed and chosen on the batch itself. Synchronous.
  */
 int dgmg_batch_create(int count, const dgmg_mesh *meshes, const int *p, const double *const *kappa,
                       const dgmg_opts *opts, dgmg_batch **out);

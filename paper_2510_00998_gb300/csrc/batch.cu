@@ -81,6 +81,21 @@ __global__ void k_seg_beta(int count, const int *__restrict__ active, double *__
     rz[i] = rzn[i];
 }
 
+// active problems, flexible (Polak-Ribiere) form for the FP32 V-cycle:
+// beta = (<r,z>_new - <r_old,z>) / <r,z>; <r,z> <- <r,z>_new
+__global__ void k_seg_beta_flex(int count, const int *__restrict__ active, double *__restrict__ rz,
+                                const double *__restrict__ rzn, const double *__restrict__ rzo,
+                                double *__restrict__ beta) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    if (!active[i]) {
+        beta[i] = 0.0;
+        return;
+    }
+    beta[i] = (rzn[i] - rzo[i]) / rz[i];
+    rz[i] = rzn[i];
+}
+
 // active problems: p = z + beta p
 __global__ void k_seg_update_p(const int64_t *__restrict__ off, const int64_t *__restrict__ len,
                                const int *__restrict__ active, const double *__restrict__ beta, double *__restrict__ p,
@@ -129,13 +144,39 @@ struct dgmg_batch {
         std::vector<int> members;            // problem indices
         int64_t cells = 0;                   // padded cells
         int64_t dof0 = 0;                    // first DoF in the batch vectors
-        BatchDG<double> *D = nullptr;        // device, one per member
-        int tile[3] = {0, 0, 0};             // cells per CTA: projection, smoothing (0: one per thread), residual
-        BlockMap *map[3] = {nullptr, nullptr, nullptr};
-        int nblocks[3] = {0, 0, 0};
+        // per precision of the hierarchy (FP64; FP32 for the mixed V-cycle):
+        // descriptors (one per member), cells per CTA of projection, smoothing
+        // (0: one thread per cell), residual, and the CTA tables
+        template <typename T>
+        struct Prec {
+            BatchDG<T> *D = nullptr;
+            int tile[3] = {0, 0, 0};
+            BlockMap *map[3] = {nullptr, nullptr, nullptr};
+            int nblocks[3] = {0, 0, 0};
+        };
+        Prec<double> p64;
+        Prec<float> p32;
+        template <typename T>
+        Prec<T> &prec() {
+            if constexpr (std::is_same<T, float>::value)
+                return p32;
+            else
+                return p64;
+        }
     };
     std::vector<Group> groups;
+    bool mixed = false;                      // FP32 V-cycle inside the FP64 CG recurrences
     BatchCG<double> *C = nullptr;            // device, (problem, level) in order
+    BatchCG<float> *C32 = nullptr;           // the same levels in FP32 (mixed)
+    template <typename T>
+    const BatchCG<T> *cg() const {
+        if constexpr (std::is_same<T, float>::value)
+            return C32;
+        else
+            return C;
+    }
+    float *r32 = nullptr, *z32 = nullptr;    // mixed: the V-cycle's vectors
+    double *rold = nullptr, *rzo = nullptr;  // mixed: previous residual, <r_old, z>
     struct LevelMaps {
         VertMap *fine = nullptr, *next = nullptr, *coarse = nullptr;
         int nfine = 0, nnext = 0, ncoarse = 0;
@@ -193,19 +234,27 @@ struct dgmg_batch {
 namespace {
 
 // result vector of Q1 level l of problem i after its part of the h-cycle
-const double *level_result(const dgmg_batch &B, int i, int l) {
-    const CGDev<double> &L = B.inst[i]->cg64[l];
+template <typename T>
+const T *level_result(const dgmg_batch &B, int i, int l) {
+    const auto &lv = cgl<T>(*B.inst[i]);
+    const CGDev<T> &L = lv[l];
     if (l == B.depth[i] - 1) return L.u[0];
     return L.u[(B.opts.nu_pre + B.opts.nu_post) & 1];
 }
 
-int build_block_map(dgmg_batch &B, dgmg_batch::Group &g, int stage) {
-    const int nf = (int)(B.inst[g.members[0]]->nloc / g.q);
+template <typename T>
+bool cells_apply(const dgmg_batch &B, int q) {
+    return B.dim == 3 && q <= (std::is_same<T, float>::value ? 5 : 4) && B.opts.block_inverse == DGMG_BLOCK_EXACT;
+}
+
+template <typename T>
+int build_block_map(dgmg_batch &B, dgmg_batch::Group &grp, int stage) {
+    auto &g = grp.prec<T>();
+    const int nf = (int)(B.inst[grp.members[0]]->nloc / grp.q);
     int tile = g.tile[stage];
     if (tile <= 0) {
-        // the one-thread-per-cell smoother where it applies (3D, exact blocks, q <= 4), else ~128 threads
-        const bool cells = stage == TILE_SMOOTH && B.dim == 3 && g.q <= 4 &&
-                           B.opts.block_inverse == DGMG_BLOCK_EXACT;
+        // the one-thread-per-cell smoother where it applies, else ~128 threads
+        const bool cells = stage == TILE_SMOOTH && cells_apply<T>(B, grp.q);
         if (cells) {
             tile = BATCH_ALIGN_CELLS;
         } else {
@@ -215,8 +264,8 @@ int build_block_map(dgmg_batch &B, dgmg_batch::Group &g, int stage) {
         }
     }
     std::vector<BlockMap> m;
-    for (size_t k = 0; k < g.members.size(); ++k) {
-        const int64_t nc = B.inst[g.members[k]]->ncell;
+    for (size_t k = 0; k < grp.members.size(); ++k) {
+        const int64_t nc = B.inst[grp.members[k]]->ncell;
         for (int64_t c0 = 0; c0 < nc; c0 += tile) m.push_back(BlockMap{(int)k, (int)c0});
     }
     g.nblocks[stage] = (int)m.size();
@@ -227,8 +276,10 @@ int build_block_map(dgmg_batch &B, dgmg_batch::Group &g, int stage) {
 // candidate cells-per-CTA value (and, for the smoothing step, the
 // one-thread-per-cell kernel) is timed on the batch's own buffers, one warm-up
 // and three timed launches; the fastest is kept.
-int tune_group(dgmg_batch &B, dgmg_batch::Group &g, cudaStream_t s) {
-    const int nf = (int)(B.inst[g.members[0]]->nloc / g.q);
+template <typename T>
+int tune_group(dgmg_batch &B, dgmg_batch::Group &grp, T *u, T *bv, cudaStream_t s) {
+    auto &g = grp.prec<T>();
+    const int nf = (int)(B.inst[grp.members[0]]->nloc / grp.q);
     const int exact = B.opts.block_inverse == DGMG_BLOCK_EXACT ? 1 : 0;
     std::vector<int> cand;
     for (int c = 1; c <= 64; c *= 2)
@@ -237,23 +288,24 @@ int tune_group(dgmg_batch &B, dgmg_batch::Group &g, cudaStream_t s) {
     cudaEvent_t e0, e1;
     LC(cudaEventCreate(&e0));
     LC(cudaEventCreate(&e1));
-    double *u = B.z + g.dof0, *bv = B.r + g.dof0;
+    u += grp.dof0;
+    bv += grp.dof0;
     for (int st = 0; st < 3; ++st) {
         std::vector<int> cs = cand;
-        if (st == TILE_SMOOTH && B.dim == 3 && g.q <= 4 && exact) cs.insert(cs.begin(), 0);
+        if (st == TILE_SMOOTH && cells_apply<T>(B, grp.q)) cs.insert(cs.begin(), 0);
         int best = cs[0];
         float best_ms = 1e30f;
         for (int c : cs) {
             g.tile[st] = c;
-            RC(build_block_map(B, g, st));
+            RC(build_block_map<T>(B, grp, st));
             auto launch = [&]() -> cudaError_t {
                 if (st == TILE_PROJECT)
-                    return launch_project_batch<double>(B.dim, g.q, g.D, g.map[st], g.nblocks[st], g.tile[st], u, 0, s);
+                    return launch_project_batch<T>(B.dim, grp.q, g.D, g.map[st], g.nblocks[st], g.tile[st], u, 0, s);
                 if (st == TILE_SMOOTH)
-                    return launch_smooth_batch<double>(B.dim, g.q, g.D, g.map[st], g.nblocks[st], g.tile[st], exact,
-                                                       u, bv, 0, s);
-                return launch_residual_batch<double>(B.dim, g.q, g.D, g.map[st], g.nblocks[st], g.tile[st],
-                                                     RES_HAS_B | RES_CORNERS, u, bv, nullptr, 0, s);
+                    return launch_smooth_batch<T>(B.dim, grp.q, g.D, g.map[st], g.nblocks[st], g.tile[st], exact, u,
+                                                  bv, 0, s);
+                return launch_residual_batch<T>(B.dim, grp.q, g.D, g.map[st], g.nblocks[st], g.tile[st],
+                                                RES_HAS_B | RES_CORNERS, u, bv, nullptr, 0, s);
             };
             float ms = 1e30f;
             if (launch() == cudaSuccess) {
@@ -270,7 +322,7 @@ int tune_group(dgmg_batch &B, dgmg_batch::Group &g, cudaStream_t s) {
             }
         }
         g.tile[st] = best;
-        RC(build_block_map(B, g, st));
+        RC(build_block_map<T>(B, grp, st));
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -285,59 +337,79 @@ void push_verts(std::vector<VertMap> &m, int desc, int64_t n) {
 // ---- batched stages
 int batch_apply(dgmg_batch &B, const double *u, const double *bvec, double *out, cudaStream_t s) {
     const int mode = bvec ? (RES_HAS_B | RES_WRITE_R) : (RES_WRITE_R | RES_NEGATE);
-    for (auto &g : B.groups) {
-        LC(launch_project_batch<double>(B.dim, g.q, g.D, g.map[TILE_PROJECT], g.nblocks[TILE_PROJECT],
-                                        g.tile[TILE_PROJECT], const_cast<double *>(u) + g.dof0, 0, s));
-        LC(launch_residual_batch<double>(B.dim, g.q, g.D, g.map[TILE_RESIDUAL], g.nblocks[TILE_RESIDUAL],
-                                         g.tile[TILE_RESIDUAL], mode, u + g.dof0, bvec ? bvec + g.dof0 : nullptr,
-                                         out + g.dof0, 0, s));
+    for (auto &grp : B.groups) {
+        auto &g = grp.p64;
+        LC(launch_project_batch<double>(B.dim, grp.q, g.D, g.map[TILE_PROJECT], g.nblocks[TILE_PROJECT],
+                                        g.tile[TILE_PROJECT], const_cast<double *>(u) + grp.dof0, 0, s));
+        LC(launch_residual_batch<double>(B.dim, grp.q, g.D, g.map[TILE_RESIDUAL], g.nblocks[TILE_RESIDUAL],
+                                         g.tile[TILE_RESIDUAL], mode, u + grp.dof0, bvec ? bvec + grp.dof0 : nullptr,
+                                         out + grp.dof0, 0, s));
     }
     return DGMG_OK;
 }
 
+template <typename T>
 int batch_cg_cycle(dgmg_batch &B, int l, cudaStream_t s) {
     const auto &m = B.lm[l];
-    const double om = B.opts.omega_cg;
-    LC(launch_coarse_solve_batch<double>(B.C, m.coarse, m.ncoarse, s));
+    const BatchCG<T> *C = B.cg<T>();
+    const T om = (T)B.opts.omega_cg;
+    LC(launch_coarse_solve_batch<T>(C, m.coarse, m.ncoarse, s));
     if (m.nfine == 0) return DGMG_OK;
     int cur = 0;
     for (int k = 0; k < B.opts.nu_pre; ++k) {
-        LC(launch_cg_jacobi_batch<double>(B.dim, B.C, m.fine, m.nfine, om, k == 0, cur, s));
+        LC(launch_cg_jacobi_batch<T>(B.dim, C, m.fine, m.nfine, om, k == 0, cur, s));
         cur ^= 1;
     }
-    LC(launch_cg_residual_batch<double>(B.dim, B.C, m.fine, m.nfine, cur, s));
-    LC(launch_h_restrict_batch<double>(B.dim, B.C, m.next, m.nnext, s));
-    RC(batch_cg_cycle(B, l + 1, s));
-    LC(launch_h_prolong_batch<double>(B.dim, B.C, m.fine, m.nfine, cur, s));
+    LC(launch_cg_residual_batch<T>(B.dim, C, m.fine, m.nfine, cur, s));
+    LC(launch_h_restrict_batch<T>(B.dim, C, m.next, m.nnext, s));
+    RC(batch_cg_cycle<T>(B, l + 1, s));
+    LC(launch_h_prolong_batch<T>(B.dim, C, m.fine, m.nfine, cur, s));
     for (int k = 0; k < B.opts.nu_post; ++k) {
-        LC(launch_cg_jacobi_batch<double>(B.dim, B.C, m.fine, m.nfine, om, false, cur, s));
+        LC(launch_cg_jacobi_batch<T>(B.dim, C, m.fine, m.nfine, om, false, cur, s));
         cur ^= 1;
     }
     return DGMG_OK;
 }
 
-// z = V(r) for every problem at once (zero initial guess)
-int batch_vcycle(dgmg_batch &B, const double *r, double *z, cudaStream_t s) {
+// z = V(r) for every problem at once (zero initial guess), in precision T
+template <typename T>
+int batch_vcycle(dgmg_batch &B, const T *r, T *z, cudaStream_t s) {
     const int exact = B.opts.block_inverse == DGMG_BLOCK_EXACT ? 1 : 0;
-    LC(cudaMemsetAsync(z, 0, sizeof(double) * B.ndof, s));
-    for (auto &g : B.groups) LC(launch_zero_traces_batch<double>(B.dim, g.q, g.D, (int)g.members.size(), s));
-    for (int k = 0; k < B.opts.nu_pre; ++k)
-        for (auto &g : B.groups)
-            LC(launch_smooth_batch<double>(B.dim, g.q, g.D, g.map[TILE_SMOOTH], g.nblocks[TILE_SMOOTH],
-                                           g.tile[TILE_SMOOTH], exact, z + g.dof0, r + g.dof0, k & 1, s));
-    for (auto &g : B.groups)
-        LC(launch_residual_batch<double>(B.dim, g.q, g.D, g.map[TILE_RESIDUAL], g.nblocks[TILE_RESIDUAL],
-                                         g.tile[TILE_RESIDUAL], RES_HAS_B | RES_CORNERS, z + g.dof0, r + g.dof0,
-                                         nullptr, B.opts.nu_pre & 1, s));
-    LC(launch_corner_gather_batch<double>(B.dim, B.C, B.gather, B.ngather, s));
-    RC(batch_cg_cycle(B, 0, s));
-    for (auto &g : B.groups)
-        LC(launch_project_batch<double>(B.dim, g.q, g.D, g.map[TILE_PROJECT], g.nblocks[TILE_PROJECT],
-                                        g.tile[TILE_PROJECT], z + g.dof0, 1, s));
-    for (int k = 0; k < B.opts.nu_post; ++k)
-        for (auto &g : B.groups)
-            LC(launch_smooth_batch<double>(B.dim, g.q, g.D, g.map[TILE_SMOOTH], g.nblocks[TILE_SMOOTH],
-                                           g.tile[TILE_SMOOTH], exact, z + g.dof0, r + g.dof0, k & 1, s));
+    LC(cudaMemsetAsync(z, 0, sizeof(T) * B.ndof, s));
+    for (auto &grp : B.groups)
+        LC(launch_zero_traces_batch<T>(B.dim, grp.q, grp.prec<T>().D, (int)grp.members.size(), s));
+    auto smooth = [&](int k) -> int {
+        for (auto &grp : B.groups) {
+            auto &g = grp.prec<T>();
+            LC(launch_smooth_batch<T>(B.dim, grp.q, g.D, g.map[TILE_SMOOTH], g.nblocks[TILE_SMOOTH],
+                                      g.tile[TILE_SMOOTH], exact, z + grp.dof0, r + grp.dof0, k & 1, s));
+        }
+        return DGMG_OK;
+    };
+    for (int k = 0; k < B.opts.nu_pre; ++k) RC(smooth(k));
+    for (auto &grp : B.groups) {
+        auto &g = grp.prec<T>();
+        LC(launch_residual_batch<T>(B.dim, grp.q, g.D, g.map[TILE_RESIDUAL], g.nblocks[TILE_RESIDUAL],
+                                    g.tile[TILE_RESIDUAL], RES_HAS_B | RES_CORNERS, z + grp.dof0, r + grp.dof0,
+                                    nullptr, B.opts.nu_pre & 1, s));
+    }
+    LC(launch_corner_gather_batch<T>(B.dim, B.cg<T>(), B.gather, B.ngather, s));
+    RC(batch_cg_cycle<T>(B, 0, s));
+    for (auto &grp : B.groups) {
+        auto &g = grp.prec<T>();
+        LC(launch_project_batch<T>(B.dim, grp.q, g.D, g.map[TILE_PROJECT], g.nblocks[TILE_PROJECT],
+                                   g.tile[TILE_PROJECT], z + grp.dof0, 1, s));
+    }
+    for (int k = 0; k < B.opts.nu_post; ++k) RC(smooth(k));
+    return DGMG_OK;
+}
+
+// z = V(r) in the batch's V-cycle precision (FP64 vectors outside)
+int batch_precondition(dgmg_batch &B, cudaStream_t s) {
+    if (!B.mixed) return batch_vcycle<double>(B, B.r, B.z, s);
+    LC(launch_cast_d2f(B.ndof, B.r, B.r32, s));
+    RC(batch_vcycle<float>(B, B.r32, B.z32, s));
+    LC(launch_cast_f2d(B.ndof, B.z32, B.z, s));
     return DGMG_OK;
 }
 
@@ -367,6 +439,7 @@ int batch_norms(dgmg_batch &B, const double *v, cudaStream_t s) {
 int alpha_step(dgmg_batch &B, cudaStream_t s) {
     RC(batch_apply(B, B.p, nullptr, B.q, s));
     RC(seg_dot(B, B.p, B.q, B.pq, s));
+    if (B.mixed) LC(cudaMemcpyAsync(B.rold, B.r, sizeof(double) * B.ndof, cudaMemcpyDeviceToDevice, s));
     count_launches(1);
     k_seg_update_xr<<<dim3(SEG_BLOCKS * 4, B.count), 256, 0, s>>>(B.d_off, B.d_len, B.active, B.rz, B.pq, B.x,
                                                                     B.r, B.p, B.q);
@@ -377,10 +450,15 @@ int alpha_step(dgmg_batch &B, cudaStream_t s) {
 // One CG iteration of every active problem: z = V(r), beta, p = z + beta p, then
 // the alpha step.
 int batch_iteration(dgmg_batch &B, cudaStream_t s) {
-    RC(batch_vcycle(B, B.r, B.z, s));
+    RC(batch_precondition(B, s));
     RC(seg_dot(B, B.r, B.z, B.rzn, s));
     count_launches(2);
-    k_seg_beta<<<small_grid(B.count), 128, 0, s>>>(B.count, B.active, B.rz, B.rzn, B.beta);
+    if (B.mixed) {
+        RC(seg_dot(B, B.rold, B.z, B.rzo, s));
+        k_seg_beta_flex<<<small_grid(B.count), 128, 0, s>>>(B.count, B.active, B.rz, B.rzn, B.rzo, B.beta);
+    } else {
+        k_seg_beta<<<small_grid(B.count), 128, 0, s>>>(B.count, B.active, B.rz, B.rzn, B.beta);
+    }
     k_seg_update_p<<<dim3(SEG_BLOCKS * 4, B.count), 256, 0, s>>>(B.d_off, B.d_len, B.active, B.beta, B.p, B.z);
     LC(cudaGetLastError());
     return alpha_step(B, s);
@@ -417,6 +495,57 @@ int run_iteration(dgmg_batch &B, cudaStream_t s) {
     return DGMG_OK;
 }
 
+// DG descriptors of a group in precision T (FP32 from the problems' FP32 hierarchies)
+template <typename T>
+std::vector<BatchDG<T>> group_descriptors(const dgmg_batch &B, const dgmg_batch::Group &grp) {
+    std::vector<BatchDG<T>> D;
+    int64_t cells = 0;
+    for (int i : grp.members) {
+        dgmg_ctx *c = B.inst[i];
+        const DGDev<T> &dg = dgmg::dg<T>(*c);
+        BatchDG<T> d{};
+        d.c = dg.c;
+        d.off = cells;
+        d.kappa = dg.kappa;
+        d.fd = dg.fd;
+        d.linv = dg.linv;
+        d.tr[0] = dg.tr[0];
+        d.tr[1] = dg.tr[1];
+        d.corners = dg.corners;
+        d.e0 = level_result<T>(B, i, 0);
+        D.push_back(d);
+        cells += (c->ncell + BATCH_ALIGN_CELLS - 1) / BATCH_ALIGN_CELLS * BATCH_ALIGN_CELLS;
+    }
+    return D;
+}
+
+// Q1 descriptors of every (problem, level) in precision T
+template <typename T>
+std::vector<BatchCG<T>> level_descriptors(const dgmg_batch &B) {
+    std::vector<BatchCG<T>> C;
+    for (int i = 0; i < B.count; ++i) {
+        dgmg_ctx *c = B.inst[i];
+        const auto &lv = cgl<T>(*c);
+        for (int l = 0; l < B.depth[i]; ++l) {
+            const CGDev<T> &L = lv[l];
+            BatchCG<T> e{};
+            e.L = L.L;
+            e.u[0] = L.u[0];
+            e.u[1] = L.u[1];
+            e.b = L.b;
+            e.r = L.r;
+            const bool last = l == B.depth[i] - 1;
+            e.b_next = last ? nullptr : lv[l + 1].b;
+            e.e_next = last ? nullptr : level_result<T>(B, i, l + 1);
+            e.Ainv = last ? c->coarse_inv : nullptr;
+            for (int a = 0; a < 3; ++a) e.n[a] = c->n[a];
+            e.corners = dgmg::dg<T>(*c).corners;
+            C.push_back(e);
+        }
+    }
+    return C;
+}
+
 }  // namespace
 
 extern "C" {
@@ -430,7 +559,7 @@ int dgmg_batch_create(int count, const dgmg_mesh *meshes, const int *p, const do
     dgmg_opts o;
     dgmg_default_opts(&o);
     if (opts) o = *opts;
-    if (o.precision != DGMG_FP64) return fail(DGMG_EINVAL, "batched solves run in DGMG_FP64");
+    if (o.precision != DGMG_FP64 && o.precision != DGMG_MIXED_FP32) return fail(DGMG_EINVAL, "unknown precision");
     if (o.nu_pre < 1) return fail(DGMG_EINVAL, "batched solves need nu_pre >= 1");
     for (int i = 0; i < count; ++i)
         if (meshes[i].dim != meshes[0].dim) return fail(DGMG_EINVAL, "all meshes of a batch have one dimension");
@@ -441,6 +570,7 @@ int dgmg_batch_create(int count, const dgmg_mesh *meshes, const int *p, const do
     oi.outer = DGMG_OUTER_PCG;
     oi.autotune = 0;
     B->opts = oi;
+    B->mixed = o.precision == DGMG_MIXED_FP32;
     // one ordinary hierarchy per problem, built on a few host threads
     B->inst.assign(count, nullptr);
     std::vector<int> rcs(count, DGMG_OK);
@@ -480,58 +610,37 @@ int dgmg_batch_create(int count, const dgmg_mesh *meshes, const int *p, const do
     int64_t dof = 0;
     for (auto &g : B->groups) {
         g.dof0 = dof;
-        std::vector<BatchDG<double>> D;
         int64_t cells = 0;
         for (int i : g.members) {
             dgmg_ctx *c = B->inst[i];
-            BatchDG<double> d{};
-            d.c = c->d64.c;
-            d.off = cells;
-            d.kappa = c->d64.kappa;
-            d.fd = c->d64.fd;
-            d.linv = c->d64.linv;
-            d.tr[0] = c->d64.tr[0];
-            d.tr[1] = c->d64.tr[1];
-            d.corners = c->d64.corners;
-            d.e0 = level_result(*B, i, 0);
-            D.push_back(d);
             B->dof_off[i] = g.dof0 + cells * c->nloc;
             B->dof_len[i] = c->ndof;
             cells += (c->ncell + BATCH_ALIGN_CELLS - 1) / BATCH_ALIGN_CELLS * BATCH_ALIGN_CELLS;
         }
         g.cells = cells;
         dof += cells * B->inst[g.members[0]]->nloc;
-        RC(B->upload(&g.D, D));
-        g.tile[TILE_SMOOTH] = 0;
-        for (int st = 0; st < 3; ++st) RC(build_block_map(*B, g, st));
+        RC(B->upload(&g.p64.D, group_descriptors<double>(*B, g)));
+        g.p64.tile[TILE_SMOOTH] = 0;
+        for (int st = 0; st < 3; ++st) RC(build_block_map<double>(*B, g, st));
+        if (B->mixed) {
+            RC(B->upload(&g.p32.D, group_descriptors<float>(*B, g)));
+            g.p32.tile[TILE_SMOOTH] = 0;
+            for (int st = 0; st < 3; ++st) RC(build_block_map<float>(*B, g, st));
+        }
     }
     B->ndof = dof;
 
-    // Q1 levels of all problems
-    std::vector<BatchCG<double>> C;
+    // Q1 levels of all problems (the same order in both precisions)
     std::vector<std::vector<int>> desc(count);
-    for (int i = 0; i < count; ++i) {
-        dgmg_ctx *c = B->inst[i];
-        for (int l = 0; l < B->depth[i]; ++l) {
-            const CGDev<double> &L = c->cg64[l];
-            BatchCG<double> e{};
-            e.L = L.L;
-            e.u[0] = L.u[0];
-            e.u[1] = L.u[1];
-            e.b = L.b;
-            e.r = L.r;
-            const bool last = l == B->depth[i] - 1;
-            e.b_next = last ? nullptr : c->cg64[l + 1].b;
-            e.e_next = last ? nullptr : level_result(*B, i, l + 1);
-            e.Ainv = last ? c->coarse_inv : nullptr;
-            for (int a = 0; a < 3; ++a) e.n[a] = c->n[a];
-            e.corners = c->d64.corners;
-            desc[i].push_back((int)C.size());
-            C.push_back(e);
+    {
+        int k = 0;
+        for (int i = 0; i < count; ++i) {
+            for (int l = 0; l < B->depth[i]; ++l) desc[i].push_back(k++);
+            B->maxdepth = std::max(B->maxdepth, B->depth[i]);
         }
-        B->maxdepth = std::max(B->maxdepth, B->depth[i]);
     }
-    RC(B->upload(&B->C, C));
+    RC(B->upload(&B->C, level_descriptors<double>(*B)));
+    if (B->mixed) RC(B->upload(&B->C32, level_descriptors<float>(*B)));
     {
         std::vector<VertMap> gm;
         for (int i = 0; i < count; ++i) push_verts(gm, desc[i][0], B->inst[i]->cg64[0].L.nv);
@@ -570,13 +679,25 @@ int dgmg_batch_create(int count, const dgmg_mesh *meshes, const int *p, const do
     for (double **v : {&B->d_norm, &B->d_bb, &B->rz, &B->rzn, &B->pq, &B->beta}) RC(B->alloc(v, count));
     RC(B->alloc(&B->part, (size_t)count * SEG_BLOCKS));
     RC(B->alloc(&B->active, count));
+    if (B->mixed) {
+        RC(B->alloc(&B->r32, B->ndof));
+        RC(B->alloc(&B->z32, B->ndof));
+        RC(B->alloc(&B->rold, B->ndof));
+        RC(B->alloc(&B->rzo, count));
+        LC(cudaMemset(B->r32, 0, sizeof(float) * B->ndof));
+        LC(cudaMemset(B->z32, 0, sizeof(float) * B->ndof));
+        LC(cudaMemset(B->rold, 0, sizeof(double) * B->ndof));
+    }
     LC(cudaMallocHost((void **)&B->h_norm, sizeof(double) * count));
     LC(cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming));
     LC(cudaStreamCreateWithFlags(&B->capture_stream, cudaStreamNonBlocking));
     for (dgmg_ctx *c : B->inst) B->bytes += c->bytes;
     LC(cudaDeviceSynchronize());
     if (o.autotune)
-        for (auto &g : B->groups) RC(tune_group(*B, g, B->capture_stream));
+        for (auto &g : B->groups) {
+            RC(tune_group<double>(*B, g, B->z, B->r, B->capture_stream));
+            if (B->mixed) RC(tune_group<float>(*B, g, B->z32, B->r32, B->capture_stream));
+        }
     *out = B.release();
     return DGMG_OK;
 }
@@ -592,7 +713,8 @@ int dgmg_batch_info(const dgmg_batch *B, dgmg_batch_info_t *info) {
     info->kernels_per_iteration = B->kernels_per_iteration;
     for (size_t k = 0; k < B->groups.size() && k < 4; ++k) {
         info->group_q[k] = B->groups[k].q;
-        for (int st = 0; st < 3; ++st) info->group_tiles[k][st] = B->groups[k].tile[st];
+        for (int st = 0; st < 3; ++st)
+            info->group_tiles[k][st] = B->mixed ? B->groups[k].p32.tile[st] : B->groups[k].p64.tile[st];
     }
     return DGMG_OK;
 }
@@ -640,7 +762,7 @@ int dgmg_batch_solve(dgmg_batch *B, const double *const *b, double *const *x, dg
     };
     mark();
     if (worst > B->opts.rtol) {
-        RC(batch_vcycle(*B, B->r, B->z, s));
+        RC(batch_precondition(*B, s));
         RC(seg_dot(*B, B->r, B->z, B->rz, s));
         LC(cudaMemcpyAsync(B->p, B->z, sizeof(double) * B->ndof, cudaMemcpyDeviceToDevice, s));
         RC(alpha_step(*B, s));

@@ -547,18 +547,6 @@ int coarse_inverse(dgmg_ctx &C) {
 }
 
 // ------------------------------------------------------------ V-cycle
-template <typename T>
-DGDev<T> &dg(dgmg_ctx &C);
-template <>
-DGDev<double> &dg<double>(dgmg_ctx &C) { return C.d64; }
-template <>
-DGDev<float> &dg<float>(dgmg_ctx &C) { return C.d32; }
-template <typename T>
-std::vector<CGDev<T>> &cgl(dgmg_ctx &C);
-template <>
-std::vector<CGDev<double>> &cgl<double>(dgmg_ctx &C) { return C.cg64; }
-template <>
-std::vector<CGDev<float>> &cgl<float>(dgmg_ctx &C) { return C.cg32; }
 
 // h-multigrid V-cycle on Q1 level l with zero initial guess; RHS in cg[l].b.
 // Returns the buffer holding the result.

@@ -218,6 +218,36 @@ int dg_vcycle(dgmg_ctx &C, const T *r, T *z, cudaStream_t s);
 // next stretch of device work on the run's stream and returns without waiting;
 // it returns 1 once the solve has finished (status and stats final), 0 while it
 // waits for device scalars or has more work to queue.
+// the DG level and the Q1 levels of ctx in precision T
+template <typename T>
+inline DGDev<T> &dg(dgmg_ctx &C) {
+    if constexpr (std::is_same<T, float>::value)
+        return C.d32;
+    else
+        return C.d64;
+}
+template <typename T>
+inline const DGDev<T> &dg(const dgmg_ctx &C) {
+    if constexpr (std::is_same<T, float>::value)
+        return C.d32;
+    else
+        return C.d64;
+}
+template <typename T>
+inline std::vector<CGDev<T>> &cgl(dgmg_ctx &C) {
+    if constexpr (std::is_same<T, float>::value)
+        return C.cg32;
+    else
+        return C.cg64;
+}
+template <typename T>
+inline const std::vector<CGDev<T>> &cgl(const dgmg_ctx &C) {
+    if constexpr (std::is_same<T, float>::value)
+        return C.cg32;
+    else
+        return C.cg64;
+}
+
 int mg_cycle64(dgmg_ctx &C, double *x, const double *b, double *r, cudaStream_t s);
 int project64(dgmg_ctx &C, double *x, cudaStream_t s);
 

@@ -257,15 +257,15 @@ def one_at_a_time(reqs, precision=0, solve_times=None):
     return times
 
 
-def batched(reqs, solves=2):
-    """All requests as one dgmg_batch (FP64): set-up time, then `solves` batched
+def batched(reqs, solves=2, precision=0):
+    """All requests as one dgmg_batch: set-up time, then `solves` batched
     solves from x = 0 (the second and later replay the captured iteration).
     Returns (setup_s, [solve_s], stats of the last solve, batch info)."""
     import torch
     from . import dgmg
     torch.cuda.synchronize()
     t = time.perf_counter()
-    batch = dgmg.Batch([(r["n"], r["p"], r["kappa"]) for r in reqs], autotune=1)
+    batch = dgmg.Batch([(r["n"], r["p"], r["kappa"]) for r in reqs], autotune=1, precision=precision)
     setup = time.perf_counter() - t
     bs = [r["b"] for r in reqs]
     times, stats = [], None
@@ -336,17 +336,26 @@ def run_batch(count=256, seed=4, max_active=32, budget_gb=64):
     solve_only = []
     t_alone = one_at_a_time(reqs, precision=0, solve_times=solve_only)
     setup, bt, bstats, binfo = batched(reqs)
+    msetup, mbt, mstats, minfo = batched(reqs, precision=1)
     lat, makespan, stats, info = serve_trace(reqs, [0.0] * count, budget_gb << 30, max_active)
     return {"workload": f"batch of {count} 3D solves, n in [8,24], p in 2..4, lognormal kappa, Fourier RHS",
             "fp64_one_at_a_time_solves_per_s": count / sum(t_alone),
             "fp64_one_at_a_time_solve_only_solves_per_s": count / sum(solve_only),
             "batched_fp64": {"setup_s": setup, "solve_s": bt, "solves_per_s": count / (setup + bt[0]),
-                             "solve_only_solves_per_s": count / min(bt), "iterations": bstats[0].iterations,
+                             "solve_only_solves_per_s": count / min(bt),
+                             "iterations_max": max(s.iterations for s in bstats),
                              "max_rel_residual": max(s.rel_residual for s in bstats),
                              "groups": binfo.groups, "kernels_per_iteration": binfo.kernels_per_iteration,
                              "tiles": {f"q={binfo.group_q[k]}": list(binfo.group_tiles[k])
                                        for k in range(min(binfo.groups, 4))},
                              "ndof": binfo.ndof},
+            "batched_mixed": {"setup_s": msetup, "solve_s": mbt, "solves_per_s": count / (msetup + mbt[0]),
+                              "solve_only_solves_per_s": count / min(mbt),
+                              "iterations_max": max(s.iterations for s in mstats),
+                              "max_rel_residual": max(s.rel_residual for s in mstats),
+                              "kernels_per_iteration": minfo.kernels_per_iteration,
+                              "tiles": {f"q={minfo.group_q[k]}": list(minfo.group_tiles[k])
+                                        for k in range(min(minfo.groups, 4))}},
             "served_mixed_solves_per_s": count / makespan,
             "served_p50_s": pct(lat, 50), "served_p99_s": pct(lat, 99),
             "max_rel_residual": max(s.rel_residual for s in stats),

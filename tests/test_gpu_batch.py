@@ -32,14 +32,15 @@ MIX3 = [((5, 6, 4), 2, "lognormal"), ((8, 8, 8), 1, "one"), ((7, 5, 6), 3, "logn
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("mix", ["3d", "2d"])
-def test_batch_solutions_match_oracle(dgmg, mix):
+@pytest.mark.parametrize("mix,prec", [("3d", 0), ("2d", 0), ("3d", 1), ("2d", 1)])
+def test_batch_solutions_match_oracle(dgmg, mix, prec):
     """Every problem of a mixed batch (sizes, degrees 1-4, kappa fields) reaches
-    its own residual bound, and its solution is the oracle's."""
+    its own residual bound, and its solution is the oracle's, with the FP64 and
+    with the FP32 V-cycle."""
     spec = MIX3 if mix == "3d" else [((12, 10), 2, "lognormal"), ((9, 9), 4, "one"), ((16, 7), 3, "lognormal"),
                                      ((6, 11), 2, "one")]
     probs = [_problem(n, p, 40 + i, kind) for i, (n, p, kind) in enumerate(spec)]
-    batch = dgmg.Batch([(n, p, kap) for (n, p, _), (_, kap, _) in zip(spec, probs)])
+    batch = dgmg.Batch([(n, p, kap) for (n, p, _), (_, kap, _) in zip(spec, probs)], precision=prec)
     bs = [torch.tensor(b, device=DEV) for _, _, b in probs]
     xs = [torch.zeros_like(b) for b in bs]
     stats, _ = batch.solve(bs, xs)
@@ -124,7 +125,7 @@ def test_batch_autotuned_tiles_same_results(dgmg):
 @pytest.mark.gpu
 def test_batch_invalid_arguments(dgmg):
     with pytest.raises(dgmg.DGMGError):
-        dgmg.Batch([((4, 4, 4), 2, None)], precision=dgmg.DGMG_MIXED_FP32)
+        dgmg.Batch([((4, 4, 4), 2, None)], precision=7)
     with pytest.raises(dgmg.DGMGError):
         dgmg.Batch([((4, 4, 4), 2, None), ((5, 5), 2, None)])
     with pytest.raises(dgmg.DGMGError):
