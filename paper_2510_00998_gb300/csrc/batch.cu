@@ -22,6 +22,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <thread>
@@ -291,6 +293,9 @@ int tune_group(dgmg_batch &B, dgmg_batch::Group &grp, T *u, T *bv, cudaStream_t 
     u += grp.dof0;
     bv += grp.dof0;
     for (int st = 0; st < 3; ++st) {
+        // mixed precision: the FP64 level only applies the operator (its problems
+        // carry no FP64 block-inverse factors), so its smoothing step is never run
+        if (std::is_same<T, double>::value && B.mixed && st == TILE_SMOOTH) continue;
         std::vector<int> cs = cand;
         if (st == TILE_SMOOTH && cells_apply<T>(B, grp.q)) cs.insert(cs.begin(), 0);
         int best = cs[0];
@@ -512,7 +517,7 @@ std::vector<BatchDG<T>> group_descriptors(const dgmg_batch &B, const dgmg_batch:
         d.tr[0] = dg.tr[0];
         d.tr[1] = dg.tr[1];
         d.corners = dg.corners;
-        d.e0 = level_result<T>(B, i, 0);
+        d.e0 = cgl<T>(*c).empty() ? nullptr : level_result<T>(B, i, 0);
         D.push_back(d);
         cells += (c->ncell + BATCH_ALIGN_CELLS - 1) / BATCH_ALIGN_CELLS * BATCH_ALIGN_CELLS;
     }
@@ -563,6 +568,15 @@ int dgmg_batch_create(int count, const dgmg_mesh *meshes, const int *p, const do
     if (o.nu_pre < 1) return fail(DGMG_EINVAL, "batched solves need nu_pre >= 1");
     for (int i = 0; i < count; ++i)
         if (meshes[i].dim != meshes[0].dim) return fail(DGMG_EINVAL, "all meshes of a batch have one dimension");
+    const bool trace = std::getenv("DGMG_TRACE_SETUP") != nullptr;
+    auto tmark = std::chrono::steady_clock::now();
+    auto phase = [&](const char *what) {
+        if (!trace) return;
+        const auto now = std::chrono::steady_clock::now();
+        std::fprintf(stderr, "dgmg batch setup %-18s %9.3f ms\n", what,
+                     std::chrono::duration<double, std::milli>(now - tmark).count());
+        tmark = now;
+    };
     std::unique_ptr<dgmg_batch> B(new dgmg_batch());
     B->count = count;
     B->dim = meshes[0].dim;
@@ -571,7 +585,9 @@ int dgmg_batch_create(int count, const dgmg_mesh *meshes, const int *p, const do
     oi.autotune = 0;
     B->opts = oi;
     B->mixed = o.precision == DGMG_MIXED_FP32;
-    // one ordinary hierarchy per problem, built on a few host threads
+    // one hierarchy per problem, built on a few host threads (without the parts
+    // the batch does not use)
+    const int flags = CREATE_NO_SOLVER | (B->mixed ? CREATE_NO_FP64_SMOOTHER | CREATE_NO_FP64_Q1 : 0);
     B->inst.assign(count, nullptr);
     std::vector<int> rcs(count, DGMG_OK);
     std::vector<std::string> errs(count);
@@ -584,7 +600,7 @@ int dgmg_batch_create(int count, const dgmg_mesh *meshes, const int *p, const do
             th.emplace_back([&, t]() {
                 cudaSetDevice(dev);
                 for (int i = t; i < count; i += nt) {
-                    rcs[i] = dgmg_create(&meshes[i], p[i], kappa ? kappa[i] : nullptr, &oi, &B->inst[i]);
+                    rcs[i] = create_ctx(&meshes[i], p[i], kappa ? kappa[i] : nullptr, &oi, flags, &B->inst[i]);
                     if (rcs[i] != DGMG_OK) errs[i] = dgmg_last_error();
                 }
             });
@@ -592,7 +608,9 @@ int dgmg_batch_create(int count, const dgmg_mesh *meshes, const int *p, const do
     }
     for (int i = 0; i < count; ++i)
         if (rcs[i] != DGMG_OK) return fail(rcs[i], "batch problem " + std::to_string(i) + ": " + errs[i]);
-    for (int i = 0; i < count; ++i) B->depth.push_back((int)B->inst[i]->cg64.size());
+    phase("hierarchies");
+    for (int i = 0; i < count; ++i)
+        B->depth.push_back((int)(B->mixed ? B->inst[i]->cg32.size() : B->inst[i]->cg64.size()));
 
     // DG groups by degree; each problem starts at a multiple of 32 cells
     for (int i = 0; i < count; ++i) {
@@ -629,6 +647,7 @@ int dgmg_batch_create(int count, const dgmg_mesh *meshes, const int *p, const do
         }
     }
     B->ndof = dof;
+    phase("dg descriptors");
 
     // Q1 levels of all problems (the same order in both precisions)
     std::vector<std::vector<int>> desc(count);
@@ -639,11 +658,13 @@ int dgmg_batch_create(int count, const dgmg_mesh *meshes, const int *p, const do
             B->maxdepth = std::max(B->maxdepth, B->depth[i]);
         }
     }
-    RC(B->upload(&B->C, level_descriptors<double>(*B)));
-    if (B->mixed) RC(B->upload(&B->C32, level_descriptors<float>(*B)));
+    if (B->mixed)
+        RC(B->upload(&B->C32, level_descriptors<float>(*B)));
+    else
+        RC(B->upload(&B->C, level_descriptors<double>(*B)));
     {
         std::vector<VertMap> gm;
-        for (int i = 0; i < count; ++i) push_verts(gm, desc[i][0], B->inst[i]->cg64[0].L.nv);
+        for (int i = 0; i < count; ++i) push_verts(gm, desc[i][0], B->inst[i]->lv[0].nv);
         B->ngather = (int)gm.size();
         RC(B->upload(&B->gather, gm));
     }
@@ -652,12 +673,12 @@ int dgmg_batch_create(int count, const dgmg_mesh *meshes, const int *p, const do
         std::vector<VertMap> fine, next, coarse;
         for (int i = 0; i < count; ++i) {
             if (l >= B->depth[i]) continue;
-            const int64_t nv = B->inst[i]->cg64[l].L.nv;
+            const int64_t nv = B->inst[i]->lv[l].nv;
             if (l == B->depth[i] - 1) {
                 push_verts(coarse, desc[i][l], nv);
             } else {
                 push_verts(fine, desc[i][l], nv);
-                push_verts(next, desc[i][l], B->inst[i]->cg64[l + 1].L.nv);
+                push_verts(next, desc[i][l], B->inst[i]->lv[l + 1].nv);
             }
         }
         auto &m = B->lm[l];
@@ -693,11 +714,14 @@ int dgmg_batch_create(int count, const dgmg_mesh *meshes, const int *p, const do
     LC(cudaStreamCreateWithFlags(&B->capture_stream, cudaStreamNonBlocking));
     for (dgmg_ctx *c : B->inst) B->bytes += c->bytes;
     LC(cudaDeviceSynchronize());
-    if (o.autotune)
+    phase("q1 descriptors");
+    if (o.autotune) {
         for (auto &g : B->groups) {
-            RC(tune_group<double>(*B, g, B->z, B->r, B->capture_stream));
+            RC(tune_group<double>(*B, g, B->z, B->r, B->capture_stream));   // mixed: the FP64 apply only
             if (B->mixed) RC(tune_group<float>(*B, g, B->z32, B->r32, B->capture_stream));
         }
+        phase("autotune");
+    }
     *out = B.release();
     return DGMG_OK;
 }

@@ -421,9 +421,17 @@ static void inverse_eigen_sums(const dgmg_ctx &C, const std::vector<double> &fd,
 }
 
 template <typename T>
-int setup_dg(dgmg_ctx &C, DGDev<T> &D, const std::vector<double> &kappa, const std::vector<double> &fd) {
+int setup_dg(dgmg_ctx &C, DGDev<T> &D, const std::vector<double> &kappa, const std::vector<double> &fd,
+             bool smoother = true) {
     fill_const(C, D.c);
     RC(C.upload(&D.kappa, convert<T>(kappa)));
+    if (!smoother) {                  // operator only (projection, residual): no block-inverse factors
+        const int64_t trn = C.ncell * 2 * C.dim * 2 * (C.nloc / C.q);
+        RC(C.alloc(&D.tr[0], trn));
+        RC(C.alloc(&D.tr[1], trn));
+        RC(C.alloc(&D.corners, C.ncell * (1 << C.dim)));
+        return DGMG_OK;
+    }
     RC(C.upload(&D.fd, convert<T>(fd)));
     if (sizeof(T) == sizeof(double)) {
         std::vector<double> linv;
@@ -835,6 +843,14 @@ void dgmg_default_opts(dgmg_opts *o) {
 }
 
 int dgmg_create(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_opts *opts, dgmg_ctx **out) {
+    return dgmg::create_ctx(mesh, p, kappa, opts, 0, out);
+}
+
+}  // extern "C"
+
+namespace dgmg {
+
+int create_ctx(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_opts *opts, int flags, dgmg_ctx **out) {
     if (!out) return fail(DGMG_EINVAL, "out is NULL");
     *out = nullptr;
     if (!mesh) return fail(DGMG_EINVAL, "mesh is NULL");
@@ -925,9 +941,9 @@ int dgmg_create(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_op
     std::vector<double> fd;
     fast_diag_factors(*C, kap, fd);
     trace.mark("fast-diag");
-    RC(setup_dg<double>(*C, C->d64, kap, fd));
+    RC(setup_dg<double>(*C, C->d64, kap, fd, !(flags & CREATE_NO_FP64_SMOOTHER)));
     trace.mark("dg upload");
-    RC(setup_cg<double>(*C, C->cg64));
+    if (!(flags & CREATE_NO_FP64_Q1)) RC(setup_cg<double>(*C, C->cg64));
     trace.mark("cg upload");
     if (o.precision == DGMG_MIXED_FP32) {
         RC(setup_dg<float>(*C, C->d32, kap, fd));
@@ -940,6 +956,12 @@ int dgmg_create(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_op
             RC(C->alloc(&C->xs32, C->ndof));
             RC(C->alloc(&C->rold32, C->ndof));
         }
+    }
+    if (flags & CREATE_NO_SOLVER) {   // a member of a batch: the batch owns the solver's vectors
+        trace.mark("rest");
+        DG_CUDA(cudaStreamSynchronize(C->setup_stream));
+        *out = C.release();
+        return DGMG_OK;
     }
     RC(C->alloc(&C->w_r, C->ndof));
     RC(C->alloc(&C->w_z, C->ndof));
@@ -981,6 +1003,10 @@ int dgmg_create(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_op
     *out = C.release();
     return DGMG_OK;
 }
+
+}  // namespace dgmg
+
+extern "C" {
 
 int dgmg_destroy(dgmg_ctx *ctx) {
     if (!ctx) return DGMG_OK;

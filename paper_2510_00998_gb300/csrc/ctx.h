@@ -248,6 +248,13 @@ inline const std::vector<CGDev<T>> &cgl(const dgmg_ctx &C) {
         return C.cg64;
 }
 
+// dgmg_create with parts left out for contexts that only serve a batch:
+// no solver workspace (work vectors, scalars, quadrature tables); no FP64
+// block-inverse factors (the FP64 level only applies the operator); no FP64 Q1
+// levels (the V-cycle runs in FP32).
+enum { CREATE_NO_SOLVER = 1, CREATE_NO_FP64_SMOOTHER = 2, CREATE_NO_FP64_Q1 = 4 };
+int create_ctx(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_opts *opts, int flags, dgmg_ctx **out);
+
 int mg_cycle64(dgmg_ctx &C, double *x, const double *b, double *r, cudaStream_t s);
 int project64(dgmg_ctx &C, double *x, cudaStream_t s);
 
