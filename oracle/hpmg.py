@@ -24,7 +24,7 @@ import numpy as np
 import scipy.linalg as sla
 import scipy.sparse as sp
 
-from . import sipg
+from . import refelem, sipg
 
 
 def interior_vertex_count(n):
@@ -159,18 +159,50 @@ def h_prolongation(n, f):
     return P
 
 
+def dg_interp_1d(nodes_f, nodes_c):
+    """I[i, j] = l_j^c(x_i^f): the degree-(q_c - 1) Lagrange basis on nodes_c at
+    the fine nodes (exact injection of the coarse polynomial space)."""
+    return refelem.lagrange_values(nodes_c, nodes_f).T
+
+
+def dg_p_prolongation(mesh_f, mesh_c):
+    """P (ndof_f x ndof_c): cellwise injection of the degree p_c DG space into
+    the degree p_f space on the same mesh, the tensor product of interp_1d along
+    every axis (node index x fastest)."""
+    I1 = dg_interp_1d(mesh_f.nodes, mesh_c.nodes)
+    Pc = I1
+    for _ in range(mesh_f.d - 1):
+        Pc = np.kron(I1, Pc)                          # (z, y, x) ordering: x fastest
+    return sp.kron(sp.identity(mesh_f.ncell, format="csr"), sp.csr_matrix(Pc), format="csr")
+
+
 class Hierarchy:
-    """The DG level plus the CG levels of the hp hierarchy."""
+    """The DG level(s) plus the CG levels of the hp hierarchy.
+
+    gradual=False: the paper's hierarchy, DG degree p straight to continuous Q1.
+    gradual=True: DG degrees p, p-1, ..., 1, then continuous Q1 (the nested
+    sequence V_DG^p > V_DG^(p-1) > ... > V_CG^1 of the paper's outlook,
+    Sec. 6.4). Every lower DG level keeps the finest penalty, so its operator is
+    the Galerkin product P^T A P of the level above; it is smoothed with its own
+    block Jacobi (nu_pre, nu_post steps)."""
 
     def __init__(self, mesh, kappa=None, factor=2, nu_pre=2, nu_post=2,
-                 omega_dg=None, omega_cg=None, interior_only=False):
+                 omega_dg=None, omega_cg=None, interior_only=False, gradual=False):
         self.mesh = mesh
         self.kappa = None if kappa is None else np.asarray(kappa, dtype=np.float64).reshape(-1)
         self.nu_pre, self.nu_post = nu_pre, nu_post
         self.omega_dg = default_omega_dg(mesh.d) if omega_dg is None else omega_dg
         self.omega_cg = default_omega_cg(mesh.d) if omega_cg is None else omega_cg
         self.smoother = sipg.BlockJacobi(mesh, self.kappa, interior_only=interior_only)
-        self.P = p_prolongation(mesh)
+        # lower DG levels (gradual p-coarsening)
+        self.dg_meshes, self.dg_smoothers, self.Pdg = [mesh], [self.smoother], []
+        if gradual:
+            for pc in range(mesh.p - 1, 0, -1):
+                mc = sipg.Mesh(mesh.n, pc, penalty_p=mesh.penalty_p)
+                self.Pdg.append(dg_p_prolongation(self.dg_meshes[-1], mc))
+                self.dg_meshes.append(mc)
+                self.dg_smoothers.append(sipg.BlockJacobi(mc, self.kappa, interior_only=interior_only))
+        self.P = p_prolongation(self.dg_meshes[-1])
         self.ns = [mesh.n]
         self.A = [q1_stiffness(mesh.n, self.kappa)]
         self.Ph = []
@@ -209,20 +241,30 @@ class Hierarchy:
         u = u + self.Ph[level] @ e
         return self.cg_jacobi(level, u, b, self.nu_post)
 
+    def vcycle_dg(self, level, r):
+        """V-cycle from DG level ``level`` with zero initial guess: smoothing,
+        residual, restriction to the next DG level (or to the CG levels below the
+        last DG level), correction, smoothing."""
+        mesh, sm = self.dg_meshes[level], self.dg_smoothers[level]
+        u = np.zeros(mesh.ndof)
+        u = sm.step_alg2(u, r, self.omega_dg, self.nu_pre)
+        res = sipg.residual(mesh, u, r, self.kappa)
+        if level == len(self.dg_meshes) - 1:
+            u = u + self.P @ self.vcycle_cg(0, self.P.T @ res)
+        else:
+            u = u + self.Pdg[level] @ self.vcycle_dg(level + 1, self.Pdg[level].T @ res)
+        return sm.step_alg2(u, r, self.omega_dg, self.nu_post)
+
     def vcycle(self, r):
         """z = V(r): hp V(nu_pre, nu_post) cycle with zero initial guess on the DG level."""
-        mesh = self.mesh
-        u = np.zeros(mesh.ndof)
-        u = self.smoother.step_alg2(u, r, self.omega_dg, self.nu_pre)
-        res = sipg.residual(mesh, u, r, self.kappa)
-        e = self.vcycle_cg(0, self.P.T @ res)
-        u = u + self.P @ e
-        return self.smoother.step_alg2(u, r, self.omega_dg, self.nu_post)
+        return self.vcycle_dg(0, r)
 
     def coarse_grid_correction(self, u, b):
-        """Alg. 6: residual, restriction, one h-V-cycle, prolongation."""
+        """Alg. 6: residual, restriction, one (h- or hp-) V-cycle, prolongation."""
         res = sipg.residual(self.mesh, u, b, self.kappa)
-        return self.P @ self.vcycle_cg(0, self.P.T @ res)
+        if len(self.dg_meshes) == 1:
+            return self.P @ self.vcycle_cg(0, self.P.T @ res)
+        return self.Pdg[0] @ self.vcycle_dg(1, self.Pdg[0].T @ res)
 
 
 def default_omega_dg(d):

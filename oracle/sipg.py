@@ -33,12 +33,16 @@ THETA = -1.0  # symmetric interior penalty in the paper's sign convention
 class Mesh:
     """Uniform tensor-product mesh of the unit box with n[dir] cells along axis dir."""
 
-    def __init__(self, n, p):
+    def __init__(self, n, p, penalty_p=None):
+        """penalty_p: degree whose penalty 2 p (p+1) / h the facets use (default p).
+        A lower level of a gradual p-hierarchy keeps the finest level's penalty:
+        its operator is then the Galerkin restriction of the finest operator."""
         self.n = tuple(int(v) for v in n)
         self.d = len(self.n)
         if self.d not in (2, 3):
             raise ValueError("d must be 2 or 3")
         self.p = int(p)
+        self.penalty_p = self.p if penalty_p is None else int(penalty_p)
         self.q = self.p + 1
         self.h = tuple(1.0 / v for v in self.n)
         self.ncell = int(np.prod(self.n))
@@ -55,8 +59,9 @@ class Mesh:
         self.dp = [dp * (2.0 / h) for h in self.h]         # physical d/dx at the high end
 
     def gamma(self, direction):
-        """Penalty gamma_F = 2 p (p+1) / h for a facet normal to ``direction``."""
-        return 2.0 * self.p * (self.p + 1) / self.h[direction]
+        """Penalty gamma_F = 2 p (p+1) / h for a facet normal to ``direction``
+        (p = penalty_p)."""
+        return 2.0 * self.penalty_p * (self.penalty_p + 1) / self.h[direction]
 
     # axis bookkeeping of the grid view
     def cell_axis(self, direction):

@@ -156,3 +156,72 @@ def test_mgmult_cycles_ballpark_tables_3_4():
         _, k2 = hpmg.mgmult(hier, b, eps=1e-7, residual_kind="prec")
         assert 0.6 * unprec <= k1 <= 2.0 * unprec
         assert 0.6 * prec <= k2 <= 2.0 * prec
+
+
+# ---- gradual p-coarsening (DG p -> p-1 -> ... -> 1 -> Q1)
+
+@pytest.mark.parametrize("n,p", [((3, 4), 3), ((2, 3, 2), 2), ((3, 2), 5)])
+def test_gradual_levels_are_galerkin_products(n, p):
+    """A lower DG level with the finest penalty is exactly P^T A P of the level
+    above (nested polynomial spaces, exact integration): the assembled matrices
+    agree, which pins the DG p-prolongation (node order, interpolation) and the
+    penalty override."""
+    kap = np.exp(np.random.default_rng(2).normal(size=int(np.prod(n))))
+    mf = sipg.Mesh(n, p)
+    mc = sipg.Mesh(n, p - 1, penalty_p=p)
+    P = hpmg.dg_p_prolongation(mf, mc)
+    Af = sipg.assemble(mf, kap).toarray()
+    Ac = sipg.assemble(mc, kap).toarray()
+    G = P.T @ Af @ P
+    assert np.abs(G - Ac).max() <= 1e-11 * np.abs(Ac).max()
+    # with the coarse degree's own penalty the product differs (the override matters)
+    Ac_own = sipg.assemble(sipg.Mesh(n, p - 1), kap).toarray()
+    assert np.abs(G - Ac_own).max() > 1e-3 * np.abs(Ac).max()
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_dg_p_prolongation_injects_polynomials(d):
+    """Interpolation of a degree-(p-1) polynomial to the degree-p nodes is exact."""
+    n, p = (2,) * d, 4
+    mf, mc = sipg.Mesh(n, p), sipg.Mesh(n, p - 1)
+    P = hpmg.dg_p_prolongation(mf, mc)
+    f = lambda X: (1 + X[..., 0] ** 3) * (0.5 - X[..., -1] ** 2) + X[..., 0] * X[..., -1]
+    uc = f(mc.node_coords()).reshape(-1)
+    uf = f(mf.node_coords()).reshape(-1)
+    assert np.abs(P @ uc - uf).max() <= 1e-13
+
+
+def test_gradual_vcycle_symmetric_positive_definite():
+    """Gradual hierarchy: symmetric smoothing around Galerkin coarse levels makes
+    the V-cycle a symmetric positive definite operator."""
+    n, p = (4, 3), 3
+    kap = np.exp(np.random.default_rng(5).normal(size=12))
+    mesh = sipg.Mesh(n, p)
+    h = hpmg.Hierarchy(mesh, kap, gradual=True)
+    assert len(h.dg_meshes) == p
+    rng = np.random.default_rng(6)
+    r, s = rng.normal(size=mesh.ndof), rng.normal(size=mesh.ndof)
+    assert abs(h.vcycle(r) @ s - r @ h.vcycle(s)) <= 1e-11 * abs(r @ h.vcycle(s))
+    V = np.column_stack([h.vcycle(e) for e in np.eye(mesh.ndof)])
+    assert np.linalg.eigvalsh(0.5 * (V + V.T)).min() > 0
+
+
+def test_gradual_p1_equals_direct():
+    """For p = 1 there is no lower DG level: both hierarchies are the same."""
+    mesh = sipg.Mesh((5, 4), 1)
+    r = np.random.default_rng(7).normal(size=mesh.ndof)
+    a = hpmg.Hierarchy(mesh).vcycle(r)
+    b = hpmg.Hierarchy(mesh, gradual=True).vcycle(r)
+    assert np.array_equal(a, b)
+
+
+def test_gradual_coarsening_needs_fewer_cycles():
+    """Shape of the paper's outlook (Sec. 6.4): the block-Jacobi smoother with
+    direct coarsening to Q1 is not p-robust; going down one degree at a time
+    needs fewer MGMult cycles at higher p."""
+    mesh = sipg.Mesh((6, 6), 5)
+    f = lambda x, y: 8 * np.pi ** 2 * np.sin(2 * np.pi * x) * np.sin(2 * np.pi * y)
+    b = sipg.load_vector(mesh, f)
+    _, k_direct = hpmg.mgmult(hpmg.Hierarchy(mesh, factor=3, nu_pre=3, nu_post=3), b, eps=1e-7)
+    _, k_grad = hpmg.mgmult(hpmg.Hierarchy(mesh, factor=3, nu_pre=3, nu_post=3, gradual=True), b, eps=1e-7)
+    assert k_grad < k_direct
