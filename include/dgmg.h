@@ -97,6 +97,12 @@ typedef struct {
                                   /* the DG-level kernels on this mesh and keeps the   */
                                   /* fastest (cached per mesh shape in the process);   */
                                   /* 0 (default): fixed heuristic                      */
+    int p_coarsening;             /* 0 (default): DG degree p straight to continuous   */
+                                  /* Q1 (Sec. 5.2); 1: gradual, DG p, p-1, ..., 1, then */
+                                  /* Q1 (the nested sequence of the outlook of Sec.    */
+                                  /* 6.4), every DG level the Galerkin product of the  */
+                                  /* one above (finest penalty) with its own           */
+                                  /* block-Jacobi smoother and nu_pre/nu_post steps    */
 } dgmg_opts;
 
 typedef struct {
@@ -110,6 +116,8 @@ typedef struct {
     int nu_pre, nu_post, precision, block_inverse, coarsening;
     size_t device_bytes;          /* device memory held by the ctx                     */
     int outer;                    /* DGMG_OUTER_* in use (AUTO resolved)               */
+    int dg_levels;                /* DG levels of the V-cycle (1, or p with gradual    */
+                                  /* p-coarsening)                                     */
     int tiles[6];                 /* cells per CTA of the DG-level kernels in use:     */
                                   /* FP64 projection, smoothing, residual, then FP32   */
                                   /* (mixed precision only, else 0); a smoothing entry */

@@ -277,26 +277,26 @@ namespace dgmg {
 int exact_block(const dgmg_ctx &C) { return C.opts.block_inverse == DGMG_BLOCK_EXACT ? 1 : 0; }
 
 template <typename T>
-void fill_const(const dgmg_ctx &C, DGConst<T> &c) {
+void fill_const(const dgmg_ctx &C, const DGSpace &S, DGConst<T> &c) {
     std::memset(&c, 0, sizeof(c));
-    const int q = C.q;
+    const int q = S.q;
     for (int a = 0; a < 3; ++a) c.n[a] = C.n[a];
     c.ncell = C.ncell;
     for (int a = 0; a < C.dim; ++a) {
         const double h = 1.0 / C.n[a];
         for (int i = 0; i < q * q; ++i) {
-            c.M[a][i] = (T)(C.re.M[i] * h / 2.0);
-            c.K[a][i] = (T)(C.re.K[i] * 2.0 / h);
+            c.M[a][i] = (T)(S.re.M[i] * h / 2.0);
+            c.K[a][i] = (T)(S.re.K[i] * 2.0 / h);
         }
         for (int i = 0; i < q; ++i) {
-            c.d0[a][i] = (T)(C.re.d0[i] * 2.0 / h);
-            c.dp[a][i] = (T)(C.re.dp[i] * 2.0 / h);
+            c.d0[a][i] = (T)(S.re.d0[i] * 2.0 / h);
+            c.dp[a][i] = (T)(S.re.dp[i] * 2.0 / h);
         }
-        c.gamma[a] = (T)(2.0 * C.p * (C.p + 1) / h);
+        c.gamma[a] = (T)(2.0 * S.penalty_p * (S.penalty_p + 1) / h);
     }
     for (int i = 0; i < q; ++i) {
-        c.hat[0][i] = (T)((1.0 - C.re.nodes[i]) / 2.0);
-        c.hat[1][i] = (T)((1.0 + C.re.nodes[i]) / 2.0);
+        c.hat[0][i] = (T)((1.0 - S.re.nodes[i]) / 2.0);
+        c.hat[1][i] = (T)((1.0 + S.re.nodes[i]) / 2.0);
     }
     c.omega = (T)C.opts.omega_dg;
 }
@@ -304,22 +304,22 @@ void fill_const(const dgmg_ctx &C, DGConst<T> &c) {
 // Per-cell fast-diagonalisation factors of the exact diagonal block:
 // Kt_a = kappa_K K_a + low-face and high-face own terms (Sec. 4.1 Schur block),
 // Kt_a S = M_a S diag(lambda), S^T M_a S = I.
-void fast_diag_factors(const dgmg_ctx &C, const std::vector<double> &kappa, std::vector<double> &fd) {
-    const int q = C.q, dim = C.dim, fds = q * q + q;
+void fast_diag_factors(const dgmg_ctx &C, const DGSpace &S, const std::vector<double> &kappa, std::vector<double> &fd) {
+    const int q = S.q, dim = C.dim, fds = q * q + q;
     fd.assign((size_t)C.ncell * dim * fds, 0.0);
     double Linv[3][QMAX * QMAX];
     double Mh[3][QMAX * QMAX], Kh[3][QMAX * QMAX], d0[3][QMAX], dp[3][QMAX], gam[3];
     for (int a = 0; a < dim; ++a) {
         const double h = 1.0 / C.n[a];
         for (int i = 0; i < q * q; ++i) {
-            Mh[a][i] = C.re.M[i] * h / 2.0;
-            Kh[a][i] = C.re.K[i] * 2.0 / h;
+            Mh[a][i] = S.re.M[i] * h / 2.0;
+            Kh[a][i] = S.re.K[i] * 2.0 / h;
         }
         for (int i = 0; i < q; ++i) {
-            d0[a][i] = C.re.d0[i] * 2.0 / h;
-            dp[a][i] = C.re.dp[i] * 2.0 / h;
+            d0[a][i] = S.re.d0[i] * 2.0 / h;
+            dp[a][i] = S.re.dp[i] * 2.0 / h;
         }
-        gam[a] = 2.0 * C.p * (C.p + 1) / h;
+        gam[a] = 2.0 * S.penalty_p * (S.penalty_p + 1) / h;
         cholesky_inverse_lower(q, Mh[a], Linv[a]);
     }
     const bool interior_only = C.opts.block_inverse == DGMG_BLOCK_INTERIOR_ONLY;
@@ -405,15 +405,16 @@ std::vector<T> convert(const std::vector<double> &v) {
 // from the fast-diagonalisation factors (the FP64 smoother multiplies by it
 // instead of dividing: FP64 division is a multi-instruction sequence on the
 // FP64 pipe, which bounds that kernel; the table costs one extra read per DoF).
-static void inverse_eigen_sums(const dgmg_ctx &C, const std::vector<double> &fd, std::vector<double> &linv) {
-    const int q = C.q, dim = C.dim, fds = q * q + q;
-    linv.assign((size_t)C.ndof, 0.0);
+static void inverse_eigen_sums(const dgmg_ctx &C, const DGSpace &S, const std::vector<double> &fd,
+                               std::vector<double> &linv) {
+    const int q = S.q, dim = C.dim, fds = q * q + q;
+    linv.assign((size_t)S.ndof, 0.0);
     parallel_for(C.ncell, [&](int64_t cell) {
         const double *lam0 = &fd[((size_t)cell * dim + 0) * fds + q * q];
         const double *lam1 = &fd[((size_t)cell * dim + 1) * fds + q * q];
         const double *lam2 = dim == 3 ? &fd[((size_t)cell * dim + 2) * fds + q * q] : nullptr;
-        double *out = &linv[(size_t)cell * C.nloc];
-        for (int64_t node = 0; node < C.nloc; ++node) {
+        double *out = &linv[(size_t)cell * S.nloc];
+        for (int64_t node = 0; node < S.nloc; ++node) {
             const int i = (int)(node % q), j = (int)((node / q) % q), k = (int)(node / (q * q));
             out[node] = 1.0 / (lam0[i] + lam1[j] + (lam2 ? lam2[k] : 0.0));
         }
@@ -421,12 +422,15 @@ static void inverse_eigen_sums(const dgmg_ctx &C, const std::vector<double> &fd,
 }
 
 template <typename T>
-int setup_dg(dgmg_ctx &C, DGDev<T> &D, const std::vector<double> &kappa, const std::vector<double> &fd,
-             bool smoother = true) {
-    fill_const(C, D.c);
-    RC(C.upload(&D.kappa, convert<T>(kappa)));
+int setup_dg(dgmg_ctx &C, const DGSpace &S, DGDev<T> &D, const std::vector<double> &kappa,
+             const std::vector<double> &fd, bool smoother = true, const T *shared_kappa = nullptr) {
+    fill_const(C, S, D.c);
+    if (shared_kappa)
+        D.kappa = const_cast<T *>(shared_kappa);
+    else
+        RC(C.upload(&D.kappa, convert<T>(kappa)));
+    const int64_t trn = C.ncell * 2 * C.dim * 2 * (S.nloc / S.q);
     if (!smoother) {                  // operator only (projection, residual): no block-inverse factors
-        const int64_t trn = C.ncell * 2 * C.dim * 2 * (C.nloc / C.q);
         RC(C.alloc(&D.tr[0], trn));
         RC(C.alloc(&D.tr[1], trn));
         RC(C.alloc(&D.corners, C.ncell * (1 << C.dim)));
@@ -435,13 +439,62 @@ int setup_dg(dgmg_ctx &C, DGDev<T> &D, const std::vector<double> &kappa, const s
     RC(C.upload(&D.fd, convert<T>(fd)));
     if (sizeof(T) == sizeof(double)) {
         std::vector<double> linv;
-        inverse_eigen_sums(C, fd, linv);
+        inverse_eigen_sums(C, S, fd, linv);
         RC(C.upload(&D.linv, convert<T>(linv)));
     }
-    const int64_t tr = C.ncell * 2 * C.dim * 2 * (C.nloc / C.q);
-    RC(C.alloc(&D.tr[0], tr));
-    RC(C.alloc(&D.tr[1], tr));
+    RC(C.alloc(&D.tr[0], trn));
+    RC(C.alloc(&D.tr[1], trn));
     RC(C.alloc(&D.corners, C.ncell * (1 << C.dim)));
+    return DGMG_OK;
+}
+
+// The lower DG levels of a gradual p-hierarchy (degrees p-1 .. 1, finest
+// penalty): fast-diagonalisation factors, constants, traces, the level's
+// vectors and the interpolation up to the next finer level, in FP64 and (mixed
+// precision) FP32; the finest residual scratch. dgs[0] (the finest space) is
+// always set.
+int setup_dg_levels(dgmg_ctx &C, const std::vector<double> &kap) {
+    C.dgs.assign(1, finest_space(C));
+    if (C.opts.p_coarsening == 0 || C.p < 2) return DGMG_OK;
+    const bool mixed = C.opts.precision == DGMG_MIXED_FP32;
+    for (int pc = C.p - 1; pc >= 1; --pc) {
+        DGSpace S;
+        S.p = pc;
+        S.q = pc + 1;
+        S.penalty_p = C.p;
+        S.nloc = C.dim == 3 ? (int64_t)S.q * S.q * S.q : (int64_t)S.q * S.q;
+        S.ndof = C.ncell * S.nloc;
+        S.re = make_refelem(pc);
+        C.dgs.push_back(S);
+    }
+    const int L = (int)C.dgs.size();
+    C.lvl64.resize(L);
+    if (mixed) C.lvl32.resize(L);
+    for (int l = 1; l < L; ++l) {
+        const DGSpace &S = C.dgs[l], &F = C.dgs[l - 1];
+        std::vector<double> fd;
+        fast_diag_factors(C, S, kap, fd);
+        // I[i][j] = l_j(x_i): this level's basis at the finer level's nodes
+        std::vector<double> I((size_t)F.q * S.q), val(S.q);
+        for (int i = 0; i < F.q; ++i) {
+            lagrange_at(S.re.nodes, F.re.nodes[i], val.data(), nullptr);
+            for (int j = 0; j < S.q; ++j) I[(size_t)i * S.q + j] = val[j];
+        }
+        auto level = [&](auto &lv, auto *kappa_dev) -> int {
+            using T = typename std::remove_pointer<decltype(kappa_dev)>::type;
+            RC(setup_dg<T>(C, S, lv.D, kap, fd, true, kappa_dev));
+            RC(C.alloc(&lv.z, S.ndof));
+            RC(C.alloc(&lv.b, S.ndof));
+            RC(C.alloc(&lv.r, S.ndof));
+            std::memset(&lv.P, 0, sizeof(lv.P));
+            for (size_t k = 0; k < I.size(); ++k) lv.P.I[k] = (T)I[k];
+            return DGMG_OK;
+        };
+        RC(level(C.lvl64[l], C.d64.kappa));
+        if (mixed) RC(level(C.lvl32[l], C.d32.kappa));
+    }
+    RC(C.alloc(&C.res64, C.ndof));
+    if (mixed) RC(C.alloc(&C.res32, C.ndof));
     return DGMG_OK;
 }
 
@@ -592,43 +645,98 @@ int cg_vcycle(dgmg_ctx &C, int l, cudaStream_t s, T **result) {
     return DGMG_OK;
 }
 
-// z = V(r) on the DG level in precision T (zero initial guess).
+// DG level l of the hierarchy in precision T (0 = the finest), and its tiles
+// (the finest level's tuned ones; launcher defaults below).
 template <typename T>
-int dg_vcycle(dgmg_ctx &C, const T *r, T *z, cudaStream_t s) {
-    DGDev<T> &D = dg<T>(C);
-    const int64_t trn = C.ncell * 2 * C.dim * 2 * (C.nloc / C.q);
-    LC(cudaMemsetAsync(z, 0, sizeof(T) * C.ndof, s));
+DGDev<T> &dg_level(dgmg_ctx &C, int l) {
+    return l == 0 ? dg<T>(C) : dglevels<T>(C)[l].D;
+}
+
+template <typename T>
+int level_smooth(dgmg_ctx &C, int l, T *z, const T *b, int cur, cudaStream_t s) {
+    DGDev<T> &D = dg_level<T>(C, l);
+    C.prof.begin(ST_SMOOTH, s);
+    LC(launch_smooth<T>(C.dim, C.dgs[l].q, D.c, l == 0 ? C.tile_of<T>(TILE_SMOOTH) : 0, exact_block(C), z, b,
+                        D.kappa, D.fd, D.linv, D.tr[cur], D.tr[cur ^ 1], s));
+    C.prof.end(s);
+    return DGMG_OK;
+}
+
+template <typename T>
+int level_cycle(dgmg_ctx &C, int l, const T *b, T *z, cudaStream_t s);
+
+// Coarse-grid correction of the iterate z of DG level l for the right-hand side
+// b, whose projections are in tr[cur]: the residual is restricted to the next
+// level (the next DG level, or the Q1 levels below the last one), solved there
+// by one cycle with zero initial guess, and the correction is prolongated into
+// z; the projections of the new z end in tr[0].
+template <typename T>
+int coarse_correction(dgmg_ctx &C, int l, T *z, const T *b, int cur, cudaStream_t s) {
+    DGDev<T> &D = dg_level<T>(C, l);
+    const DGSpace &S = C.dgs[l];
+    const int tres = l == 0 ? C.tile_of<T>(TILE_RESIDUAL) : 0, tproj = l == 0 ? C.tile_of<T>(TILE_PROJECT) : 0;
+    if (l == (int)C.dgs.size() - 1) {
+        C.prof.begin(ST_RESIDUAL, s);
+        LC(launch_residual<T>(C.dim, S.q, D.c, tres, RES_HAS_B | RES_CORNERS, z, b, D.kappa, D.tr[cur], nullptr,
+                              D.corners, s));
+        C.prof.end(s);
+        auto &lv = cgl<T>(C);
+        C.prof.begin(ST_CG, s);
+        LC(launch_corner_gather<T>(C.dim, C.n, D.corners, lv[0].b, s));
+        T *e0 = nullptr;
+        RC(cg_vcycle<T>(C, 0, s, &e0));
+        C.prof.end(s);
+        C.prof.begin(ST_PROJECT, s);
+        LC(launch_project<T>(C.dim, S.q, D.c, tproj, z, e0, D.tr[0], s));   // z += P e0
+        C.prof.end(s);
+        return DGMG_OK;
+    }
+    auto &lvl = dglevels<T>(C);
+    DGLevelDev<T> &N = lvl[l + 1];
+    T *res = l == 0 ? (std::is_same<T, float>::value ? (T *)C.res32 : (T *)C.res64) : lvl[l].r;
+    C.prof.begin(ST_RESIDUAL, s);
+    LC(launch_residual<T>(C.dim, S.q, D.c, tres, RES_HAS_B | RES_WRITE_R, z, b, D.kappa, D.tr[cur], res, nullptr,
+                          s));
+    C.prof.end(s);
+    C.prof.begin(ST_CG, s);
+    LC(launch_dg_transfer<T>(C.dim, S.q, false, C.ncell, N.P, res, N.b, s));
+    C.prof.end(s);
+    RC(level_cycle<T>(C, l + 1, N.b, N.z, s));
+    C.prof.begin(ST_CG, s);
+    LC(launch_dg_transfer<T>(C.dim, S.q, true, C.ncell, N.P, N.z, z, s));
+    C.prof.end(s);
+    C.prof.begin(ST_PROJECT, s);
+    LC(launch_project<T>(C.dim, S.q, D.c, tproj, z, nullptr, D.tr[0], s));
+    C.prof.end(s);
+    return DGMG_OK;
+}
+
+// One V(nu_pre, nu_post) cycle from DG level l with zero initial guess.
+template <typename T>
+int level_cycle(dgmg_ctx &C, int l, const T *b, T *z, cudaStream_t s) {
+    DGDev<T> &D = dg_level<T>(C, l);
+    const DGSpace &S = C.dgs[l];
+    const int64_t trn = C.ncell * 2 * C.dim * 2 * (S.nloc / S.q);
+    LC(cudaMemsetAsync(z, 0, sizeof(T) * S.ndof, s));
     LC(cudaMemsetAsync(D.tr[0], 0, sizeof(T) * trn, s));   // projections of z = 0
     int cur = 0;
     for (int k = 0; k < C.opts.nu_pre; ++k) {
-        C.prof.begin(ST_SMOOTH, s);
-        LC(launch_smooth<T>(C.dim, C.q, D.c, C.tile_of<T>(TILE_SMOOTH), exact_block(C), z, r, D.kappa, D.fd,
-                            D.linv, D.tr[cur], D.tr[cur ^ 1], s));
-        C.prof.end(s);
+        RC(level_smooth<T>(C, l, z, b, cur, s));
         cur ^= 1;
     }
-    C.prof.begin(ST_RESIDUAL, s);
-    LC(launch_residual<T>(C.dim, C.q, D.c, C.tile_of<T>(TILE_RESIDUAL), RES_HAS_B | RES_CORNERS, z, r, D.kappa,
-                          D.tr[cur], nullptr, D.corners, s));
-    C.prof.end(s);
-    auto &lv = cgl<T>(C);
-    C.prof.begin(ST_CG, s);
-    LC(launch_corner_gather<T>(C.dim, C.n, D.corners, lv[0].b, s));
-    T *e0 = nullptr;
-    RC(cg_vcycle<T>(C, 0, s, &e0));
-    C.prof.end(s);
-    C.prof.begin(ST_PROJECT, s);
-    LC(launch_project<T>(C.dim, C.q, D.c, C.tile_of<T>(TILE_PROJECT), z, e0, D.tr[0], s));   // z += P e0
-    C.prof.end(s);
+    RC(coarse_correction<T>(C, l, z, b, cur, s));
     cur = 0;
     for (int k = 0; k < C.opts.nu_post; ++k) {
-        C.prof.begin(ST_SMOOTH, s);
-        LC(launch_smooth<T>(C.dim, C.q, D.c, C.tile_of<T>(TILE_SMOOTH), exact_block(C), z, r, D.kappa, D.fd,
-                            D.linv, D.tr[cur], D.tr[cur ^ 1], s));
-        C.prof.end(s);
+        RC(level_smooth<T>(C, l, z, b, cur, s));
         cur ^= 1;
     }
     return DGMG_OK;
+}
+
+// z = V(r) on the DG level in precision T (zero initial guess).
+template <typename T>
+int dg_vcycle(dgmg_ctx &C, const T *r, T *z, cudaStream_t s) {
+    return level_cycle<T>(C, 0, r, z, s);
 }
 
 // One cycle of the stationary hp-multigrid iteration (Alg. 7, MGMult) in FP64:
@@ -640,24 +748,10 @@ int mg_cycle64(dgmg_ctx &C, double *x, const double *b, double *r, cudaStream_t 
     DGDev<double> &D = C.d64;
     int cur = 0;
     for (int k = 0; k < C.opts.nu_pre; ++k) {
-        C.prof.begin(ST_SMOOTH, s);
-        LC(launch_smooth<double>(C.dim, C.q, D.c, C.tile[0][TILE_SMOOTH], exact_block(C), x, b, D.kappa, D.fd,
-                                 D.linv, D.tr[cur], D.tr[cur ^ 1], s));
-        C.prof.end(s);
+        RC(level_smooth<double>(C, 0, x, b, cur, s));
         cur ^= 1;
     }
-    C.prof.begin(ST_RESIDUAL, s);
-    LC(launch_residual<double>(C.dim, C.q, D.c, C.tile[0][TILE_RESIDUAL], RES_HAS_B | RES_CORNERS, x, b, D.kappa,
-                               D.tr[cur], nullptr, D.corners, s));
-    C.prof.end(s);
-    C.prof.begin(ST_CG, s);
-    LC(launch_corner_gather<double>(C.dim, C.n, D.corners, C.cg64[0].b, s));
-    double *e0 = nullptr;
-    RC(cg_vcycle<double>(C, 0, s, &e0));
-    C.prof.end(s);
-    C.prof.begin(ST_PROJECT, s);
-    LC(launch_project<double>(C.dim, C.q, D.c, C.tile[0][TILE_PROJECT], x, e0, D.tr[0], s));   // x += P e0
-    C.prof.end(s);
+    RC(coarse_correction<double>(C, 0, x, b, cur, s));
     if (r) {
         C.prof.begin(ST_RESIDUAL, s);
         LC(launch_residual<double>(C.dim, C.q, D.c, C.tile[0][TILE_RESIDUAL], RES_HAS_B | RES_WRITE_R, x, b,
@@ -840,6 +934,7 @@ void dgmg_default_opts(dgmg_opts *o) {
     o->outer = DGMG_OUTER_AUTO;
     o->delta = 0.1;
     o->autotune = 0;
+    o->p_coarsening = 0;
 }
 
 int dgmg_create(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_opts *opts, dgmg_ctx **out) {
@@ -879,6 +974,7 @@ int create_ctx(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_opt
     if (o.outer == DGMG_OUTER_RELIABLE && o.precision != DGMG_MIXED_FP32)
         return fail(DGMG_EINVAL, "DGMG_OUTER_RELIABLE needs DGMG_MIXED_FP32");
     if (!(o.delta > 0 && o.delta < 1)) return fail(DGMG_EINVAL, "delta must be in (0, 1)");
+    if (o.p_coarsening != 0 && o.p_coarsening != 1) return fail(DGMG_EINVAL, "p_coarsening must be 0 or 1");
     if (o.outer == DGMG_OUTER_AUTO) o.outer = o.precision == DGMG_MIXED_FP32 ? DGMG_OUTER_RELIABLE : DGMG_OUTER_PCG;
 
     std::unique_ptr<dgmg_ctx> C(new dgmg_ctx());
@@ -939,14 +1035,15 @@ int create_ctx(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_opt
     trace.mark("coarse inverse");
 
     std::vector<double> fd;
-    fast_diag_factors(*C, kap, fd);
+    const DGSpace S0 = finest_space(*C);
+    fast_diag_factors(*C, S0, kap, fd);
     trace.mark("fast-diag");
-    RC(setup_dg<double>(*C, C->d64, kap, fd, !(flags & CREATE_NO_FP64_SMOOTHER)));
+    RC(setup_dg<double>(*C, S0, C->d64, kap, fd, !(flags & CREATE_NO_FP64_SMOOTHER)));
     trace.mark("dg upload");
     if (!(flags & CREATE_NO_FP64_Q1)) RC(setup_cg<double>(*C, C->cg64));
     trace.mark("cg upload");
     if (o.precision == DGMG_MIXED_FP32) {
-        RC(setup_dg<float>(*C, C->d32, kap, fd));
+        RC(setup_dg<float>(*C, S0, C->d32, kap, fd));
         RC(setup_cg<float>(*C, C->cg32));
         RC(C->alloc(&C->r32, C->ndof));
         RC(C->alloc(&C->z32, C->ndof));
@@ -957,6 +1054,8 @@ int create_ctx(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_opt
             RC(C->alloc(&C->rold32, C->ndof));
         }
     }
+    RC(setup_dg_levels(*C, kap));
+    trace.mark("dg levels");
     if (flags & CREATE_NO_SOLVER) {   // a member of a batch: the batch owns the solver's vectors
         trace.mark("rest");
         DG_CUDA(cudaStreamSynchronize(C->setup_stream));
@@ -1037,6 +1136,7 @@ int dgmg_info(const dgmg_ctx *C, dgmg_info_t *info) {
     info->coarsening = C->opts.coarsening;
     info->device_bytes = C->bytes;
     info->outer = C->opts.outer;
+    info->dg_levels = (int)C->dgs.size();
     const bool mixed = C->opts.precision == DGMG_MIXED_FP32;
     for (int k = 0; k < 6; ++k) info->tiles[k] = (k < 3 || mixed) ? C->tile[k / 3][k % 3] : 0;
     return DGMG_OK;
@@ -1242,6 +1342,19 @@ int dgmg_estimate_bytes(const dgmg_mesh *mesh, int p, const dgmg_opts *opts, siz
     size_t total = sz(nv * nv, 8) + dg64 + cg64 + 5 * sz(ndof, 8) + sz(S_NSCAL, 8) + sz(2 * DOT_BLOCKS, 8) +
                    sz(p + 2, 8) + sz((int64_t)q * (p + 2), 8) + sz(3 * (p + 2), 8);
     if (mixed) total += dg32 + cg32 + 2 * sz(ndof, 4) + (reliable ? 4 * sz(ndof, 4) : 0);
+    if (o.p_coarsening == 1 && p >= 2) {
+        // lower DG levels p-1 .. 1 (kappa shared with the finest level): factors,
+        // traces, corners, iterate, right-hand side and residual; FP64 also the
+        // table of inverse eigenvalue sums; the finest residual scratch
+        for (int pc = p - 1; pc >= 1; --pc) {
+            const int ql = pc + 1;
+            const int64_t nl = dim == 3 ? (int64_t)ql * ql * ql : (int64_t)ql * ql, nd = ncell * nl;
+            const int64_t trl = ncell * 2 * dim * 2 * (nl / ql), fdl = ncell * dim * (ql * ql + ql);
+            total += sz(fdl, 8) + sz(nd, 8) + 2 * sz(trl, 8) + sz(ncell << dim, 8) + 3 * sz(nd, 8);
+            if (mixed) total += sz(fdl, 4) + 2 * sz(trl, 4) + sz(ncell << dim, 4) + 3 * sz(nd, 4);
+        }
+        total += sz(ndof, 8) + (mixed ? sz(ndof, 4) : 0);
+    }
     *bytes = total;
     return DGMG_OK;
 }

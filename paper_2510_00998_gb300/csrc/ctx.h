@@ -101,6 +101,26 @@ struct StageProfiler {
     }
 };
 
+// A DG space of the hierarchy: degree, nodes per axis, 1D reference element
+// and the degree whose penalty its facets use (the finest degree on every
+// level of a gradual p-hierarchy, which makes each level the Galerkin product
+// of the one above).
+struct DGSpace {
+    int p = 0, q = 0, penalty_p = 0;
+    int64_t nloc = 0, ndof = 0;
+    RefElem1D re;
+};
+
+// A lower DG level of a gradual p-hierarchy (levels 1 .. L-1; level 0 is the
+// finest, held in dgmg_ctx::d64 / d32): its operator data, its iterate,
+// right-hand side and residual, and the interpolation up to the next finer level.
+template <typename T>
+struct DGLevelDev {
+    DGDev<T> D;
+    T *z = nullptr, *b = nullptr, *r = nullptr;
+    DGInterp<T> P;
+};
+
 struct dgmg_ctx {
     int dim = 0, p = 0, q = 0;
     int n[3] = {1, 1, 1};
@@ -122,6 +142,13 @@ struct dgmg_ctx {
     DGDev<float> d32;
     std::vector<CGDev<double>> cg64;
     std::vector<CGDev<float>> cg32;
+    // DG spaces of the hierarchy ([0] = finest); more than one with gradual
+    // p-coarsening, whose lower levels live in lvl64 / lvl32 ([0] unused)
+    std::vector<DGSpace> dgs;
+    std::vector<DGLevelDev<double>> lvl64;
+    std::vector<DGLevelDev<float>> lvl32;
+    double *res64 = nullptr;                      // finest-level residual before its restriction
+    float *res32 = nullptr;
     // work vectors
     float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *xs32 = nullptr, *rold32 = nullptr;
     double *w_r = nullptr, *w_z = nullptr, *w_p = nullptr, *w_q = nullptr, *w_rold = nullptr;
@@ -218,6 +245,25 @@ int dg_vcycle(dgmg_ctx &C, const T *r, T *z, cudaStream_t s);
 // next stretch of device work on the run's stream and returns without waiting;
 // it returns 1 once the solve has finished (status and stats final), 0 while it
 // waits for device scalars or has more work to queue.
+template <typename T>
+inline std::vector<DGLevelDev<T>> &dglevels(dgmg_ctx &C) {
+    if constexpr (std::is_same<T, float>::value)
+        return C.lvl32;
+    else
+        return C.lvl64;
+}
+
+inline DGSpace finest_space(const dgmg_ctx &C) {
+    DGSpace S;
+    S.p = C.p;
+    S.q = C.q;
+    S.penalty_p = C.p;
+    S.nloc = C.nloc;
+    S.ndof = C.ndof;
+    S.re = C.re;
+    return S;
+}
+
 // the DG level and the Q1 levels of ctx in precision T
 template <typename T>
 inline DGDev<T> &dg(dgmg_ctx &C) {

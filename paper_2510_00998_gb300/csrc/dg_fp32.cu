@@ -45,6 +45,12 @@ cudaError_t launch_zero_traces_batch<float>(int dim, int q, const BatchDG<float>
     return launch_zero_traces_batch_impl<float>(dim, q, D, count, s);
 }
 
+template <>
+cudaError_t launch_dg_transfer<float>(int dim, int qf, bool prolong, int64_t ncell, const DGInterp<float> &P,
+                                   const float *in, float *out, cudaStream_t s) {
+    return launch_dg_transfer_impl<float>(dim, qf, prolong, ncell, P, in, out, s);
+}
+
 cudaError_t wait_timeouts_fp32(unsigned long long *count) { return read_wait_timeouts(count); }
 
 }  // namespace dgmg

@@ -45,6 +45,12 @@ cudaError_t launch_zero_traces_batch<double>(int dim, int q, const BatchDG<doubl
     return launch_zero_traces_batch_impl<double>(dim, q, D, count, s);
 }
 
+template <>
+cudaError_t launch_dg_transfer<double>(int dim, int qf, bool prolong, int64_t ncell, const DGInterp<double> &P,
+                                   const double *in, double *out, cudaStream_t s) {
+    return launch_dg_transfer_impl<double>(dim, qf, prolong, ncell, P, in, out, s);
+}
+
 cudaError_t wait_timeouts_fp64(unsigned long long *count) { return read_wait_timeouts(count); }
 
 }  // namespace dgmg

@@ -722,6 +722,7 @@ __global__ void __launch_bounds__(256) k_residual(DGConst<T> c, int cpb, int mod
 }  // namespace dgmg
 
 #include "smooth_cells.cuh"
+#include "dg_transfer.cuh"
 
 namespace dgmg {
 

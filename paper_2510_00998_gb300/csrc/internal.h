@@ -84,6 +84,18 @@ struct CGLevelDev {
     int mc[3];               // interior vertices per axis of the coarser level
 };
 
+// Interpolation from DG degree q_c - 1 = q_f - 2 to degree q_f - 1 on the same
+// cell: I[i_f][j_c] = l_j^c(x_i^f), row-major q_f x q_c (gradual p-hierarchy).
+template <typename T>
+struct DGInterp {
+    T I[QMAX * QMAX];
+};
+// prolong: out += (I (x) I (x) I) in (coarse -> fine); else out = (I^T (x) ...) in.
+// qf: nodes per axis of the finer level (3..7).
+template <typename T>
+cudaError_t launch_dg_transfer(int dim, int qf, bool prolong, int64_t ncell, const DGInterp<T> &P, const T *in,
+                               T *out, cudaStream_t s);
+
 // ---- batched launches: many independent instances of one degree share a launch
 // Per instance (DG level): its constants (mesh, h-scaled 1D matrices), its first
 // cell in the group's concatenated vectors (a multiple of 32 cells, so every

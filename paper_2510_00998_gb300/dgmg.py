@@ -47,7 +47,7 @@ class Opts(ctypes.Structure):
                 ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int), ("precision", ctypes.c_int),
                 ("block_inverse", ctypes.c_int), ("coarsening", ctypes.c_int),
                 ("rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("outer", ctypes.c_int),
-                ("delta", ctypes.c_double), ("autotune", ctypes.c_int)]
+                ("delta", ctypes.c_double), ("autotune", ctypes.c_int), ("p_coarsening", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -57,7 +57,8 @@ class Info(ctypes.Structure):
                 ("omega_dg", ctypes.c_double), ("omega_cg", ctypes.c_double),
                 ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int), ("precision", ctypes.c_int),
                 ("block_inverse", ctypes.c_int), ("coarsening", ctypes.c_int),
-                ("device_bytes", ctypes.c_size_t), ("outer", ctypes.c_int), ("tiles", ctypes.c_int * 6)]
+                ("device_bytes", ctypes.c_size_t), ("outer", ctypes.c_int), ("dg_levels", ctypes.c_int),
+                ("tiles", ctypes.c_int * 6)]
 
 
 class Stats(ctypes.Structure):

@@ -70,7 +70,7 @@ def sin_product_rhs_2d(ctx, device):
     return b
 
 
-def tables34(meshes=(9, 27, 81, 243), degrees=(2, 3, 4, 5, 6), nu=3, device="cuda"):
+def tables34(meshes=(9, 27, 81, 243), degrees=(2, 3, 4, 5, 6), nu=3, device="cuda", p_coarsening=0):
     """MGMult cycles (Alg. 7) to reduce the unpreconditioned and the
     preconditioned residual by 1e-7 on n x n meshes, factor-3 h-coarsening, the
     "sin-product" right-hand side: the setting of the paper's Tables 3-4.
@@ -83,7 +83,7 @@ def tables34(meshes=(9, 27, 81, 243), degrees=(2, 3, 4, 5, 6), nu=3, device="cud
             ks = []
             for outer in (dgmg.DGMG_OUTER_MGMULT, dgmg.DGMG_OUTER_MGMULT_PREC):
                 ctx = dgmg.Context((n, n), p, outer=outer, coarsening=3, nu_pre=nu, nu_post=nu, rtol=1e-7,
-                                   maxit=1000)
+                                   maxit=1000, p_coarsening=p_coarsening)
                 b = sin_product_rhs_2d(ctx, device)
                 x = torch.zeros_like(b)
                 st, _ = ctx.solve(b, x)
@@ -151,8 +151,12 @@ def main():
             kw["max_active"] = a.max_active
         print(json.dumps(run_serve(**kw)))
     elif a.name == "tables34":
-        res = tables34()
-        print(json.dumps({f"{n}x{n} p={p}": {"unprec": v[0], "prec": v[1]} for (n, p), v in res.items()}))
+        out = {}
+        for pc in (0, 1):
+            res = tables34(p_coarsening=pc)
+            out["gradual" if pc else "direct"] = {f"{n}x{n} p={p}": {"unprec": v[0], "prec": v[1]}
+                                                  for (n, p), v in res.items()}
+        print(json.dumps(out))
     else:
         print(json.dumps(run(a.name, a.solves, a.warmup)))
 
