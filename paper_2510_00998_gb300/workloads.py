@@ -29,6 +29,10 @@ WORKLOADS = {
     "3d32_p3": dict(n=(32, 32, 32), p=3, kappa=None, precision=0),
     "3d64_p4_mixed": dict(n=(64, 64, 64), p=4, kappa="lognormal3", precision=1),
     "3d64_p4_fp64": dict(n=(64, 64, 64), p=4, kappa="lognormal3", precision=0),
+    # the same problems with gradual p-coarsening (DG p, p-1, ..., 1, then Q1)
+    "3d32_p3_gradual": dict(n=(32, 32, 32), p=3, kappa=None, precision=0, p_coarsening=1),
+    "3d64_p4_mixed_gradual": dict(n=(64, 64, 64), p=4, kappa="lognormal3", precision=1, p_coarsening=1),
+    "3d64_p4_fp64_gradual": dict(n=(64, 64, 64), p=4, kappa="lognormal3", precision=0, p_coarsening=1),
 }
 
 
@@ -98,7 +102,8 @@ def make(name, device="cuda", **overrides):
     from . import dgmg
     w = dict(WORKLOADS[name])
     w.update(overrides)
-    ctx = dgmg.Context(w["n"], w["p"], kappa_field(w["kappa"], w["n"]), precision=w["precision"], autotune=1)
+    ctx = dgmg.Context(w["n"], w["p"], kappa_field(w["kappa"], w["n"]), precision=w["precision"], autotune=1,
+                       p_coarsening=w.get("p_coarsening", 0))
     return ctx, sine_rhs(ctx, device)
 
 
