@@ -54,6 +54,8 @@ def parse():
     # a profiler, whose per-launch overhead distorts the tuner's timings (for this
     # workload the defaults are the tiles the tuner picks)
     ap.add_argument("--no-autotune", action="store_true")
+    # skip the 64^3 p=4 mixed-precision section (the FP32 smoothing step)
+    ap.add_argument("--no-mixed", action="store_true")
     return ap.parse_args()
 
 
@@ -210,6 +212,67 @@ SERVE_REQUESTS = 24
 SERVE_RATE = 2.0      # arrival rate as a multiple of the FP64 one-at-a-time capacity
 
 
+def measured_hbm_gbs():
+    """Copy bandwidth measured on this machine (MEASURED_PEAKS.json beside bench.py),
+    else the profiling recipe's fallback."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def timed_ms(fn, flush, stream, reps):
+    """Mean device time of fn() over reps calls, L2 flushed before each (outside
+    the events)."""
+    import torch
+    total = 0.0
+    for _ in range(reps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1)
+    return total / reps
+
+
+def mixed_section(flush, stream):
+    """64^3 cells, p = 4, lognormal kappa: the FP32 V-cycle inside reliable-update
+    FP32 CG with FP64 residuals; solve time and the FP32 smoothing step against the
+    HBM roofline (algorithmic bytes per launch / mean launch time)."""
+    import torch
+    from paper_2510_00998_gb300 import dgmg, workloads
+    ctx, b = workloads.make("3d64_p4_mixed")
+    x = torch.zeros_like(b)
+
+    def solve():
+        x.zero_()
+        return ctx.solve(b, x)[0]
+
+    st = solve()
+    ms = timed_ms(solve, flush, stream, 2)
+    ctx.profile(True)
+    solve()
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    sm_ms = prof["smooth"][0] / max(prof["smooth"][1], 1)
+    d, q = 3, 5
+    nbytes = smooth_bytes_per_cell(d, q, 4) * ctx.info.ncell
+    peak, how = measured_hbm_gbs()
+    achieved = nbytes / (sm_ms * 1e-3) / 1e9
+    kern = "k_smooth_cells<float,5>" if ctx.info.tiles[4] == 0 else "k_smooth<3,5,float>"
+    return {"workload": "sipg_3d_64^3_p4_lognormal_kappa_mixed", "ndof": ctx.ndof, "solve_ms": ms,
+            "iterations": st.iterations, "rel_residual": st.rel_residual, "fp64_applies": st.fp64_applies,
+            "smoothing_step": {"kernel": kern, "avg_launch_ms": sm_ms, "gdofs": ctx.ndof / (sm_ms * 1e-3) / 1e9,
+                               "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
+                                            "unit": "GB/s", "frac": achieved / peak, "peak_source": how,
+                                            "bytes_per_launch": nbytes}}}
+
+
 def serving_run():
     """Solves/s and p50/p99 latency (arrival to completion, rel. residual 1e-10)
     of the mixed-precision solve server against plain FP64 one-at-a-time solving,
@@ -330,9 +393,18 @@ def run_gb300(args):
             e2e_units += float(ndof) * st.iterations * (ctx.opts.nu_pre + ctx.opts.nu_post)
     e2e_t, e2e_u = reduce_max_sum((e2e_ms, e2e_units), world, dev)
 
+    # GDoF/s of one FP64 apply (warm-up projection + cell equation) and the time
+    # of one FP64 V-cycle, on the same context
+    y = torch.empty_like(b)
+    apply_ms = timed_ms(lambda: ctx.apply(b, y), flush, stream, 10)
+    vcycle_ms = timed_ms(lambda: ctx.vcycle(b, y), flush, stream, 10)
+
     serving = None
     if rank == 0 and not args.no_serving:
         serving = serving_run()
+    mixed = None
+    if rank == 0 and not args.no_mixed:
+        mixed = mixed_section(flush, stream)
 
     # the smoothing kernel the tuned context runs (tile 0 = one thread per cell)
     cells_kernel = ctx.info.tiles[1] == 0 and d == 3 and q <= 4
@@ -369,6 +441,9 @@ def run_gb300(args):
             "solves_per_s": args.steps / (t_max * 1e-3),
             "iterations": statistics.median(iters), "rel_residual_max": max(relres),
             "smoothing_steps": smooth_steps_total, "stage_share": shares,
+            "apply": {"ms": apply_ms, "gdofs": ndof / (apply_ms * 1e-3) / 1e9},
+            "vcycle_ms": vcycle_ms,
+            "mixed_64cube_p4": mixed,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)
