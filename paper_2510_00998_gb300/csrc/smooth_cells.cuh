@@ -117,11 +117,12 @@ struct CellGeo {
     // area A is staged. That halves the shared memory per CTA, so more CTAs
     // are resident (a 32^3 mesh fits in one wave).
     static constexpr bool LEAN = sizeof(T) == 8;
-    // shared memory (values of T), per cell: area A holds b, then the factors,
-    // then the new u; area B (FP32) holds two neighbour-face slots, then the
-    // previous u, then two faces of new traces
-    static constexpr int PA = NL > 3 * FDS ? NL : 3 * FDS;
-    static constexpr int PB = LEAN ? 0 : (NL > 4 * NF ? NL : 4 * NF);
+    // shared memory (values of T), per cell. FP32: area A holds b, then the
+    // previous u (prefetched as soon as b is in registers), then the new u; area
+    // B holds two neighbour-face slots, then the factors, then two faces of new
+    // traces. FP64: area A holds b, then the factors, then the new u.
+    static constexpr int PA = LEAN ? (NL > 3 * FDS ? NL : 3 * FDS) : NL;
+    static constexpr int PB = LEAN ? 0 : (4 * NF > 3 * FDS ? 4 * NF : 3 * FDS);
     static constexpr size_t OFF_B = (size_t)W * PA;
     static constexpr size_t OFF_K = OFF_B + (size_t)W * PB;   // kF [6][W]
     static constexpr size_t OFF_NB = OFF_K + 6 * W;          // neighbour cell [6][W] (int)
@@ -314,8 +315,8 @@ __device__ __forceinline__ void smooth_cells_body(const DGConst<T> &c, int64_t c
     using G = CellGeo<T, Q>;
     constexpr int W = G::W, NL = G::NL, NF = G::NF, FDS = G::FDS, TR = G::TR;
     extern __shared__ __align__(128) unsigned char smem_c[];
-    T *sA = reinterpret_cast<T *>(smem_c);              // b -> factors -> new u
-    T *sB = sA + G::OFF_B;                               // face slots -> (table) -> previous u -> new traces
+    T *sA = reinterpret_cast<T *>(smem_c);              // b -> previous u (FP32) or factors (FP64) -> new u
+    T *sB = sA + G::OFF_B;                               // FP32: face slots -> factors -> new traces
     // face slot s (0, 1) of area B: sB + s * W * 2 NF
     T *sK = sA + G::OFF_K;
     int *sNb = reinterpret_cast<int *>(sA + G::OFF_NB);
@@ -378,10 +379,14 @@ __device__ __forceinline__ void smooth_cells_body(const DGConst<T> &c, int64_t c
     T R[NL];
 #pragma unroll
     for (int e = 0; e < NL; ++e) R[e] = active ? sA[lane * NL + e] : T(0);
-    // the factors into the same area, behind the facet work
+    // FP32: the previous iterate into the same area (behind the facet work and
+    // the inverse); FP64: the factors
     fence_proxy_async_smem();
     __syncwarp();
-    stage_bulk<T>(full, lane, &bars[1], sA, fd + cell0 * 3 * FDS, W * 3 * FDS, ncl * 3 * FDS);
+    if (G::LEAN)
+        stage_bulk<T>(full, lane, &bars[1], sA, fd + cell0 * 3 * FDS, W * 3 * FDS, ncl * 3 * FDS);
+    else
+        stage_bulk<T>(full, lane, &bars[1], sA, u + cell0 * NL, W * NL, ncl * NL);
 
     // r -= N u_nb: the two faces normal to axis p, then rotate the next axis to x
 #pragma unroll 1
@@ -414,24 +419,24 @@ __device__ __forceinline__ void smooth_cells_body(const DGConst<T> &c, int64_t c
         }
         rotate<T, Q>(R);
     }
-    // FP32: the previous iterate into area B (the face slots are free now)
+    // FP32: the factors into area B (the face slots are free now)
     if (!G::LEAN) {
         fence_proxy_async_smem();
         __syncwarp();
-        stage_bulk<T>(full, lane, &bars[2], sB, u + cell0 * NL, W * NL, ncl * NL);
+        stage_bulk<T>(full, lane, &bars[2], sB, fd + cell0 * 3 * FDS, W * 3 * FDS, ncl * 3 * FDS);
     }
 
     // A_KK^{-1} by fast diagonalisation: S^T along x, y, z; scale by the
     // inverse eigenvalue sums; S along z, y, x
     if (full) {
-        if (!warp_wait_copies(&bars[1], lane)) {
-            if (!G::LEAN) warp_wait_copies(&bars[2], lane);
+        if (!warp_wait_copies(&bars[G::LEAN ? 1 : 2], lane)) {
+            if (!G::LEAN) warp_wait_copies(&bars[1], lane);
             return;
         }
     } else {
         __syncwarp();
     }
-    const T *myFD = sA + lane * 3 * FDS;
+    const T *myFD = (G::LEAN ? sA : sB) + lane * 3 * FDS;
     if (active) {
 #pragma unroll 1
         for (int p = 0; p < 3; ++p) {
@@ -472,16 +477,17 @@ __device__ __forceinline__ void smooth_cells_body(const DGConst<T> &c, int64_t c
         }
     }
 
-    // u <- (1 - w) u + w y, stored through area A
+    // u <- (1 - w) u + w y, stored through area A (the barrier also ends every
+    // lane's reads of the factors before area A (FP64) or B (FP32) is rewritten)
     if (!G::LEAN && full) {
-        if (!warp_wait_copies(&bars[2], lane)) return;
+        if (!warp_wait_copies(&bars[1], lane)) return;
     } else {
         __syncwarp();
     }
-    T *myU = sA + lane * NL;                            // overlaps other lanes' factors: after the barrier
+    T *myU = sA + lane * NL;
     if (active) {
         const T om = c.omega, keep = T(1) - om;
-        const T *uo = G::LEAN ? u + cell * NL : sB + lane * NL;
+        const T *uo = G::LEAN ? u + cell * NL : sA + lane * NL;
 #pragma unroll
         for (int e = 0; e < NL; ++e) R[e] = keep * uo[e] + om * R[e];
 #pragma unroll
