@@ -526,13 +526,17 @@ __device__ __forceinline__ void smooth_cells_body(const DGConst<T> &c, int64_t c
         }
         __syncwarp();
         // 2 faces x [W][2 NF] -> [cell][face 2p + side], in 8-byte (FP32) or 16-byte (FP64) pieces
+        // (constant divisors only: the index split is a multiply and a shift)
         using V = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
         constexpr int NV = NF;                          // 2 NF values = NF pieces of two
-        for (int idx = lane; idx < ncl * 2 * NV; idx += W) {
-            const int side = idx / (ncl * NV), r = idx - side * (ncl * NV);
-            const int j = r / NV, part = r - j * NV;
-            const V v = reinterpret_cast<const V *>(sB + side * W * 2 * NF + j * 2 * NF)[part];
-            reinterpret_cast<V *>(tr_out + (cell0 + j) * TR + (2 * p + side) * 2 * NF)[part] = v;
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const V *src = reinterpret_cast<const V *>(sB + side * W * 2 * NF);
+            V *dst = reinterpret_cast<V *>(tr_out + cell0 * TR + (2 * p + side) * 2 * NF);
+            for (int idx = lane; idx < ncl * NV; idx += W) {
+                const int j = idx / NV, part = idx - j * NV;
+                dst[j * (TR / 2) + part] = src[idx];
+            }
         }
         __syncwarp();
         if (p < 2) rotate<T, Q>(R);
