@@ -198,7 +198,7 @@ class Hierarchy:
         self.dg_meshes, self.dg_smoothers, self.Pdg = [mesh], [self.smoother], []
         if gradual:
             for pc in range(mesh.p - 1, 0, -1):
-                mc = sipg.Mesh(mesh.n, pc, penalty_p=mesh.penalty_p)
+                mc = sipg.Mesh(mesh.n, pc, penalty_p=mesh.penalty_p, basis=mesh.basis)
                 self.Pdg.append(dg_p_prolongation(self.dg_meshes[-1], mc))
                 self.dg_meshes.append(mc)
                 self.dg_smoothers.append(sipg.BlockJacobi(mc, self.kappa, interior_only=interior_only))

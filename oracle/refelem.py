@@ -77,29 +77,41 @@ def lagrange_derivs(nodes, x):
     return D
 
 
-def mass_1d(p):
+def basis_nodes(p, basis="gll"):
+    """Nodes of the degree-p Lagrange basis: Gauss-Lobatto-Legendre ("gll", the
+    paper's default) or Gauss-Legendre ("gl", Sec. 6.5: no nodes on the cell
+    boundary, diagonal mass matrix)."""
+    if basis == "gll":
+        return gll_nodes(p)
+    if basis == "gl":
+        return gauss_legendre(p + 1)[0]
+    raise ValueError(basis)
+
+
+def mass_1d(p, basis="gll"):
     """Exact 1D mass matrix M[i,j] = int_{-1}^{1} l_i l_j (Gauss-Legendre, p+1 points)."""
     xg, wg = gauss_legendre(p + 1)
-    V = lagrange_values(gll_nodes(p), xg)
+    V = lagrange_values(basis_nodes(p, basis), xg)
     return (V * wg) @ V.T
 
 
-def stiffness_1d(p):
+def stiffness_1d(p, basis="gll"):
     """Exact 1D stiffness matrix K[i,j] = int_{-1}^{1} l_i' l_j'."""
     xg, wg = gauss_legendre(p + 1)
-    D = lagrange_derivs(gll_nodes(p), xg)
+    D = lagrange_derivs(basis_nodes(p, basis), xg)
     return (D * wg) @ D.T
 
 
-def endpoint_values(p):
-    """(e0, ep): values of each basis function at xi = -1 and xi = +1."""
-    x = gll_nodes(p)
+def endpoint_values(p, basis="gll"):
+    """(e0, ep): values of each basis function at xi = -1 and xi = +1 (unit
+    vectors for GLL, dense for GL)."""
+    x = basis_nodes(p, basis)
     V = lagrange_values(x, np.array([-1.0, 1.0]))
     return V[:, 0].copy(), V[:, 1].copy()
 
 
-def endpoint_derivs(p):
+def endpoint_derivs(p, basis="gll"):
     """(d0, dp): derivatives d/dxi of each basis function at xi = -1 and xi = +1."""
-    x = gll_nodes(p)
+    x = basis_nodes(p, basis)
     D = lagrange_derivs(x, np.array([-1.0, 1.0]))
     return D[:, 0].copy(), D[:, 1].copy()

@@ -33,10 +33,11 @@ THETA = -1.0  # symmetric interior penalty in the paper's sign convention
 class Mesh:
     """Uniform tensor-product mesh of the unit box with n[dir] cells along axis dir."""
 
-    def __init__(self, n, p, penalty_p=None):
+    def __init__(self, n, p, penalty_p=None, basis="gll"):
         """penalty_p: degree whose penalty 2 p (p+1) / h the facets use (default p).
         A lower level of a gradual p-hierarchy keeps the finest level's penalty:
-        its operator is then the Galerkin restriction of the finest operator."""
+        its operator is then the Galerkin restriction of the finest operator.
+        basis: nodes of the Lagrange basis, "gll" (default) or "gl" (Sec. 6.5)."""
         self.n = tuple(int(v) for v in n)
         self.d = len(self.n)
         if self.d not in (2, 3):
@@ -48,13 +49,14 @@ class Mesh:
         self.ncell = int(np.prod(self.n))
         self.nloc = self.q ** self.d
         self.ndof = self.ncell * self.nloc
-        self.nodes = refelem.gll_nodes(self.p)
-        Mr = refelem.mass_1d(self.p)
-        Kr = refelem.stiffness_1d(self.p)
+        self.basis = basis
+        self.nodes = refelem.basis_nodes(self.p, basis)
+        Mr = refelem.mass_1d(self.p, basis)
+        Kr = refelem.stiffness_1d(self.p, basis)
         self.M = [Mr * (h / 2.0) for h in self.h]          # 1D mass on a cell of width h
         self.K = [Kr * (2.0 / h) for h in self.h]          # 1D stiffness
-        self.e0, self.ep = refelem.endpoint_values(self.p)
-        d0, dp = refelem.endpoint_derivs(self.p)
+        self.e0, self.ep = refelem.endpoint_values(self.p, basis)
+        d0, dp = refelem.endpoint_derivs(self.p, basis)
         self.d0 = [d0 * (2.0 / h) for h in self.h]         # physical d/dx at the low end
         self.dp = [dp * (2.0 / h) for h in self.h]         # physical d/dx at the high end
 
