@@ -441,7 +441,7 @@ class BlockJacobi:
         self.mesh = mesh
         self.kappa = None if kappa is None else np.asarray(kappa, dtype=np.float64).reshape(-1)
         if interior_only:
-            big = Mesh(tuple(3 for _ in range(mesh.d)), mesh.p)
+            big = Mesh(tuple(3 for _ in range(mesh.d)), mesh.p, penalty_p=mesh.penalty_p, basis=mesh.basis)
             big.h = mesh.h
             big.M, big.K, big.d0, big.dp = mesh.M, mesh.K, mesh.d0, mesh.dp
             Bi = block_diagonal(big)[(3 ** mesh.d) // 2]

@@ -59,3 +59,39 @@ def test_gl_mgmult_iterates_are_the_gll_iterates():
     x_gll, _ = hpmg.mgmult(hpmg.Hierarchy(mg, kap, gradual=True), b_gll, eps=0.0, maxit=K)
     x_gl, _ = hpmg.mgmult(hpmg.Hierarchy(ml, kap, gradual=True), b_gl, eps=0.0, maxit=K)
     assert np.abs(x_gl - E @ x_gll).max() <= 1e-11 * np.abs(x_gl).max()
+
+
+def test_two_peak_rhs_is_minus_laplacian():
+    """The closed-form f of the "two-peak" solution equals -Lap u by fourth-order
+    central differences, and u vanishes on the boundary of the unit square."""
+    from paper_2510_00998_gb300 import workloads as w
+    rng = np.random.default_rng(5)
+    x, y = rng.uniform(0.05, 0.95, 200), rng.uniform(0.05, 0.95, 200)
+    h = 1e-3
+    u = lambda a, b: w.two_peak_u(a, b)
+
+    def d2(fm2, fm1, f0, fp1, fp2):
+        return (-fm2 + 16 * fm1 - 30 * f0 + 16 * fp1 - fp2) / (12 * h * h)
+
+    lap = d2(u(x - 2 * h, y), u(x - h, y), u(x, y), u(x + h, y), u(x + 2 * h, y)) + \
+        d2(u(x, y - 2 * h), u(x, y - h), u(x, y), u(x, y + h), u(x, y + 2 * h))
+    f = w.two_peak_f(x, y)
+    assert np.abs(f + lap).max() <= 1e-6 * np.abs(f).max()
+    t = np.linspace(0, 1, 11)
+    for a, b in ((t, 0 * t), (t, 0 * t + 1), (0 * t, t), (0 * t + 1, t)):
+        assert np.abs(w.two_peak_u(a, b)).max() == 0.0
+
+
+@pytest.mark.parametrize("n,p", [((5, 4), 2), ((3, 4, 3), 2)])
+def test_gl_interior_only_block_is_the_gll_one_in_another_basis(n, p):
+    """Technique 4's block (an interior cell's block, own kappa) transforms like
+    the exact blocks: B_GL = E^-T B_GLL E^-1 per cell."""
+    kap = np.exp(np.random.default_rng(6).normal(size=int(np.prod(n))))
+    mg, ml = sipg.Mesh(n, p), sipg.Mesh(n, p, basis="gl")
+    E = _change_of_basis(mg).toarray()[:mg.nloc, :mg.nloc]
+    Ei = np.linalg.inv(E)
+    for interior_only in (False, True):
+        Bg = sipg.BlockJacobi(mg, kap, interior_only=interior_only).B
+        Bl = sipg.BlockJacobi(ml, kap, interior_only=interior_only).B
+        for c in range(mg.ncell):
+            assert np.abs(Bl[c] - Ei.T @ Bg[c] @ Ei).max() <= 1e-10 * np.abs(Bl[c]).max()
