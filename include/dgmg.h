@@ -72,6 +72,16 @@ extern "C" {
                                   /* rtol ||x_1 - x_0||                                */
 
 /* block inverse used by the block-Jacobi smoother (Eq. block-Jacobi-IP) */
+#define DGMG_BASIS_GLL 0          /* Gauss-Lobatto-Legendre nodes (Sec. 2.2): the end  */
+                                  /* nodes carry the traces, non-diagonal mass matrix  */
+#define DGMG_BASIS_GL 1           /* Gauss-Legendre nodes (Sec. 6.5): diagonal mass    */
+                                  /* matrix, every node contributes to a trace (dense  */
+                                  /* cell-to-facet projection, Sec. 4.1). The same     */
+                                  /* discrete problem in another basis; solves run the */
+                                  /* sum-factorised per-pencil smoother (the           */
+                                  /* one-thread-per-cell smoother is GLL-only), and    */
+                                  /* batched solves take GLL only                      */
+
 #define DGMG_BLOCK_EXACT 0        /* exact diagonal block A_KK of every cell           */
 #define DGMG_BLOCK_INTERIOR_ONLY 1/* Technique 4: the block of an interior cell, with  */
                                   /* the cell's own kappa, for every cell              */
@@ -103,6 +113,8 @@ typedef struct {
                                   /* 6.4), every DG level the Galerkin product of the  */
                                   /* one above (finest penalty) with its own           */
                                   /* block-Jacobi smoother and nu_pre/nu_post steps    */
+    int basis;                    /* nodes of the 1D Lagrange basis of the DG space:   */
+                                  /* DGMG_BASIS_GLL (default) or DGMG_BASIS_GL         */
 } dgmg_opts;
 
 typedef struct {
@@ -183,8 +195,8 @@ int dgmg_destroy(dgmg_ctx *ctx);
 /* Describe ctx (host struct, filled synchronously). */
 int dgmg_info(const dgmg_ctx *ctx, dgmg_info_t *info);
 
-/* Number of nodes per cell q^d and the GLL node coordinates on [-1,1]
- * (HOST array of q doubles) of ctx's basis. */
+/* The 1D node coordinates on [-1,1] of ctx's basis (GLL, or GL with
+ * opts.basis = DGMG_BASIS_GL): HOST array of q doubles, ascending. */
 int dgmg_gll_nodes(const dgmg_ctx *ctx, double *nodes_host);
 
 /*

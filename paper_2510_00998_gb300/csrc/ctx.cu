@@ -297,7 +297,10 @@ void fill_const(const dgmg_ctx &C, const DGSpace &S, DGConst<T> &c) {
     for (int i = 0; i < q; ++i) {
         c.hat[0][i] = (T)((1.0 - S.re.nodes[i]) / 2.0);
         c.hat[1][i] = (T)((1.0 + S.re.nodes[i]) / 2.0);
+        c.v0[i] = (T)S.re.e0[i];
+        c.vp[i] = (T)S.re.ep[i];
     }
+    c.gl = S.re.basis == DGMG_BASIS_GL ? 1 : 0;
     c.omega = (T)C.opts.omega_dg;
 }
 
@@ -333,7 +336,7 @@ void fast_diag_factors(const dgmg_ctx &C, const DGSpace &S, const std::vector<do
         double Kt[QMAX * QMAX];
         for (int i = 0; i < q; ++i)
             for (int j = 0; j < q; ++j) {
-                const double e0i = i == 0, e0j = j == 0, epi = i == q - 1, epj = j == q - 1;
+                const double e0i = S.re.e0[i], e0j = S.re.e0[j], epi = S.re.ep[i], epj = S.re.ep[j];
                 double v = kK * Kh[a][i * q + j];
                 v += kL * (wL * (e0i * d0[a][j] + d0[a][i] * e0j) + gam[a] * e0i * e0j);
                 v += kR * (-wR * (epi * dp[a][j] + dp[a][i] * epj) + gam[a] * epi * epj);
@@ -464,7 +467,7 @@ int setup_dg_levels(dgmg_ctx &C, const std::vector<double> &kap) {
         S.penalty_p = C.p;
         S.nloc = C.dim == 3 ? (int64_t)S.q * S.q * S.q : (int64_t)S.q * S.q;
         S.ndof = C.ncell * S.nloc;
-        S.re = make_refelem(pc);
+        S.re = make_refelem(pc, C.opts.basis);
         C.dgs.push_back(S);
     }
     const int L = (int)C.dgs.size();
@@ -807,8 +810,8 @@ int apply64(dgmg_ctx &C, const double *u, const double *b, double *out, cudaStre
 // are cached per (dimension, degree, mesh, precision, block inverse) for the
 // process, so a repeated shape is tuned once.
 struct TileKey {
-    int v[7];
-    bool operator<(const TileKey &o) const { return std::lexicographical_compare(v, v + 7, o.v, o.v + 7); }
+    int v[8];
+    bool operator<(const TileKey &o) const { return std::lexicographical_compare(v, v + 8, o.v, o.v + 8); }
 };
 static std::mutex g_tile_mu;
 static std::map<TileKey, std::array<int, 6>> g_tile_cache;
@@ -884,7 +887,7 @@ static int tune_tiles(dgmg_ctx &C, T *u, T *b, int *tile, bool trace) {
 
 static int autotune_tiles(dgmg_ctx &C) {
     const bool mixed = C.opts.precision == DGMG_MIXED_FP32;
-    const TileKey key{{C.dim, C.q, C.n[0], C.n[1], C.n[2], C.opts.precision, C.opts.block_inverse}};
+    const TileKey key{{C.dim, C.q, C.n[0], C.n[1], C.n[2], C.opts.precision, C.opts.block_inverse, C.opts.basis}};
     {
         std::lock_guard<std::mutex> lk(g_tile_mu);
         auto it = g_tile_cache.find(key);
@@ -935,6 +938,7 @@ void dgmg_default_opts(dgmg_opts *o) {
     o->delta = 0.1;
     o->autotune = 0;
     o->p_coarsening = 0;
+    o->basis = DGMG_BASIS_GLL;
 }
 
 int dgmg_create(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_opts *opts, dgmg_ctx **out) {
@@ -975,6 +979,8 @@ int create_ctx(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_opt
         return fail(DGMG_EINVAL, "DGMG_OUTER_RELIABLE needs DGMG_MIXED_FP32");
     if (!(o.delta > 0 && o.delta < 1)) return fail(DGMG_EINVAL, "delta must be in (0, 1)");
     if (o.p_coarsening != 0 && o.p_coarsening != 1) return fail(DGMG_EINVAL, "p_coarsening must be 0 or 1");
+    if (o.basis != DGMG_BASIS_GLL && o.basis != DGMG_BASIS_GL)
+        return fail(DGMG_EINVAL, "basis must be DGMG_BASIS_GLL or DGMG_BASIS_GL");
     if (o.outer == DGMG_OUTER_AUTO) o.outer = o.precision == DGMG_MIXED_FP32 ? DGMG_OUTER_RELIABLE : DGMG_OUTER_PCG;
 
     std::unique_ptr<dgmg_ctx> C(new dgmg_ctx());
@@ -1009,7 +1015,7 @@ int create_ctx(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_opt
         }
     }
     SetupTrace trace;
-    C->re = make_refelem(p);
+    C->re = make_refelem(p, o.basis);
     trace.mark("refelem");
 
     // Q1 hierarchy

@@ -203,7 +203,8 @@ __device__ __forceinline__ void facet_mass(const T *sM, bool active, int t, T *s
 // r -= N u_nb: the neighbours' part of the facet terms of the cell equation
 // (all terms of Eq. weak_form_IP_facet_spaces that involve the neighbour's
 // projections), lifted into the cell. sF holds the mass-applied neighbour
-// fields G = M_t g, H = M_t h. For the low face (cell = K^+):
+// fields G = M_t g, H = M_t h; e_0, e_p are the end values of the 1D basis
+// (the first / last unit vector for GLL nodes). For the low face (cell = K^+):
 //   N = kF [ e_0 (x) (H/2 - gamma G) - d_0 (x) G/2 ],
 // for the high face (cell = K^-):
 //   N = kF [ e_p (x) (-H/2 - gamma G) + d_p (x) G/2 ].
@@ -222,7 +223,13 @@ __device__ __forceinline__ void lift_neighbours(const DGConst<T> &c, bool active
             if (mask & (1 << (2 * dir))) {
                 const T Gv = sF[((2 * dir) * 2 + 0) * G::NF + t];
                 const T Hv = sF[((2 * dir) * 2 + 1) * G::NF + t];
-                x[0] -= kL * (half * Hv - c.gamma[dir] * Gv);
+                const T s0 = kL * (half * Hv - c.gamma[dir] * Gv);
+                if (c.gl) {
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) x[i] -= s0 * c.v0[i];
+                } else {
+                    x[0] -= s0;
+                }
                 const T a = kL * half * Gv;
 #pragma unroll
                 for (int i = 0; i < Q; ++i) x[i] += a * c.d0[dir][i];
@@ -230,7 +237,13 @@ __device__ __forceinline__ void lift_neighbours(const DGConst<T> &c, bool active
             if (mask & (1 << (2 * dir + 1))) {
                 const T Gv = sF[((2 * dir + 1) * 2 + 0) * G::NF + t];
                 const T Hv = sF[((2 * dir + 1) * 2 + 1) * G::NF + t];
-                x[Q - 1] -= kR * (-half * Hv - c.gamma[dir] * Gv);
+                const T sp = kR * (-half * Hv - c.gamma[dir] * Gv);
+                if (c.gl) {
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) x[i] -= sp * c.vp[i];
+                } else {
+                    x[Q - 1] -= sp;
+                }
                 const T a = kR * half * Gv;
 #pragma unroll
                 for (int i = 0; i < Q; ++i) x[i] -= a * c.dp[dir][i];
@@ -246,6 +259,8 @@ __device__ __forceinline__ void lift_neighbours(const DGConst<T> &c, bool active
 // low face  kF_L ( w_L (e0 d0^T + d0 e0^T) + gamma e0 e0^T ),
 // high face kF_R (-w_R (ep dp^T + dp ep^T) + gamma ep ep^T ),
 // kF = harmonic mean and w = 1/2 inside, kF = kappa_K and w = 1 on the boundary.
+// With GLL nodes e0 / ep are the first / last unit vector, so the face terms
+// live in row and column 0 and q-1 only.
 template <int DIM, int Q, typename T>
 __device__ __forceinline__ void build_block_1d(const DGConst<T> &c, const T *sT, bool active, int t, const T *myK,
                                                int mask, T *myKT) {
@@ -253,6 +268,20 @@ __device__ __forceinline__ void build_block_1d(const DGConst<T> &c, const T *sT,
     if (!active) return;
     const T *K = sT, *d0 = sT + DIM * Q * Q, *dp = d0 + DIM * Q;
     const T kK = myK[G::NFACE];
+    if (c.gl) {                               // dense end values: every entry has face terms
+        for (int e = t; e < DIM * Q * Q; e += G::NF) {
+            const int a = e / (Q * Q), i = (e / Q) % Q, j = e % Q;
+            const bool inL = mask & (1 << (2 * a)), inR = mask & (1 << (2 * a + 1));
+            const T kL = inL ? myK[2 * a] : kK, wL = inL ? T(0.5) : T(1);
+            const T kR = inR ? myK[2 * a + 1] : kK, wR = inR ? T(0.5) : T(1);
+            const T e0i = c.v0[i], e0j = c.v0[j], epi = c.vp[i], epj = c.vp[j];
+            T v = kK * K[e];
+            v += kL * (wL * (e0i * d0[a * Q + j] + d0[a * Q + i] * e0j) + c.gamma[a] * e0i * e0j);
+            v += kR * (-wR * (epi * dp[a * Q + j] + dp[a * Q + i] * epj) + c.gamma[a] * epi * epj);
+            myKT[e] = v;
+        }
+        return;
+    }
     for (int e = t; e < DIM * Q * Q; e += G::NF) {
         const int a = e / (Q * Q), i = (e / Q) % Q, j = e % Q;
         T v = kK * K[e];
@@ -343,7 +372,8 @@ __device__ __forceinline__ void subtract_block_apply(const DGConst<T> &c, bool a
     __syncthreads();
 }
 
-// Value and +axis derivative of a pencil at both ends, written to the trace array.
+// Value and +axis derivative of a pencil at both ends (Sec. 4.1 projection onto
+// the facet spaces), written to the trace array.
 template <int DIM, int Q, typename T>
 __device__ __forceinline__ void write_pencil_traces(const DGConst<T> &c, int dir, int t, const T *x,
                                                     T *__restrict__ trc) {
@@ -354,11 +384,21 @@ __device__ __forceinline__ void write_pencil_traces(const DGConst<T> &c, int dir
         dlo += c.d0[dir][i] * x[i];
         dhi += c.dp[dir][i] * x[i];
     }
+    T vlo = x[0], vhi = x[Q - 1];
+    if (c.gl) {                               // GL nodes: the end values are dense dot products
+        vlo = T(0);
+        vhi = T(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            vlo += c.v0[i] * x[i];
+            vhi += c.vp[i] * x[i];
+        }
+    }
     T *lo = trc + (2 * dir) * 2 * G::NF;
     T *hi = trc + (2 * dir + 1) * 2 * G::NF;
-    lo[t] = x[0];
+    lo[t] = vlo;
     lo[G::NF + t] = dlo;
-    hi[t] = x[Q - 1];
+    hi[t] = vhi;
     hi[G::NF + t] = dhi;
 }
 
@@ -848,7 +888,7 @@ struct DGLaunch {
             const bool aligned = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(b) |
                                    reinterpret_cast<uintptr_t>(fd) | reinterpret_cast<uintptr_t>(linv)) & 15) == 0 &&
                                  ((reinterpret_cast<uintptr_t>(tri) | reinterpret_cast<uintptr_t>(tro)) & tra) == 0;
-            if (cpb <= 0 && exact && aligned) return smooth_cells(c, u, b, kappa, fd, linv, tri, tro, s);
+            if (cpb <= 0 && exact && aligned && !c.gl) return smooth_cells(c, u, b, kappa, fd, linv, tri, tro, s);
         }
         if (cpb <= 0) cpb = default_cpb();
         const size_t sm = smem_smooth<DIM, Q, T>(cpb, exact != 0);

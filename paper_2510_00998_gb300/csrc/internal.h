@@ -34,15 +34,17 @@ cudaError_t wait_timeouts_fp32(unsigned long long *count);
 cudaError_t wait_timeouts_fp64(unsigned long long *count);
 
 // ------------------------------------------------------- reference element
-// 1D GLL Lagrange element of degree p on [-1,1] (paper Sec. 2.2), computed
-// on the host in double precision.
+// 1D Lagrange element of degree p on [-1,1] with GLL (Sec. 2.2) or GL
+// (Sec. 6.5) nodes, computed on the host in double precision.
 struct RefElem1D {
     int p = 0, q = 0;
-    std::vector<double> nodes;            // q GLL nodes
+    int basis = DGMG_BASIS_GLL;
+    std::vector<double> nodes;            // q nodes, ascending
     std::vector<double> M, K;             // q x q exact mass / stiffness on [-1,1], row-major
+    std::vector<double> e0, ep;           // l_j(-1), l_j(+1): unit vectors for GLL, dense for GL
     std::vector<double> d0, dp;           // l_j'(-1), l_j'(+1)
 };
-RefElem1D make_refelem(int p);
+RefElem1D make_refelem(int p, int basis = DGMG_BASIS_GLL);
 void gauss_legendre(int m, std::vector<double> &x, std::vector<double> &w);
 // values and derivatives of the Lagrange basis on `nodes` at x
 void lagrange_at(const std::vector<double> &nodes, double x, double *val, double *der);
@@ -66,6 +68,11 @@ struct DGConst {
     T gamma[3];
     T hat[2][QMAX];
     T omega;
+    // GL basis (gl != 0): the end values l_j(-1), l_j(+1) of the 1D basis,
+    // which then are dense; with GLL (gl == 0) they are the unit vectors of
+    // the end nodes and the kernels index those nodes directly
+    int gl;
+    T v0[QMAX], vp[QMAX];
 };
 
 // Q1 level description for the CG kernels.

@@ -4,7 +4,8 @@
 // GLL nodes: the end points and the roots of P_p' (Sec. 2.2 basis), found by
 // Newton's method from the Chebyshev-Gauss-Lobatto points. Gauss-Legendre
 // rules: Newton's method on P_m from the usual cosine initial guesses, weights
-// 2 / ((1 - x^2) P_m'(x)^2). Legendre values through the three-term recurrence.
+// 2 / ((1 - x^2) P_m'(x)^2); the q GL points are also the nodes of the GL
+// basis (Sec. 6.5). Legendre values through the three-term recurrence.
 // Exact 1D mass and stiffness matrices use q-point Gauss-Legendre quadrature
 // (degree 2p integrands), matching the paper's remark that the GLL mass matrix
 // is not diagonal (exact integration, Sec. 4.1).
@@ -94,14 +95,15 @@ void lagrange_at(const std::vector<double> &nodes, double x, double *val, double
     }
 }
 
-RefElem1D make_refelem(int p) {
+RefElem1D make_refelem(int p, int basis) {
     RefElem1D r;
     r.p = p;
     r.q = p + 1;
+    r.basis = basis;
     const int q = r.q;
-    r.nodes = gll_points(p);
     std::vector<double> xg, wg;
     gauss_legendre(q, xg, wg);
+    r.nodes = basis == DGMG_BASIS_GL ? xg : gll_points(p);
     r.M.assign(q * q, 0.0);
     r.K.assign(q * q, 0.0);
     std::vector<double> v(q), d(q);
@@ -113,10 +115,14 @@ RefElem1D make_refelem(int p) {
                 r.K[i * q + j] += wg[g] * d[i] * d[j];
             }
     }
+    r.e0.assign(q, 0.0);
+    r.ep.assign(q, 0.0);
     r.d0.assign(q, 0.0);
     r.dp.assign(q, 0.0);
-    lagrange_at(r.nodes, -1.0, nullptr, r.d0.data());
-    lagrange_at(r.nodes, 1.0, nullptr, r.dp.data());
+    // with GLL nodes the end values are exactly the unit vectors (the factor
+    // (x - x_end) of every other basis function vanishes in floating point)
+    lagrange_at(r.nodes, -1.0, r.e0.data(), r.d0.data());
+    lagrange_at(r.nodes, 1.0, r.ep.data(), r.dp.data());
     return r;
 }
 

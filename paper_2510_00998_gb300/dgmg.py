@@ -24,6 +24,8 @@ DGMG_OUTER_PCG = 1
 DGMG_OUTER_RELIABLE = 2
 DGMG_OUTER_MGMULT = 3
 DGMG_OUTER_MGMULT_PREC = 4
+DGMG_BASIS_GLL = 0
+DGMG_BASIS_GL = 1
 DGMG_PENDING = 0
 DGMG_RUNNING = 1
 DGMG_DONE = 2
@@ -47,7 +49,8 @@ class Opts(ctypes.Structure):
                 ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int), ("precision", ctypes.c_int),
                 ("block_inverse", ctypes.c_int), ("coarsening", ctypes.c_int),
                 ("rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("outer", ctypes.c_int),
-                ("delta", ctypes.c_double), ("autotune", ctypes.c_int), ("p_coarsening", ctypes.c_int)]
+                ("delta", ctypes.c_double), ("autotune", ctypes.c_int), ("p_coarsening", ctypes.c_int),
+                ("basis", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):

@@ -16,6 +16,9 @@ Workloads (every input seeded and synthetic):
   serve          Poisson arrivals (default_rng(5)) of requests with n in [8,48],
                  p in 2..5, kappa in {1, lognormal, two-phase 1/100}, at
                  multiples of the FP64 one-at-a-time capacity; p50/p99 latency
+  tables34       MGMult cycle counts of Tables 3-4 ("sin-product", GLL), 2D
+                 9^2 .. 243^2, p = 2..6, direct and gradual p-coarsening
+  table5         the same for the "two-peak" solution in the GLL and the GL basis
 """
 import argparse
 import json
@@ -74,21 +77,71 @@ def sin_product_rhs_2d(ctx, device):
     return b
 
 
-def tables34(meshes=(9, 27, 81, 243), degrees=(2, 3, 4, 5, 6), nu=3, device="cuda", p_coarsening=0):
+# "two-peak" solution of Sec. 6 (Eq. two_peak_exact): u = g h with the bubble
+# g = x(1-x)y(1-y) and h = 2 G_1 - G_2, G_k a Gaussian of width sigma_k centred
+# at (x_0k, y_0k)
+TWO_PEAK = ((0.3, 0.4, 0.2, 2.0), (0.8, 0.6, 0.1, -1.0))   # (x0, y0, sigma, weight)
+
+
+def two_peak_u(x, y, xp=np):
+    """The "two-peak" reference solution at points (x, y); xp = numpy or torch."""
+    h = 0.0
+    for x0, y0, sg, w in TWO_PEAK:
+        h = h + w * xp.exp(-((x - x0) ** 2 + (y - y0) ** 2) / (2 * sg * sg))
+    return x * (1 - x) * y * (1 - y) * h
+
+
+def two_peak_f(x, y, xp=np):
+    """f = -Lap u for the "two-peak" solution, written out by the product rule:
+    Lap(g h) = h Lap g + 2 grad g . grad h + g Lap h with, per Gaussian G of
+    width s, grad G = -(x - x0, y - y0) G / s^2 and Lap G = (r^2 / s^4 - 2 / s^2) G."""
+    g = x * (1 - x) * y * (1 - y)
+    gx, gy = (1 - 2 * x) * y * (1 - y), x * (1 - x) * (1 - 2 * y)
+    lap_g = -2 * (y * (1 - y) + x * (1 - x))
+    h = hx = hy = lap_h = 0.0
+    for x0, y0, sg, w in TWO_PEAK:
+        s2 = sg * sg
+        dx, dy = x - x0, y - y0
+        r2 = dx * dx + dy * dy
+        G = w * xp.exp(-r2 / (2 * s2))
+        h = h + G
+        hx = hx - dx / s2 * G
+        hy = hy - dy / s2 * G
+        lap_h = lap_h + (r2 / (s2 * s2) - 2 / s2) * G
+    return -(h * lap_g + 2 * (gx * hx + gy * hy) + g * lap_h)
+
+
+def two_peak_rhs_2d(ctx, device):
+    """b = (f, phi_i) for the "two-peak" solution, through the library's quadrature."""
+    import torch
+    mq = ctx.p + 2
+    xq = torch.empty(int(ctx.info.ncell) * mq ** 2 * 2, dtype=torch.float64, device=device)
+    ctx.quad_points(xq)
+    X = xq.view(-1, 2)
+    f = two_peak_f(X[:, 0], X[:, 1], torch)
+    b = torch.empty(ctx.ndof, dtype=torch.float64, device=device)
+    ctx.load_vector(f.contiguous(), b)
+    return b
+
+
+def tables34(meshes=(9, 27, 81, 243), degrees=(2, 3, 4, 5, 6), nu=3, device="cuda", p_coarsening=0,
+             rhs="sin_product", basis=0):
     """MGMult cycles (Alg. 7) to reduce the unpreconditioned and the
-    preconditioned residual by 1e-7 on n x n meshes, factor-3 h-coarsening, the
-    "sin-product" right-hand side: the setting of the paper's Tables 3-4.
+    preconditioned residual by 1e-7 on n x n meshes, factor-3 h-coarsening: the
+    setting of the paper's Tables 3-4 ("sin-product" or "two-peak" right-hand
+    side, GLL basis) and Table 5 ("two-peak", GL basis: basis=1).
     Returns {(n, p): (cycles unpreconditioned, cycles preconditioned)}."""
     import torch
     from . import dgmg
+    make_rhs = {"sin_product": sin_product_rhs_2d, "two_peak": two_peak_rhs_2d}[rhs]
     out = {}
     for n in meshes:
         for p in degrees:
             ks = []
             for outer in (dgmg.DGMG_OUTER_MGMULT, dgmg.DGMG_OUTER_MGMULT_PREC):
                 ctx = dgmg.Context((n, n), p, outer=outer, coarsening=3, nu_pre=nu, nu_post=nu, rtol=1e-7,
-                                   maxit=1000, p_coarsening=p_coarsening)
-                b = sin_product_rhs_2d(ctx, device)
+                                   maxit=1000, p_coarsening=p_coarsening, basis=basis)
+                b = make_rhs(ctx, device)
                 x = torch.zeros_like(b)
                 st, _ = ctx.solve(b, x)
                 ks.append(int(st.iterations))
@@ -135,7 +188,7 @@ def run(name, solves=3, warmup=1):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("name", choices=sorted(WORKLOADS) + ["batch", "serve", "tables34"])
+    ap.add_argument("name", choices=sorted(WORKLOADS) + ["batch", "serve", "tables34", "table5"])
     ap.add_argument("--solves", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--count", type=int, default=0)
@@ -161,6 +214,12 @@ def main():
             res = tables34(p_coarsening=pc)
             out["gradual" if pc else "direct"] = {f"{n}x{n} p={p}": {"unprec": v[0], "prec": v[1]}
                                                   for (n, p), v in res.items()}
+        print(json.dumps(out))
+    elif a.name == "table5":
+        out = {}
+        for basis, key in ((0, "two_peak_gll"), (1, "two_peak_gl")):
+            res = tables34(rhs="two_peak", basis=basis)
+            out[key] = {f"{n}x{n} p={p}": {"unprec": v[0], "prec": v[1]} for (n, p), v in res.items()}
         print(json.dumps(out))
     else:
         print(json.dumps(run(a.name, a.solves, a.warmup)))
