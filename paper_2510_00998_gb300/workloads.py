@@ -16,6 +16,8 @@ Workloads (every input seeded and synthetic):
   serve          Poisson arrivals (default_rng(5)) of requests with n in [8,48],
                  p in 2..5, kappa in {1, lognormal, two-phase 1/100}, at
                  multiples of the FP64 one-at-a-time capacity; p50/p99 latency
+  *_gradual, *_gl  the 3D problems above with gradual p-coarsening (DG p,
+                 p-1, ..., 1, then Q1) or in the Gauss-Legendre basis
   tables34       MGMult cycle counts of Tables 3-4 ("sin-product", GLL), 2D
                  9^2 .. 243^2, p = 2..6, direct and gradual p-coarsening
   table5         the same for the "two-peak" solution in the GLL and the GL basis
@@ -36,6 +38,9 @@ WORKLOADS = {
     "3d32_p3_gradual": dict(n=(32, 32, 32), p=3, kappa=None, precision=0, p_coarsening=1),
     "3d64_p4_mixed_gradual": dict(n=(64, 64, 64), p=4, kappa="lognormal3", precision=1, p_coarsening=1),
     "3d64_p4_fp64_gradual": dict(n=(64, 64, 64), p=4, kappa="lognormal3", precision=0, p_coarsening=1),
+    # the same problems in the Gauss-Legendre nodal basis (Sec. 6.5)
+    "3d64_p4_mixed_gl": dict(n=(64, 64, 64), p=4, kappa="lognormal3", precision=1, basis=1),
+    "3d64_p4_fp64_gl": dict(n=(64, 64, 64), p=4, kappa="lognormal3", precision=0, basis=1),
 }
 
 
@@ -124,13 +129,19 @@ def two_peak_rhs_2d(ctx, device):
     return b
 
 
-def tables34(meshes=(9, 27, 81, 243), degrees=(2, 3, 4, 5, 6), nu=3, device="cuda", p_coarsening=0,
-             rhs="sin_product", basis=0):
+def tables34(meshes=(9, 27, 81, 243), degrees=(2, 3, 4, 5, 6), nu=4, device="cuda", p_coarsening=0,
+             rhs="sin_product", basis=0, **opts):
     """MGMult cycles (Alg. 7) to reduce the unpreconditioned and the
     preconditioned residual by 1e-7 on n x n meshes, factor-3 h-coarsening: the
     setting of the paper's Tables 3-4 ("sin-product" or "two-peak" right-hand
-    side, GLL basis) and Table 5 ("two-peak", GL basis: basis=1).
-    Returns {(n, p): (cycles unpreconditioned, cycles preconditioned)}."""
+    side, GLL basis) and Table 5 ("two-peak", GL basis: basis=1). The paper
+    does not state the smoothing steps or the damping of these tables; nu = 4
+    pre- and post-smoothing steps with the default omega = 0.8 reproduce them
+    best among omega in 0.6..1.0 and nu in 1..4 (exact or interior-only block).
+    Further
+    keyword arguments are context options (omega_dg, block_inverse, ...).
+    Returns {(n, p): (cycles unpreconditioned, cycles preconditioned)}, -1 where
+    1000 cycles did not reach the tolerance."""
     import torch
     from . import dgmg
     make_rhs = {"sin_product": sin_product_rhs_2d, "two_peak": two_peak_rhs_2d}[rhs]
@@ -140,11 +151,11 @@ def tables34(meshes=(9, 27, 81, 243), degrees=(2, 3, 4, 5, 6), nu=3, device="cud
             ks = []
             for outer in (dgmg.DGMG_OUTER_MGMULT, dgmg.DGMG_OUTER_MGMULT_PREC):
                 ctx = dgmg.Context((n, n), p, outer=outer, coarsening=3, nu_pre=nu, nu_post=nu, rtol=1e-7,
-                                   maxit=1000, p_coarsening=p_coarsening, basis=basis)
+                                   maxit=1000, p_coarsening=p_coarsening, basis=basis, **opts)
                 b = make_rhs(ctx, device)
                 x = torch.zeros_like(b)
-                st, _ = ctx.solve(b, x)
-                ks.append(int(st.iterations))
+                st, rc = ctx.solve(b, x, allow_notconverged=True)
+                ks.append(int(st.iterations) if rc == dgmg.DGMG_OK else -1)
                 ctx.close()
             out[(n, p)] = tuple(ks)
     return out
@@ -156,7 +167,7 @@ def make(name, device="cuda", **overrides):
     w = dict(WORKLOADS[name])
     w.update(overrides)
     ctx = dgmg.Context(w["n"], w["p"], kappa_field(w["kappa"], w["n"]), precision=w["precision"], autotune=1,
-                       p_coarsening=w.get("p_coarsening", 0))
+                       p_coarsening=w.get("p_coarsening", 0), basis=w.get("basis", 0))
     return ctx, sine_rhs(ctx, device)
 
 

@@ -245,10 +245,12 @@ def test_table5_cycle_counts_match_oracle(dgmg, n, p):
 
 
 def test_table5_shape(dgmg):
-    """Parity unpinned (omega, nu and the penalty of Tables 3-5 are not stated):
-    on 9^2, 27^2, 81^2 and p = 2..4 the GL cycle counts stay within 0.5x-2x of
-    Table 5, and, as Sec. 6.5 reports, close to the GLL counts for the same
-    two-peak problem (within 20% or 2 cycles)."""
+    """Parity unpinned (omega, nu and the penalty of Tables 3-5 are not stated;
+    nu = 4, omega = 0.8 is the reading that reproduces them best): on 9^2, 27^2,
+    81^2 and p = 2..4 the GL cycle counts lie between 0.7x the count of Table 5
+    and one cycle above it, and, as Sec. 6.5 reports, stay close to the GLL
+    counts of the same two-peak problem: the unpreconditioned count at or a
+    little above the GLL one, the preconditioned one within a cycle."""
     from paper_2510_00998_gb300 import workloads
     rows = np.loadtxt(os.path.join(GOLDEN, "table5_two_peak_cycles.txt"))
     meshes, degrees = (9, 27, 81), (2, 3, 4)
@@ -259,7 +261,7 @@ def test_table5_shape(dgmg):
         if key not in gl:
             continue
         k_un, k_pr = gl[key]
-        assert 0.5 * gl_un <= k_un <= 2.0 * gl_un, (key, k_un, gl_un)
-        assert 0.5 * gl_pr <= k_pr <= 2.0 * gl_pr, (key, k_pr, gl_pr)
-        for a, b in zip(gl[key], gll[key]):
-            assert abs(a - b) <= max(2, 0.2 * b), (key, gl[key], gll[key])
+        assert 0.7 * gl_un <= k_un <= gl_un + 1, (key, k_un, gl_un)
+        assert 0.7 * gl_pr <= k_pr <= gl_pr + 1, (key, k_pr, gl_pr)
+        assert gll[key][0] <= k_un <= 1.1 * gll[key][0] + 1, (key, gl[key], gll[key])
+        assert abs(k_pr - gll[key][1]) <= 1, (key, gl[key], gll[key])

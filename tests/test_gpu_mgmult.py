@@ -86,10 +86,11 @@ def test_mgmult_cycle_counts_match_oracle(dgmg, n, p):
 @pytest.mark.gpu
 def test_mgmult_tables_3_4_shape(dgmg):
     """Parity unpinned (the paper states neither omega, nu nor the penalty for
-    Tables 3-4): on 9^2 ... 243^2 with factor-3 coarsening and nu = 3 the cycle
-    counts are h-robust (unpreconditioned: within 1.5x across the meshes;
-    preconditioned: not growing with refinement), grow with p, and stay within
-    0.5x-2x of the printed counts."""
+    Tables 3-4): on 9^2 ... 243^2 with factor-3 coarsening, nu = 4 and omega = 0.8
+    (the reading that reproduces the printed tables best) the cycle counts are
+    h-robust (unpreconditioned: within 1.5x across the meshes; preconditioned: not
+    growing with refinement), grow with p, and lie between 0.7x the printed
+    count and one cycle above it."""
     from paper_2510_00998_gb300 import workloads
     rows = np.loadtxt(os.path.join(GOLDEN, "table3_4_cycles.txt"))
     got = workloads.tables34(meshes=(9, 27, 81, 243), degrees=(2, 3))
@@ -103,5 +104,5 @@ def test_mgmult_tables_3_4_shape(dgmg):
     for n, p, unprec, prec in rows:
         if (int(n), int(p)) in got:
             k_un, k_pr = got[(int(n), int(p))]
-            assert 0.5 * unprec <= k_un <= 2.0 * unprec, (n, p, k_un, unprec)
-            assert 0.5 * prec <= k_pr <= 2.0 * prec, (n, p, k_pr, prec)
+            assert 0.7 * unprec <= k_un <= unprec + 1, (n, p, k_un, unprec)
+            assert 0.7 * prec <= k_pr <= prec + 1, (n, p, k_pr, prec)
