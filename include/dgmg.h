@@ -102,7 +102,7 @@ typedef struct {
                                   /* (default 1e-10)                                   */
     int maxit;                    /* dgmg_solve iteration cap (default 200)            */
     int outer;                    /* DGMG_OUTER_* (default AUTO)                       */
-    double delta;                 /* reliable-update factor, 0 < delta < 1 (0.1)       */
+    double delta;                 /* reliable-update factor, 0 < delta < 1 (0.01)      */
     int autotune;                 /* 1: dgmg_create times the candidate tile shapes of */
                                   /* the DG-level kernels on this mesh and keeps the   */
                                   /* fastest (cached per mesh shape in the process);   */

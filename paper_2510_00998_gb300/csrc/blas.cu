@@ -31,6 +31,33 @@ __global__ void k_dot_partial(int64_t n, const double *__restrict__ x, const dou
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
+// The same with 16-byte loads, two per vector in flight per thread (x, y
+// 16-byte aligned); the n % 2 tail goes to the last thread of the grid.
+__global__ void __launch_bounds__(DOT_THREADS) k_dot_partial_v(int64_t n, const double *__restrict__ x,
+                                                               const double *__restrict__ y,
+                                                               double *__restrict__ partials) {
+    __shared__ double sh[32];
+    const double2 *x2 = reinterpret_cast<const double2 *>(x), *y2 = reinterpret_cast<const double2 *>(y);
+    const int64_t n2 = n >> 1, stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double s0 = 0.0, s1 = 0.0;
+    for (; i + stride < n2; i += 2 * stride) {
+        const double2 a = x2[i], b = y2[i], c = x2[i + stride], d = y2[i + stride];
+        s0 = fma(a.x, b.x, s0);
+        s0 = fma(a.y, b.y, s0);
+        s1 = fma(c.x, d.x, s1);
+        s1 = fma(c.y, d.y, s1);
+    }
+    if (i < n2) {
+        const double2 a = x2[i], b = y2[i];
+        s0 = fma(a.x, b.x, s0);
+        s0 = fma(a.y, b.y, s0);
+    }
+    if ((n & 1) && blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) s1 = fma(x[n - 1], y[n - 1], s1);
+    const double s = block_sum(s0 + s1, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
 __global__ void k_dot2_partial(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
                                const double *__restrict__ z, double *__restrict__ partials) {
     __shared__ double sh[32];
@@ -92,6 +119,104 @@ __global__ void k_f2d(int64_t n, const float *__restrict__ x, double *__restrict
 __global__ void k_copy_scalar(const double *src, double *dst) { *dst = *src; }
 
 // FP32 vectors with FP64 accumulation (the inner loop of the mixed solver)
+//
+// Vectorised form: 16-byte loads, two float4 per vector in flight per thread;
+// the four products of a float4 are summed in FP32 (fused multiply-adds) and
+// each such group sum is accumulated in FP64. A group sum carries an error of
+// a few FP32 ulps of its terms, the order of the FP32 rounding of the vector
+// entries themselves. The n % 4 tail goes to the last thread of the grid.
+__device__ __forceinline__ float dot4(const float4 a, const float4 b) {
+    return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x)));
+}
+
+// partials[block] = sum x.y; with z: partials[gridDim + block] = sum z.y
+template <bool TWO>
+__global__ void __launch_bounds__(DOT_THREADS) k_dotf_partial_v(int64_t n, const float *__restrict__ x,
+                                                                const float *__restrict__ y,
+                                                                const float *__restrict__ z,
+                                                                double *__restrict__ partials) {
+    __shared__ double sh[32];
+    const float4 *x4 = reinterpret_cast<const float4 *>(x), *y4 = reinterpret_cast<const float4 *>(y);
+    const float4 *z4 = reinterpret_cast<const float4 *>(z);
+    const int64_t n4 = n >> 2, stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double s = 0.0, t = 0.0;
+    for (; i + stride < n4; i += 2 * stride) {
+        const float4 b0 = y4[i], b1 = y4[i + stride];
+        const float4 a0 = x4[i], a1 = x4[i + stride];
+        if (TWO) {
+            const float4 c0 = z4[i], c1 = z4[i + stride];
+            t += (double)dot4(c0, b0) + (double)dot4(c1, b1);
+        }
+        s += (double)dot4(a0, b0) + (double)dot4(a1, b1);
+    }
+    if (i < n4) {
+        const float4 b0 = y4[i];
+        s += (double)dot4(x4[i], b0);
+        if (TWO) t += (double)dot4(z4[i], b0);
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1)
+        for (int64_t k = n4 << 2; k < n; ++k) {
+            s += (double)x[k] * (double)y[k];
+            if (TWO) t += (double)z[k] * (double)y[k];
+        }
+    s = block_sum(s, sh);
+    if (TWO) {
+        __syncthreads();
+        t = block_sum(t, sh);
+    }
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = s;
+        if (TWO) partials[gridDim.x + blockIdx.x] = t;
+    }
+}
+
+// xs += alpha p, r -= alpha q, rold = old r, and partials[block] = sum of the
+// new r squared (the CG update and the residual norm in one pass; 16-byte
+// aligned vectors; group sums as in k_dotf_partial_v)
+__global__ void __launch_bounds__(DOT_THREADS) k_update_xr_dot_f(int64_t n, float *__restrict__ xs,
+                                                                 float *__restrict__ r, float *__restrict__ rold,
+                                                                 const float *__restrict__ p,
+                                                                 const float *__restrict__ q,
+                                                                 const double *__restrict__ scal,
+                                                                 double *__restrict__ partials) {
+    __shared__ double sh[32];
+    const float alpha = (float)(scal[0] / scal[1]);
+    float4 *xs4 = reinterpret_cast<float4 *>(xs), *r4 = reinterpret_cast<float4 *>(r);
+    float4 *ro4 = reinterpret_cast<float4 *>(rold);
+    const float4 *p4 = reinterpret_cast<const float4 *>(p), *q4 = reinterpret_cast<const float4 *>(q);
+    const int64_t n4 = n >> 2, stride = (int64_t)gridDim.x * blockDim.x;
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+        const float4 ri = r4[i], pi = p4[i], qi = q4[i];
+        float4 xi = xs4[i];
+        if (rold) ro4[i] = ri;
+        xi.x = fmaf(alpha, pi.x, xi.x);
+        xi.y = fmaf(alpha, pi.y, xi.y);
+        xi.z = fmaf(alpha, pi.z, xi.z);
+        xi.w = fmaf(alpha, pi.w, xi.w);
+        float4 rn;
+        rn.x = fmaf(-alpha, qi.x, ri.x);
+        rn.y = fmaf(-alpha, qi.y, ri.y);
+        rn.z = fmaf(-alpha, qi.z, ri.z);
+        rn.w = fmaf(-alpha, qi.w, ri.w);
+        xs4[i] = xi;
+        r4[i] = rn;
+        s += (double)dot4(rn, rn);
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1)
+        for (int64_t k = n4 << 2; k < n; ++k) {
+            const float ri = r[k];
+            if (rold) rold[k] = ri;
+            xs[k] = fmaf(alpha, p[k], xs[k]);
+            const float rn = fmaf(-alpha, q[k], ri);
+            r[k] = rn;
+            s += (double)rn * (double)rn;
+        }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
 __global__ void k_dotf_partial(int64_t n, const float *__restrict__ x, const float *__restrict__ y,
                                double *__restrict__ partials) {
     __shared__ double sh[32];
@@ -164,25 +289,65 @@ __global__ void k_quad_points(int dim, int n0, int n1, int n2, int mq, const dou
 }
 
 // b[cell][node] = sum_g w_g f_g phi_node(x_g) with phi = product of 1D Lagrange
-// values V[i][g] (q x mq) and w = product of the 1D Gauss weights scaled to the cell.
-__global__ void k_load_vector(int dim, int q, int mq, int64_t ncell, const double *__restrict__ V,
-                              const double *__restrict__ wq, const double *__restrict__ fq, double *__restrict__ b) {
-    const int nl = dim == 3 ? q * q * q : q * q;
+// values V[i][g] (q x mq) and w = product of the 1D Gauss weights scaled to the
+// cell, sum-factorised: one CTA per cell contracts the mq^d point values with
+// W_a[i][g] = V[i][g] w_a[g] one axis at a time (x, then y, then z).
+constexpr int LV_THREADS = 128;
+constexpr int LV_MQ = QMAX + 1;     // Gauss points per axis of the load quadrature (p + 2)
+__global__ void __launch_bounds__(LV_THREADS) k_load_vector(int dim, int q, int mq, int64_t ncell,
+                                                            const double *__restrict__ V,
+                                                            const double *__restrict__ wq,
+                                                            const double *__restrict__ fq, double *__restrict__ b) {
+    __shared__ double sW[3][QMAX * LV_MQ];
+    __shared__ double sF[LV_MQ * LV_MQ * LV_MQ];
+    __shared__ double s1[QMAX * LV_MQ * LV_MQ];
+    __shared__ double s2[QMAX * QMAX * LV_MQ];
+    const int64_t cell = blockIdx.x;
+    const int t = threadIdx.x;
     const int npc = dim == 3 ? mq * mq * mq : mq * mq;
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= ncell * nl) return;
-    const int64_t cell = idx / nl;
-    const int node = (int)(idx % nl);
-    const int a[3] = {node % q, (node / q) % q, node / (q * q)};
-    const double *f = fq + cell * npc;
-    double s = 0.0;
-    for (int g = 0; g < npc; ++g) {
-        const int gi[3] = {g % mq, (g / mq) % mq, g / (mq * mq)};
-        double w = 1.0;
-        for (int d = 0; d < dim; ++d) w *= wq[d * mq + gi[d]] * V[a[d] * mq + gi[d]];
-        s += w * f[g];
+    for (int e = t; e < dim * q * mq; e += blockDim.x) {
+        const int a = e / (q * mq), r = e - a * q * mq, g = r % mq;
+        sW[a][r] = V[r] * wq[a * mq + g];
     }
-    b[idx] = s;
+    for (int e = t; e < npc; e += blockDim.x) sF[e] = fq[cell * npc + e];
+    __syncthreads();
+    // x: s1[i + q (g2 + mq g3)] = sum_g1 W_x[i][g1] f[g1 + mq (g2 + mq g3)]
+    const int n1 = dim == 3 ? q * mq * mq : q * mq;
+    for (int e = t; e < n1; e += blockDim.x) {
+        const int i = e % q, rest = e / q;
+        double s = 0.0;
+        for (int g = 0; g < mq; ++g) s = fma(sW[0][i * mq + g], sF[g + mq * rest], s);
+        s1[e] = s;
+    }
+    __syncthreads();
+    const int nl = dim == 3 ? q * q * q : q * q;
+    double *out = b + cell * nl;
+    if (dim == 2) {
+        // y: b[i + q j] = sum_g2 W_y[j][g2] s1[i + q g2]
+        for (int e = t; e < nl; e += blockDim.x) {
+            const int i = e % q, j = e / q;
+            double s = 0.0;
+            for (int g = 0; g < mq; ++g) s = fma(sW[1][j * mq + g], s1[i + q * g], s);
+            out[e] = s;
+        }
+        return;
+    }
+    // y: s2[i + q (j + q g3)] = sum_g2 W_y[j][g2] s1[i + q (g2 + mq g3)]
+    const int n2 = q * q * mq;
+    for (int e = t; e < n2; e += blockDim.x) {
+        const int i = e % q, j = (e / q) % q, g3 = e / (q * q);
+        double s = 0.0;
+        for (int g = 0; g < mq; ++g) s = fma(sW[1][j * mq + g], s1[i + q * (g + mq * g3)], s);
+        s2[e] = s;
+    }
+    __syncthreads();
+    // z: b[i + q (j + q k)] = sum_g3 W_z[k][g3] s2[i + q (j + q g3)]
+    for (int e = t; e < nl; e += blockDim.x) {
+        const int ij = e % (q * q), k = e / (q * q);
+        double s = 0.0;
+        for (int g = 0; g < mq; ++g) s = fma(sW[2][k * mq + g], s2[ij + q * q * g], s);
+        out[e] = s;
+    }
 }
 
 inline unsigned grid_for(int64_t n) {
@@ -192,9 +357,18 @@ inline unsigned grid_for(int64_t n) {
 
 }  // namespace
 
+inline bool aligned16(const void *a, const void *b, const void *c = nullptr, const void *d = nullptr,
+                      const void *e = nullptr) {
+    return ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(c) |
+             reinterpret_cast<uintptr_t>(d) | reinterpret_cast<uintptr_t>(e)) & 15) == 0;
+}
+
 cudaError_t launch_dot(int64_t n, const double *x, const double *y, double *partials, double *out, cudaStream_t s) {
     count_launches(2);
-    k_dot_partial<<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(n, x, y, partials);
+    if (aligned16(x, y))
+        k_dot_partial_v<<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(n, x, y, partials);
+    else
+        k_dot_partial<<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(n, x, y, partials);
     k_reduce<<<1, 512, 0, s>>>(DOT_BLOCKS, partials, out);
     return cudaGetLastError();
 }
@@ -262,14 +436,18 @@ cudaError_t launch_load_vector(int dim, int q, int mq, int64_t ncell, const doub
     const int64_t nl = dim == 3 ? (int64_t)q * q * q : (int64_t)q * q;
     const int64_t tot = ncell * nl;
     if (tot == 0) return cudaSuccess;
+    if (q > QMAX || mq > LV_MQ || ncell > 0x7fffffff) return cudaErrorInvalidValue;
     count_launches(1);
-    k_load_vector<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(dim, q, mq, ncell, V, wq, fq, b);
+    k_load_vector<<<(unsigned)ncell, LV_THREADS, 0, s>>>(dim, q, mq, ncell, V, wq, fq, b);
     return cudaGetLastError();
 }
 
 cudaError_t launch_dotf(int64_t n, const float *x, const float *y, double *partials, double *out, cudaStream_t s) {
     count_launches(2);
-    k_dotf_partial<<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(n, x, y, partials);
+    if (aligned16(x, y))
+        k_dotf_partial_v<false><<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(n, x, y, nullptr, partials);
+    else
+        k_dotf_partial<<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(n, x, y, partials);
     k_reduce<<<1, 512, 0, s>>>(DOT_BLOCKS, partials, out);
     return cudaGetLastError();
 }
@@ -277,7 +455,10 @@ cudaError_t launch_dotf(int64_t n, const float *x, const float *y, double *parti
 cudaError_t launch_dot2f(int64_t n, const float *x, const float *y, const float *z, double *partials,
                          double *out_xy, double *out_zy, cudaStream_t s) {
     count_launches(3);
-    k_dot2f_partial<<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(n, x, y, z, partials);
+    if (aligned16(x, y, z))
+        k_dotf_partial_v<true><<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(n, x, y, z, partials);
+    else
+        k_dot2f_partial<<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(n, x, y, z, partials);
     k_reduce<<<1, 512, 0, s>>>(DOT_BLOCKS, partials, out_xy);
     k_reduce<<<1, 512, 0, s>>>(DOT_BLOCKS, partials + DOT_BLOCKS, out_zy);
     return cudaGetLastError();
@@ -287,6 +468,19 @@ cudaError_t launch_update_xr_f(int64_t n, float *xs, float *r, float *rold, cons
                                const double *scal, cudaStream_t s) {
     count_launches(1);
     k_update_xr_f<<<grid_for(n), 256, 0, s>>>(n, xs, r, rold, p, q, scal);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_xr_dot_f(int64_t n, float *xs, float *r, float *rold, const float *p, const float *q,
+                                   const double *scal, double *partials, double *out_rr, cudaStream_t s) {
+    if (!aligned16(xs, r, rold, p, q)) {
+        const cudaError_t e = launch_update_xr_f(n, xs, r, rold, p, q, scal, s);
+        if (e != cudaSuccess) return e;
+        return launch_dotf(n, r, r, partials, out_rr, s);
+    }
+    count_launches(2);
+    k_update_xr_dot_f<<<DOT_BLOCKS, DOT_THREADS, 0, s>>>(n, xs, r, rold, p, q, scal, partials);
+    k_reduce<<<1, 512, 0, s>>>(DOT_BLOCKS, partials, out_rr);
     return cudaGetLastError();
 }
 

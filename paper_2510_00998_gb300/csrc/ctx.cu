@@ -935,7 +935,7 @@ void dgmg_default_opts(dgmg_opts *o) {
     o->rtol = 1e-10;
     o->maxit = 200;
     o->outer = DGMG_OUTER_AUTO;
-    o->delta = 0.1;
+    o->delta = 0.01;
     o->autotune = 0;
     o->p_coarsening = 0;
     o->basis = DGMG_BASIS_GLL;

@@ -221,6 +221,9 @@ cudaError_t launch_dot2f(int64_t n, const float *x, const float *y, const float 
                          double *out_xy, double *out_zy, cudaStream_t s);
 cudaError_t launch_update_xr_f(int64_t n, float *xs, float *r, float *rold, const float *p, const float *q,
                                const double *scal, cudaStream_t s);
+// launch_update_xr_f and *out_rr = ||r||^2 of the updated r, in one pass over the vectors
+cudaError_t launch_update_xr_dot_f(int64_t n, float *xs, float *r, float *rold, const float *p, const float *q,
+                                   const double *scal, double *partials, double *out_rr, cudaStream_t s);
 cudaError_t launch_update_p_f(int64_t n, float *p, const float *z, const double *scal, cudaStream_t s);
 cudaError_t launch_accumulate_f2d(int64_t n, double *x, float *xs, cudaStream_t s);
 cudaError_t launch_quad_points(int dim, int q, const int *n, int mq, const double *xq1,
@@ -233,7 +236,7 @@ int64_t corner_scratch_count(const dgmg_ctx *C);
 int residual_restrict_with_scratch(dgmg_ctx *C, const double *u, const double *b, const double *traces,
                                    double *r, double *rc, double *corner_scratch, cudaStream_t s);
 
-constexpr int DOT_BLOCKS = 304;     // 2 x 152 SMs
+constexpr int DOT_BLOCKS = 608;     // 4 x 152 SMs
 constexpr int DOT_THREADS = 256;
 
 }  // namespace dgmg

@@ -209,8 +209,7 @@ int SolveRun::reliable_chunk(bool update_dir, cudaStream_t st) {
     RC(apply32(*C, p32, q32, st));
     C->prof.begin(ST_VECTOR, st);
     LC(launch_dotf(n, p32, q32, C->partials, C->scal + S_PQ, st));
-    LC(launch_update_xr_f(n, xs, r32, rold32, p32, q32, C->scal, st));
-    LC(launch_dotf(n, r32, r32, C->partials, C->scal + S_RR, st));
+    LC(launch_update_xr_dot_f(n, xs, r32, rold32, p32, q32, C->scal, C->partials, C->scal + S_RR, st));
     C->prof.end(st);
     return copy_scalars(C, st);
 }
