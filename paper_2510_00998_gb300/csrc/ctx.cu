@@ -681,7 +681,7 @@ int coarse_correction(dgmg_ctx &C, int l, T *z, const T *b, int cur, cudaStream_
     if (l == (int)C.dgs.size() - 1) {
         C.prof.begin(ST_RESIDUAL, s);
         LC(launch_residual<T>(C.dim, S.q, D.c, tres, RES_HAS_B | RES_CORNERS, z, b, D.kappa, D.tr[cur], nullptr,
-                              D.corners, s));
+                              D.corners, exact_fd(C, D), s));
         C.prof.end(s);
         auto &lv = cgl<T>(C);
         C.prof.begin(ST_CG, s);
@@ -699,7 +699,7 @@ int coarse_correction(dgmg_ctx &C, int l, T *z, const T *b, int cur, cudaStream_
     T *res = l == 0 ? (std::is_same<T, float>::value ? (T *)C.res32 : (T *)C.res64) : lvl[l].r;
     C.prof.begin(ST_RESIDUAL, s);
     LC(launch_residual<T>(C.dim, S.q, D.c, tres, RES_HAS_B | RES_WRITE_R, z, b, D.kappa, D.tr[cur], res, nullptr,
-                          s));
+                          exact_fd(C, D), s));
     C.prof.end(s);
     C.prof.begin(ST_CG, s);
     LC(launch_dg_transfer<T>(C.dim, S.q, false, C.ncell, N.P, res, N.b, s));
@@ -758,7 +758,7 @@ int mg_cycle64(dgmg_ctx &C, double *x, const double *b, double *r, cudaStream_t 
     if (r) {
         C.prof.begin(ST_RESIDUAL, s);
         LC(launch_residual<double>(C.dim, C.q, D.c, C.tile[0][TILE_RESIDUAL], RES_HAS_B | RES_WRITE_R, x, b,
-                                   D.kappa, D.tr[0], r, nullptr, s));
+                                   D.kappa, D.tr[0], r, nullptr, exact_fd(C, D), s));
         C.prof.end(s);
     }
     return DGMG_OK;
@@ -796,7 +796,7 @@ int apply64(dgmg_ctx &C, const double *u, const double *b, double *out, cudaStre
     const int mode = b ? (RES_HAS_B | RES_WRITE_R) : (RES_WRITE_R | RES_NEGATE);
     C.prof.begin(ST_RESIDUAL, s);
     LC(launch_residual<double>(C.dim, C.q, D.c, C.tile[0][TILE_RESIDUAL], mode, u, b, D.kappa, D.tr[0], out,
-                               nullptr, s));
+                               nullptr, exact_fd(C, D), s));
     C.prof.end(s);
     return DGMG_OK;
 }
@@ -817,7 +817,7 @@ static std::mutex g_tile_mu;
 static std::map<TileKey, std::array<int, 6>> g_tile_cache;
 
 template <typename T>
-static int tune_tiles(dgmg_ctx &C, T *u, T *b, int *tile, bool trace) {
+static int tune_tiles(dgmg_ctx &C, T *u, T *b, int *tile, bool trace, bool smooth) {
     DGDev<T> &D = dg<T>(C);
     cudaStream_t s = C.setup_stream;
     const int nf = (int)(C.nloc / C.q);
@@ -871,13 +871,16 @@ static int tune_tiles(dgmg_ctx &C, T *u, T *b, int *tile, bool trace) {
     });
     std::vector<int> cs = cand;
     if (C.dim == 3 && C.q <= (std::is_same<T, float>::value ? 5 : 4) && exact_block(C)) cs.insert(cs.begin(), 0);
-    tile[TILE_SMOOTH] = pick("smooth", cs, [&](int c) {
-        return launch_smooth<T>(C.dim, C.q, D.c, c, exact_block(C), u, b, D.kappa, D.fd, D.linv, D.tr[0],
-                                D.tr[1], s);
-    });
-    tile[TILE_RESIDUAL] = pick("residual", cand, [&](int c) {
+    if (smooth)                     // (the FP64 smoother of a mixed-precision context never runs)
+        tile[TILE_SMOOTH] = pick("smooth", cs, [&](int c) {
+            return launch_smooth<T>(C.dim, C.q, D.c, c, exact_block(C), u, b, D.kappa, D.fd, D.linv, D.tr[0],
+                                    D.tr[1], s);
+        });
+    std::vector<int> cr = cand;
+    if (C.dim == 3 && C.q <= (std::is_same<T, float>::value ? 5 : 4) && exact_fd(C, D)) cr.insert(cr.begin(), 0);
+    tile[TILE_RESIDUAL] = pick("residual", cr, [&](int c) {
         return launch_residual<T>(C.dim, C.q, D.c, c, RES_HAS_B | RES_CORNERS, u, b, D.kappa, D.tr[0], nullptr,
-                                  D.corners, s);
+                                  D.corners, exact_fd(C, D), s);
     });
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -897,8 +900,8 @@ static int autotune_tiles(dgmg_ctx &C) {
         }
     }
     const bool trace = std::getenv("DGMG_TRACE_SETUP") != nullptr;
-    RC(tune_tiles<double>(C, C.w_z, C.w_r, C.tile[0], trace));
-    if (mixed) RC(tune_tiles<float>(C, C.z32, C.r32, C.tile[1], trace));
+    RC(tune_tiles<double>(C, C.w_z, C.w_r, C.tile[0], trace, !mixed));
+    if (mixed) RC(tune_tiles<float>(C, C.z32, C.r32, C.tile[1], trace, true));
     std::array<int, 6> v;
     for (int k = 0; k < 6; ++k) v[k] = C.tile[k / 3][k % 3];
     std::lock_guard<std::mutex> lk(g_tile_mu);
@@ -1003,8 +1006,10 @@ int create_ctx(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_opt
     while (C->cpb * nf > 256) --C->cpb;
     for (int k = 0; k < 2; ++k)
         for (int st = 0; st < 3; ++st) C->tile[k][st] = C->cpb;
-    C->tile[0][TILE_SMOOTH] = 0;   // the one-thread-per-cell smoother where it applies
+    C->tile[0][TILE_SMOOTH] = 0;   // the one-thread-per-cell smoother and residual where they apply
     C->tile[1][TILE_SMOOTH] = 0;
+    C->tile[0][TILE_RESIDUAL] = 0;
+    C->tile[1][TILE_RESIDUAL] = 0;
 
     std::vector<double> kap(C->ncell, 1.0);
     if (kappa) {
@@ -1228,7 +1233,7 @@ int dgmg_residual_restrict(dgmg_ctx *C, const double *u, const double *b, const 
     if (r) mode |= RES_WRITE_R;
     if (rc) mode |= RES_CORNERS;
     LC(launch_residual<double>(C->dim, C->q, C->d64.c, C->tile[0][TILE_RESIDUAL], mode, u, b, C->d64.kappa, traces, r,
-                               C->d64.corners, s));
+                               C->d64.corners, exact_fd(*C, C->d64), s));
     if (rc) LC(launch_corner_gather<double>(C->dim, C->n, C->d64.corners, rc, s));
     return DGMG_OK;
 }
@@ -1417,7 +1422,7 @@ int residual_restrict_with_scratch(dgmg_ctx *C, const double *u, const double *b
     if (r) mode |= RES_WRITE_R;
     if (rc) mode |= RES_CORNERS;
     LC(launch_residual<double>(C->dim, C->q, C->d64.c, C->tile[0][TILE_RESIDUAL], mode, u, b, C->d64.kappa, traces, r,
-                               corner_scratch, s));
+                               corner_scratch, exact_fd(*C, C->d64), s));
     if (rc) LC(launch_corner_gather<double>(C->dim, C->n, corner_scratch, rc, s));
     return DGMG_OK;
 }

@@ -231,6 +231,12 @@ namespace dgmg {
 
 int check_ctx(const dgmg_ctx *C);
 int exact_block(const dgmg_ctx &C);
+// the level's per-cell factors when they factor the exact diagonal blocks A_KK
+// (the one-thread-per-cell residual forms A_KK u from them), else null
+template <typename T>
+inline const T *exact_fd(const dgmg_ctx &C, const DGDev<T> &D) {
+    return exact_block(C) ? D.fd : nullptr;
+}
 // y = A u (b == NULL) or out = b - A u, FP64
 int apply64(dgmg_ctx &C, const double *u, const double *b, double *out, cudaStream_t s);
 // y = A u in FP32

@@ -20,8 +20,8 @@ cudaError_t launch_smooth<float>(int dim, int q, const DGConst<float> &c, int cp
 template <>
 cudaError_t launch_residual<float>(int dim, int q, const DGConst<float> &c, int cpb, int mode, const float *u,
                                   const float *b, const float *kappa, const float *tr, float *r, float *corners,
-                                  cudaStream_t s) {
-    return launch_residual_impl<float>(dim, q, c, cpb, mode, u, b, kappa, tr, r, corners, s);
+                                  const float *fd, cudaStream_t s) {
+    return launch_residual_impl<float>(dim, q, c, cpb, mode, u, b, kappa, tr, r, corners, fd, s);
 }
 
 template <>

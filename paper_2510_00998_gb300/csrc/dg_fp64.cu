@@ -20,8 +20,8 @@ cudaError_t launch_smooth<double>(int dim, int q, const DGConst<double> &c, int 
 template <>
 cudaError_t launch_residual<double>(int dim, int q, const DGConst<double> &c, int cpb, int mode, const double *u,
                                   const double *b, const double *kappa, const double *tr, double *r, double *corners,
-                                  cudaStream_t s) {
-    return launch_residual_impl<double>(dim, q, c, cpb, mode, u, b, kappa, tr, r, corners, s);
+                                  const double *fd, cudaStream_t s) {
+    return launch_residual_impl<double>(dim, q, c, cpb, mode, u, b, kappa, tr, r, corners, fd, s);
 }
 
 template <>

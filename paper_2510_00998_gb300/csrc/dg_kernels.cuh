@@ -925,6 +925,25 @@ struct DGLaunch {
             return cudaErrorInvalidValue;
         }
     }
+    static cudaError_t residual_cells(const DGConst<T> &c, int mode, const T *u, const T *b, const T *kappa,
+                                      const T *fd, const T *tr, T *r, T *corners, cudaStream_t s) {
+        if constexpr (CELLS_OK) {
+            using CG = CellGeo<T, Q>;
+            static bool attr = false;
+            if (!attr) {
+                cudaFuncSetAttribute(k_residual_cells<T, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)CG::BYTES);
+                attr = true;
+            }
+            const int64_t grid = (c.ncell + CG::W - 1) / CG::W;
+            if (grid == 0) return cudaSuccess;
+            count_launches(1);
+            k_residual_cells<T, Q><<<(unsigned)grid, CG::W, CG::BYTES, s>>>(c, mode, u, b, kappa, fd, tr, r, corners);
+            return cudaGetLastError();
+        } else {
+            return cudaErrorInvalidValue;
+        }
+    }
     // ---- batched forms (map: one entry per CTA; cpb cells per CTA, 32 for the
     // one-thread-per-cell smoother)
     static cudaError_t project_batch(const BatchDG<T> *D, const BlockMap *map, int nblocks, int cpb, T *u,
@@ -990,7 +1009,17 @@ struct DGLaunch {
         return cudaGetLastError();
     }
     static cudaError_t residual(const DGConst<T> &c, int cpb, int mode, const T *u, const T *b, const T *kappa,
-                                const T *tr, T *r, T *corners, cudaStream_t s) {
+                                const T *tr, T *r, T *corners, const T *fd, cudaStream_t s) {
+        if constexpr (CELLS_OK) {
+            // bulk copies of u, b, the factors and r want 16-byte alignment; the
+            // face pieces 8- (FP32) or 16-byte (FP64) aligned traces
+            const uintptr_t tra = std::is_same<T, float>::value ? 7 : 15;
+            const uintptr_t vec = reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(fd) |
+                                  ((mode & RES_HAS_B) ? reinterpret_cast<uintptr_t>(b) : 0) |
+                                  ((mode & RES_WRITE_R) ? reinterpret_cast<uintptr_t>(r) : 0);
+            if (cpb <= 0 && fd && !c.gl && (vec & 15) == 0 && (reinterpret_cast<uintptr_t>(tr) & tra) == 0)
+                return residual_cells(c, mode, u, b, kappa, fd, tr, r, corners, s);
+        }
         if (cpb <= 0) cpb = default_cpb();
         const size_t sm = smem_residual<DIM, Q, T>(cpb);
         static bool attr = false;
@@ -1035,8 +1064,8 @@ cudaError_t launch_smooth_impl(int dim, int q, const DGConst<T> &c, int cpb, int
 }
 template <typename T>
 cudaError_t launch_residual_impl(int dim, int q, const DGConst<T> &c, int cpb, int mode, const T *u, const T *b,
-                                 const T *kappa, const T *tr, T *r, T *corners, cudaStream_t s) {
-    DGMG_DISPATCH(dim, q, residual(c, cpb, mode, u, b, kappa, tr, r, corners, s))
+                                 const T *kappa, const T *tr, T *r, T *corners, const T *fd, cudaStream_t s) {
+    DGMG_DISPATCH(dim, q, residual(c, cpb, mode, u, b, kappa, tr, r, corners, fd, s))
 }
 template <typename T>
 cudaError_t launch_project_batch_impl(int dim, int q, const BatchDG<T> *D, const BlockMap *map, int nblocks, int cpb,

@@ -149,9 +149,12 @@ cudaError_t launch_smooth(int dim, int q, const DGConst<T> &c, int cpb, int exac
                           const T *kappa, const T *fd, const T *linv, const T *tr_in, T *tr_out, cudaStream_t s);
 // mode bits for launch_residual
 enum { RES_HAS_B = 1, RES_WRITE_R = 2, RES_CORNERS = 4, RES_NEGATE = 8 };
+// fd: the level's fast-diagonalisation factors of the exact diagonal blocks, or
+// null; with them (3D, q small enough, cpb <= 0) the one-thread-per-cell kernel
+// runs, which forms A_KK u from the factors
 template <typename T>
 cudaError_t launch_residual(int dim, int q, const DGConst<T> &c, int cpb, int mode, const T *u,
-                            const T *b, const T *kappa, const T *tr, T *r, T *corners,
+                            const T *b, const T *kappa, const T *tr, T *r, T *corners, const T *fd,
                             cudaStream_t s);
 
 template <typename T>

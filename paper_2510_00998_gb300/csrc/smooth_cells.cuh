@@ -544,6 +544,272 @@ __device__ __forceinline__ void smooth_cells_body(const DGConst<T> &c, int64_t c
     if (full && lane == 0) bulk_wait_read_all();
 }
 
+// P = S^T M (TRANSPOSE false) or its transpose M S, for a q x q factor S
+// (row-major in shared memory) and the symmetric 1D mass M.
+template <typename T, int Q, bool TRANSPOSE>
+__device__ __forceinline__ void load_mass_factor(const T *src, const T *M, T *P) {
+    T S[Q * Q];
+    load_matrix<T, Q, false>(src, S);
+#pragma unroll
+    for (int m = 0; m < Q; ++m)
+#pragma unroll
+        for (int n = 0; n < Q; ++n) {
+            T v = T(0);
+#pragma unroll
+            for (int l = 0; l < Q; ++l) v += S[l * Q + m] * M[l * Q + n];
+            if (TRANSPOSE)
+                P[n * Q + m] = v;
+            else
+                P[m * Q + n] = v;
+        }
+}
+
+// Residual r = b - A u with one thread per cell, 3D, exact diagonal blocks
+// (Alg. 2 stage 3; the residual of a V-cycle level and the operator apply),
+// with A u = A_KK u + N u_nb. A_KK u from the cell's fast-diagonalisation
+// factors: Kt_a S_a = M_a S_a Lambda_a with S_a^T M_a S_a = I gives
+// A_KK = (M S)^(x3) (Lambda_x + Lambda_y + Lambda_z) (S^T M)^(x3), so A_KK u
+// takes the six tensor passes of the smoother's inverse, with P_a = S_a^T M_a
+// and its transpose, and a multiplication by the eigenvalue sums instead of a
+// division. Then b is added and the neighbour terms are lifted as in the
+// smoothing step. Outputs as for k_residual: r (negated for y = A u) and the
+// cell corner sums of the p-restriction.
+// Staging: u and the factors by bulk copies; FP32: b into u's area once u is
+// in registers, the neighbour faces through the slots once the factors are
+// used; FP64 (LEAN): the factors into u's area, b and the faces read per lane.
+// r leaves through area A by a bulk store.
+template <typename T, int Q>
+__device__ __forceinline__ void residual_cells_body(const DGConst<T> &c, int64_t cell0, int mode,
+                                                    const T *__restrict__ u, const T *__restrict__ b,
+                                                    const T *__restrict__ kappa, const T *__restrict__ fd,
+                                                    const T *__restrict__ tr, T *__restrict__ rout,
+                                                    T *__restrict__ corners) {
+    using G = CellGeo<T, Q>;
+    constexpr int W = G::W, NL = G::NL, NF = G::NF, FDS = G::FDS, TR = G::TR;
+    extern __shared__ __align__(128) unsigned char smem_c[];
+    T *sA = reinterpret_cast<T *>(smem_c);              // u -> b (FP32) or factors (FP64) -> r
+    T *sB = sA + G::OFF_B;                               // FP32: factors -> face slots
+    T *sK = sA + G::OFF_K;
+    int *sNb = reinterpret_cast<int *>(sA + G::OFF_NB);
+    __shared__ __align__(8) uint64_t bars[4];
+    __shared__ T sM[3][Q * Q];
+    const int lane = threadIdx.x;
+    const int ncl = (int)min((int64_t)W, c.ncell - cell0);
+    const bool full = ncl == W;
+    const bool active = lane < ncl;
+    const int64_t cell = cell0 + lane;
+    const bool has_b = (mode & RES_HAS_B) != 0;
+
+    for (int e = lane; e < 3 * Q * Q; e += W) sM[e / (Q * Q)][e % (Q * Q)] = c.M[e / (Q * Q)][e % (Q * Q)];
+    if (full && lane == 0) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
+        fence_mbar_init();
+        fence_proxy_async_smem();
+    }
+    stage_bulk<T>(full, lane, &bars[0], sA, u + cell0 * NL, W * NL, ncl * NL);
+    if (!G::LEAN) stage_bulk<T>(full, lane, &bars[2], sB, fd + cell0 * 3 * FDS, W * 3 * FDS, ncl * 3 * FDS);
+    int mask = 0;
+    {
+        T kK = T(1);
+        if (active) {
+            int ci[3];
+            cell_coords<3>(cell, c.n, ci);
+            mask = interior_mask<3>(ci, c.n);
+            kK = kappa[cell];
+        }
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            int nb = -1;
+            T kF = T(0);
+            if (mask & (1 << f)) {
+                const int64_t st = axis_stride<3>(c.n, f >> 1);
+                nb = (int)((f & 1) ? cell + st : cell - st);
+                const T kN = kappa[nb];
+                kF = T(2) * kK * kN / (kK + kN);
+            }
+            sNb[f * W + lane] = nb;
+            sK[f * W + lane] = kF;
+        }
+    }
+    __syncwarp();
+
+    if (full) {
+        if (!warp_wait_copies(&bars[0], lane)) {
+            if (!G::LEAN) warp_wait_copies(&bars[2], lane);
+            return;
+        }
+    } else {
+        __syncwarp();
+    }
+    T R[NL];
+#pragma unroll
+    for (int e = 0; e < NL; ++e) R[e] = active ? sA[lane * NL + e] : T(0);
+    fence_proxy_async_smem();
+    __syncwarp();
+    // area A: the factors (FP64) or b (FP32)
+    if (G::LEAN)
+        stage_bulk<T>(full, lane, &bars[1], sA, fd + cell0 * 3 * FDS, W * 3 * FDS, ncl * 3 * FDS);
+    else if (has_b)
+        stage_bulk<T>(full, lane, &bars[1], sA, b + cell0 * NL, W * NL, ncl * NL);
+    const bool b_staged = !G::LEAN && has_b;
+
+    // R = A_KK u: P along x, y, z; times the eigenvalue sums; P^T along z, y, x
+    if (full) {
+        if (!warp_wait_copies(&bars[G::LEAN ? 1 : 2], lane)) {
+            if (b_staged) warp_wait_copies(&bars[1], lane);
+            return;
+        }
+    } else {
+        __syncwarp();
+    }
+    const T *myFD = (G::LEAN ? sA : sB) + lane * 3 * FDS;
+    if (active) {
+#pragma unroll 1
+        for (int p = 0; p < 3; ++p) {
+            T P[Q * Q];
+            load_mass_factor<T, Q, false>(myFD + p * FDS, sM[p], P);
+            pass_x<T, Q>(P, R);
+            rotate<T, Q>(R);
+        }
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            const T lz = myFD[2 * FDS + Q * Q + k];
+#pragma unroll
+            for (int j = 0; j < Q; ++j) {
+                const T lyz = myFD[1 * FDS + Q * Q + j] + lz;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) R[i + Q * (j + Q * k)] *= myFD[Q * Q + i] + lyz;
+            }
+        }
+#pragma unroll 1
+        for (int p = 2; p >= 0; --p) {
+            T P[Q * Q];
+            rotate_back<T, Q>(R);
+            load_mass_factor<T, Q, true>(myFD + p * FDS, sM[p], P);
+            pass_x<T, Q>(P, R);
+        }
+    }
+    // R = b - A_KK u
+    if (b_staged && full) {
+        if (!warp_wait_copies(&bars[1], lane)) return;
+    } else {
+        __syncwarp();
+    }
+    if (active) {
+        const T *bb = has_b ? (G::LEAN ? b + cell * NL : sA + lane * NL) : nullptr;
+#pragma unroll
+        for (int e = 0; e < NL; ++e) R[e] = (bb ? bb[e] : T(0)) - R[e];
+    }
+    // FP32: the neighbour faces into the slots (every lane is done with the factors)
+    if (!G::LEAN) {
+        fence_proxy_async_smem();
+        __syncwarp();
+        stage_face<T, Q>(0, ncl, lane, sNb, tr, sB);
+        stage_face<T, Q>(1, ncl, lane, sNb, tr, sB + W * 2 * NF);
+    }
+    // R -= N u_nb, face pair by face pair as in the smoothing step
+#pragma unroll 1
+    for (int p = 0; p < 3; ++p) {
+        T dv[Q];
+        const int ta = p == 2 ? 0 : p + 1, tb = p == 0 ? 2 : p - 1;
+        const int sa = p == 1 ? Q : 1, sb = p == 1 ? 1 : Q;
+        const T gam = c.gamma[p];
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const int f = 2 * p + side;
+            if (!G::LEAN) {
+                if (f < 5)
+                    cp_async_wait<1>();
+                else
+                    cp_async_wait<0>();
+                __syncwarp();
+            }
+            if (active && (mask & (1 << f))) {
+#pragma unroll
+                for (int n = 0; n < Q; ++n) dv[n] = side ? c.dp[p][n] : c.d0[p][n];
+                const T *fld = G::LEAN ? tr + (int64_t)sNb[f * W + lane] * TR + (f ^ 1) * 2 * NF
+                                       : sB + side * W * 2 * NF + lane * 2 * NF;
+                lift_x_face<T, Q>(side, fld, sa, sb, sM[ta], sM[tb], dv, gam, sK[f * W + lane], R);
+            }
+            if (!G::LEAN) {
+                __syncwarp();
+                if (f + 2 < 6) stage_face<T, Q>(f + 2, ncl, lane, sNb, tr, sB + side * W * 2 * NF);
+            }
+        }
+        rotate<T, Q>(R);
+    }
+    if (mode & RES_NEGATE) {
+#pragma unroll
+        for (int e = 0; e < NL; ++e) R[e] = -R[e];
+    }
+    if (mode & RES_WRITE_R) {
+        __syncwarp();                                  // every lane is done with area A
+        if (active) {
+#pragma unroll
+            for (int e = 0; e < NL; ++e) sA[lane * NL + e] = R[e];
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (full) {
+            if (lane == 0) {
+                bulk_store(rout + cell0 * NL, sA, (unsigned)(W * NL * sizeof(T)));
+                bulk_commit();
+            }
+        } else {
+            for (int e = lane; e < ncl * NL; e += W) rout[cell0 * NL + e] = sA[e];
+        }
+    }
+    if ((mode & RES_CORNERS) && active) {
+        // corner (cx, cy, cz): sum over the nodes of hat_cx(x_i) hat_cy(y_j) hat_cz(z_k) r_ijk
+        T X[2][Q * Q];
+#pragma unroll
+        for (int t = 0; t < Q * Q; ++t) {
+            T s0 = T(0), s1 = T(0);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                s0 += c.hat[0][i] * R[i + Q * t];
+                s1 += c.hat[1][i] * R[i + Q * t];
+            }
+            X[0][t] = s0;
+            X[1][t] = s1;
+        }
+        T out[8];
+#pragma unroll
+        for (int cx = 0; cx < 2; ++cx)
+#pragma unroll
+            for (int cy = 0; cy < 2; ++cy) {
+                T Y[Q];
+#pragma unroll
+                for (int k = 0; k < Q; ++k) {
+                    T sy = T(0);
+#pragma unroll
+                    for (int j = 0; j < Q; ++j) sy += c.hat[cy][j] * X[cx][j + Q * k];
+                    Y[k] = sy;
+                }
+#pragma unroll
+                for (int cz = 0; cz < 2; ++cz) {
+                    T sz = T(0);
+#pragma unroll
+                    for (int k = 0; k < Q; ++k) sz += c.hat[cz][k] * Y[k];
+                    out[cx | (cy << 1) | (cz << 2)] = sz;
+                }
+            }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) corners[cell * 8 + k] = out[k];
+    }
+    if ((mode & RES_WRITE_R) && full && lane == 0) bulk_wait_read_all();
+}
+
+template <typename T, int Q>
+__global__ void __launch_bounds__(32) k_residual_cells(const __grid_constant__ DGConst<T> c, int mode,
+                                                       const T *__restrict__ u, const T *__restrict__ b,
+                                                       const T *__restrict__ kappa, const T *__restrict__ fd,
+                                                       const T *__restrict__ tr, T *__restrict__ rout,
+                                                       T *__restrict__ corners) {
+    residual_cells_body<T, Q>(c, (int64_t)blockIdx.x * CellGeo<T, Q>::W, mode, u, b, kappa, fd, tr, rout, corners);
+}
+
 template <typename T, int Q>
 __global__ void __launch_bounds__(32) k_smooth_cells(const __grid_constant__ DGConst<T> c, T *__restrict__ u,
                                                      const T *__restrict__ b, const T *__restrict__ kappa,

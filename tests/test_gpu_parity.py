@@ -353,7 +353,7 @@ def test_autotuned_tiles(dgmg, n, p, prec):
     for tune in (0, 1):
         ctx = dgmg.Context(n, p, kap, precision=prec, autotune=tune)
         tiles = list(ctx.info.tiles)
-        assert all(t >= 0 for t in tiles) and tiles[0] > 0 and tiles[2] > 0
+        assert all(t >= 0 for t in tiles) and tiles[0] > 0   # 0: the one-thread-per-cell kernel
         if prec == 0:
             assert tiles[3:] == [0, 0, 0]
         x = torch.zeros(mesh.ndof, dtype=torch.float64, device=DEV)
