@@ -304,99 +304,36 @@ void fill_const(const dgmg_ctx &C, const DGSpace &S, DGConst<T> &c) {
     c.omega = (T)C.opts.omega_dg;
 }
 
-// Per-cell fast-diagonalisation factors of the exact diagonal block:
-// Kt_a = kappa_K K_a + low-face and high-face own terms (Sec. 4.1 Schur block),
-// Kt_a S = M_a S diag(lambda), S^T M_a S = I.
-void fast_diag_factors(const dgmg_ctx &C, const DGSpace &S, const std::vector<double> &kappa, std::vector<double> &fd) {
-    const int q = S.q, dim = C.dim, fds = q * q + q;
-    fd.assign((size_t)C.ncell * dim * fds, 0.0);
-    double Linv[3][QMAX * QMAX];
-    double Mh[3][QMAX * QMAX], Kh[3][QMAX * QMAX], d0[3][QMAX], dp[3][QMAX], gam[3];
-    for (int a = 0; a < dim; ++a) {
+// Input of the device kernel that computes the per-cell fast-diagonalisation
+// factors of the exact diagonal blocks (Kt_a = kappa_K K_a + the own-face terms
+// of the two faces normal to axis a, Sec. 4.1; Kt_a S = M_a S diag(lambda),
+// S^T M_a S = I): the h-scaled 1D data of space S per axis.
+static int fd_input(const dgmg_ctx &C, const DGSpace &S, FDInput &in) {
+    std::memset(&in, 0, sizeof(in));
+    const int q = S.q;
+    in.dim = C.dim;
+    in.q = q;
+    in.interior_only = C.opts.block_inverse == DGMG_BLOCK_INTERIOR_ONLY ? 1 : 0;
+    for (int a = 0; a < 3; ++a) in.n[a] = C.n[a];
+    for (int i = 0; i < q; ++i) {
+        in.e0[i] = S.re.e0[i];
+        in.ep[i] = S.re.ep[i];
+    }
+    for (int a = 0; a < C.dim; ++a) {
         const double h = 1.0 / C.n[a];
+        double Mh[QMAX * QMAX];
         for (int i = 0; i < q * q; ++i) {
-            Mh[a][i] = S.re.M[i] * h / 2.0;
-            Kh[a][i] = S.re.K[i] * 2.0 / h;
+            Mh[i] = S.re.M[i] * h / 2.0;
+            in.Kh[a][i] = S.re.K[i] * 2.0 / h;
         }
         for (int i = 0; i < q; ++i) {
-            d0[a][i] = S.re.d0[i] * 2.0 / h;
-            dp[a][i] = S.re.dp[i] * 2.0 / h;
+            in.d0[a][i] = S.re.d0[i] * 2.0 / h;
+            in.dp[a][i] = S.re.dp[i] * 2.0 / h;
         }
-        gam[a] = 2.0 * S.penalty_p * (S.penalty_p + 1) / h;
-        cholesky_inverse_lower(q, Mh[a], Linv[a]);
+        in.gam[a] = 2.0 * S.penalty_p * (S.penalty_p + 1) / h;
+        if (!cholesky_inverse_lower(q, Mh, in.Linv[a])) return fail(DGMG_EINVAL, "1D mass matrix not SPD");
     }
-    const bool interior_only = C.opts.block_inverse == DGMG_BLOCK_INTERIOR_ONLY;
-    bool uniform = true;
-    for (int64_t i = 1; i < C.ncell; ++i)
-        if (kappa[i] != kappa[0]) {
-            uniform = false;
-            break;
-        }
-    auto factor = [&](int a, double kK, double kL, double wL, double kR, double wR, double *out) {
-        double Kt[QMAX * QMAX];
-        for (int i = 0; i < q; ++i)
-            for (int j = 0; j < q; ++j) {
-                const double e0i = S.re.e0[i], e0j = S.re.e0[j], epi = S.re.ep[i], epj = S.re.ep[j];
-                double v = kK * Kh[a][i * q + j];
-                v += kL * (wL * (e0i * d0[a][j] + d0[a][i] * e0j) + gam[a] * e0i * e0j);
-                v += kR * (-wR * (epi * dp[a][j] + dp[a][i] * epj) + gam[a] * epi * epj);
-                Kt[i * q + j] = v;
-            }
-        gen_eig_sym(q, Kt, Linv[a], out, out + q * q);
-    };
-    auto cell_factors = [&](int64_t cell, double *dst) {
-        int ci[3] = {(int)(cell % C.n[0]), (int)((cell / C.n[0]) % C.n[1]),
-                     (int)(cell / ((int64_t)C.n[0] * C.n[1]))};
-        const double kK = kappa[cell];
-        for (int a = 0; a < dim; ++a) {
-            const int64_t stride = a == 0 ? 1 : (a == 1 ? C.n[0] : (int64_t)C.n[0] * C.n[1]);
-            double kL, wL, kR, wR;
-            if (interior_only) {
-                kL = kR = kK;
-                wL = wR = 0.5;
-            } else {
-                if (ci[a] > 0) {
-                    const double kN = kappa[cell - stride];
-                    kL = 2.0 * kK * kN / (kK + kN);
-                    wL = 0.5;
-                } else {
-                    kL = kK;
-                    wL = 1.0;
-                }
-                if (ci[a] < C.n[a] - 1) {
-                    const double kN = kappa[cell + stride];
-                    kR = 2.0 * kK * kN / (kK + kN);
-                    wR = 0.5;
-                } else {
-                    kR = kK;
-                    wR = 1.0;
-                }
-            }
-            factor(a, kK, kL, wL, kR, wR, dst + a * fds);
-        }
-    };
-    if (uniform) {
-        // at most four distinct 1D blocks per axis: interior, low boundary, high
-        // boundary, both (one cell along the axis)
-        std::vector<double> tab((size_t)dim * 4 * fds);
-        const double k = kappa[0];
-        for (int a = 0; a < dim; ++a)
-            for (int cls = 0; cls < 4; ++cls) {
-                const bool lo = (cls & 1) && !interior_only, hi = (cls & 2) && !interior_only;
-                factor(a, k, k, lo ? 1.0 : 0.5, k, hi ? 1.0 : 0.5, &tab[((size_t)a * 4 + cls) * fds]);
-            }
-        parallel_for(C.ncell, [&](int64_t cell) {
-            int ci[3] = {(int)(cell % C.n[0]), (int)((cell / C.n[0]) % C.n[1]),
-                         (int)(cell / ((int64_t)C.n[0] * C.n[1]))};
-            for (int a = 0; a < dim; ++a) {
-                const int cls = (ci[a] == 0 ? 1 : 0) | (ci[a] == C.n[a] - 1 ? 2 : 0);
-                std::memcpy(&fd[((size_t)cell * dim + a) * fds], &tab[((size_t)a * 4 + cls) * fds],
-                            sizeof(double) * fds);
-            }
-        });
-    } else {
-        parallel_for(C.ncell, [&](int64_t cell) { cell_factors(cell, &fd[(size_t)cell * dim * fds]); });
-    }
+    return DGMG_OK;
 }
 
 template <typename T>
@@ -404,29 +341,13 @@ std::vector<T> convert(const std::vector<double> &v) {
     return std::vector<T>(v.begin(), v.end());
 }
 
-// 1 / (lambda_x[i] + lambda_y[j] (+ lambda_z[k])) for every node of every cell,
-// from the fast-diagonalisation factors (the FP64 smoother multiplies by it
-// instead of dividing: FP64 division is a multi-instruction sequence on the
-// FP64 pipe, which bounds that kernel; the table costs one extra read per DoF).
-static void inverse_eigen_sums(const dgmg_ctx &C, const DGSpace &S, const std::vector<double> &fd,
-                               std::vector<double> &linv) {
-    const int q = S.q, dim = C.dim, fds = q * q + q;
-    linv.assign((size_t)S.ndof, 0.0);
-    parallel_for(C.ncell, [&](int64_t cell) {
-        const double *lam0 = &fd[((size_t)cell * dim + 0) * fds + q * q];
-        const double *lam1 = &fd[((size_t)cell * dim + 1) * fds + q * q];
-        const double *lam2 = dim == 3 ? &fd[((size_t)cell * dim + 2) * fds + q * q] : nullptr;
-        double *out = &linv[(size_t)cell * S.nloc];
-        for (int64_t node = 0; node < S.nloc; ++node) {
-            const int i = (int)(node % q), j = (int)((node / q) % q), k = (int)(node / (q * q));
-            out[node] = 1.0 / (lam0[i] + lam1[j] + (lam2 ? lam2[k] : 0.0));
-        }
-    });
-}
-
+// One DG level in precision T: constants, kappa (uploaded, or shared with the
+// finest level), the per-cell factors computed on the device from the FP64
+// kappa of the finest level (C.d64.kappa, uploaded first), the FP64 table of
+// inverse eigenvalue sums, traces and corner sums.
 template <typename T>
-int setup_dg(dgmg_ctx &C, const DGSpace &S, DGDev<T> &D, const std::vector<double> &kappa,
-             const std::vector<double> &fd, bool smoother = true, const T *shared_kappa = nullptr) {
+int setup_dg(dgmg_ctx &C, const DGSpace &S, DGDev<T> &D, const std::vector<double> &kappa, bool smoother = true,
+             const T *shared_kappa = nullptr) {
     fill_const(C, S, D.c);
     if (shared_kappa)
         D.kappa = const_cast<T *>(shared_kappa);
@@ -439,11 +360,14 @@ int setup_dg(dgmg_ctx &C, const DGSpace &S, DGDev<T> &D, const std::vector<doubl
         RC(C.alloc(&D.corners, C.ncell * (1 << C.dim)));
         return DGMG_OK;
     }
-    RC(C.upload(&D.fd, convert<T>(fd)));
+    FDInput in;
+    RC(fd_input(C, S, in));
+    RC(C.alloc(&D.fd, (size_t)C.ncell * C.dim * (S.q * S.q + S.q)));
+    LC(launch_fd_factors<T>(in, C.d64.kappa, C.ncell, D.fd, C.setup_stream));
     if (sizeof(T) == sizeof(double)) {
-        std::vector<double> linv;
-        inverse_eigen_sums(C, S, fd, linv);
-        RC(C.upload(&D.linv, convert<T>(linv)));
+        RC(C.alloc(&D.linv, (size_t)S.ndof));
+        LC(launch_inverse_eigen_sums(C.dim, S.q, C.ncell, reinterpret_cast<const double *>(D.fd),
+                                     reinterpret_cast<double *>(D.linv), C.setup_stream));
     }
     RC(C.alloc(&D.tr[0], trn));
     RC(C.alloc(&D.tr[1], trn));
@@ -475,8 +399,6 @@ int setup_dg_levels(dgmg_ctx &C, const std::vector<double> &kap) {
     if (mixed) C.lvl32.resize(L);
     for (int l = 1; l < L; ++l) {
         const DGSpace &S = C.dgs[l], &F = C.dgs[l - 1];
-        std::vector<double> fd;
-        fast_diag_factors(C, S, kap, fd);
         // I[i][j] = l_j(x_i): this level's basis at the finer level's nodes
         std::vector<double> I((size_t)F.q * S.q), val(S.q);
         for (int i = 0; i < F.q; ++i) {
@@ -485,7 +407,7 @@ int setup_dg_levels(dgmg_ctx &C, const std::vector<double> &kap) {
         }
         auto level = [&](auto &lv, auto *kappa_dev) -> int {
             using T = typename std::remove_pointer<decltype(kappa_dev)>::type;
-            RC(setup_dg<T>(C, S, lv.D, kap, fd, true, kappa_dev));
+            RC(setup_dg<T>(C, S, lv.D, kap, true, kappa_dev));
             RC(C.alloc(&lv.z, S.ndof));
             RC(C.alloc(&lv.b, S.ndof));
             RC(C.alloc(&lv.r, S.ndof));
@@ -1045,16 +967,13 @@ int create_ctx(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_opt
     RC(coarse_inverse(*C));
     trace.mark("coarse inverse");
 
-    std::vector<double> fd;
     const DGSpace S0 = finest_space(*C);
-    fast_diag_factors(*C, S0, kap, fd);
-    trace.mark("fast-diag");
-    RC(setup_dg<double>(*C, S0, C->d64, kap, fd, !(flags & CREATE_NO_FP64_SMOOTHER)));
-    trace.mark("dg upload");
+    RC(setup_dg<double>(*C, S0, C->d64, kap, !(flags & CREATE_NO_FP64_SMOOTHER)));
+    trace.mark("dg fp64 (factors on the device)");
     if (!(flags & CREATE_NO_FP64_Q1)) RC(setup_cg<double>(*C, C->cg64));
     trace.mark("cg upload");
     if (o.precision == DGMG_MIXED_FP32) {
-        RC(setup_dg<float>(*C, S0, C->d32, kap, fd));
+        RC(setup_dg<float>(*C, S0, C->d32, kap));
         RC(setup_cg<float>(*C, C->cg32));
         RC(C->alloc(&C->r32, C->ndof));
         RC(C->alloc(&C->z32, C->ndof));

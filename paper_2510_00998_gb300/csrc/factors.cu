@@ -1,0 +1,165 @@
+// Per-cell fast-diagonalisation factors of the exact diagonal blocks, computed
+// on the device at set-up: the GPU form of the paper's independent per-cell
+// "matrix inversion" tasks (Technique 6), one thread per (cell, axis).
+//
+// For axis a of cell K the 1D block is
+//   Kt_a = kappa_K K_a + low face  kF_L (w_L (e0 d0^T + d0 e0^T) + gamma e0 e0^T)
+//                      + high face kF_R (-w_R (ep dp^T + dp ep^T) + gamma ep ep^T)
+// (kF the harmonic mean of kappa and w = 1/2 inside, kF = kappa_K and w = 1 on
+// the boundary; Technique 4: the interior values for every cell), and the
+// factors solve Kt_a S = M_a S Lambda with S^T M_a S = I: with L L^T = M_a,
+// C = L^-1 Kt_a L^-T = V Lambda V^T by cyclic Jacobi rotations, S = L^-T V.
+// Everything is computed in FP64; the output is FP64 or rounded to FP32.
+#include "internal.h"
+
+namespace dgmg {
+
+namespace {
+
+// Eigen-decomposition of the symmetric n x n matrix A (overwritten) by cyclic
+// Jacobi rotations, row by row (Jacobi 1846): V = eigenvectors (columns),
+// lam = eigenvalues. Stops when the off-diagonal part is at rounding level or a
+// sweep rotates nothing; at most 64 sweeps.
+__device__ void jacobi_eig_dev(int n, double *A, double *V, double *lam) {
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) V[i * n + j] = i == j ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 64; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                const double v = A[i * n + j] * A[i * n + j];
+                tot += v;
+                if (i != j) off += v;
+            }
+        if (off <= 1e-30 * tot) break;
+        int rotations = 0;
+        for (int p = 0; p < n - 1; ++p)
+            for (int r = p + 1; r < n; ++r) {
+                const double apr = A[p * n + r];
+                if (fabs(apr) <= 1e-18 * sqrt(fabs(A[p * n + p] * A[r * n + r])) || fabs(apr) < 1e-300) continue;
+                ++rotations;
+                // the rotation that zeroes A[p][r]: tan t = sign(theta) / (|theta| + sqrt(theta^2 + 1))
+                const double theta = (A[r * n + r] - A[p * n + p]) / (2.0 * apr);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; ++k) {
+                    const double akp = A[k * n + p], akr = A[k * n + r];
+                    A[k * n + p] = c * akp - s * akr;
+                    A[k * n + r] = s * akp + c * akr;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double apk = A[p * n + k], ark = A[r * n + k];
+                    A[p * n + k] = c * apk - s * ark;
+                    A[r * n + k] = s * apk + c * ark;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double vkp = V[k * n + p], vkr = V[k * n + r];
+                    V[k * n + p] = c * vkp - s * vkr;
+                    V[k * n + r] = s * vkp + c * vkr;
+                }
+            }
+        if (rotations == 0) break;
+    }
+    for (int i = 0; i < n; ++i) lam[i] = A[i * n + i];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_fd_factors(const __grid_constant__ FDInput in,
+                                                    const double *__restrict__ kappa, int64_t ncell,
+                                                    T *__restrict__ fd) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= ncell * in.dim) return;
+    const int64_t cell = idx / in.dim;
+    const int a = (int)(idx - cell * in.dim), q = in.q;
+    const int ci[3] = {(int)(cell % in.n[0]), (int)((cell / in.n[0]) % in.n[1]),
+                       (int)(cell / ((int64_t)in.n[0] * in.n[1]))};
+    const int64_t stride = a == 0 ? 1 : (a == 1 ? (int64_t)in.n[0] : (int64_t)in.n[0] * in.n[1]);
+    const double kK = kappa[cell];
+    double kL = kK, wL = 0.5, kR = kK, wR = 0.5;
+    if (!in.interior_only) {
+        if (ci[a] > 0) {
+            const double kN = kappa[cell - stride];
+            kL = 2.0 * kK * kN / (kK + kN);
+        } else {
+            wL = 1.0;
+        }
+        if (ci[a] < in.n[a] - 1) {
+            const double kN = kappa[cell + stride];
+            kR = 2.0 * kK * kN / (kK + kN);
+        } else {
+            wR = 1.0;
+        }
+    }
+    const double *K = in.Kh[a], *L = in.Linv[a], *d0 = in.d0[a], *dp = in.dp[a];
+    const double g = in.gam[a];
+    double Kt[QMAX * QMAX], Tm[QMAX * QMAX], C[QMAX * QMAX], V[QMAX * QMAX], lam[QMAX];
+    for (int i = 0; i < q; ++i)
+        for (int j = 0; j < q; ++j) {
+            const double e0i = in.e0[i], e0j = in.e0[j], epi = in.ep[i], epj = in.ep[j];
+            Kt[i * q + j] = kK * K[i * q + j] + kL * (wL * (e0i * d0[j] + d0[i] * e0j) + g * e0i * e0j) +
+                            kR * (-wR * (epi * dp[j] + dp[i] * epj) + g * epi * epj);
+        }
+    // C = L^-1 Kt L^-T, symmetrised
+    for (int i = 0; i < q; ++i)
+        for (int j = 0; j < q; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < q; ++k) s += L[i * q + k] * Kt[k * q + j];
+            Tm[i * q + j] = s;
+        }
+    for (int i = 0; i < q; ++i)
+        for (int j = 0; j < q; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < q; ++k) s += Tm[i * q + k] * L[j * q + k];
+            C[i * q + j] = s;
+        }
+    for (int i = 0; i < q; ++i)
+        for (int j = i + 1; j < q; ++j) C[i * q + j] = C[j * q + i] = 0.5 * (C[i * q + j] + C[j * q + i]);
+    jacobi_eig_dev(q, C, V, lam);
+    // S = L^-T V: S[m][i] = sum_k L[k][m] V[k][i]; stored [S (q x q) | lambda (q)]
+    T *out = fd + idx * (q * q + q);
+    for (int m = 0; m < q; ++m)
+        for (int i = 0; i < q; ++i) {
+            double s = 0.0;
+            for (int k = m; k < q; ++k) s += L[k * q + m] * V[k * q + i];   // L^-1 is lower triangular
+            out[m * q + i] = (T)s;
+        }
+    for (int i = 0; i < q; ++i) out[q * q + i] = (T)lam[i];
+}
+
+// linv[cell][node] = 1 / (lambda_x[i] + lambda_y[j] (+ lambda_z[k])) from the factors
+__global__ void k_inverse_eigen_sums(int dim, int q, int64_t ncell, const double *__restrict__ fd,
+                                     double *__restrict__ linv) {
+    const int64_t nloc = dim == 3 ? (int64_t)q * q * q : (int64_t)q * q;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= ncell * nloc) return;
+    const int64_t cell = idx / nloc;
+    const int node = (int)(idx - cell * nloc), fds = q * q + q;
+    const double *f = fd + cell * dim * fds + q * q;
+    double s = f[node % q] + f[fds + (node / q) % q];
+    if (dim == 3) s += f[2 * fds + node / (q * q)];
+    linv[idx] = 1.0 / s;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_fd_factors(const FDInput &in, const double *kappa, int64_t ncell, T *fd, cudaStream_t s) {
+    const int64_t n = ncell * in.dim;
+    if (n == 0) return cudaSuccess;
+    count_launches(1);
+    k_fd_factors<T><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(in, kappa, ncell, fd);
+    return cudaGetLastError();
+}
+template cudaError_t launch_fd_factors<double>(const FDInput &, const double *, int64_t, double *, cudaStream_t);
+template cudaError_t launch_fd_factors<float>(const FDInput &, const double *, int64_t, float *, cudaStream_t);
+
+cudaError_t launch_inverse_eigen_sums(int dim, int q, int64_t ncell, const double *fd, double *linv,
+                                      cudaStream_t s) {
+    const int64_t n = ncell * (dim == 3 ? (int64_t)q * q * q : (int64_t)q * q);
+    if (n == 0) return cudaSuccess;
+    count_launches(1);
+    k_inverse_eigen_sums<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dim, q, ncell, fd, linv);
+    return cudaGetLastError();
+}
+
+}  // namespace dgmg

@@ -49,11 +49,27 @@ void gauss_legendre(int m, std::vector<double> &x, std::vector<double> &w);
 // values and derivatives of the Lagrange basis on `nodes` at x
 void lagrange_at(const std::vector<double> &nodes, double x, double *val, double *der);
 
-// Symmetric generalized eigenproblem Kt S = M S diag(lam), S^T M S = I, by
-// Cholesky of M and cyclic Jacobi rotations. Kt, M: q x q row-major.
-void gen_eig_sym(int q, const double *Kt, const double *Lchol_inv, double *S, double *lam);
 // lower Cholesky factor inverse of the SPD q x q matrix M (row-major)
 bool cholesky_inverse_lower(int q, const double *M, double *Linv);
+
+// Input of the per-cell fast-diagonalisation factor kernel for one DG space
+// (the h-scaled 1D data per axis; see factors.cu).
+struct FDInput {
+    int dim, q, interior_only;
+    int n[3];
+    double Kh[3][QMAX * QMAX];      // stiffness
+    double Linv[3][QMAX * QMAX];    // inverse of the lower Cholesky factor of the mass
+    double d0[3][QMAX], dp[3][QMAX];
+    double e0[QMAX], ep[QMAX];
+    double gam[3];
+};
+// fd[cell][axis] = [S (q x q) | lambda (q)] for every cell (FP64 arithmetic,
+// output in T); kappa: per-cell FP64 on the device
+template <typename T>
+cudaError_t launch_fd_factors(const FDInput &in, const double *kappa, int64_t ncell, T *fd, cudaStream_t s);
+// linv[cell][node] = 1 / (sum of the cell's eigenvalues at the node)
+cudaError_t launch_inverse_eigen_sums(int dim, int q, int64_t ncell, const double *fd, double *linv,
+                                      cudaStream_t s);
 
 // ------------------------------------------------------------ kernels API
 // Constant data of one DG level, passed to kernels by value.

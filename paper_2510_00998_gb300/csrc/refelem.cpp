@@ -151,77 +151,4 @@ bool cholesky_inverse_lower(int q, const double *M, double *Linv) {
     return true;
 }
 
-// Eigen-decomposition of a symmetric matrix by cyclic Jacobi rotations
-// (Jacobi 1846; the classical cyclic-by-row variant). A is overwritten.
-static void jacobi_eig(int n, double *A, double *V, double *lam) {
-    for (int i = 0; i < n; ++i)
-        for (int j = 0; j < n; ++j) V[i * n + j] = (i == j) ? 1.0 : 0.0;
-    for (int sweep = 0; sweep < 64; ++sweep) {
-        double off = 0.0, tot = 0.0;
-        for (int i = 0; i < n; ++i)
-            for (int j = 0; j < n; ++j) {
-                tot += A[i * n + j] * A[i * n + j];
-                if (i != j) off += A[i * n + j] * A[i * n + j];
-            }
-        // converged once the off-diagonal part is at the rounding level
-        if (off <= 1e-30 * tot) break;
-        int rotations = 0;
-        for (int p = 0; p < n - 1; ++p)
-            for (int r = p + 1; r < n; ++r) {
-                const double apr = A[p * n + r];
-                // an element negligible against its diagonal pair is left alone
-                if (std::fabs(apr) <= 1e-18 * std::sqrt(std::fabs(A[p * n + p] * A[r * n + r])) ||
-                    std::fabs(apr) < 1e-300)
-                    continue;
-                ++rotations;
-                const double theta = (A[r * n + r] - A[p * n + p]) / (2.0 * apr);
-                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
-                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
-                for (int k = 0; k < n; ++k) {          // A <- A G (columns p, r)
-                    const double akp = A[k * n + p], akr = A[k * n + r];
-                    A[k * n + p] = c * akp - s * akr;
-                    A[k * n + r] = s * akp + c * akr;
-                }
-                for (int k = 0; k < n; ++k) {          // A <- G^T A (rows p, r)
-                    const double apk = A[p * n + k], ark = A[r * n + k];
-                    A[p * n + k] = c * apk - s * ark;
-                    A[r * n + k] = s * apk + c * ark;
-                }
-                for (int k = 0; k < n; ++k) {          // V <- V G
-                    const double vkp = V[k * n + p], vkr = V[k * n + r];
-                    V[k * n + p] = c * vkp - s * vkr;
-                    V[k * n + r] = s * vkp + c * vkr;
-                }
-            }
-        if (rotations == 0) break;
-    }
-    for (int i = 0; i < n; ++i) lam[i] = A[i * n + i];
-}
-
-void gen_eig_sym(int q, const double *Kt, const double *Linv, double *S, double *lam) {
-    // C = Linv Kt Linv^T, C = V diag(lam) V^T, S = Linv^T V
-    double T[QMAX * QMAX], C[QMAX * QMAX], V[QMAX * QMAX];
-    for (int i = 0; i < q; ++i)
-        for (int j = 0; j < q; ++j) {
-            double s = 0.0;
-            for (int k = 0; k < q; ++k) s += Linv[i * q + k] * Kt[k * q + j];
-            T[i * q + j] = s;
-        }
-    for (int i = 0; i < q; ++i)
-        for (int j = 0; j < q; ++j) {
-            double s = 0.0;
-            for (int k = 0; k < q; ++k) s += T[i * q + k] * Linv[j * q + k];
-            C[i * q + j] = s;
-        }
-    for (int i = 0; i < q; ++i)            // exact symmetry before the rotations
-        for (int j = i + 1; j < q; ++j) C[i * q + j] = C[j * q + i] = 0.5 * (C[i * q + j] + C[j * q + i]);
-    jacobi_eig(q, C, V, lam);
-    for (int m = 0; m < q; ++m)
-        for (int i = 0; i < q; ++i) {
-            double s = 0.0;
-            for (int k = 0; k < q; ++k) s += Linv[k * q + m] * V[k * q + i];
-            S[m * q + i] = s;
-        }
-}
-
 }  // namespace dgmg
