@@ -200,6 +200,21 @@ int dgmg_info(const dgmg_ctx *ctx, dgmg_info_t *info);
 int dgmg_gll_nodes(const dgmg_ctx *ctx, double *nodes_host);
 
 /*
+ * Replace ctx's coefficient field by kappa_host (HOST array of ncell doubles,
+ * each positive and finite, layout as for dgmg_create) without rebuilding the
+ * hierarchy: the Q1 operators P^T A P, their Galerkin coarsenings and the
+ * coarsest inverse are recomputed on the host into the existing device
+ * buffers, and the per-cell fast-diagonalisation factors of every DG level
+ * on the device (the exact diagonal blocks A_KK of Sec. 4.1 for the new
+ * kappa: the paper's independent per-cell inversion tasks, Technique 6, for
+ * coefficients that change between solves). No allocation; captured solver
+ * graphs stay valid. Blocking: returns when the device data are updated. No
+ * work of ctx may be in flight on other streams. DGMG_EINVAL for an invalid
+ * kappa (ctx unchanged).
+ */
+int dgmg_update_kappa(dgmg_ctx *ctx, const double *kappa_host);
+
+/*
  * y = A u (the SIPG operator, Eq. matrix_form_IP), FP64, DG layout. Runs the
  * warm-up projection (Alg. 4 preamble) and the cell equation of Alg. 2 stage 3
  * on the stored projections. u and y must not overlap.

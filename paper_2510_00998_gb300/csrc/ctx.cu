@@ -341,6 +341,19 @@ std::vector<T> convert(const std::vector<double> &v) {
     return std::vector<T>(v.begin(), v.end());
 }
 
+// The per-cell factors (and, FP64, the table of inverse eigenvalue sums) of
+// level D from the FP64 kappa of the finest level, on the set-up stream.
+template <typename T>
+int compute_factors(dgmg_ctx &C, const DGSpace &S, DGDev<T> &D) {
+    FDInput in;
+    RC(fd_input(C, S, in));
+    LC(launch_fd_factors<T>(in, C.d64.kappa, C.ncell, D.fd, C.setup_stream));
+    if (sizeof(T) == sizeof(double))
+        LC(launch_inverse_eigen_sums(C.dim, S.q, C.ncell, reinterpret_cast<const double *>(D.fd),
+                                     reinterpret_cast<double *>(D.linv), C.setup_stream));
+    return DGMG_OK;
+}
+
 // One DG level in precision T: constants, kappa (uploaded, or shared with the
 // finest level), the per-cell factors computed on the device from the FP64
 // kappa of the finest level (C.d64.kappa, uploaded first), the FP64 table of
@@ -360,15 +373,9 @@ int setup_dg(dgmg_ctx &C, const DGSpace &S, DGDev<T> &D, const std::vector<doubl
         RC(C.alloc(&D.corners, C.ncell * (1 << C.dim)));
         return DGMG_OK;
     }
-    FDInput in;
-    RC(fd_input(C, S, in));
     RC(C.alloc(&D.fd, (size_t)C.ncell * C.dim * (S.q * S.q + S.q)));
-    LC(launch_fd_factors<T>(in, C.d64.kappa, C.ncell, D.fd, C.setup_stream));
-    if (sizeof(T) == sizeof(double)) {
-        RC(C.alloc(&D.linv, (size_t)S.ndof));
-        LC(launch_inverse_eigen_sums(C.dim, S.q, C.ncell, reinterpret_cast<const double *>(D.fd),
-                                     reinterpret_cast<double *>(D.linv), C.setup_stream));
-    }
+    if (sizeof(T) == sizeof(double)) RC(C.alloc(&D.linv, (size_t)S.ndof));
+    RC(compute_factors<T>(C, S, D));
     RC(C.alloc(&D.tr[0], trn));
     RC(C.alloc(&D.tr[1], trn));
     RC(C.alloc(&D.corners, C.ncell * (1 << C.dim)));
@@ -479,8 +486,31 @@ int setup_cg(dgmg_ctx &C, std::vector<CGDev<T>> &out) {
     return DGMG_OK;
 }
 
+// The Q1 levels for kappa: the Galerkin level-0 operator P^T A P and the
+// coarsenings by factor f while some axis can be coarsened.
+static void build_q1_levels(int dim, const int *n, int f, const std::vector<double> &kap,
+                            std::vector<CGLevelHost> &lv) {
+    lv.clear();
+    lv.emplace_back();
+    build_level0(dim, n, kap, lv[0]);
+    for (;;) {
+        CGLevelHost &F = lv.back();
+        bool any = false;
+        for (int a = 0; a < dim; ++a) any = any || can_coarsen(F.n[a], f);
+        if (!any) break;
+        for (int a = 0; a < dim; ++a) {
+            int nc = 0;
+            axis_tables(F.n[a], f, F, a, nc);
+            F.mc[a] = nc;
+        }
+        CGLevelHost Cl;
+        build_coarse(dim, F, Cl);
+        lv.push_back(std::move(Cl));
+    }
+}
+
 // dense inverse of the coarsest operator via Cholesky (FP64, host)
-int coarse_inverse(dgmg_ctx &C) {
+int coarse_inverse(dgmg_ctx &C, std::vector<double> &inv) {
     const CGLevelHost &L = C.lv.back();
     const int64_t nc = L.nv;
     if (nc > 4096) return fail(DGMG_EINVAL, "coarsest level has more than 4096 unknowns");
@@ -516,7 +546,8 @@ int coarse_inverse(dgmg_ctx &C) {
         }
     }
     // inverse column by column: solve L y = e_c, L^T x = y
-    std::vector<double> inv((size_t)nc * nc, 0.0), y(nc);
+    inv.assign((size_t)nc * nc, 0.0);
+    std::vector<double> y(nc);
     for (int64_t c = 0; c < nc; ++c) {
         for (int64_t i = 0; i < nc; ++i) {
             double s = (i == c) ? 1.0 : 0.0;
@@ -529,7 +560,7 @@ int coarse_inverse(dgmg_ctx &C) {
             inv[i * nc + c] = s / Lc[i * nc + i];
         }
     }
-    return C.upload(&C.coarse_inv, inv);
+    return DGMG_OK;
 }
 
 // ------------------------------------------------------------ V-cycle
@@ -946,25 +977,13 @@ int create_ctx(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_opt
     trace.mark("refelem");
 
     // Q1 hierarchy
-    C->lv.emplace_back();
-    build_level0(C->dim, C->n, kap, C->lv[0]);
-    const int f = o.coarsening;
-    for (;;) {
-        CGLevelHost &F = C->lv.back();
-        bool any = false;
-        for (int a = 0; a < C->dim; ++a) any = any || can_coarsen(F.n[a], f);
-        if (!any) break;
-        for (int a = 0; a < C->dim; ++a) {
-            int nc = 0;
-            axis_tables(F.n[a], f, F, a, nc);
-            F.mc[a] = nc;
-        }
-        CGLevelHost Cl;
-        build_coarse(C->dim, F, Cl);
-        C->lv.push_back(std::move(Cl));
-    }
+    build_q1_levels(C->dim, C->n, o.coarsening, kap, C->lv);
     trace.mark("q1 levels");
-    RC(coarse_inverse(*C));
+    {
+        std::vector<double> inv;
+        RC(coarse_inverse(*C, inv));
+        RC(C->upload(&C->coarse_inv, inv));
+    }
     trace.mark("coarse inverse");
 
     const DGSpace S0 = finest_space(*C);
@@ -1069,6 +1088,54 @@ int dgmg_info(const dgmg_ctx *C, dgmg_info_t *info) {
     info->dg_levels = (int)C->dgs.size();
     const bool mixed = C->opts.precision == DGMG_MIXED_FP32;
     for (int k = 0; k < 6; ++k) info->tiles[k] = (k < 3 || mixed) ? C->tile[k / 3][k % 3] : 0;
+    return DGMG_OK;
+}
+
+int dgmg_update_kappa(dgmg_ctx *C, const double *kappa) {
+    using namespace dgmg;
+    RC(check_ctx(C));
+    if (!kappa) return fail(DGMG_EINVAL, "kappa is NULL");
+    std::vector<double> kap(kappa, kappa + C->ncell);
+    for (int64_t i = 0; i < C->ncell; ++i)
+        if (!(kap[i] > 0.0) || !std::isfinite(kap[i]))
+            return fail(DGMG_EINVAL, "kappa must be positive and finite (cell " + std::to_string(i) + ")");
+    // host: the Q1 operators of the new kappa (same shapes) and the coarsest inverse
+    std::vector<CGLevelHost> lv;
+    build_q1_levels(C->dim, C->n, C->opts.coarsening, kap, lv);
+    if (lv.size() != C->lv.size()) return fail(DGMG_EINVAL, "Q1 hierarchy changed shape");
+    C->lv = std::move(lv);
+    std::vector<double> inv;
+    RC(coarse_inverse(*C, inv));
+    cudaStream_t s = C->setup_stream;
+    // everything in flight on the context's own stream must see the old data
+    DG_CUDA(cudaStreamSynchronize(s));
+    const bool mixed = C->opts.precision == DGMG_MIXED_FP32;
+    const std::vector<float> kap32 = convert<float>(kap);
+    DG_CUDA(cudaMemcpyAsync(C->d64.kappa, kap.data(), sizeof(double) * C->ncell, cudaMemcpyHostToDevice, s));
+    if (mixed)
+        DG_CUDA(cudaMemcpyAsync(C->d32.kappa, kap32.data(), sizeof(float) * C->ncell, cudaMemcpyHostToDevice, s));
+    DG_CUDA(cudaMemcpyAsync(C->coarse_inv, inv.data(), sizeof(double) * inv.size(), cudaMemcpyHostToDevice, s));
+    std::vector<std::vector<float>> st32(C->lv.size());
+    for (size_t l = 0; l < C->lv.size(); ++l) {
+        const std::vector<double> &st = C->lv[l].st;
+        if (l < C->cg64.size())
+            DG_CUDA(cudaMemcpyAsync(C->cg64[l].st, st.data(), sizeof(double) * st.size(), cudaMemcpyHostToDevice, s));
+        if (mixed) {
+            st32[l] = convert<float>(st);
+            DG_CUDA(cudaMemcpyAsync(C->cg32[l].st, st32[l].data(), sizeof(float) * st.size(),
+                                    cudaMemcpyHostToDevice, s));
+        }
+    }
+    // device: the per-cell factors of every DG level that has them
+    for (size_t l = 0; l < C->dgs.size(); ++l) {
+        DGDev<double> &D64 = l == 0 ? C->d64 : C->lvl64[l].D;
+        if (D64.fd) RC(compute_factors<double>(*C, C->dgs[l], D64));
+        if (mixed) {
+            DGDev<float> &D32 = l == 0 ? C->d32 : C->lvl32[l].D;
+            if (D32.fd) RC(compute_factors<float>(*C, C->dgs[l], D32));
+        }
+    }
+    DG_CUDA(cudaStreamSynchronize(s));
     return DGMG_OK;
 }
 

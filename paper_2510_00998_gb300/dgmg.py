@@ -95,6 +95,7 @@ _SIGS = {
     "dgmg_destroy": (_I, [_P]),
     "dgmg_info": (_I, [_P, ctypes.POINTER(Info)]),
     "dgmg_gll_nodes": (_I, [_P, _P]),
+    "dgmg_update_kappa": (_I, [_P, _P]),
     "dgmg_apply": (_I, [_P, _P, _P, _P]),
     "dgmg_residual": (_I, [_P, _P, _P, _P, _P]),
     "dgmg_smooth": (_I, [_P, _P, _P, _I, _P]),
@@ -370,6 +371,15 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def update_kappa(self, kappa):
+        """New per-cell coefficients for the same mesh and degree (dgmg_update_kappa)."""
+        import numpy as np
+        k = np.ascontiguousarray(np.asarray(kappa, dtype=np.float64).reshape(-1))
+        if k.size != int(self.info.ncell):
+            raise ValueError("kappa needs one value per cell")
+        _check(self.lib.dgmg_update_kappa(self.h, k.ctypes.data_as(ctypes.c_void_p)))
+        self._kappa_keep = k
 
     def gll_nodes(self):
         import numpy as np

@@ -365,3 +365,30 @@ def test_autotuned_tiles(dgmg, n, p, prec):
     x_ref, _, _ = hpmg.pcg(hpmg.Hierarchy(mesh, kap), b, rtol=1e-13)
     for x in xs:
         assert np.linalg.norm(x - x_ref) <= 1e-9 * np.linalg.norm(x_ref)
+
+
+@pytest.mark.parametrize("n,p,prec,gradual", [((8, 7, 6), 3, 0, 0), ((9, 8, 7), 4, 1, 0), ((12, 10), 4, 0, 1),
+                                              ((6, 6, 5), 3, 1, 1)])
+def test_update_kappa_equals_fresh_context(dgmg, n, p, prec, gradual):
+    """dgmg_update_kappa (factors recomputed on the device, Q1 operators on the
+    host, no allocation) gives the context of the new kappa: the V-cycle equals a
+    fresh context's to rounding, the solve meets the oracle bound."""
+    kap1, kap2 = _kappa(n, "lognormal", 31), _kappa(n, "lognormal", 32)
+    mesh = sipg.Mesh(n, p)
+    ctx = dgmg.Context(n, p, kap1, precision=prec, p_coarsening=gradual)
+    ctx.update_kappa(kap2)
+    fresh = dgmg.Context(n, p, kap2, precision=prec, p_coarsening=gradual)
+    assert ctx.info.device_bytes == fresh.info.device_bytes
+    r = np.random.default_rng(33).normal(size=mesh.ndof)
+    e1, e2 = (torch.empty(mesh.ndof, dtype=torch.float64, device=DEV) for _ in range(2))
+    ctx.vcycle(_t(r), e1)
+    fresh.vcycle(_t(r), e2)
+    assert _rel(_np(e1), _np(e2)) <= (1e-13 if prec == 0 else 1e-6)
+    b = np.random.default_rng(34).normal(size=mesh.ndof)
+    x = torch.zeros(mesh.ndof, dtype=torch.float64, device=DEV)
+    st, _ = ctx.solve(_t(b), x)
+    assert st.rel_residual <= 1e-10
+    x_ref, _, _ = hpmg.pcg(hpmg.Hierarchy(mesh, kap2), b, rtol=1e-13)
+    assert np.linalg.norm(_np(x) - x_ref) <= 1e-9 * np.linalg.norm(x_ref)
+    with pytest.raises(dgmg.DGMGError):
+        ctx.update_kappa(-kap2)
