@@ -39,7 +39,7 @@ SAMPLE_STEPS = 60
 FP64_PEAK_TFLOPS = 1.25          # nominal GB300 dense FP64 (no FP64 entry in the measured peaks)
 # DRAM bytes (read + write) of one launch of k_smooth_cells<double,4> on this
 # workload, from one ncu capture (profiles/k_smooth_cells_fp64_32cube_p3.md)
-SMOOTH_TRAFFIC_BYTES = 115_337_472 + 12_144_640
+SMOOTH_TRAFFIC_BYTES = 115_310_336 + 10_941_184
 
 
 def parse():
@@ -82,8 +82,10 @@ def reduce_max_sum(values, world, device):
 # ---------------------------------------------------------------- flop model
 def smooth_flops(n, q):
     """Floating-point operations of one launch of the fused smoothing kernel as
-    implemented (an FMA counts 2, a division 1): facet mass on the two
-    neighbour fields of every interior face side, lifting, S^T / Lambda^-1 / S
+    implemented (an FMA counts 2, a multiplication or division 1): facet mass on
+    the two neighbour fields of every interior face side (each 1D mass in its
+    rank-one form diag(w) - u u^T: per pencil of q values a dot product, q
+    multiplications and q FMAs, 5q operations), lifting, S^T / Lambda^-1 / S
     along every axis, damped update, new traces of every face."""
     d = len(n)
     ncell = 1
@@ -95,7 +97,7 @@ def smooth_flops(n, q):
     for a in range(d):
         other = ncell // n[a]
         sides += 2 * (n[a] - 1) * other
-    facet_mass = sides * 2 * (d - 1) * nf * q * 2
+    facet_mass = sides * 2 * (d - 1) * 5 * nf
     lift = sides * nf * (q * 2 + 4)
     per_cell = 2 * d * nl * q * 2 + nl * 3 + nl * 3 + d * nf * 2 * q * 2
     return facet_mass + lift + ncell * per_cell

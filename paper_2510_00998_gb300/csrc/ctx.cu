@@ -302,6 +302,23 @@ void fill_const(const dgmg_ctx &C, const DGSpace &S, DGConst<T> &c) {
     }
     c.gl = S.re.basis == DGMG_BASIS_GL ? 1 : 0;
     c.omega = (T)C.opts.omega_dg;
+    // M_ref = diag(w) + sigma l l^T: w the row sums (the lumped quadrature
+    // weights), l_i = 1 / prod_{m != i} (x_i - x_m) the leading coefficient of
+    // the basis function l_i, sigma from the first entry (sigma <= 0)
+    std::vector<double> w(q, 0.0), lc(q, 1.0);
+    for (int i = 0; i < q; ++i) {
+        for (int j = 0; j < q; ++j) w[i] += S.re.M[i * q + j];
+        for (int m = 0; m < q; ++m)
+            if (m != i) lc[i] /= S.re.nodes[i] - S.re.nodes[m];
+    }
+    const double sigma = std::min(0.0, (S.re.M[0] - w[0]) / (lc[0] * lc[0]));
+    for (int a = 0; a < C.dim; ++a) {
+        const double h = 1.0 / C.n[a];
+        for (int i = 0; i < q; ++i) {
+            c.mw[a][i] = (T)(w[i] * h / 2.0);
+            c.mu[a][i] = (T)(std::sqrt(-sigma * h / 2.0) * lc[i]);
+        }
+    }
 }
 
 // Input of the device kernel that computes the per-cell fast-diagonalisation

@@ -89,6 +89,12 @@ struct DGConst {
     // the end nodes and the kernels index those nodes directly
     int gl;
     T v0[QMAX], vp[QMAX];
+    // the 1D mass of axis a as diag(mw[a]) - mu[a] mu[a]^T: with GLL nodes the
+    // exact mass is the lumped GLL-quadrature mass plus a rank-one term (the rule
+    // is exact to degree 2p - 1; for the degree-2p products l_i l_j its error
+    // is a multiple of the product of their leading coefficients); with GL nodes
+    // the mass is diagonal and mu = 0
+    T mw[3][QMAX], mu[3][QMAX];
 };
 
 // Q1 level description for the CG kernels.

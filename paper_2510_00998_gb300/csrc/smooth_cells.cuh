@@ -223,13 +223,14 @@ __device__ __forceinline__ void pass_x(const T *A, T *R) {
 // r -= N u_nb for the face normal to the current x axis on side `side`, whose
 // neighbour fields fld = [g | h] (q^2 each) are indexed sa * a + sb * b at the
 // current tangential position (a, b) = (y, z). With G, H the fields after the
-// tangential mass M_a (x) M_b (Ma, Mb: the 1D masses of the original axes now
-// at y and z, in shared memory):
+// tangential mass M_a (x) M_b (the 1D masses of the original axes now at y and
+// z, applied in their rank-one form M = diag(w) - u u^T: 3q operations per
+// pencil instead of q^2; wa, ua / wb, ub in shared memory):
 //   low face:  N = kF [e_0 (x) (H/2 - gamma G) - d_0 (x) G/2],
 //   high face: N = kF [e_p (x) (-H/2 - gamma G) + d_p (x) G/2].
 template <typename T, int Q>
-__device__ __forceinline__ void lift_x_face(int side, const T *fld, int sa, int sb, const T *Ma, const T *Mb,
-                                            const T *dv, T gam, T kF, T *R) {
+__device__ __forceinline__ void lift_x_face(int side, const T *fld, int sa, int sb, const T *wa, const T *ua,
+                                            const T *wb, const T *ub, const T *dv, T gam, T kF, T *R) {
     constexpr int NF = Q * Q;
     const T g2 = kF * gam, wv = T(0.5) * kF, sgn = side ? T(-1) : T(1);
     // value field: end layer += kF gamma G; all layers += sgn kF/2 G d
@@ -237,27 +238,27 @@ __device__ __forceinline__ void lift_x_face(int side, const T *fld, int sa, int 
 #pragma unroll
     for (int comp = 0; comp < 2; ++comp) {
         const T *f = fld + comp * NF;
-        T t1[NF];                                      // t1[a + q b] = sum_b' Mb[b][b'] f(a, b')
+        T t1[NF];                                      // t1[a + q b] = (M_b f(a, .))[b]
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
             T col[Q];
+            T s = T(0);
 #pragma unroll
-            for (int bb = 0; bb < Q; ++bb) col[bb] = f[sa * a + sb * bb];
-#pragma unroll
-            for (int b = 0; b < Q; ++b) {
-                T s = T(0);
-#pragma unroll
-                for (int bb = 0; bb < Q; ++bb) s += Mb[b * Q + bb] * col[bb];
-                t1[a + Q * b] = s;
+            for (int bb = 0; bb < Q; ++bb) {
+                col[bb] = f[sa * a + sb * bb];
+                s += ub[bb] * col[bb];
             }
+#pragma unroll
+            for (int b = 0; b < Q; ++b) t1[a + Q * b] = wb[b] * col[b] - ub[b] * s;
         }
 #pragma unroll
-        for (int b = 0; b < Q; ++b)
+        for (int b = 0; b < Q; ++b) {
+            T s = T(0);
+#pragma unroll
+            for (int aa = 0; aa < Q; ++aa) s += ua[aa] * t1[aa + Q * b];
 #pragma unroll
             for (int a = 0; a < Q; ++a) {
-                T v = T(0);
-#pragma unroll
-                for (int aa = 0; aa < Q; ++aa) v += Ma[a * Q + aa] * t1[aa + Q * b];
+                const T v = wa[a] * t1[a + Q * b] - ua[a] * s;
                 T *pen = R + Q * (a + Q * b);              // the pencil along x at (a, b)
                 if (comp == 0) {
                     const T w = sgn * wv * v;
@@ -268,6 +269,7 @@ __device__ __forceinline__ void lift_x_face(int side, const T *fld, int sa, int 
                     if (side) pen[Q - 1] += wv * v; else pen[0] -= wv * v;
                 }
             }
+        }
     }
 }
 
@@ -321,7 +323,7 @@ __device__ __forceinline__ void smooth_cells_body(const DGConst<T> &c, int64_t c
     T *sK = sA + G::OFF_K;
     int *sNb = reinterpret_cast<int *>(sA + G::OFF_NB);
     __shared__ __align__(8) uint64_t bars[4];
-    __shared__ T sM[3][Q * Q];
+    __shared__ T sMw[3][Q], sMu[3][Q];
     const int lane = threadIdx.x;
     const int ncl = (int)min((int64_t)W, c.ncell - cell0);
     const bool full = ncl == W;                          // bulk copies need whole 32-cell blocks
@@ -329,7 +331,10 @@ __device__ __forceinline__ void smooth_cells_body(const DGConst<T> &c, int64_t c
     const int64_t cell = cell0 + lane;
     const bool table = linv != nullptr;
 
-    for (int e = lane; e < 3 * Q * Q; e += W) sM[e / (Q * Q)][e % (Q * Q)] = c.M[e / (Q * Q)][e % (Q * Q)];
+    for (int e = lane; e < 3 * Q; e += W) {
+        sMw[e / Q][e % Q] = c.mw[e / Q][e % Q];
+        sMu[e / Q][e % Q] = c.mu[e / Q][e % Q];
+    }
     if (full && lane == 0) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
@@ -410,7 +415,8 @@ __device__ __forceinline__ void smooth_cells_body(const DGConst<T> &c, int64_t c
                 for (int n = 0; n < Q; ++n) dv[n] = side ? c.dp[p][n] : c.d0[p][n];
                 const T *fld = G::LEAN ? tr_in + (int64_t)sNb[f * W + lane] * TR + (f ^ 1) * 2 * NF
                                        : sB + side * W * 2 * NF + lane * 2 * NF;
-                lift_x_face<T, Q>(side, fld, sa, sb, sM[ta], sM[tb], dv, gam, sK[f * W + lane], R);
+                lift_x_face<T, Q>(side, fld, sa, sb, sMw[ta], sMu[ta], sMw[tb], sMu[tb], dv, gam,
+                                  sK[f * W + lane], R);
             }
             if (!G::LEAN) {
                 __syncwarp();
@@ -592,7 +598,7 @@ __device__ __forceinline__ void residual_cells_body(const DGConst<T> &c, int64_t
     T *sK = sA + G::OFF_K;
     int *sNb = reinterpret_cast<int *>(sA + G::OFF_NB);
     __shared__ __align__(8) uint64_t bars[4];
-    __shared__ T sM[3][Q * Q];
+    __shared__ T sM[3][Q * Q], sMw[3][Q], sMu[3][Q];
     const int lane = threadIdx.x;
     const int ncl = (int)min((int64_t)W, c.ncell - cell0);
     const bool full = ncl == W;
@@ -601,6 +607,10 @@ __device__ __forceinline__ void residual_cells_body(const DGConst<T> &c, int64_t
     const bool has_b = (mode & RES_HAS_B) != 0;
 
     for (int e = lane; e < 3 * Q * Q; e += W) sM[e / (Q * Q)][e % (Q * Q)] = c.M[e / (Q * Q)][e % (Q * Q)];
+    for (int e = lane; e < 3 * Q; e += W) {
+        sMw[e / Q][e % Q] = c.mw[e / Q][e % Q];
+        sMu[e / Q][e % Q] = c.mu[e / Q][e % Q];
+    }
     if (full && lane == 0) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
@@ -730,7 +740,8 @@ __device__ __forceinline__ void residual_cells_body(const DGConst<T> &c, int64_t
                 for (int n = 0; n < Q; ++n) dv[n] = side ? c.dp[p][n] : c.d0[p][n];
                 const T *fld = G::LEAN ? tr + (int64_t)sNb[f * W + lane] * TR + (f ^ 1) * 2 * NF
                                        : sB + side * W * 2 * NF + lane * 2 * NF;
-                lift_x_face<T, Q>(side, fld, sa, sb, sM[ta], sM[tb], dv, gam, sK[f * W + lane], R);
+                lift_x_face<T, Q>(side, fld, sa, sb, sMw[ta], sMu[ta], sMw[tb], sMu[tb], dv, gam,
+                                  sK[f * W + lane], R);
             }
             if (!G::LEAN) {
                 __syncwarp();

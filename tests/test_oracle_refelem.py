@@ -67,3 +67,20 @@ def test_endpoint_tables_gll():
         assert abs(d0 @ x - 1.0) < 1e-12 and abs(dp @ x - 1.0) < 1e-12
         if p >= 2:
             assert abs(d0 @ x ** 2 - (-2.0)) < 1e-12 and abs(dp @ x ** 2 - 2.0) < 1e-12
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6])
+def test_gll_mass_is_lumped_plus_rank_one(p):
+    """The exact GLL mass equals the lumped (row-sum) mass plus sigma l l^T with
+    l_i = 1 / prod_{m != i} (x_i - x_m), the leading coefficient of the basis
+    function l_i, and sigma < 0: the q-point GLL rule is exact to degree 2p - 1,
+    so its error on l_i l_j is proportional to the product of leading
+    coefficients. The smoothing kernels apply the facet masses in this form."""
+    M = refelem.mass_1d(p)
+    x = refelem.gll_nodes(p)
+    w = M.sum(axis=1)
+    assert np.abs(w - refelem.gll_weights(p)).max() <= 1e-14      # row sums = the GLL weights
+    lc = np.array([1.0 / np.prod([x[i] - x[m] for m in range(p + 1) if m != i]) for i in range(p + 1)])
+    sigma = (M[0, 0] - w[0]) / lc[0] ** 2
+    assert sigma < 0
+    assert np.abs(M - np.diag(w) - sigma * np.outer(lc, lc)).max() <= 1e-13
