@@ -249,6 +249,16 @@ bool cells_apply(const dgmg_batch &B, int q) {
     return B.dim == 3 && q <= (std::is_same<T, float>::value ? 5 : 4) && B.opts.block_inverse == DGMG_BLOCK_EXACT;
 }
 
+// The one-thread-per-cell kernel for stage `stage` of precision T: the smoothing
+// step, and the residual where the level carries the exact blocks' factors (the
+// FP64 level of a mixed batch only applies the operator and has none).
+template <typename T>
+bool cells_stage(const dgmg_batch &B, int q, int stage) {
+    if (!cells_apply<T>(B, q)) return false;
+    if (stage == TILE_SMOOTH) return true;
+    return stage == TILE_RESIDUAL && !(std::is_same<T, double>::value && B.mixed);
+}
+
 template <typename T>
 int build_block_map(dgmg_batch &B, dgmg_batch::Group &grp, int stage) {
     auto &g = grp.prec<T>();
@@ -256,7 +266,7 @@ int build_block_map(dgmg_batch &B, dgmg_batch::Group &grp, int stage) {
     int tile = g.tile[stage];
     if (tile <= 0) {
         // the one-thread-per-cell smoother where it applies, else ~128 threads
-        const bool cells = stage == TILE_SMOOTH && cells_apply<T>(B, grp.q);
+        const bool cells = cells_stage<T>(B, grp.q, stage);
         if (cells) {
             tile = BATCH_ALIGN_CELLS;
         } else {
@@ -297,7 +307,7 @@ int tune_group(dgmg_batch &B, dgmg_batch::Group &grp, T *u, T *bv, cudaStream_t 
         // carry no FP64 block-inverse factors), so its smoothing step is never run
         if (std::is_same<T, double>::value && B.mixed && st == TILE_SMOOTH) continue;
         std::vector<int> cs = cand;
-        if (st == TILE_SMOOTH && cells_apply<T>(B, grp.q)) cs.insert(cs.begin(), 0);
+        if (cells_stage<T>(B, grp.q, st)) cs.insert(cs.begin(), 0);
         int best = cs[0];
         float best_ms = 1e30f;
         for (int c : cs) {

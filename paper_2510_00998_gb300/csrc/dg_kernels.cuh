@@ -816,6 +816,18 @@ __global__ void __launch_bounds__(32) k_smooth_cells_batch(const BatchDG<T> *__r
                             sd.tr[cur], sd.tr[cur ^ 1]);
 }
 
+template <typename T, int Q>
+__global__ void __launch_bounds__(32) k_residual_cells_batch(const BatchDG<T> *__restrict__ D,
+                                                              const BlockMap *__restrict__ map, int mode, const T *u,
+                                                              const T *b, T *r, int cur) {
+    constexpr int NL = Q * Q * Q;
+    __shared__ __align__(16) BatchDG<T> sd;
+    const BlockMap m = map[blockIdx.x];
+    load_batch_desc(D + m.inst, &sd);
+    residual_cells_body<T, Q>(sd.c, m.cell0, mode, u + sd.off * NL, b ? b + sd.off * NL : nullptr, sd.kappa, sd.fd,
+                              sd.tr[cur], r ? r + sd.off * NL : nullptr, sd.corners);
+}
+
 template <int DIM, int Q, typename T>
 __global__ void __launch_bounds__(256) k_residual_batch(const BatchDG<T> *__restrict__ D,
                                                          const BlockMap *__restrict__ map, int cpb, int mode,
@@ -990,7 +1002,21 @@ struct DGLaunch {
     static cudaError_t residual_batch(const BatchDG<T> *D, const BlockMap *map, int nblocks, int cpb, int mode,
                                       const T *u, const T *b, T *r, int cur, cudaStream_t s) {
         if (nblocks <= 0) return cudaSuccess;
-        if (cpb <= 0) cpb = default_cpb();
+        if constexpr (CELLS_OK) {
+            if (cpb <= 0) {          // the map holds 32-cell blocks; every problem carries its factors
+                using CG = CellGeo<T, Q>;
+                static bool attr = false;
+                if (!attr) {
+                    cudaFuncSetAttribute(k_residual_cells_batch<T, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)CG::BYTES);
+                    attr = true;
+                }
+                count_launches(1);
+                k_residual_cells_batch<T, Q><<<nblocks, CG::W, CG::BYTES, s>>>(D, map, mode, u, b, r, cur);
+                return cudaGetLastError();
+            }
+        }
+        if (cpb <= 0) return cudaErrorInvalidValue;   // the map was built for 32-cell blocks
         static bool attr = false;
         if (!attr) {
             cudaFuncSetAttribute(k_residual_batch<DIM, Q, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,

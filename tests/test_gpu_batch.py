@@ -116,7 +116,8 @@ def test_batch_autotuned_tiles_same_results(dgmg):
         stats, _ = batch.solve(bs, xs)
         assert max(s.rel_residual for s in stats) <= 1e-10
         inf = batch.info()
-        assert all(inf.group_tiles[k][0] > 0 and inf.group_tiles[k][2] > 0 for k in range(inf.groups))
+        # 0: the one-thread-per-cell kernel (smoothing step and residual)
+        assert all(inf.group_tiles[k][0] > 0 and min(inf.group_tiles[k]) >= 0 for k in range(inf.groups))
         out.append([x.cpu().numpy() for x in xs])
     for a, b in zip(*out):
         assert np.abs(a - b).max() <= 1e-9 * np.abs(a).max()
