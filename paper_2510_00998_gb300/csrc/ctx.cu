@@ -922,6 +922,28 @@ int dgmg_create(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_op
 
 namespace dgmg {
 
+// Contexts allocate from the device's default stream-ordered memory pool
+// (cudaMallocAsync on their set-up stream). By default the pool returns freed
+// memory to the driver at every synchronisation, so a process that destroys
+// and creates hierarchies (a server, a batch after a batch) pays for mapping
+// the memory again on every allocation: the pool of the current device keeps
+// what is freed instead (a property of this process's pool, not of the GPU).
+static void keep_pool_memory() {
+    static std::mutex mu;
+    static std::vector<int> done;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    std::lock_guard<std::mutex> lk(mu);
+    if (std::find(done.begin(), done.end(), dev) != done.end()) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+    done.push_back(dev);
+}
+
 int create_ctx(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_opts *opts, int flags, dgmg_ctx **out) {
     if (!out) return fail(DGMG_EINVAL, "out is NULL");
     *out = nullptr;
@@ -956,6 +978,7 @@ int create_ctx(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_opt
         return fail(DGMG_EINVAL, "basis must be DGMG_BASIS_GLL or DGMG_BASIS_GL");
     if (o.outer == DGMG_OUTER_AUTO) o.outer = o.precision == DGMG_MIXED_FP32 ? DGMG_OUTER_RELIABLE : DGMG_OUTER_PCG;
 
+    keep_pool_memory();
     std::unique_ptr<dgmg_ctx> C(new dgmg_ctx());
     {
         cudaError_t e = cudaStreamCreateWithFlags(&C->setup_stream, cudaStreamNonBlocking);

@@ -173,19 +173,41 @@ struct dgmg_ctx {
     cudaStream_t capture_stream = nullptr;
     bool use_graphs = true;
 
+    // Device memory of the context: buffers are carved (256-byte aligned) out of
+    // chunks of at least ARENA_CHUNK bytes, each one stream-ordered allocation
+    // on the context's own stream (no device-wide synchronisation with solves
+    // running on other streams); a buffer larger than a chunk gets its own.
+    // A context makes a handful of allocation calls instead of one per buffer.
+    // `bytes` counts the buffers themselves (what dgmg_estimate_bytes predicts).
+    static constexpr size_t ARENA_CHUNK = 8u << 20, ARENA_ALIGN = 256;
+    char *arena_ptr = nullptr;
+    size_t arena_left = 0;
     template <typename T>
     int alloc(T **ptr, size_t count) {
         *ptr = nullptr;
         if (count == 0) count = 1;
-        // stream-ordered allocation on the context's own stream: no device-wide
-        // synchronisation with solves running on other streams
-        cudaError_t e = cudaMallocAsync((void **)ptr, count * sizeof(T), setup_stream);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return fail(DGMG_ENOMEM, std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) +
-                                         " bytes failed: " + cudaGetErrorString(e));
+        const size_t need = (count * sizeof(T) + ARENA_ALIGN - 1) / ARENA_ALIGN * ARENA_ALIGN;
+        if (need > arena_left) {
+            const size_t chunk = need > ARENA_CHUNK / 2 ? need : ARENA_CHUNK;
+            void *p = nullptr;
+            cudaError_t e = cudaMallocAsync(&p, chunk, setup_stream);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(DGMG_ENOMEM, std::string("cudaMalloc of ") + std::to_string(chunk) +
+                                             " bytes failed: " + cudaGetErrorString(e));
+            }
+            allocs.push_back(p);
+            if (chunk == need) {       // a buffer of its own; the open chunk stays open
+                *ptr = reinterpret_cast<T *>(p);
+                bytes += count * sizeof(T);
+                return DGMG_OK;
+            }
+            arena_ptr = reinterpret_cast<char *>(p);
+            arena_left = chunk;
         }
-        allocs.push_back(*ptr);
+        *ptr = reinterpret_cast<T *>(arena_ptr);
+        arena_ptr += need;
+        arena_left -= need;
         bytes += count * sizeof(T);
         return DGMG_OK;
     }
