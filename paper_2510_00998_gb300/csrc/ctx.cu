@@ -360,8 +360,14 @@ std::vector<T> convert(const std::vector<double> &v) {
 
 // The per-cell factors (and, FP64, the table of inverse eigenvalue sums) of
 // level D from the FP64 kappa of the finest level, on the set-up stream.
+// FP32 factors are the rounded FP64 ones when those exist (fd64).
 template <typename T>
-int compute_factors(dgmg_ctx &C, const DGSpace &S, DGDev<T> &D) {
+int compute_factors(dgmg_ctx &C, const DGSpace &S, DGDev<T> &D, const double *fd64 = nullptr) {
+    if (std::is_same<T, float>::value && fd64) {
+        LC(launch_cast_d2f((int64_t)C.ncell * C.dim * (S.q * S.q + S.q), fd64, reinterpret_cast<float *>(D.fd),
+                           C.setup_stream));
+        return DGMG_OK;
+    }
     FDInput in;
     RC(fd_input(C, S, in));
     LC(launch_fd_factors<T>(in, C.d64.kappa, C.ncell, D.fd, C.setup_stream));
@@ -377,7 +383,7 @@ int compute_factors(dgmg_ctx &C, const DGSpace &S, DGDev<T> &D) {
 // inverse eigenvalue sums, traces and corner sums.
 template <typename T>
 int setup_dg(dgmg_ctx &C, const DGSpace &S, DGDev<T> &D, const std::vector<double> &kappa, bool smoother = true,
-             const T *shared_kappa = nullptr) {
+             const T *shared_kappa = nullptr, const double *fd64 = nullptr) {
     fill_const(C, S, D.c);
     if (shared_kappa)
         D.kappa = const_cast<T *>(shared_kappa);
@@ -392,7 +398,7 @@ int setup_dg(dgmg_ctx &C, const DGSpace &S, DGDev<T> &D, const std::vector<doubl
     }
     RC(C.alloc(&D.fd, (size_t)C.ncell * C.dim * (S.q * S.q + S.q)));
     if (sizeof(T) == sizeof(double)) RC(C.alloc(&D.linv, (size_t)S.ndof));
-    RC(compute_factors<T>(C, S, D));
+    RC(compute_factors<T>(C, S, D, fd64));
     RC(C.alloc(&D.tr[0], trn));
     RC(C.alloc(&D.tr[1], trn));
     RC(C.alloc(&D.corners, C.ncell * (1 << C.dim)));
@@ -429,9 +435,9 @@ int setup_dg_levels(dgmg_ctx &C, const std::vector<double> &kap) {
             lagrange_at(S.re.nodes, F.re.nodes[i], val.data(), nullptr);
             for (int j = 0; j < S.q; ++j) I[(size_t)i * S.q + j] = val[j];
         }
-        auto level = [&](auto &lv, auto *kappa_dev) -> int {
+        auto level = [&](auto &lv, auto *kappa_dev, const double *fd64) -> int {
             using T = typename std::remove_pointer<decltype(kappa_dev)>::type;
-            RC(setup_dg<T>(C, S, lv.D, kap, true, kappa_dev));
+            RC(setup_dg<T>(C, S, lv.D, kap, true, kappa_dev, fd64));
             RC(C.alloc(&lv.z, S.ndof));
             RC(C.alloc(&lv.b, S.ndof));
             RC(C.alloc(&lv.r, S.ndof));
@@ -439,8 +445,8 @@ int setup_dg_levels(dgmg_ctx &C, const std::vector<double> &kap) {
             for (size_t k = 0; k < I.size(); ++k) lv.P.I[k] = (T)I[k];
             return DGMG_OK;
         };
-        RC(level(C.lvl64[l], C.d64.kappa));
-        if (mixed) RC(level(C.lvl32[l], C.d32.kappa));
+        RC(level(C.lvl64[l], C.d64.kappa, nullptr));
+        if (mixed) RC(level(C.lvl32[l], C.d32.kappa, C.lvl64[l].D.fd));
     }
     RC(C.alloc(&C.res64, C.ndof));
     if (mixed) RC(C.alloc(&C.res32, C.ndof));
@@ -1032,7 +1038,7 @@ int create_ctx(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_opt
     if (!(flags & CREATE_NO_FP64_Q1)) RC(setup_cg<double>(*C, C->cg64));
     trace.mark("cg upload");
     if (o.precision == DGMG_MIXED_FP32) {
-        RC(setup_dg<float>(*C, S0, C->d32, kap));
+        RC(setup_dg<float>(*C, S0, C->d32, kap, true, nullptr, C->d64.fd));
         RC(setup_cg<float>(*C, C->cg32));
         RC(C->alloc(&C->r32, C->ndof));
         RC(C->alloc(&C->z32, C->ndof));
@@ -1172,7 +1178,7 @@ int dgmg_update_kappa(dgmg_ctx *C, const double *kappa) {
         if (D64.fd) RC(compute_factors<double>(*C, C->dgs[l], D64));
         if (mixed) {
             DGDev<float> &D32 = l == 0 ? C->d32 : C->lvl32[l].D;
-            if (D32.fd) RC(compute_factors<float>(*C, C->dgs[l], D32));
+            if (D32.fd) RC(compute_factors<float>(*C, C->dgs[l], D32, D64.fd));
         }
     }
     DG_CUDA(cudaStreamSynchronize(s));
