@@ -234,7 +234,8 @@ struct dgmg_ctx {
 };
 
 // slots of ctx->scal
-enum { S_RZ = 0, S_PQ = 1, S_BETA = 2, S_RR = 3, S_RZN = 4, S_RZO = 5, S_BB = 6, S_ZZ = 7, S_ZZ0 = 8, S_NSCAL = 16 };
+enum { S_RZ = 0, S_PQ = 1, S_BETA = 2, S_RR = 3, S_RZN = 4, S_RZO = 5, S_BB = 6, S_ZZ = 7, S_ZZ0 = 8, S_XX = 9,
+       S_NSCAL = 16 };
 
 
 #define RC(x)                           \

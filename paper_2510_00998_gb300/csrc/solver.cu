@@ -104,8 +104,8 @@ int scalars_ready(dgmg_ctx *C, bool blocking) {
 }
 
 enum {
-    P_START, P_WAIT0, P_WAIT1, P_ITER, P_WAIT_RR, P_FINAL, P_WAIT_FINAL,   // FP64 PCG
-    R_START, R_WAIT0, R_ITER, R_WAIT_RR, R_WAIT_UPD, R_CONT, R_FINAL, R_WAIT_FIN,   // reliable updates
+    P_START, P_WAITX, P_WAIT0, P_WAIT1, P_ITER, P_WAIT_RR, P_FINAL, P_WAIT_FINAL,   // FP64 PCG
+    R_START, R_WAITX, R_WAIT0, R_ITER, R_WAIT_RR, R_WAIT_UPD, R_CONT, R_FINAL, R_WAIT_FIN,   // reliable updates
     M_START, M_WAIT0, M_ITER, M_WAIT,                                              // MGMult
     S_DONE
 };
@@ -245,14 +245,36 @@ int SolveRun::advance(bool blocking) {
     for (;;) {
         switch (state) {
             // ------------------------------------------------ FP64 PCG
+            // The initial residual: r = b when the initial guess is zero (the
+            // host reads ||x||^2 first), else the FP64 apply r = b - A x.
             case P_START:
-                ADV(apply64(*C, x, b, r, s));          // r = b - A x
-                ++nres;
+            case R_START:
                 ADV_CUDA(launch_dot(n, b, b, C->partials, C->scal + S_BB, s));
-                ADV_CUDA(launch_dot(n, r, r, C->partials, C->scal + S_RR, s));
+                ADV_CUDA(launch_dot(n, x, x, C->partials, C->scal + S_XX, s));
                 ADV(post_scalars(C, s));
-                state = P_WAIT0;
+                state = state == P_START ? P_WAITX : R_WAITX;
                 break;
+            case P_WAITX:
+            case R_WAITX: {
+                const int rdy = scalars_ready(C, blocking);
+                if (rdy < 0) ADV(rdy);
+                if (!rdy) return 0;
+                if (C->host_scal[S_XX] == 0.0) {
+                    C->prof.begin(ST_VECTOR, s);
+                    ADV_CUDA(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+                    C->prof.end(s);
+                } else {
+                    ADV(apply64(*C, x, b, r, s));
+                    ++nres;
+                }
+                C->prof.begin(ST_VECTOR, s);
+                ADV_CUDA(launch_dot(n, r, r, C->partials, C->scal + S_RR, s));
+                if (state == R_WAITX) ADV_CUDA(launch_cast_d2f(n, r, r32, s));
+                C->prof.end(s);
+                ADV(post_scalars(C, s));
+                state = state == P_WAITX ? P_WAIT0 : R_WAIT0;
+                break;
+            }
             case P_WAIT0: {
                 const int rdy = scalars_ready(C, blocking);
                 if (rdy < 0) ADV(rdy);
@@ -331,17 +353,6 @@ int SolveRun::advance(bool blocking) {
                 return 1;
             }
             // ------------------------------------------------ reliable updates
-            case R_START:
-                ADV_CUDA(launch_dot(n, b, b, C->partials, C->scal + S_BB, s));
-                ADV(apply64(*C, x, b, r, s));
-                ++nres;
-                C->prof.begin(ST_VECTOR, s);
-                ADV_CUDA(launch_dot(n, r, r, C->partials, C->scal + S_RR, s));
-                ADV_CUDA(launch_cast_d2f(n, r, r32, s));
-                C->prof.end(s);
-                ADV(post_scalars(C, s));
-                state = R_WAIT0;
-                break;
             case R_WAIT0: {
                 const int rdy = scalars_ready(C, blocking);
                 if (rdy < 0) ADV(rdy);
