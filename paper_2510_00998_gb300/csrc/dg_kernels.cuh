@@ -34,6 +34,7 @@ struct Geo {
     static constexpr int VEC = 16 / (int)sizeof(T);            // elements per 16-byte vector
     static constexpr int FDSP = (FDS + VEC - 1) / VEC * VEC;   // per axis in shared memory (padded)
     static constexpr int QQV = (Q * Q + VEC - 1) / VEC;        // 16-byte vectors covering S
+    static constexpr int NDOT = NFACE * 2 * (DIM == 3 ? Q : 1); // facet-mass dot products per cell
     // volume index of node i of the pencil along `dir` at tangential position t
     static __device__ __forceinline__ int vidx(int dir, int t, int i) {
         if (DIM == 2) return dir == 0 ? i + Q * t : t + Q * i;
@@ -64,12 +65,6 @@ __device__ __forceinline__ int64_t axis_stride(const int *n, int dir) {
 template <typename T>
 __device__ __forceinline__ void block_copy(T *__restrict__ dst, const T *__restrict__ src, int64_t count) {
     for (int64_t i = threadIdx.x; i < count; i += blockDim.x) dst[i] = src[i];
-}
-
-// Copy the 1D mass matrices of all axes into shared memory (all threads).
-template <int DIM, int Q, typename T>
-__device__ __forceinline__ void stage_masses(const DGConst<T> &c, T *sM) {
-    for (int e = threadIdx.x; e < DIM * Q * Q; e += blockDim.x) sM[e] = c.M[e / (Q * Q)][e % (Q * Q)];
 }
 
 // Load one q x q factor matrix (16-byte aligned in shared memory) into
@@ -142,61 +137,62 @@ __device__ __forceinline__ void load_neighbour_traces(const DGConst<T> &c, int64
 // Apply the facet mass matrix (tensor product of the tangential 1D masses) to
 // both components of every interior face of the cell, in place. Needs all
 // threads of the CTA (contains barriers); `active` threads do the arithmetic.
-// Each thread keeps the rows of the (h-scaled) 1D masses it needs in registers:
-// its first tangential index ia with the masses of axes 0 and 1 (first pass),
-// its second index ib with the masses of axes 1 and 2 (second pass). sM: the
-// per-axis masses staged in shared memory, [axis][q*q].
+// Each 1D mass in its rank-one form M = diag(w) - mu mu^T (sW, sU: [axis][q]
+// in shared memory): per pass, first the dot products mu . (pencil) of every
+// face, component and pencil, spread over the cell's threads into sD
+// ([NFACE][2][lines], lines = q in 3D, 1 in 2D), then every node
+// out = w f - mu (dot). Pass 0 runs along the lower tangential index ia,
+// pass 1 (3D) along the upper one ib.
 template <int DIM, int Q, typename T>
-__device__ __forceinline__ void facet_mass(const T *sM, bool active, int t, T *sF, int mask) {
+__device__ __forceinline__ void facet_mass(const T *sW, const T *sU, bool active, int t, T *sF, T *sD, int mask) {
     using G = Geo<DIM, Q, T>;
     constexpr int NPASS = DIM - 1;
+    constexpr int LINES = DIM == 3 ? Q : 1;
+    constexpr int ND = G::NFACE * 2 * LINES;
     const int ia = t % Q, ib = t / Q;
-    T ra[2][Q], rb[2][Q];
-#pragma unroll
-    for (int m = 0; m < Q; ++m) {
-        ra[0][m] = sM[0 * Q * Q + ia * Q + m];
-        ra[1][m] = sM[1 * Q * Q + ia * Q + m];
-        rb[0][m] = DIM == 3 ? sM[1 * Q * Q + ib * Q + m] : T(0);
-        rb[1][m] = DIM == 3 ? sM[2 * Q * Q + ib * Q + m] : T(0);
-    }
 #pragma unroll
     for (int pass = 0; pass < NPASS; ++pass) {
-        T out[G::NFACE][2];
         if (active) {
-#pragma unroll
-            for (int f = 0; f < G::NFACE; ++f) {
+            for (int d = t; d < ND; d += G::NF) {
+                const int line = d % LINES, fc = d / LINES, f = fc >> 1;
                 const int dir = f >> 1;
-                // tangential axes: ta (lower) in {0, 1}, tb (upper) in {1, 2}
-                const int ta = dir == 0 ? 1 : 0;
-                const int tb = dir == 2 ? 1 : 2;
+                const int ax = pass == 0 ? (dir == 0 ? 1 : 0) : (dir == 2 ? 1 : 2);   // the pass's axis
+                T s = T(0);
+                if (mask & (1 << f)) {
+                    const T *fld = sF + fc * G::NF;
 #pragma unroll
-                for (int comp = 0; comp < 2; ++comp) {
-                    const T *fld = sF + (f * 2 + comp) * G::NF;
-                    T s = T(0);
-                    if (mask & (1 << f)) {
-                        if (DIM == 2) {
-#pragma unroll
-                            for (int m = 0; m < Q; ++m) s += ra[ta][m] * fld[m];
-                        } else if (pass == 0) {
-#pragma unroll
-                            for (int m = 0; m < Q; ++m) s += ra[ta][m] * fld[m + Q * ib];
-                        } else {
-#pragma unroll
-                            for (int m = 0; m < Q; ++m) s += rb[tb - 1][m] * fld[ia + Q * m];
-                        }
-                    }
-                    out[f][comp] = s;
+                    for (int m = 0; m < Q; ++m)
+                        s += sU[ax * Q + m] * (pass == 0 ? fld[m + Q * line] : fld[line + Q * m]);
                 }
+                sD[d] = s;
             }
         }
         __syncthreads();
         if (active) {
 #pragma unroll
-            for (int f = 0; f < G::NFACE; ++f)
+            for (int f = 0; f < G::NFACE; ++f) {
+                if (!(mask & (1 << f))) continue;
+                const int dir = f >> 1;
+                const int ax = pass == 0 ? (dir == 0 ? 1 : 0) : (dir == 2 ? 1 : 2);
+                const int node = pass == 0 ? ia : ib, line = DIM == 3 ? (pass == 0 ? ib : ia) : 0;
+                const T w = sW[ax * Q + node], mu = sU[ax * Q + node];
 #pragma unroll
-                for (int comp = 0; comp < 2; ++comp) sF[(f * 2 + comp) * G::NF + t] = out[f][comp];
+                for (int comp = 0; comp < 2; ++comp) {
+                    T *fld = sF + (f * 2 + comp) * G::NF;
+                    fld[t] = w * fld[t] - mu * sD[(f * 2 + comp) * LINES + line];
+                }
+            }
         }
         __syncthreads();
+    }
+}
+
+// stage the rank-one mass data of every axis: sW[a][i], sU[a][i]
+template <int DIM, int Q, typename T>
+__device__ __forceinline__ void stage_mass_rank1(const DGConst<T> &c, T *sW, T *sU) {
+    for (int e = threadIdx.x; e < DIM * Q; e += blockDim.x) {
+        sW[e] = c.mw[e / Q][e % Q];
+        sU[e] = c.mu[e / Q][e % Q];
     }
 }
 
@@ -508,7 +504,8 @@ __device__ __forceinline__ void k_smooth_body(const DGConst<T> &c, int64_t cell0
     T *sR = sU + cpb * G::NL;
     T *sF = sR + cpb * G::NL;
     T *sK = sF + cpb * G::NFACE * 2 * G::NF;   // [cpb][NFACE + 1]
-    T *sA = sK + cpb * (G::NFACE + 1);         // inexact block only: [cpb][NL] x 2, [cpb][DIM*Q*Q]
+    T *sDot = sK + cpb * (G::NFACE + 1);       // [cpb][facet-mass dot products]
+    T *sA = sDot + cpb * G::NDOT;              // inexact block only: [cpb][NL] x 2, [cpb][DIM*Q*Q]
     T *sB = sA + cpb * G::NL;
     T *sKT = sB + cpb * G::NL;
     const int lc = threadIdx.x / G::NF, t = threadIdx.x - lc * G::NF;
@@ -516,9 +513,9 @@ __device__ __forceinline__ void k_smooth_body(const DGConst<T> &c, int64_t cell0
     const bool active = lc < ncl;
     const int64_t cell = cell0 + lc;
     int ci[3] = {0, 0, 0};
-    __shared__ T sM[DIM * Q * Q];
+    __shared__ T sMw[DIM * Q], sMu[DIM * Q];
     __shared__ T sT[DIM * Q * Q + 2 * DIM * Q];
-    stage_masses<DIM, Q, T>(c, sM);
+    stage_mass_rank1<DIM, Q, T>(c, sMw, sMu);
     if (!exact) stage_block_tables<DIM, Q, T>(c, sT);
     block_copy(sU, u + cell0 * G::NL, (int64_t)ncl * G::NL);
     block_copy(sR, b + cell0 * G::NL, (int64_t)ncl * G::NL);
@@ -535,7 +532,7 @@ __device__ __forceinline__ void k_smooth_body(const DGConst<T> &c, int64_t cell0
     T *myU = sU + lc * G::NL;
     const int mask = active ? interior_mask<DIM>(ci, c.n) : 0;
     if (!exact) build_block_1d<DIM, Q, T>(c, sT, active, t, myK, mask, sKT + lc * DIM * Q * Q);
-    facet_mass<DIM, Q, T>(sM, active, t, myF, mask);
+    facet_mass<DIM, Q, T>(sMw, sMu, active, t, myF, sDot + lc * G::NDOT, mask);
     lift_neighbours<DIM, Q, T>(c, active, t, myR, myF, myK, mask);
     if (!exact)
         subtract_block_apply<DIM, Q, T>(c, active, t, myU, myR, sA + lc * G::NL, sB + lc * G::NL,
@@ -676,14 +673,15 @@ __device__ __forceinline__ void k_residual_body(const DGConst<T> &c, int64_t cel
     T *sF = sB + cpb * G::NL;
     T *sKT = sF + cpb * G::NFACE * 2 * G::NF;   // [cpb][DIM][Q*Q]
     T *sK = sKT + cpb * DIM * Q * Q;            // [cpb][NFACE + 1]
+    T *sDot = sK + cpb * (G::NFACE + 1);        // [cpb][facet-mass dot products]
     const int lc = threadIdx.x / G::NF, t = threadIdx.x - lc * G::NF;
     const int ncl = (int)min((int64_t)cpb, c.ncell - cell0);
     const bool active = lc < ncl;
     const int64_t cell = cell0 + lc;
     int ci[3] = {0, 0, 0};
-    __shared__ T sM[DIM * Q * Q];
+    __shared__ T sMw[DIM * Q], sMu[DIM * Q];
     __shared__ T sT[DIM * Q * Q + 2 * DIM * Q];
-    stage_masses<DIM, Q, T>(c, sM);
+    stage_mass_rank1<DIM, Q, T>(c, sMw, sMu);
     stage_block_tables<DIM, Q, T>(c, sT);
     block_copy(sU, u + cell0 * G::NL, (int64_t)ncl * G::NL);
     if (mode & RES_HAS_B) {
@@ -701,7 +699,7 @@ __device__ __forceinline__ void k_residual_body(const DGConst<T> &c, int64_t cel
     T *myKT = sKT + lc * DIM * Q * Q;
     const int mask = active ? interior_mask<DIM>(ci, c.n) : 0;
     build_block_1d<DIM, Q, T>(c, sT, active, t, myK, mask, myKT);
-    facet_mass<DIM, Q, T>(sM, active, t, myF, mask);   // contains barriers
+    facet_mass<DIM, Q, T>(sMw, sMu, active, t, myF, sDot + lc * G::NDOT, mask);   // contains barriers
     T *myR = sR + lc * G::NL;
     T *myU = sU + lc * G::NL;
     lift_neighbours<DIM, Q, T>(c, active, t, myR, myF, myK, mask);
@@ -859,13 +857,14 @@ template <int DIM, int Q, typename T>
 constexpr size_t smem_smooth(int cpb, bool exact) {
     using G = Geo<DIM, Q, T>;
     return (size_t)cpb *
-           (DIM * G::FDSP + 2 * G::NL + G::NFACE * 2 * G::NF + G::NFACE + 1 + (exact ? 0 : 2 * G::NL + DIM * Q * Q)) *
+           (DIM * G::FDSP + 2 * G::NL + G::NFACE * 2 * G::NF + G::NFACE + 1 + G::NDOT +
+            (exact ? 0 : 2 * G::NL + DIM * Q * Q)) *
            sizeof(T);
 }
 template <int DIM, int Q, typename T>
 constexpr size_t smem_residual(int cpb) {
     using G = Geo<DIM, Q, T>;
-    return (size_t)cpb * (4 * G::NL + G::NFACE * 2 * G::NF + DIM * Q * Q + G::NFACE + 1) * sizeof(T);
+    return (size_t)cpb * (4 * G::NL + G::NFACE * 2 * G::NF + DIM * Q * Q + G::NFACE + 1 + G::NDOT) * sizeof(T);
 }
 
 template <int DIM, int Q, typename T>
