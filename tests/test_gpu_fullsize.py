@@ -96,3 +96,28 @@ def test_window_block_matches_full_block_on_small_mesh():
     full = sipg.block_diagonal(mesh, kappa)
     for c in [0, 7, 33, mesh.ncell - 1, 61]:
         assert np.abs(_window_block(mesh, kappa, c) - full[c]).max() <= 1e-13 * np.abs(full[c]).max()
+
+
+@pytest.mark.gpu
+def test_full_size_fp32_vcycle_against_fp64():
+    """64^3, p = 4, lognormal kappa: the FP32 V-cycle of the mixed-precision
+    context (one-thread-per-cell smoothing and residual kernels at the bench's
+    launch configuration) against the FP64 V-cycle of an FP64 context, whose
+    kernels match the oracle on smaller meshes; every output within the FP32
+    V-cycle bound of the small-mesh tests (2e-5 of the maximum)."""
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2510_00998_gb300 import dgmg as m
+    n, p = (64, 64, 64), 4
+    kappa = np.exp(np.random.default_rng(3).normal(size=int(np.prod(n))))
+    r = torch.tensor(np.random.default_rng(41).normal(size=int(np.prod(n)) * (p + 1) ** 3), device=DEV)
+    outs = []
+    for prec in (m.DGMG_FP64, m.DGMG_MIXED_FP32):
+        ctx = m.Context(n, p, kappa, precision=prec, autotune=1)
+        e = torch.empty_like(r)
+        ctx.vcycle(r, e)
+        torch.cuda.synchronize()
+        outs.append(e)
+        ctx.close()
+    assert float((outs[1] - outs[0]).abs().max() / outs[0].abs().max()) <= 2e-5
+    assert m.wait_timeouts() == 0
