@@ -930,7 +930,7 @@ namespace dgmg {
 
 // Contexts allocate from the device's default stream-ordered memory pool
 // (cudaMallocAsync on their set-up stream). By default the pool returns freed
-// memory to the driver at every synchronisation, so a process that destroys
+// memory to the CUDA driver at every synchronisation, so a process that destroys
 // and creates hierarchies (a server, a batch after a batch) pays for mapping
 // the memory again on every allocation: the pool of the current device keeps
 // what is freed instead (a property of this process's pool, not of the GPU).

@@ -87,7 +87,7 @@ __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bu
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
 
-// Lane 0 waits for `bar`; the verdict is shared with the warp. A wait that runs
+// Lane 0 waits for `bar`; the outcome is shared with the warp. A wait that runs
 // out is counted, then waited for once more (the copies must land before the
 // CTA's shared memory is released).
 __device__ __forceinline__ bool warp_wait_copies(uint64_t *bar, int lane) {
