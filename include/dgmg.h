@@ -354,10 +354,12 @@ typedef struct {
  * h-restriction, h-prolongation, vertex gather, dense coarsest solve). All
  * meshes have the same dimension. opts (NULL = defaults) apply to every
  * problem; nu_pre >= 1 (DGMG_EINVAL otherwise). precision DGMG_FP64, or
- * DGMG_MIXED_FP32: the V-cycle runs in FP32 (the dense coarsest solve stays
- * FP64) inside FP64 CG recurrences with FP64 residuals (flexible
- * Polak-Ribiere beta). With opts->autotune the cells per CTA of each group's
- * launches are timed and chosen on the batch itself. Synchronous.
+ * DGMG_MIXED_FP32: reliable-update CG as in dgmg_solve, batched: the CG
+ * recurrences, V-cycle and operator in FP32 (the dense coarsest solve stays
+ * FP64; flexible Polak-Ribiere beta, FP64 dot products), the FP64 solution and
+ * true residuals refreshed for the whole batch at reliable updates (`delta`).
+ * With opts->autotune the cells per CTA of each group's launches are timed and
+ * chosen on the batch itself. Synchronous.
  */
 int dgmg_batch_create(int count, const dgmg_mesh *meshes, const int *p, const double *const *kappa,
                       const dgmg_opts *opts, dgmg_batch **out);
@@ -365,11 +367,12 @@ int dgmg_batch_create(int count, const dgmg_mesh *meshes, const int *p, const do
 int dgmg_batch_info(const dgmg_batch *batch, dgmg_batch_info_t *info);
 
 /*
- * Solve A_i x_i = b_i for every problem: FP64 preconditioned conjugate
- * gradients with the problem's own hp V-cycle, one CG recurrence per problem
- * (its own alpha and beta), all problems advanced by the same batched
- * launches; a problem that met ||b_i - A_i x_i||_2 <= rtol ||b_i||_2 stops
- * changing while the others continue. b[i], x[i]: DEVICE vectors of problem i
+ * Solve A_i x_i = b_i for every problem: preconditioned conjugate gradients
+ * (FP64, or the mixed-precision reliable-update form) with the problem's own
+ * hp V-cycle, one CG recurrence per problem (its own alpha and beta), all
+ * problems advanced by the same batched launches; a problem that met
+ * ||b_i - A_i x_i||_2 <= rtol ||b_i||_2 (FP64 true residual) stops changing
+ * while the others continue. b[i], x[i]: DEVICE vectors of problem i
  * (x[i] holds the initial guess and receives the solution). stats: HOST array
  * of `count` (may be NULL): each problem's iterations and recomputed true
  * residual. Blocks until done. DGMG_ENOTCONVERGED after maxit iterations.
