@@ -842,7 +842,10 @@ static int tune_tiles(dgmg_ctx &C, T *u, T *b, int *tile, bool trace, bool smoot
         }
         return best;
     };
-    tile[TILE_PROJECT] = pick("project", cand, [&](int c) {
+    std::vector<int> cp = cand;
+    if (C.dim == 3 && C.q <= (std::is_same<T, float>::value ? 5 : 4) && C.opts.basis == DGMG_BASIS_GLL)
+        cp.insert(cp.begin(), 0);
+    tile[TILE_PROJECT] = pick("project", cp, [&](int c) {
         return launch_project<T>(C.dim, C.q, D.c, c, u, nullptr, D.tr[0], s);
     });
     std::vector<int> cs = cand;

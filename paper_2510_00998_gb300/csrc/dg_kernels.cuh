@@ -877,6 +877,25 @@ struct DGLaunch {
         return c;
     }
     static cudaError_t project(const DGConst<T> &c, int cpb, T *u, const T *e0, T *tr, cudaStream_t s) {
+        if constexpr (CELLS_OK) {
+            // bulk copies want a 16-byte aligned u; the trace pieces 8- (FP32) or 16-byte (FP64) aligned traces
+            const uintptr_t tra = std::is_same<T, float>::value ? 7 : 15;
+            if (cpb <= 0 && !c.gl && (reinterpret_cast<uintptr_t>(u) & 15) == 0 &&
+                (reinterpret_cast<uintptr_t>(tr) & tra) == 0) {
+                using CG = CellGeo<T, Q>;
+                static bool attr_c = false;
+                if (!attr_c) {
+                    cudaFuncSetAttribute(k_project_cells<T, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)CG::BYTES);
+                    attr_c = true;
+                }
+                const int64_t grid = (c.ncell + CG::W - 1) / CG::W;
+                if (grid == 0) return cudaSuccess;
+                count_launches(1);
+                k_project_cells<T, Q><<<(unsigned)grid, CG::W, CG::BYTES, s>>>(c, u, e0, tr);
+                return cudaGetLastError();
+            }
+        }
         if (cpb <= 0) cpb = default_cpb();
         const size_t sm = smem_project<DIM, Q, T>(cpb);
         static bool attr = false;

@@ -291,6 +291,52 @@ __device__ __forceinline__ void x_face_traces(int side, const T *R, const T *dv,
         }
 }
 
+// Traces of the cell tensor R (one per lane) to tr_out[cell][face][2][q^2]: the
+// faces normal to axis p, then rotate. FP32: through area B (two faces of the
+// CTA's cells) with coalesced copy-out; FP64 (LEAN): written per lane. R ends
+// rotated.
+template <typename T, int Q>
+__device__ __forceinline__ void cells_write_traces(const DGConst<T> &c, T *R, int lane, bool active, int64_t cell,
+                                                   int64_t cell0, int ncl, T *sB, T *__restrict__ tr_out) {
+    using G = CellGeo<T, Q>;
+    constexpr int W = G::W, NF = G::NF, TR = G::TR;
+#pragma unroll 1
+    for (int p = 0; p < 3; ++p) {
+        const int sa = p == 1 ? Q : 1, sb = p == 1 ? 1 : Q;
+        if (active) {
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                T dv[Q];
+#pragma unroll
+                for (int n = 0; n < Q; ++n) dv[n] = side ? c.dp[p][n] : c.d0[p][n];
+                T *dst = G::LEAN ? tr_out + cell * TR + (2 * p + side) * 2 * NF
+                                 : sB + side * W * 2 * NF + lane * 2 * NF;
+                x_face_traces<T, Q>(side, R, dv, sa, sb, dst);
+            }
+        }
+        if (G::LEAN) {
+            if (p < 2) rotate<T, Q>(R);
+            continue;
+        }
+        __syncwarp();
+        // 2 faces x [W][2 NF] -> [cell][face 2p + side], in 8-byte (FP32) or 16-byte (FP64) pieces
+        // (constant divisors only: the index split is a multiply and a shift)
+        using V = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+        constexpr int NV = NF;                          // 2 NF values = NF pieces of two
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const V *src = reinterpret_cast<const V *>(sB + side * W * 2 * NF);
+            V *dst = reinterpret_cast<V *>(tr_out + cell0 * TR + (2 * p + side) * 2 * NF);
+            for (int idx = lane; idx < ncl * NV; idx += W) {
+                const int j = idx / NV, part = idx - j * NV;
+                dst[j * (TR / 2) + part] = src[idx];
+            }
+        }
+        __syncwarp();
+        if (p < 2) rotate<T, Q>(R);
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ T div_approx(T a, T b);
 template <>
@@ -510,44 +556,102 @@ __device__ __forceinline__ void smooth_cells_body(const DGConst<T> &c, int64_t c
         for (int e = lane; e < ncl * NL; e += W) u[cell0 * NL + e] = sA[e];
     }
 
-    // traces of the new iterate: the faces normal to axis p through area B, then
-    // rotate; copied out to tr[cell][face][2][q^2]
-#pragma unroll 1
-    for (int p = 0; p < 3; ++p) {
-        const int sa = p == 1 ? Q : 1, sb = p == 1 ? 1 : Q;
-        if (active) {
-#pragma unroll
-            for (int side = 0; side < 2; ++side) {
-                T dv[Q];
-#pragma unroll
-                for (int n = 0; n < Q; ++n) dv[n] = side ? c.dp[p][n] : c.d0[p][n];
-                T *dst = G::LEAN ? tr_out + cell * TR + (2 * p + side) * 2 * NF
-                                 : sB + side * W * 2 * NF + lane * 2 * NF;
-                x_face_traces<T, Q>(side, R, dv, sa, sb, dst);
-            }
-        }
-        if (G::LEAN) {
-            if (p < 2) rotate<T, Q>(R);
-            continue;
-        }
-        __syncwarp();
-        // 2 faces x [W][2 NF] -> [cell][face 2p + side], in 8-byte (FP32) or 16-byte (FP64) pieces
-        // (constant divisors only: the index split is a multiply and a shift)
-        using V = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
-        constexpr int NV = NF;                          // 2 NF values = NF pieces of two
-#pragma unroll
-        for (int side = 0; side < 2; ++side) {
-            const V *src = reinterpret_cast<const V *>(sB + side * W * 2 * NF);
-            V *dst = reinterpret_cast<V *>(tr_out + cell0 * TR + (2 * p + side) * 2 * NF);
-            for (int idx = lane; idx < ncl * NV; idx += W) {
-                const int j = idx / NV, part = idx - j * NV;
-                dst[j * (TR / 2) + part] = src[idx];
-            }
-        }
-        __syncwarp();
-        if (p < 2) rotate<T, Q>(R);
-    }
+    // traces of the new iterate
+    cells_write_traces<T, Q>(c, R, lane, active, cell, cell0, ncl, sB, tr_out);
     if (full && lane == 0) bulk_wait_read_all();
+}
+
+// Warm-up projection (Alg. 4 preamble) with one thread per cell, 3D, GLL:
+// optionally u += P e (the p-prolongation of the Q1 correction e, Sec. 5.1,
+// trilinear hats of the cell's corner values at the GLL nodes), then the
+// traces of every face. u arrives by a bulk copy; the updated u (with e)
+// leaves by a bulk store, the traces as in the smoothing step.
+template <typename T, int Q>
+__device__ __forceinline__ void project_cells_body(const DGConst<T> &c, int64_t cell0, T *__restrict__ u,
+                                                   const T *__restrict__ e0, T *__restrict__ tr) {
+    using G = CellGeo<T, Q>;
+    constexpr int W = G::W, NL = G::NL;
+    extern __shared__ __align__(128) unsigned char smem_c[];
+    T *sA = reinterpret_cast<T *>(smem_c);              // u
+    T *sB = sA + G::OFF_B;                               // FP32: trace staging
+    __shared__ __align__(8) uint64_t bars[1];
+    const int lane = threadIdx.x;
+    const int ncl = (int)min((int64_t)W, c.ncell - cell0);
+    const bool full = ncl == W;
+    const bool active = lane < ncl;
+    const int64_t cell = cell0 + lane;
+    if (full && lane == 0) {
+        mbar_init(&bars[0], 1);
+        fence_mbar_init();
+        fence_proxy_async_smem();
+    }
+    stage_bulk<T>(full, lane, &bars[0], sA, u + cell0 * NL, W * NL, ncl * NL);
+    // the corner values of the correction (zero at boundary vertices)
+    T ec[8];
+    if (e0 != nullptr && active) {
+        int ci[3];
+        cell_coords<3>(cell, c.n, ci);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            bool interior = true;
+            int64_t vid = 0, stride = 1;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const int v = ci[a] + ((k >> a) & 1);
+                interior = interior && v >= 1 && v <= c.n[a] - 1;
+                vid += (int64_t)(v - 1) * stride;
+                stride *= (c.n[a] - 1);
+            }
+            ec[k] = interior ? e0[vid] : T(0);
+        }
+    }
+    if (full) {
+        if (!warp_wait_copies(&bars[0], lane)) return;
+    } else {
+        __syncwarp();
+    }
+    T R[NL];
+#pragma unroll
+    for (int e = 0; e < NL; ++e) R[e] = active ? sA[lane * NL + e] : T(0);
+    if (e0 != nullptr) {
+        if (active) {
+            // u(i,j,k) += sum over corners of e_c hat_cx(x_i) hat_cy(y_j) hat_cz(z_k), axis by axis
+            T Z[4][Q];
+#pragma unroll
+            for (int cxy = 0; cxy < 4; ++cxy)
+#pragma unroll
+                for (int k = 0; k < Q; ++k) Z[cxy][k] = ec[cxy] * c.hat[0][k] + ec[cxy + 4] * c.hat[1][k];
+#pragma unroll
+            for (int k = 0; k < Q; ++k)
+#pragma unroll
+                for (int j = 0; j < Q; ++j) {
+                    const T y0 = Z[0][k] * c.hat[0][j] + Z[2][k] * c.hat[1][j];   // cx = 0
+                    const T y1 = Z[1][k] * c.hat[0][j] + Z[3][k] * c.hat[1][j];   // cx = 1
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) R[i + Q * (j + Q * k)] += y0 * c.hat[0][i] + y1 * c.hat[1][i];
+                }
+#pragma unroll
+            for (int e = 0; e < NL; ++e) sA[lane * NL + e] = R[e];
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (full) {
+            if (lane == 0) {
+                bulk_store(u + cell0 * NL, sA, (unsigned)(W * NL * sizeof(T)));
+                bulk_commit();
+            }
+        } else {
+            for (int e = lane; e < ncl * NL; e += W) u[cell0 * NL + e] = sA[e];
+        }
+    }
+    cells_write_traces<T, Q>(c, R, lane, active, cell, cell0, ncl, sB, tr);
+    if (e0 != nullptr && full && lane == 0) bulk_wait_read_all();
+}
+
+template <typename T, int Q>
+__global__ void __launch_bounds__(32) k_project_cells(const __grid_constant__ DGConst<T> c, T *__restrict__ u,
+                                                      const T *__restrict__ e0, T *__restrict__ tr) {
+    project_cells_body<T, Q>(c, (int64_t)blockIdx.x * CellGeo<T, Q>::W, u, e0, tr);
 }
 
 // P = S^T M (TRANSPOSE false) or its transpose M S, for a q x q factor S
