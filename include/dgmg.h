@@ -465,11 +465,13 @@ int dgmg_profile_read(dgmg_ctx *ctx, double *ms, long long *launches, int nstage
 /* Number of CUDA kernels this library has launched in this process. */
 long long dgmg_kernel_launches(void);
 
-/* Bounded device-side waits (mbarrier phases of the bulk copies in the FP32
- * smoothing kernel) that ran out of iterations on the CURRENT device since the
- * library was loaded; 0 in every healthy run. A kernel whose wait runs out
- * abandons its cells for that launch (their u and traces keep the old values),
- * so a nonzero count means the results of that run are not to be trusted.
+/* Bounded device-side waits that ran out of iterations on the CURRENT device
+ * since the library was loaded: the mbarrier phases of the bulk copies in the
+ * one-thread-per-cell kernels, and the grid barrier of the Q1 cycle run as one
+ * cooperative launch. 0 in every healthy run. A smoothing kernel whose wait
+ * runs out abandons its cells for that launch (their u and traces keep the old
+ * values); after a grid-barrier wait ran out, every later Q1 cycle launch
+ * returns without work. A nonzero count means the results are not to be trusted.
  * Synchronous (reads device memory); *count (HOST) receives the number.
  * Returns DGMG_EINVAL for a NULL pointer, DGMG_ECUDA if the read fails. */
 int dgmg_wait_timeouts(unsigned long long *count);

@@ -624,6 +624,74 @@ int cg_vcycle(dgmg_ctx &C, int l, cudaStream_t s, T **result) {
     return DGMG_OK;
 }
 
+// The whole Q1 cycle from level 0 (RHS in cg[0].b) as one cooperative launch
+// when the context has its plan; the launch per step otherwise.
+template <typename T>
+int q1_cycle(dgmg_ctx &C, cudaStream_t s, T **result) {
+    auto &lv = cgl<T>(C);
+    Q1Plan<T> *plan = q1plan<T>(C);
+    if (!plan || C.q1_blocks <= 0) return cg_vcycle<T>(C, 0, s, result);
+    unsigned long long *bar = C.q1bar + (std::is_same<T, float>::value ? 1 : 0);
+    LC(launch_q1_cycle<T>(C.dim, plan, bar, C.q1_blocks, s));
+    *result = lv.size() == 1 ? lv[0].u[0] : lv[0].u[(C.opts.nu_pre + C.opts.nu_post) & 1];
+    return DGMG_OK;
+}
+
+// Build the plan of q1_cycle for precision T. The cooperative launch is kept
+// only if it can also be captured into a CUDA graph (the solve replays its
+// iterations as graphs); otherwise the Q1 levels keep one launch per step.
+template <typename T>
+int setup_q1_plan(dgmg_ctx &C) {
+    auto &lv = cgl<T>(C);
+    const int nl = (int)lv.size();
+    if (nl == 0 || nl > Q1_MAXLEV || C.q1_blocks <= 0) return DGMG_OK;
+    Q1Plan<T> h;
+    std::memset(&h, 0, sizeof(h));
+    h.nlev = nl;
+    h.nu_pre = C.opts.nu_pre;
+    h.nu_post = C.opts.nu_post;
+    h.omega = (T)C.opts.omega_cg;
+    h.ncoarse = lv[nl - 1].L.nv;
+    // the trailing levels small enough for one block: up to 512 vertices in
+    // FP32; in FP64 (about 2 FMA per clock per SM) up to 128
+    const int64_t local_max = std::is_same<T, float>::value ? 512 : 128;
+    h.local_from = nl;
+    while (h.local_from > 0 && lv[h.local_from - 1].L.nv <= local_max) --h.local_from;
+    h.Ainv = C.coarse_inv;
+    for (int l = 0; l < nl; ++l) {
+        h.L[l] = lv[l].L;
+        h.u0[l] = lv[l].u[0];
+        h.u1[l] = lv[l].u[1];
+        h.b[l] = lv[l].b;
+        h.r[l] = lv[l].r;
+    }
+    Q1Plan<T> *d = nullptr;
+    RC(C.upload(&d, std::vector<Q1Plan<T>>{h}));
+    if (!C.q1bar) {
+        RC(C.alloc(&C.q1bar, 2));
+        DG_CUDA(cudaMemsetAsync(C.q1bar, 0, 2 * sizeof(unsigned long long), C.setup_stream));
+    }
+    static std::atomic<int> capture_ok{-1};   // per precision: unknown, no, yes
+    if (capture_ok.load() < 0 && C.capture_stream) {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        bool ok = cudaStreamBeginCapture(C.capture_stream, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+        if (ok) {
+            const cudaError_t el = launch_q1_cycle<T>(C.dim, d, C.q1bar, C.q1_blocks, C.capture_stream);
+            g_kernel_launches.fetch_sub(1);   // captured, not launched
+            const cudaError_t ee = cudaStreamEndCapture(C.capture_stream, &graph);
+            ok = el == cudaSuccess && ee == cudaSuccess && graph &&
+                 cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        capture_ok.store(ok ? 1 : 0);
+    }
+    if (capture_ok.load() == 1) q1plan<T>(C) = d;   // else the plan stays unused
+    return DGMG_OK;
+}
+
 // DG level l of the hierarchy in precision T (0 = the finest), and its tiles
 // (the finest level's tuned ones; launcher defaults below).
 template <typename T>
@@ -663,7 +731,7 @@ int coarse_correction(dgmg_ctx &C, int l, T *z, const T *b, int cur, cudaStream_
         C.prof.begin(ST_CG, s);
         LC(launch_corner_gather<T>(C.dim, C.n, D.corners, lv[0].b, s));
         T *e0 = nullptr;
-        RC(cg_vcycle<T>(C, 0, s, &e0));
+        RC(q1_cycle<T>(C, s, &e0));
         C.prof.end(s);
         C.prof.begin(ST_PROJECT, s);
         LC(launch_project<T>(C.dim, S.q, D.c, tproj, z, e0, D.tr[0], s));   // z += P e0
@@ -1038,11 +1106,19 @@ int create_ctx(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_opt
     const DGSpace S0 = finest_space(*C);
     RC(setup_dg<double>(*C, S0, C->d64, kap, !(flags & CREATE_NO_FP64_SMOOTHER)));
     trace.mark("dg fp64 (factors on the device)");
-    if (!(flags & CREATE_NO_FP64_Q1)) RC(setup_cg<double>(*C, C->cg64));
+    if (!(flags & CREATE_NO_SOLVER)) {   // a batch member runs its Q1 levels in the batch's kernels
+        // the Q1 cycle as one cooperative launch, one block per SM
+        C->q1_blocks = std::max(0, q1_cycle_max_blocks<double>(C->dim));
+    }
+    if (!(flags & CREATE_NO_FP64_Q1)) {
+        RC(setup_cg<double>(*C, C->cg64));
+        RC(setup_q1_plan<double>(*C));
+    }
     trace.mark("cg upload");
     if (o.precision == DGMG_MIXED_FP32) {
         RC(setup_dg<float>(*C, S0, C->d32, kap, true, nullptr, C->d64.fd));
         RC(setup_cg<float>(*C, C->cg32));
+        RC(setup_q1_plan<float>(*C));
         RC(C->alloc(&C->r32, C->ndof));
         RC(C->alloc(&C->z32, C->ndof));
         if (o.outer == DGMG_OUTER_RELIABLE) {
@@ -1388,6 +1464,8 @@ int dgmg_estimate_bytes(const dgmg_mesh *mesh, int p, const dgmg_opts *opts, siz
     size_t total = sz(nv * nv, 8) + dg64 + cg64 + 5 * sz(ndof, 8) + sz(S_NSCAL, 8) + sz(2 * DOT_BLOCKS, 8) +
                    sz(p + 2, 8) + sz((int64_t)q * (p + 2), 8) + sz(3 * (p + 2), 8);
     if (mixed) total += dg32 + cg32 + 2 * sz(ndof, 4) + (reliable ? 4 * sz(ndof, 4) : 0);
+    if (q1_cycle_max_blocks<double>(dim) > 0)   // the plans of the cooperative Q1 cycle and their barrier
+        total += sizeof(Q1Plan<double>) + (mixed ? sizeof(Q1Plan<float>) : 0) + 2 * sizeof(unsigned long long);
     if (o.p_coarsening == 1 && p >= 2) {
         // lower DG levels p-1 .. 1 (kappa shared with the finest level): factors,
         // traces, corners, iterate, right-hand side and residual; FP64 also the
@@ -1432,11 +1510,12 @@ long long dgmg_kernel_launches(void) { return g_kernel_launches.load(); }
 
 int dgmg_wait_timeouts(unsigned long long *count) {
     if (!count) return fail(DGMG_EINVAL, "dgmg_wait_timeouts: count is NULL");
-    unsigned long long a = 0, b = 0;
+    unsigned long long a = 0, b = 0, c = 0;
     cudaError_t e = wait_timeouts_fp32(&a);
     if (e == cudaSuccess) e = wait_timeouts_fp64(&b);
+    if (e == cudaSuccess) e = q1_barrier_timeouts(&c);
     if (e != cudaSuccess) return cuda_fail(e, "dgmg_wait_timeouts");
-    *count = a + b;
+    *count = a + b + c;
     return DGMG_OK;
 }
 

@@ -138,6 +138,12 @@ struct dgmg_ctx {
     std::vector<CGLevelHost> lv;
     int64_t ncoarse = 0;
     double *coarse_inv = nullptr;
+    // the Q1 cycle as one cooperative launch (q1_blocks > 0): per precision its
+    // plan and two barrier words; q1_blocks = 0 keeps the launch per step
+    Q1Plan<double> *q1plan64 = nullptr;
+    Q1Plan<float> *q1plan32 = nullptr;
+    unsigned long long *q1bar = nullptr;          // arrival counters [FP64, FP32]
+    int q1_blocks = 0;
     DGDev<double> d64;
     DGDev<float> d32;
     std::vector<CGDev<double>> cg64;
@@ -307,6 +313,13 @@ inline const DGDev<T> &dg(const dgmg_ctx &C) {
         return C.d32;
     else
         return C.d64;
+}
+template <typename T>
+inline Q1Plan<T> *&q1plan(dgmg_ctx &C) {
+    if constexpr (std::is_same<T, float>::value)
+        return C.q1plan32;
+    else
+        return C.q1plan64;
 }
 template <typename T>
 inline std::vector<CGDev<T>> &cgl(dgmg_ctx &C) {

@@ -155,6 +155,30 @@ struct BatchCG {
     int n[3];
     const T *corners;
 };
+// The Q1 h-cycle of one problem as one cooperative launch: every level's
+// operator and transfer tables, its vectors, the coarsest inverse.
+constexpr int Q1_MAXLEV = 24;
+constexpr int Q1_TPB = 256;
+template <typename T>
+struct Q1Plan {
+    int nlev, nu_pre, nu_post;
+    int local_from;        // levels >= this one run in one block (nlev: none)
+    T omega;
+    int64_t ncoarse;
+    const double *Ainv;
+    CGLevelDev<T> L[Q1_MAXLEV];
+    T *u0[Q1_MAXLEV], *u1[Q1_MAXLEV], *b[Q1_MAXLEV], *r[Q1_MAXLEV];
+};
+// e on level 0 (u0 or u1 of level 0, by the parity of nu_pre + nu_post) from b
+// on level 0; bar: the plan's own arrival counter (zero before its first
+// launch; every launch on it with the same number of blocks)
+template <typename T>
+cudaError_t launch_q1_cycle(int dim, const Q1Plan<T> *plan, unsigned long long *bar, int blocks, cudaStream_t s);
+// the most blocks of the cooperative launch (one per SM), 0 if it cannot run
+template <typename T>
+int q1_cycle_max_blocks(int dim);
+cudaError_t q1_barrier_timeouts(unsigned long long *count);
+
 // CTA -> (descriptor, first vertex (or row) of the CTA)
 struct VertMap {
     int desc, v0;

@@ -392,3 +392,34 @@ def test_update_kappa_equals_fresh_context(dgmg, n, p, prec, gradual):
     assert np.linalg.norm(_np(x) - x_ref) <= 1e-9 * np.linalg.norm(x_ref)
     with pytest.raises(dgmg.DGMGError):
         ctx.update_kappa(-kap2)
+
+
+@pytest.mark.parametrize("n,p,nu,prec", [((24, 20, 18), 1, (2, 2), 0), ((24, 20, 18), 1, (3, 1), 0),
+                                         ((17, 33, 9), 1, (1, 2), 0), ((70, 52), 1, (2, 2), 0),
+                                         ((61, 45), 2, (0, 3), 0), ((24, 20, 18), 1, (2, 2), 1),
+                                         ((48, 44, 40), 1, (2, 2), 0)])
+def test_vcycle_q1_one_launch(dgmg, n, p, nu, prec):
+    """The Q1 levels of a V-cycle run as one cooperative launch: the finer
+    levels on the whole grid with grid-wide barriers, the small levels (up to 512
+    vertices in FP32, 128 in FP64) and the coarsest solve in one block. Meshes
+    with several grid-wide
+    levels, odd and even numbers of Jacobi steps (the result buffer flips with
+    their parity) and nu_pre = 0 (no pre-smoothing: a zeroed iterate)."""
+    kap = _kappa(n, "lognormal", 4)
+    mesh = sipg.Mesh(n, p)
+    ctx = dgmg.Context(n, p, kap, nu_pre=nu[0], nu_post=nu[1],
+                       precision=dgmg.DGMG_MIXED_FP32 if prec else dgmg.DGMG_FP64)
+    hier = hpmg.Hierarchy(mesh, kap, nu_pre=nu[0], nu_post=nu[1])
+    assert hier.A[0].shape[0] > 512                 # at least one level on the whole grid
+    r = np.random.default_rng(11).normal(size=mesh.ndof)
+    e = torch.empty(mesh.ndof, dtype=torch.float64, device=DEV)
+    ctx.vcycle(_t(r), e)
+    torch.cuda.synchronize()
+    before = dgmg.kernel_launches()
+    ctx.vcycle(_t(r), e)
+    torch.cuda.synchronize()
+    launches = dgmg.kernel_launches() - before
+    # a launch per step would take 7 or more for each of the hier.nlevels - 1 levels
+    assert launches <= sum(nu) + 8 < sum(nu) + 1 + 7 * (hier.nlevels - 1)
+    assert _rel(_np(e), hier.vcycle(r)) <= (2e-5 if prec else 1e-11)
+    assert dgmg.wait_timeouts() == 0
