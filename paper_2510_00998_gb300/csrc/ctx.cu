@@ -653,8 +653,10 @@ int setup_q1_plan(dgmg_ctx &C) {
     h.omega = (T)C.opts.omega_cg;
     h.ncoarse = lv[nl - 1].L.nv;
     // the trailing levels small enough for one block: up to 512 vertices in
-    // FP32; in FP64 (about 2 FMA per clock per SM) up to 128
-    const int64_t local_max = std::is_same<T, float>::value ? 512 : 128;
+    // FP32; in FP64 (about 2 FMA per clock per SM) only a one-vertex coarsest
+    // level (measured on the 32^3, p = 3 hierarchy: a 27-vertex level is
+    // faster on the whole grid, 146 against 159 us per cycle)
+    const int64_t local_max = std::is_same<T, float>::value ? 512 : 1;
     h.local_from = nl;
     while (h.local_from > 0 && lv[h.local_from - 1].L.nv <= local_max) --h.local_from;
     h.Ainv = C.coarse_inv;

@@ -401,7 +401,8 @@ def test_update_kappa_equals_fresh_context(dgmg, n, p, prec, gradual):
 def test_vcycle_q1_one_launch(dgmg, n, p, nu, prec):
     """The Q1 levels of a V-cycle run as one cooperative launch: the finer
     levels on the whole grid with grid-wide barriers, the small levels (up to 512
-    vertices in FP32, 128 in FP64) and the coarsest solve in one block. Meshes
+    vertices in FP32; in FP64 only a one-vertex coarsest level) and the coarsest
+    solve in one block. Meshes
     with several grid-wide
     levels, odd and even numbers of Jacobi steps (the result buffer flips with
     their parity) and nu_pre = 0 (no pre-smoothing: a zeroed iterate)."""
