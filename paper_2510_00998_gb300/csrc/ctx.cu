@@ -637,6 +637,15 @@ int q1_cycle(dgmg_ctx &C, cudaStream_t s, T **result) {
     return DGMG_OK;
 }
 
+// Blocks of the cooperative Q1 cycle: as many as the kernels of both
+// precisions in use keep co-resident (every launch on a plan's arrival counter
+// has the same block count); 0 where the launch is not possible.
+static int q1_blocks_for(int dim, bool mixed) {
+    int qb = q1_cycle_max_blocks<double>(dim);
+    if (mixed) qb = std::min(qb, q1_cycle_max_blocks<float>(dim));
+    return std::max(0, qb);
+}
+
 // Build the plan of q1_cycle for precision T. The cooperative launch is kept
 // only if it can also be captured into a CUDA graph (the solve replays its
 // iterations as graphs); otherwise the Q1 levels keep one launch per step.
@@ -1109,8 +1118,7 @@ int create_ctx(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_opt
     RC(setup_dg<double>(*C, S0, C->d64, kap, !(flags & CREATE_NO_FP64_SMOOTHER)));
     trace.mark("dg fp64 (factors on the device)");
     if (!(flags & CREATE_NO_SOLVER)) {   // a batch member runs its Q1 levels in the batch's kernels
-        // the Q1 cycle as one cooperative launch, one block per SM
-        C->q1_blocks = std::max(0, q1_cycle_max_blocks<double>(C->dim));
+        C->q1_blocks = q1_blocks_for(C->dim, o.precision == DGMG_MIXED_FP32);
     }
     if (!(flags & CREATE_NO_FP64_Q1)) {
         RC(setup_cg<double>(*C, C->cg64));
@@ -1466,7 +1474,7 @@ int dgmg_estimate_bytes(const dgmg_mesh *mesh, int p, const dgmg_opts *opts, siz
     size_t total = sz(nv * nv, 8) + dg64 + cg64 + 5 * sz(ndof, 8) + sz(S_NSCAL, 8) + sz(2 * DOT_BLOCKS, 8) +
                    sz(p + 2, 8) + sz((int64_t)q * (p + 2), 8) + sz(3 * (p + 2), 8);
     if (mixed) total += dg32 + cg32 + 2 * sz(ndof, 4) + (reliable ? 4 * sz(ndof, 4) : 0);
-    if (q1_cycle_max_blocks<double>(dim) > 0)   // the plans of the cooperative Q1 cycle and their barrier
+    if (q1_blocks_for(dim, mixed) > 0)   // the plans of the cooperative Q1 cycle and their counters
         total += sizeof(Q1Plan<double>) + (mixed ? sizeof(Q1Plan<float>) : 0) + 2 * sizeof(unsigned long long);
     if (o.p_coarsening == 1 && p >= 2) {
         // lower DG levels p-1 .. 1 (kappa shared with the finest level): factors,
