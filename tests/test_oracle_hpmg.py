@@ -112,6 +112,31 @@ def test_vcycle_matches_dense_error_propagation(n, p, kind):
     assert np.max(np.abs(np.linalg.eigvals(E))) < 1.0
 
 
+@pytest.mark.parametrize("n,p,nu", [((6, 5), 2, (0, 3)), ((6, 6), 1, (3, 1)), ((4, 3, 4), 1, (1, 2))])
+def test_vcycle_unequal_smoothing_counts(n, p, nu):
+    """V(nu_pre, nu_post) with nu_pre != nu_post: the cycle equals the dense
+    error-propagation product, and its transpose is the cycle with the counts
+    swapped (the Jacobi and block-Jacobi iterations and every Galerkin coarse
+    correction are self-adjoint in the A inner product, so the A-adjoint of
+    J^b C J^a is J^a C J^b on every level), which a swapped order of pre- and
+    post-smoothing, or a lost step, breaks."""
+    mesh = sipg.Mesh(n, p)
+    kap = np.exp(np.random.default_rng(2).normal(size=mesh.ncell))
+    h12 = hpmg.Hierarchy(mesh, kap, nu_pre=nu[0], nu_post=nu[1])
+    h21 = hpmg.Hierarchy(mesh, kap, nu_pre=nu[1], nu_post=nu[0])
+    assert h12.nlevels >= 2
+    Ad = sipg.assemble(mesh, kap).toarray()
+    B, _ = _dense_vcycle(h12, Ad)
+    rng = np.random.default_rng(6)
+    r, s = rng.normal(size=mesh.ndof), rng.normal(size=mesh.ndof)
+    z = h12.vcycle(r)
+    assert np.abs(z - B @ r).max() <= 1e-12 * np.abs(z).max()
+    lhs, rhs = s @ z, r @ h21.vcycle(s)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs) + 1e-14
+    # and the cycle itself is not symmetric for unequal counts
+    assert abs(s @ z - r @ h12.vcycle(s)) > 1e-8 * abs(lhs)
+
+
 @pytest.mark.parametrize("n,p,kind", [((8, 8), 2, "one"), ((4, 4, 4), 2, "lognormal"), ((5, 5), 3, "lognormal")])
 def test_pcg_matches_direct_solve(n, p, kind):
     mesh = sipg.Mesh(n, p)
