@@ -235,9 +235,10 @@ __global__ void k_coarse_solve(int64_t nc, const double *__restrict__ Ainv, cons
 }
 
 // ---- the whole Q1 h-cycle of one problem in one cooperative launch: every step
-// of cg_vcycle (point Jacobi, residual, restriction, the dense coarsest solve,
-// prolongation) as a grid-stride loop over the level's vertices, the steps
-// separated by a grid-wide barrier instead of kernel boundaries. The vectors
+// of the launch-per-step cycle (point Jacobi, residual, restriction, the dense
+// coarsest solve, prolongation) as a loop over the level's vertices split among
+// the blocks, the steps separated by a grid-wide barrier instead of kernel
+// boundaries. The vectors
 // are written and read again inside the one launch, so the per-vertex bodies
 // take them through plain pointers (no __restrict__: no loads through the
 // non-coherent read-only cache); only the stencils and tables use __ldg.
