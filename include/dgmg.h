@@ -239,7 +239,11 @@ int dgmg_smooth(dgmg_ctx *ctx, double *u, const double *b, int nsteps, void *str
  * levels and the dense coarsest solve, p-prolongation fused into the next
  * projection, nu_post smoothing steps. In DGMG_MIXED_FP32 precision the cycle
  * runs in FP32 (r rounded on entry, e widened on exit); the coarsest solve is
- * FP64 in both. r and e are FP64 and must not overlap.
+ * FP64 in both. r and e are FP64 and must not overlap. The Q1 part is one
+ * cooperative kernel launch (all its blocks co-resident, steps separated by a
+ * bounded grid barrier; see dgmg_wait_timeouts) where the device supports it
+ * and the launch can be captured into a CUDA graph, else one launch per step;
+ * the results agree to rounding.
  */
 int dgmg_vcycle(dgmg_ctx *ctx, const double *r, double *e, void *stream);
 
