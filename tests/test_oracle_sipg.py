@@ -208,3 +208,67 @@ def test_diagonal_block_is_a_kronecker_sum_inverted_by_fast_diagonalisation(n, p
         assert L.min() > 0
         Ainv = Sf @ np.diag(1.0 / L) @ Sf.T
         assert np.abs(Ainv - np.linalg.inv(Bc)).max() <= 1e-11 * np.abs(Ainv).max()
+
+
+def _interior_kron_block(mesh):
+    """Closed form of the diagonal block of a cell whose facets are all interior,
+    for kappa = 1 on the cell and its neighbours: the Kronecker sum over axes of
+    Kt_a = K + 1/2 (e0 d0^T + d0 e0^T) + gamma e0 e0^T - 1/2 (ep dp^T + dp ep^T)
+    + gamma ep ep^T with 1D masses on the other axes (Sec. 4.1 block structure;
+    every facet term of an interior facet carries the weight 1/2 of the averages)."""
+    d = mesh.d
+    Kt = []
+    for a in range(d):
+        e0, ep, d0, dp, g = mesh.e0, mesh.ep, mesh.d0[a], mesh.dp[a], mesh.gamma(a)
+        Kt.append(mesh.K[a] + 0.5 * (np.outer(e0, d0) + np.outer(d0, e0)) + g * np.outer(e0, e0)
+                  - 0.5 * (np.outer(ep, dp) + np.outer(dp, ep)) + g * np.outer(ep, ep))
+    A = np.zeros((mesh.nloc, mesh.nloc))
+    for a in range(d):
+        f = np.ones((1, 1))
+        for b in reversed(range(d)):
+            f = np.kron(f, Kt[a] if b == a else mesh.M[b])
+        A += f
+    return A
+
+
+@pytest.mark.parametrize("n,p", [((4, 3, 5), 2), ((3, 4), 3), ((3, 3, 3), 1), ((5, 3), 4)])
+def test_interior_only_block_is_an_interior_cells_assembled_block(n, p):
+    """Technique 4 (Sec. 4.1): every cell uses the diagonal block of an interior
+    cell. With kappa = 1 that block is read off the assembled matrix (quadrature
+    of the weak form, facet by facet) at a cell with no boundary facet, and it
+    equals the closed-form Kronecker sum of the all-interior 1D operators."""
+    mesh = sipg.Mesh(n, p)
+    A = sipg.assemble(mesh).toarray()
+    nn = list(mesh.n) + [1] * (3 - mesh.d)
+    ci = [1, 1, 0 if mesh.d == 2 else 1]
+    c = ci[0] + nn[0] * (ci[1] + nn[1] * ci[2])
+    nl = mesh.nloc
+    Aint = A[c * nl:(c + 1) * nl, c * nl:(c + 1) * nl]
+    Kron = _interior_kron_block(mesh)
+    assert np.abs(Kron - Aint).max() <= 1e-12 * np.abs(Aint).max()
+    B = sipg.BlockJacobi(mesh, interior_only=True).B
+    for k in range(mesh.ncell):
+        assert np.abs(B[k] - Aint).max() <= 1e-12 * np.abs(Aint).max()
+
+
+@pytest.mark.parametrize("n,p", [((4, 3, 5), 2), ((3, 4), 3), ((5, 3), 2)])
+def test_interior_only_block_scales_with_the_cells_own_kappa(n, p):
+    """With a lognormal kappa the Technique 4 block of every cell, boundary and
+    corner cells included, is kappa_K times the kappa = 1 interior block (the
+    reading of Technique 4 for cellwise kappa: the interior block with the
+    cell's own coefficient on the cell and on all its facets). On a cell that
+    touches the boundary it differs from the exact block, whose boundary facets
+    carry the weight 1 instead of 1/2, and so does its inverse."""
+    mesh = sipg.Mesh(n, p)
+    kap = np.exp(np.random.default_rng(13).normal(size=mesh.ncell))
+    Kron = _interior_kron_block(mesh)
+    B = sipg.BlockJacobi(mesh, kap, interior_only=True).B
+    exact = sipg.block_diagonal(mesh, kap)
+    nn = list(mesh.n) + [1] * (3 - mesh.d)
+    for k in range(mesh.ncell):
+        ref = kap[k] * Kron
+        assert np.abs(B[k] - ref).max() <= 1e-12 * np.abs(ref).max()
+        ci = [k % nn[0], (k // nn[0]) % nn[1], k // (nn[0] * nn[1])]
+        on_boundary = any(ci[a] in (0, nn[a] - 1) for a in range(mesh.d))
+        if on_boundary:
+            assert np.abs(B[k] - exact[k]).max() > 1e-3 * np.abs(exact[k]).max()
