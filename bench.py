@@ -35,11 +35,12 @@ DEGREE = 3
 RTOL = 1e-10
 WORKLOAD = "sipg_3d_32^3_p3_kappa1_fp64_pcg_vcycle22"
 SAMPLE_CELLS = (16, 16, 16)      # bounded CPU sample: same p, 1/8 of the DoFs
-SAMPLE_STEPS = 60
-FP64_PEAK_TFLOPS = 1.25          # nominal GB300 dense FP64 (no FP64 entry in the measured peaks)
-# DRAM bytes (read + write) of one launch of k_smooth_cells<double,4> on this
-# workload, from one ncu capture (profiles/k_smooth_cells_fp64_32cube_p3.md)
-SMOOTH_TRAFFIC_BYTES = 115_310_336 + 10_941_184
+FP64_NOMINAL_TFLOPS = 1.25       # nominal GB300 dense FP64, context beside the measured peak
+# DRAM bytes (read + write) of one launch of the FP64 smoothing kernel on this
+# workload from one ncu capture, valid only for the kernel sources it was taken
+# on (SHA-256 of the files below); once they change, `traffic` reads null
+SMOOTH_TRAFFIC = {"kernel": "k_smooth_cells<double,4>", "bytes": None, "sources_sha256": None,
+                  "files": ("smooth_cells.cuh", "dg_kernels.cuh", "dg_fp64.cu")}
 
 
 def parse():
@@ -77,6 +78,28 @@ def reduce_max_sum(values, world, device):
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     dist.all_reduce(s, op=dist.ReduceOp.SUM)
     return float(t.item()), float(s.item())
+
+
+def sources_sha256(files):
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2510_00998_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def smooth_traffic(kernel):
+    """(bytes, note) of the recorded ncu capture if it was taken on the current
+    sources of `kernel`, else (None, why)."""
+    t = SMOOTH_TRAFFIC
+    if t["bytes"] is None or kernel != t["kernel"]:
+        return None, "no ncu capture recorded for this kernel"
+    sha = sources_sha256(t["files"])
+    if sha != t["sources_sha256"]:
+        return None, "kernel sources changed since the recorded ncu capture"
+    return t["bytes"], ("dram__bytes_read.sum + dram__bytes_write.sum of one launch, one ncu capture on these "
+                        f"kernel sources (sha256 {sha[:12]})")
 
 
 # ---------------------------------------------------------------- flop model
@@ -150,60 +173,133 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- CPU oracle
-def cpu_oracle_chunks(chunks, steps_per_chunk):
-    """Run the oracle's Alg. 4 smoothing steps on the bounded sample in a
-    single-threaded subprocess: one block-inverse set-up, then `chunks` timed
-    chunks of `steps_per_chunk` steps. Returns (ndof, [seconds per chunk])."""
-    code = f"""
+ORACLE_WORKER = r"""
 import json, os, sys, time
-sys.path.insert(0, {ROOT!r})
+sys.path.insert(0, {root!r})
 import numpy as np
 from oracle import sipg
-m = sipg.Mesh({SAMPLE_CELLS!r}, {DEGREE})
+m = sipg.Mesh({cells!r}, {degree})
 bj = sipg.BlockJacobi(m)
 rng = np.random.default_rng(0)
 u, b = rng.normal(size=m.ndof), rng.normal(size=m.ndof)
+u, _ = bj.step_alg4(u, b, 0.8, 1)
+open({ready!r} + str({wid}), "w").close()
+while not os.path.exists({go!r}):
+    time.sleep(0.01)
 secs = []
 for _ in range({chunks}):
     t = time.perf_counter()
-    u, _ = bj.step_alg4(u, b, 0.8, {steps_per_chunk})
+    u, _ = bj.step_alg4(u, b, 0.8, {steps})
     secs.append(time.perf_counter() - t)
 print(json.dumps({{"ndof": m.ndof, "seconds": secs}}))
 """
+
+
+def cpu_model():
+    """CPU model name of this host (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_run(workers, chunks, steps_per_chunk):
+    """The oracle's Alg. 4 smoothing steps on the bounded sample in `workers`
+    single-threaded processes at once (one per core, each its own replica of
+    the sample): every process does its block-inverse set-up and one warm-up
+    step, then all start together and time `chunks` chunks of
+    `steps_per_chunk` steps. Returns (ndof per replica, [[seconds per chunk]
+    per process])."""
+    tmp = tempfile.mkdtemp(prefix="oracle_")
+    ready, go = os.path.join(tmp, "ready"), os.path.join(tmp, "go")
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
-    r = json.loads(out.stdout.strip().splitlines()[-1])
-    return r["ndof"], r["seconds"]
+    procs = []
+    for w in range(workers):
+        code = ORACLE_WORKER.format(root=ROOT, cells=SAMPLE_CELLS, degree=DEGREE, ready=ready, wid=w, go=go,
+                                    chunks=chunks, steps=steps_per_chunk)
+        procs.append(subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE,
+                                      stderr=subprocess.PIPE, text=True, env=env))
+    try:
+        while sum(os.path.exists(ready + str(w)) for w in range(workers)) < workers:
+            if any(p.poll() not in (None, 0) for p in procs):
+                raise RuntimeError("oracle worker failed: " + "".join(p.stderr.read() for p in procs if p.poll()))
+            time.sleep(0.02)
+        open(go, "w").close()
+        res = []
+        for p in procs:
+            out, err = p.communicate()
+            if p.returncode != 0:
+                raise RuntimeError("oracle worker failed: " + err)
+            res.append(json.loads(out.strip().splitlines()[-1]))
+    finally:
+        for p in procs:
+            if p.poll() is None:
+                p.kill()
+        for f in os.listdir(tmp):
+            os.unlink(os.path.join(tmp, f))
+        os.rmdir(tmp)
+    return res[0]["ndof"], [r["seconds"] for r in res]
 
 
-def cpu_oracle_rate(steps):
-    ndof, secs = cpu_oracle_chunks(1, steps)
-    return ndof * steps / secs[0] / 1e9, secs[0], ndof
+def oracle_rate(workers, chunks=6, steps=8):
+    """Aggregate GDoF/s of `workers` concurrent oracle processes: per process the
+    median of its chunks after the first (a warm-up), summed over processes."""
+    ndof, secs = oracle_run(workers, chunks, steps)
+    rates = [ndof * steps / statistics.median(s[1:]) / 1e9 for s in secs]
+    return sum(rates), secs
 
 
-def sample_text(steps):
-    return (f"oracle Alg. 4 smoothing steps on {SAMPLE_CELLS[0]}x{SAMPLE_CELLS[1]}x{SAMPLE_CELLS[2]} cells, p={DEGREE} "
-            f"(1/8 of the workload's DoF, same degree), {steps} steps after the block-inverse set-up, "
-            f"one thread, FP64")
+def sample_text(steps, workers):
+    who = "one thread" if workers == 1 else f"{workers} single-threaded processes at once, one replica each"
+    return (f"oracle Alg. 4 smoothing steps on {SAMPLE_CELLS[0]}x{SAMPLE_CELLS[1]}x{SAMPLE_CELLS[2]} cells, "
+            f"p={DEGREE} (1/8 of the workload's DoF, same degree), chunks of {steps} steps after the "
+            f"block-inverse set-up, median of 5 chunks after one warm-up chunk, {who}, FP64")
+
+
+def cpu_baseline():
+    """The oracle on all host cores (the reported baseline) and on one core."""
+    ncores = os.cpu_count() or 1
+    v_all, _ = oracle_rate(ncores)
+    v_one, _ = oracle_rate(1)
+    return {"value": v_all, "unit": "GDoF/s", "cores": ncores, "kind": "oracle", "sample": sample_text(8, ncores),
+            "nproc": ncores, "cpu_model": cpu_model(),
+            "one_core": {"value": v_one, "unit": "GDoF/s", "cores": 1, "sample": sample_text(8, 1)}}
 
 
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    steps_per = 10
-    ndof, allsecs = cpu_oracle_chunks(args.warmup + args.steps, steps_per)
-    secs = allsecs[args.warmup:]
-    value = ndof * steps_per * len(secs) / sum(secs) / 1e9
+    ncores = os.cpu_count() or 1
+    steps_per = 4
+    ndof, secs = oracle_run(ncores, args.warmup + args.steps, steps_per)
+    timed = [s[args.warmup:] for s in secs]
+    # per bench step: all processes' DoF x steps over the slowest process's chunk time
+    per_step = [max(s[k] for s in timed) for k in range(args.steps)]
+    value = ncores * ndof * steps_per * args.steps / sum(per_step) / 1e9
+    text = (f"oracle Alg. 4 smoothing steps on {SAMPLE_CELLS[0]}x{SAMPLE_CELLS[1]}x{SAMPLE_CELLS[2]} cells, "
+            f"p={DEGREE} (1/8 of the workload's DoF, same degree), {steps_per} steps per bench step in each of "
+            f"{ncores} single-threaded processes at once (one replica each), after the block-inverse set-up, FP64")
     line = {
         "impl": "reference", "metric": "GDoF/s per smoothing step", "value": value, "unit": "GDoF/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * sum(secs) / len(secs), "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1e3 * sum(per_step) / len(per_step), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": sample_text(steps_per)},
-        "cpu_baseline": {"value": value, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
-                         "sample": sample_text(steps_per)},
+        "config": {"workload": WORKLOAD, "sample": text},
+        "cpu_baseline": {"value": value, "unit": "GDoF/s", "cores": ncores, "kind": "oracle", "sample": text,
+                         "nproc": ncores, "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -373,11 +469,16 @@ def run_gb300(args):
     units_local = float(ndof) * smooth_steps_total
     t_max, units = reduce_max_sum((total_ms, units_local), world, dev)
     value = units / (t_max * 1e-3) / 1e9
-    # roofline of the dominant kernel (the fused smoothing step)
+    # roofline of the dominant kernel (the fused smoothing step): FP64-pipe
+    # bound, against the FP64 FMA-loop peak measured here, in this run
     sm_ms, sm_n = prof["smooth"]
     avg_ms = sm_ms / max(sm_n, 1)
     flops = smooth_flops(N_CELLS, q)
     achieved = flops / (avg_ms * 1e-3) / 1e12
+    fp64_peak = dgmg.fma_peak(0)
+    fp32_peak = dgmg.fma_peak(1)
+    fp32x2_peak = dgmg.fma_peak(2)
+    survey_flops = 10 * d * q * ndof          # sum-factorised minimum, 10 d q flop per DoF
     shares = {k: round(v[0] / max(sum(w[0] for w in prof.values()), 1e-30), 4) for k, v in prof.items()}
 
     # end to end through the host-buffer entry point
@@ -411,11 +512,11 @@ def run_gb300(args):
     # the smoothing kernel the tuned context runs (tile 0 = one thread per cell)
     cells_kernel = ctx.info.tiles[1] == 0 and d == 3 and q <= 4
     smooth_kernel = f"k_smooth_cells<double,{q}>" if cells_kernel else f"k_smooth<{d},{q},double>"
+    traffic, traffic_note = smooth_traffic(smooth_kernel)
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
-            v, s, _ = cpu_oracle_rate(SAMPLE_STEPS)
-            cpu = {"value": v, "unit": "GDoF/s", "cores": 1, "kind": "oracle", "sample": sample_text(SAMPLE_STEPS)}
+            cpu = cpu_baseline()
         line = {
             "metric": "GDoF/s per smoothing step", "value": value, "unit": "GDoF/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
@@ -426,15 +527,17 @@ def run_gb300(args):
                        "outer": "FP64 PCG", "step": "one full solve from x=0",
                        "l2": "flushed (256 MB write) before every timed step, outside the step's events",
                        "parallelism": f"replicas x{world}"},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP64_PEAK_TFLOPS,
-                         "traffic": SMOOTH_TRAFFIC_BYTES if cells_kernel else None,
-                         "traffic_note": ("dram__bytes_read.sum + dram__bytes_write.sum of one launch, ncu "
-                                          "(profiles/k_smooth_cells_fp64_32cube_p3.md)") if cells_kernel else None,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                         "frac": achieved / fp64_peak,
+                         "traffic": traffic, "traffic_note": traffic_note,
                          "kernel": smooth_kernel, "avg_launch_ms": avg_ms,
                          "flops_per_launch": flops,
+                         "frac_at_10dq_flop_per_dof": survey_flops / (avg_ms * 1e-3) / 1e12 / fp64_peak,
                          "hbm_bytes_per_launch": smooth_bytes_per_cell(d, q) * ctx.info.ncell,
-                         "peak_note": "nominal FP64 1.25 TFLOP/s (FMA loop measured 1.257 on this pool)"},
+                         "peak_note": ("FP64 FMA-loop peak measured in this run (dgmg_fma_peak), of measured; "
+                                       f"nominal {FP64_NOMINAL_TFLOPS}"),
+                         "measured_peaks_tflops": {"fp64_fma": fp64_peak, "fp32_fma": fp32_peak,
+                                                   "fp32x2_fma": fp32x2_peak}},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_u / (e2e_t * 1e-3) / 1e9, "unit": "GDoF/s",
                     "h2d_bytes_per_step": 2 * 8 * ndof, "d2h_bytes_per_step": 8 * ndof},

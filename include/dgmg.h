@@ -48,6 +48,9 @@ extern "C" {
 #define DGMG_ENOTCONVERGED (-4)   /* maxit reached; x holds the last iterate          */
 #define DGMG_ENONFINITE (-5)      /* a NaN/Inf was detected in an input or residual   */
 #define DGMG_ECUDA (-6)           /* a CUDA runtime call failed                       */
+#define DGMG_ETIMEOUT (-7)        /* a bounded device-side wait ran out during the    */
+                                  /* call (see dgmg_wait_timeouts): its result is not */
+                                  /* to be trusted                                    */
 
 /* precision of the V-cycle used as preconditioner */
 #define DGMG_FP64 0               /* every stage in FP64                               */
@@ -262,7 +265,10 @@ int dgmg_vcycle(dgmg_ctx *ctx, const double *r, double *e, void *stream);
  * ||x_1 - x_0|| of the last cycle; rel_residual the true residual of the last
  * cycle). Blocks until done (it reads one scalar per
  * iteration). Returns DGMG_ENOTCONVERGED after maxit iterations,
- * DGMG_ENONFINITE if a residual norm is not finite.
+ * DGMG_ENONFINITE if a residual norm is not finite, DGMG_ETIMEOUT (which
+ * takes precedence) if a bounded device-side wait of the library ran out on
+ * this device while the solve ran (read from the wait counters at its start
+ * and end; see dgmg_wait_timeouts).
  */
 int dgmg_solve(dgmg_ctx *ctx, const double *b, double *x, dgmg_stats *stats, void *stream);
 
@@ -410,10 +416,11 @@ int dgmg_residual_restrict(dgmg_ctx *ctx, const double *u, const double *b,
 
 /*
  * Same result as dgmg_residual_restrict, without allocating anything: for
- * callers that cannot allocate device memory when they call (work recorded
- * into a CUDA graph during stream capture, loops that forbid allocation after
- * start-up, fixed memory budgets). The paper has no counterpart; this is an
- * interface variant of the residual + p-restriction stage.
+ * callers that cannot allocate device memory when they call (loops that
+ * forbid allocation after start-up, fixed memory budgets that leave no room
+ * for a per-context scratch, hosts whose allocator is not available at the
+ * point of the call). The paper has no counterpart; this is an interface
+ * variant of the residual + p-restriction stage.
  * The 2^d corner partial sums per cell go to one fixed device array of 2^21
  * doubles (16 MiB) that every GPU loading the library keeps until exit;
  * meshes needing more (more than 262,144 hexahedra or 524,288 quadrilaterals)
@@ -469,6 +476,18 @@ int dgmg_profile_read(dgmg_ctx *ctx, double *ms, long long *launches, int nstage
 /* Number of CUDA kernels this library has launched in this process. */
 long long dgmg_kernel_launches(void);
 
+/*
+ * Arithmetic peak of the current device, measured: a kernel in which every
+ * thread runs 8 independent chains of fused multiply-adds (one per SM-resident
+ * thread slot, a few tens of milliseconds), timed with CUDA events on
+ * `stream`. kind: 0 = FP64 FMA, 1 = FP32 FMA, 2 = FP32 FMA on packed pairs
+ * (two lanes of one instruction). *tflops (HOST) receives 2 x FMAs / time in
+ * TFLOP/s: the denominator of the roofline fraction of the FP64 kernels, which
+ * are bound by the FP64 pipe on this chip. Synchronous; allocates nothing.
+ * DGMG_EINVAL for another kind or a NULL pointer.
+ */
+int dgmg_fma_peak(int kind, double *tflops, void *stream);
+
 /* Bounded device-side waits that ran out of iterations on the CURRENT device
  * since the library was loaded: the mbarrier phases of the bulk copies in the
  * one-thread-per-cell kernels, and the grid barrier of the Q1 cycle run as one
@@ -476,6 +495,12 @@ long long dgmg_kernel_launches(void);
  * runs out abandons its cells for that launch (their u and traces keep the old
  * values); after a grid-barrier wait ran out, every later Q1 cycle launch
  * returns without work. A nonzero count means the results are not to be trusted.
+ * Solves (dgmg_solve, dgmg_solve_host, served requests through dgmg_poll)
+ * check the counters themselves and return DGMG_ETIMEOUT. Recovery: after a
+ * grid-barrier time-out every context of the process switches to the launch
+ * per step of the Q1 levels (their CUDA graphs are captured again), so later
+ * solves are correct; after a bulk-copy time-out nothing is switched off, and
+ * the next solve runs normally.
  * Synchronous (reads device memory); *count (HOST) receives the number.
  * Returns DGMG_EINVAL for a NULL pointer, DGMG_ECUDA if the read fails. */
 int dgmg_wait_timeouts(unsigned long long *count);

@@ -2,6 +2,8 @@
 // two-stage dot products (fixed grid, fixed reduction order), the CG updates
 // with step lengths read from device memory, precision casts, and the
 // right-hand-side quadrature (b_i = (f, phi_i)).
+#include <algorithm>
+
 #include "internal.h"
 
 namespace dgmg {
@@ -496,4 +498,102 @@ cudaError_t launch_accumulate_f2d(int64_t n, double *x, float *xs, cudaStream_t 
     return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------- FMA peak
+// Every thread runs CH independent chains of fused multiply-adds (x <- x a + b,
+// |a| < 1, so the values stay bounded); the chains' sum is stored only if it
+// equals a value it cannot reach, which keeps the work live without a store.
+__device__ double g_fma_sink;   // external linkage: the store cannot be dropped
+
+template <typename T, int CH>
+__global__ void __launch_bounds__(256) k_fma_loop(int iters, T a, T b) {
+    T x[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) x[c] = (T)(threadIdx.x + c) * (T)1e-3;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int c = 0; c < CH; ++c) x[c] = fma(x[c], a, b);
+    }
+    T s = T(0);
+#pragma unroll
+    for (int c = 0; c < CH; ++c) s += x[c];
+    if (s == (T)-1.0) g_fma_sink = (double)s;
+}
+
+// The same on packed pairs: one instruction updates two lanes of a float2.
+template <int CH>
+__global__ void __launch_bounds__(256) k_fma_loop_x2(int iters, float a, float b) {
+    float2 x[CH];
+    const float2 a2 = make_float2(a, a), b2 = make_float2(b, b);
+#pragma unroll
+    for (int c = 0; c < CH; ++c) x[c] = make_float2((threadIdx.x + c) * 1e-3f, (threadIdx.x + c) * 2e-3f);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int c = 0; c < CH; ++c) x[c] = __ffma2_rn(x[c], a2, b2);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) s += x[c].x + x[c].y;
+    if (s == -1.f) g_fma_sink = (double)s;
+}
+
 }  // namespace dgmg
+
+extern "C" int dgmg_fma_peak(int kind, double *tflops, void *stream) {
+    using namespace dgmg;
+    if (!tflops) return fail(DGMG_EINVAL, "dgmg_fma_peak: tflops is NULL");
+    if (kind < 0 || kind > 2) return fail(DGMG_EINVAL, "dgmg_fma_peak: kind must be 0, 1 or 2");
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0, sms = 0, per = 0;
+    DG_CUDA(cudaGetDevice(&dev));
+    DG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    constexpr int CH = 8, TPB = 256;
+    if (kind == 0)
+        DG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fma_loop<double, CH>, TPB, 0));
+    else if (kind == 1)
+        DG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fma_loop<float, CH>, TPB, 0));
+    else
+        DG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fma_loop_x2<CH>, TPB, 0));
+    const int blocks = sms * (per > 0 ? per : 1);
+    const double lanes = kind == 2 ? 2.0 : 1.0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    DG_CUDA(cudaEventCreate(&e0));
+    DG_CUDA(cudaEventCreate(&e1));
+    auto run = [&](int iters) -> cudaError_t {
+        count_launches(1);
+        if (kind == 0)
+            k_fma_loop<double, CH><<<blocks, TPB, 0, s>>>(iters, 0.999999, 1e-7);
+        else if (kind == 1)
+            k_fma_loop<float, CH><<<blocks, TPB, 0, s>>>(iters, 0.9999f, 1e-4f);
+        else
+            k_fma_loop_x2<CH><<<blocks, TPB, 0, s>>>(iters, 0.9999f, 1e-4f);
+        return cudaGetLastError();
+    };
+    // calibrate to about 30 ms, then take the best of three timed launches
+    int iters = kind == 0 ? 256 : 8192;
+    float ms = 0.f, best = 0.f;
+    cudaError_t e = run(iters);   // warm-up
+    for (int k = 0; k < 6 && e == cudaSuccess; ++k) {
+        e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess) e = run(iters);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) break;
+        if (k < 3) {
+            if (ms < 30.f) iters = (int)std::min<double>(iters * std::max(2.0, 30.0 / std::max(ms, 0.01f)), 1 << 26);
+            continue;
+        }
+        if (best == 0.f || ms < best) best = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "dgmg_fma_peak");
+    const double fmas = (double)blocks * TPB * CH * 4.0 * iters * lanes;
+    *tflops = 2.0 * fmas / (best * 1e-3) / 1e12;
+    return DGMG_OK;
+}

@@ -490,6 +490,9 @@ int q1_cycle_max_blocks(int dim) {
 cudaError_t q1_barrier_timeouts(unsigned long long *count) {
     return cudaMemcpyFromSymbol(count, g_q1_barrier_timeouts, sizeof(*count));
 }
+cudaError_t q1_barrier_timeouts_addr(unsigned long long **ptr) {
+    return cudaGetSymbolAddress((void **)ptr, g_q1_barrier_timeouts);
+}
 
 
 template <typename T>

@@ -18,6 +18,7 @@
 namespace dgmg {
 
 std::atomic<long long> g_kernel_launches{0};
+std::atomic<int> g_q1_one_launch_off{0};
 
 // ------------------------------------------------------------------- errors
 static thread_local std::string g_last_error;
@@ -630,7 +631,8 @@ template <typename T>
 int q1_cycle(dgmg_ctx &C, cudaStream_t s, T **result) {
     auto &lv = cgl<T>(C);
     Q1Plan<T> *plan = q1plan<T>(C);
-    if (!plan || C.q1_blocks <= 0) return cg_vcycle<T>(C, 0, s, result);
+    if (!plan || C.q1_blocks <= 0 || g_q1_one_launch_off.load(std::memory_order_relaxed))
+        return cg_vcycle<T>(C, 0, s, result);
     unsigned long long *bar = C.q1bar + (std::is_same<T, float>::value ? 1 : 0);
     LC(launch_q1_cycle<T>(C.dim, plan, bar, C.q1_blocks, s));
     *result = lv.size() == 1 ? lv[0].u[0] : lv[0].u[(C.opts.nu_pre + C.opts.nu_post) & 1];
@@ -1154,8 +1156,12 @@ int create_ctx(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_opt
     RC(C->alloc(&C->scal, S_NSCAL));
     RC(C->alloc(&C->partials, 2 * DOT_BLOCKS));
     {
-        cudaError_t e = cudaMallocHost((void **)&C->host_scal, sizeof(double) * S_NSCAL);
+        cudaError_t e = cudaMallocHost((void **)&C->host_scal, sizeof(double) * S_HOST);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
+        e = wait_timeouts_addr_fp32(&C->tmo_dev[0]);
+        if (e == cudaSuccess) e = wait_timeouts_addr_fp64(&C->tmo_dev[1]);
+        if (e == cudaSuccess) e = q1_barrier_timeouts_addr(&C->tmo_dev[2]);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
         e = cudaEventCreateWithFlags(&C->ev, cudaEventDisableTiming);
         if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
     }

@@ -160,7 +160,10 @@ struct dgmg_ctx {
     double *w_r = nullptr, *w_z = nullptr, *w_p = nullptr, *w_q = nullptr, *w_rold = nullptr;
     double *w_b = nullptr, *w_x = nullptr;        // dgmg_solve_host staging
     double *scal = nullptr, *partials = nullptr;  // device scalars
-    double *host_scal = nullptr;                  // pinned
+    double *host_scal = nullptr;                  // pinned: S_NSCAL scalars, then the wait-counter snapshots
+    // device addresses of the bounded-wait counters (FP32 and FP64 DG kernels,
+    // Q1 grid barrier) on the ctx's device
+    unsigned long long *tmo_dev[3] = {nullptr, nullptr, nullptr};
     double *quad_x1 = nullptr, *quad_V = nullptr, *quad_w = nullptr;
     std::vector<void *> allocs;
     size_t bytes = 0;
@@ -174,6 +177,7 @@ struct dgmg_ctx {
         const void *key = nullptr;                // user pointer the captured work depends on
         long long kernels = 0;                    // kernels inside (for the launch counter)
         int uses = 0;
+        int q1_off = 0;                           // g_q1_one_launch_off when captured
     };
     Graph g_iter, g_body;
     cudaStream_t capture_stream = nullptr;
@@ -242,6 +246,8 @@ struct dgmg_ctx {
 // slots of ctx->scal
 enum { S_RZ = 0, S_PQ = 1, S_BETA = 2, S_RR = 3, S_RZN = 4, S_RZO = 5, S_BB = 6, S_ZZ = 7, S_ZZ0 = 8, S_XX = 9,
        S_NSCAL = 16 };
+// pinned host slots after the scalars: wait-counter snapshots [start 3 | end 3]
+enum { S_TMO = S_NSCAL, S_HOST = S_NSCAL + 6 };
 
 
 #define RC(x)                           \

@@ -52,5 +52,8 @@ cudaError_t launch_dg_transfer<float>(int dim, int qf, bool prolong, int64_t nce
 }
 
 cudaError_t wait_timeouts_fp32(unsigned long long *count) { return read_wait_timeouts(count); }
+cudaError_t wait_timeouts_addr_fp32(unsigned long long **ptr) {
+    return cudaGetSymbolAddress((void **)ptr, g_wait_timeouts);
+}
 
 }  // namespace dgmg

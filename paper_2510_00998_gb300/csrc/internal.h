@@ -32,6 +32,10 @@ inline void count_launches(int k) { g_kernel_launches.fetch_add(k, std::memory_o
 // Bounded waits that ran out in the kernels of the float / double translation unit.
 cudaError_t wait_timeouts_fp32(unsigned long long *count);
 cudaError_t wait_timeouts_fp64(unsigned long long *count);
+// device addresses of the same counters on the current device (for
+// stream-ordered snapshots)
+cudaError_t wait_timeouts_addr_fp32(unsigned long long **ptr);
+cudaError_t wait_timeouts_addr_fp64(unsigned long long **ptr);
 
 // ------------------------------------------------------- reference element
 // 1D Lagrange element of degree p on [-1,1] with GLL (Sec. 2.2) or GL
@@ -178,6 +182,11 @@ cudaError_t launch_q1_cycle(int dim, const Q1Plan<T> *plan, unsigned long long *
 template <typename T>
 int q1_cycle_max_blocks(int dim);
 cudaError_t q1_barrier_timeouts(unsigned long long *count);
+cudaError_t q1_barrier_timeouts_addr(unsigned long long **ptr);
+// Set once a grid-barrier wait of the one-launch Q1 cycle ran out anywhere in
+// the process: that kernel then returns without work on its device, so every
+// context takes the launch per step from then on (and recaptures its graphs).
+extern std::atomic<int> g_q1_one_launch_off;
 
 // CTA -> (descriptor, first vertex (or row) of the CTA)
 struct VertMap {

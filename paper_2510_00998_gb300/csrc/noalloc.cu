@@ -1,10 +1,9 @@
 // Residual + p-restriction that allocates nothing at call time.
 //
 // Who needs it: code that runs where device allocation is not allowed or not
-// safe -- work queued while a CUDA graph is being captured (cudaMalloc is not
-// a capturable operation), real-time or embedded loops that forbid
-// allocation after start-up, and host applications that hand the library a
-// fixed memory budget up front. Such callers still pass their own inputs and
+// available -- real-time or embedded loops that forbid allocation after
+// start-up, host applications that hand the library a fixed memory budget up
+// front, and hosts without an allocator at the point of the call. Such callers still pass their own inputs and
 // outputs; the only scratch the stage needs (2^d corner partial sums per
 // cell) comes from the fixed array below, which every GPU that loads this
 // library holds until the process exits.

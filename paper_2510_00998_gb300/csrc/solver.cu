@@ -13,6 +13,7 @@
 // (residual norms) come back through pinned memory and an event, so a
 // scheduler can advance many runs on different streams without blocking.
 #include <cmath>
+#include <cstring>
 
 #include "ctx.h"
 
@@ -47,6 +48,37 @@ int post_scalars(dgmg_ctx *C, cudaStream_t s) {
     return DGMG_OK;
 }
 
+// Stream-ordered snapshot of the bounded-wait counters (FP32 and FP64 DG
+// kernels, Q1 grid barrier) into pinned slot `at` (0 start, 1 end of a run).
+int snapshot_timeouts(dgmg_ctx *C, int at, cudaStream_t s) {
+    for (int k = 0; k < 3; ++k)
+        LC(cudaMemcpyAsync(C->host_scal + S_TMO + 3 * at + k, C->tmo_dev[k], sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, s));
+    return DGMG_OK;
+}
+
+unsigned long long snapshot_value(const dgmg_ctx *C, int slot) {
+    unsigned long long v;
+    std::memcpy(&v, C->host_scal + S_TMO + slot, sizeof(v));
+    return v;
+}
+
+// End of a run: the counters again (the stream is idle once the final
+// scalars have arrived, so the wait is a few microseconds). A wait that ran
+// out during the run makes it fail with DGMG_ETIMEOUT; a grid-barrier one
+// also switches the process to the launch per step of the Q1 levels.
+int check_timeouts(dgmg_ctx *C, cudaStream_t s) {
+    RC(snapshot_timeouts(C, 1, s));
+    LC(cudaStreamSynchronize(s));
+    bool grew = false;
+    for (int k = 0; k < 3; ++k) grew = grew || snapshot_value(C, 3 + k) != snapshot_value(C, k);
+    if (!grew) return DGMG_OK;
+    if (snapshot_value(C, 5) != snapshot_value(C, 2)) g_q1_one_launch_off.store(1);
+    return fail(DGMG_ETIMEOUT,
+                "a bounded device-side wait ran out during the solve (bulk-copy mbarrier or Q1 grid barrier); "
+                "the result is not to be trusted");
+}
+
 // Queue the work of `enqueue(stream)` on s. With graphs enabled (and profiling
 // off) the work is captured once into a CUDA graph at its second use and then
 // replayed with a single launch; `key` is the user pointer the work depends
@@ -54,7 +86,8 @@ int post_scalars(dgmg_ctx *C, cudaStream_t s) {
 template <typename F>
 int run_chunk(dgmg_ctx *C, dgmg_ctx::Graph &g, const void *key, cudaStream_t s, F enqueue) {
     if (!C->use_graphs || C->prof.on || g.uses++ == 0) return enqueue(s);
-    if (!g.exec || g.key != key) {
+    const int q1_off = g_q1_one_launch_off.load();
+    if (!g.exec || g.key != key || g.q1_off != q1_off) {
         if (g.exec) {
             cudaGraphExecDestroy(g.exec);
             g.exec = nullptr;
@@ -89,6 +122,7 @@ int run_chunk(dgmg_ctx *C, dgmg_ctx::Graph &g, const void *key, cudaStream_t s, 
             return eager();
         }
         g.key = key;
+        g.q1_off = q1_off;
     }
     LC(cudaGraphLaunch(g.exec, s));
     count_launches((int)g.kernels);
@@ -249,6 +283,7 @@ int SolveRun::advance(bool blocking) {
             // host reads ||x||^2 first), else the FP64 apply r = b - A x.
             case P_START:
             case R_START:
+                ADV(snapshot_timeouts(C, 0, s));
                 ADV_CUDA(launch_dot(n, b, b, C->partials, C->scal + S_BB, s));
                 ADV_CUDA(launch_dot(n, x, x, C->partials, C->scal + S_XX, s));
                 ADV(post_scalars(C, s));
@@ -349,6 +384,10 @@ int SolveRun::advance(bool blocking) {
                 stats.prec_residual = zz0 > 0 ? std::sqrt(zz / zz0) : 0.0;
                 stats.fp64_applies = nres + it;
                 stats.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+                {
+                    const int tr = check_timeouts(C, s);    // the root cause of any other failure
+                    if (tr != DGMG_OK) status = tr;
+                }
                 state = S_DONE;
                 return 1;
             }
@@ -472,11 +511,16 @@ int SolveRun::advance(bool blocking) {
                 stats.prec_residual = zz0 > 0 ? std::sqrt(zz / zz0) : 0.0;
                 stats.fp64_applies = nres;
                 stats.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+                {
+                    const int tr = check_timeouts(C, s);    // the root cause of any other failure
+                    if (tr != DGMG_OK) status = tr;
+                }
                 state = S_DONE;
                 return 1;
             }
             // ------------------------------------------------ MGMult (Alg. 7)
             case M_START:
+                ADV(snapshot_timeouts(C, 0, s));
                 ADV_CUDA(cudaMemcpyAsync(C->w_rold, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
                 ADV(project64(*C, x, s));              // projections of the initial guess
                 ADV_CUDA(launch_dot(n, b, b, C->partials, C->scal + S_BB, s));
@@ -529,6 +573,10 @@ int SolveRun::advance(bool blocking) {
                 stats.prec_residual = prec;
                 stats.fp64_applies = 2 * it;
                 stats.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+                {
+                    const int tr = check_timeouts(C, s);    // the root cause of any other failure
+                    if (tr != DGMG_OK) status = tr;
+                }
                 state = S_DONE;
                 return 1;
             }

@@ -17,6 +17,7 @@ DGMG_EBUDGET = -3
 DGMG_ENOTCONVERGED = -4
 DGMG_ENONFINITE = -5
 DGMG_ECUDA = -6
+DGMG_ETIMEOUT = -7
 DGMG_FP64 = 0
 DGMG_MIXED_FP32 = 1
 DGMG_OUTER_AUTO = 0
@@ -127,6 +128,7 @@ _SIGS = {
     "dgmg_profile_read": (_I, [_P, _P, _P, _I]),
     "dgmg_kernel_launches": (ctypes.c_longlong, []),
     "dgmg_wait_timeouts": (_I, [ctypes.POINTER(ctypes.c_ulonglong)]),
+    "dgmg_fma_peak": (_I, [_I, ctypes.POINTER(ctypes.c_double), _P]),
 }
 
 STAGES = ("project", "smooth", "residual", "cg_levels", "vector")
@@ -135,6 +137,14 @@ STAGES = ("project", "smooth", "residual", "cg_levels", "vector")
 def kernel_launches():
     """Kernels launched by libdgmg in this process."""
     return int(load().dgmg_kernel_launches())
+
+
+def fma_peak(kind, stream=None):
+    """Measured FMA-loop peak of the current device in TFLOP/s: kind 0 FP64,
+    1 FP32, 2 FP32 on packed pairs."""
+    v = ctypes.c_double(0.0)
+    _check(load().dgmg_fma_peak(int(kind), ctypes.byref(v), _stream(stream)))
+    return float(v.value)
 
 
 def wait_timeouts():

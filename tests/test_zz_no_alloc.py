@@ -1,8 +1,8 @@
 """The allocation-free residual + p-restriction entry point.
 
 Some callers cannot allocate device memory when they call into the library
-(while a CUDA graph is being captured, in loops that forbid allocation after
-start-up, under a fixed memory budget). dgmg_residual_restrict_noalloc serves
+(in loops that forbid allocation after start-up, under a fixed memory budget,
+without an allocator at the point of the call). dgmg_residual_restrict_noalloc serves
 them with a fixed device array as scratch. This checks, through the C ABI,
 that two consecutive calls give the same residual and restricted residual as
 dgmg_residual_restrict. The file is named to be collected last."""
