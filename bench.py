@@ -475,9 +475,11 @@ def run_gb300(args):
     avg_ms = sm_ms / max(sm_n, 1)
     flops = smooth_flops(N_CELLS, q)
     achieved = flops / (avg_ms * 1e-3) / 1e12
+    peak_clocks = ClockSampler(local)
     fp64_peak = dgmg.fma_peak(0)
     fp32_peak = dgmg.fma_peak(1)
     fp32x2_peak = dgmg.fma_peak(2)
+    peak_clk = peak_clocks.stop()
     survey_flops = 10 * d * q * ndof          # sum-factorised minimum, 10 d q flop per DoF
     shares = {k: round(v[0] / max(sum(w[0] for w in prof.values()), 1e-30), 4) for k, v in prof.items()}
 
@@ -537,7 +539,7 @@ def run_gb300(args):
                          "peak_note": ("FP64 FMA-loop peak measured in this run (dgmg_fma_peak), of measured; "
                                        f"nominal {FP64_NOMINAL_TFLOPS}"),
                          "measured_peaks_tflops": {"fp64_fma": fp64_peak, "fp32_fma": fp32_peak,
-                                                   "fp32x2_fma": fp32x2_peak}},
+                                                   "fp32x2_fma": fp32x2_peak, "clocks": peak_clk}},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_u / (e2e_t * 1e-3) / 1e9, "unit": "GDoF/s",
                     "h2d_bytes_per_step": 2 * 8 * ndof, "d2h_bytes_per_step": 8 * ndof},

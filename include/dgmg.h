@@ -478,9 +478,10 @@ long long dgmg_kernel_launches(void);
 
 /*
  * Arithmetic peak of the current device, measured: a kernel in which every
- * thread runs 8 independent chains of fused multiply-adds (one per SM-resident
- * thread slot, a few tens of milliseconds), timed with CUDA events on
- * `stream`. kind: 0 = FP64 FMA, 1 = FP32 FMA, 2 = FP32 FMA on packed pairs
+ * thread runs 8 independent chains of fused multiply-adds, launched with 1, 2,
+ * 4, ... resident 256-thread blocks per SM up to the occupancy limit (a few
+ * tens of milliseconds each), timed with CUDA events on `stream`; the best
+ * launch shape gives the result. kind: 0 = FP64 FMA, 1 = FP32 FMA, 2 = FP32 FMA on packed pairs
  * (two lanes of one instruction). *tflops (HOST) receives 2 x FMAs / time in
  * TFLOP/s: the denominator of the roofline fraction of the FP64 kernels, which
  * are bound by the FP64 pipe on this chip. Synchronous; allocates nothing.

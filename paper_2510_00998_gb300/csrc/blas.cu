@@ -558,12 +558,12 @@ extern "C" int dgmg_fma_peak(int kind, double *tflops, void *stream) {
         DG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fma_loop<float, CH>, TPB, 0));
     else
         DG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fma_loop_x2<CH>, TPB, 0));
-    const int blocks = sms * (per > 0 ? per : 1);
+    per = per > 0 ? per : 1;
     const double lanes = kind == 2 ? 2.0 : 1.0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     DG_CUDA(cudaEventCreate(&e0));
     DG_CUDA(cudaEventCreate(&e1));
-    auto run = [&](int iters) -> cudaError_t {
+    auto run = [&](int blocks, int iters) -> cudaError_t {
         count_launches(1);
         if (kind == 0)
             k_fma_loop<double, CH><<<blocks, TPB, 0, s>>>(iters, 0.999999, 1e-7);
@@ -573,27 +573,41 @@ extern "C" int dgmg_fma_peak(int kind, double *tflops, void *stream) {
             k_fma_loop_x2<CH><<<blocks, TPB, 0, s>>>(iters, 0.9999f, 1e-4f);
         return cudaGetLastError();
     };
-    // calibrate to about 30 ms, then take the best of three timed launches
-    int iters = kind == 0 ? 256 : 8192;
-    float ms = 0.f, best = 0.f;
-    cudaError_t e = run(iters);   // warm-up
-    for (int k = 0; k < 6 && e == cudaSuccess; ++k) {
-        e = cudaEventRecord(e0, s);
-        if (e == cudaSuccess) e = run(iters);
-        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (e != cudaSuccess) break;
-        if (k < 3) {
-            if (ms < 30.f) iters = (int)std::min<double>(iters * std::max(2.0, 30.0 / std::max(ms, 0.01f)), 1 << 26);
-            continue;
+    // resident blocks per SM from one to the occupancy limit; per shape the
+    // iterations are calibrated to about 30 ms, then the best of three timed
+    // launches is kept; the best shape gives the peak
+    double best_rate = 0.0;
+    cudaError_t e = cudaSuccess;
+    int shapes[16], nshape = 0;
+    for (int b = 1; b < per && nshape < 15; b *= 2) shapes[nshape++] = b;
+    shapes[nshape++] = per;
+    for (int si = 0; si < nshape && e == cudaSuccess; ++si) {
+        const int blocks = sms * shapes[si];
+        int iters = kind == 0 ? 64 : 2048;
+        float ms = 0.f, best = 0.f;
+        e = run(blocks, iters);   // warm-up
+        for (int k = 0; k < 6 && e == cudaSuccess; ++k) {
+            e = cudaEventRecord(e0, s);
+            if (e == cudaSuccess) e = run(blocks, iters);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) break;
+            if (k < 3) {
+                if (ms < 30.f)
+                    iters = (int)std::min<double>(iters * std::max(2.0, 30.0 / std::max(ms, 0.01f)), 1 << 26);
+                continue;
+            }
+            if (best == 0.f || ms < best) best = ms;
         }
-        if (best == 0.f || ms < best) best = ms;
+        if (e == cudaSuccess && best > 0.f) {
+            const double fmas = (double)blocks * TPB * CH * 4.0 * iters * lanes;
+            best_rate = std::max(best_rate, 2.0 * fmas / (best * 1e-3) / 1e12);
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (e != cudaSuccess) return cuda_fail(e, "dgmg_fma_peak");
-    const double fmas = (double)blocks * TPB * CH * 4.0 * iters * lanes;
-    *tflops = 2.0 * fmas / (best * 1e-3) / 1e12;
+    *tflops = best_rate;
     return DGMG_OK;
 }
