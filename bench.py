@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     # library default tiles instead of timing candidates at set-up: for runs under
     # a profiler, whose per-launch overhead distorts the tuner's timings (for this
     # workload the defaults are the tiles the tuner picks)
@@ -306,8 +307,10 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- serving
-SERVE_REQUESTS = 24
-SERVE_RATE = 2.0      # arrival rate as a multiple of the FP64 one-at-a-time capacity
+SERVE_RATES = (0.25, 0.5, 1.0, 2.0, 4.0, 8.0, 16.0, 32.0)   # x the FP64 one-at-a-time capacity
+SERVE_MAX_REQUESTS = 128
+SERVE_WINDOW_S = 16.0    # arrival window per rate at most: fewer requests at the low rates
+SERVE_FP64_SAMPLE = 8    # served results checked against an FP64 solve of the same request
 
 
 def measured_hbm_gbs():
@@ -375,25 +378,82 @@ def serving_run():
     """Solves/s and p50/p99 latency (arrival to completion, rel. residual 1e-10)
     of the mixed-precision solve server against plain FP64 one-at-a-time solving,
     for Poisson arrivals of requests with n in [8,48]^3 cells, p in 2..5 and
-    kappa in {1, lognormal, two-phase} at SERVE_RATE x the FP64 capacity."""
+    kappa in {1, lognormal, two-phase}, at rising multiples of the FP64
+    capacity until the served rate stops tracking the arrival rate (the served
+    capacity); the error of a sample of served results against FP64 solves of
+    the same requests."""
     import numpy as np
+    import torch
+    from paper_2510_00998_gb300 import dgmg
     from paper_2510_00998_gb300 import workloads as wl
-    reqs = wl.request_stream("serve", SERVE_REQUESTS, 5)
+    reqs = wl.request_stream("serve", SERVE_MAX_REQUESTS, 5)
     wl.build_rhs(reqs)
     service = wl.one_at_a_time(reqs, precision=0)
     capacity = len(service) / sum(service)
     gaps = np.random.default_rng(1005).exponential(size=len(reqs))
-    arrivals = list(np.cumsum(gaps / (SERVE_RATE * capacity)))
-    fifo = wl.fifo_latencies(arrivals, service)
-    lat, makespan, stats, info = wl.serve_trace(reqs, arrivals, 96 << 30, 16)
-    return {"requests": len(reqs), "rate_per_s": SERVE_RATE * capacity,
-            "rate_x_fp64_capacity": SERVE_RATE,
-            "served_mixed": {"solves_per_s": len(reqs) / makespan, "p50_s": wl.pct(lat, 50),
-                             "p99_s": wl.pct(lat, 99), "max_rel_residual": max(s.rel_residual for s in stats)},
-            "fp64_one_at_a_time": {"solves_per_s": len(reqs) / max(a + l for a, l in zip(arrivals, fifo)),
-                                   "p50_s": wl.pct(fifo, 50), "p99_s": wl.pct(fifo, 99)},
-            "workload": "Poisson arrivals, n in [8,48]^3, p in 2..5, kappa in {1, lognormal, two-phase 1/100}, "
-                        "8 random Fourier modes (seeds 5, 1005)"}
+    rates, xs_last, sub_last = [], None, None
+    for m in SERVE_RATES:
+        lam = m * capacity
+        n = int(min(SERVE_MAX_REQUESTS, max(32, lam * SERVE_WINDOW_S)))
+        sub = reqs[:n]
+        arrivals = list(np.cumsum(gaps[:n] / lam))
+        fifo = wl.fifo_latencies(arrivals, service[:n])
+        lat, makespan, stats, info, xs = wl.serve_trace(sub, arrivals, 96 << 30, 16, return_x=True)
+        served = n / makespan
+        rates.append({"rate_x_fp64_capacity": m, "rate_per_s": lam, "requests": n,
+                      "served_mixed": {"solves_per_s": served, "p50_s": wl.pct(lat, 50), "p99_s": wl.pct(lat, 99),
+                                       "max_rel_residual": max(st.rel_residual for st in stats)},
+                      "fp64_one_at_a_time": {"solves_per_s": n / max(a + l for a, l in zip(arrivals, fifo)),
+                                             "p50_s": wl.pct(fifo, 50), "p99_s": wl.pct(fifo, 99)}})
+        xs_last, sub_last = xs, sub
+        if served < 0.8 * lam:
+            break                       # saturated: the served rate no longer follows the arrivals
+    # accuracy: served (mixed-precision) results against FP64 solves of the same requests
+    errs = []
+    for k in range(min(SERVE_FP64_SAMPLE, len(sub_last))):
+        r = sub_last[k]
+        ctx = dgmg.Context(r["n"], r["p"], r["kappa"], precision=0, rtol=1e-12)
+        x64 = torch.zeros_like(r["b"])
+        ctx.solve(r["b"], x64)
+        ctx.close()
+        errs.append(float(torch.linalg.norm(xs_last[k] - x64) / torch.linalg.norm(x64)))
+    served_all = [e["served_mixed"]["solves_per_s"] for e in rates]
+    return {"fp64_capacity_solves_per_s": capacity,
+            "served_capacity_solves_per_s": max(served_all),
+            "saturated": rates[-1]["served_mixed"]["solves_per_s"] < 0.8 * rates[-1]["rate_per_s"],
+            "rates": rates,
+            "max_rel_err_vs_fp64": max(errs), "fp64_check_sample": len(errs),
+            "workload": "Poisson arrivals (seeds 5, 1005), n in [8,48]^3, p in 2..5, kappa in {1, lognormal, "
+                        "two-phase 1/100}, 8 random Fourier modes; up to 128 requests per rate, "
+                        "16 slots, 96 GB budget; FP64 check: rtol 1e-12 FP64 PCG"}
+
+
+BATCH_COUNT = 256
+
+
+def batch_run():
+    """256 independent solves (n in [8,24]^3, p in {2,3,4}, lognormal kappa,
+    8 Fourier modes, default_rng(4)) as one batch (one persistent launch per
+    stage and degree group), FP64 and mixed precision, against FP64 solves one
+    at a time; solves/s with and without set-up."""
+    from paper_2510_00998_gb300 import workloads as wl
+    reqs = wl.request_stream("batch", BATCH_COUNT, 4)
+    wl.build_rhs(reqs)
+    solve_only = []
+    alone = wl.one_at_a_time(reqs, precision=0, solve_times=solve_only)
+    out = {"workload": f"{BATCH_COUNT} 3D solves, n in [8,24], p in 2..4, lognormal kappa, Fourier RHS "
+                       "(default_rng(4)), every problem to rel. residual 1e-10",
+           "fp64_one_at_a_time": {"solves_per_s": BATCH_COUNT / sum(alone),
+                                  "solve_only_solves_per_s": BATCH_COUNT / sum(solve_only)}}
+    for name, prec in (("batched_fp64", 0), ("batched_mixed", 1)):
+        setup, times, stats, info = wl.batched(reqs, solves=3, precision=prec)
+        out[name] = {"setup_s": setup, "solve_s": min(times),
+                     "solves_per_s": BATCH_COUNT / (setup + min(times)),
+                     "solve_only_solves_per_s": BATCH_COUNT / min(times),
+                     "iterations_max": max(s.iterations for s in stats),
+                     "max_rel_residual": max(s.rel_residual for s in stats),
+                     "kernels_per_iteration": info.kernels_per_iteration, "ndof": info.ndof}
+    return out
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -507,6 +567,9 @@ def run_gb300(args):
     serving = None
     if rank == 0 and not args.no_serving:
         serving = serving_run()
+    batch = None
+    if rank == 0 and not args.no_batch:
+        batch = batch_run()
     mixed = None
     if rank == 0 and not args.no_mixed:
         mixed = mixed_section(flush, stream)
@@ -552,6 +615,7 @@ def run_gb300(args):
             "vcycle_ms": vcycle_ms,
             "mixed_64cube_p4": mixed,
             "serving": serving,
+            "batch": batch,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

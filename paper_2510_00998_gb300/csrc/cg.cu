@@ -400,51 +400,66 @@ __global__ void __launch_bounds__(Q1_TPB) k_q1_cycle(const Q1Plan<T> *__restrict
     for (int l = lg - 1; l >= 0; --l) ec = q1_up<DIM, T>(p, l, ec, on_grid, grid);
 }
 
-// ---- batched forms: CTA k covers vertices [v0, v0 + BATCH_VERTS) of descriptor
-// map[k].desc (one level of one instance); all instances share the launch.
+// ---- batched forms: work item k covers vertices [v0, v0 + BATCH_VERTS) of
+// descriptor map[k].desc (one level of one instance); all instances share one
+// persistent launch per stage, whose CTAs stride through the nb work items.
 template <int DIM, typename T>
 __global__ void __launch_bounds__(BATCH_VERTS) k_corner_gather_batch(const BatchCG<T> *__restrict__ D,
-                                                                     const VertMap *__restrict__ map) {
-    const VertMap m = map[blockIdx.x];
-    const BatchCG<T> &d = D[m.desc];
-    corner_gather_at<DIM, T>(d.n[0], d.n[1], d.n[2], d.corners, d.b, (int64_t)m.v0 + threadIdx.x);
+                                                                     const VertMap *__restrict__ map, int nb) {
+    for (int k = blockIdx.x; k < nb; k += gridDim.x) {
+        const VertMap m = map[k];
+        const BatchCG<T> &d = D[m.desc];
+        corner_gather_at<DIM, T>(d.n[0], d.n[1], d.n[2], d.corners, d.b, (int64_t)m.v0 + threadIdx.x);
+    }
 }
 template <int DIM, typename T>
 __global__ void __launch_bounds__(BATCH_VERTS) k_cg_jacobi_batch(const BatchCG<T> *__restrict__ D,
-                                                                 const VertMap *__restrict__ map, T omega,
+                                                                 const VertMap *__restrict__ map, int nb, T omega,
                                                                  int zero_guess, int cur) {
-    const VertMap m = map[blockIdx.x];
-    const BatchCG<T> &d = D[m.desc];
-    cg_jacobi_at<DIM, T>(d.L, d.u[cur], d.b, d.u[cur ^ 1], omega, zero_guess, (int64_t)m.v0 + threadIdx.x);
+    for (int k = blockIdx.x; k < nb; k += gridDim.x) {
+        const VertMap m = map[k];
+        const BatchCG<T> &d = D[m.desc];
+        cg_jacobi_at<DIM, T>(d.L, d.u[cur], d.b, d.u[cur ^ 1], omega, zero_guess, (int64_t)m.v0 + threadIdx.x);
+    }
 }
 template <int DIM, typename T>
 __global__ void __launch_bounds__(BATCH_VERTS) k_cg_residual_batch(const BatchCG<T> *__restrict__ D,
-                                                                   const VertMap *__restrict__ map, int cur) {
-    const VertMap m = map[blockIdx.x];
-    const BatchCG<T> &d = D[m.desc];
-    cg_residual_at<DIM, T>(d.L, d.u[cur], d.b, d.r, (int64_t)m.v0 + threadIdx.x);
+                                                                   const VertMap *__restrict__ map, int nb, int cur) {
+    for (int k = blockIdx.x; k < nb; k += gridDim.x) {
+        const VertMap m = map[k];
+        const BatchCG<T> &d = D[m.desc];
+        cg_residual_at<DIM, T>(d.L, d.u[cur], d.b, d.r, (int64_t)m.v0 + threadIdx.x);
+    }
 }
 template <int DIM, typename T>
 __global__ void __launch_bounds__(BATCH_VERTS) k_h_restrict_batch(const BatchCG<T> *__restrict__ D,
-                                                                  const VertMap *__restrict__ map) {
-    const VertMap m = map[blockIdx.x];
-    const BatchCG<T> &d = D[m.desc];
-    h_restrict_at<DIM, T>(d.L, d.r, d.b_next, (int64_t)m.v0 + threadIdx.x);
+                                                                  const VertMap *__restrict__ map, int nb) {
+    for (int k = blockIdx.x; k < nb; k += gridDim.x) {
+        const VertMap m = map[k];
+        const BatchCG<T> &d = D[m.desc];
+        h_restrict_at<DIM, T>(d.L, d.r, d.b_next, (int64_t)m.v0 + threadIdx.x);
+    }
 }
 template <int DIM, typename T>
 __global__ void __launch_bounds__(BATCH_VERTS) k_h_prolong_batch(const BatchCG<T> *__restrict__ D,
-                                                                 const VertMap *__restrict__ map, int cur) {
-    const VertMap m = map[blockIdx.x];
-    const BatchCG<T> &d = D[m.desc];
-    h_prolong_at<DIM, T>(d.L, d.e_next, d.u[cur], (int64_t)m.v0 + threadIdx.x);
+                                                                 const VertMap *__restrict__ map, int nb, int cur) {
+    for (int k = blockIdx.x; k < nb; k += gridDim.x) {
+        const VertMap m = map[k];
+        const BatchCG<T> &d = D[m.desc];
+        h_prolong_at<DIM, T>(d.L, d.e_next, d.u[cur], (int64_t)m.v0 + threadIdx.x);
+    }
 }
 template <typename T>
 __global__ void __launch_bounds__(BATCH_VERTS) k_coarse_solve_batch(const BatchCG<T> *__restrict__ D,
-                                                                    const VertMap *__restrict__ map) {
-    const VertMap m = map[blockIdx.x];
-    const BatchCG<T> &d = D[m.desc];
-    coarse_row<T>(d.L.nv, d.Ainv, d.b, d.u[0], (int64_t)m.v0 + threadIdx.x);
+                                                                    const VertMap *__restrict__ map, int nb) {
+    for (int k = blockIdx.x; k < nb; k += gridDim.x) {
+        const VertMap m = map[k];
+        const BatchCG<T> &d = D[m.desc];
+        coarse_row<T>(d.L.nv, d.Ainv, d.b, d.u[0], (int64_t)m.v0 + threadIdx.x);
+    }
 }
+
+inline unsigned persistent_blocks(const void *fn, int threads, int nb) { return persistent_grid(fn, threads, 0, nb); }
 
 inline unsigned blocks_for(int64_t n) { return (unsigned)((n + TPB - 1) / TPB); }
 
@@ -566,9 +581,9 @@ cudaError_t launch_corner_gather_batch(int dim, const BatchCG<T> *D, const VertM
     if (nb <= 0) return cudaSuccess;
     count_launches(1);
     if (dim == 3)
-        k_corner_gather_batch<3, T><<<nb, BATCH_VERTS, 0, s>>>(D, map);
+        k_corner_gather_batch<3, T><<<persistent_blocks((const void *)k_corner_gather_batch<3, T>, BATCH_VERTS, nb), BATCH_VERTS, 0, s>>>(D, map, nb);
     else
-        k_corner_gather_batch<2, T><<<nb, BATCH_VERTS, 0, s>>>(D, map);
+        k_corner_gather_batch<2, T><<<persistent_blocks((const void *)k_corner_gather_batch<2, T>, BATCH_VERTS, nb), BATCH_VERTS, 0, s>>>(D, map, nb);
     return cudaGetLastError();
 }
 
@@ -578,9 +593,11 @@ cudaError_t launch_cg_jacobi_batch(int dim, const BatchCG<T> *D, const VertMap *
     if (nb <= 0) return cudaSuccess;
     count_launches(1);
     if (dim == 3)
-        k_cg_jacobi_batch<3, T><<<nb, BATCH_VERTS, 0, s>>>(D, map, omega, zero_guess ? 1 : 0, cur);
+        k_cg_jacobi_batch<3, T><<<persistent_blocks((const void *)k_cg_jacobi_batch<3, T>, BATCH_VERTS, nb), BATCH_VERTS, 0, s>>>(
+            D, map, nb, omega, zero_guess ? 1 : 0, cur);
     else
-        k_cg_jacobi_batch<2, T><<<nb, BATCH_VERTS, 0, s>>>(D, map, omega, zero_guess ? 1 : 0, cur);
+        k_cg_jacobi_batch<2, T><<<persistent_blocks((const void *)k_cg_jacobi_batch<2, T>, BATCH_VERTS, nb), BATCH_VERTS, 0, s>>>(
+            D, map, nb, omega, zero_guess ? 1 : 0, cur);
     return cudaGetLastError();
 }
 
@@ -590,9 +607,11 @@ cudaError_t launch_cg_residual_batch(int dim, const BatchCG<T> *D, const VertMap
     if (nb <= 0) return cudaSuccess;
     count_launches(1);
     if (dim == 3)
-        k_cg_residual_batch<3, T><<<nb, BATCH_VERTS, 0, s>>>(D, map, cur);
+        k_cg_residual_batch<3, T><<<persistent_blocks((const void *)k_cg_residual_batch<3, T>, BATCH_VERTS, nb), BATCH_VERTS, 0, s>>>(
+            D, map, nb, cur);
     else
-        k_cg_residual_batch<2, T><<<nb, BATCH_VERTS, 0, s>>>(D, map, cur);
+        k_cg_residual_batch<2, T><<<persistent_blocks((const void *)k_cg_residual_batch<2, T>, BATCH_VERTS, nb), BATCH_VERTS, 0, s>>>(
+            D, map, nb, cur);
     return cudaGetLastError();
 }
 
@@ -601,9 +620,11 @@ cudaError_t launch_h_restrict_batch(int dim, const BatchCG<T> *D, const VertMap 
     if (nb <= 0) return cudaSuccess;
     count_launches(1);
     if (dim == 3)
-        k_h_restrict_batch<3, T><<<nb, BATCH_VERTS, 0, s>>>(D, map);
+        k_h_restrict_batch<3, T><<<persistent_blocks((const void *)k_h_restrict_batch<3, T>, BATCH_VERTS, nb), BATCH_VERTS, 0, s>>>(
+            D, map, nb);
     else
-        k_h_restrict_batch<2, T><<<nb, BATCH_VERTS, 0, s>>>(D, map);
+        k_h_restrict_batch<2, T><<<persistent_blocks((const void *)k_h_restrict_batch<2, T>, BATCH_VERTS, nb), BATCH_VERTS, 0, s>>>(
+            D, map, nb);
     return cudaGetLastError();
 }
 
@@ -613,9 +634,11 @@ cudaError_t launch_h_prolong_batch(int dim, const BatchCG<T> *D, const VertMap *
     if (nb <= 0) return cudaSuccess;
     count_launches(1);
     if (dim == 3)
-        k_h_prolong_batch<3, T><<<nb, BATCH_VERTS, 0, s>>>(D, map, cur);
+        k_h_prolong_batch<3, T><<<persistent_blocks((const void *)k_h_prolong_batch<3, T>, BATCH_VERTS, nb), BATCH_VERTS, 0, s>>>(
+            D, map, nb, cur);
     else
-        k_h_prolong_batch<2, T><<<nb, BATCH_VERTS, 0, s>>>(D, map, cur);
+        k_h_prolong_batch<2, T><<<persistent_blocks((const void *)k_h_prolong_batch<2, T>, BATCH_VERTS, nb), BATCH_VERTS, 0, s>>>(
+            D, map, nb, cur);
     return cudaGetLastError();
 }
 
@@ -623,7 +646,7 @@ template <typename T>
 cudaError_t launch_coarse_solve_batch(const BatchCG<T> *D, const VertMap *map, int nb, cudaStream_t s) {
     if (nb <= 0) return cudaSuccess;
     count_launches(1);
-    k_coarse_solve_batch<T><<<nb, BATCH_VERTS, 0, s>>>(D, map);
+    k_coarse_solve_batch<T><<<persistent_blocks((const void *)k_coarse_solve_batch<T>, BATCH_VERTS, nb), BATCH_VERTS, 0, s>>>(D, map, nb);
     return cudaGetLastError();
 }
 

@@ -20,6 +20,31 @@ namespace dgmg {
 std::atomic<long long> g_kernel_launches{0};
 std::atomic<int> g_q1_one_launch_off{0};
 
+unsigned persistent_grid(const void *fn, int threads, size_t smem, int64_t items) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, size_t>, int> cap;
+    if (items <= 0) return 0;
+    int c = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cap.find({fn, smem});
+        if (it != cap.end()) c = it->second;
+    }
+    if (c == 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem) != cudaSuccess) {
+            cudaGetLastError();
+            per = 1;
+        }
+        c = std::max(1, sms * std::max(per, 1));
+        std::lock_guard<std::mutex> lk(mu);
+        cap[{fn, smem}] = c;
+    }
+    return (unsigned)std::min<int64_t>(items, c);
+}
+
 // ------------------------------------------------------------------- errors
 static thread_local std::string g_last_error;
 
@@ -390,7 +415,7 @@ int setup_dg(dgmg_ctx &C, const DGSpace &S, DGDev<T> &D, const std::vector<doubl
         D.kappa = const_cast<T *>(shared_kappa);
     else
         RC(C.upload(&D.kappa, convert<T>(kappa)));
-    const int64_t trn = C.ncell * 2 * C.dim * 2 * (S.nloc / S.q);
+    const int64_t trn = C.ncell * 2 * C.dim * trace_face_stride<T>((int)(S.nloc / S.q));
     if (!smoother) {                  // operator only (projection, residual): no block-inverse factors
         RC(C.alloc(&D.tr[0], trn));
         RC(C.alloc(&D.tr[1], trn));
@@ -776,7 +801,7 @@ template <typename T>
 int level_cycle(dgmg_ctx &C, int l, const T *b, T *z, cudaStream_t s) {
     DGDev<T> &D = dg_level<T>(C, l);
     const DGSpace &S = C.dgs[l];
-    const int64_t trn = C.ncell * 2 * C.dim * 2 * (S.nloc / S.q);
+    const int64_t trn = C.ncell * 2 * C.dim * trace_face_stride<T>((int)(S.nloc / S.q));
     LC(cudaMemsetAsync(z, 0, sizeof(T) * S.ndof, s));
     LC(cudaMemsetAsync(D.tr[0], 0, sizeof(T) * trn, s));   // projections of z = 0
     int cur = 0;
@@ -878,7 +903,7 @@ static int tune_tiles(dgmg_ctx &C, T *u, T *b, int *tile, bool trace, bool smoot
     DGDev<T> &D = dg<T>(C);
     cudaStream_t s = C.setup_stream;
     const int nf = (int)(C.nloc / C.q);
-    const int64_t trn = C.ncell * 2 * C.dim * 2 * nf;
+    const int64_t trn = C.ncell * 2 * C.dim * trace_face_stride<T>(nf);
     std::vector<int> cand;
     for (int c = 1; c <= 64; c *= 2)
         if (c * nf >= 32 && c * nf <= 256) cand.push_back(c);
@@ -1450,10 +1475,12 @@ int dgmg_estimate_bytes(const dgmg_mesh *mesh, int p, const dgmg_opts *opts, siz
     for (int a = 0; a < dim; ++a) n[a] = mesh->n[a];
     const int64_t ncell = (int64_t)n[0] * n[1] * n[2];
     const int64_t nloc = dim == 3 ? (int64_t)q * q * q : (int64_t)q * q, ndof = ncell * nloc;
-    const int64_t nf = nloc / q, tr = ncell * 2 * dim * 2 * nf, ns = dim == 3 ? 27 : 9;
+    const int64_t nf = nloc / q, ns = dim == 3 ? 27 : 9;
+    const int64_t tr = ncell * 2 * dim * trace_face_stride<double>((int)nf);
+    const int64_t tr32 = ncell * 2 * dim * trace_face_stride<float>((int)nf);
     auto sz = [](int64_t count, size_t elem) { return (size_t)std::max<int64_t>(count, 1) * elem; };
     size_t dg64 = sz(ncell, 8) + sz(ncell * dim * (q * q + q), 8) + sz(ndof, 8) + 2 * sz(tr, 8) + sz(ncell << dim, 8);
-    size_t dg32 = sz(ncell, 4) + sz(ncell * dim * (q * q + q), 4) + 2 * sz(tr, 4) + sz(ncell << dim, 4);
+    size_t dg32 = sz(ncell, 4) + sz(ncell * dim * (q * q + q), 4) + 2 * sz(tr32, 4) + sz(ncell << dim, 4);
     size_t cg64 = 0, cg32 = 0;
     int cur[3] = {n[0], n[1], n[2]};
     int64_t nv = 1;
@@ -1489,9 +1516,11 @@ int dgmg_estimate_bytes(const dgmg_mesh *mesh, int p, const dgmg_opts *opts, siz
         for (int pc = p - 1; pc >= 1; --pc) {
             const int ql = pc + 1;
             const int64_t nl = dim == 3 ? (int64_t)ql * ql * ql : (int64_t)ql * ql, nd = ncell * nl;
-            const int64_t trl = ncell * 2 * dim * 2 * (nl / ql), fdl = ncell * dim * (ql * ql + ql);
+            const int64_t trl = ncell * 2 * dim * trace_face_stride<double>((int)(nl / ql));
+            const int64_t trl32 = ncell * 2 * dim * trace_face_stride<float>((int)(nl / ql));
+            const int64_t fdl = ncell * dim * (ql * ql + ql);
             total += sz(fdl, 8) + sz(nd, 8) + 2 * sz(trl, 8) + sz(ncell << dim, 8) + 3 * sz(nd, 8);
-            if (mixed) total += sz(fdl, 4) + 2 * sz(trl, 4) + sz(ncell << dim, 4) + 3 * sz(nd, 4);
+            if (mixed) total += sz(fdl, 4) + 2 * sz(trl32, 4) + sz(ncell << dim, 4) + 3 * sz(nd, 4);
         }
         total += sz(ndof, 8) + (mixed ? sz(ndof, 4) : 0);
     }

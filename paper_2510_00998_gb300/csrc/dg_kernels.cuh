@@ -28,7 +28,8 @@ struct Geo {
     static constexpr int NL = DIM == 3 ? Q * Q * Q : Q * Q;   // nodes per cell
     static constexpr int NF = NL / Q;                          // nodes per face = threads per cell
     static constexpr int NFACE = 2 * DIM;
-    static constexpr int TR = NFACE * 2 * NF;                  // trace values per cell
+    static constexpr int FS = trace_face_stride<T>(NF);         // trace values per face (padded)
+    static constexpr int TR = NFACE * FS;                      // trace values per cell
     static constexpr int NC = 1 << DIM;                        // corners per cell
     static constexpr int FDS = Q * Q + Q;                      // fast-diag factors per axis (global)
     static constexpr int VEC = 16 / (int)sizeof(T);            // elements per 16-byte vector
@@ -118,7 +119,7 @@ __device__ __forceinline__ void load_neighbour_traces(const DGConst<T> &c, int64
         T g = T(0), h = T(0);
         if (inside) {
             const int64_t nb = cell + (side ? axis_stride<DIM>(c.n, dir) : -axis_stride<DIM>(c.n, dir));
-            const T *src = tr + nb * G::TR + (f ^ 1) * 2 * G::NF;
+            const T *src = tr + nb * G::TR + (f ^ 1) * G::FS;
             g = src[t];
             h = src[G::NF + t];
             if (t == 0) {
@@ -390,8 +391,8 @@ __device__ __forceinline__ void write_pencil_traces(const DGConst<T> &c, int dir
             vhi += c.vp[i] * x[i];
         }
     }
-    T *lo = trc + (2 * dir) * 2 * G::NF;
-    T *hi = trc + (2 * dir + 1) * 2 * G::NF;
+    T *lo = trc + (2 * dir) * G::FS;
+    T *hi = trc + (2 * dir + 1) * G::FS;
     lo[t] = vlo;
     lo[G::NF + t] = dlo;
     hi[t] = vhi;
@@ -765,10 +766,12 @@ __global__ void __launch_bounds__(256) k_residual(DGConst<T> c, int cpb, int mod
 namespace dgmg {
 
 // ---------------------------------------------------------------------------
-// Batched launches: CTA k serves the cells [cell0, cell0 + tile) of instance
-// map[k].inst; it copies that instance's descriptor (constants and array
-// pointers) into shared memory and runs the same body as the single-instance
-// kernel on the instance's slice of the group vectors.
+// Batched launches: work item k serves the cells [cell0, cell0 + tile) of
+// instance map[k].inst; its CTA copies that instance's descriptor (constants
+// and array pointers) into shared memory and runs the same body as the
+// single-instance kernel on the instance's slice of the group vectors. One
+// persistent launch per stage: as many CTAs as stay resident, each striding
+// through the work items.
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ void load_batch_desc(const BatchDG<T> *__restrict__ src, BatchDG<T> *dst) {
@@ -779,63 +782,81 @@ __device__ __forceinline__ void load_batch_desc(const BatchDG<T> *__restrict__ s
     __syncthreads();
 }
 
+// Persistent: the CTAs stride through the nblocks work items of the map; a
+// barrier ends every thread's use of the descriptor and of the staging memory
+// before the next item is loaded.
 template <int DIM, int Q, typename T>
 __global__ void __launch_bounds__(256) k_project_batch(const BatchDG<T> *__restrict__ D,
-                                                        const BlockMap *__restrict__ map, int cpb, T *u,
+                                                        const BlockMap *__restrict__ map, int nblocks, int cpb, T *u,
                                                         int with_e0) {
     using G = Geo<DIM, Q, T>;
     __shared__ __align__(16) BatchDG<T> sd;
-    const BlockMap m = map[blockIdx.x];
-    load_batch_desc(D + m.inst, &sd);
-    k_project_body<DIM, Q, T>(sd.c, m.cell0, cpb, u + sd.off * G::NL, with_e0 ? sd.e0 : nullptr, sd.tr[0]);
+    for (int k = blockIdx.x; k < nblocks; k += gridDim.x) {
+        if (k != (int)blockIdx.x) __syncthreads();
+        const BlockMap m = map[k];
+        load_batch_desc(D + m.inst, &sd);
+        k_project_body<DIM, Q, T>(sd.c, m.cell0, cpb, u + sd.off * G::NL, with_e0 ? sd.e0 : nullptr, sd.tr[0]);
+    }
 }
 
 template <int DIM, int Q, typename T>
 __global__ void __launch_bounds__(256) k_smooth_batch(const BatchDG<T> *__restrict__ D,
-                                                       const BlockMap *__restrict__ map, int cpb, int exact, T *u,
-                                                       const T *b, int cur) {
+                                                       const BlockMap *__restrict__ map, int nblocks, int cpb,
+                                                       int exact, T *u, const T *b, int cur) {
     using G = Geo<DIM, Q, T>;
     __shared__ __align__(16) BatchDG<T> sd;
-    const BlockMap m = map[blockIdx.x];
-    load_batch_desc(D + m.inst, &sd);
-    k_smooth_body<DIM, Q, T>(sd.c, m.cell0, cpb, exact, u + sd.off * G::NL, b + sd.off * G::NL, sd.kappa, sd.fd,
-                             sd.linv, sd.tr[cur], sd.tr[cur ^ 1]);
+    for (int k = blockIdx.x; k < nblocks; k += gridDim.x) {
+        if (k != (int)blockIdx.x) __syncthreads();
+        const BlockMap m = map[k];
+        load_batch_desc(D + m.inst, &sd);
+        k_smooth_body<DIM, Q, T>(sd.c, m.cell0, cpb, exact, u + sd.off * G::NL, b + sd.off * G::NL, sd.kappa, sd.fd,
+                                 sd.linv, sd.tr[cur], sd.tr[cur ^ 1]);
+    }
 }
 
 template <typename T, int Q>
 __global__ void __launch_bounds__(32) k_smooth_cells_batch(const BatchDG<T> *__restrict__ D,
-                                                            const BlockMap *__restrict__ map, T *u, const T *b,
-                                                            int cur) {
+                                                            const BlockMap *__restrict__ map, int nblocks, T *u,
+                                                            const T *b, int cur) {
     constexpr int NL = Q * Q * Q;
     __shared__ __align__(16) BatchDG<T> sd;
-    const BlockMap m = map[blockIdx.x];
-    load_batch_desc(D + m.inst, &sd);
-    smooth_cells_body<T, Q>(sd.c, m.cell0, u + sd.off * NL, b + sd.off * NL, sd.kappa, sd.fd, sd.linv,
-                            sd.tr[cur], sd.tr[cur ^ 1]);
+    for (int k = blockIdx.x; k < nblocks; k += gridDim.x) {
+        if (k != (int)blockIdx.x) __syncthreads();
+        const BlockMap m = map[k];
+        load_batch_desc(D + m.inst, &sd);
+        smooth_cells_body<T, Q>(sd.c, m.cell0, u + sd.off * NL, b + sd.off * NL, sd.kappa, sd.fd, sd.linv,
+                                sd.tr[cur], sd.tr[cur ^ 1], k != (int)blockIdx.x);
+    }
 }
 
 template <typename T, int Q>
 __global__ void __launch_bounds__(32) k_residual_cells_batch(const BatchDG<T> *__restrict__ D,
-                                                              const BlockMap *__restrict__ map, int mode, const T *u,
-                                                              const T *b, T *r, int cur) {
+                                                              const BlockMap *__restrict__ map, int nblocks, int mode,
+                                                              const T *u, const T *b, T *r, int cur) {
     constexpr int NL = Q * Q * Q;
     __shared__ __align__(16) BatchDG<T> sd;
-    const BlockMap m = map[blockIdx.x];
-    load_batch_desc(D + m.inst, &sd);
-    residual_cells_body<T, Q>(sd.c, m.cell0, mode, u + sd.off * NL, b ? b + sd.off * NL : nullptr, sd.kappa, sd.fd,
-                              sd.tr[cur], r ? r + sd.off * NL : nullptr, sd.corners);
+    for (int k = blockIdx.x; k < nblocks; k += gridDim.x) {
+        if (k != (int)blockIdx.x) __syncthreads();
+        const BlockMap m = map[k];
+        load_batch_desc(D + m.inst, &sd);
+        residual_cells_body<T, Q>(sd.c, m.cell0, mode, u + sd.off * NL, b ? b + sd.off * NL : nullptr, sd.kappa,
+                                  sd.fd, sd.tr[cur], r ? r + sd.off * NL : nullptr, sd.corners, k != (int)blockIdx.x);
+    }
 }
 
 template <int DIM, int Q, typename T>
 __global__ void __launch_bounds__(256) k_residual_batch(const BatchDG<T> *__restrict__ D,
-                                                         const BlockMap *__restrict__ map, int cpb, int mode,
-                                                         const T *u, const T *b, T *r, int cur) {
+                                                         const BlockMap *__restrict__ map, int nblocks, int cpb,
+                                                         int mode, const T *u, const T *b, T *r, int cur) {
     using G = Geo<DIM, Q, T>;
     __shared__ __align__(16) BatchDG<T> sd;
-    const BlockMap m = map[blockIdx.x];
-    load_batch_desc(D + m.inst, &sd);
-    k_residual_body<DIM, Q, T>(sd.c, m.cell0, cpb, mode, u + sd.off * G::NL, b ? b + sd.off * G::NL : nullptr,
-                               sd.kappa, sd.tr[cur], r ? r + sd.off * G::NL : nullptr, sd.corners);
+    for (int k = blockIdx.x; k < nblocks; k += gridDim.x) {
+        if (k != (int)blockIdx.x) __syncthreads();
+        const BlockMap m = map[k];
+        load_batch_desc(D + m.inst, &sd);
+        k_residual_body<DIM, Q, T>(sd.c, m.cell0, cpb, mode, u + sd.off * G::NL, b ? b + sd.off * G::NL : nullptr,
+                                   sd.kappa, sd.tr[cur], r ? r + sd.off * G::NL : nullptr, sd.corners);
+    }
 }
 
 // tr[0] of instance blockIdx.x := 0 (projections of a zero iterate)
@@ -879,7 +900,7 @@ struct DGLaunch {
     static cudaError_t project(const DGConst<T> &c, int cpb, T *u, const T *e0, T *tr, cudaStream_t s) {
         if constexpr (CELLS_OK) {
             // bulk copies want a 16-byte aligned u; the trace pieces 8- (FP32) or 16-byte (FP64) aligned traces
-            const uintptr_t tra = std::is_same<T, float>::value ? 7 : 15;
+            const uintptr_t tra = 15;   // bulk copies of whole (padded) faces
             if (cpb <= 0 && !c.gl && (reinterpret_cast<uintptr_t>(u) & 15) == 0 &&
                 (reinterpret_cast<uintptr_t>(tr) & tra) == 0) {
                 using CG = CellGeo<T, Q>;
@@ -914,7 +935,7 @@ struct DGLaunch {
         if constexpr (CELLS_OK) {
             // bulk copies want 16-byte aligned vectors, factors and table; the face
             // pieces 8- (FP32) or 16-byte (FP64) aligned traces
-            const uintptr_t tra = std::is_same<T, float>::value ? 7 : 15;
+            const uintptr_t tra = 15;   // bulk copies of whole (padded) faces
             const bool aligned = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(b) |
                                    reinterpret_cast<uintptr_t>(fd) | reinterpret_cast<uintptr_t>(linv)) & 15) == 0 &&
                                  ((reinterpret_cast<uintptr_t>(tri) | reinterpret_cast<uintptr_t>(tro)) & tra) == 0;
@@ -974,8 +995,8 @@ struct DGLaunch {
             return cudaErrorInvalidValue;
         }
     }
-    // ---- batched forms (map: one entry per CTA; cpb cells per CTA, 32 for the
-    // one-thread-per-cell smoother)
+    // ---- batched forms (map: one entry per work item of cpb cells, 32 for the
+    // one-thread-per-cell kernels; persistent grids)
     static cudaError_t project_batch(const BatchDG<T> *D, const BlockMap *map, int nblocks, int cpb, T *u,
                                      int with_e0, cudaStream_t s) {
         if (nblocks <= 0) return cudaSuccess;
@@ -986,7 +1007,9 @@ struct DGLaunch {
             attr = true;
         }
         count_launches(1);
-        k_project_batch<DIM, Q, T><<<nblocks, cpb * G::NF, smem_project<DIM, Q, T>(cpb), s>>>(D, map, cpb, u, with_e0);
+        const size_t smp = smem_project<DIM, Q, T>(cpb);
+        k_project_batch<DIM, Q, T><<<persistent_grid((const void *)k_project_batch<DIM, Q, T>, cpb * G::NF, smp, nblocks),
+                                     cpb * G::NF, smp, s>>>(D, map, nblocks, cpb, u, with_e0);
         return cudaGetLastError();
     }
     static cudaError_t smooth_batch(const BatchDG<T> *D, const BlockMap *map, int nblocks, int cpb, int exact, T *u,
@@ -1002,7 +1025,9 @@ struct DGLaunch {
                     attr = true;
                 }
                 count_launches(1);
-                k_smooth_cells_batch<T, Q><<<nblocks, CG::W, CG::BYTES, s>>>(D, map, u, b, cur);
+                k_smooth_cells_batch<T, Q><<<persistent_grid((const void *)k_smooth_cells_batch<T, Q>, CG::W, CG::BYTES,
+                                                             nblocks),
+                                             CG::W, CG::BYTES, s>>>(D, map, nblocks, u, b, cur);
                 return cudaGetLastError();
             }
         }
@@ -1013,8 +1038,9 @@ struct DGLaunch {
             attr = true;
         }
         count_launches(1);
-        k_smooth_batch<DIM, Q, T><<<nblocks, cpb * G::NF, smem_smooth<DIM, Q, T>(cpb, exact != 0), s>>>(
-            D, map, cpb, exact, u, b, cur);
+        const size_t sms = smem_smooth<DIM, Q, T>(cpb, exact != 0);
+        k_smooth_batch<DIM, Q, T><<<persistent_grid((const void *)k_smooth_batch<DIM, Q, T>, cpb * G::NF, sms, nblocks),
+                                    cpb * G::NF, sms, s>>>(D, map, nblocks, cpb, exact, u, b, cur);
         return cudaGetLastError();
     }
     static cudaError_t residual_batch(const BatchDG<T> *D, const BlockMap *map, int nblocks, int cpb, int mode,
@@ -1030,7 +1056,9 @@ struct DGLaunch {
                     attr = true;
                 }
                 count_launches(1);
-                k_residual_cells_batch<T, Q><<<nblocks, CG::W, CG::BYTES, s>>>(D, map, mode, u, b, r, cur);
+                k_residual_cells_batch<T, Q><<<persistent_grid((const void *)k_residual_cells_batch<T, Q>, CG::W,
+                                                               CG::BYTES, nblocks),
+                                               CG::W, CG::BYTES, s>>>(D, map, nblocks, mode, u, b, r, cur);
                 return cudaGetLastError();
             }
         }
@@ -1042,8 +1070,9 @@ struct DGLaunch {
             attr = true;
         }
         count_launches(1);
-        k_residual_batch<DIM, Q, T><<<nblocks, cpb * G::NF, smem_residual<DIM, Q, T>(cpb), s>>>(D, map, cpb, mode, u,
-                                                                                                b, r, cur);
+        const size_t smr = smem_residual<DIM, Q, T>(cpb);
+        k_residual_batch<DIM, Q, T><<<persistent_grid((const void *)k_residual_batch<DIM, Q, T>, cpb * G::NF, smr, nblocks),
+                                      cpb * G::NF, smr, s>>>(D, map, nblocks, cpb, mode, u, b, r, cur);
         return cudaGetLastError();
     }
     static cudaError_t zero_traces_batch(const BatchDG<T> *D, int count, cudaStream_t s) {
@@ -1057,7 +1086,7 @@ struct DGLaunch {
         if constexpr (CELLS_OK) {
             // bulk copies of u, b, the factors and r want 16-byte alignment; the
             // face pieces 8- (FP32) or 16-byte (FP64) aligned traces
-            const uintptr_t tra = std::is_same<T, float>::value ? 7 : 15;
+            const uintptr_t tra = 15;   // bulk copies of whole (padded) faces
             const uintptr_t vec = reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(fd) |
                                   ((mode & RES_HAS_B) ? reinterpret_cast<uintptr_t>(b) : 0) |
                                   ((mode & RES_WRITE_R) ? reinterpret_cast<uintptr_t>(r) : 0);

@@ -26,6 +26,15 @@ int cuda_fail(cudaError_t e, const char *what);
         if (e_ != cudaSuccess) return ::dgmg::cuda_fail(e_, #call); \
     } while (0)
 
+// Values stored per cell face in a trace buffer: the value and the normal
+// derivative at the q^(d-1) face nodes, padded so that every face of every cell
+// starts on a 16-byte boundary (a bulk copy moves one face). Only FP32 with an
+// odd number of face nodes pads (2 values per face for q = 5 in 3D).
+template <typename T>
+__host__ __device__ constexpr int trace_face_stride(int nf) {
+    return (2 * nf * (int)sizeof(T) + 15) / 16 * 16 / (int)sizeof(T);
+}
+
 // Process-wide count of kernels launched by the library (dgmg_kernel_launches).
 extern std::atomic<long long> g_kernel_launches;
 inline void count_launches(int k) { g_kernel_launches.fetch_add(k, std::memory_order_relaxed); }
@@ -193,6 +202,12 @@ struct VertMap {
     int desc, v0;
 };
 constexpr int BATCH_VERTS = 256;   // vertices (rows) per CTA of the batched Q1 kernels
+
+// CTAs of a persistent batched launch of kernel `fn` (threads per CTA, dynamic
+// shared memory) over `items` work items: as many as stay resident on the
+// current device at once, at most `items` (cached per kernel and shared-memory
+// size; a process drives devices of one kind).
+unsigned persistent_grid(const void *fn, int threads, size_t smem, int64_t items);
 
 // Launch wrappers (implemented per precision in dg_fp64.cu / dg_fp32.cu).
 // All return cudaError_t of the launch.

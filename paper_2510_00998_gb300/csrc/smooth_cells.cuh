@@ -7,17 +7,18 @@
 // staged in shared memory in the order they are consumed:
 //   - b and the fast-diagonalisation factors: one bulk (TMA) copy each,
 //     completing on an mbarrier;
-//   - the neighbours' traces, face by face through two slots, with cp.async
-//     (16-byte pieces, or 8-byte ones where a face of one cell, 2 q^2 values,
-//     is not a multiple of 16 bytes: FP32 with odd q);
+//   - the neighbours' traces, face by face through two slots: every lane
+//     fetches its neighbour's face with one bulk copy (faces are padded to
+//     16 bytes in the trace buffers), the copies of a face completing on one
+//     mbarrier whose byte count lane 0 posts;
 //   - FP32: u of the previous iterate by a bulk copy into the slot area once
 //     the faces are consumed, overlapping the inverse;
 //   - FP64: the per-node table of inverse eigenvalue sums into the slot area
 //     once the faces are consumed (FP64 division is a long sequence on the
 //     FP64 pipe, which bounds the FP64 kernel), then u of the previous iterate
 //     into the same area once the table is used, overlapping the last passes.
-// The new u leaves through a bulk store; the new traces through the face slots
-// with coalesced stores. A lane reads its own cell with stride q^3 (odd for odd
+// The new u leaves through a bulk store; every lane writes its new traces into
+// its face slots and stores each face with one bulk store. A lane reads its own cell with stride q^3 (odd for odd
 // q, so a warp's 32 loads hit 32 banks).
 //
 // The split update of the exact block (u <- (1 - w) u + w A_KK^{-1}(b - N u_nb))
@@ -86,31 +87,49 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(smem_addr(bar)) : "memory");
+}
+// Set up the CTA's mbarriers (lane 0). `reuse`: a persistent CTA's next work
+// item; every phase of the previous item has completed, so the objects are
+// invalidated first, and every lane's accesses of the staging areas are
+// ordered before the bulk copies of the new item.
+__device__ __forceinline__ void cells_init_bars(uint64_t *bars, int count, int lane, bool reuse) {
+    if (reuse) fence_proxy_async_smem();
+    __syncwarp();
+    if (lane == 0) {
+        for (int i = 0; i < count; ++i) {
+            if (reuse) mbar_inval(&bars[i]);
+            mbar_init(&bars[i], 1);
+        }
+        fence_mbar_init();
+        fence_proxy_async_smem();
+    }
+    __syncwarp();
+}
 
-// Lane 0 waits for `bar`; the outcome is shared with the warp. A wait that runs
-// out is counted, then waited for once more (the copies must land before the
-// CTA's shared memory is released).
-__device__ __forceinline__ bool warp_wait_copies(uint64_t *bar, int lane) {
+// Lane 0 waits for phase `parity` of `bar`; the outcome is shared with the
+// warp. A wait that runs out is counted, then waited for once more (the copies
+// must land before the CTA's shared memory is released).
+__device__ __forceinline__ bool warp_wait_phase(uint64_t *bar, unsigned parity, int lane) {
     int ok = 1;
     if (lane == 0) {
-        if (!mbar_wait_bounded(bar, 0)) {
+        if (!mbar_wait_bounded(bar, parity)) {
             atomicAdd(&g_wait_timeouts, 1ull);
-            mbar_wait_bounded(bar, 0);
+            mbar_wait_bounded(bar, parity);
             ok = 0;
         }
     }
     __syncwarp();
     return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
+__device__ __forceinline__ bool warp_wait_copies(uint64_t *bar, int lane) { return warp_wait_phase(bar, 0, lane); }
 
 template <typename T, int Q>
 struct CellGeo {
-    static constexpr int NL = Q * Q * Q, NF = Q * Q, TR = 12 * NF, FDS = Q * Q + Q;
+    static constexpr int NL = Q * Q * Q, NF = Q * Q, FDS = Q * Q + Q;
+    static constexpr int FS = trace_face_stride<T>(NF), TR = 6 * FS;   // trace values per face / cell
     static constexpr int W = 32;                       // cells per CTA (one per lane)
-    // copy granule of the face staging: 16 bytes where a face of one cell allows it
-    static constexpr int PIECE = (2 * NF * (int)sizeof(T)) % 16 == 0 ? 16 : 8;
-    static constexpr int PER_PIECE = PIECE / (int)sizeof(T);   // values per piece
-    static constexpr int PIECES = 2 * NF / PER_PIECE;          // pieces per face of one cell
     // FP64 (LEAN): the kernel is bound by the FP64 pipe, not by memory, so the
     // neighbour faces, the table and the previous u are read straight from
     // global memory by each lane and the traces written the same way; only
@@ -119,34 +138,29 @@ struct CellGeo {
     static constexpr bool LEAN = sizeof(T) == 8;
     // shared memory (values of T), per cell. FP32: area A holds b, then the
     // previous u (prefetched as soon as b is in registers), then the new u; area
-    // B holds two neighbour-face slots, then the factors, then two faces of new
-    // traces. FP64: area A holds b, then the factors, then the new u.
+    // B holds two neighbour-face slots (FS values each), then the factors, then
+    // two faces of new traces. FP64: area A holds b, then the factors, then the
+    // new u.
     static constexpr int PA = LEAN ? (NL > 3 * FDS ? NL : 3 * FDS) : NL;
-    static constexpr int PB = LEAN ? 0 : (4 * NF > 3 * FDS ? 4 * NF : 3 * FDS);
+    static constexpr int PB = LEAN ? 0 : (2 * FS > 3 * FDS ? 2 * FS : 3 * FDS);
     static constexpr size_t OFF_B = (size_t)W * PA;
     static constexpr size_t OFF_K = OFF_B + (size_t)W * PB;   // kF [6][W]
     static constexpr size_t OFF_NB = OFF_K + 6 * W;          // neighbour cell [6][W] (int)
     static constexpr size_t BYTES = OFF_NB * sizeof(T) + 6 * W * sizeof(int);
 };
 
-// Stage face f of the neighbours of the CTA's cells (their face f^1) into a slot.
+// Stage face f of the lane's neighbour nb (the neighbour's face f^1) into the
+// lane's part of a face slot: one bulk copy per lane that has a neighbour, all
+// completing on `bar`, whose byte count lane 0 posts before any copy is issued.
+// The caller has ended every read of the slot (proxy fence and warp barrier).
 template <typename T, int Q>
-__device__ __forceinline__ void stage_face(int f, int ncl, int lane, const int *sNb, const T *__restrict__ tr,
-                                           T *slot) {
+__device__ __forceinline__ void stage_face(int f, int nb, int lane, const T *__restrict__ tr, T *slot, uint64_t *bar) {
     using G = CellGeo<T, Q>;
-    for (int idx = lane; idx < ncl * G::PIECES; idx += G::W) {
-        const int j = idx / G::PIECES, part = idx - j * G::PIECES;
-        const int nb = sNb[f * G::W + j];
-        if (nb >= 0) {
-            T *dst = slot + j * 2 * G::NF + G::PER_PIECE * part;
-            const T *src = tr + (int64_t)nb * G::TR + (f ^ 1) * 2 * G::NF + G::PER_PIECE * part;
-            if (G::PIECE == 16)
-                cp_async16(dst, src);
-            else
-                cp_async8(dst, src);
-        }
-    }
-    cp_async_commit();
+    const unsigned with = __ballot_sync(0xffffffffu, nb >= 0);
+    if (lane == 0) mbar_arrive_expect_tx(bar, (unsigned)(__popc(with) * G::FS * (int)sizeof(T)));
+    __syncwarp();
+    if (nb >= 0)
+        bulk_load(slot + lane * G::FS, tr + (int64_t)nb * G::TR + (f ^ 1) * G::FS, (unsigned)(G::FS * sizeof(T)), bar);
 }
 
 // The cell tensor R[x + q y + q^2 z] is kept in registers and only ever worked
@@ -235,6 +249,10 @@ __device__ __forceinline__ void lift_x_face(int side, const T *fld, int sa, int 
     const T g2 = kF * gam, wv = T(0.5) * kF, sgn = side ? T(-1) : T(1);
     // value field: end layer += kF gamma G; all layers += sgn kF/2 G d
     // derivative field: end layer -= sgn kF/2 H
+    // (side may be a run-time value: the end layer of the other side gets a
+    // zero coefficient, so one copy of the code serves both faces)
+    const T lo = side ? T(0) : T(1), hi = T(1) - lo;
+    const T g_lo = lo * g2, g_hi = hi * g2, h_lo = -lo * wv, h_hi = hi * wv, swv = sgn * wv;
 #pragma unroll
     for (int comp = 0; comp < 2; ++comp) {
         const T *f = fld + comp * NF;
@@ -261,12 +279,14 @@ __device__ __forceinline__ void lift_x_face(int side, const T *fld, int sa, int 
                 const T v = wa[a] * t1[a + Q * b] - ua[a] * s;
                 T *pen = R + Q * (a + Q * b);              // the pencil along x at (a, b)
                 if (comp == 0) {
-                    const T w = sgn * wv * v;
-                    if (side) pen[Q - 1] += g2 * v; else pen[0] += g2 * v;
+                    const T w = swv * v;
+                    pen[0] += g_lo * v;
+                    pen[Q - 1] += g_hi * v;
 #pragma unroll
                     for (int n = 0; n < Q; ++n) pen[n] += w * dv[n];
                 } else {
-                    if (side) pen[Q - 1] += wv * v; else pen[0] -= wv * v;
+                    pen[0] += h_lo * v;
+                    pen[Q - 1] += h_hi * v;
                 }
             }
         }
@@ -291,50 +311,41 @@ __device__ __forceinline__ void x_face_traces(int side, const T *R, const T *dv,
         }
 }
 
-// Traces of the cell tensor R (one per lane) to tr_out[cell][face][2][q^2]: the
-// faces normal to axis p, then rotate. FP32: through area B (two faces of the
-// CTA's cells) with coalesced copy-out; FP64 (LEAN): written per lane. R ends
-// rotated.
+// Traces of the cell tensor R (one per lane) to tr_out[cell][face][FS]: the
+// faces normal to axis p, then rotate. FP32: every lane writes its two faces
+// into its face slots of area B and stores each with one bulk store (a slot is
+// rewritten once the lane's previous stores have read it); FP64 (LEAN):
+// written per lane. R ends rotated. Only lanes with `write` store.
 template <typename T, int Q>
-__device__ __forceinline__ void cells_write_traces(const DGConst<T> &c, T *R, int lane, bool active, int64_t cell,
-                                                   int64_t cell0, int ncl, T *sB, T *__restrict__ tr_out) {
+__device__ __forceinline__ void cells_write_traces(const DGConst<T> &c, T *R, int lane, bool write, int64_t cell,
+                                                   T *sB, T *__restrict__ tr_out) {
     using G = CellGeo<T, Q>;
-    constexpr int W = G::W, NF = G::NF, TR = G::TR;
+    constexpr int W = G::W, FS = G::FS, TR = G::TR;
 #pragma unroll 1
     for (int p = 0; p < 3; ++p) {
         const int sa = p == 1 ? Q : 1, sb = p == 1 ? 1 : Q;
-        if (active) {
-#pragma unroll
+        if (!G::LEAN && p > 0) bulk_wait_read_all();
+        if (write) {
+#pragma unroll 1
             for (int side = 0; side < 2; ++side) {
                 T dv[Q];
 #pragma unroll
                 for (int n = 0; n < Q; ++n) dv[n] = side ? c.dp[p][n] : c.d0[p][n];
-                T *dst = G::LEAN ? tr_out + cell * TR + (2 * p + side) * 2 * NF
-                                 : sB + side * W * 2 * NF + lane * 2 * NF;
+                T *dst = G::LEAN ? tr_out + cell * TR + (2 * p + side) * FS : sB + (side * W + lane) * FS;
                 x_face_traces<T, Q>(side, R, dv, sa, sb, dst);
             }
-        }
-        if (G::LEAN) {
-            if (p < 2) rotate<T, Q>(R);
-            continue;
-        }
-        __syncwarp();
-        // 2 faces x [W][2 NF] -> [cell][face 2p + side], in 8-byte (FP32) or 16-byte (FP64) pieces
-        // (constant divisors only: the index split is a multiply and a shift)
-        using V = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
-        constexpr int NV = NF;                          // 2 NF values = NF pieces of two
+            if (!G::LEAN) {
+                fence_proxy_async_smem();
 #pragma unroll
-        for (int side = 0; side < 2; ++side) {
-            const V *src = reinterpret_cast<const V *>(sB + side * W * 2 * NF);
-            V *dst = reinterpret_cast<V *>(tr_out + cell0 * TR + (2 * p + side) * 2 * NF);
-            for (int idx = lane; idx < ncl * NV; idx += W) {
-                const int j = idx / NV, part = idx - j * NV;
-                dst[j * (TR / 2) + part] = src[idx];
+                for (int side = 0; side < 2; ++side)
+                    bulk_store(tr_out + cell * TR + (2 * p + side) * FS, sB + (side * W + lane) * FS,
+                               (unsigned)(FS * sizeof(T)));
+                bulk_commit();
             }
         }
-        __syncwarp();
         if (p < 2) rotate<T, Q>(R);
     }
+    if (!G::LEAN) bulk_wait_read_all();
 }
 
 template <typename T>
@@ -343,6 +354,33 @@ template <>
 __device__ __forceinline__ float div_approx<float>(float a, float b) { return __fdividef(a, b); }
 template <>
 __device__ __forceinline__ double div_approx<double>(double a, double b) { return a / b; }
+
+// Divide the transformed cell tensor R[x + q y + q^2 z] by the eigenvalue sums
+// lambda_x + lambda_y + lambda_z of the fast diagonalisation (fd: the cell's
+// factors, axis a at a * (q^2 + q), lambda after S), or multiply it by the
+// precomputed table of their inverses (li, q^3 values) when there is one.
+template <typename T, int Q>
+__device__ __forceinline__ void scale_inverse(T *R, const T *fd, const T *li) {
+    constexpr int FDS = Q * Q + Q;
+    if (li) {
+#pragma unroll
+        for (int e = 0; e < Q * Q * Q; ++e) R[e] *= li[e];
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+        const T lz = fd[2 * FDS + Q * Q + k];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            const T lyz = fd[1 * FDS + Q * Q + j] + lz;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int e = i + Q * (j + Q * k);
+                R[e] = div_approx<T>(R[e], fd[Q * Q + i] + lyz);
+            }
+        }
+    }
+}
 
 // Bulk copy of `bytes` into shared memory on `bar` (lane 0 issues).
 template <typename T>
@@ -359,33 +397,31 @@ __device__ __forceinline__ void stage_bulk(bool full, int lane, uint64_t *bar, T
 }
 
 template <typename T, int Q>
-__device__ __forceinline__ void smooth_cells_body(const DGConst<T> &c, int64_t cell0, T *__restrict__ u, const T *__restrict__ b, const T *__restrict__ kappa, const T *__restrict__ fd, const T *__restrict__ linv, const T *__restrict__ tr_in, T *__restrict__ tr_out) {
+__device__ __forceinline__ void smooth_cells_body(const DGConst<T> &c, int64_t cell0, T *__restrict__ u, const T *__restrict__ b, const T *__restrict__ kappa, const T *__restrict__ fd, const T *__restrict__ linv, const T *__restrict__ tr_in, T *__restrict__ tr_out, bool reuse = false) {
     using G = CellGeo<T, Q>;
-    constexpr int W = G::W, NL = G::NL, NF = G::NF, FDS = G::FDS, TR = G::TR;
+    constexpr int W = G::W, NL = G::NL, NF = G::NF, FDS = G::FDS, TR = G::TR, FS = G::FS;
     extern __shared__ __align__(128) unsigned char smem_c[];
     T *sA = reinterpret_cast<T *>(smem_c);              // b -> previous u (FP32) or factors (FP64) -> new u
     T *sB = sA + G::OFF_B;                               // FP32: face slots -> factors -> new traces
-    // face slot s (0, 1) of area B: sB + s * W * 2 NF
+    // face slot s (0, 1) of area B, lane l: sB + (s * W + l) * FS
     T *sK = sA + G::OFF_K;
     int *sNb = reinterpret_cast<int *>(sA + G::OFF_NB);
-    __shared__ __align__(8) uint64_t bars[4];
+    // mbarriers: 0 b, 1 previous u (FP32) / factors (FP64), 2 factors (FP32),
+    // 4 and 5 the face slots (FP32; phase k = the slot's k-th face)
+    __shared__ __align__(8) uint64_t bars[6];
     __shared__ T sMw[3][Q], sMu[3][Q];
     const int lane = threadIdx.x;
     const int ncl = (int)min((int64_t)W, c.ncell - cell0);
-    const bool full = ncl == W;                          // bulk copies need whole 32-cell blocks
+    const bool full = ncl == W;                          // bulk copies of b, u, factors: whole 32-cell blocks
     const bool active = lane < ncl;
     const int64_t cell = cell0 + lane;
     const bool table = linv != nullptr;
+    bool ok = true;                                      // false once a bounded wait ran out
 
+    cells_init_bars(bars, 6, lane, reuse);
     for (int e = lane; e < 3 * Q; e += W) {
         sMw[e / Q][e % Q] = c.mw[e / Q][e % Q];
         sMu[e / Q][e % Q] = c.mu[e / Q][e % Q];
-    }
-    if (full && lane == 0) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
-        fence_mbar_init();
-        fence_proxy_async_smem();
     }
     stage_bulk<T>(full, lane, &bars[0], sA, b + cell0 * NL, W * NL, ncl * NL);
     // neighbours and facet coefficients of this lane's cell
@@ -414,19 +450,15 @@ __device__ __forceinline__ void smooth_cells_body(const DGConst<T> &c, int64_t c
     }
     __syncwarp();
     if (!G::LEAN) {
-        stage_face<T, Q>(0, ncl, lane, sNb, tr_in, sB);
-        stage_face<T, Q>(1, ncl, lane, sNb, tr_in, sB + W * 2 * NF);
+        stage_face<T, Q>(0, sNb[0 * W + lane], lane, tr_in, sB, &bars[4]);
+        stage_face<T, Q>(1, sNb[1 * W + lane], lane, tr_in, sB + W * FS, &bars[5]);
     }
 
     // r = b
-    if (full) {
-        if (!warp_wait_copies(&bars[0], lane)) {
-            cp_async_wait<0>();
-            return;
-        }
-    } else {
+    if (full)
+        ok = warp_wait_copies(&bars[0], lane) && ok;
+    else
         __syncwarp();
-    }
     T R[NL];
 #pragma unroll
     for (int e = 0; e < NL; ++e) R[e] = active ? sA[lane * NL + e] : T(0);
@@ -446,27 +478,22 @@ __device__ __forceinline__ void smooth_cells_body(const DGConst<T> &c, int64_t c
         const int ta = p == 2 ? 0 : p + 1, tb = p == 0 ? 2 : p - 1;
         const int sa = p == 1 ? Q : 1, sb = p == 1 ? 1 : Q;   // the y faces are stored transposed
         const T gam = c.gamma[p];
-#pragma unroll
+#pragma unroll 1
         for (int side = 0; side < 2; ++side) {
             const int f = 2 * p + side;
-            if (!G::LEAN) {
-                if (f < 5)
-                    cp_async_wait<1>();
-                else
-                    cp_async_wait<0>();
-                __syncwarp();
-            }
+            if (!G::LEAN) ok = warp_wait_phase(&bars[4 + side], (unsigned)(p & 1), lane) && ok;
             if (active && (mask & (1 << f))) {
 #pragma unroll
                 for (int n = 0; n < Q; ++n) dv[n] = side ? c.dp[p][n] : c.d0[p][n];
-                const T *fld = G::LEAN ? tr_in + (int64_t)sNb[f * W + lane] * TR + (f ^ 1) * 2 * NF
-                                       : sB + side * W * 2 * NF + lane * 2 * NF;
+                const T *fld = G::LEAN ? tr_in + (int64_t)sNb[f * W + lane] * TR + (f ^ 1) * FS
+                                       : sB + (side * W + lane) * FS;
                 lift_x_face<T, Q>(side, fld, sa, sb, sMw[ta], sMu[ta], sMw[tb], sMu[tb], dv, gam,
                                   sK[f * W + lane], R);
             }
-            if (!G::LEAN) {
+            if (!G::LEAN && f + 2 < 6) {
+                fence_proxy_async_smem();
                 __syncwarp();
-                if (f + 2 < 6) stage_face<T, Q>(f + 2, ncl, lane, sNb, tr_in, sB + side * W * 2 * NF);
+                stage_face<T, Q>(f + 2, sNb[(f + 2) * W + lane], lane, tr_in, sB + side * W * FS, &bars[4 + side]);
             }
         }
         rotate<T, Q>(R);
@@ -480,62 +507,31 @@ __device__ __forceinline__ void smooth_cells_body(const DGConst<T> &c, int64_t c
 
     // A_KK^{-1} by fast diagonalisation: S^T along x, y, z; scale by the
     // inverse eigenvalue sums; S along z, y, x
-    if (full) {
-        if (!warp_wait_copies(&bars[G::LEAN ? 1 : 2], lane)) {
-            if (!G::LEAN) warp_wait_copies(&bars[1], lane);
-            return;
-        }
-    } else {
+    if (full)
+        ok = warp_wait_copies(&bars[G::LEAN ? 1 : 2], lane) && ok;
+    else
         __syncwarp();
-    }
     const T *myFD = (G::LEAN ? sA : sB) + lane * 3 * FDS;
-    if (active) {
+    // S^T along x, y, z; the inverse eigenvalue sums; S along x, y, z (the
+    // tensor-product factors commute, so both halves take the axes in the same
+    // order and one loop body serves all six passes)
 #pragma unroll 1
-        for (int p = 0; p < 3; ++p) {
-            T S[Q * Q];
-            load_matrix<T, Q, true>(myFD + p * FDS, S);
-            pass_x<T, Q>(S, R);
-            rotate<T, Q>(R);
-        }
+    for (int k = 0; k < 6 && active; ++k) {
+        if (k == 3) scale_inverse<T, Q>(R, myFD, table ? linv + cell * NL : nullptr);
+        T S[Q * Q];
+        if (k < 3)
+            load_matrix<T, Q, true>(myFD + k * FDS, S);
+        else
+            load_matrix<T, Q, false>(myFD + (k - 3) * FDS, S);
+        pass_x<T, Q>(S, R);
+        rotate<T, Q>(R);
     }
-    if (active) {
-        if (table) {
-            const T *li = linv + cell * NL;
-#pragma unroll
-            for (int e = 0; e < NL; ++e) R[e] *= li[e];
-        } else {
-#pragma unroll
-            for (int k = 0; k < Q; ++k) {
-                const T lz = myFD[2 * FDS + Q * Q + k];
-#pragma unroll
-                for (int j = 0; j < Q; ++j) {
-                    const T lyz = myFD[1 * FDS + Q * Q + j] + lz;
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) {
-                        const int e = i + Q * (j + Q * k);
-                        R[e] = div_approx<T>(R[e], myFD[Q * Q + i] + lyz);
-                    }
-                }
-            }
-        }
-    }
-    if (active) {
-#pragma unroll 1
-        for (int p = 2; p >= 0; --p) {
-            T S[Q * Q];
-            rotate_back<T, Q>(R);
-            load_matrix<T, Q, false>(myFD + p * FDS, S);
-            pass_x<T, Q>(S, R);
-        }
-    }
-
     // u <- (1 - w) u + w y, stored through area A (the barrier also ends every
     // lane's reads of the factors before area A (FP64) or B (FP32) is rewritten)
-    if (!G::LEAN && full) {
-        if (!warp_wait_copies(&bars[1], lane)) return;
-    } else {
+    if (!G::LEAN && full)
+        ok = warp_wait_copies(&bars[1], lane) && ok;
+    else
         __syncwarp();
-    }
     T *myU = sA + lane * NL;
     if (active) {
         const T om = c.omega, keep = T(1) - om;
@@ -547,18 +543,21 @@ __device__ __forceinline__ void smooth_cells_body(const DGConst<T> &c, int64_t c
     }
     fence_proxy_async_smem();
     __syncwarp();
-    if (full) {
-        if (lane == 0) {
-            bulk_store(u + cell0 * NL, sA, (unsigned)(W * NL * sizeof(T)));
-            bulk_commit();
+    // a launch whose wait ran out leaves u and the traces of its cells unchanged
+    if (ok) {
+        if (full) {
+            if (lane == 0) {
+                bulk_store(u + cell0 * NL, sA, (unsigned)(W * NL * sizeof(T)));
+                bulk_commit();
+            }
+        } else {
+            for (int e = lane; e < ncl * NL; e += W) u[cell0 * NL + e] = sA[e];
         }
-    } else {
-        for (int e = lane; e < ncl * NL; e += W) u[cell0 * NL + e] = sA[e];
+        // traces of the new iterate
+        cells_write_traces<T, Q>(c, R, lane, active, cell, sB, tr_out);
     }
-
-    // traces of the new iterate
-    cells_write_traces<T, Q>(c, R, lane, active, cell, cell0, ncl, sB, tr_out);
-    if (full && lane == 0) bulk_wait_read_all();
+    bulk_wait_read_all();
+    (void)NF;
 }
 
 // Warm-up projection (Alg. 4 preamble) with one thread per cell, 3D, GLL:
@@ -644,8 +643,8 @@ __device__ __forceinline__ void project_cells_body(const DGConst<T> &c, int64_t 
             for (int e = lane; e < ncl * NL; e += W) u[cell0 * NL + e] = sA[e];
         }
     }
-    cells_write_traces<T, Q>(c, R, lane, active, cell, cell0, ncl, sB, tr);
-    if (e0 != nullptr && full && lane == 0) bulk_wait_read_all();
+    cells_write_traces<T, Q>(c, R, lane, active, cell, sB, tr);
+    bulk_wait_read_all();
 }
 
 template <typename T, int Q>
@@ -693,15 +692,17 @@ __device__ __forceinline__ void residual_cells_body(const DGConst<T> &c, int64_t
                                                     const T *__restrict__ u, const T *__restrict__ b,
                                                     const T *__restrict__ kappa, const T *__restrict__ fd,
                                                     const T *__restrict__ tr, T *__restrict__ rout,
-                                                    T *__restrict__ corners) {
+                                                    T *__restrict__ corners, bool reuse = false) {
     using G = CellGeo<T, Q>;
-    constexpr int W = G::W, NL = G::NL, NF = G::NF, FDS = G::FDS, TR = G::TR;
+    constexpr int W = G::W, NL = G::NL, NF = G::NF, FDS = G::FDS, TR = G::TR, FS = G::FS;
     extern __shared__ __align__(128) unsigned char smem_c[];
     T *sA = reinterpret_cast<T *>(smem_c);              // u -> b (FP32) or factors (FP64) -> r
     T *sB = sA + G::OFF_B;                               // FP32: factors -> face slots
     T *sK = sA + G::OFF_K;
     int *sNb = reinterpret_cast<int *>(sA + G::OFF_NB);
-    __shared__ __align__(8) uint64_t bars[4];
+    // mbarriers: 0 u, 1 b (FP32) / factors (FP64), 2 factors (FP32), 4 and 5
+    // the face slots (FP32; phase k = the slot's k-th face)
+    __shared__ __align__(8) uint64_t bars[6];
     __shared__ T sM[3][Q * Q], sMw[3][Q], sMu[3][Q];
     const int lane = threadIdx.x;
     const int ncl = (int)min((int64_t)W, c.ncell - cell0);
@@ -710,17 +711,13 @@ __device__ __forceinline__ void residual_cells_body(const DGConst<T> &c, int64_t
     const int64_t cell = cell0 + lane;
     const bool has_b = (mode & RES_HAS_B) != 0;
 
+    cells_init_bars(bars, 6, lane, reuse);
     for (int e = lane; e < 3 * Q * Q; e += W) sM[e / (Q * Q)][e % (Q * Q)] = c.M[e / (Q * Q)][e % (Q * Q)];
     for (int e = lane; e < 3 * Q; e += W) {
         sMw[e / Q][e % Q] = c.mw[e / Q][e % Q];
         sMu[e / Q][e % Q] = c.mu[e / Q][e % Q];
     }
-    if (full && lane == 0) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
-        fence_mbar_init();
-        fence_proxy_async_smem();
-    }
+    bool ok = true;                                      // false once a bounded wait ran out
     stage_bulk<T>(full, lane, &bars[0], sA, u + cell0 * NL, W * NL, ncl * NL);
     if (!G::LEAN) stage_bulk<T>(full, lane, &bars[2], sB, fd + cell0 * 3 * FDS, W * 3 * FDS, ncl * 3 * FDS);
     int mask = 0;
@@ -748,14 +745,10 @@ __device__ __forceinline__ void residual_cells_body(const DGConst<T> &c, int64_t
     }
     __syncwarp();
 
-    if (full) {
-        if (!warp_wait_copies(&bars[0], lane)) {
-            if (!G::LEAN) warp_wait_copies(&bars[2], lane);
-            return;
-        }
-    } else {
+    if (full)
+        ok = warp_wait_copies(&bars[0], lane) && ok;
+    else
         __syncwarp();
-    }
     T R[NL];
 #pragma unroll
     for (int e = 0; e < NL; ++e) R[e] = active ? sA[lane * NL + e] : T(0);
@@ -768,48 +761,41 @@ __device__ __forceinline__ void residual_cells_body(const DGConst<T> &c, int64_t
         stage_bulk<T>(full, lane, &bars[1], sA, b + cell0 * NL, W * NL, ncl * NL);
     const bool b_staged = !G::LEAN && has_b;
 
-    // R = A_KK u: P along x, y, z; times the eigenvalue sums; P^T along z, y, x
-    if (full) {
-        if (!warp_wait_copies(&bars[G::LEAN ? 1 : 2], lane)) {
-            if (b_staged) warp_wait_copies(&bars[1], lane);
-            return;
-        }
-    } else {
+    // R = A_KK u: P along x, y, z; times the eigenvalue sums; P^T along x, y, z
+    // (the tensor-product factors commute: one loop body for all six passes)
+    if (full)
+        ok = warp_wait_copies(&bars[G::LEAN ? 1 : 2], lane) && ok;
+    else
         __syncwarp();
-    }
     const T *myFD = (G::LEAN ? sA : sB) + lane * 3 * FDS;
-    if (active) {
 #pragma unroll 1
-        for (int p = 0; p < 3; ++p) {
-            T P[Q * Q];
-            load_mass_factor<T, Q, false>(myFD + p * FDS, sM[p], P);
-            pass_x<T, Q>(P, R);
-            rotate<T, Q>(R);
-        }
+    for (int k = 0; k < 6 && active; ++k) {
+        if (k == 3) {
 #pragma unroll
-        for (int k = 0; k < Q; ++k) {
-            const T lz = myFD[2 * FDS + Q * Q + k];
+            for (int kz = 0; kz < Q; ++kz) {
+                const T lz = myFD[2 * FDS + Q * Q + kz];
 #pragma unroll
-            for (int j = 0; j < Q; ++j) {
-                const T lyz = myFD[1 * FDS + Q * Q + j] + lz;
+                for (int j = 0; j < Q; ++j) {
+                    const T lyz = myFD[1 * FDS + Q * Q + j] + lz;
 #pragma unroll
-                for (int i = 0; i < Q; ++i) R[i + Q * (j + Q * k)] *= myFD[Q * Q + i] + lyz;
+                    for (int i = 0; i < Q; ++i) R[i + Q * (j + Q * kz)] *= myFD[Q * Q + i] + lyz;
+                }
             }
         }
-#pragma unroll 1
-        for (int p = 2; p >= 0; --p) {
-            T P[Q * Q];
-            rotate_back<T, Q>(R);
-            load_mass_factor<T, Q, true>(myFD + p * FDS, sM[p], P);
-            pass_x<T, Q>(P, R);
-        }
+        T P[Q * Q];
+        const int ax = k < 3 ? k : k - 3;
+        if (k < 3)
+            load_mass_factor<T, Q, false>(myFD + ax * FDS, sM[ax], P);
+        else
+            load_mass_factor<T, Q, true>(myFD + ax * FDS, sM[ax], P);
+        pass_x<T, Q>(P, R);
+        rotate<T, Q>(R);
     }
     // R = b - A_KK u
-    if (b_staged && full) {
-        if (!warp_wait_copies(&bars[1], lane)) return;
-    } else {
+    if (b_staged && full)
+        ok = warp_wait_copies(&bars[1], lane) && ok;
+    else
         __syncwarp();
-    }
     if (active) {
         const T *bb = has_b ? (G::LEAN ? b + cell * NL : sA + lane * NL) : nullptr;
 #pragma unroll
@@ -819,8 +805,8 @@ __device__ __forceinline__ void residual_cells_body(const DGConst<T> &c, int64_t
     if (!G::LEAN) {
         fence_proxy_async_smem();
         __syncwarp();
-        stage_face<T, Q>(0, ncl, lane, sNb, tr, sB);
-        stage_face<T, Q>(1, ncl, lane, sNb, tr, sB + W * 2 * NF);
+        stage_face<T, Q>(0, sNb[0 * W + lane], lane, tr, sB, &bars[4]);
+        stage_face<T, Q>(1, sNb[1 * W + lane], lane, tr, sB + W * FS, &bars[5]);
     }
     // R -= N u_nb, face pair by face pair as in the smoothing step
 #pragma unroll 1
@@ -829,27 +815,22 @@ __device__ __forceinline__ void residual_cells_body(const DGConst<T> &c, int64_t
         const int ta = p == 2 ? 0 : p + 1, tb = p == 0 ? 2 : p - 1;
         const int sa = p == 1 ? Q : 1, sb = p == 1 ? 1 : Q;
         const T gam = c.gamma[p];
-#pragma unroll
+#pragma unroll 1
         for (int side = 0; side < 2; ++side) {
             const int f = 2 * p + side;
-            if (!G::LEAN) {
-                if (f < 5)
-                    cp_async_wait<1>();
-                else
-                    cp_async_wait<0>();
-                __syncwarp();
-            }
+            if (!G::LEAN) ok = warp_wait_phase(&bars[4 + side], (unsigned)(p & 1), lane) && ok;
             if (active && (mask & (1 << f))) {
 #pragma unroll
                 for (int n = 0; n < Q; ++n) dv[n] = side ? c.dp[p][n] : c.d0[p][n];
-                const T *fld = G::LEAN ? tr + (int64_t)sNb[f * W + lane] * TR + (f ^ 1) * 2 * NF
-                                       : sB + side * W * 2 * NF + lane * 2 * NF;
+                const T *fld = G::LEAN ? tr + (int64_t)sNb[f * W + lane] * TR + (f ^ 1) * FS
+                                       : sB + (side * W + lane) * FS;
                 lift_x_face<T, Q>(side, fld, sa, sb, sMw[ta], sMu[ta], sMw[tb], sMu[tb], dv, gam,
                                   sK[f * W + lane], R);
             }
-            if (!G::LEAN) {
+            if (!G::LEAN && f + 2 < 6) {
+                fence_proxy_async_smem();
                 __syncwarp();
-                if (f + 2 < 6) stage_face<T, Q>(f + 2, ncl, lane, sNb, tr, sB + side * W * 2 * NF);
+                stage_face<T, Q>(f + 2, sNb[(f + 2) * W + lane], lane, tr, sB + side * W * FS, &bars[4 + side]);
             }
         }
         rotate<T, Q>(R);
@@ -858,7 +839,7 @@ __device__ __forceinline__ void residual_cells_body(const DGConst<T> &c, int64_t
 #pragma unroll
         for (int e = 0; e < NL; ++e) R[e] = -R[e];
     }
-    if (mode & RES_WRITE_R) {
+    if ((mode & RES_WRITE_R) && ok) {
         __syncwarp();                                  // every lane is done with area A
         if (active) {
 #pragma unroll
@@ -875,7 +856,7 @@ __device__ __forceinline__ void residual_cells_body(const DGConst<T> &c, int64_t
             for (int e = lane; e < ncl * NL; e += W) rout[cell0 * NL + e] = sA[e];
         }
     }
-    if ((mode & RES_CORNERS) && active) {
+    if ((mode & RES_CORNERS) && active && ok) {
         // corner (cx, cy, cz): sum over the nodes of hat_cx(x_i) hat_cy(y_j) hat_cz(z_k) r_ijk
         T X[2][Q * Q];
 #pragma unroll
@@ -913,7 +894,7 @@ __device__ __forceinline__ void residual_cells_body(const DGConst<T> &c, int64_t
 #pragma unroll
         for (int k = 0; k < 8; ++k) corners[cell * 8 + k] = out[k];
     }
-    if ((mode & RES_WRITE_R) && full && lane == 0) bulk_wait_read_all();
+    bulk_wait_read_all();
 }
 
 template <typename T, int Q>

@@ -369,9 +369,10 @@ def fifo_latencies(arrivals, service):
     return out
 
 
-def serve_trace(reqs, arrivals, budget, max_active, precision=1):
+def serve_trace(reqs, arrivals, budget, max_active, precision=1, return_x=False):
     """Submit each request at its arrival time to a server; returns
-    (latencies, makespan, stats list)."""
+    (latencies, makespan, stats list, server info), and the solutions with
+    `return_x`."""
     import torch
     from . import dgmg
     srv = dgmg.Server(budget, max_active, precision=precision)
@@ -400,6 +401,8 @@ def serve_trace(reqs, arrivals, budget, max_active, precision=1):
     stats = [done[i][1] for i in range(len(reqs))]
     info = srv.info()
     srv.close()
+    if return_x:
+        return lat, makespan, stats, info, xs
     return lat, makespan, stats, info
 
 
