@@ -505,16 +505,33 @@ cudaError_t launch_accumulate_f2d(int64_t n, double *x, float *xs, cudaStream_t 
 // equals a value it cannot reach, which keeps the work live without a store.
 __device__ double g_fma_sink;   // external linkage: the store cannot be dropped
 
+// Register operands only: a and b pass through an opaque move per chain, so the
+// multiply-add reads no constant-bank operand.
+__device__ __forceinline__ double opaque(double v) {
+    double r;
+    asm volatile("mov.b64 %0, %1;" : "=d"(r) : "d"(v));
+    return r;
+}
+__device__ __forceinline__ float opaque(float v) {
+    float r;
+    asm volatile("mov.b32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
 template <typename T, int CH>
 __global__ void __launch_bounds__(256) k_fma_loop(int iters, T a, T b) {
-    T x[CH];
+    T x[CH], ac[CH], bc[CH];
 #pragma unroll
-    for (int c = 0; c < CH; ++c) x[c] = (T)(threadIdx.x + c) * (T)1e-3;
+    for (int c = 0; c < CH; ++c) {
+        x[c] = (T)(threadIdx.x + c) * (T)1e-3;
+        ac[c] = opaque(a);
+        bc[c] = opaque(b);
+    }
     for (int i = 0; i < iters; ++i) {
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int c = 0; c < CH; ++c) x[c] = fma(x[c], a, b);
+            for (int c = 0; c < CH; ++c) x[c] = fma(x[c], ac[c], bc[c]);
     }
     T s = T(0);
 #pragma unroll
@@ -526,7 +543,7 @@ __global__ void __launch_bounds__(256) k_fma_loop(int iters, T a, T b) {
 template <int CH>
 __global__ void __launch_bounds__(256) k_fma_loop_x2(int iters, float a, float b) {
     float2 x[CH];
-    const float2 a2 = make_float2(a, a), b2 = make_float2(b, b);
+    const float2 a2 = make_float2(opaque(a), opaque(a)), b2 = make_float2(opaque(b), opaque(b));
 #pragma unroll
     for (int c = 0; c < CH; ++c) x[c] = make_float2((threadIdx.x + c) * 1e-3f, (threadIdx.x + c) * 2e-3f);
     for (int i = 0; i < iters; ++i) {

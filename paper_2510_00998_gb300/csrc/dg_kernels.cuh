@@ -309,22 +309,25 @@ __device__ __forceinline__ void build_block_1d(const DGConst<T> &c, const T *sT,
 // 2D: a = M_y u, bb = Kt_y u; y = Kt_x a + M_x bb. Contains barriers.
 template <int DIM, int Q, typename T>
 __device__ __forceinline__ void subtract_block_apply(const DGConst<T> &c, bool active, int t, const T *myU, T *myR,
-                                                     T *myA, T *myB, const T *myKT) {
+                                                     T *myA, T *myB, const T *myKT, const T *sMw, const T *sMu) {
     using G = Geo<DIM, Q, T>;
     constexpr int D = DIM - 1;   // first pass along the highest axis
+    // the 1D masses in their rank-one form M x = w o x - mu (mu . x) (exact
+    // for the GLL mass; mu = 0 for the diagonal GL mass): 3q operations per
+    // pencil instead of q^2
     if (active) {
         T x[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) x[i] = myU[G::vidx(D, t, i)];
+        T dz = T(0);
+#pragma unroll
+        for (int m = 0; m < Q; ++m) dz += sMu[D * Q + m] * x[m];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            T sa = T(0), sb = T(0);
+            T sb = T(0);
 #pragma unroll
-            for (int m = 0; m < Q; ++m) {
-                sa += c.M[D][i * Q + m] * x[m];
-                sb += myKT[D * Q * Q + i * Q + m] * x[m];
-            }
-            myA[G::vidx(D, t, i)] = sa;
+            for (int m = 0; m < Q; ++m) sb += myKT[D * Q * Q + i * Q + m] * x[m];
+            myA[G::vidx(D, t, i)] = sMw[D * Q + i] * x[i] - sMu[D * Q + i] * dz;
             myB[G::vidx(D, t, i)] = sb;
         }
     }
@@ -337,15 +340,18 @@ __device__ __forceinline__ void subtract_block_apply(const DGConst<T> &c, bool a
                 xa[i] = myA[G::vidx(1, t, i)];
                 xb[i] = myB[G::vidx(1, t, i)];
             }
+            T da = T(0), db = T(0);
+#pragma unroll
+            for (int m = 0; m < Q; ++m) {
+                da += sMu[Q + m] * xa[m];
+                db += sMu[Q + m] * xb[m];
+            }
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                T sc = T(0), se = T(0);
+                T se = sMw[Q + i] * xb[i] - sMu[Q + i] * db;
 #pragma unroll
-                for (int m = 0; m < Q; ++m) {
-                    sc += c.M[1][i * Q + m] * xa[m];
-                    se += myKT[1 * Q * Q + i * Q + m] * xa[m] + c.M[1][i * Q + m] * xb[m];
-                }
-                myA[G::vidx(1, t, i)] = sc;
+                for (int m = 0; m < Q; ++m) se += myKT[1 * Q * Q + i * Q + m] * xa[m];
+                myA[G::vidx(1, t, i)] = sMw[Q + i] * xa[i] - sMu[Q + i] * da;
                 myB[G::vidx(1, t, i)] = se;
             }
         }
@@ -358,11 +364,14 @@ __device__ __forceinline__ void subtract_block_apply(const DGConst<T> &c, bool a
             xa[i] = myA[G::vidx(0, t, i)];
             xb[i] = myB[G::vidx(0, t, i)];
         }
+        T db = T(0);
+#pragma unroll
+        for (int m = 0; m < Q; ++m) db += sMu[m] * xb[m];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            T s = T(0);
+            T s = sMw[i] * xb[i] - sMu[i] * db;
 #pragma unroll
-            for (int m = 0; m < Q; ++m) s += myKT[i * Q + m] * xa[m] + c.M[0][i * Q + m] * xb[m];
+            for (int m = 0; m < Q; ++m) s += myKT[i * Q + m] * xa[m];
             myR[G::vidx(0, t, i)] -= s;
         }
     }
@@ -537,7 +546,7 @@ __device__ __forceinline__ void k_smooth_body(const DGConst<T> &c, int64_t cell0
     lift_neighbours<DIM, Q, T>(c, active, t, myR, myF, myK, mask);
     if (!exact)
         subtract_block_apply<DIM, Q, T>(c, active, t, myU, myR, sA + lc * G::NL, sB + lc * G::NL,
-                                        sKT + lc * DIM * Q * Q);
+                                        sKT + lc * DIM * Q * Q, sMw, sMu);
     const T *myS = sFD + lc * DIM * G::FDSP;     // S_a at a*FDSP, lambda_a at a*FDSP + Q*Q
     // S^T along the axes 0..DIM-2
 #pragma unroll
@@ -704,7 +713,7 @@ __device__ __forceinline__ void k_residual_body(const DGConst<T> &c, int64_t cel
     T *myR = sR + lc * G::NL;
     T *myU = sU + lc * G::NL;
     lift_neighbours<DIM, Q, T>(c, active, t, myR, myF, myK, mask);
-    subtract_block_apply<DIM, Q, T>(c, active, t, myU, myR, sA + lc * G::NL, sB + lc * G::NL, myKT);
+    subtract_block_apply<DIM, Q, T>(c, active, t, myU, myR, sA + lc * G::NL, sB + lc * G::NL, myKT, sMw, sMu);
     T rr[Q];
     if (active) {
 #pragma unroll
@@ -898,7 +907,7 @@ struct DGLaunch {
         return c;
     }
     static cudaError_t project(const DGConst<T> &c, int cpb, T *u, const T *e0, T *tr, cudaStream_t s) {
-        if constexpr (CELLS_OK) {
+        if constexpr (CELLS_OK) if (c.ncell < (int64_t(1) << 31)) {   // 32-bit cell indices
             // bulk copies want a 16-byte aligned u; the trace pieces 8- (FP32) or 16-byte (FP64) aligned traces
             const uintptr_t tra = 15;   // bulk copies of whole (padded) faces
             if (cpb <= 0 && !c.gl && (reinterpret_cast<uintptr_t>(u) & 15) == 0 &&
@@ -932,7 +941,7 @@ struct DGLaunch {
     }
     static cudaError_t smooth(const DGConst<T> &c, int cpb, int exact, T *u, const T *b, const T *kappa,
                               const T *fd, const T *linv, const T *tri, T *tro, cudaStream_t s) {
-        if constexpr (CELLS_OK) {
+        if constexpr (CELLS_OK) if (c.ncell < (int64_t(1) << 31)) {   // 32-bit cell indices
             // bulk copies want 16-byte aligned vectors, factors and table; the face
             // pieces 8- (FP32) or 16-byte (FP64) aligned traces
             const uintptr_t tra = 15;   // bulk copies of whole (padded) faces
@@ -1083,7 +1092,7 @@ struct DGLaunch {
     }
     static cudaError_t residual(const DGConst<T> &c, int cpb, int mode, const T *u, const T *b, const T *kappa,
                                 const T *tr, T *r, T *corners, const T *fd, cudaStream_t s) {
-        if constexpr (CELLS_OK) {
+        if constexpr (CELLS_OK) if (c.ncell < (int64_t(1) << 31)) {   // 32-bit cell indices
             // bulk copies of u, b, the factors and r want 16-byte alignment; the
             // face pieces 8- (FP32) or 16-byte (FP64) aligned traces
             const uintptr_t tra = 15;   // bulk copies of whole (padded) faces

@@ -125,6 +125,16 @@ __device__ __forceinline__ bool warp_wait_phase(uint64_t *bar, unsigned parity, 
 }
 __device__ __forceinline__ bool warp_wait_copies(uint64_t *bar, int lane) { return warp_wait_phase(bar, 0, lane); }
 
+// Cell coordinates with 32-bit division (the one-thread-per-cell kernels run on
+// meshes of fewer than 2^31 cells; the launchers check).
+__device__ __forceinline__ void cell_coords32(int64_t cell, const int *n, int *ci) {
+    const unsigned c = (unsigned)cell, n0 = (unsigned)n[0], n1 = (unsigned)n[1];
+    const unsigned r = c / n0;
+    ci[0] = (int)(c - r * n0);
+    ci[1] = (int)(r % n1);
+    ci[2] = (int)(r / n1);
+}
+
 template <typename T, int Q>
 struct CellGeo {
     static constexpr int NL = Q * Q * Q, NF = Q * Q, FDS = Q * Q + Q;
@@ -249,10 +259,6 @@ __device__ __forceinline__ void lift_x_face(int side, const T *fld, int sa, int 
     const T g2 = kF * gam, wv = T(0.5) * kF, sgn = side ? T(-1) : T(1);
     // value field: end layer += kF gamma G; all layers += sgn kF/2 G d
     // derivative field: end layer -= sgn kF/2 H
-    // (side may be a run-time value: the end layer of the other side gets a
-    // zero coefficient, so one copy of the code serves both faces)
-    const T lo = side ? T(0) : T(1), hi = T(1) - lo;
-    const T g_lo = lo * g2, g_hi = hi * g2, h_lo = -lo * wv, h_hi = hi * wv, swv = sgn * wv;
 #pragma unroll
     for (int comp = 0; comp < 2; ++comp) {
         const T *f = fld + comp * NF;
@@ -279,14 +285,12 @@ __device__ __forceinline__ void lift_x_face(int side, const T *fld, int sa, int 
                 const T v = wa[a] * t1[a + Q * b] - ua[a] * s;
                 T *pen = R + Q * (a + Q * b);              // the pencil along x at (a, b)
                 if (comp == 0) {
-                    const T w = swv * v;
-                    pen[0] += g_lo * v;
-                    pen[Q - 1] += g_hi * v;
+                    const T w = sgn * wv * v;
+                    if (side) pen[Q - 1] += g2 * v; else pen[0] += g2 * v;
 #pragma unroll
                     for (int n = 0; n < Q; ++n) pen[n] += w * dv[n];
                 } else {
-                    pen[0] += h_lo * v;
-                    pen[Q - 1] += h_hi * v;
+                    if (side) pen[Q - 1] += wv * v; else pen[0] -= wv * v;
                 }
             }
         }
@@ -424,34 +428,37 @@ __device__ __forceinline__ void smooth_cells_body(const DGConst<T> &c, int64_t c
         sMu[e / Q][e % Q] = c.mu[e / Q][e % Q];
     }
     stage_bulk<T>(full, lane, &bars[0], sA, b + cell0 * NL, W * NL, ncl * NL);
-    // neighbours and facet coefficients of this lane's cell
+    // neighbours of this lane's cell; the first two neighbour faces are
+    // requested before the coefficients are loaded, so their copies overlap
+    // the kappa loads
     int mask = 0;
-    {
-        T kK = T(1);
-        if (active) {
-            int ci[3];
-            cell_coords<3>(cell, c.n, ci);
-            mask = interior_mask<3>(ci, c.n);
-            kK = kappa[cell];
-        }
+    if (active) {
+        int ci[3];
+        cell_coords32(cell, c.n, ci);
+        mask = interior_mask<3>(ci, c.n);
+    }
 #pragma unroll
-        for (int f = 0; f < 6; ++f) {
-            int nb = -1;
-            T kF = T(0);
-            if (mask & (1 << f)) {
-                const int64_t s = axis_stride<3>(c.n, f >> 1);
-                nb = (int)((f & 1) ? cell + s : cell - s);
-                const T kN = kappa[nb];
-                kF = T(2) * kK * kN / (kK + kN);
-            }
-            sNb[f * W + lane] = nb;
-            sK[f * W + lane] = kF;
+    for (int f = 0; f < 6; ++f) {
+        int nb = -1;
+        if (mask & (1 << f)) {
+            const int s = f < 2 ? 1 : (f < 4 ? c.n[0] : c.n[0] * c.n[1]);
+            nb = (int)cell + ((f & 1) ? s : -s);
         }
+        sNb[f * W + lane] = nb;
     }
     __syncwarp();
     if (!G::LEAN) {
         stage_face<T, Q>(0, sNb[0 * W + lane], lane, tr_in, sB, &bars[4]);
         stage_face<T, Q>(1, sNb[1 * W + lane], lane, tr_in, sB + W * FS, &bars[5]);
+    }
+    // facet coefficients: harmonic means of kappa (0 where there is no neighbour)
+    {
+        const T kK = active ? kappa[cell] : T(1);
+        T kN[6];
+#pragma unroll
+        for (int f = 0; f < 6; ++f) kN[f] = (mask & (1 << f)) ? kappa[sNb[f * W + lane]] : T(0);
+#pragma unroll
+        for (int f = 0; f < 6; ++f) sK[f * W + lane] = (mask & (1 << f)) ? T(2) * kK * kN[f] / (kK + kN[f]) : T(0);
     }
 
     // r = b
@@ -478,7 +485,7 @@ __device__ __forceinline__ void smooth_cells_body(const DGConst<T> &c, int64_t c
         const int ta = p == 2 ? 0 : p + 1, tb = p == 0 ? 2 : p - 1;
         const int sa = p == 1 ? Q : 1, sb = p == 1 ? 1 : Q;   // the y faces are stored transposed
         const T gam = c.gamma[p];
-#pragma unroll 1
+#pragma unroll
         for (int side = 0; side < 2; ++side) {
             const int f = 2 * p + side;
             if (!G::LEAN) ok = warp_wait_phase(&bars[4 + side], (unsigned)(p & 1), lane) && ok;
@@ -725,7 +732,7 @@ __device__ __forceinline__ void residual_cells_body(const DGConst<T> &c, int64_t
         T kK = T(1);
         if (active) {
             int ci[3];
-            cell_coords<3>(cell, c.n, ci);
+            cell_coords32(cell, c.n, ci);
             mask = interior_mask<3>(ci, c.n);
             kK = kappa[cell];
         }
@@ -815,7 +822,7 @@ __device__ __forceinline__ void residual_cells_body(const DGConst<T> &c, int64_t
         const int ta = p == 2 ? 0 : p + 1, tb = p == 0 ? 2 : p - 1;
         const int sa = p == 1 ? Q : 1, sb = p == 1 ? 1 : Q;
         const T gam = c.gamma[p];
-#pragma unroll 1
+#pragma unroll
         for (int side = 0; side < 2; ++side) {
             const int f = 2 * p + side;
             if (!G::LEAN) ok = warp_wait_phase(&bars[4 + side], (unsigned)(p & 1), lane) && ok;
