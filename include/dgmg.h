@@ -456,6 +456,24 @@ int dgmg_coarse_solve(dgmg_ctx *ctx, const double *r, double *e, void *stream);
 /* Unknowns of Q1 level `level` (HOST query); -1 if out of range. */
 int64_t dgmg_cg_size(const dgmg_ctx *ctx, int level);
 
+/*
+ * The volume term of the operator on its own, r = b - kappa_K E u_K for every
+ * cell, where E is the element stiffness matrix of a unit coefficient, the
+ * cell integral (grad u, grad v)_K of Eq. weak_form_IP, one dense q^3 x q^3
+ * matrix shared by all cells of the uniform mesh (Sec. 4.1: the dense local
+ * mat-vecs): the cell contraction that could run on the tensor cores, exposed
+ * to measure that choice. 3D, p = 4 (q = 5) only. u, b, r: DEVICE FP32 DG
+ * vectors (layout as above, 16-byte aligned, r aliasing neither u nor b);
+ * kappa is ctx's coefficient. method 0: sum factorisation on the CUDA cores
+ * (FP32; the shared generalised eigenvectors of the 1D stiffness and mass
+ * factor E into six passes of q x q matrices); method 1: a dense contraction
+ * D = U E^T on the tensor cores (tcgen05, TF32 operands, FP32 accumulation,
+ * tiles of 128 cells; results to TF32 accuracy, about 1e-3 relative). The
+ * first call builds E and the factors (a one-time device allocation in ctx).
+ * DGMG_EINVAL for another dimension or degree, or misaligned vectors.
+ */
+int dgmg_volume_residual_f32(dgmg_ctx *ctx, const float *u, const float *b, float *r, int method, void *stream);
+
 /* ---- instrumentation ---- */
 
 /*

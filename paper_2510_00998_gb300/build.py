@@ -16,6 +16,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdgmg.so")
 SOURCES = ["dg_fp64.cu", "dg_fp32.cu", "ctx.cu", "solver.cu", "server.cu", "batch.cu", "cg.cu", "blas.cu", "noalloc.cu",
+           "volume.cu",
            "factors.cu", "refelem.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -1555,12 +1555,13 @@ long long dgmg_kernel_launches(void) { return g_kernel_launches.load(); }
 
 int dgmg_wait_timeouts(unsigned long long *count) {
     if (!count) return fail(DGMG_EINVAL, "dgmg_wait_timeouts: count is NULL");
-    unsigned long long a = 0, b = 0, c = 0;
+    unsigned long long a = 0, b = 0, c = 0, v = 0;
     cudaError_t e = wait_timeouts_fp32(&a);
     if (e == cudaSuccess) e = wait_timeouts_fp64(&b);
     if (e == cudaSuccess) e = q1_barrier_timeouts(&c);
+    if (e == cudaSuccess) e = wait_timeouts_volume(&v);
     if (e != cudaSuccess) return cuda_fail(e, "dgmg_wait_timeouts");
-    *count = a + b + c;
+    *count = a + b + c + v;
     return DGMG_OK;
 }
 

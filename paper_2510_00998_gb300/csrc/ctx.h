@@ -160,6 +160,10 @@ struct dgmg_ctx {
     double *w_r = nullptr, *w_z = nullptr, *w_p = nullptr, *w_q = nullptr, *w_rold = nullptr;
     double *w_b = nullptr, *w_x = nullptr;        // dgmg_solve_host staging
     double *scal = nullptr, *partials = nullptr;  // device scalars
+    // the volume-term A/B entry (dgmg_volume_residual_f32), built at its first
+    // call: E in the swizzled operand layout, and the shared 1D factors P | P^T | L
+    float *vol_esw = nullptr;
+    float vol_fac[165] = {};
     double *host_scal = nullptr;                  // pinned: S_NSCAL scalars, then the wait-counter snapshots
     // device addresses of the bounded-wait counters (FP32 and FP64 DG kernels,
     // Q1 grid barrier) on the ctx's device

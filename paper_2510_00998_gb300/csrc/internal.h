@@ -41,6 +41,7 @@ inline void count_launches(int k) { g_kernel_launches.fetch_add(k, std::memory_o
 // Bounded waits that ran out in the kernels of the float / double translation unit.
 cudaError_t wait_timeouts_fp32(unsigned long long *count);
 cudaError_t wait_timeouts_fp64(unsigned long long *count);
+cudaError_t wait_timeouts_volume(unsigned long long *count);
 // device addresses of the same counters on the current device (for
 // stream-ordered snapshots)
 cudaError_t wait_timeouts_addr_fp32(unsigned long long **ptr);

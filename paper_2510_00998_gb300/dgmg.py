@@ -114,6 +114,7 @@ _SIGS = {
     "dgmg_h_prolong": (_I, [_P, _I, _P, _P, _P]),
     "dgmg_coarse_solve": (_I, [_P, _P, _P, _P]),
     "dgmg_cg_size": (ctypes.c_int64, [_P, _I]),
+    "dgmg_volume_residual_f32": (_I, [_P, _P, _P, _P, _I, _P]),
     "dgmg_estimate_bytes": (_I, [ctypes.POINTER(Mesh), _I, ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_size_t)]),
     "dgmg_server_create": (_I, [ctypes.c_size_t, _I, ctypes.POINTER(Opts), ctypes.POINTER(_P)]),
     "dgmg_submit": (_I, [_P, ctypes.POINTER(Mesh), _I, _P, _P, _P, ctypes.POINTER(ctypes.c_uint64)]),
@@ -447,6 +448,15 @@ class Context:
         array instead of the context's (allocates nothing; see dgmg.h)."""
         _check(self.lib.dgmg_residual_restrict_noalloc(self.h, _ptr(u), _ptr(b), _ptr(traces), _ptr(r), _ptr(rc),
                                                        _stream(stream)))
+
+    def volume_residual_f32(self, u, b, r, method, stream=None):
+        """r = b - kappa_K E u_K per cell (FP32 tensors; method 0 sum-factorised,
+        1 tensor cores, TF32): the volume term of the operator alone."""
+        for t in (u, b, r):
+            if not t.is_cuda or not t.is_contiguous() or t.dtype != __import__("torch").float32:
+                raise ValueError("FP32 contiguous CUDA tensors expected")
+        _check(self.lib.dgmg_volume_residual_f32(self.h, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(b.data_ptr()),
+                                                 ctypes.c_void_p(r.data_ptr()), int(method), _stream(stream)))
 
     def cg_smooth(self, level, u, b, nsteps, stream=None):
         _check(self.lib.dgmg_cg_smooth(self.h, int(level), _ptr(u), _ptr(b), int(nsteps), _stream(stream)))

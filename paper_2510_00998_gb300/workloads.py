@@ -21,6 +21,8 @@ Workloads (every input seeded and synthetic):
   tables34       MGMult cycle counts of Tables 3-4 ("sin-product", GLL), 2D
                  9^2 .. 243^2, p = 2..6, direct and gradual p-coarsening
   table5         the same for the "two-peak" solution in the GLL and the GL basis
+  volume_ab      the volume term r = b - kappa E u alone, 64^3 cells, p = 4, FP32:
+                 sum-factorised CUDA-core kernel vs tcgen05 tensor-core contraction
 """
 import argparse
 import json
@@ -197,9 +199,46 @@ def run(name, solves=3, warmup=1):
             "launches": dgmg.kernel_launches(), "tiles": list(ctx.info.tiles)}
 
 
+def run_volume_ab(n=(64, 64, 64), reps=20):
+    """The volume term r = b - kappa E u (3D, p = 4, FP32 vectors) in both forms
+    of dgmg_volume_residual_f32: sum-factorised CUDA-core kernel (method 0) and
+    tcgen05 tensor-core contraction (method 1, TF32). Mean CUDA-event time per
+    launch over `reps` launches (inputs larger than L2), algorithmic HBM bytes
+    (u, b, r in FP32 and kappa in FP64 per cell) against the measured copy rate,
+    and the TF32 result's difference from the FP32 one."""
+    import torch
+    from . import dgmg
+    kappa = np.exp(np.random.default_rng(3).normal(size=int(np.prod(n))))
+    ctx = dgmg.Context(n, 4, kappa)
+    g = torch.Generator(device="cuda").manual_seed(9)
+    u = torch.randn(ctx.ndof, dtype=torch.float32, device="cuda", generator=g)
+    b = torch.randn(ctx.ndof, dtype=torch.float32, device="cuda", generator=g)
+    out = {"workload": f"volume term, {n[0]}x{n[1]}x{n[2]} cells, p = 4, FP32", "ncell": int(ctx.info.ncell)}
+    bytes_per_launch = int(ctx.info.ncell) * (3 * 125 * 4 + 8)
+    res = {}
+    for method, name in ((0, "sum_factorised_fp32"), (1, "tcgen05_tf32")):
+        r = torch.empty_like(u)
+        for _ in range(3):
+            ctx.volume_residual_f32(u, b, r, method)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            ctx.volume_residual_f32(u, b, r, method)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res[method] = r
+        out[name] = {"ms": ms, "gb_per_s": bytes_per_launch / (ms * 1e-3) / 1e9, "bytes_per_launch": bytes_per_launch}
+    vol = (b - res[0]).abs().max().item()
+    out["tf32_max_diff_rel"] = float((res[1] - res[0]).abs().max().item() / vol)
+    out["wait_timeouts"] = dgmg.wait_timeouts()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("name", choices=sorted(WORKLOADS) + ["batch", "serve", "tables34", "table5"])
+    ap.add_argument("name", choices=sorted(WORKLOADS) + ["batch", "serve", "tables34", "table5", "volume_ab"])
     ap.add_argument("--solves", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--count", type=int, default=0)
@@ -232,6 +271,8 @@ def main():
             res = tables34(rhs="two_peak", basis=basis)
             out[key] = {f"{n}x{n} p={p}": {"unprec": v[0], "prec": v[1]} for (n, p), v in res.items()}
         print(json.dumps(out))
+    elif a.name == "volume_ab":
+        print(json.dumps(run_volume_ab()))
     else:
         print(json.dumps(run(a.name, a.solves, a.warmup)))
 
