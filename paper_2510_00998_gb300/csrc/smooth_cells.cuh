@@ -226,9 +226,47 @@ __device__ __forceinline__ void load_matrix(const T *src, T *S) {
         for (int n = 0; n < Q; ++n) S[m * Q + n] = TRANSPOSE ? v[n * Q + m] : v[m * Q + n];
 }
 
+// Along x with packed pairs of pencils (FP32): outputs of pencils t and t + 1 by
+// one two-lane FMA per term, the matrix entry duplicated in both lanes (the
+// same roundings as the scalar form, half the issue slots).
+template <int Q>
+__device__ __forceinline__ void pass_x2(const float *A, float *R) {
+#pragma unroll
+    for (int t = 0; t + 1 < Q * Q; t += 2) {
+        float2 x[Q];
+#pragma unroll
+        for (int n = 0; n < Q; ++n) x[n] = make_float2(R[n + Q * t], R[n + Q * (t + 1)]);
+#pragma unroll
+        for (int m = 0; m < Q; ++m) {
+            float2 s = __fmul2_rn(make_float2(A[m * Q], A[m * Q]), x[0]);
+#pragma unroll
+            for (int n = 1; n < Q; ++n) s = __ffma2_rn(make_float2(A[m * Q + n], A[m * Q + n]), x[n], s);
+            R[m + Q * t] = s.x;
+            R[m + Q * (t + 1)] = s.y;
+        }
+    }
+    if ((Q * Q) & 1) {
+        constexpr int t = Q * Q - 1;
+        float x[Q];
+#pragma unroll
+        for (int n = 0; n < Q; ++n) x[n] = R[n + Q * t];
+#pragma unroll
+        for (int m = 0; m < Q; ++m) {
+            float s = 0.f;
+#pragma unroll
+            for (int n = 0; n < Q; ++n) s += A[m * Q + n] * x[n];
+            R[m + Q * t] = s;
+        }
+    }
+}
+
 // Along x: R[., a, b] <- A R[., a, b] for every pencil (A row-major q x q).
 template <typename T, int Q>
 __device__ __forceinline__ void pass_x(const T *A, T *R) {
+    if constexpr (sizeof(T) == 4) {
+        pass_x2<Q>(reinterpret_cast<const float *>(A), reinterpret_cast<float *>(R));
+        return;
+    }
 #pragma unroll
     for (int t = 0; t < Q * Q; ++t) {
         T x[Q];
@@ -275,6 +313,43 @@ __device__ __forceinline__ void lift_x_face(int side, const T *fld, int sa, int 
 #pragma unroll
             for (int b = 0; b < Q; ++b) t1[a + Q * b] = wb[b] * col[b] - ub[b] * s;
         }
+        if constexpr (sizeof(T) == 4) {
+            if (comp == 0) {
+                T vv[NF];
+#pragma unroll
+                for (int b = 0; b < Q; ++b) {
+                    T s = T(0);
+#pragma unroll
+                    for (int aa = 0; aa < Q; ++aa) s += ua[aa] * t1[aa + Q * b];
+#pragma unroll
+                    for (int a = 0; a < Q; ++a) vv[a + Q * b] = wa[a] * t1[a + Q * b] - ua[a] * s;
+                }
+                // pencils t, t + 1: pen[n] += (sgn wv v) dv[n] by two-lane FMAs
+                float *Rf = reinterpret_cast<float *>(R);
+#pragma unroll
+                for (int t = 0; t < NF; t += 2) {
+                    if (t + 1 < NF) {
+                        const float2 w2 = make_float2((float)(sgn * wv * vv[t]), (float)(sgn * wv * vv[t + 1]));
+#pragma unroll
+                        for (int n = 0; n < Q; ++n) {
+                            float2 pp = make_float2(Rf[Q * t + n], Rf[Q * (t + 1) + n]);
+                            pp = __ffma2_rn(w2, make_float2((float)dv[n], (float)dv[n]), pp);
+                            Rf[Q * t + n] = pp.x;
+                            Rf[Q * (t + 1) + n] = pp.y;
+                        }
+                    } else {
+                        const T w = sgn * wv * vv[t];
+#pragma unroll
+                        for (int n = 0; n < Q; ++n) R[Q * t + n] += w * dv[n];
+                    }
+                }
+#pragma unroll
+                for (int t = 0; t < NF; ++t) {
+                    if (side) R[Q * t + Q - 1] += g2 * vv[t]; else R[Q * t] += g2 * vv[t];
+                }
+                continue;
+            }
+        }
 #pragma unroll
         for (int b = 0; b < Q; ++b) {
             T s = T(0);
@@ -302,6 +377,33 @@ __device__ __forceinline__ void lift_x_face(int side, const T *fld, int sa, int 
 template <typename T, int Q>
 __device__ __forceinline__ void x_face_traces(int side, const T *R, const T *dv, int sa, int sb, T *dst) {
     constexpr int NF = Q * Q;
+    if constexpr (sizeof(T) == 4) {
+        // derivative traces of pencils t and t + 1 by two-lane FMAs
+#pragma unroll
+        for (int t = 0; t < NF; t += 2) {
+            const int a0 = t % Q, b0 = t / Q;
+            const float *p0 = reinterpret_cast<const float *>(R) + Q * t;
+            if (t + 1 < NF) {
+                const int a1 = (t + 1) % Q, b1 = (t + 1) / Q;
+                const float *p1 = p0 + Q;
+                float2 d = __fmul2_rn(make_float2((float)dv[0], (float)dv[0]), make_float2(p0[0], p1[0]));
+#pragma unroll
+                for (int n = 1; n < Q; ++n)
+                    d = __ffma2_rn(make_float2((float)dv[n], (float)dv[n]), make_float2(p0[n], p1[n]), d);
+                dst[sa * a0 + sb * b0] = side ? (T)p0[Q - 1] : (T)p0[0];
+                dst[sa * a1 + sb * b1] = side ? (T)p1[Q - 1] : (T)p1[0];
+                dst[NF + sa * a0 + sb * b0] = (T)d.x;
+                dst[NF + sa * a1 + sb * b1] = (T)d.y;
+            } else {
+                T d = T(0);
+#pragma unroll
+                for (int n = 0; n < Q; ++n) d += dv[n] * R[Q * t + n];
+                dst[sa * a0 + sb * b0] = side ? R[Q * t + Q - 1] : R[Q * t];
+                dst[NF + sa * a0 + sb * b0] = d;
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int b = 0; b < Q; ++b)
 #pragma unroll
