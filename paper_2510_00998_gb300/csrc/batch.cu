@@ -593,6 +593,7 @@ std::vector<BatchDG<T>> group_descriptors(const dgmg_batch &B, const dgmg_batch:
         d.off = cells;
         d.kappa = dg.kappa;
         d.fd = dg.fd;
+        d.fdr = dg.fdr;
         d.linv = dg.linv;
         d.tr[0] = dg.tr[0];
         d.tr[1] = dg.tr[1];

@@ -389,9 +389,19 @@ std::vector<T> convert(const std::vector<double> &v) {
 // FP32 factors are the rounded FP64 ones when those exist (fd64).
 template <typename T>
 int compute_factors(dgmg_ctx &C, const DGSpace &S, DGDev<T> &D, const double *fd64 = nullptr) {
+    // the residual's factors [S^T M | lambda], from the FP64 factors where there are some
+    MassTables mt;
+    std::memset(&mt, 0, sizeof(mt));
+    for (int a = 0; a < C.dim; ++a) {
+        const double h = 1.0 / C.n[a];
+        for (int i = 0; i < S.q * S.q; ++i) mt.M[a][i] = S.re.M[i] * h / 2.0;
+    }
     if (std::is_same<T, float>::value && fd64) {
         LC(launch_cast_d2f((int64_t)C.ncell * C.dim * (S.q * S.q + S.q), fd64, reinterpret_cast<float *>(D.fd),
                            C.setup_stream));
+        if (D.fdr)
+            LC((launch_residual_factors<double, float>(C.dim, S.q, C.ncell, fd64, mt,
+                                                       reinterpret_cast<float *>(D.fdr), C.setup_stream)));
         return DGMG_OK;
     }
     FDInput in;
@@ -400,6 +410,7 @@ int compute_factors(dgmg_ctx &C, const DGSpace &S, DGDev<T> &D, const double *fd
     if (sizeof(T) == sizeof(double))
         LC(launch_inverse_eigen_sums(C.dim, S.q, C.ncell, reinterpret_cast<const double *>(D.fd),
                                      reinterpret_cast<double *>(D.linv), C.setup_stream));
+    if (D.fdr) LC((launch_residual_factors<T, T>(C.dim, S.q, C.ncell, D.fd, mt, D.fdr, C.setup_stream)));
     return DGMG_OK;
 }
 
@@ -423,6 +434,7 @@ int setup_dg(dgmg_ctx &C, const DGSpace &S, DGDev<T> &D, const std::vector<doubl
         return DGMG_OK;
     }
     RC(C.alloc(&D.fd, (size_t)C.ncell * C.dim * (S.q * S.q + S.q)));
+    RC(C.alloc(&D.fdr, (size_t)C.ncell * C.dim * (S.q * S.q + S.q)));
     if (sizeof(T) == sizeof(double)) RC(C.alloc(&D.linv, (size_t)S.ndof));
     RC(compute_factors<T>(C, S, D, fd64));
     RC(C.alloc(&D.tr[0], trn));
@@ -1479,8 +1491,9 @@ int dgmg_estimate_bytes(const dgmg_mesh *mesh, int p, const dgmg_opts *opts, siz
     const int64_t tr = ncell * 2 * dim * trace_face_stride<double>((int)nf);
     const int64_t tr32 = ncell * 2 * dim * trace_face_stride<float>((int)nf);
     auto sz = [](int64_t count, size_t elem) { return (size_t)std::max<int64_t>(count, 1) * elem; };
-    size_t dg64 = sz(ncell, 8) + sz(ncell * dim * (q * q + q), 8) + sz(ndof, 8) + 2 * sz(tr, 8) + sz(ncell << dim, 8);
-    size_t dg32 = sz(ncell, 4) + sz(ncell * dim * (q * q + q), 4) + 2 * sz(tr32, 4) + sz(ncell << dim, 4);
+    size_t dg64 = sz(ncell, 8) + 2 * sz(ncell * dim * (q * q + q), 8) + sz(ndof, 8) + 2 * sz(tr, 8) +
+                  sz(ncell << dim, 8);   // kappa, factors and residual factors, table, traces, corners
+    size_t dg32 = sz(ncell, 4) + 2 * sz(ncell * dim * (q * q + q), 4) + 2 * sz(tr32, 4) + sz(ncell << dim, 4);
     size_t cg64 = 0, cg32 = 0;
     int cur[3] = {n[0], n[1], n[2]};
     int64_t nv = 1;
@@ -1519,8 +1532,8 @@ int dgmg_estimate_bytes(const dgmg_mesh *mesh, int p, const dgmg_opts *opts, siz
             const int64_t trl = ncell * 2 * dim * trace_face_stride<double>((int)(nl / ql));
             const int64_t trl32 = ncell * 2 * dim * trace_face_stride<float>((int)(nl / ql));
             const int64_t fdl = ncell * dim * (ql * ql + ql);
-            total += sz(fdl, 8) + sz(nd, 8) + 2 * sz(trl, 8) + sz(ncell << dim, 8) + 3 * sz(nd, 8);
-            if (mixed) total += sz(fdl, 4) + 2 * sz(trl32, 4) + sz(ncell << dim, 4) + 3 * sz(nd, 4);
+            total += 2 * sz(fdl, 8) + sz(nd, 8) + 2 * sz(trl, 8) + sz(ncell << dim, 8) + 3 * sz(nd, 8);
+            if (mixed) total += 2 * sz(fdl, 4) + 2 * sz(trl32, 4) + sz(ncell << dim, 4) + 3 * sz(nd, 4);
         }
         total += sz(ndof, 8) + (mixed ? sz(ndof, 4) : 0);
     }

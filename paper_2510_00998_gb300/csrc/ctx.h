@@ -36,6 +36,7 @@ struct DGDev {
     DGConst<T> c;
     T *kappa = nullptr, *fd = nullptr, *tr[2] = {nullptr, nullptr}, *corners = nullptr;
     T *linv = nullptr;   // per-node 1 / (sum of the cell's eigenvalues); FP64 only
+    T *fdr = nullptr;    // the residual's factors [S^T M | lambda] per cell and axis
 };
 
 template <typename T>
@@ -274,7 +275,7 @@ int exact_block(const dgmg_ctx &C);
 // (the one-thread-per-cell residual forms A_KK u from them), else null
 template <typename T>
 inline const T *exact_fd(const dgmg_ctx &C, const DGDev<T> &D) {
-    return exact_block(C) ? D.fd : nullptr;
+    return exact_block(C) ? D.fdr : nullptr;
 }
 // y = A u (b == NULL) or out = b - A u, FP64
 int apply64(dgmg_ctx &C, const double *u, const double *b, double *out, cudaStream_t s);

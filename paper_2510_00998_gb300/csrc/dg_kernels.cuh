@@ -849,7 +849,7 @@ __global__ void __launch_bounds__(32) k_residual_cells_batch(const BatchDG<T> *_
         const BlockMap m = map[k];
         load_batch_desc(D + m.inst, &sd);
         residual_cells_body<T, Q>(sd.c, m.cell0, mode, u + sd.off * NL, b ? b + sd.off * NL : nullptr, sd.kappa,
-                                  sd.fd, sd.tr[cur], r ? r + sd.off * NL : nullptr, sd.corners, k != (int)blockIdx.x);
+                                  sd.fdr, sd.tr[cur], r ? r + sd.off * NL : nullptr, sd.corners, k != (int)blockIdx.x);
     }
 }
 

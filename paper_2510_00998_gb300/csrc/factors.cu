@@ -162,4 +162,43 @@ cudaError_t launch_inverse_eigen_sums(int dim, int q, int64_t ncell, const doubl
     return cudaGetLastError();
 }
 
+// Factors of the residual's A_KK u = (M S)^(xd) (sum of Lambda) (S^T M)^(xd):
+// per (cell, axis) the matrix P = S^T M_a (q x q, row-major) and Lambda, in the
+// layout of the smoother's factors [P | Lambda], from the cell's [S | Lambda]
+// (FP64 or FP32) and the h-scaled 1D mass of the axis (FP64).
+template <typename TI, typename TO>
+__global__ void k_residual_factors(int dim, int q, int64_t ncell, const TI *__restrict__ fd, MassTables m,
+                                   TO *__restrict__ fdr) {
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= ncell * dim) return;
+    const int a = (int)(id % dim);
+    const int fds = q * q + q;
+    const TI *S = fd + id * fds;
+    TO *P = fdr + id * fds;
+    const double *M = m.M[a];
+    for (int i = 0; i < q; ++i)
+        for (int n = 0; n < q; ++n) {
+            double v = 0.0;
+            for (int l = 0; l < q; ++l) v += (double)S[l * q + i] * M[l * q + n];
+            P[i * q + n] = (TO)v;
+        }
+    for (int i = 0; i < q; ++i) P[q * q + i] = (TO)S[q * q + i];
+}
+
+template <typename TI, typename TO>
+cudaError_t launch_residual_factors(int dim, int q, int64_t ncell, const TI *fd, const MassTables &m, TO *fdr,
+                                    cudaStream_t s) {
+    const int64_t n = ncell * dim;
+    if (n == 0) return cudaSuccess;
+    count_launches(1);
+    k_residual_factors<TI, TO><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(dim, q, ncell, fd, m, fdr);
+    return cudaGetLastError();
+}
+template cudaError_t launch_residual_factors<double, double>(int, int, int64_t, const double *, const MassTables &,
+                                                             double *, cudaStream_t);
+template cudaError_t launch_residual_factors<double, float>(int, int, int64_t, const double *, const MassTables &,
+                                                            float *, cudaStream_t);
+template cudaError_t launch_residual_factors<float, float>(int, int, int64_t, const float *, const MassTables &,
+                                                           float *, cudaStream_t);
+
 }  // namespace dgmg

@@ -81,6 +81,15 @@ struct FDInput {
 // output in T); kappa: per-cell FP64 on the device
 template <typename T>
 cudaError_t launch_fd_factors(const FDInput &in, const double *kappa, int64_t ncell, T *fd, cudaStream_t s);
+// The h-scaled 1D masses of the axes (FP64), by value.
+struct MassTables {
+    double M[3][QMAX * QMAX];
+};
+// fdr[cell][axis] = [S^T M_a (q x q) | lambda (q)] from fd[cell][axis] = [S | lambda]:
+// the factors the one-thread-per-cell residual applies A_KK u with
+template <typename TI, typename TO>
+cudaError_t launch_residual_factors(int dim, int q, int64_t ncell, const TI *fd, const MassTables &m, TO *fdr,
+                                    cudaStream_t s);
 // linv[cell][node] = 1 / (sum of the cell's eigenvalues at the node)
 cudaError_t launch_inverse_eigen_sums(int dim, int q, int64_t ncell, const double *fd, double *linv,
                                       cudaStream_t s);
@@ -148,6 +157,7 @@ struct BatchDG {
     DGConst<T> c;
     int64_t off;
     const T *kappa, *fd, *linv;
+    const T *fdr;         // the residual's factors [S^T M | lambda] (null: operator-only level)
     T *tr[2];
     T *corners;
     const T *e0;          // the instance's Q1 level-0 correction (p-prolongation source)

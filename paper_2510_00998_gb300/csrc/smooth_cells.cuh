@@ -762,26 +762,6 @@ __global__ void __launch_bounds__(32) k_project_cells(const __grid_constant__ DG
     project_cells_body<T, Q>(c, (int64_t)blockIdx.x * CellGeo<T, Q>::W, u, e0, tr);
 }
 
-// P = S^T M (TRANSPOSE false) or its transpose M S, for a q x q factor S
-// (row-major in shared memory) and the symmetric 1D mass M.
-template <typename T, int Q, bool TRANSPOSE>
-__device__ __forceinline__ void load_mass_factor(const T *src, const T *M, T *P) {
-    T S[Q * Q];
-    load_matrix<T, Q, false>(src, S);
-#pragma unroll
-    for (int m = 0; m < Q; ++m)
-#pragma unroll
-        for (int n = 0; n < Q; ++n) {
-            T v = T(0);
-#pragma unroll
-            for (int l = 0; l < Q; ++l) v += S[l * Q + m] * M[l * Q + n];
-            if (TRANSPOSE)
-                P[n * Q + m] = v;
-            else
-                P[m * Q + n] = v;
-        }
-}
-
 // Residual r = b - A u with one thread per cell, 3D, exact diagonal blocks
 // (Alg. 2 stage 3; the residual of a V-cycle level and the operator apply),
 // with A u = A_KK u + N u_nb. A_KK u from the cell's fast-diagonalisation
@@ -789,7 +769,8 @@ __device__ __forceinline__ void load_mass_factor(const T *src, const T *M, T *P)
 // A_KK = (M S)^(x3) (Lambda_x + Lambda_y + Lambda_z) (S^T M)^(x3), so A_KK u
 // takes the six tensor passes of the smoother's inverse, with P_a = S_a^T M_a
 // and its transpose, and a multiplication by the eigenvalue sums instead of a
-// division. Then b is added and the neighbour terms are lifted as in the
+// division. fd holds [P_a | Lambda_a] per cell and axis (computed once at
+// set-up from the smoother's factors). Then b is added and the neighbour terms are lifted as in the
 // smoothing step. Outputs as for k_residual: r (negated for y = A u) and the
 // cell corner sums of the p-restriction.
 // Staging: u and the factors by bulk copies; FP32: b into u's area once u is
@@ -812,7 +793,7 @@ __device__ __forceinline__ void residual_cells_body(const DGConst<T> &c, int64_t
     // mbarriers: 0 u, 1 b (FP32) / factors (FP64), 2 factors (FP32), 4 and 5
     // the face slots (FP32; phase k = the slot's k-th face)
     __shared__ __align__(8) uint64_t bars[6];
-    __shared__ T sM[3][Q * Q], sMw[3][Q], sMu[3][Q];
+    __shared__ T sMw[3][Q], sMu[3][Q];
     const int lane = threadIdx.x;
     const int ncl = (int)min((int64_t)W, c.ncell - cell0);
     const bool full = ncl == W;
@@ -821,7 +802,6 @@ __device__ __forceinline__ void residual_cells_body(const DGConst<T> &c, int64_t
     const bool has_b = (mode & RES_HAS_B) != 0;
 
     cells_init_bars(bars, 6, lane, reuse);
-    for (int e = lane; e < 3 * Q * Q; e += W) sM[e / (Q * Q)][e % (Q * Q)] = c.M[e / (Q * Q)][e % (Q * Q)];
     for (int e = lane; e < 3 * Q; e += W) {
         sMw[e / Q][e % Q] = c.mw[e / Q][e % Q];
         sMu[e / Q][e % Q] = c.mu[e / Q][e % Q];
@@ -894,9 +874,9 @@ __device__ __forceinline__ void residual_cells_body(const DGConst<T> &c, int64_t
         T P[Q * Q];
         const int ax = k < 3 ? k : k - 3;
         if (k < 3)
-            load_mass_factor<T, Q, false>(myFD + ax * FDS, sM[ax], P);
+            load_matrix<T, Q, false>(myFD + ax * FDS, P);   // P_a = S_a^T M_a, precomputed per cell
         else
-            load_mass_factor<T, Q, true>(myFD + ax * FDS, sM[ax], P);
+            load_matrix<T, Q, true>(myFD + ax * FDS, P);    // its transpose M_a S_a
         pass_x<T, Q>(P, R);
         rotate<T, Q>(R);
     }
