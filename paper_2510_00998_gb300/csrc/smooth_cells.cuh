@@ -146,18 +146,35 @@ struct CellGeo {
     // area A is staged. That halves the shared memory per CTA, so more CTAs
     // are resident (a 32^3 mesh fits in one wave).
     static constexpr bool LEAN = sizeof(T) == 8;
-    // shared memory (values of T), per cell. FP32: area A holds b, then the
-    // previous u (prefetched as soon as b is in registers), then the new u; area
-    // B holds two neighbour-face slots (FS values each), then the factors, then
-    // two faces of new traces. FP64: area A holds b, then the factors, then the
+    // shared memory (values of T), per cell. FP32 smoothing step: area A holds
+    // b, then one neighbour-face slot (FS values) during the facet lifting, then
+    // the previous u, then the new u, then one slot of new traces; area B holds
+    // the other face slot, then the factors, then the other trace slot (8
+    // one-warp CTAs fit per SM). FP64: area A holds b, then the factors, then the
     // new u.
     static constexpr int PA = LEAN ? (NL > 3 * FDS ? NL : 3 * FDS) : NL;
-    static constexpr int PB = LEAN ? 0 : (2 * FS > 3 * FDS ? 2 * FS : 3 * FDS);
+    static constexpr int PB = LEAN ? 0 : (FS > 3 * FDS ? FS : 3 * FDS);
     static constexpr size_t OFF_B = (size_t)W * PA;
-    static constexpr size_t OFF_K = OFF_B + (size_t)W * PB;   // kF [6][W]
-    static constexpr size_t OFF_NB = OFF_K + 6 * W;          // neighbour cell [6][W] (int)
-    static constexpr size_t BYTES = OFF_NB * sizeof(T) + 6 * W * sizeof(int);
+    static constexpr size_t BYTES = (OFF_B + (size_t)W * PB) * sizeof(T);
+    static_assert(LEAN || FS <= NL, "a face slot fits area A");
 };
+
+// Neighbour across face f (= 2 axis + side) of `cell`, -1 where face f is on the
+// boundary (bit f of mask clear); s1, s2: the cell strides along y and z.
+__device__ __forceinline__ int cell_neighbour(int f, int mask, int64_t cell, int s1, int s2) {
+    if (!(mask & (1 << f))) return -1;
+    const int s = f < 2 ? 1 : (f < 4 ? s1 : s2);
+    return (int)cell + ((f & 1) ? s : -s);
+}
+
+// Facet coefficient of a face: the harmonic mean of kappa with the neighbour
+// nb, 0 without one (the face then has no neighbour term).
+template <typename T>
+__device__ __forceinline__ T facet_kappa(int nb, T kK, const T *__restrict__ kappa) {
+    if (nb < 0) return T(0);
+    const T kN = kappa[nb];
+    return T(2) * kK * kN / (kK + kN);
+}
 
 // Stage face f of the lane's neighbour nb (the neighbour's face f^1) into the
 // lane's part of a face slot: one bulk copy per lane that has a neighbour, all
@@ -419,14 +436,15 @@ __device__ __forceinline__ void x_face_traces(int side, const T *R, const T *dv,
 
 // Traces of the cell tensor R (one per lane) to tr_out[cell][face][FS]: the
 // faces normal to axis p, then rotate. FP32: every lane writes its two faces
-// into its face slots of area B and stores each with one bulk store (a slot is
+// into its parts of two slots of shared memory (slot0, slot1: W x FS values
+// each, free for the whole call) and stores each with one bulk store (a slot is
 // rewritten once the lane's previous stores have read it); FP64 (LEAN):
 // written per lane. R ends rotated. Only lanes with `write` store.
 template <typename T, int Q>
 __device__ __forceinline__ void cells_write_traces(const DGConst<T> &c, T *R, int lane, bool write, int64_t cell,
-                                                   T *sB, T *__restrict__ tr_out) {
+                                                   T *slot0, T *slot1, T *__restrict__ tr_out) {
     using G = CellGeo<T, Q>;
-    constexpr int W = G::W, FS = G::FS, TR = G::TR;
+    constexpr int FS = G::FS, TR = G::TR;
 #pragma unroll 1
     for (int p = 0; p < 3; ++p) {
         const int sa = p == 1 ? Q : 1, sb = p == 1 ? 1 : Q;
@@ -437,14 +455,14 @@ __device__ __forceinline__ void cells_write_traces(const DGConst<T> &c, T *R, in
                 T dv[Q];
 #pragma unroll
                 for (int n = 0; n < Q; ++n) dv[n] = side ? c.dp[p][n] : c.d0[p][n];
-                T *dst = G::LEAN ? tr_out + cell * TR + (2 * p + side) * FS : sB + (side * W + lane) * FS;
+                T *dst = G::LEAN ? tr_out + cell * TR + (2 * p + side) * FS : (side ? slot1 : slot0) + lane * FS;
                 x_face_traces<T, Q>(side, R, dv, sa, sb, dst);
             }
             if (!G::LEAN) {
                 fence_proxy_async_smem();
 #pragma unroll
                 for (int side = 0; side < 2; ++side)
-                    bulk_store(tr_out + cell * TR + (2 * p + side) * FS, sB + (side * W + lane) * FS,
+                    bulk_store(tr_out + cell * TR + (2 * p + side) * FS, (side ? slot1 : slot0) + lane * FS,
                                (unsigned)(FS * sizeof(T)));
                 bulk_commit();
             }
@@ -505,15 +523,15 @@ __device__ __forceinline__ void stage_bulk(bool full, int lane, uint64_t *bar, T
 template <typename T, int Q>
 __device__ __forceinline__ void smooth_cells_body(const DGConst<T> &c, int64_t cell0, T *__restrict__ u, const T *__restrict__ b, const T *__restrict__ kappa, const T *__restrict__ fd, const T *__restrict__ linv, const T *__restrict__ tr_in, T *__restrict__ tr_out, bool reuse = false) {
     using G = CellGeo<T, Q>;
-    constexpr int W = G::W, NL = G::NL, NF = G::NF, FDS = G::FDS, TR = G::TR, FS = G::FS;
+    constexpr int W = G::W, NL = G::NL, FDS = G::FDS, TR = G::TR, FS = G::FS;
     extern __shared__ __align__(128) unsigned char smem_c[];
-    T *sA = reinterpret_cast<T *>(smem_c);              // b -> previous u (FP32) or factors (FP64) -> new u
-    T *sB = sA + G::OFF_B;                               // FP32: face slots -> factors -> new traces
-    // face slot s (0, 1) of area B, lane l: sB + (s * W + l) * FS
-    T *sK = sA + G::OFF_K;
-    int *sNb = reinterpret_cast<int *>(sA + G::OFF_NB);
+    // area A: b -> face slot 1 (FP32) or the factors (FP64) -> previous u (FP32)
+    //         -> new u -> trace slot 1
+    // area B (FP32): face slot 0 -> factors -> trace slot 0
+    T *sA = reinterpret_cast<T *>(smem_c);
+    T *sB = sA + G::OFF_B;
     // mbarriers: 0 b, 1 previous u (FP32) / factors (FP64), 2 factors (FP32),
-    // 4 and 5 the face slots (FP32; phase k = the slot's k-th face)
+    // 4 face slot 0, 5 face slot 1 (phase k = the slot's k-th face)
     __shared__ __align__(8) uint64_t bars[6];
     __shared__ T sMw[3][Q], sMu[3][Q];
     const int lane = threadIdx.x;
@@ -530,38 +548,17 @@ __device__ __forceinline__ void smooth_cells_body(const DGConst<T> &c, int64_t c
         sMu[e / Q][e % Q] = c.mu[e / Q][e % Q];
     }
     stage_bulk<T>(full, lane, &bars[0], sA, b + cell0 * NL, W * NL, ncl * NL);
-    // neighbours of this lane's cell; the first two neighbour faces are
-    // requested before the coefficients are loaded, so their copies overlap
-    // the kappa loads
+    // neighbours of this lane's cell (a mask of interior faces and the strides);
+    // the first neighbour face is requested at once
     int mask = 0;
     if (active) {
         int ci[3];
         cell_coords32(cell, c.n, ci);
         mask = interior_mask<3>(ci, c.n);
     }
-#pragma unroll
-    for (int f = 0; f < 6; ++f) {
-        int nb = -1;
-        if (mask & (1 << f)) {
-            const int s = f < 2 ? 1 : (f < 4 ? c.n[0] : c.n[0] * c.n[1]);
-            nb = (int)cell + ((f & 1) ? s : -s);
-        }
-        sNb[f * W + lane] = nb;
-    }
-    __syncwarp();
-    if (!G::LEAN) {
-        stage_face<T, Q>(0, sNb[0 * W + lane], lane, tr_in, sB, &bars[4]);
-        stage_face<T, Q>(1, sNb[1 * W + lane], lane, tr_in, sB + W * FS, &bars[5]);
-    }
-    // facet coefficients: harmonic means of kappa (0 where there is no neighbour)
-    {
-        const T kK = active ? kappa[cell] : T(1);
-        T kN[6];
-#pragma unroll
-        for (int f = 0; f < 6; ++f) kN[f] = (mask & (1 << f)) ? kappa[sNb[f * W + lane]] : T(0);
-#pragma unroll
-        for (int f = 0; f < 6; ++f) sK[f * W + lane] = (mask & (1 << f)) ? T(2) * kK * kN[f] / (kK + kN[f]) : T(0);
-    }
+    const int s1 = c.n[0], s2 = c.n[0] * c.n[1];
+    if (!G::LEAN) stage_face<T, Q>(0, cell_neighbour(0, mask, cell, s1, s2), lane, tr_in, sB, &bars[4]);
+    const T kK = active ? kappa[cell] : T(1);
 
     // r = b
     if (full)
@@ -571,14 +568,13 @@ __device__ __forceinline__ void smooth_cells_body(const DGConst<T> &c, int64_t c
     T R[NL];
 #pragma unroll
     for (int e = 0; e < NL; ++e) R[e] = active ? sA[lane * NL + e] : T(0);
-    // FP32: the previous iterate into the same area (behind the facet work and
-    // the inverse); FP64: the factors
     fence_proxy_async_smem();
     __syncwarp();
+    // area A is free: FP32 the second neighbour face, FP64 the factors
     if (G::LEAN)
         stage_bulk<T>(full, lane, &bars[1], sA, fd + cell0 * 3 * FDS, W * 3 * FDS, ncl * 3 * FDS);
     else
-        stage_bulk<T>(full, lane, &bars[1], sA, u + cell0 * NL, W * NL, ncl * NL);
+        stage_face<T, Q>(1, cell_neighbour(1, mask, cell, s1, s2), lane, tr_in, sA, &bars[5]);
 
     // r -= N u_nb: the two faces normal to axis p, then rotate the next axis to x
 #pragma unroll 1
@@ -590,40 +586,43 @@ __device__ __forceinline__ void smooth_cells_body(const DGConst<T> &c, int64_t c
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
             const int f = 2 * p + side;
+            const int nb = cell_neighbour(f, mask, cell, s1, s2);
+            const T kF = facet_kappa<T>(nb, kK, kappa);
+            T *slot = side ? sA : sB;
             if (!G::LEAN) ok = warp_wait_phase(&bars[4 + side], (unsigned)(p & 1), lane) && ok;
-            if (active && (mask & (1 << f))) {
+            if (active && nb >= 0) {
 #pragma unroll
                 for (int n = 0; n < Q; ++n) dv[n] = side ? c.dp[p][n] : c.d0[p][n];
-                const T *fld = G::LEAN ? tr_in + (int64_t)sNb[f * W + lane] * TR + (f ^ 1) * FS
-                                       : sB + (side * W + lane) * FS;
-                lift_x_face<T, Q>(side, fld, sa, sb, sMw[ta], sMu[ta], sMw[tb], sMu[tb], dv, gam,
-                                  sK[f * W + lane], R);
+                const T *fld = G::LEAN ? tr_in + (int64_t)nb * TR + (f ^ 1) * FS : slot + lane * FS;
+                lift_x_face<T, Q>(side, fld, sa, sb, sMw[ta], sMu[ta], sMw[tb], sMu[tb], dv, gam, kF, R);
             }
             if (!G::LEAN && f + 2 < 6) {
                 fence_proxy_async_smem();
                 __syncwarp();
-                stage_face<T, Q>(f + 2, sNb[(f + 2) * W + lane], lane, tr_in, sB + side * W * FS, &bars[4 + side]);
+                stage_face<T, Q>(f + 2, cell_neighbour(f + 2, mask, cell, s1, s2), lane, tr_in, slot,
+                                 &bars[4 + side]);
             }
         }
         rotate<T, Q>(R);
     }
-    // FP32: the factors into area B (the face slots are free now)
+    // FP32: the factors into area B and the previous u into area A (the face
+    // slots are free now; u is first needed after the inverse)
     if (!G::LEAN) {
         fence_proxy_async_smem();
         __syncwarp();
         stage_bulk<T>(full, lane, &bars[2], sB, fd + cell0 * 3 * FDS, W * 3 * FDS, ncl * 3 * FDS);
+        stage_bulk<T>(full, lane, &bars[1], sA, u + cell0 * NL, W * NL, ncl * NL);
     }
 
     // A_KK^{-1} by fast diagonalisation: S^T along x, y, z; scale by the
-    // inverse eigenvalue sums; S along z, y, x
+    // inverse eigenvalue sums; S along x, y, z
     if (full)
         ok = warp_wait_copies(&bars[G::LEAN ? 1 : 2], lane) && ok;
     else
         __syncwarp();
     const T *myFD = (G::LEAN ? sA : sB) + lane * 3 * FDS;
-    // S^T along x, y, z; the inverse eigenvalue sums; S along x, y, z (the
-    // tensor-product factors commute, so both halves take the axes in the same
-    // order and one loop body serves all six passes)
+    // (the tensor-product factors commute, so both halves take the axes in the
+    // same order and one loop body serves all six passes)
 #pragma unroll 1
     for (int k = 0; k < 6 && active; ++k) {
         if (k == 3) scale_inverse<T, Q>(R, myFD, table ? linv + cell * NL : nullptr);
@@ -635,6 +634,7 @@ __device__ __forceinline__ void smooth_cells_body(const DGConst<T> &c, int64_t c
         pass_x<T, Q>(S, R);
         rotate<T, Q>(R);
     }
+
     // u <- (1 - w) u + w y, stored through area A (the barrier also ends every
     // lane's reads of the factors before area A (FP64) or B (FP32) is rewritten)
     if (!G::LEAN && full)
@@ -658,15 +658,16 @@ __device__ __forceinline__ void smooth_cells_body(const DGConst<T> &c, int64_t c
             if (lane == 0) {
                 bulk_store(u + cell0 * NL, sA, (unsigned)(W * NL * sizeof(T)));
                 bulk_commit();
+                bulk_wait_read_all();                    // area A is read: trace slot 1
             }
         } else {
             for (int e = lane; e < ncl * NL; e += W) u[cell0 * NL + e] = sA[e];
         }
-        // traces of the new iterate
-        cells_write_traces<T, Q>(c, R, lane, active, cell, sB, tr_out);
+        __syncwarp();
+        // traces of the new iterate (FP32: slots in areas B and A)
+        cells_write_traces<T, Q>(c, R, lane, active, cell, sB, sA, tr_out);
     }
     bulk_wait_read_all();
-    (void)NF;
 }
 
 // Warm-up projection (Alg. 4 preamble) with one thread per cell, 3D, GLL:
@@ -752,7 +753,10 @@ __device__ __forceinline__ void project_cells_body(const DGConst<T> &c, int64_t 
             for (int e = lane; e < ncl * NL; e += W) u[cell0 * NL + e] = sA[e];
         }
     }
-    cells_write_traces<T, Q>(c, R, lane, active, cell, sB, tr);
+    // area A (u) becomes the second trace slot once its store has read it
+    if (e0 != nullptr && full && lane == 0) bulk_wait_read_all();
+    __syncwarp();
+    cells_write_traces<T, Q>(c, R, lane, active, cell, sB, sA, tr);
     bulk_wait_read_all();
 }
 
@@ -786,12 +790,10 @@ __device__ __forceinline__ void residual_cells_body(const DGConst<T> &c, int64_t
     using G = CellGeo<T, Q>;
     constexpr int W = G::W, NL = G::NL, NF = G::NF, FDS = G::FDS, TR = G::TR, FS = G::FS;
     extern __shared__ __align__(128) unsigned char smem_c[];
-    T *sA = reinterpret_cast<T *>(smem_c);              // u -> b (FP32) or factors (FP64) -> r
-    T *sB = sA + G::OFF_B;                               // FP32: factors -> face slots
-    T *sK = sA + G::OFF_K;
-    int *sNb = reinterpret_cast<int *>(sA + G::OFF_NB);
-    // mbarriers: 0 u, 1 b (FP32) / factors (FP64), 2 factors (FP32), 4 and 5
-    // the face slots (FP32; phase k = the slot's k-th face)
+    T *sA = reinterpret_cast<T *>(smem_c);              // u -> b (FP32) or factors (FP64) -> face slot 1 -> r
+    T *sB = sA + G::OFF_B;                               // FP32: factors -> face slot 0
+    // mbarriers: 0 u, 1 b (FP32) / factors (FP64), 2 factors (FP32), 4 face
+    // slot 0 (area B), 5 face slot 1 (area A) (FP32; phase k = the slot's k-th face)
     __shared__ __align__(8) uint64_t bars[6];
     __shared__ T sMw[3][Q], sMu[3][Q];
     const int lane = threadIdx.x;
@@ -810,29 +812,13 @@ __device__ __forceinline__ void residual_cells_body(const DGConst<T> &c, int64_t
     stage_bulk<T>(full, lane, &bars[0], sA, u + cell0 * NL, W * NL, ncl * NL);
     if (!G::LEAN) stage_bulk<T>(full, lane, &bars[2], sB, fd + cell0 * 3 * FDS, W * 3 * FDS, ncl * 3 * FDS);
     int mask = 0;
-    {
-        T kK = T(1);
-        if (active) {
-            int ci[3];
-            cell_coords32(cell, c.n, ci);
-            mask = interior_mask<3>(ci, c.n);
-            kK = kappa[cell];
-        }
-#pragma unroll
-        for (int f = 0; f < 6; ++f) {
-            int nb = -1;
-            T kF = T(0);
-            if (mask & (1 << f)) {
-                const int64_t st = axis_stride<3>(c.n, f >> 1);
-                nb = (int)((f & 1) ? cell + st : cell - st);
-                const T kN = kappa[nb];
-                kF = T(2) * kK * kN / (kK + kN);
-            }
-            sNb[f * W + lane] = nb;
-            sK[f * W + lane] = kF;
-        }
+    if (active) {
+        int ci[3];
+        cell_coords32(cell, c.n, ci);
+        mask = interior_mask<3>(ci, c.n);
     }
-    __syncwarp();
+    const int s1 = c.n[0], s2 = c.n[0] * c.n[1];
+    const T kK = active ? kappa[cell] : T(1);
 
     if (full)
         ok = warp_wait_copies(&bars[0], lane) && ok;
@@ -890,12 +876,13 @@ __device__ __forceinline__ void residual_cells_body(const DGConst<T> &c, int64_t
 #pragma unroll
         for (int e = 0; e < NL; ++e) R[e] = (bb ? bb[e] : T(0)) - R[e];
     }
-    // FP32: the neighbour faces into the slots (every lane is done with the factors)
+    // FP32: the neighbour faces into the slots (every lane is done with the
+    // factors in area B and with b in area A)
     if (!G::LEAN) {
         fence_proxy_async_smem();
         __syncwarp();
-        stage_face<T, Q>(0, sNb[0 * W + lane], lane, tr, sB, &bars[4]);
-        stage_face<T, Q>(1, sNb[1 * W + lane], lane, tr, sB + W * FS, &bars[5]);
+        stage_face<T, Q>(0, cell_neighbour(0, mask, cell, s1, s2), lane, tr, sB, &bars[4]);
+        stage_face<T, Q>(1, cell_neighbour(1, mask, cell, s1, s2), lane, tr, sA, &bars[5]);
     }
     // R -= N u_nb, face pair by face pair as in the smoothing step
 #pragma unroll 1
@@ -907,19 +894,20 @@ __device__ __forceinline__ void residual_cells_body(const DGConst<T> &c, int64_t
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
             const int f = 2 * p + side;
+            const int nb = cell_neighbour(f, mask, cell, s1, s2);
+            const T kF = facet_kappa<T>(nb, kK, kappa);
+            T *slot = side ? sA : sB;
             if (!G::LEAN) ok = warp_wait_phase(&bars[4 + side], (unsigned)(p & 1), lane) && ok;
-            if (active && (mask & (1 << f))) {
+            if (active && nb >= 0) {
 #pragma unroll
                 for (int n = 0; n < Q; ++n) dv[n] = side ? c.dp[p][n] : c.d0[p][n];
-                const T *fld = G::LEAN ? tr + (int64_t)sNb[f * W + lane] * TR + (f ^ 1) * FS
-                                       : sB + (side * W + lane) * FS;
-                lift_x_face<T, Q>(side, fld, sa, sb, sMw[ta], sMu[ta], sMw[tb], sMu[tb], dv, gam,
-                                  sK[f * W + lane], R);
+                const T *fld = G::LEAN ? tr + (int64_t)nb * TR + (f ^ 1) * FS : slot + lane * FS;
+                lift_x_face<T, Q>(side, fld, sa, sb, sMw[ta], sMu[ta], sMw[tb], sMu[tb], dv, gam, kF, R);
             }
             if (!G::LEAN && f + 2 < 6) {
                 fence_proxy_async_smem();
                 __syncwarp();
-                stage_face<T, Q>(f + 2, sNb[(f + 2) * W + lane], lane, tr, sB + side * W * FS, &bars[4 + side]);
+                stage_face<T, Q>(f + 2, cell_neighbour(f + 2, mask, cell, s1, s2), lane, tr, slot, &bars[4 + side]);
             }
         }
         rotate<T, Q>(R);
