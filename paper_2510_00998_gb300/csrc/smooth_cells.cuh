@@ -318,17 +318,50 @@ __device__ __forceinline__ void lift_x_face(int side, const T *fld, int sa, int 
     for (int comp = 0; comp < 2; ++comp) {
         const T *f = fld + comp * NF;
         T t1[NF];                                      // t1[a + q b] = (M_b f(a, .))[b]
+        if constexpr (sizeof(T) == 4) {
+            // rows a and a + 1 together by two-lane FMAs
 #pragma unroll
-        for (int a = 0; a < Q; ++a) {
-            T col[Q];
-            T s = T(0);
+            for (int a = 0; a + 1 < Q; a += 2) {
+                float2 col[Q];
+                float2 s2 = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int bb = 0; bb < Q; ++bb) {
-                col[bb] = f[sa * a + sb * bb];
-                s += ub[bb] * col[bb];
+                for (int bb = 0; bb < Q; ++bb) {
+                    col[bb] = make_float2((float)f[sa * a + sb * bb], (float)f[sa * (a + 1) + sb * bb]);
+                    s2 = __ffma2_rn(make_float2((float)ub[bb], (float)ub[bb]), col[bb], s2);
+                }
+#pragma unroll
+                for (int b = 0; b < Q; ++b) {
+                    const float2 t = __ffma2_rn(make_float2(-(float)ub[b], -(float)ub[b]), s2,
+                                                __fmul2_rn(make_float2((float)wb[b], (float)wb[b]), col[b]));
+                    t1[a + Q * b] = (T)t.x;
+                    t1[a + 1 + Q * b] = (T)t.y;
+                }
             }
+            if (Q & 1) {
+                constexpr int a = Q - 1;
+                T col[Q];
+                T s = T(0);
 #pragma unroll
-            for (int b = 0; b < Q; ++b) t1[a + Q * b] = wb[b] * col[b] - ub[b] * s;
+                for (int bb = 0; bb < Q; ++bb) {
+                    col[bb] = f[sa * a + sb * bb];
+                    s += ub[bb] * col[bb];
+                }
+#pragma unroll
+                for (int b = 0; b < Q; ++b) t1[a + Q * b] = wb[b] * col[b] - ub[b] * s;
+            }
+        } else {
+#pragma unroll
+            for (int a = 0; a < Q; ++a) {
+                T col[Q];
+                T s = T(0);
+#pragma unroll
+                for (int bb = 0; bb < Q; ++bb) {
+                    col[bb] = f[sa * a + sb * bb];
+                    s += ub[bb] * col[bb];
+                }
+#pragma unroll
+                for (int b = 0; b < Q; ++b) t1[a + Q * b] = wb[b] * col[b] - ub[b] * s;
+            }
         }
         if constexpr (sizeof(T) == 4) {
             if (comp == 0) {
