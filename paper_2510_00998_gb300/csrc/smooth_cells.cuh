@@ -634,16 +634,21 @@ __device__ __forceinline__ void smooth_cells_body(const DGConst<T> &c, int64_t c
                 __syncwarp();
                 stage_face<T, Q>(f + 2, cell_neighbour(f + 2, mask, cell, s1, s2), lane, tr_in, slot,
                                  &bars[4 + side]);
+            } else if (!G::LEAN && f == 4) {
+                // area B is free after the last face of slot 0: the factors, whose copy
+                // overlaps the lifting of face 5
+                fence_proxy_async_smem();
+                __syncwarp();
+                stage_bulk<T>(full, lane, &bars[2], sB, fd + cell0 * 3 * FDS, W * 3 * FDS, ncl * 3 * FDS);
             }
         }
         rotate<T, Q>(R);
     }
-    // FP32: the factors into area B and the previous u into area A (the face
-    // slots are free now; u is first needed after the inverse)
+    // FP32: the previous u into area A (face slot 1 is free now; u is first
+    // needed after the inverse)
     if (!G::LEAN) {
         fence_proxy_async_smem();
         __syncwarp();
-        stage_bulk<T>(full, lane, &bars[2], sB, fd + cell0 * 3 * FDS, W * 3 * FDS, ncl * 3 * FDS);
         stage_bulk<T>(full, lane, &bars[1], sA, u + cell0 * NL, W * NL, ncl * NL);
     }
 
