@@ -118,6 +118,12 @@ typedef struct {
                                   /* block-Jacobi smoother and nu_pre/nu_post steps    */
     int basis;                    /* nodes of the 1D Lagrange basis of the DG space:   */
                                   /* DGMG_BASIS_GLL (default) or DGMG_BASIS_GL         */
+    int recompute_block;          /* 0 (default): the per-cell factors of the block    */
+                                  /* inverses A_KK^-1 are computed once at set-up      */
+                                  /* (Technique 3, precomputed); 1: recomputed on the  */
+                                  /* device before every smoothing step (the paper's   */
+                                  /* "recompute" variant of Table 6, Sec. 6.6); same   */
+                                  /* results. Batched solves take 0 (DGMG_EINVAL)      */
 } dgmg_opts;
 
 typedef struct {

@@ -649,6 +649,7 @@ int dgmg_batch_create(int count, const dgmg_mesh *meshes, const int *p, const do
     if (o.nu_pre < 1) return fail(DGMG_EINVAL, "batched solves need nu_pre >= 1");
     if (o.p_coarsening != 0) return fail(DGMG_EINVAL, "batched solves coarsen p directly to Q1 (p_coarsening 0)");
     if (o.basis != DGMG_BASIS_GLL) return fail(DGMG_EINVAL, "batched solves use the GLL basis");
+    if (o.recompute_block != 0) return fail(DGMG_EINVAL, "batched solves use the precomputed block factors");
     for (int i = 0; i < count; ++i)
         if (meshes[i].dim != meshes[0].dim) return fail(DGMG_EINVAL, "all meshes of a batch have one dimension");
     const bool trace = std::getenv("DGMG_TRACE_SETUP") != nullptr;

@@ -406,11 +406,26 @@ int compute_factors(dgmg_ctx &C, const DGSpace &S, DGDev<T> &D, const double *fd
     }
     FDInput in;
     RC(fd_input(C, S, in));
+    const_cast<DGSpace &>(S).fdin = in;
     LC(launch_fd_factors<T>(in, C.d64.kappa, C.ncell, D.fd, C.setup_stream));
     if (sizeof(T) == sizeof(double))
         LC(launch_inverse_eigen_sums(C.dim, S.q, C.ncell, reinterpret_cast<const double *>(D.fd),
                                      reinterpret_cast<double *>(D.linv), C.setup_stream));
     if (D.fdr) LC((launch_residual_factors<T, T>(C.dim, S.q, C.ncell, D.fd, mt, D.fdr, C.setup_stream)));
+    return DGMG_OK;
+}
+
+// The "recompute" variant of the block inverse (Table 6, opts.recompute_block):
+// the level's per-cell factors (and, FP64, the table of inverse eigenvalue
+// sums) computed again on stream s, before a smoothing step, from the same
+// input as at set-up; the residual's factors stay the set-up ones.
+template <typename T>
+int recompute_factors(dgmg_ctx &C, const DGSpace &S, DGDev<T> &D, cudaStream_t s) {
+    if (!D.fd) return DGMG_OK;
+    LC(launch_fd_factors<T>(S.fdin, C.d64.kappa, C.ncell, D.fd, s));
+    if (sizeof(T) == sizeof(double) && D.linv)
+        LC(launch_inverse_eigen_sums(C.dim, S.q, C.ncell, reinterpret_cast<const double *>(D.fd),
+                                     reinterpret_cast<double *>(D.linv), s));
     return DGMG_OK;
 }
 
@@ -753,6 +768,7 @@ template <typename T>
 int level_smooth(dgmg_ctx &C, int l, T *z, const T *b, int cur, cudaStream_t s) {
     DGDev<T> &D = dg_level<T>(C, l);
     C.prof.begin(ST_SMOOTH, s);
+    if (C.opts.recompute_block) RC(recompute_factors<T>(C, C.dgs[l], D, s));
     LC(launch_smooth<T>(C.dim, C.dgs[l].q, D.c, l == 0 ? C.tile_of<T>(TILE_SMOOTH) : 0, exact_block(C), z, b,
                         D.kappa, D.fd, D.linv, D.tr[cur], D.tr[cur ^ 1], s));
     C.prof.end(s);
@@ -1039,6 +1055,7 @@ void dgmg_default_opts(dgmg_opts *o) {
     o->autotune = 0;
     o->p_coarsening = 0;
     o->basis = DGMG_BASIS_GLL;
+    o->recompute_block = 0;
 }
 
 int dgmg_create(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_opts *opts, dgmg_ctx **out) {
@@ -1103,6 +1120,7 @@ int create_ctx(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_opt
     if (o.p_coarsening != 0 && o.p_coarsening != 1) return fail(DGMG_EINVAL, "p_coarsening must be 0 or 1");
     if (o.basis != DGMG_BASIS_GLL && o.basis != DGMG_BASIS_GL)
         return fail(DGMG_EINVAL, "basis must be DGMG_BASIS_GLL or DGMG_BASIS_GL");
+    if (o.recompute_block != 0 && o.recompute_block != 1) return fail(DGMG_EINVAL, "recompute_block must be 0 or 1");
     if (o.outer == DGMG_OUTER_AUTO) o.outer = o.precision == DGMG_MIXED_FP32 ? DGMG_OUTER_RELIABLE : DGMG_OUTER_PCG;
 
     keep_pool_memory();
@@ -1362,6 +1380,7 @@ int dgmg_smooth(dgmg_ctx *C, double *u, const double *b, int nsteps, void *strea
     int cur = 0;
     for (int k = 0; k < nsteps; ++k) {
         C->prof.begin(ST_SMOOTH, s);
+        if (C->opts.recompute_block) RC(recompute_factors<double>(*C, C->dgs[0], D, s));
         LC(launch_smooth<double>(C->dim, C->q, D.c, C->tile[0][TILE_SMOOTH], exact_block(*C), u, b, D.kappa, D.fd, D.linv,
                                  D.tr[cur], D.tr[cur ^ 1], s));
         C->prof.end(s);

@@ -110,6 +110,7 @@ struct DGSpace {
     int p = 0, q = 0, penalty_p = 0;
     int64_t nloc = 0, ndof = 0;
     RefElem1D re;
+    FDInput fdin{};          // input of the factor kernel (kept for recompute_block)
 };
 
 // A lower DG level of a gradual p-hierarchy (levels 1 .. L-1; level 0 is the

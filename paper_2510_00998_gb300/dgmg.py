@@ -51,7 +51,7 @@ class Opts(ctypes.Structure):
                 ("block_inverse", ctypes.c_int), ("coarsening", ctypes.c_int),
                 ("rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("outer", ctypes.c_int),
                 ("delta", ctypes.c_double), ("autotune", ctypes.c_int), ("p_coarsening", ctypes.c_int),
-                ("basis", ctypes.c_int)]
+                ("basis", ctypes.c_int), ("recompute_block", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):

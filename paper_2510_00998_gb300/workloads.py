@@ -23,6 +23,8 @@ Workloads (every input seeded and synthetic):
   table5         the same for the "two-peak" solution in the GLL and the GL basis
   volume_ab      the volume term r = b - kappa E u alone, 64^3 cells, p = 4, FP32:
                  sum-factorised CUDA-core kernel vs tcgen05 tensor-core contraction
+  table6         the setting of Table 6: 2D 729^2 cells, FP64, p = 1..6, smoothing
+                 step with the block factors precomputed vs recomputed per step
 """
 import argparse
 import json
@@ -236,9 +238,39 @@ def run_volume_ab(n=(64, 64, 64), reps=20):
     return out
 
 
+def run_table6(n=729, degrees=(1, 2, 3, 4, 5, 6), steps=10):
+    """The setting of the paper's Table 6 on the GPU: 2D, n x n cells, FP64, the
+    fused single-touch smoothing step (Alg. 4) with the block inverses'
+    factors precomputed at set-up and recomputed before every step
+    (opts.recompute_block); time per step and per DoF (CUDA events of the
+    library's per-stage profile, smoothing stage only)."""
+    import torch
+    from . import dgmg
+    out = {"workload": f"2D {n}x{n} cells, kappa = 1, FP64, {steps} smoothing steps", "rows": []}
+    for p in degrees:
+        row = {"p": p}
+        for rb, key in ((0, "precomputed"), (1, "recompute")):
+            ctx = dgmg.Context((n, n), p, None, recompute_block=rb)
+            g = torch.Generator(device="cuda").manual_seed(5)
+            u = torch.randn(ctx.ndof, dtype=torch.float64, device="cuda", generator=g)
+            b = torch.randn(ctx.ndof, dtype=torch.float64, device="cuda", generator=g)
+            ctx.smooth(u, b, 2)
+            torch.cuda.synchronize()
+            ctx.profile(True)
+            ctx.smooth(u, b, steps)
+            torch.cuda.synchronize()
+            ms, k = ctx.profile_read()["smooth"]
+            ctx.profile(False)
+            row[key] = {"ms_per_step": ms / k, "ns_per_dof": ms / k * 1e6 / ctx.ndof}
+            row["ndof"] = ctx.ndof
+            ctx.close()
+        out["rows"].append(row)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("name", choices=sorted(WORKLOADS) + ["batch", "serve", "tables34", "table5", "volume_ab"])
+    ap.add_argument("name", choices=sorted(WORKLOADS) + ["batch", "serve", "tables34", "table5", "volume_ab", "table6"])
     ap.add_argument("--solves", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--count", type=int, default=0)
@@ -273,6 +305,8 @@ def main():
         print(json.dumps(out))
     elif a.name == "volume_ab":
         print(json.dumps(run_volume_ab()))
+    elif a.name == "table6":
+        print(json.dumps(run_table6()))
     else:
         print(json.dumps(run(a.name, a.solves, a.warmup)))
 
