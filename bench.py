@@ -106,12 +106,15 @@ def smooth_traffic(kernel):
 
 # ---------------------------------------------------------------- flop model
 def smooth_flops(n, q):
-    """Floating-point operations of one launch of the fused smoothing kernel as
-    implemented (an FMA counts 2, a multiplication or division 1): facet mass on
-    the two neighbour fields of every interior face side (each 1D mass in its
-    rank-one form diag(w) - u u^T: per pencil of q values a dot product, q
-    multiplications and q FMAs, 5q operations), lifting, S^T / Lambda^-1 / S
-    along every axis, damped update, new traces of every face."""
+    """Floating-point operations of one launch of the FP64 fused smoothing kernel
+    as implemented (an FMA counts 2, a multiplication 1): facet mass on the two
+    neighbour fields of every interior face side (each 1D mass in its rank-one
+    form diag(w) - u u^T: per pencil of q values a dot product, q multiplications
+    and q FMAs, 5q operations); lifting (per face node q FMAs for the value
+    field, one for the derivative field); S^T and S along every axis; the
+    inverse eigenvalue sums (with the damping folded in) as one multiplication
+    per node; the update (1 - omega) u + y as one FMA per node; the derivative
+    traces of every face."""
     d = len(n)
     ncell = 1
     for v in n:
@@ -123,8 +126,8 @@ def smooth_flops(n, q):
         other = ncell // n[a]
         sides += 2 * (n[a] - 1) * other
     facet_mass = sides * 2 * (d - 1) * 5 * nf
-    lift = sides * nf * (q * 2 + 4)
-    per_cell = 2 * d * nl * q * 2 + nl * 3 + nl * 3 + d * nf * 2 * q * 2
+    lift = sides * nf * (q * 2 + 2)
+    per_cell = 2 * d * nl * q * 2 + nl * 1 + nl * 2 + d * nf * 2 * q * 2
     return facet_mass + lift + ncell * per_cell
 
 

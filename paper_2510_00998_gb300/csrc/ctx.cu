@@ -410,7 +410,7 @@ int compute_factors(dgmg_ctx &C, const DGSpace &S, DGDev<T> &D, const double *fd
     LC(launch_fd_factors<T>(in, C.d64.kappa, C.ncell, D.fd, C.setup_stream));
     if (sizeof(T) == sizeof(double))
         LC(launch_inverse_eigen_sums(C.dim, S.q, C.ncell, reinterpret_cast<const double *>(D.fd),
-                                     reinterpret_cast<double *>(D.linv), C.setup_stream));
+                                     C.opts.omega_dg, reinterpret_cast<double *>(D.linv), C.setup_stream));
     if (D.fdr) LC((launch_residual_factors<T, T>(C.dim, S.q, C.ncell, D.fd, mt, D.fdr, C.setup_stream)));
     return DGMG_OK;
 }
@@ -425,7 +425,7 @@ int recompute_factors(dgmg_ctx &C, const DGSpace &S, DGDev<T> &D, cudaStream_t s
     LC(launch_fd_factors<T>(S.fdin, C.d64.kappa, C.ncell, D.fd, s));
     if (sizeof(T) == sizeof(double) && D.linv)
         LC(launch_inverse_eigen_sums(C.dim, S.q, C.ncell, reinterpret_cast<const double *>(D.fd),
-                                     reinterpret_cast<double *>(D.linv), s));
+                                     C.opts.omega_dg, reinterpret_cast<double *>(D.linv), s));
     return DGMG_OK;
 }
 

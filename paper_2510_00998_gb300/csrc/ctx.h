@@ -35,7 +35,7 @@ template <typename T>
 struct DGDev {
     DGConst<T> c;
     T *kappa = nullptr, *fd = nullptr, *tr[2] = {nullptr, nullptr}, *corners = nullptr;
-    T *linv = nullptr;   // per-node 1 / (sum of the cell's eigenvalues); FP64 only
+    T *linv = nullptr;   // per-node omega / (sum of the cell's eigenvalues); FP64 only
     T *fdr = nullptr;    // the residual's factors [S^T M | lambda] per cell and axis
 };
 

@@ -586,7 +586,8 @@ __device__ __forceinline__ void k_smooth_body(const DGConst<T> &c, int64_t cell0
 #pragma unroll
             for (int i = 0; i < Q; ++i) x[i] = myR[G::vidx(D, t, i)];
             // 1 / (lambda_x + lambda_y + lambda_z): from the per-node table when
-            // one is given (saves a division per node), else divided here
+            // one is given (saves a division per node; the table holds omega /
+            // the sum, so the damping is then already applied), else divided here
             const T *li = linv ? linv + cell * G::NL : nullptr;
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
@@ -642,7 +643,7 @@ __device__ __forceinline__ void k_smooth_body(const DGConst<T> &c, int64_t cell0
             T s = T(0);
 #pragma unroll
             for (int i = 0; i < Q; ++i) s += S[m * Q + i] * x[i];
-            un[m] = keep * myU[G::vidx(0, t, m)] + om * s;
+            un[m] = linv ? keep * myU[G::vidx(0, t, m)] + s : keep * myU[G::vidx(0, t, m)] + om * s;
         }
 #pragma unroll
         for (int i = 0; i < Q; ++i) myU[G::vidx(0, t, i)] = un[i];

@@ -126,8 +126,9 @@ __global__ void __launch_bounds__(128) k_fd_factors(const __grid_constant__ FDIn
     for (int i = 0; i < q; ++i) out[q * q + i] = (T)lam[i];
 }
 
-// linv[cell][node] = 1 / (lambda_x[i] + lambda_y[j] (+ lambda_z[k])) from the factors
-__global__ void k_inverse_eigen_sums(int dim, int q, int64_t ncell, const double *__restrict__ fd,
+// linv[cell][node] = omega / (lambda_x[i] + lambda_y[j] (+ lambda_z[k])) from the
+// factors: the inverse eigenvalue sums with the smoother's damping folded in
+__global__ void k_inverse_eigen_sums(int dim, int q, int64_t ncell, const double *__restrict__ fd, double omega,
                                      double *__restrict__ linv) {
     const int64_t nloc = dim == 3 ? (int64_t)q * q * q : (int64_t)q * q;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -137,7 +138,7 @@ __global__ void k_inverse_eigen_sums(int dim, int q, int64_t ncell, const double
     const double *f = fd + cell * dim * fds + q * q;
     double s = f[node % q] + f[fds + (node / q) % q];
     if (dim == 3) s += f[2 * fds + node / (q * q)];
-    linv[idx] = 1.0 / s;
+    linv[idx] = omega / s;
 }
 
 }  // namespace
@@ -153,12 +154,12 @@ cudaError_t launch_fd_factors(const FDInput &in, const double *kappa, int64_t nc
 template cudaError_t launch_fd_factors<double>(const FDInput &, const double *, int64_t, double *, cudaStream_t);
 template cudaError_t launch_fd_factors<float>(const FDInput &, const double *, int64_t, float *, cudaStream_t);
 
-cudaError_t launch_inverse_eigen_sums(int dim, int q, int64_t ncell, const double *fd, double *linv,
-                                      cudaStream_t s) {
+cudaError_t launch_inverse_eigen_sums(int dim, int q, int64_t ncell, const double *fd, double omega,
+                                      double *linv, cudaStream_t s) {
     const int64_t n = ncell * (dim == 3 ? (int64_t)q * q * q : (int64_t)q * q);
     if (n == 0) return cudaSuccess;
     count_launches(1);
-    k_inverse_eigen_sums<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dim, q, ncell, fd, linv);
+    k_inverse_eigen_sums<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dim, q, ncell, fd, omega, linv);
     return cudaGetLastError();
 }
 

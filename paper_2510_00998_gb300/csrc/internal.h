@@ -90,9 +90,10 @@ struct MassTables {
 template <typename TI, typename TO>
 cudaError_t launch_residual_factors(int dim, int q, int64_t ncell, const TI *fd, const MassTables &m, TO *fdr,
                                     cudaStream_t s);
-// linv[cell][node] = 1 / (sum of the cell's eigenvalues at the node)
-cudaError_t launch_inverse_eigen_sums(int dim, int q, int64_t ncell, const double *fd, double *linv,
-                                      cudaStream_t s);
+// linv[cell][node] = omega / (sum of the cell's eigenvalues at the node): the
+// smoother's damping folded into the table
+cudaError_t launch_inverse_eigen_sums(int dim, int q, int64_t ncell, const double *fd, double omega,
+                                      double *linv, cudaStream_t s);
 
 // ------------------------------------------------------------ kernels API
 // Constant data of one DG level, passed to kernels by value.

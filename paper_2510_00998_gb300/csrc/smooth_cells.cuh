@@ -307,13 +307,21 @@ __device__ __forceinline__ void pass_x(const T *A, T *R) {
 // pencil instead of q^2; wa, ua / wb, ub in shared memory):
 //   low face:  N = kF [e_0 (x) (H/2 - gamma G) - d_0 (x) G/2],
 //   high face: N = kF [e_p (x) (-H/2 - gamma G) + d_p (x) G/2].
+// The two terms of G share one vector: the pencil at (a, b) takes
+// G(a, b) c with c = sgn kF/2 d + kF gamma e_end, formed once per face.
 template <typename T, int Q>
 __device__ __forceinline__ void lift_x_face(int side, const T *fld, int sa, int sb, const T *wa, const T *ua,
                                             const T *wb, const T *ub, const T *dv, T gam, T kF, T *R) {
     constexpr int NF = Q * Q;
-    const T g2 = kF * gam, wv = T(0.5) * kF, sgn = side ? T(-1) : T(1);
-    // value field: end layer += kF gamma G; all layers += sgn kF/2 G d
-    // derivative field: end layer -= sgn kF/2 H
+    const T wv = T(0.5) * kF;
+    // value field: all layers += G c; derivative field: end layer -= sgn kF/2 H
+    T cg[Q];
+    {
+        const T sw = side ? -wv : wv;
+#pragma unroll
+        for (int n = 0; n < Q; ++n) cg[n] = sw * dv[n];
+        cg[side ? Q - 1 : 0] += kF * gam;
+    }
 #pragma unroll
     for (int comp = 0; comp < 2; ++comp) {
         const T *f = fld + comp * NF;
@@ -374,28 +382,23 @@ __device__ __forceinline__ void lift_x_face(int side, const T *fld, int sa, int 
 #pragma unroll
                     for (int a = 0; a < Q; ++a) vv[a + Q * b] = wa[a] * t1[a + Q * b] - ua[a] * s;
                 }
-                // pencils t, t + 1: pen[n] += (sgn wv v) dv[n] by two-lane FMAs
+                // pencils t, t + 1: pen[n] += v c[n] by two-lane FMAs
                 float *Rf = reinterpret_cast<float *>(R);
 #pragma unroll
                 for (int t = 0; t < NF; t += 2) {
                     if (t + 1 < NF) {
-                        const float2 w2 = make_float2((float)(sgn * wv * vv[t]), (float)(sgn * wv * vv[t + 1]));
+                        const float2 v2 = make_float2((float)vv[t], (float)vv[t + 1]);
 #pragma unroll
                         for (int n = 0; n < Q; ++n) {
                             float2 pp = make_float2(Rf[Q * t + n], Rf[Q * (t + 1) + n]);
-                            pp = __ffma2_rn(w2, make_float2((float)dv[n], (float)dv[n]), pp);
+                            pp = __ffma2_rn(v2, make_float2((float)cg[n], (float)cg[n]), pp);
                             Rf[Q * t + n] = pp.x;
                             Rf[Q * (t + 1) + n] = pp.y;
                         }
                     } else {
-                        const T w = sgn * wv * vv[t];
 #pragma unroll
-                        for (int n = 0; n < Q; ++n) R[Q * t + n] += w * dv[n];
+                        for (int n = 0; n < Q; ++n) R[Q * t + n] += vv[t] * cg[n];
                     }
-                }
-#pragma unroll
-                for (int t = 0; t < NF; ++t) {
-                    if (side) R[Q * t + Q - 1] += g2 * vv[t]; else R[Q * t] += g2 * vv[t];
                 }
                 continue;
             }
@@ -410,10 +413,8 @@ __device__ __forceinline__ void lift_x_face(int side, const T *fld, int sa, int 
                 const T v = wa[a] * t1[a + Q * b] - ua[a] * s;
                 T *pen = R + Q * (a + Q * b);              // the pencil along x at (a, b)
                 if (comp == 0) {
-                    const T w = sgn * wv * v;
-                    if (side) pen[Q - 1] += g2 * v; else pen[0] += g2 * v;
 #pragma unroll
-                    for (int n = 0; n < Q; ++n) pen[n] += w * dv[n];
+                    for (int n = 0; n < Q; ++n) pen[n] += v * cg[n];
                 } else {
                     if (side) pen[Q - 1] += wv * v; else pen[0] -= wv * v;
                 }
@@ -478,7 +479,8 @@ __device__ __forceinline__ void cells_write_traces(const DGConst<T> &c, T *R, in
                                                    T *slot0, T *slot1, T *__restrict__ tr_out) {
     using G = CellGeo<T, Q>;
     constexpr int FS = G::FS, TR = G::TR;
-#pragma unroll 1
+    // unrolled: the two rotations become register renames
+#pragma unroll
     for (int p = 0; p < 3; ++p) {
         const int sa = p == 1 ? Q : 1, sb = p == 1 ? 1 : Q;
         if (!G::LEAN && p > 0) bulk_wait_read_all();
@@ -673,8 +675,9 @@ __device__ __forceinline__ void smooth_cells_body(const DGConst<T> &c, int64_t c
         rotate<T, Q>(R);
     }
 
-    // u <- (1 - w) u + w y, stored through area A (the barrier also ends every
-    // lane's reads of the factors before area A (FP64) or B (FP32) is rewritten)
+    // u <- (1 - w) u + w y (w already in y when the inverse came from the table),
+    // stored through area A (the barrier also ends every lane's reads of the
+    // factors before area A (FP64) or B (FP32) is rewritten)
     if (!G::LEAN && full)
         ok = warp_wait_copies(&bars[1], lane) && ok;
     else
@@ -683,8 +686,13 @@ __device__ __forceinline__ void smooth_cells_body(const DGConst<T> &c, int64_t c
     if (active) {
         const T om = c.omega, keep = T(1) - om;
         const T *uo = G::LEAN ? u + cell * NL : sA + lane * NL;
+        if (table) {
 #pragma unroll
-        for (int e = 0; e < NL; ++e) R[e] = keep * uo[e] + om * R[e];
+            for (int e = 0; e < NL; ++e) R[e] = keep * uo[e] + R[e];
+        } else {
+#pragma unroll
+            for (int e = 0; e < NL; ++e) R[e] = keep * uo[e] + om * R[e];
+        }
 #pragma unroll
         for (int e = 0; e < NL; ++e) myU[e] = R[e];
     }
