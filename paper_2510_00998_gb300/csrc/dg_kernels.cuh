@@ -307,6 +307,8 @@ __device__ __forceinline__ void build_block_1d(const DGConst<T> &c, const T *sT,
 // R -= A_KK U with A_KK = sum_a Kt_a (x) M (x) M by sum factorisation:
 // 3D: a = M_z u, bb = Kt_z u; c = M_y a, e = Kt_y a + M_y bb; y = Kt_x c + M_x e.
 // 2D: a = M_y u, bb = Kt_y u; y = Kt_x a + M_x bb. Contains barriers.
+// myB may be myU: each thread reads its whole pencil of u before writing the
+// same positions, and u is not read again.
 template <int DIM, int Q, typename T>
 __device__ __forceinline__ void subtract_block_apply(const DGConst<T> &c, bool active, int t, const T *myU, T *myR,
                                                      T *myA, T *myB, const T *myKT, const T *sMw, const T *sMu) {
@@ -677,11 +679,12 @@ template <int DIM, int Q, typename T>
 __device__ __forceinline__ void k_residual_body(const DGConst<T> &c, int64_t cell0, int cpb, int mode, const T *__restrict__ u, const T *__restrict__ b, const T *__restrict__ kappa, const T *__restrict__ tr, T *__restrict__ rout, T *__restrict__ corners) {
     using G = Geo<DIM, Q, T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    // u is read once, by the first pass of the A_KK apply, which overwrites it
+    // with one of its two intermediate tensors (sA holds the other)
     T *sU = reinterpret_cast<T *>(smem_raw);
     T *sR = sU + cpb * G::NL;
     T *sA = sR + cpb * G::NL;
-    T *sB = sA + cpb * G::NL;
-    T *sF = sB + cpb * G::NL;
+    T *sF = sA + cpb * G::NL;
     T *sKT = sF + cpb * G::NFACE * 2 * G::NF;   // [cpb][DIM][Q*Q]
     T *sK = sKT + cpb * DIM * Q * Q;            // [cpb][NFACE + 1]
     T *sDot = sK + cpb * (G::NFACE + 1);        // [cpb][facet-mass dot products]
@@ -714,7 +717,7 @@ __device__ __forceinline__ void k_residual_body(const DGConst<T> &c, int64_t cel
     T *myR = sR + lc * G::NL;
     T *myU = sU + lc * G::NL;
     lift_neighbours<DIM, Q, T>(c, active, t, myR, myF, myK, mask);
-    subtract_block_apply<DIM, Q, T>(c, active, t, myU, myR, sA + lc * G::NL, sB + lc * G::NL, myKT, sMw, sMu);
+    subtract_block_apply<DIM, Q, T>(c, active, t, myU, myR, sA + lc * G::NL, myU, myKT, sMw, sMu);
     T rr[Q];
     if (active) {
 #pragma unroll
@@ -895,7 +898,7 @@ constexpr size_t smem_smooth(int cpb, bool exact) {
 template <int DIM, int Q, typename T>
 constexpr size_t smem_residual(int cpb) {
     using G = Geo<DIM, Q, T>;
-    return (size_t)cpb * (4 * G::NL + G::NFACE * 2 * G::NF + DIM * Q * Q + G::NFACE + 1 + G::NDOT) * sizeof(T);
+    return (size_t)cpb * (3 * G::NL + G::NFACE * 2 * G::NF + DIM * Q * Q + G::NFACE + 1 + G::NDOT) * sizeof(T);
 }
 
 template <int DIM, int Q, typename T>
