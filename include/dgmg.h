@@ -480,6 +480,22 @@ int64_t dgmg_cg_size(const dgmg_ctx *ctx, int level);
  */
 int dgmg_volume_residual_f32(dgmg_ctx *ctx, const float *u, const float *b, float *r, int method, void *stream);
 
+/*
+ * y = A u in FP32 on the finest level of a DGMG_MIXED_FP32 ctx: the operator of
+ * the FP32 CG recurrences of the reliable-update solver (Eq. matrix_form_IP,
+ * the cell equation of Alg. 2 stage 3 with b = 0), exposed to test and time its
+ * forms. u, y: DEVICE FP32 DG vectors (layout as above, 16-byte aligned for the
+ * one-thread-per-cell forms), y not aliasing u; ctx's FP32 traces are scratch.
+ * form 0: the solver's choice (form 1 or the one-thread-per-cell kernel with
+ * A_KK u in the direct sum-factorised form sum_a Kt_a (x) M (x) M, which keeps
+ * the rounding of form 1); form 1: the per-pencil kernel; form 2: one thread per
+ * cell with A_KK u through the fast-diagonalisation factors (the V-cycle's
+ * residual; its FP32 rounding costs the CG recurrences iterations). All forms
+ * agree to FP32 rounding. DGMG_EINVAL for an FP64 ctx, NULL or aliasing vectors
+ * or another form.
+ */
+int dgmg_apply_f32(dgmg_ctx *ctx, const float *u, float *y, int form, void *stream);
+
 /* ---- instrumentation ---- */
 
 /*

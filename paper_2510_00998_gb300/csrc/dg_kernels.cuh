@@ -1008,6 +1008,27 @@ struct DGLaunch {
             return cudaErrorInvalidValue;
         }
     }
+    // the direct-form one-thread-per-cell residual (FP32: the CG operator)
+    static cudaError_t residual_cells_direct(const DGConst<T> &c, int mode, const T *u, const T *b, const T *kappa,
+                                             const T *tr, T *r, T *corners, cudaStream_t s) {
+        if constexpr (CELLS_OK && sizeof(T) == 4) {
+            using CG = CellGeo<T, Q>;
+            static bool attr = false;
+            if (!attr) {
+                cudaFuncSetAttribute(k_residual_cells_direct<T, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)CG::BYTES);
+                attr = true;
+            }
+            const int64_t grid = (c.ncell + CG::W - 1) / CG::W;
+            if (grid == 0) return cudaSuccess;
+            count_launches(1);
+            k_residual_cells_direct<T, Q><<<(unsigned)grid, CG::W, CG::BYTES, s>>>(c, mode, u, b, kappa, tr, r,
+                                                                                   corners);
+            return cudaGetLastError();
+        } else {
+            return cudaErrorInvalidValue;
+        }
+    }
     // ---- batched forms (map: one entry per work item of cpb cells, 32 for the
     // one-thread-per-cell kernels; persistent grids)
     static cudaError_t project_batch(const BatchDG<T> *D, const BlockMap *map, int nblocks, int cpb, T *u,
@@ -1105,6 +1126,10 @@ struct DGLaunch {
                                   ((mode & RES_WRITE_R) ? reinterpret_cast<uintptr_t>(r) : 0);
             if (cpb <= 0 && fd && !c.gl && (vec & 15) == 0 && (reinterpret_cast<uintptr_t>(tr) & tra) == 0)
                 return residual_cells(c, mode, u, b, kappa, fd, tr, r, corners, s);
+            // without factors (the FP32 CG operator): A_KK u in the direct form
+            if (sizeof(T) == 4 && cpb <= 0 && !fd && !c.gl && (vec & 15) == 0 &&
+                (reinterpret_cast<uintptr_t>(tr) & tra) == 0)
+                return residual_cells_direct(c, mode, u, b, kappa, tr, r, corners, s);
         }
         if (cpb <= 0) cpb = default_cpb();
         const size_t sm = smem_residual<DIM, Q, T>(cpb);

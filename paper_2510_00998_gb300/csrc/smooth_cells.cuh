@@ -812,6 +812,121 @@ __global__ void __launch_bounds__(32) k_project_cells(const __grid_constant__ DG
     project_cells_body<T, Q>(c, (int64_t)blockIdx.x * CellGeo<T, Q>::W, u, e0, tr);
 }
 
+// Kt_a of the cell along axis a (row-major q x q, GLL): kappa_K K_a plus the
+// cell's own facet terms of the two faces normal to a (rows and columns 0 and
+// q - 1); kF[f] is the facet coefficient of an interior face f (bit f of mask),
+// a boundary face takes kappa_K with weight 1 (Nitsche). The same entries as the
+// per-pencil kernels' block tables.
+template <typename T, int Q, int A>
+__device__ __forceinline__ void build_kt(const DGConst<T> &c, T kK, const T *kF, int mask, T *Kt) {
+    const bool inL = mask & (1 << (2 * A)), inR = mask & (1 << (2 * A + 1));
+    const T kL = inL ? kF[2 * A] : kK, wL = inL ? T(0.5) : T(1);
+    const T kR = inR ? kF[2 * A + 1] : kK, wR = inR ? T(0.5) : T(1);
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            T v = kK * c.K[A][i * Q + j];
+            if (i == 0 || j == 0) {
+                if (i == 0 && j == 0)
+                    v += kL * (T(2) * wL * c.d0[A][0] + c.gamma[A]);
+                else
+                    v += kL * wL * c.d0[A][i == 0 ? j : i];
+            }
+            if (i == Q - 1 || j == Q - 1) {
+                if (i == Q - 1 && j == Q - 1)
+                    v += kR * (c.gamma[A] - T(2) * wR * c.dp[A][Q - 1]);
+                else
+                    v -= kR * wR * c.dp[A][i == Q - 1 ? j : i];
+            }
+            Kt[i * Q + j] = v;
+        }
+}
+
+// R = A_KK u in the direct sum-factorised form A_KK = sum_a Kt_a (x) M (x) M
+// (the rounding of the per-pencil kernels, which the FP32 CG recurrences need),
+// one thread per cell: u in the lane's part Y of shared memory (natural order
+// x + q y + q^2 z), overwritten by the second intermediate. With the 1D masses
+// in their rank-one form M x = w o x - mu (mu . x):
+//   along z: R = M_z u, Y = Kt_z u;
+//   along y: R <- M_y R, Y <- Kt_y R + M_y Y;
+//   along x: R <- Kt_x R + M_x Y.
+// Each pencil reads and writes only its own positions of Y, and the axes are
+// fixed at compile time (no rotation of R).
+template <typename T, int Q>
+__device__ __forceinline__ void direct_volume(const DGConst<T> &c, T kK, const T *kF, int mask, T *Y, T *R) {
+    T Kt[Q * Q];
+    build_kt<T, Q, 2>(c, kK, kF, mask, Kt);
+#pragma unroll
+    for (int j = 0; j < Q; ++j)
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            T x[Q];
+#pragma unroll
+            for (int n = 0; n < Q; ++n) x[n] = Y[i + Q * j + Q * Q * n];
+            T d = T(0);
+#pragma unroll
+            for (int n = 0; n < Q; ++n) d += c.mu[2][n] * x[n];
+#pragma unroll
+            for (int m = 0; m < Q; ++m) {
+                T sb = T(0);
+#pragma unroll
+                for (int n = 0; n < Q; ++n) sb += Kt[m * Q + n] * x[n];
+                R[i + Q * j + Q * Q * m] = c.mw[2][m] * x[m] - c.mu[2][m] * d;
+                Y[i + Q * j + Q * Q * m] = sb;
+            }
+            asm volatile("" ::: "memory");   // keeps later pencils' loads here (no spills)
+        }
+    build_kt<T, Q, 1>(c, kK, kF, mask, Kt);
+#pragma unroll
+    for (int k = 0; k < Q; ++k)
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            T xa[Q], xb[Q];
+#pragma unroll
+            for (int n = 0; n < Q; ++n) {
+                xa[n] = R[i + Q * n + Q * Q * k];
+                xb[n] = Y[i + Q * n + Q * Q * k];
+            }
+            T da = T(0), db = T(0);
+#pragma unroll
+            for (int n = 0; n < Q; ++n) {
+                da += c.mu[1][n] * xa[n];
+                db += c.mu[1][n] * xb[n];
+            }
+#pragma unroll
+            for (int m = 0; m < Q; ++m) {
+                T se = c.mw[1][m] * xb[m] - c.mu[1][m] * db;
+#pragma unroll
+                for (int n = 0; n < Q; ++n) se += Kt[m * Q + n] * xa[n];
+                R[i + Q * m + Q * Q * k] = c.mw[1][m] * xa[m] - c.mu[1][m] * da;
+                Y[i + Q * m + Q * Q * k] = se;
+            }
+            asm volatile("" ::: "memory");
+        }
+    build_kt<T, Q, 0>(c, kK, kF, mask, Kt);
+#pragma unroll
+    for (int t = 0; t < Q * Q; ++t) {
+        T xa[Q], xb[Q];
+#pragma unroll
+        for (int n = 0; n < Q; ++n) {
+            xa[n] = R[n + Q * t];
+            xb[n] = Y[n + Q * t];
+        }
+        T db = T(0);
+#pragma unroll
+        for (int n = 0; n < Q; ++n) db += c.mu[0][n] * xb[n];
+#pragma unroll
+        for (int m = 0; m < Q; ++m) {
+            T sy = c.mw[0][m] * xb[m] - c.mu[0][m] * db;
+#pragma unroll
+            for (int n = 0; n < Q; ++n) sy += Kt[m * Q + n] * xa[n];
+            R[m + Q * t] = sy;
+        }
+        asm volatile("" ::: "memory");
+    }
+}
+
 // Residual r = b - A u with one thread per cell, 3D, exact diagonal blocks
 // (Alg. 2 stage 3; the residual of a V-cycle level and the operator apply),
 // with A u = A_KK u + N u_nb. A_KK u from the cell's fast-diagonalisation
@@ -827,7 +942,11 @@ __global__ void __launch_bounds__(32) k_project_cells(const __grid_constant__ DG
 // in registers, the neighbour faces through the slots once the factors are
 // used; FP64 (LEAN): the factors into u's area, b and the faces read per lane.
 // r leaves through area A by a bulk store.
-template <typename T, int Q>
+// DIRECT (FP32, fd unused): A_KK u in the direct form (direct_volume) instead,
+// for the operator of the FP32 CG recurrences; u stays in area A for the
+// volume passes, the first neighbour face is staged into area B at once, b is
+// read per lane.
+template <typename T, int Q, bool DIRECT = false>
 __device__ __forceinline__ void residual_cells_body(const DGConst<T> &c, int64_t cell0, int mode,
                                                     const T *__restrict__ u, const T *__restrict__ b,
                                                     const T *__restrict__ kappa, const T *__restrict__ fd,
@@ -855,8 +974,10 @@ __device__ __forceinline__ void residual_cells_body(const DGConst<T> &c, int64_t
         sMu[e / Q][e % Q] = c.mu[e / Q][e % Q];
     }
     bool ok = true;                                      // false once a bounded wait ran out
+    static_assert(!DIRECT || !G::LEAN, "the direct form is the FP32 operator's");
     stage_bulk<T>(full, lane, &bars[0], sA, u + cell0 * NL, W * NL, ncl * NL);
-    if (!G::LEAN) stage_bulk<T>(full, lane, &bars[2], sB, fd + cell0 * 3 * FDS, W * 3 * FDS, ncl * 3 * FDS);
+    if (!G::LEAN && !DIRECT)
+        stage_bulk<T>(full, lane, &bars[2], sB, fd + cell0 * 3 * FDS, W * 3 * FDS, ncl * 3 * FDS);
     int mask = 0;
     if (active) {
         int ci[3];
@@ -864,6 +985,7 @@ __device__ __forceinline__ void residual_cells_body(const DGConst<T> &c, int64_t
         mask = interior_mask<3>(ci, c.n);
     }
     const int s1 = c.n[0], s2 = c.n[0] * c.n[1];
+    if (DIRECT) stage_face<T, Q>(0, cell_neighbour(0, mask, cell, s1, s2), lane, tr, sB, &bars[4]);
     const T kK = active ? kappa[cell] : T(1);
 
     if (full)
@@ -871,6 +993,23 @@ __device__ __forceinline__ void residual_cells_body(const DGConst<T> &c, int64_t
     else
         __syncwarp();
     T R[NL];
+    if constexpr (DIRECT) {
+        if (active) {
+            T kF[6];
+#pragma unroll
+            for (int f = 0; f < 6; ++f) kF[f] = facet_kappa<T>(cell_neighbour(f, mask, cell, s1, s2), kK, kappa);
+            direct_volume<T, Q>(c, kK, kF, mask, sA + lane * NL, R);
+            const T *bb = has_b ? b + cell * NL : nullptr;
+#pragma unroll
+            for (int e = 0; e < NL; ++e) R[e] = (bb ? bb[e] : T(0)) - R[e];
+        } else {
+#pragma unroll
+            for (int e = 0; e < NL; ++e) R[e] = T(0);
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        stage_face<T, Q>(1, cell_neighbour(1, mask, cell, s1, s2), lane, tr, sA, &bars[5]);
+    } else {
 #pragma unroll
     for (int e = 0; e < NL; ++e) R[e] = active ? sA[lane * NL + e] : T(0);
     fence_proxy_async_smem();
@@ -930,6 +1069,7 @@ __device__ __forceinline__ void residual_cells_body(const DGConst<T> &c, int64_t
         stage_face<T, Q>(0, cell_neighbour(0, mask, cell, s1, s2), lane, tr, sB, &bars[4]);
         stage_face<T, Q>(1, cell_neighbour(1, mask, cell, s1, s2), lane, tr, sA, &bars[5]);
     }
+    }   // !DIRECT
     // R -= N u_nb, face pair by face pair as in the smoothing step
 #pragma unroll 1
     for (int p = 0; p < 3; ++p) {
@@ -1027,6 +1167,17 @@ __global__ void __launch_bounds__(32) k_residual_cells(const __grid_constant__ D
                                                        const T *__restrict__ tr, T *__restrict__ rout,
                                                        T *__restrict__ corners) {
     residual_cells_body<T, Q>(c, (int64_t)blockIdx.x * CellGeo<T, Q>::W, mode, u, b, kappa, fd, tr, rout, corners);
+}
+
+// The same output with A_KK u in the direct form (FP32 CG operator; no factors).
+template <typename T, int Q>
+__global__ void __launch_bounds__(32) k_residual_cells_direct(const __grid_constant__ DGConst<T> c, int mode,
+                                                              const T *__restrict__ u, const T *__restrict__ b,
+                                                              const T *__restrict__ kappa,
+                                                              const T *__restrict__ tr, T *__restrict__ rout,
+                                                              T *__restrict__ corners) {
+    residual_cells_body<T, Q, true>(c, (int64_t)blockIdx.x * CellGeo<T, Q>::W, mode, u, b, kappa, nullptr, tr, rout,
+                                    corners);
 }
 
 template <typename T, int Q>

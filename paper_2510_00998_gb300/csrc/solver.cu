@@ -603,6 +603,29 @@ int dgmg_solve(dgmg_ctx *C, const double *b, double *x, dgmg_stats *stats, void 
     return run.status;
 }
 
+int dgmg_apply_f32(dgmg_ctx *C, const float *u, float *y, int form, void *stream) {
+    RC(check_ctx(C));
+    if (C->opts.precision != DGMG_MIXED_FP32) return fail(DGMG_EINVAL, "dgmg_apply_f32: needs a mixed-precision ctx");
+    if (!u || !y) return fail(DGMG_EINVAL, "dgmg_apply_f32: NULL vector");
+    if (u == y) return fail(DGMG_EINVAL, "dgmg_apply_f32: y must not alias u");
+    if (form < 0 || form > 2) return fail(DGMG_EINVAL, "dgmg_apply_f32: form must be 0, 1 or 2");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (form == 0) return dgmg::apply32(*C, u, y, s);
+    DGDev<float> &D = C->d32;
+    C->prof.begin(ST_PROJECT, s);
+    LC(dgmg::launch_project<float>(C->dim, C->q, D.c, C->tile[1][TILE_PROJECT], const_cast<float *>(u), nullptr,
+                                   D.tr[0], s));
+    C->prof.end(s);
+    // form 1: the per-pencil kernel (a positive tile), form 2: one thread per
+    // cell through the fast-diagonalisation factors
+    const int tile = form == 1 ? std::max(1, 128 / (C->dim == 3 ? C->q * C->q : C->q)) : 0;
+    C->prof.begin(ST_RESIDUAL, s);
+    LC(dgmg::launch_residual<float>(C->dim, C->q, D.c, tile, dgmg::RES_WRITE_R | dgmg::RES_NEGATE, u, nullptr,
+                                    D.kappa, D.tr[0], y, nullptr, form == 2 ? D.fdr : nullptr, s));
+    C->prof.end(s);
+    return DGMG_OK;
+}
+
 int dgmg_solve_host(dgmg_ctx *C, const double *b_host, double *x_host, dgmg_stats *stats, void *stream) {
     RC(check_ctx(C));
     if (!b_host || !x_host) return fail(DGMG_EINVAL, "b_host and x_host must not be NULL");

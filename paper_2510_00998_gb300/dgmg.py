@@ -115,6 +115,7 @@ _SIGS = {
     "dgmg_coarse_solve": (_I, [_P, _P, _P, _P]),
     "dgmg_cg_size": (ctypes.c_int64, [_P, _I]),
     "dgmg_volume_residual_f32": (_I, [_P, _P, _P, _P, _I, _P]),
+    "dgmg_apply_f32": (_I, [_P, _P, _P, _I, _P]),
     "dgmg_estimate_bytes": (_I, [ctypes.POINTER(Mesh), _I, ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_size_t)]),
     "dgmg_server_create": (_I, [ctypes.c_size_t, _I, ctypes.POINTER(Opts), ctypes.POINTER(_P)]),
     "dgmg_submit": (_I, [_P, ctypes.POINTER(Mesh), _I, _P, _P, _P, ctypes.POINTER(ctypes.c_uint64)]),
@@ -457,6 +458,16 @@ class Context:
                 raise ValueError("FP32 contiguous CUDA tensors expected")
         _check(self.lib.dgmg_volume_residual_f32(self.h, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(b.data_ptr()),
                                                  ctypes.c_void_p(r.data_ptr()), int(method), _stream(stream)))
+
+    def apply_f32(self, u, y, form=0, stream=None):
+        """y = A u in FP32 (mixed-precision ctx): the operator of the FP32 CG
+        recurrences; form 0 the solver's choice, 1 per pencil, 2 one thread per
+        cell through the fast-diagonalisation factors."""
+        for t in (u, y):
+            if not t.is_cuda or not t.is_contiguous() or t.dtype != __import__("torch").float32:
+                raise ValueError("FP32 contiguous CUDA tensors expected")
+        _check(self.lib.dgmg_apply_f32(self.h, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                       int(form), _stream(stream)))
 
     def cg_smooth(self, level, u, b, nsteps, stream=None):
         _check(self.lib.dgmg_cg_smooth(self.h, int(level), _ptr(u), _ptr(b), int(nsteps), _stream(stream)))
