@@ -405,8 +405,8 @@ int batch_apply32(dgmg_batch &B, const float *u, float *out, cudaStream_t s) {
         LC(launch_project_batch<float>(B.dim, grp.q, g.D, g.map[TILE_PROJECT], g.nblocks[TILE_PROJECT],
                                        g.tile[TILE_PROJECT], const_cast<float *>(u) + grp.dof0, 0, s));
         LC(launch_residual_batch<float>(B.dim, grp.q, g.D, g.map[TILE_RESIDUAL], g.nblocks[TILE_RESIDUAL],
-                                        g.tile[TILE_RESIDUAL], RES_WRITE_R | RES_NEGATE, u + grp.dof0, nullptr,
-                                        out + grp.dof0, 0, s));
+                                        g.tile[TILE_RESIDUAL], RES_WRITE_R | RES_NEGATE | RES_DIRECT, u + grp.dof0,
+                                        nullptr, out + grp.dof0, 0, s));
     }
     return DGMG_OK;
 }

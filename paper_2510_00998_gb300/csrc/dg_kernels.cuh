@@ -857,6 +857,21 @@ __global__ void __launch_bounds__(32) k_residual_cells_batch(const BatchDG<T> *_
     }
 }
 
+template <typename T, int Q>
+__global__ void __launch_bounds__(32) k_residual_cells_batch_direct(const BatchDG<T> *__restrict__ D,
+                                                                     const BlockMap *__restrict__ map, int nblocks,
+                                                                     int mode, const T *u, T *r, int cur) {
+    constexpr int NL = Q * Q * Q;
+    __shared__ __align__(16) BatchDG<T> sd;
+    for (int k = blockIdx.x; k < nblocks; k += gridDim.x) {
+        if (k != (int)blockIdx.x) __syncthreads();
+        const BlockMap m = map[k];
+        load_batch_desc(D + m.inst, &sd);
+        residual_cells_body<T, Q, true>(sd.c, m.cell0, mode, u + sd.off * NL, nullptr, sd.kappa, nullptr, sd.tr[cur],
+                                        r ? r + sd.off * NL : nullptr, nullptr, k != (int)blockIdx.x);
+    }
+}
+
 template <int DIM, int Q, typename T>
 __global__ void __launch_bounds__(256) k_residual_batch(const BatchDG<T> *__restrict__ D,
                                                          const BlockMap *__restrict__ map, int nblocks, int cpb,
@@ -1081,6 +1096,23 @@ struct DGLaunch {
                                       const T *u, const T *b, T *r, int cur, cudaStream_t s) {
         if (nblocks <= 0) return cudaSuccess;
         if constexpr (CELLS_OK) {
+            if constexpr (sizeof(T) == 4) {
+                if (cpb <= 0 && (mode & RES_DIRECT)) {   // the FP32 CG operator: no b, no corners
+                    using CG = CellGeo<T, Q>;
+                    static bool attr = false;
+                    if (!attr) {
+                        cudaFuncSetAttribute(k_residual_cells_batch_direct<T, Q>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CG::BYTES);
+                        attr = true;
+                    }
+                    count_launches(1);
+                    k_residual_cells_batch_direct<T, Q>
+                        <<<persistent_grid((const void *)k_residual_cells_batch_direct<T, Q>, CG::W, CG::BYTES,
+                                           nblocks),
+                           CG::W, CG::BYTES, s>>>(D, map, nblocks, mode, u, r, cur);
+                    return cudaGetLastError();
+                }
+            }
             if (cpb <= 0) {          // the map holds 32-cell blocks; every problem carries its factors
                 using CG = CellGeo<T, Q>;
                 static bool attr = false;

@@ -230,7 +230,9 @@ template <typename T>
 cudaError_t launch_smooth(int dim, int q, const DGConst<T> &c, int cpb, int exact, T *u, const T *b,
                           const T *kappa, const T *fd, const T *linv, const T *tr_in, T *tr_out, cudaStream_t s);
 // mode bits for launch_residual
-enum { RES_HAS_B = 1, RES_WRITE_R = 2, RES_CORNERS = 4, RES_NEGATE = 8 };
+// RES_DIRECT (batched FP32 one-thread-per-cell residual): A_KK u in the direct
+// sum-factorised form instead of through the factors (the FP32 CG operator)
+enum { RES_HAS_B = 1, RES_WRITE_R = 2, RES_CORNERS = 4, RES_NEGATE = 8, RES_DIRECT = 16 };
 // fd: the level's fast-diagonalisation factors of the exact diagonal blocks, or
 // null; with them (3D, q small enough, cpb <= 0) the one-thread-per-cell kernel
 // runs, which forms A_KK u from the factors

@@ -147,11 +147,12 @@ enum {
 }  // namespace
 
 // y = A u in FP32 (warm-up projection + cell equation on the FP32 hierarchy).
-// The operator of the FP32 CG recurrences takes the direct sum-factorised
-// kernel: forming A_KK u through the eigenbasis of the fast-diagonalisation
-// factors (the one-thread-per-cell residual), in FP32, cost the 64^3 p = 4
-// lognormal solve five more iterations (42 instead of 37); the V-cycle's
-// residual, a preconditioner step, keeps the faster kernel.
+// The operator of the FP32 CG recurrences forms A_KK u in the direct
+// sum-factorised form (one thread per cell where that kernel applies, no
+// factors passed): forming it through the eigenbasis of the fast-diagonalisation
+// factors, in FP32, cost the 64^3 p = 4 lognormal solve five more iterations
+// (42 instead of 37); the V-cycle's residual, a preconditioner step, keeps the
+// eigenbasis kernel, which is faster.
 int apply32(dgmg_ctx &C, const float *u, float *y, cudaStream_t s) {
     DGDev<float> &D = C.d32;
     C.prof.begin(ST_PROJECT, s);
