@@ -36,6 +36,7 @@ struct Geo {
     static constexpr int FDSP = (FDS + VEC - 1) / VEC * VEC;   // per axis in shared memory (padded)
     static constexpr int QQV = (Q * Q + VEC - 1) / VEC;        // 16-byte vectors covering S
     static constexpr int NDOT = NFACE * 2 * (DIM == 3 ? Q : 1); // facet-mass dot products per cell
+    static constexpr int NLC = NFACE * 2 * Q;                  // lifting coefficients per cell
     // volume index of node i of the pencil along `dir` at tangential position t
     static __device__ __forceinline__ int vidx(int dir, int t, int i) {
         if (DIM == 2) return dir == 0 ? i + Q * t : t + Q * i;
@@ -204,10 +205,29 @@ __device__ __forceinline__ void stage_mass_rank1(const DGConst<T> &c, T *sW, T *
 // (the first / last unit vector for GLL nodes). For the low face (cell = K^+):
 //   N = kF [ e_0 (x) (H/2 - gamma G) - d_0 (x) G/2 ],
 // for the high face (cell = K^-):
-//   N = kF [ e_p (x) (-H/2 - gamma G) + d_p (x) G/2 ].
+//   N = kF [ e_p (x) (-H/2 - gamma G) + d_p (x) G/2 ],
+// so the pencil at a face node takes G cG - H cH with, per face,
+//   low:  cG = kF (d_0/2 + gamma e_0),   cH = kF e_0 / 2,
+//   high: cG = kF (gamma e_p - d_p/2),   cH = -kF e_p / 2,
+// formed once per cell (lift_coefficients: sC[face][cG | cH]).
+template <int DIM, int Q, typename T>
+__device__ __forceinline__ void lift_coefficients(const DGConst<T> &c, bool active, int t, const T *sKF, int mask,
+                                                  T *sC) {
+    using G = Geo<DIM, Q, T>;
+    if (!active) return;
+    for (int e = t; e < G::NFACE * Q; e += G::NF) {
+        const int f = e / Q, i = e - f * Q, dir = f >> 1, side = f & 1;
+        if (!(mask & (1 << f))) continue;
+        const T kF = sKF[f], h = T(0.5);
+        const T ev = c.gl ? (side ? c.vp[i] : c.v0[i]) : T(i == (side ? Q - 1 : 0) ? 1 : 0);
+        sC[f * 2 * Q + i] = side ? kF * (c.gamma[dir] * ev - h * c.dp[dir][i]) : kF * (h * c.d0[dir][i] + c.gamma[dir] * ev);
+        sC[f * 2 * Q + Q + i] = side ? -(kF * h * ev) : kF * h * ev;
+    }
+}
+
 template <int DIM, int Q, typename T>
 __device__ __forceinline__ void lift_neighbours(const DGConst<T> &c, bool active, int t, T *sR, const T *sF,
-                                                const T *sKF, int mask) {
+                                                const T *sC, int mask) {
     using G = Geo<DIM, Q, T>;
 #pragma unroll
     for (int dir = 0; dir < DIM; ++dir) {
@@ -215,35 +235,22 @@ __device__ __forceinline__ void lift_neighbours(const DGConst<T> &c, bool active
             T x[Q];
 #pragma unroll
             for (int i = 0; i < Q; ++i) x[i] = sR[G::vidx(dir, t, i)];
-            const T half = T(0.5);
-            const T kL = sKF[2 * dir], kR = sKF[2 * dir + 1];
-            if (mask & (1 << (2 * dir))) {
-                const T Gv = sF[((2 * dir) * 2 + 0) * G::NF + t];
-                const T Hv = sF[((2 * dir) * 2 + 1) * G::NF + t];
-                const T s0 = kL * (half * Hv - c.gamma[dir] * Gv);
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                const int f = 2 * dir + side;
+                if (!(mask & (1 << f))) continue;
+                const T Gv = sF[(f * 2 + 0) * G::NF + t];
+                const T Hv = sF[(f * 2 + 1) * G::NF + t];
+                const T *cf = sC + f * 2 * Q;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) x[i] += Gv * cf[i];
                 if (c.gl) {
 #pragma unroll
-                    for (int i = 0; i < Q; ++i) x[i] -= s0 * c.v0[i];
+                    for (int i = 0; i < Q; ++i) x[i] -= Hv * cf[Q + i];
                 } else {
-                    x[0] -= s0;
+                    const int end = side ? Q - 1 : 0;
+                    x[end] -= Hv * cf[Q + end];
                 }
-                const T a = kL * half * Gv;
-#pragma unroll
-                for (int i = 0; i < Q; ++i) x[i] += a * c.d0[dir][i];
-            }
-            if (mask & (1 << (2 * dir + 1))) {
-                const T Gv = sF[((2 * dir + 1) * 2 + 0) * G::NF + t];
-                const T Hv = sF[((2 * dir + 1) * 2 + 1) * G::NF + t];
-                const T sp = kR * (-half * Hv - c.gamma[dir] * Gv);
-                if (c.gl) {
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) x[i] -= sp * c.vp[i];
-                } else {
-                    x[Q - 1] -= sp;
-                }
-                const T a = kR * half * Gv;
-#pragma unroll
-                for (int i = 0; i < Q; ++i) x[i] -= a * c.dp[dir][i];
             }
 #pragma unroll
             for (int i = 0; i < Q; ++i) sR[G::vidx(dir, t, i)] = x[i];
@@ -517,7 +524,8 @@ __device__ __forceinline__ void k_smooth_body(const DGConst<T> &c, int64_t cell0
     T *sF = sR + cpb * G::NL;
     T *sK = sF + cpb * G::NFACE * 2 * G::NF;   // [cpb][NFACE + 1]
     T *sDot = sK + cpb * (G::NFACE + 1);       // [cpb][facet-mass dot products]
-    T *sA = sDot + cpb * G::NDOT;              // inexact block only: [cpb][NL] x 2, [cpb][DIM*Q*Q]
+    T *sC = sDot + cpb * G::NDOT;              // [cpb][lifting coefficients]
+    T *sA = sC + cpb * G::NLC;                 // inexact block only: [cpb][NL] x 2, [cpb][DIM*Q*Q]
     T *sB = sA + cpb * G::NL;
     T *sKT = sB + cpb * G::NL;
     const int lc = threadIdx.x / G::NF, t = threadIdx.x - lc * G::NF;
@@ -544,8 +552,9 @@ __device__ __forceinline__ void k_smooth_body(const DGConst<T> &c, int64_t cell0
     T *myU = sU + lc * G::NL;
     const int mask = active ? interior_mask<DIM>(ci, c.n) : 0;
     if (!exact) build_block_1d<DIM, Q, T>(c, sT, active, t, myK, mask, sKT + lc * DIM * Q * Q);
+    lift_coefficients<DIM, Q, T>(c, active, t, myK, mask, sC + lc * G::NLC);   // read after facet_mass's barriers
     facet_mass<DIM, Q, T>(sMw, sMu, active, t, myF, sDot + lc * G::NDOT, mask);
-    lift_neighbours<DIM, Q, T>(c, active, t, myR, myF, myK, mask);
+    lift_neighbours<DIM, Q, T>(c, active, t, myR, myF, sC + lc * G::NLC, mask);
     if (!exact)
         subtract_block_apply<DIM, Q, T>(c, active, t, myU, myR, sA + lc * G::NL, sB + lc * G::NL,
                                         sKT + lc * DIM * Q * Q, sMw, sMu);
@@ -688,6 +697,7 @@ __device__ __forceinline__ void k_residual_body(const DGConst<T> &c, int64_t cel
     T *sKT = sF + cpb * G::NFACE * 2 * G::NF;   // [cpb][DIM][Q*Q]
     T *sK = sKT + cpb * DIM * Q * Q;            // [cpb][NFACE + 1]
     T *sDot = sK + cpb * (G::NFACE + 1);        // [cpb][facet-mass dot products]
+    T *sC = sDot + cpb * G::NDOT;               // [cpb][lifting coefficients]
     const int lc = threadIdx.x / G::NF, t = threadIdx.x - lc * G::NF;
     const int ncl = (int)min((int64_t)cpb, c.ncell - cell0);
     const bool active = lc < ncl;
@@ -713,10 +723,11 @@ __device__ __forceinline__ void k_residual_body(const DGConst<T> &c, int64_t cel
     T *myKT = sKT + lc * DIM * Q * Q;
     const int mask = active ? interior_mask<DIM>(ci, c.n) : 0;
     build_block_1d<DIM, Q, T>(c, sT, active, t, myK, mask, myKT);
+    lift_coefficients<DIM, Q, T>(c, active, t, myK, mask, sC + lc * G::NLC);   // read after facet_mass's barriers
     facet_mass<DIM, Q, T>(sMw, sMu, active, t, myF, sDot + lc * G::NDOT, mask);   // contains barriers
     T *myR = sR + lc * G::NL;
     T *myU = sU + lc * G::NL;
-    lift_neighbours<DIM, Q, T>(c, active, t, myR, myF, myK, mask);
+    lift_neighbours<DIM, Q, T>(c, active, t, myR, myF, sC + lc * G::NLC, mask);
     subtract_block_apply<DIM, Q, T>(c, active, t, myU, myR, sA + lc * G::NL, myU, myKT, sMw, sMu);
     T rr[Q];
     if (active) {
@@ -906,14 +917,15 @@ template <int DIM, int Q, typename T>
 constexpr size_t smem_smooth(int cpb, bool exact) {
     using G = Geo<DIM, Q, T>;
     return (size_t)cpb *
-           (DIM * G::FDSP + 2 * G::NL + G::NFACE * 2 * G::NF + G::NFACE + 1 + G::NDOT +
+           (DIM * G::FDSP + 2 * G::NL + G::NFACE * 2 * G::NF + G::NFACE + 1 + G::NDOT + G::NLC +
             (exact ? 0 : 2 * G::NL + DIM * Q * Q)) *
            sizeof(T);
 }
 template <int DIM, int Q, typename T>
 constexpr size_t smem_residual(int cpb) {
     using G = Geo<DIM, Q, T>;
-    return (size_t)cpb * (3 * G::NL + G::NFACE * 2 * G::NF + DIM * Q * Q + G::NFACE + 1 + G::NDOT) * sizeof(T);
+    return (size_t)cpb * (3 * G::NL + G::NFACE * 2 * G::NF + DIM * Q * Q + G::NFACE + 1 + G::NDOT + G::NLC) *
+           sizeof(T);
 }
 
 template <int DIM, int Q, typename T>
