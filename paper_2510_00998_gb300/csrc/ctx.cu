@@ -935,6 +935,10 @@ static int tune_tiles(dgmg_ctx &C, T *u, T *b, int *tile, bool trace, bool smoot
     std::vector<int> cand;
     for (int c = 1; c <= 64; c *= 2)
         if (c * nf >= 32 && c * nf <= 256) cand.push_back(c);
+    // and the most cells whose pencils fit 256 threads (q = 5: 10 cells, 250
+    // threads, the last warp nearly full; FP64 work of idle lanes is lost)
+    if (nf <= 256 && 256 / nf * nf >= 32 && std::find(cand.begin(), cand.end(), 256 / nf) == cand.end())
+        cand.push_back(256 / nf);
     if (cand.empty()) cand.push_back(C.cpb);
     DG_CUDA(cudaMemsetAsync(u, 0, sizeof(T) * C.ndof, s));
     DG_CUDA(cudaMemsetAsync(b, 0, sizeof(T) * C.ndof, s));
@@ -1140,8 +1144,7 @@ int create_ctx(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_opt
     C->ndof = C->ncell * C->nloc;
     C->opts = o;
     const int nf = (int)(C->nloc / C->q);
-    C->cpb = std::max(1, 128 / nf);
-    while (C->cpb * nf > 256) --C->cpb;
+    C->cpb = std::max(1, 256 / nf);   // per-pencil tile: as many cells as fit 256 threads
     for (int k = 0; k < 2; ++k)
         for (int st = 0; st < 3; ++st) C->tile[k][st] = C->cpb;
     C->tile[0][TILE_SMOOTH] = 0;   // the one-thread-per-cell smoother and residual where they apply

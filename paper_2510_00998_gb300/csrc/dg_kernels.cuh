@@ -123,15 +123,22 @@ __device__ __forceinline__ void load_neighbour_traces(const DGConst<T> &c, int64
             const T *src = tr + nb * G::TR + (f ^ 1) * G::FS;
             g = src[t];
             h = src[G::NF + t];
-            if (t == 0) {
-                const T kN = kappa[nb];
-                sKF[f] = T(2) * kK * kN / (kK + kN);
-            }
-        } else if (t == 0) {
-            sKF[f] = T(0);
         }
         sF[(f * 2 + 0) * G::NF + t] = g;
         sF[(f * 2 + 1) * G::NF + t] = h;
+    }
+    // the facet coefficients, one face per thread (a division each: spread over
+    // the cell's threads rather than all in thread 0, whose warp would issue
+    // them with one lane active)
+    for (int f = t; f < G::NFACE; f += G::NF) {
+        const int dir = f >> 1, side = f & 1;
+        const int cn = ci[dir] + (side ? 1 : -1);
+        T kf = T(0);
+        if (cn >= 0 && cn < c.n[dir]) {
+            const T kN = kappa[cell + (side ? axis_stride<DIM>(c.n, dir) : -axis_stride<DIM>(c.n, dir))];
+            kf = T(2) * kK * kN / (kK + kN);
+        }
+        sKF[f] = kf;
     }
     if (t == 0) *sKappa = kK;
 }
@@ -931,12 +938,10 @@ constexpr size_t smem_residual(int cpb) {
 template <int DIM, int Q, typename T>
 struct DGLaunch {
     using G = Geo<DIM, Q, T>;
-    // cells per CTA when the caller leaves the choice (cpb <= 0): about 128 threads
-    static int default_cpb() {
-        int c = std::max(1, 128 / G::NF);
-        while (c > 1 && c * G::NF > 256) --c;
-        return c;
-    }
+    // cells per CTA when the caller leaves the choice (cpb <= 0): as many as fit
+    // 256 threads (q = 5: 10 cells, 250 threads), so the last warp is nearly
+    // full (FP64 work of idle lanes is lost)
+    static int default_cpb() { return std::max(1, 256 / G::NF); }
     static cudaError_t project(const DGConst<T> &c, int cpb, T *u, const T *e0, T *tr, cudaStream_t s) {
         if constexpr (CELLS_OK) if (c.ncell < (int64_t(1) << 31)) {   // 32-bit cell indices
             // bulk copies want a 16-byte aligned u; the trace pieces 8- (FP32) or 16-byte (FP64) aligned traces
