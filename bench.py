@@ -39,8 +39,8 @@ FP64_NOMINAL_TFLOPS = 1.25       # nominal GB300 dense FP64, context beside the 
 # DRAM bytes (read + write) of one launch of the FP64 smoothing kernel on this
 # workload from one ncu capture, valid only for the kernel sources it was taken
 # on (SHA-256 of the files below); once they change, `traffic` reads null
-SMOOTH_TRAFFIC = {"kernel": "k_smooth_cells<double,4>", "bytes": 115_428_096 + 11_230_976,
-                  "sources_sha256": "f47cea1978ea377a215a67a0db2e49ade5e92235bd1dfe697c733fad50be3446",
+SMOOTH_TRAFFIC = {"kernel": "k_smooth_cells<double,4>", "bytes": 115_310_592 + 10_941_440,
+                  "sources_sha256": "f75a5166e1094d61b428fdf002d3c7904b389dd664949ce1fa24fb8b2b25865e",
                   "files": ("smooth_cells.cuh", "dg_kernels.cuh", "dg_fp64.cu")}
 
 
