@@ -435,12 +435,20 @@ int recompute_factors(dgmg_ctx &C, const DGSpace &S, DGDev<T> &D, cudaStream_t s
 // inverse eigenvalue sums, traces and corner sums.
 template <typename T>
 int setup_dg(dgmg_ctx &C, const DGSpace &S, DGDev<T> &D, const std::vector<double> &kappa, bool smoother = true,
-             const T *shared_kappa = nullptr, const double *fd64 = nullptr) {
+             const T *shared_kappa = nullptr, const double *fd64 = nullptr, const T *shared_kfac = nullptr) {
     fill_const(C, S, D.c);
     if (shared_kappa)
         D.kappa = const_cast<T *>(shared_kappa);
     else
         RC(C.upload(&D.kappa, convert<T>(kappa)));
+    // facet coefficients (from the FP64 kappa of the finest level, uploaded first)
+    if (shared_kfac) {
+        D.kfac = const_cast<T *>(shared_kfac);
+    } else {
+        RC(C.alloc(&D.kfac, C.ncell * 2 * C.dim));
+        LC(launch_facet_coefficients<T>(C.dim, C.n, C.ncell, C.d64.kappa, D.kfac, C.setup_stream));
+    }
+    D.c.kfac = D.kfac;
     const int64_t trn = C.ncell * 2 * C.dim * trace_face_stride<T>((int)(S.nloc / S.q));
     if (!smoother) {                  // operator only (projection, residual): no block-inverse factors
         RC(C.alloc(&D.tr[0], trn));
@@ -488,9 +496,9 @@ int setup_dg_levels(dgmg_ctx &C, const std::vector<double> &kap) {
             lagrange_at(S.re.nodes, F.re.nodes[i], val.data(), nullptr);
             for (int j = 0; j < S.q; ++j) I[(size_t)i * S.q + j] = val[j];
         }
-        auto level = [&](auto &lv, auto *kappa_dev, const double *fd64) -> int {
+        auto level = [&](auto &lv, auto *kappa_dev, const double *fd64, decltype(kappa_dev) kfac_dev) -> int {
             using T = typename std::remove_pointer<decltype(kappa_dev)>::type;
-            RC(setup_dg<T>(C, S, lv.D, kap, true, kappa_dev, fd64));
+            RC(setup_dg<T>(C, S, lv.D, kap, true, kappa_dev, fd64, kfac_dev));
             RC(C.alloc(&lv.z, S.ndof));
             RC(C.alloc(&lv.b, S.ndof));
             RC(C.alloc(&lv.r, S.ndof));
@@ -498,8 +506,8 @@ int setup_dg_levels(dgmg_ctx &C, const std::vector<double> &kap) {
             for (size_t k = 0; k < I.size(); ++k) lv.P.I[k] = (T)I[k];
             return DGMG_OK;
         };
-        RC(level(C.lvl64[l], C.d64.kappa, nullptr));
-        if (mixed) RC(level(C.lvl32[l], C.d32.kappa, C.lvl64[l].D.fd));
+        RC(level(C.lvl64[l], C.d64.kappa, nullptr, C.d64.kfac));
+        if (mixed) RC(level(C.lvl32[l], C.d32.kappa, C.lvl64[l].D.fd, C.d32.kfac));
     }
     RC(C.alloc(&C.res64, C.ndof));
     if (mixed) RC(C.alloc(&C.res32, C.ndof));
@@ -1314,6 +1322,9 @@ int dgmg_update_kappa(dgmg_ctx *C, const double *kappa) {
     if (mixed)
         DG_CUDA(cudaMemcpyAsync(C->d32.kappa, kap32.data(), sizeof(float) * C->ncell, cudaMemcpyHostToDevice, s));
     DG_CUDA(cudaMemcpyAsync(C->coarse_inv, inv.data(), sizeof(double) * inv.size(), cudaMemcpyHostToDevice, s));
+    // facet coefficients (the lower DG levels share the finest level's)
+    LC(launch_facet_coefficients<double>(C->dim, C->n, C->ncell, C->d64.kappa, C->d64.kfac, s));
+    if (mixed) LC(launch_facet_coefficients<float>(C->dim, C->n, C->ncell, C->d64.kappa, C->d32.kfac, s));
     std::vector<std::vector<float>> st32(C->lv.size());
     for (size_t l = 0; l < C->lv.size(); ++l) {
         const std::vector<double> &st = C->lv[l].st;
@@ -1514,8 +1525,10 @@ int dgmg_estimate_bytes(const dgmg_mesh *mesh, int p, const dgmg_opts *opts, siz
     const int64_t tr32 = ncell * 2 * dim * trace_face_stride<float>((int)nf);
     auto sz = [](int64_t count, size_t elem) { return (size_t)std::max<int64_t>(count, 1) * elem; };
     size_t dg64 = sz(ncell, 8) + 2 * sz(ncell * dim * (q * q + q), 8) + sz(ndof, 8) + 2 * sz(tr, 8) +
-                  sz(ncell << dim, 8);   // kappa, factors and residual factors, table, traces, corners
-    size_t dg32 = sz(ncell, 4) + 2 * sz(ncell * dim * (q * q + q), 4) + 2 * sz(tr32, 4) + sz(ncell << dim, 4);
+                  sz(ncell << dim, 8) + sz(ncell * 2 * dim, 8);   // kappa, factors and residual factors,
+                                                                  // table, traces, corners, facet coefficients
+    size_t dg32 = sz(ncell, 4) + 2 * sz(ncell * dim * (q * q + q), 4) + 2 * sz(tr32, 4) + sz(ncell << dim, 4) +
+                  sz(ncell * 2 * dim, 4);
     size_t cg64 = 0, cg32 = 0;
     int cur[3] = {n[0], n[1], n[2]};
     int64_t nv = 1;

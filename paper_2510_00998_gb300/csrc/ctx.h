@@ -37,6 +37,7 @@ struct DGDev {
     T *kappa = nullptr, *fd = nullptr, *tr[2] = {nullptr, nullptr}, *corners = nullptr;
     T *linv = nullptr;   // per-node omega / (sum of the cell's eigenvalues); FP64 only
     T *fdr = nullptr;    // the residual's factors [S^T M | lambda] per cell and axis
+    T *kfac = nullptr;   // facet coefficients [cell][face]
 };
 
 template <typename T>

@@ -127,19 +127,8 @@ __device__ __forceinline__ void load_neighbour_traces(const DGConst<T> &c, int64
         sF[(f * 2 + 0) * G::NF + t] = g;
         sF[(f * 2 + 1) * G::NF + t] = h;
     }
-    // the facet coefficients, one face per thread (a division each: spread over
-    // the cell's threads rather than all in thread 0, whose warp would issue
-    // them with one lane active)
-    for (int f = t; f < G::NFACE; f += G::NF) {
-        const int dir = f >> 1, side = f & 1;
-        const int cn = ci[dir] + (side ? 1 : -1);
-        T kf = T(0);
-        if (cn >= 0 && cn < c.n[dir]) {
-            const T kN = kappa[cell + (side ? axis_stride<DIM>(c.n, dir) : -axis_stride<DIM>(c.n, dir))];
-            kf = T(2) * kK * kN / (kK + kN);
-        }
-        sKF[f] = kf;
-    }
+    // the facet coefficients (formed at set-up: the harmonic means of kappa)
+    for (int f = t; f < G::NFACE; f += G::NF) sKF[f] = c.kfac[cell * G::NFACE + f];
     if (t == 0) *sKappa = kK;
 }
 

@@ -141,7 +141,42 @@ __global__ void k_inverse_eigen_sums(int dim, int q, int64_t ncell, const double
     linv[idx] = omega / s;
 }
 
+// kfac[cell][f]: the harmonic mean of kappa across face f (0 on the boundary)
+template <typename T>
+__global__ void k_facet_coefficients(int dim, int n0, int n1, int n2, int64_t ncell, const double *__restrict__ kappa,
+                                     T *__restrict__ kfac) {
+    const int nface = 2 * dim;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= ncell * nface) return;
+    const int64_t cell = idx / nface;
+    const int f = (int)(idx - cell * nface), a = f >> 1, side = f & 1;
+    const int64_t s1 = n0, s2 = (int64_t)n0 * n1;
+    const int ci[3] = {(int)(cell % n0), (int)((cell / s1) % n1), (int)(cell / s2)};
+    const int na = a == 0 ? n0 : (a == 1 ? n1 : n2);
+    const int cn = ci[a] + (side ? 1 : -1);
+    double v = 0.0;
+    if (cn >= 0 && cn < na) {
+        const int64_t st = a == 0 ? 1 : (a == 1 ? s1 : s2);
+        const double kK = kappa[cell], kN = kappa[cell + (side ? st : -st)];
+        v = 2.0 * kK * kN / (kK + kN);
+    }
+    kfac[idx] = (T)v;
+}
+
 }  // namespace
+
+template <typename T>
+cudaError_t launch_facet_coefficients(int dim, const int *n, int64_t ncell, const double *kappa, T *kfac,
+                                      cudaStream_t s) {
+    const int64_t m = ncell * 2 * dim;
+    if (m == 0) return cudaSuccess;
+    count_launches(1);
+    k_facet_coefficients<T><<<(unsigned)((m + 255) / 256), 256, 0, s>>>(dim, n[0], n[1], dim == 3 ? n[2] : 1, ncell,
+                                                                        kappa, kfac);
+    return cudaGetLastError();
+}
+template cudaError_t launch_facet_coefficients<double>(int, const int *, int64_t, const double *, double *, cudaStream_t);
+template cudaError_t launch_facet_coefficients<float>(int, const int *, int64_t, const double *, float *, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_fd_factors(const FDInput &in, const double *kappa, int64_t ncell, T *fd, cudaStream_t s) {

@@ -90,6 +90,11 @@ struct MassTables {
 template <typename TI, typename TO>
 cudaError_t launch_residual_factors(int dim, int q, int64_t ncell, const TI *fd, const MassTables &m, TO *fdr,
                                     cudaStream_t s);
+// kfac[cell][2 axis + side] = 2 kappa_K kappa_N / (kappa_K + kappa_N) across each
+// interior face (0 on the boundary), from the FP64 kappa
+template <typename T>
+cudaError_t launch_facet_coefficients(int dim, const int *n, int64_t ncell, const double *kappa, T *kfac,
+                                      cudaStream_t s);
 // linv[cell][node] = omega / (sum of the cell's eigenvalues at the node): the
 // smoother's damping folded into the table
 cudaError_t launch_inverse_eigen_sums(int dim, int q, int64_t ncell, const double *fd, double omega,
@@ -119,6 +124,10 @@ struct DGConst {
     // is a multiple of the product of their leading coefficients); with GL nodes
     // the mass is diagonal and mu = 0
     T mw[3][QMAX], mu[3][QMAX];
+    // facet coefficients kfac[cell][face = 2 axis + side]: the harmonic mean of
+    // the cell's and the neighbour's kappa on an interior face, 0 on a boundary
+    // face (formed once per level, updated with kappa)
+    const T *kfac;
 };
 
 // Q1 level description for the CG kernels.

@@ -167,14 +167,6 @@ __device__ __forceinline__ int cell_neighbour(int f, int mask, int64_t cell, int
     return (int)cell + ((f & 1) ? s : -s);
 }
 
-// Facet coefficient of a face: the harmonic mean of kappa with the neighbour
-// nb, 0 without one (the face then has no neighbour term).
-template <typename T>
-__device__ __forceinline__ T facet_kappa(int nb, T kK, const T *__restrict__ kappa) {
-    if (nb < 0) return T(0);
-    const T kN = kappa[nb];
-    return T(2) * kK * kN / (kK + kN);
-}
 
 // Stage face f of the lane's neighbour nb (the neighbour's face f^1) into the
 // lane's part of a face slot: one bulk copy per lane that has a neighbour, all
@@ -593,7 +585,6 @@ __device__ __forceinline__ void smooth_cells_body(const DGConst<T> &c, int64_t c
     }
     const int s1 = c.n[0], s2 = c.n[0] * c.n[1];
     if (!G::LEAN) stage_face<T, Q>(0, cell_neighbour(0, mask, cell, s1, s2), lane, tr_in, sB, &bars[4]);
-    const T kK = active ? kappa[cell] : T(1);
 
     // r = b
     if (full)
@@ -622,7 +613,7 @@ __device__ __forceinline__ void smooth_cells_body(const DGConst<T> &c, int64_t c
         for (int side = 0; side < 2; ++side) {
             const int f = 2 * p + side;
             const int nb = cell_neighbour(f, mask, cell, s1, s2);
-            const T kF = facet_kappa<T>(nb, kK, kappa);
+            const T kF = nb >= 0 ? c.kfac[cell * 6 + f] : T(0);
             T *slot = side ? sA : sB;
             if (!G::LEAN) ok = warp_wait_phase(&bars[4 + side], (unsigned)(p & 1), lane) && ok;
             if (active && nb >= 0) {
@@ -997,7 +988,7 @@ __device__ __forceinline__ void residual_cells_body(const DGConst<T> &c, int64_t
         if (active) {
             T kF[6];
 #pragma unroll
-            for (int f = 0; f < 6; ++f) kF[f] = facet_kappa<T>(cell_neighbour(f, mask, cell, s1, s2), kK, kappa);
+            for (int f = 0; f < 6; ++f) kF[f] = c.kfac[cell * 6 + f];
             direct_volume<T, Q>(c, kK, kF, mask, sA + lane * NL, R);
             const T *bb = has_b ? b + cell * NL : nullptr;
 #pragma unroll
@@ -1081,7 +1072,7 @@ __device__ __forceinline__ void residual_cells_body(const DGConst<T> &c, int64_t
         for (int side = 0; side < 2; ++side) {
             const int f = 2 * p + side;
             const int nb = cell_neighbour(f, mask, cell, s1, s2);
-            const T kF = facet_kappa<T>(nb, kK, kappa);
+            const T kF = nb >= 0 ? c.kfac[cell * 6 + f] : T(0);
             T *slot = side ? sA : sB;
             if (!G::LEAN) ok = warp_wait_phase(&bars[4 + side], (unsigned)(p & 1), lane) && ok;
             if (active && nb >= 0) {
