@@ -975,18 +975,22 @@ static int tune_tiles(dgmg_ctx &C, T *u, T *b, int *tile, bool trace, bool smoot
         return ms;
     };
     const char *tname = sizeof(T) == 8 ? "fp64" : "fp32";
+    // the fastest candidate; the one-thread-per-cell kernel (tile 0) is kept
+    // unless another tile is more than 3% faster, so that a near tie in the
+    // three-launch timing does not flip the choice from run to run
     auto pick = [&](const char *stage, std::vector<int> cs, auto launch_with) {
         int best = cs[0];
-        float best_ms = INF;
+        float best_ms = INF, ms0 = INF;
         for (int c : cs) {
             const float ms = time_it([&] { return launch_with(c); });
             if (trace) std::fprintf(stderr, "dgmg autotune %s %-9s tile %2d: %8.4f ms\n", tname, stage, c, ms / 3);
+            if (c == 0) ms0 = ms;
             if (ms < best_ms) {
                 best_ms = ms;
                 best = c;
             }
         }
-        return best;
+        return ms0 < INF && ms0 <= 1.03f * best_ms ? 0 : best;
     };
     std::vector<int> cp = cand;
     if (C.dim == 3 && C.q <= (std::is_same<T, float>::value ? 5 : 4) && C.opts.basis == DGMG_BASIS_GLL)
