@@ -1002,65 +1002,65 @@ __device__ __forceinline__ void residual_cells_body(const DGConst<T> &c, int64_t
         stage_face<T, Q>(1, cell_neighbour(1, mask, cell, s1, s2), lane, tr, sA, &bars[5]);
     } else {
 #pragma unroll
-    for (int e = 0; e < NL; ++e) R[e] = active ? sA[lane * NL + e] : T(0);
-    fence_proxy_async_smem();
-    __syncwarp();
-    // area A: the factors (FP64) or b (FP32)
-    if (G::LEAN)
-        stage_bulk<T>(full, lane, &bars[1], sA, fd + cell0 * 3 * FDS, W * 3 * FDS, ncl * 3 * FDS);
-    else if (has_b)
-        stage_bulk<T>(full, lane, &bars[1], sA, b + cell0 * NL, W * NL, ncl * NL);
-    const bool b_staged = !G::LEAN && has_b;
-
-    // R = A_KK u: P along x, y, z; times the eigenvalue sums; P^T along x, y, z
-    // (the tensor-product factors commute: one loop body for all six passes)
-    if (full)
-        ok = warp_wait_copies(&bars[G::LEAN ? 1 : 2], lane) && ok;
-    else
-        __syncwarp();
-    const T *myFD = (G::LEAN ? sA : sB) + lane * 3 * FDS;
-#pragma unroll 1
-    for (int k = 0; k < 6 && active; ++k) {
-        if (k == 3) {
-#pragma unroll
-            for (int kz = 0; kz < Q; ++kz) {
-                const T lz = myFD[2 * FDS + Q * Q + kz];
-#pragma unroll
-                for (int j = 0; j < Q; ++j) {
-                    const T lyz = myFD[1 * FDS + Q * Q + j] + lz;
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) R[i + Q * (j + Q * kz)] *= myFD[Q * Q + i] + lyz;
-                }
-            }
-        }
-        T P[Q * Q];
-        const int ax = k < 3 ? k : k - 3;
-        if (k < 3)
-            load_matrix<T, Q, false>(myFD + ax * FDS, P);   // P_a = S_a^T M_a, precomputed per cell
-        else
-            load_matrix<T, Q, true>(myFD + ax * FDS, P);    // its transpose M_a S_a
-        pass_x<T, Q>(P, R);
-        rotate<T, Q>(R);
-    }
-    // R = b - A_KK u
-    if (b_staged && full)
-        ok = warp_wait_copies(&bars[1], lane) && ok;
-    else
-        __syncwarp();
-    if (active) {
-        const T *bb = has_b ? (G::LEAN ? b + cell * NL : sA + lane * NL) : nullptr;
-#pragma unroll
-        for (int e = 0; e < NL; ++e) R[e] = (bb ? bb[e] : T(0)) - R[e];
-    }
-    // FP32: the neighbour faces into the slots (every lane is done with the
-    // factors in area B and with b in area A)
-    if (!G::LEAN) {
+        for (int e = 0; e < NL; ++e) R[e] = active ? sA[lane * NL + e] : T(0);
         fence_proxy_async_smem();
         __syncwarp();
-        stage_face<T, Q>(0, cell_neighbour(0, mask, cell, s1, s2), lane, tr, sB, &bars[4]);
-        stage_face<T, Q>(1, cell_neighbour(1, mask, cell, s1, s2), lane, tr, sA, &bars[5]);
+        // area A: the factors (FP64) or b (FP32)
+        if (G::LEAN)
+            stage_bulk<T>(full, lane, &bars[1], sA, fd + cell0 * 3 * FDS, W * 3 * FDS, ncl * 3 * FDS);
+        else if (has_b)
+            stage_bulk<T>(full, lane, &bars[1], sA, b + cell0 * NL, W * NL, ncl * NL);
+        const bool b_staged = !G::LEAN && has_b;
+
+        // R = A_KK u: P along x, y, z; times the eigenvalue sums; P^T along x, y, z
+        // (the tensor-product factors commute: one loop body for all six passes)
+        if (full)
+            ok = warp_wait_copies(&bars[G::LEAN ? 1 : 2], lane) && ok;
+        else
+            __syncwarp();
+        const T *myFD = (G::LEAN ? sA : sB) + lane * 3 * FDS;
+#pragma unroll 1
+        for (int k = 0; k < 6 && active; ++k) {
+            if (k == 3) {
+#pragma unroll
+                for (int kz = 0; kz < Q; ++kz) {
+                    const T lz = myFD[2 * FDS + Q * Q + kz];
+#pragma unroll
+                    for (int j = 0; j < Q; ++j) {
+                        const T lyz = myFD[1 * FDS + Q * Q + j] + lz;
+#pragma unroll
+                        for (int i = 0; i < Q; ++i) R[i + Q * (j + Q * kz)] *= myFD[Q * Q + i] + lyz;
+                    }
+                }
+            }
+            T P[Q * Q];
+            const int ax = k < 3 ? k : k - 3;
+            if (k < 3)
+                load_matrix<T, Q, false>(myFD + ax * FDS, P);   // P_a = S_a^T M_a, precomputed per cell
+            else
+                load_matrix<T, Q, true>(myFD + ax * FDS, P);    // its transpose M_a S_a
+            pass_x<T, Q>(P, R);
+            rotate<T, Q>(R);
+        }
+        // R = b - A_KK u
+        if (b_staged && full)
+            ok = warp_wait_copies(&bars[1], lane) && ok;
+        else
+            __syncwarp();
+        if (active) {
+            const T *bb = has_b ? (G::LEAN ? b + cell * NL : sA + lane * NL) : nullptr;
+#pragma unroll
+            for (int e = 0; e < NL; ++e) R[e] = (bb ? bb[e] : T(0)) - R[e];
+        }
+        // FP32: the neighbour faces into the slots (every lane is done with the
+        // factors in area B and with b in area A)
+        if (!G::LEAN) {
+            fence_proxy_async_smem();
+            __syncwarp();
+            stage_face<T, Q>(0, cell_neighbour(0, mask, cell, s1, s2), lane, tr, sB, &bars[4]);
+            stage_face<T, Q>(1, cell_neighbour(1, mask, cell, s1, s2), lane, tr, sA, &bars[5]);
+        }
     }
-    }   // !DIRECT
     // R -= N u_nb, face pair by face pair as in the smoothing step
 #pragma unroll 1
     for (int p = 0; p < 3; ++p) {
