@@ -366,7 +366,7 @@ __device__ __forceinline__ const T *q1_up(const Q1Plan<T> &p, int l, const T *ec
 // coarsest solve run in block 0 alone, separated by block barriers; the larger
 // levels use the whole grid.
 template <int DIM, typename T>
-__global__ void __launch_bounds__(Q1_TPB) k_q1_cycle(const Q1Plan<T> *__restrict__ P, unsigned long long *bar) {
+__global__ void __launch_bounds__(q1_tpb<T>()) k_q1_cycle(const Q1Plan<T> *__restrict__ P, unsigned long long *bar) {
     if (*(volatile unsigned long long *)&g_q1_barrier_timeouts != 0) return;
     const Q1Plan<T> &p = *P;
     const int nl = p.nlev, ls = p.local_from;
@@ -474,7 +474,7 @@ template <typename T>
 cudaError_t launch_q1_cycle(int dim, const Q1Plan<T> *plan, unsigned long long *bar, int blocks, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(blocks);
-    cfg.blockDim = dim3(Q1_TPB);
+    cfg.blockDim = dim3(q1_tpb<T>());
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;   // all blocks co-resident: the grid barrier cannot wait on an unscheduled block
@@ -493,7 +493,7 @@ int q1_cycle_max_blocks(int dim) {
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
     int coop = 0;
     if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, q1_cycle_fn<T>(dim), Q1_TPB, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, q1_cycle_fn<T>(dim), q1_tpb<T>(), 0) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }

@@ -693,15 +693,16 @@ int q1_cycle(dgmg_ctx &C, cudaStream_t s, T **result) {
     Q1Plan<T> *plan = q1plan<T>(C);
     if (!plan || C.q1_blocks <= 0 || g_q1_one_launch_off.load(std::memory_order_relaxed))
         return cg_vcycle<T>(C, 0, s, result);
-    unsigned long long *bar = C.q1bar + (std::is_same<T, float>::value ? 1 : 0);
-    LC(launch_q1_cycle<T>(C.dim, plan, bar, C.q1_blocks, s));
+    const int pi = std::is_same<T, float>::value ? 1 : 0;
+    LC(launch_q1_cycle<T>(C.dim, plan, C.q1bar + pi, C.q1_blocks_t[pi], s));
     *result = lv.size() == 1 ? lv[0].u[0] : lv[0].u[(C.opts.nu_pre + C.opts.nu_post) & 1];
     return DGMG_OK;
 }
 
-// Blocks of the cooperative Q1 cycle: as many as the kernels of both
-// precisions in use keep co-resident (every launch on a plan's arrival counter
-// has the same block count); 0 where the launch is not possible.
+// The cooperative Q1 cycle is used when the kernels of both precisions in use
+// can be launched co-resident (> 0); each precision launches as many blocks as
+// its kernel keeps co-resident (q1_blocks_t; every launch on a plan's arrival
+// counter has the same block count); 0 where the launch is not possible.
 static int q1_blocks_for(int dim, bool mixed) {
     int qb = q1_cycle_max_blocks<double>(dim);
     if (mixed) qb = std::min(qb, q1_cycle_max_blocks<float>(dim));
@@ -750,7 +751,8 @@ int setup_q1_plan(dgmg_ctx &C) {
         cudaGraphExec_t exec = nullptr;
         bool ok = cudaStreamBeginCapture(C.capture_stream, cudaStreamCaptureModeRelaxed) == cudaSuccess;
         if (ok) {
-            const cudaError_t el = launch_q1_cycle<T>(C.dim, d, C.q1bar, C.q1_blocks, C.capture_stream);
+            const int pi = std::is_same<T, float>::value ? 1 : 0;
+            const cudaError_t el = launch_q1_cycle<T>(C.dim, d, C.q1bar + pi, C.q1_blocks_t[pi], C.capture_stream);
             g_kernel_launches.fetch_sub(1);   // captured, not launched
             const cudaError_t ee = cudaStreamEndCapture(C.capture_stream, &graph);
             ok = el == cudaSuccess && ee == cudaSuccess && graph &&
@@ -1191,6 +1193,8 @@ int create_ctx(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_opt
     trace.mark("dg fp64 (factors on the device)");
     if (!(flags & CREATE_NO_SOLVER)) {   // a batch member runs its Q1 levels in the batch's kernels
         C->q1_blocks = q1_blocks_for(C->dim, o.precision == DGMG_MIXED_FP32);
+        C->q1_blocks_t[0] = q1_cycle_max_blocks<double>(C->dim);
+        C->q1_blocks_t[1] = o.precision == DGMG_MIXED_FP32 ? q1_cycle_max_blocks<float>(C->dim) : 0;
     }
     if (!(flags & CREATE_NO_FP64_Q1)) {
         RC(setup_cg<double>(*C, C->cg64));

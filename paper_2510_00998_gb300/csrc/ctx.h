@@ -147,6 +147,7 @@ struct dgmg_ctx {
     Q1Plan<float> *q1plan32 = nullptr;
     unsigned long long *q1bar = nullptr;          // arrival counters [FP64, FP32]
     int q1_blocks = 0;
+    int q1_blocks_t[2] = {0, 0};                   // blocks of the cycle per precision [FP64, FP32]
     DGDev<double> d64;
     DGDev<float> d32;
     std::vector<CGDev<double>> cg64;

@@ -192,7 +192,11 @@ struct BatchCG {
 // The Q1 h-cycle of one problem as one cooperative launch: every level's
 // operator and transfer tables, its vectors, the coarsest inverse.
 constexpr int Q1_MAXLEV = 24;
-constexpr int Q1_TPB = 256;
+// threads per block of the cooperative cycle: FP32 512 (one block per SM, more
+// loads of the vertex loops in flight, fewer barrier arrivals, and 512 threads
+// for the levels run in block 0), FP64 256 (two per SM; 512 spill in FP64)
+template <typename T>
+constexpr int q1_tpb() { return sizeof(T) == 4 ? 512 : 256; }
 template <typename T>
 struct Q1Plan {
     int nlev, nu_pre, nu_post;
