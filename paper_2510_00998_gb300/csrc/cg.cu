@@ -369,6 +369,20 @@ template <int DIM, typename T>
 __global__ void __launch_bounds__(q1_tpb<T>()) k_q1_cycle(const Q1Plan<T> *__restrict__ P, unsigned long long *bar) {
     if (*(volatile unsigned long long *)&g_q1_barrier_timeouts != 0) return;
     const Q1Plan<T> &p = *P;
+    // the finest level's stencil is first read after the zero-guess Jacobi step:
+    // every block requests its share into L2 now (a hint; 16-byte pieces)
+    if (threadIdx.x == 0 && p.nlev > 0) {
+        const uint64_t bytes = (uint64_t)(DIM == 3 ? 27 : 9) * p.L[0].nv * sizeof(T);
+        const uint64_t chunk = ((bytes + gridDim.x - 1) / gridDim.x + 15) / 16 * 16;
+        const uint64_t off = (uint64_t)blockIdx.x * chunk;
+        const unsigned char *base = reinterpret_cast<const unsigned char *>(p.L[0].st);
+        if (off < bytes && (reinterpret_cast<uintptr_t>(base) & 15) == 0) {
+            const uint64_t n = (bytes - off < chunk ? bytes - off : chunk) / 16 * 16;
+            if (n > 0)
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(base + off), "r"((unsigned)n)
+                             : "memory");
+        }
+    }
     const int nl = p.nlev, ls = p.local_from;
     GridSync grid{bar, 0ull, 0u};
     const GridEach on_grid;
