@@ -365,8 +365,8 @@ __device__ __forceinline__ const T *q1_up(const Q1Plan<T> &p, int l, const T *ec
 // threshold is lower in FP64, whose FMA throughput per SM is low) and the
 // coarsest solve run in block 0 alone, separated by block barriers; the larger
 // levels use the whole grid.
-template <int DIM, typename T>
-__global__ void __launch_bounds__(q1_tpb<T>()) k_q1_cycle(const Q1Plan<T> *__restrict__ P, unsigned long long *bar) {
+template <int DIM, typename T, int TPB>
+__global__ void __launch_bounds__(TPB) k_q1_cycle(const Q1Plan<T> *__restrict__ P, unsigned long long *bar) {
     if (*(volatile unsigned long long *)&g_q1_barrier_timeouts != 0) return;
     const Q1Plan<T> &p = *P;
     // the finest level's stencil is first read after the zero-guess Jacobi step:
@@ -479,16 +479,21 @@ inline unsigned blocks_for(int64_t n) { return (unsigned)((n + TPB - 1) / TPB); 
 
 }  // namespace
 
+// the kernel of precision T, dimension dim, 256 or (wide, FP32) 512 threads
 template <typename T>
-const void *q1_cycle_fn(int dim) {
-    return dim == 3 ? (const void *)k_q1_cycle<3, T> : (const void *)k_q1_cycle<2, T>;
+const void *q1_cycle_fn(int dim, bool wide) {
+    if (wide && sizeof(T) == 4)
+        return dim == 3 ? (const void *)k_q1_cycle<3, T, Q1_TPB_WIDE> : (const void *)k_q1_cycle<2, T, Q1_TPB_WIDE>;
+    return dim == 3 ? (const void *)k_q1_cycle<3, T, Q1_TPB> : (const void *)k_q1_cycle<2, T, Q1_TPB>;
 }
 
 template <typename T>
-cudaError_t launch_q1_cycle(int dim, const Q1Plan<T> *plan, unsigned long long *bar, int blocks, cudaStream_t s) {
+cudaError_t launch_q1_cycle(int dim, const Q1Plan<T> *plan, unsigned long long *bar, int blocks, bool wide,
+                            cudaStream_t s) {
+    const bool w = wide && sizeof(T) == 4;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(blocks);
-    cfg.blockDim = dim3(q1_tpb<T>());
+    cfg.blockDim = dim3(w ? Q1_TPB_WIDE : Q1_TPB);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;   // all blocks co-resident: the grid barrier cannot wait on an unscheduled block
@@ -496,18 +501,23 @@ cudaError_t launch_q1_cycle(int dim, const Q1Plan<T> *plan, unsigned long long *
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     count_launches(1);
-    if (dim == 3) return cudaLaunchKernelEx(&cfg, k_q1_cycle<3, T>, plan, bar);
-    return cudaLaunchKernelEx(&cfg, k_q1_cycle<2, T>, plan, bar);
+    if (w) {
+        if (dim == 3) return cudaLaunchKernelEx(&cfg, k_q1_cycle<3, T, Q1_TPB_WIDE>, plan, bar);
+        return cudaLaunchKernelEx(&cfg, k_q1_cycle<2, T, Q1_TPB_WIDE>, plan, bar);
+    }
+    if (dim == 3) return cudaLaunchKernelEx(&cfg, k_q1_cycle<3, T, Q1_TPB>, plan, bar);
+    return cudaLaunchKernelEx(&cfg, k_q1_cycle<2, T, Q1_TPB>, plan, bar);
 }
 
 template <typename T>
-int q1_cycle_max_blocks(int dim) {
+int q1_cycle_max_blocks(int dim, bool wide) {
     int dev = 0, sms = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
     int coop = 0;
     if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, q1_cycle_fn<T>(dim), q1_tpb<T>(), 0) != cudaSuccess) {
+    const int tpb = wide && sizeof(T) == 4 ? Q1_TPB_WIDE : Q1_TPB;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, q1_cycle_fn<T>(dim, wide), tpb, 0) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -687,9 +697,11 @@ cudaError_t launch_coarse_solve_batch(const BatchCG<T> *D, const VertMap *map, i
 DGMG_CG_INST(double)
 DGMG_CG_INST(float)
 
-template cudaError_t launch_q1_cycle<double>(int, const Q1Plan<double> *, unsigned long long *, int, cudaStream_t);
-template cudaError_t launch_q1_cycle<float>(int, const Q1Plan<float> *, unsigned long long *, int, cudaStream_t);
-template int q1_cycle_max_blocks<double>(int);
-template int q1_cycle_max_blocks<float>(int);
+template cudaError_t launch_q1_cycle<double>(int, const Q1Plan<double> *, unsigned long long *, int, bool,
+                                              cudaStream_t);
+template cudaError_t launch_q1_cycle<float>(int, const Q1Plan<float> *, unsigned long long *, int, bool,
+                                             cudaStream_t);
+template int q1_cycle_max_blocks<double>(int, bool);
+template int q1_cycle_max_blocks<float>(int, bool);
 
 }  // namespace dgmg

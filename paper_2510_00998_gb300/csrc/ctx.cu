@@ -694,7 +694,7 @@ int q1_cycle(dgmg_ctx &C, cudaStream_t s, T **result) {
     if (!plan || C.q1_blocks <= 0 || g_q1_one_launch_off.load(std::memory_order_relaxed))
         return cg_vcycle<T>(C, 0, s, result);
     const int pi = std::is_same<T, float>::value ? 1 : 0;
-    LC(launch_q1_cycle<T>(C.dim, plan, C.q1bar + pi, C.q1_blocks_t[pi], s));
+    LC(launch_q1_cycle<T>(C.dim, plan, C.q1bar + pi, C.q1_blocks_t[pi], C.q1_wide, s));
     *result = lv.size() == 1 ? lv[0].u[0] : lv[0].u[(C.opts.nu_pre + C.opts.nu_post) & 1];
     return DGMG_OK;
 }
@@ -704,8 +704,8 @@ int q1_cycle(dgmg_ctx &C, cudaStream_t s, T **result) {
 // its kernel keeps co-resident (q1_blocks_t; every launch on a plan's arrival
 // counter has the same block count); 0 where the launch is not possible.
 static int q1_blocks_for(int dim, bool mixed) {
-    int qb = q1_cycle_max_blocks<double>(dim);
-    if (mixed) qb = std::min(qb, q1_cycle_max_blocks<float>(dim));
+    int qb = q1_cycle_max_blocks<double>(dim, false);
+    if (mixed) qb = std::min(qb, q1_cycle_max_blocks<float>(dim, false));
     return std::max(0, qb);
 }
 
@@ -752,7 +752,8 @@ int setup_q1_plan(dgmg_ctx &C) {
         bool ok = cudaStreamBeginCapture(C.capture_stream, cudaStreamCaptureModeRelaxed) == cudaSuccess;
         if (ok) {
             const int pi = std::is_same<T, float>::value ? 1 : 0;
-            const cudaError_t el = launch_q1_cycle<T>(C.dim, d, C.q1bar + pi, C.q1_blocks_t[pi], C.capture_stream);
+            const cudaError_t el =
+                launch_q1_cycle<T>(C.dim, d, C.q1bar + pi, C.q1_blocks_t[pi], C.q1_wide, C.capture_stream);
             g_kernel_launches.fetch_sub(1);   // captured, not launched
             const cudaError_t ee = cudaStreamEndCapture(C.capture_stream, &graph);
             ok = el == cudaSuccess && ee == cudaSuccess && graph &&
@@ -1193,8 +1194,13 @@ int create_ctx(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_opt
     trace.mark("dg fp64 (factors on the device)");
     if (!(flags & CREATE_NO_SOLVER)) {   // a batch member runs its Q1 levels in the batch's kernels
         C->q1_blocks = q1_blocks_for(C->dim, o.precision == DGMG_MIXED_FP32);
-        C->q1_blocks_t[0] = q1_cycle_max_blocks<double>(C->dim);
-        C->q1_blocks_t[1] = o.precision == DGMG_MIXED_FP32 ? q1_cycle_max_blocks<float>(C->dim) : 0;
+        C->q1_wide = !(flags & CREATE_SHARED_GPU);
+        C->q1_blocks_t[0] = q1_cycle_max_blocks<double>(C->dim, false);
+        C->q1_blocks_t[1] = o.precision == DGMG_MIXED_FP32 ? q1_cycle_max_blocks<float>(C->dim, C->q1_wide) : 0;
+        // beside other solves (server): no more blocks than the FP64 kernel's one per
+        // SM, so that the cooperative launch finds room among concurrent kernels
+        if (!C->q1_wide && C->q1_blocks_t[1] > C->q1_blocks_t[0] && C->q1_blocks_t[0] > 0)
+            C->q1_blocks_t[1] = C->q1_blocks_t[0];
     }
     if (!(flags & CREATE_NO_FP64_Q1)) {
         RC(setup_cg<double>(*C, C->cg64));

@@ -148,6 +148,7 @@ struct dgmg_ctx {
     unsigned long long *q1bar = nullptr;          // arrival counters [FP64, FP32]
     int q1_blocks = 0;
     int q1_blocks_t[2] = {0, 0};                   // blocks of the cycle per precision [FP64, FP32]
+    bool q1_wide = true;                           // FP32 cycle in 512-thread blocks
     DGDev<double> d64;
     DGDev<float> d32;
     std::vector<CGDev<double>> cg64;
@@ -353,8 +354,10 @@ inline const std::vector<CGDev<T>> &cgl(const dgmg_ctx &C) {
 // dgmg_create with parts left out for contexts that only serve a batch:
 // no solver workspace (work vectors, scalars, quadrature tables); no FP64
 // block-inverse factors (the FP64 level only applies the operator); no FP64 Q1
-// levels (the V-cycle runs in FP32).
-enum { CREATE_NO_SOLVER = 1, CREATE_NO_FP64_SMOOTHER = 2, CREATE_NO_FP64_Q1 = 4 };
+// levels (the V-cycle runs in FP32). CREATE_SHARED_GPU (solve server): the Q1
+// cycle's cooperative launch in 256-thread blocks, one per SM, which fit beside
+// the kernels of concurrent solves.
+enum { CREATE_NO_SOLVER = 1, CREATE_NO_FP64_SMOOTHER = 2, CREATE_NO_FP64_Q1 = 4, CREATE_SHARED_GPU = 8 };
 int create_ctx(const dgmg_mesh *mesh, int p, const double *kappa, const dgmg_opts *opts, int flags, dgmg_ctx **out);
 
 int mg_cycle64(dgmg_ctx &C, double *x, const double *b, double *r, cudaStream_t s);

@@ -192,11 +192,13 @@ struct BatchCG {
 // The Q1 h-cycle of one problem as one cooperative launch: every level's
 // operator and transfer tables, its vectors, the coarsest inverse.
 constexpr int Q1_MAXLEV = 24;
-// threads per block of the cooperative cycle: FP32 512 (one block per SM, more
-// loads of the vertex loops in flight, fewer barrier arrivals, and 512 threads
-// for the levels run in block 0), FP64 256 (two per SM; 512 spill in FP64)
-template <typename T>
-constexpr int q1_tpb() { return sizeof(T) == 4 ? 512 : 256; }
+// threads per block of the cooperative cycle: 256, or (FP32, wide) 512: one
+// block per SM, more loads of the vertex loops in flight, fewer barrier
+// arrivals, and 512 threads for the levels run in block 0. A 512-thread block
+// holds a whole SM's registers, so its cooperative launch waits for empty SMs
+// where other solves share the GPU (the solve server keeps 256); in FP64 the
+// 512-thread kernel spills.
+constexpr int Q1_TPB = 256, Q1_TPB_WIDE = 512;
 template <typename T>
 struct Q1Plan {
     int nlev, nu_pre, nu_post;
@@ -211,10 +213,11 @@ struct Q1Plan {
 // on level 0; bar: the plan's own arrival counter (zero before its first
 // launch; every launch on it with the same number of blocks)
 template <typename T>
-cudaError_t launch_q1_cycle(int dim, const Q1Plan<T> *plan, unsigned long long *bar, int blocks, cudaStream_t s);
+cudaError_t launch_q1_cycle(int dim, const Q1Plan<T> *plan, unsigned long long *bar, int blocks, bool wide,
+                            cudaStream_t s);
 // the most blocks of the cooperative launch (one per SM), 0 if it cannot run
 template <typename T>
-int q1_cycle_max_blocks(int dim);
+int q1_cycle_max_blocks(int dim, bool wide);
 cudaError_t q1_barrier_timeouts(unsigned long long *count);
 cudaError_t q1_barrier_timeouts_addr(unsigned long long **ptr);
 // Set once a grid-barrier wait of the one-launch Q1 cycle ran out anywhere in

@@ -131,7 +131,7 @@ struct dgmg_server {
             const double *kp = r->has_kappa ? r->kappa.data() : nullptr;
             lk.unlock();
             dgmg_ctx *ctx = nullptr;
-            const int rc = dgmg_create(&r->mesh, r->p, kp, &opts, &ctx);
+            const int rc = create_ctx(&r->mesh, r->p, kp, &opts, CREATE_SHARED_GPU, &ctx);
             const std::string err = rc == DGMG_OK ? "" : dgmg_last_error();
             size_t actual = 0;
             if (rc == DGMG_OK) {
