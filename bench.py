@@ -39,8 +39,8 @@ FP64_NOMINAL_TFLOPS = 1.25       # nominal GB300 dense FP64, context beside the 
 # DRAM bytes (read + write) of one launch of the FP64 smoothing kernel on this
 # workload from one ncu capture, valid only for the kernel sources it was taken
 # on (SHA-256 of the files below); once they change, `traffic` reads null
-SMOOTH_TRAFFIC = {"kernel": "k_smooth_cells<double,4>", "bytes": 116_652_544 + 10_885_376,
-                  "sources_sha256": "6587668896306014285e408166b1b94f3da7ee96a090b396b0e3edf6ff675a68",
+SMOOTH_TRAFFIC = {"kernel": "k_smooth_cells<double,4>", "bytes": 116_628_736 + 10_494_464,
+                  "sources_sha256": "7b1b09b1125962089f573f3432c4a423ffed4cdec4c1dcacfab6e84818cc62ad",
                   "files": ("smooth_cells.cuh", "dg_kernels.cuh", "dg_fp64.cu")}
 
 

@@ -36,17 +36,6 @@ static __device__ unsigned long long g_wait_timeouts;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
 __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
@@ -274,19 +263,19 @@ template <typename T, int Q>
 __device__ __forceinline__ void pass_x(const T *A, T *R) {
     if constexpr (sizeof(T) == 4) {
         pass_x2<Q>(reinterpret_cast<const float *>(A), reinterpret_cast<float *>(R));
-        return;
-    }
+    } else {
 #pragma unroll
-    for (int t = 0; t < Q * Q; ++t) {
-        T x[Q];
+        for (int t = 0; t < Q * Q; ++t) {
+            T x[Q];
 #pragma unroll
-        for (int n = 0; n < Q; ++n) x[n] = R[n + Q * t];
+            for (int n = 0; n < Q; ++n) x[n] = R[n + Q * t];
 #pragma unroll
-        for (int m = 0; m < Q; ++m) {
-            T s = T(0);
+            for (int m = 0; m < Q; ++m) {
+                T s = T(0);
 #pragma unroll
-            for (int n = 0; n < Q; ++n) s += A[m * Q + n] * x[n];
-            R[m + Q * t] = s;
+                for (int n = 0; n < Q; ++n) s += A[m * Q + n] * x[n];
+                R[m + Q * t] = s;
+            }
         }
     }
 }
@@ -445,19 +434,19 @@ __device__ __forceinline__ void x_face_traces(int side, const T *R, const T *dv,
                 dst[NF + sa * a0 + sb * b0] = d;
             }
         }
-        return;
+    } else {
+#pragma unroll
+        for (int b = 0; b < Q; ++b)
+#pragma unroll
+            for (int a = 0; a < Q; ++a) {
+                const T *pen = R + Q * (a + Q * b);
+                T d = T(0);
+#pragma unroll
+                for (int n = 0; n < Q; ++n) d += dv[n] * pen[n];
+                dst[sa * a + sb * b] = side ? pen[Q - 1] : pen[0];
+                dst[NF + sa * a + sb * b] = d;
+            }
     }
-#pragma unroll
-    for (int b = 0; b < Q; ++b)
-#pragma unroll
-        for (int a = 0; a < Q; ++a) {
-            const T *pen = R + Q * (a + Q * b);
-            T d = T(0);
-#pragma unroll
-            for (int n = 0; n < Q; ++n) d += dv[n] * pen[n];
-            dst[sa * a + sb * b] = side ? pen[Q - 1] : pen[0];
-            dst[NF + sa * a + sb * b] = d;
-        }
 }
 
 // Traces of the cell tensor R (one per lane) to tr_out[cell][face][FS]: the
@@ -944,7 +933,7 @@ __device__ __forceinline__ void residual_cells_body(const DGConst<T> &c, int64_t
                                                     const T *__restrict__ tr, T *__restrict__ rout,
                                                     T *__restrict__ corners, bool reuse = false) {
     using G = CellGeo<T, Q>;
-    constexpr int W = G::W, NL = G::NL, NF = G::NF, FDS = G::FDS, TR = G::TR, FS = G::FS;
+    constexpr int W = G::W, NL = G::NL, FDS = G::FDS, TR = G::TR, FS = G::FS;
     extern __shared__ __align__(128) unsigned char smem_c[];
     T *sA = reinterpret_cast<T *>(smem_c);              // u -> b (FP32) or factors (FP64) -> face slot 1 -> r
     T *sB = sA + G::OFF_B;                               // FP32: factors -> face slot 0
