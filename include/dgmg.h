@@ -491,8 +491,9 @@ int dgmg_volume_residual_f32(dgmg_ctx *ctx, const float *u, const float *b, floa
  * the rounding of form 1); form 1: the per-pencil kernel; form 2: one thread per
  * cell with A_KK u through the fast-diagonalisation factors (the V-cycle's
  * residual; its FP32 rounding costs the CG recurrences iterations). All forms
- * agree to FP32 rounding. DGMG_EINVAL for an FP64 ctx, NULL or aliasing vectors
- * or another form.
+ * agree to FP32 rounding. DGMG_EINVAL for an FP64 ctx, NULL or aliasing vectors,
+ * another form, or form 2 on a ctx with interior-only blocks
+ * (DGMG_BLOCK_INTERIOR_ONLY, whose factors are not those of A_KK).
  */
 int dgmg_apply_f32(dgmg_ctx *ctx, const float *u, float *y, int form, void *stream);
 

@@ -613,6 +613,10 @@ int dgmg_apply_f32(dgmg_ctx *C, const float *u, float *y, int form, void *stream
     cudaStream_t s = (cudaStream_t)stream;
     if (form == 0) return dgmg::apply32(*C, u, y, s);
     DGDev<float> &D = C->d32;
+    // form 2 forms A_KK u from the per-cell factors, which factor A_KK only with
+    // exact blocks (with interior-only blocks they hold the interior cell's block)
+    const float *fd = dgmg::exact_fd(*C, D);
+    if (form == 2 && !fd) return fail(DGMG_EINVAL, "dgmg_apply_f32: form 2 needs exact per-cell blocks");
     C->prof.begin(ST_PROJECT, s);
     LC(dgmg::launch_project<float>(C->dim, C->q, D.c, C->tile[1][TILE_PROJECT], const_cast<float *>(u), nullptr,
                                    D.tr[0], s));
@@ -622,7 +626,7 @@ int dgmg_apply_f32(dgmg_ctx *C, const float *u, float *y, int form, void *stream
     const int tile = form == 1 ? std::max(1, 128 / (C->dim == 3 ? C->q * C->q : C->q)) : 0;
     C->prof.begin(ST_RESIDUAL, s);
     LC(dgmg::launch_residual<float>(C->dim, C->q, D.c, tile, dgmg::RES_WRITE_R | dgmg::RES_NEGATE, u, nullptr,
-                                    D.kappa, D.tr[0], y, nullptr, form == 2 ? D.fdr : nullptr, s));
+                                    D.kappa, D.tr[0], y, nullptr, form == 2 ? fd : nullptr, s));
     C->prof.end(s);
     return DGMG_OK;
 }

@@ -87,3 +87,28 @@ def test_fp32_operator_rejects_fp64_ctx_and_bad_arguments(dgmg):
     with pytest.raises(dgmg.DGMGError) as ei:
         ctx.apply_f32(x, x.clone(), 3)
     assert ei.value.code == dgmg.DGMG_EINVAL
+
+
+def test_fp32_operator_with_interior_only_blocks(dgmg):
+    """Technique 4 contexts: forms 0 and 1 never use the block factors and still
+    give A u; form 2 (A_KK u from the per-cell factors, which there factor the
+    interior cell's block, not A_KK) is rejected."""
+    n, p = (5, 4, 6), 4
+    mesh = sipg.Mesh(n, p)
+    rng = np.random.default_rng(23)
+    kappa = np.exp(rng.normal(size=mesh.ncell))
+    u = rng.normal(size=mesh.ndof).astype(np.float32)
+    ref = sipg.apply(mesh, u.astype(np.float64), kappa)
+    ctx = dgmg.Context(n, p, kappa, precision=dgmg.DGMG_MIXED_FP32,
+                       block_inverse=dgmg.DGMG_BLOCK_INTERIOR_ONLY)
+    ut = torch.tensor(u, device="cuda:0")
+    for form in (0, 1):
+        y = torch.full_like(ut, float("nan"))
+        ctx.apply_f32(ut, y, form)
+        torch.cuda.synchronize()
+        yv = y.cpu().numpy().astype(np.float64)
+        assert np.linalg.norm(yv - ref) <= TOL_NORM * np.linalg.norm(ref)
+    with pytest.raises(dgmg.DGMGError) as ei:
+        ctx.apply_f32(ut, torch.empty_like(ut), 2)
+    assert ei.value.code == dgmg.DGMG_EINVAL
+    assert dgmg.wait_timeouts() == 0
