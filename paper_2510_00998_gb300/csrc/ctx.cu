@@ -1453,6 +1453,7 @@ static int check_level(dgmg_ctx *C, int level, bool need_next) {
     RC(check_ctx(C));
     if (level < 0 || level >= (int)C->lv.size() - (need_next ? 1 : 0))
         return fail(DGMG_EINVAL, "level out of range");
+    if (C->cg64.size() != C->lv.size()) return fail(DGMG_EINVAL, "ctx holds no FP64 Q1 levels");
     return DGMG_OK;
 }
 
