@@ -180,7 +180,10 @@ def _check(rc, allow=()):
     return rc
 
 
-def _ptr(t):
+def _ptr(t, n=None, dtype=None):
+    """Device pointer of a contiguous CUDA tensor of `dtype` (float64 unless
+    given) holding at least `n` elements (the length the library reads or
+    writes; unchecked when n is None or negative)."""
     if t is None:
         return None
     import torch
@@ -188,9 +191,16 @@ def _ptr(t):
         raise TypeError("expected a torch.Tensor")
     if not t.is_cuda or not t.is_contiguous():
         raise ValueError("tensor must be a contiguous CUDA tensor")
-    if t.dtype != torch.float64:
-        raise ValueError("tensor must be float64")
+    if t.dtype != (torch.float64 if dtype is None else dtype):
+        raise ValueError(f"tensor must be {torch.float64 if dtype is None else dtype}")
+    if n is not None and n >= 0 and t.numel() < n:
+        raise ValueError(f"tensor holds {t.numel()} elements, {n} needed")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _f32(t, n):
+    import torch
+    return _ptr(t, n, torch.float32)
 
 
 def _stream(stream):
@@ -205,6 +215,26 @@ def _mesh(n):
     for a in range(3):
         m.n[a] = int(n[a]) if a < len(n) else 1
     return m
+
+
+def _ncell(n):
+    c = 1
+    for v in n:
+        c *= int(v)
+    return c
+
+
+def _ndof(n, p):
+    return _ncell(n) * (int(p) + 1) ** len(n)
+
+
+def _kappa(kappa, n):
+    """Contiguous float64 copy of one coefficient per cell of mesh n."""
+    import numpy as np
+    k = np.ascontiguousarray(np.asarray(kappa, dtype=np.float64).reshape(-1))
+    if k.size != _ncell(n):
+        raise ValueError("kappa needs one value per cell")
+    return k
 
 
 def _opts(**opts):
@@ -237,13 +267,14 @@ class Server:
 
     def submit(self, n, p, b, x, kappa=None):
         """Queue a solve; b, x: contiguous CUDA float64 tensors kept alive until done."""
-        import numpy as np
         kp = None
         if kappa is not None:
-            k = np.ascontiguousarray(np.asarray(kappa, dtype=np.float64).reshape(-1))
+            k = _kappa(kappa, n)
             kp = k.ctypes.data_as(ctypes.c_void_p)
         t = ctypes.c_uint64()
-        _check(self.lib.dgmg_submit(self.h, ctypes.byref(_mesh(n)), int(p), kp, _ptr(b), _ptr(x), ctypes.byref(t)))
+        nd = _ndof(n, p)
+        _check(self.lib.dgmg_submit(self.h, ctypes.byref(_mesh(n)), int(p), kp, _ptr(b, nd), _ptr(x, nd),
+                                    ctypes.byref(t)))
         self._keep[t.value] = (b, x)
         return int(t.value)
 
@@ -279,7 +310,6 @@ class Batch:
 
     def __init__(self, problems, **opts):
         """problems: list of (n, p, kappa or None); all meshes of one dimension."""
-        import numpy as np
         self.lib = load()
         self.opts = _opts(**opts)
         k = len(problems)
@@ -287,11 +317,13 @@ class Batch:
         ps = (ctypes.c_int * k)()
         kps = (ctypes.c_void_p * k)()
         self._kappa_keep = []
+        self._ndof = []
         for i, (n, p, kappa) in enumerate(problems):
             meshes[i] = _mesh(n)
             ps[i] = int(p)
+            self._ndof.append(_ndof(n, p))
             if kappa is not None:
-                a = np.ascontiguousarray(np.asarray(kappa, dtype=np.float64).reshape(-1))
+                a = _kappa(kappa, n)
                 self._kappa_keep.append(a)
                 kps[i] = a.ctypes.data
         h = ctypes.c_void_p()
@@ -311,8 +343,8 @@ class Batch:
         k = self.count
         if len(bs) != k or len(xs) != k:
             raise ValueError("one b and one x per problem")
-        bp = (ctypes.c_void_p * k)(*[t.data_ptr() for t in bs])
-        xp = (ctypes.c_void_p * k)(*[t.data_ptr() for t in xs])
+        bp = (ctypes.c_void_p * k)(*[_ptr(t, nd).value for t, nd in zip(bs, self._ndof)])
+        xp = (ctypes.c_void_p * k)(*[_ptr(t, nd).value for t, nd in zip(xs, self._ndof)])
         st = (Stats * k)()
         allow = (DGMG_ENOTCONVERGED,) if allow_notconverged else ()
         rc = _check(self.lib.dgmg_batch_solve(self.h, ctypes.cast(bp, _P), ctypes.cast(xp, _P), ctypes.cast(st, _P),
@@ -356,8 +388,7 @@ class Context:
         kap_ptr = None
         self._kappa_keep = None
         if kappa is not None:
-            import numpy as np
-            k = np.ascontiguousarray(np.asarray(kappa, dtype=np.float64).reshape(-1))
+            k = _kappa(kappa, n)
             self._kappa_keep = k
             kap_ptr = k.ctypes.data_as(ctypes.c_void_p)
         h = ctypes.c_void_p()
@@ -386,10 +417,7 @@ class Context:
 
     def update_kappa(self, kappa):
         """New per-cell coefficients for the same mesh and degree (dgmg_update_kappa)."""
-        import numpy as np
-        k = np.ascontiguousarray(np.asarray(kappa, dtype=np.float64).reshape(-1))
-        if k.size != int(self.info.ncell):
-            raise ValueError("kappa needs one value per cell")
+        k = _kappa(kappa, self.n)
         _check(self.lib.dgmg_update_kappa(self.h, k.ctypes.data_as(ctypes.c_void_p)))
         self._kappa_keep = k
 
@@ -403,21 +431,26 @@ class Context:
         return int(self.lib.dgmg_cg_size(self.h, int(level)))
 
     def apply(self, u, y, stream=None):
-        _check(self.lib.dgmg_apply(self.h, _ptr(u), _ptr(y), _stream(stream)))
+        n = self.ndof
+        _check(self.lib.dgmg_apply(self.h, _ptr(u, n), _ptr(y, n), _stream(stream)))
 
     def residual(self, u, b, r, stream=None):
-        _check(self.lib.dgmg_residual(self.h, _ptr(u), _ptr(b), _ptr(r), _stream(stream)))
+        n = self.ndof
+        _check(self.lib.dgmg_residual(self.h, _ptr(u, n), _ptr(b, n), _ptr(r, n), _stream(stream)))
 
     def smooth(self, u, b, nsteps, stream=None):
-        _check(self.lib.dgmg_smooth(self.h, _ptr(u), _ptr(b), int(nsteps), _stream(stream)))
+        n = self.ndof
+        _check(self.lib.dgmg_smooth(self.h, _ptr(u, n), _ptr(b, n), int(nsteps), _stream(stream)))
 
     def vcycle(self, r, e, stream=None):
-        _check(self.lib.dgmg_vcycle(self.h, _ptr(r), _ptr(e), _stream(stream)))
+        n = self.ndof
+        _check(self.lib.dgmg_vcycle(self.h, _ptr(r, n), _ptr(e, n), _stream(stream)))
 
     def solve(self, b, x, stream=None, allow_notconverged=False):
         st = Stats()
         allow = (DGMG_ENOTCONVERGED,) if allow_notconverged else ()
-        rc = _check(self.lib.dgmg_solve(self.h, _ptr(b), _ptr(x), ctypes.byref(st), _stream(stream)), allow)
+        n = self.ndof
+        rc = _check(self.lib.dgmg_solve(self.h, _ptr(b, n), _ptr(x, n), ctypes.byref(st), _stream(stream)), allow)
         return st, rc
 
     def solve_host(self, b_host, x_host, stream=None):
@@ -426,63 +459,73 @@ class Context:
         for t in (b_host, x_host):
             if t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
                 raise ValueError("host tensors must be contiguous CPU float64")
+            if t.numel() < self.ndof:
+                raise ValueError(f"host tensor holds {t.numel()} elements, {self.ndof} needed")
         st = Stats()
         _check(self.lib.dgmg_solve_host(self.h, ctypes.c_void_p(b_host.data_ptr()),
                                         ctypes.c_void_p(x_host.data_ptr()), ctypes.byref(st), _stream(stream)))
         return st
 
+    def _quad_per_cell(self):
+        return (self.info.p + 2) ** self.info.dim
+
     def quad_points(self, xq, stream=None):
-        _check(self.lib.dgmg_quad_points(self.h, _ptr(xq), _stream(stream)))
+        n = int(self.info.ncell) * self._quad_per_cell() * self.info.dim
+        _check(self.lib.dgmg_quad_points(self.h, _ptr(xq, n), _stream(stream)))
 
     def load_vector(self, fq, b, stream=None):
-        _check(self.lib.dgmg_load_vector(self.h, _ptr(fq), _ptr(b), _stream(stream)))
+        n = int(self.info.ncell) * self._quad_per_cell()
+        _check(self.lib.dgmg_load_vector(self.h, _ptr(fq, n), _ptr(b, self.ndof), _stream(stream)))
 
     def project(self, u, e, traces, stream=None):
-        _check(self.lib.dgmg_project(self.h, _ptr(u), _ptr(e), _ptr(traces), _stream(stream)))
+        _check(self.lib.dgmg_project(self.h, _ptr(u, self.ndof), _ptr(e, int(self.info.nvert0)),
+                                     _ptr(traces, self.trace_size()), _stream(stream)))
+
+    def _rr_args(self, u, b, traces, r, rc):
+        n = self.ndof
+        return (_ptr(u, n), _ptr(b, n), _ptr(traces, self.trace_size()), _ptr(r, n), _ptr(rc, int(self.info.nvert0)))
 
     def residual_restrict(self, u, b, traces, r, rc, stream=None):
-        _check(self.lib.dgmg_residual_restrict(self.h, _ptr(u), _ptr(b), _ptr(traces), _ptr(r), _ptr(rc),
-                                               _stream(stream)))
+        _check(self.lib.dgmg_residual_restrict(self.h, *self._rr_args(u, b, traces, r, rc), _stream(stream)))
 
     def residual_restrict_noalloc(self, u, b, traces, r, rc, stream=None):
         """As residual_restrict, with the scratch in the library's fixed device
         array instead of the context's (allocates nothing; see dgmg.h)."""
-        _check(self.lib.dgmg_residual_restrict_noalloc(self.h, _ptr(u), _ptr(b), _ptr(traces), _ptr(r), _ptr(rc),
-                                                       _stream(stream)))
+        _check(self.lib.dgmg_residual_restrict_noalloc(self.h, *self._rr_args(u, b, traces, r, rc), _stream(stream)))
 
     def volume_residual_f32(self, u, b, r, method, stream=None):
         """r = b - kappa_K E u_K per cell (FP32 tensors; method 0 sum-factorised,
         1 tensor cores, TF32): the volume term of the operator alone."""
-        for t in (u, b, r):
-            if not t.is_cuda or not t.is_contiguous() or t.dtype != __import__("torch").float32:
-                raise ValueError("FP32 contiguous CUDA tensors expected")
-        _check(self.lib.dgmg_volume_residual_f32(self.h, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(b.data_ptr()),
-                                                 ctypes.c_void_p(r.data_ptr()), int(method), _stream(stream)))
+        n = self.ndof
+        _check(self.lib.dgmg_volume_residual_f32(self.h, _f32(u, n), _f32(b, n), _f32(r, n), int(method),
+                                                 _stream(stream)))
 
     def apply_f32(self, u, y, form=0, stream=None):
         """y = A u in FP32 (mixed-precision ctx): the operator of the FP32 CG
         recurrences; form 0 the solver's choice, 1 per pencil, 2 one thread per
         cell through the fast-diagonalisation factors."""
-        for t in (u, y):
-            if not t.is_cuda or not t.is_contiguous() or t.dtype != __import__("torch").float32:
-                raise ValueError("FP32 contiguous CUDA tensors expected")
-        _check(self.lib.dgmg_apply_f32(self.h, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(y.data_ptr()),
-                                       int(form), _stream(stream)))
+        n = self.ndof
+        _check(self.lib.dgmg_apply_f32(self.h, _f32(u, n), _f32(y, n), int(form), _stream(stream)))
 
     def cg_smooth(self, level, u, b, nsteps, stream=None):
-        _check(self.lib.dgmg_cg_smooth(self.h, int(level), _ptr(u), _ptr(b), int(nsteps), _stream(stream)))
+        n = self.cg_size(level)
+        _check(self.lib.dgmg_cg_smooth(self.h, int(level), _ptr(u, n), _ptr(b, n), int(nsteps), _stream(stream)))
 
     def cg_residual(self, level, u, b, r, stream=None):
-        _check(self.lib.dgmg_cg_residual(self.h, int(level), _ptr(u), _ptr(b), _ptr(r), _stream(stream)))
+        n = self.cg_size(level)
+        _check(self.lib.dgmg_cg_residual(self.h, int(level), _ptr(u, n), _ptr(b, n), _ptr(r, n), _stream(stream)))
 
     def h_restrict(self, level, rf, rc, stream=None):
-        _check(self.lib.dgmg_h_restrict(self.h, int(level), _ptr(rf), _ptr(rc), _stream(stream)))
+        _check(self.lib.dgmg_h_restrict(self.h, int(level), _ptr(rf, self.cg_size(level)),
+                                        _ptr(rc, self.cg_size(level + 1)), _stream(stream)))
 
     def h_prolong(self, level, ec, uf, stream=None):
-        _check(self.lib.dgmg_h_prolong(self.h, int(level), _ptr(ec), _ptr(uf), _stream(stream)))
+        _check(self.lib.dgmg_h_prolong(self.h, int(level), _ptr(ec, self.cg_size(level + 1)),
+                                       _ptr(uf, self.cg_size(level)), _stream(stream)))
 
     def coarse_solve(self, r, e, stream=None):
-        _check(self.lib.dgmg_coarse_solve(self.h, _ptr(r), _ptr(e), _stream(stream)))
+        n = int(self.info.ncoarse)
+        _check(self.lib.dgmg_coarse_solve(self.h, _ptr(r, n), _ptr(e, n), _stream(stream)))
 
     def profile(self, enable=True):
         _check(self.lib.dgmg_profile(self.h, 1 if enable else 0))

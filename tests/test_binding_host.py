@@ -1,0 +1,38 @@
+"""Argument checks of the Python binding that run before any library call:
+vector lengths from the mesh and degree, one coefficient per cell, tensors on
+the device (CPU only: nothing here reaches a kernel)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def dgmg():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2510_00998_gb300 import dgmg as m
+    return m
+
+
+def test_sizes_from_mesh_and_degree(dgmg):
+    assert dgmg._ncell((4, 5, 6)) == 120
+    assert dgmg._ndof((4, 5, 6), 3) == 120 * 64
+    assert dgmg._ndof((7, 3), 4) == 21 * 25
+
+
+def test_kappa_needs_one_value_per_cell(dgmg):
+    k = dgmg._kappa([[1.0, 2.0], [3.0, 4.0]], (2, 2))
+    assert k.dtype == np.float64 and k.flags["C_CONTIGUOUS"] and k.tolist() == [1.0, 2.0, 3.0, 4.0]
+    with pytest.raises(ValueError):
+        dgmg._kappa(np.ones(15), (4, 4))
+    with pytest.raises(ValueError):
+        dgmg.Context((4, 4), 2, kappa=np.ones(17))      # rejected before the context is created
+
+
+def test_pointer_checks(dgmg):
+    with pytest.raises(TypeError):
+        dgmg._ptr(np.zeros(4))
+    with pytest.raises(ValueError):
+        dgmg._ptr(torch.zeros(4, dtype=torch.float64))  # host tensor
+    assert dgmg._ptr(None) is None

@@ -424,3 +424,35 @@ def test_vcycle_q1_one_launch(dgmg, n, p, nu, prec):
     assert launches <= sum(nu) + 8 < sum(nu) + 1 + 7 * (hier.nlevels - 1)
     assert _rel(_np(e), hier.vcycle(r)) <= (2e-5 if prec else 1e-11)
     assert dgmg.wait_timeouts() == 0
+
+
+def test_binding_rejects_short_vectors(dgmg):
+    """Every method checks that its tensors hold the lengths the library reads
+    or writes (DG vectors, traces, Q1 levels), before anything is launched."""
+    ctx = dgmg.Context((4, 4, 4), 2)
+
+    def z(n, dtype=torch.float64):
+        return torch.zeros(max(n, 0), dtype=dtype, device=DEV)
+    nd, nt, n0 = ctx.ndof, ctx.trace_size(), ctx.cg_size(0)
+    short = z(nd - 1)
+    calls = [lambda: ctx.apply(short, z(nd)), lambda: ctx.apply(z(nd), short),
+             lambda: ctx.residual(z(nd), z(nd), short), lambda: ctx.smooth(short, z(nd), 1),
+             lambda: ctx.vcycle(z(nd), short), lambda: ctx.solve(short, z(nd)),
+             lambda: ctx.project(z(nd), z(n0 - 1), z(nt)), lambda: ctx.project(z(nd), None, z(nt - 1)),
+             lambda: ctx.residual_restrict(z(nd), z(nd), z(nt), z(nd), z(n0 - 1)),
+             lambda: ctx.cg_residual(0, z(n0), z(n0), z(n0 - 1)),
+             lambda: ctx.h_restrict(0, z(n0), z(ctx.cg_size(1) - 1)),
+             lambda: ctx.h_prolong(0, z(ctx.cg_size(1) - 1), z(n0)),
+             lambda: ctx.coarse_solve(z(int(ctx.info.ncoarse) - 1), z(int(ctx.info.ncoarse))),
+             lambda: ctx.solve_host(torch.zeros(nd - 1, dtype=torch.float64), torch.zeros(nd, dtype=torch.float64))]
+    launches = dgmg.kernel_launches()
+    for call in calls:
+        with pytest.raises(ValueError):
+            call()
+    assert dgmg.kernel_launches() == launches
+    ctx32 = dgmg.Context((4, 4, 4), 4, precision=dgmg.DGMG_MIXED_FP32)
+    with pytest.raises(ValueError):
+        ctx32.apply_f32(z(ctx32.ndof - 1, torch.float32), z(ctx32.ndof, torch.float32))
+    batch = dgmg.Batch([((4, 4, 4), 2, None), ((5, 4, 3), 3, None)])
+    with pytest.raises(ValueError):
+        batch.solve([z(nd), z(60 * 64 - 1)], [z(nd), z(60 * 64)])
