@@ -124,3 +124,11 @@ def test_too_few_load_vector_points(monkeypatch):
     orig = sipg.load_vector
     monkeypatch.setattr(sipg, "load_vector", lambda mesh, f, nquad=None: orig(mesh, f, mesh.q - 1))
     _fails(S.test_load_vector_and_l2_error_closed_forms)
+
+
+def test_technique4_wrong_centre_cell(monkeypatch):
+    # the Technique 4 block taken from the cell before the centre of the 3^d
+    # helper mesh (a cell with a boundary facet) instead of the centre cell
+    orig = sipg.block_diagonal
+    monkeypatch.setattr(sipg, "block_diagonal", lambda mesh, kappa=None: np.roll(orig(mesh, kappa), 1, axis=0))
+    _fails(S.test_interior_only_block_is_an_interior_cells_assembled_block, (3, 4), 3)
