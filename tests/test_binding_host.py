@@ -36,3 +36,17 @@ def test_pointer_checks(dgmg):
     with pytest.raises(ValueError):
         dgmg._ptr(torch.zeros(4, dtype=torch.float64))  # host tensor
     assert dgmg._ptr(None) is None
+
+
+def test_missing_library_fails_loudly(dgmg, monkeypatch, tmp_path):
+    """No fallback: without libdgmg.so every entry of the binding raises."""
+    monkeypatch.setattr(dgmg, "_lib", None)
+    missing = str(tmp_path / "libdgmg.so")
+    with pytest.raises(OSError):
+        dgmg.load(missing)
+    monkeypatch.setattr(dgmg, "LIB_PATH", missing)
+    monkeypatch.setattr(dgmg.load, "__defaults__", (missing,))
+    with pytest.raises(OSError):
+        dgmg.Context((4, 4), 2)
+    with pytest.raises(OSError):
+        dgmg.kernel_launches()
