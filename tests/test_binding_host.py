@@ -50,3 +50,23 @@ def test_missing_library_fails_loudly(dgmg, monkeypatch, tmp_path):
         dgmg.Context((4, 4), 2)
     with pytest.raises(OSError):
         dgmg.kernel_launches()
+
+
+def test_estimate_bytes_on_the_host(dgmg):
+    """dgmg_estimate_bytes (the server's admission size; equal to a context's
+    allocations, checked on the GPU) is host arithmetic: it validates its
+    arguments and grows with the problem as its arrays do."""
+    for bad in [((4, 4), 0), ((4, 4), 7), ((1, 4), 2), ((4, 4, 4, 4), 2)]:
+        with pytest.raises(dgmg.DGMGError) as ei:
+            dgmg.estimate_bytes(*bad)
+        assert ei.value.code == dgmg.DGMG_EINVAL
+    with pytest.raises(dgmg.DGMGError):
+        dgmg.estimate_bytes((8, 8, 8), 3, coarsening=4)
+    b16, b32 = dgmg.estimate_bytes((16, 16, 16), 3), dgmg.estimate_bytes((32, 32, 32), 3)
+    ndof = 32 ** 3 * 64
+    # at least the five FP64 solver vectors, the DG iterate's table and two trace buffers
+    assert b32 >= (5 + 1) * 8 * ndof + 2 * 8 * 32 ** 3 * 6 * 2 * 16
+    assert 7.5 <= b32 / b16 <= 8.1                      # linear in the cells (the coarse inverse is small)
+    mixed = dgmg.estimate_bytes((32, 32, 32), 3, precision=dgmg.DGMG_MIXED_FP32)
+    assert b32 < mixed < 2 * b32                         # FP32 copies of the DG and Q1 levels on top
+    assert dgmg.estimate_bytes((32, 32, 32), 3, p_coarsening=1) > b32
