@@ -70,3 +70,15 @@ def test_estimate_bytes_on_the_host(dgmg):
     mixed = dgmg.estimate_bytes((32, 32, 32), 3, precision=dgmg.DGMG_MIXED_FP32)
     assert b32 < mixed < 2 * b32                         # FP32 copies of the DG and Q1 levels on top
     assert dgmg.estimate_bytes((32, 32, 32), 3, p_coarsening=1) > b32
+
+
+def test_default_options_are_the_documented_ones(dgmg):
+    """dgmg_default_opts fills the defaults the header states (the readings of
+    the unstated parameters: omega 0.8 on both level kinds, V(2,2), exact
+    blocks, coarsening factor 2, rtol 1e-10)."""
+    o = dgmg.default_opts()
+    assert (o.omega_dg, o.omega_cg, o.nu_pre, o.nu_post) == (0.8, 0.8, 2, 2)
+    assert o.precision == dgmg.DGMG_FP64 and o.block_inverse == dgmg.DGMG_BLOCK_EXACT
+    assert (o.coarsening, o.rtol, o.maxit, o.delta) == (2, 1e-10, 200, 0.01)
+    assert (o.autotune, o.p_coarsening, o.basis, o.recompute_block) == (0, 0, dgmg.DGMG_BASIS_GLL, 0)
+    assert b"sm_103a" in dgmg.load().dgmg_version()
