@@ -333,7 +333,8 @@ int dgmg_submit(dgmg_server *server, const dgmg_mesh *mesh, int p, const double 
  * State of a ticket (DGMG_PENDING / RUNNING / DONE / FAILED) and, once finished,
  * its stats (HOST, may be NULL; `seconds` = submit to completion, `queue_seconds`
  * = submit to admission). Returns the request's error code when it FAILED.
- * Thread-safe.
+ * DONE or FAILED is reported once: that poll releases the request's record, and
+ * later polls of the ticket return DGMG_EINVAL (unknown ticket). Thread-safe.
  */
 int dgmg_poll(dgmg_server *server, uint64_t ticket, int *status, dgmg_stats *stats);
 

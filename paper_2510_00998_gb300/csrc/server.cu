@@ -336,9 +336,15 @@ int dgmg_poll(dgmg_server *S, uint64_t ticket, int *status, dgmg_stats *stats) {
     if (it == S->requests.end()) return fail(DGMG_EINVAL, "unknown ticket");
     Request *r = it->second.get();
     *status = r->status;
-    if (stats && (r->status == DGMG_DONE || r->status == DGMG_FAILED)) *stats = r->stats;
-    if (r->status == DGMG_FAILED) return fail(r->rc, r->error);
-    return DGMG_OK;
+    if (r->status != DGMG_DONE && r->status != DGMG_FAILED) return DGMG_OK;
+    // the result is handed over once: the scheduler no longer touches a finished
+    // request, so its record is released here and the table stays bounded
+    if (stats) *stats = r->stats;
+    const int rc = r->rc;
+    const bool failed = r->status == DGMG_FAILED;
+    const std::string err = r->error;
+    S->requests.erase(it);
+    return failed ? fail(rc, err) : DGMG_OK;
 }
 
 int dgmg_server_info(dgmg_server *S, dgmg_server_info_t *info) {

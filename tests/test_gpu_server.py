@@ -89,6 +89,11 @@ def test_results_in_the_mix_equal_results_alone(dgmg, precision):
     assert seen_active >= 2          # work of several requests was on the GPU together
     inf = srv.info()
     assert inf.done == len(probs) and inf.failed == 0
+    # a finished request is reported once; its record is then released
+    for t in tickets:
+        with pytest.raises(dgmg.DGMGError) as ei:
+            srv.poll(t)
+        assert ei.value.code == dgmg.DGMG_EINVAL
     srv.close()
 
 
