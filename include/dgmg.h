@@ -77,7 +77,7 @@ extern "C" {
 /* block inverse used by the block-Jacobi smoother (Eq. block-Jacobi-IP) */
 #define DGMG_BASIS_GLL 0          /* Gauss-Lobatto-Legendre nodes (Sec. 2.2): the end  */
                                   /* nodes carry the traces, non-diagonal mass matrix  */
-#define DGMG_BASIS_GL 1           /* Gauss-Legendre nodes (Sec. 6.5): diagonal mass    */
+#define DGMG_BASIS_GL 1           /* Gauss-Legendre nodes (Sec. 6.4): diagonal mass    */
                                   /* matrix, every node contributes to a trace (dense  */
                                   /* cell-to-facet projection, Sec. 4.1). The same     */
                                   /* discrete problem in another basis; solves run the */
@@ -122,7 +122,7 @@ typedef struct {
                                   /* inverses A_KK^-1 are computed once at set-up      */
                                   /* (Technique 3, precomputed); 1: recomputed on the  */
                                   /* device before every smoothing step (the paper's   */
-                                  /* "recompute" variant of Table 6, Sec. 6.6); same   */
+                                  /* "recompute" variant of Table 6, Sec. 7.1); same   */
                                   /* results. Batched solves take 0 (DGMG_EINVAL)      */
 } dgmg_opts;
 

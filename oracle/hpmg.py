@@ -182,7 +182,7 @@ class Hierarchy:
     gradual=False: the paper's hierarchy, DG degree p straight to continuous Q1.
     gradual=True: DG degrees p, p-1, ..., 1, then continuous Q1 (the nested
     sequence V_DG^p > V_DG^(p-1) > ... > V_CG^1 of the paper's outlook,
-    Sec. 6.4). Every lower DG level keeps the finest penalty, so its operator is
+    Sec. 6.3). Every lower DG level keeps the finest penalty, so its operator is
     the Galerkin product P^T A P of the level above; it is smoothed with its own
     block Jacobi (nu_pre, nu_post steps)."""
 

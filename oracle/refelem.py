@@ -79,7 +79,7 @@ def lagrange_derivs(nodes, x):
 
 def basis_nodes(p, basis="gll"):
     """Nodes of the degree-p Lagrange basis: Gauss-Lobatto-Legendre ("gll", the
-    paper's default) or Gauss-Legendre ("gl", Sec. 6.5: no nodes on the cell
+    paper's default) or Gauss-Legendre ("gl", Sec. 6.4: no nodes on the cell
     boundary, diagonal mass matrix)."""
     if basis == "gll":
         return gll_nodes(p)

@@ -37,7 +37,7 @@ class Mesh:
         """penalty_p: degree whose penalty 2 p (p+1) / h the facets use (default p).
         A lower level of a gradual p-hierarchy keeps the finest level's penalty:
         its operator is then the Galerkin restriction of the finest operator.
-        basis: nodes of the Lagrange basis, "gll" (default) or "gl" (Sec. 6.5)."""
+        basis: nodes of the Lagrange basis, "gll" (default) or "gl" (Sec. 6.4)."""
         self.n = tuple(int(v) for v in n)
         self.d = len(self.n)
         if self.d not in (2, 3):
@@ -479,7 +479,7 @@ class BlockJacobi:
 
 
 # ---------------------------------------------------------------------------
-# Right-hand side and error measures (Sec. 6.1)
+# Right-hand side and error measures (Sec. 6 and 6.1)
 # ---------------------------------------------------------------------------
 
 def load_vector(mesh, f, nquad=None):

@@ -49,7 +49,7 @@ cudaError_t wait_timeouts_addr_fp64(unsigned long long **ptr);
 
 // ------------------------------------------------------- reference element
 // 1D Lagrange element of degree p on [-1,1] with GLL (Sec. 2.2) or GL
-// (Sec. 6.5) nodes, computed on the host in double precision.
+// (Sec. 6.4) nodes, computed on the host in double precision.
 struct RefElem1D {
     int p = 0, q = 0;
     int basis = DGMG_BASIS_GLL;

@@ -5,7 +5,7 @@
 // Newton's method from the Chebyshev-Gauss-Lobatto points. Gauss-Legendre
 // rules: Newton's method on P_m from the usual cosine initial guesses, weights
 // 2 / ((1 - x^2) P_m'(x)^2); the q GL points are also the nodes of the GL
-// basis (Sec. 6.5). Legendre values through the three-term recurrence.
+// basis (Sec. 6.4). Legendre values through the three-term recurrence.
 // Exact 1D mass and stiffness matrices use q-point Gauss-Legendre quadrature
 // (degree 2p integrands), matching the paper's remark that the GLL mass matrix
 // is not diagonal (exact integration, Sec. 4.1).

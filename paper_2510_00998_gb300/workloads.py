@@ -42,7 +42,7 @@ WORKLOADS = {
     "3d32_p3_gradual": dict(n=(32, 32, 32), p=3, kappa=None, precision=0, p_coarsening=1),
     "3d64_p4_mixed_gradual": dict(n=(64, 64, 64), p=4, kappa="lognormal3", precision=1, p_coarsening=1),
     "3d64_p4_fp64_gradual": dict(n=(64, 64, 64), p=4, kappa="lognormal3", precision=0, p_coarsening=1),
-    # the same problems in the Gauss-Legendre nodal basis (Sec. 6.5)
+    # the same problems in the Gauss-Legendre nodal basis (Sec. 6.4)
     "3d64_p4_mixed_gl": dict(n=(64, 64, 64), p=4, kappa="lognormal3", precision=1, basis=1),
     "3d64_p4_fp64_gl": dict(n=(64, 64, 64), p=4, kappa="lognormal3", precision=0, basis=1),
 }
@@ -74,7 +74,7 @@ def sine_rhs(ctx, device):
 
 def sin_product_rhs_2d(ctx, device):
     """b = (f, phi_i) for the "sin-product" solution sin(2 pi x) sin(2 pi y) of
-    Sec. 6.4 (f = 8 pi^2 sin(2 pi x) sin(2 pi y)), through the library's quadrature."""
+    Sec. 6 (f = 8 pi^2 sin(2 pi x) sin(2 pi y)), through the library's quadrature."""
     import torch
     mq = ctx.p + 2
     xq = torch.empty(int(ctx.info.ncell) * mq ** 2 * 2, dtype=torch.float64, device=device)

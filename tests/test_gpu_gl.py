@@ -1,4 +1,4 @@
-"""The Gauss-Legendre nodal basis (Sec. 6.5) on the GPU: every stage of the path
+"""The Gauss-Legendre nodal basis (Sec. 6.4) on the GPU: every stage of the path
 against the oracle in the GL basis, the basis invariance of the discrete
 solution (GPU against GPU, no oracle), and the shape of Table 5."""
 import os
@@ -192,7 +192,7 @@ def _gll_to_gl(x, n, p):
 @pytest.mark.parametrize("n,p", [((24, 20), 3), ((10, 9, 8), 2), ((7, 6, 8), 4)])
 def test_solution_is_basis_invariant(dgmg, n, p):
     """The same load f gives the same discrete function in both bases: x_GL = E
-    x_GLL, with E the GLL basis evaluated at the GL nodes (Sec. 6.5: the basis
+    x_GLL, with E the GLL basis evaluated at the GL nodes (Sec. 6.4: the basis
     changes the algebra, not the discrete solution). GPU against GPU."""
     from paper_2510_00998_gb300 import workloads
     kap = _kappa(n, 11)
@@ -248,7 +248,7 @@ def test_table5_shape(dgmg):
     """Parity unpinned (omega, nu and the penalty of Tables 3-5 are not stated;
     nu = 4, omega = 0.8 is the reading that reproduces them best): on 9^2, 27^2,
     81^2 and p = 2..4 the GL cycle counts lie between 0.7x the count of Table 5
-    and one cycle above it, and, as Sec. 6.5 reports, stay close to the GLL
+    and one cycle above it, and, as Sec. 6.4 reports, stay close to the GLL
     counts of the same two-peak problem: the unpreconditioned count at or a
     little above the GLL one, the preconditioned one within a cycle."""
     from paper_2510_00998_gb300 import workloads

@@ -62,7 +62,7 @@ def test_mgmult_iterates_match_oracle(dgmg, n, p, factor, kind):
 @pytest.mark.gpu
 @pytest.mark.parametrize("n,p", [((9, 9), 2), ((9, 9), 3), ((27, 27), 2)])
 def test_mgmult_cycle_counts_match_oracle(dgmg, n, p):
-    """Both exit criteria of Sec. 6.4 (unpreconditioned and preconditioned
+    """Both exit criteria of Sec. 6.3 (unpreconditioned and preconditioned
     residual, 1e-7) take the oracle's number of cycles (+-1 where the ratio
     lands at the threshold)."""
     nu = 3

@@ -1,4 +1,4 @@
-"""The "recompute" variant of the block inverse (paper Table 6, Sec. 6.6):
+"""The "recompute" variant of the block inverse (paper Table 6, Sec. 7.1):
 with opts.recompute_block the per-cell factors of A_KK^-1 are computed again
 before every smoothing step instead of once at set-up. Same factors, so the
 smoothing steps, V-cycles and solves equal the precomputed ones (and so the

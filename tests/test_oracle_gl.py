@@ -1,4 +1,4 @@
-"""Gauss-Legendre basis (Sec. 6.5) in the oracle: the same SIPG problem in another
+"""Gauss-Legendre basis (Sec. 6.4) in the oracle: the same SIPG problem in another
 nodal basis. Every operator of the method (the bilinear form, the cellwise block
 inverses, the Q1 transfer, which evaluates continuous functions at the nodes)
 is basis-independent in function space, so a GL computation equals the GLL one

@@ -151,7 +151,7 @@ def test_pcg_matches_direct_solve(n, p, kind):
 @pytest.mark.parametrize("d,p,ns", [(2, 1, (8, 16, 32)), (2, 2, (4, 8, 16)), (2, 3, (4, 8, 16)), (3, 1, (4, 8)),
                                     (3, 2, (2, 4, 8))])
 def test_manufactured_solution_rate(d, p, ns):
-    """L2 error of the discrete solution decays like h^(p+1) (Sec. 6.2)."""
+    """L2 error of the discrete solution decays like h^(p+1) (Sec. 6.1)."""
     if d == 2:
         uex = lambda x, y: np.sin(np.pi * x) * np.sin(np.pi * y)
         f = lambda x, y: 2 * np.pi ** 2 * uex(x, y)
@@ -184,7 +184,7 @@ def test_mgmult_cycles_ballpark_tables_3_4():
 
 
 def test_mgmult_cycles_ballpark_table_5_gl():
-    """Table 5 (Sec. 6.5): the "two-peak" solution in the GL basis, same setting;
+    """Table 5 (Sec. 6.4): the "two-peak" solution in the GL basis, same setting;
     the GL counts stay close to the GLL ones (unpreconditioned at or slightly
     above, preconditioned within one cycle)."""
     from paper_2510_00998_gb300 import workloads
@@ -261,7 +261,7 @@ def test_gradual_p1_equals_direct():
 
 
 def test_gradual_coarsening_needs_fewer_cycles():
-    """Shape of the paper's outlook (Sec. 6.4): the block-Jacobi smoother with
+    """Shape of the paper's outlook (Sec. 6.3): the block-Jacobi smoother with
     direct coarsening to Q1 is not p-robust; going down one degree at a time
     needs fewer MGMult cycles at higher p."""
     mesh = sipg.Mesh((6, 6), 5)

@@ -65,7 +65,7 @@ def test_reference_element_matches_oracle(dump, p, basis):
         assert np.array_equal(dump[("e0", p, basis)], np.eye(q)[0])
         assert np.array_equal(dump[("ep", p, basis)], np.eye(q)[-1])
     else:
-        # GL: the exact mass is the diagonal of the Gauss weights (Sec. 6.5)
+        # GL: the exact mass is the diagonal of the Gauss weights (Sec. 6.4)
         assert np.abs(M - np.diag(refelem.gauss_legendre(q)[1])).max() <= 1e-14
 
 
