@@ -28,12 +28,15 @@ from . import refelem, sipg
 
 
 def interior_vertex_count(n):
+    """Unknowns of the Q1 space with strong Dirichlet conditions: the interior
+    vertices (Sec. 2.2.3, 2.4)."""
     return int(np.prod([v - 1 for v in n]))
 
 
 def p_prolongation(mesh):
     """P (ndof x nvert): value at every DG node of the Q1 hat of each interior
-    vertex of the cell (products of 1D hats (1-xi)/2, (1+xi)/2)."""
+    vertex of the cell (products of 1D hats (1-xi)/2, (1+xi)/2): the
+    p-prolongation of Eq. prolongation (Sec. 5.1)."""
     d, q = mesh.d, mesh.q
     m = [v - 1 for v in mesh.n]
     xi = mesh.nodes
@@ -65,7 +68,8 @@ def p_prolongation(mesh):
 
 def q1_stiffness(n, kappa=None):
     """kappa-weighted Q1 stiffness on the interior vertices, assembled cell by cell
-    from the element integrals (grad hat_a, grad hat_b) by 2-point Gauss quadrature."""
+    from the element integrals (grad hat_a, grad hat_b) by 2-point Gauss quadrature
+    (Eq. weak_form_cg, Sec. 2.4)."""
     d = len(n)
     h = [1.0 / v for v in n]
     xg, wg = np.polynomial.legendre.leggauss(2)
@@ -117,24 +121,28 @@ def q1_stiffness(n, kappa=None):
 
 
 def coarse_positions(n, f):
-    """Fine vertex indices that are coarse vertices along one axis: 0, f, 2f, ..., n."""
+    """Fine vertex indices that are coarse vertices along one axis: 0, f, 2f, ..., n
+    (the h-coarsening of Sec. 5.2, factor f)."""
     pos = list(range(0, n, f))
     pos.append(n)
     return pos
 
 
 def can_coarsen(v, f):
-    """An axis with v cells is coarsened only if at least two coarse cells remain."""
+    """An axis with v cells is coarsened only if at least two coarse cells remain
+    (the stop rule of the h-coarsening, Sec. 5.2)."""
     return v > f
 
 
 def coarsen_n(n, f):
+    """Cells per axis of the next coarser Q1 mesh (Sec. 5.2)."""
     return tuple(len(coarse_positions(v, f)) - 1 if can_coarsen(v, f) else v for v in n)
 
 
 def interp_1d(n, f):
     """Nested Q1 interpolation along one axis, interior vertices only:
-    (n-1) x (nc-1) with linear weights between neighbouring coarse vertices."""
+    (n-1) x (nc-1) with linear weights between neighbouring coarse vertices
+    (one factor of the h-prolongation, Sec. 5.2)."""
     if not can_coarsen(n, f):
         return sp.identity(max(n - 1, 0), format='csr')
     pos = coarse_positions(n, f)
@@ -151,7 +159,8 @@ def interp_1d(n, f):
 
 def h_prolongation(n, f):
     """P_h between interior-vertex vectors of the meshes n and coarsen_n(n, f)
-    (x fastest: the Kronecker product z (x) y (x) x of the 1D interpolations)."""
+    (x fastest: the Kronecker product z (x) y (x) x of the 1D interpolations;
+    the h-prolongation of Sec. 5.2)."""
     mats = [interp_1d(v, f) for v in n]
     P = mats[0]
     for t in range(1, len(n)):
@@ -161,14 +170,15 @@ def h_prolongation(n, f):
 
 def dg_interp_1d(nodes_f, nodes_c):
     """I[i, j] = l_j^c(x_i^f): the degree-(q_c - 1) Lagrange basis on nodes_c at
-    the fine nodes (exact injection of the coarse polynomial space)."""
+    the fine nodes (exact injection of the coarse polynomial space; the nested DG
+    spaces of the gradual p-coarsening the outlook of Sec. 6.3 proposes)."""
     return refelem.lagrange_values(nodes_c, nodes_f).T
 
 
 def dg_p_prolongation(mesh_f, mesh_c):
     """P (ndof_f x ndof_c): cellwise injection of the degree p_c DG space into
     the degree p_f space on the same mesh, the tensor product of interp_1d along
-    every axis (node index x fastest)."""
+    every axis (node index x fastest; Sec. 6.3 outlook)."""
     I1 = dg_interp_1d(mesh_f.nodes, mesh_c.nodes)
     Pc = I1
     for _ in range(mesh_f.d - 1):
@@ -218,21 +228,24 @@ class Hierarchy:
 
     @property
     def nlevels(self):
+        """Q1 levels below the DG level(s), the coarsest included."""
         return len(self.A)
 
     def coarse_solve(self, r):
+        """Exact solve on the coarsest Q1 level (Alg. 6 coarse solve)."""
         if self.coarse_chol is None:
             return np.zeros(0)
         return sla.cho_solve(self.coarse_chol, r)
 
     def cg_jacobi(self, level, u, b, nsteps):
+        """``nsteps`` damped point-Jacobi steps on a Q1 level (Sec. 2.4 smoother)."""
         A, D = self.A[level], self.D[level]
         for _ in range(nsteps):
             u = u + self.omega_cg * (b - A @ u) / D
         return u
 
     def vcycle_cg(self, level, b):
-        """h-multigrid V-cycle on CG level ``level`` with zero initial guess."""
+        """h-multigrid V-cycle on CG level ``level`` with zero initial guess (Sec. 5.2)."""
         if level == self.nlevels - 1:
             return self.coarse_solve(b)
         u = self.cg_jacobi(level, np.zeros_like(b), b, self.nu_pre)
@@ -244,7 +257,8 @@ class Hierarchy:
     def vcycle_dg(self, level, r):
         """V-cycle from DG level ``level`` with zero initial guess: smoothing,
         residual, restriction to the next DG level (or to the CG levels below the
-        last DG level), correction, smoothing."""
+        last DG level), correction, smoothing (Alg. 6 with the smoothing of Alg. 4
+        around it, Sec. 5.1)."""
         mesh, sm = self.dg_meshes[level], self.dg_smoothers[level]
         u = np.zeros(mesh.ndof)
         u = sm.step_alg2(u, r, self.omega_dg, self.nu_pre)
@@ -256,7 +270,8 @@ class Hierarchy:
         return sm.step_alg2(u, r, self.omega_dg, self.nu_post)
 
     def vcycle(self, r):
-        """z = V(r): hp V(nu_pre, nu_post) cycle with zero initial guess on the DG level."""
+        """z = V(r): hp V(nu_pre, nu_post) cycle with zero initial guess on the DG level
+        (Sec. 5.2)."""
         return self.vcycle_dg(0, r)
 
     def coarse_grid_correction(self, u, b):
@@ -281,7 +296,9 @@ def default_omega_cg(d):
 
 
 def pcg(hier, b, x0=None, rtol=1e-10, maxit=200, flexible=False):
-    """FP64 preconditioned CG with the V-cycle as preconditioner. Stops when
+    """FP64 preconditioned CG with the V-cycle as preconditioner (the multigrid
+    cycle as the preconditioner P^-1 of Sec. 5.1 "Exit criterion"; Alg. 7 iterates
+    it stationarily, see ``mgmult``). Stops when
     ||b - A x||_2 <= rtol ||b||_2 (recursively updated residual). Returns
     (x, iterations, history of relative residuals)."""
     mesh = hier.mesh

@@ -13,7 +13,8 @@ from numpy.polynomial import legendre as npleg
 
 
 def gll_nodes(p):
-    """GLL nodes of degree p on [-1,1]: the endpoints and the roots of P_p'.
+    """GLL nodes of degree p on [-1,1]: the endpoints and the roots of P_p' (the
+    Gauss-Lobatto nodes of the DG basis, Sec. 2.2.1).
 
     Roots come from numpy's Legendre companion matrix and are polished with
     Newton's method on P_p' so that they are accurate to rounding.
@@ -33,7 +34,8 @@ def gll_nodes(p):
 
 
 def gll_weights(p):
-    """GLL quadrature weights w_j = 2 / (p (p+1) P_p(x_j)^2)."""
+    """GLL quadrature weights w_j = 2 / (p (p+1) P_p(x_j)^2) (the lumped part of the
+    GLL mass, Sec. 4.1 "Structure of block-matrices")."""
     x = gll_nodes(p)
     c = np.zeros(p + 1)
     c[p] = 1.0
@@ -41,12 +43,14 @@ def gll_weights(p):
 
 
 def gauss_legendre(m):
-    """m-point Gauss-Legendre rule on [-1,1] (exact for degree 2m-1)."""
+    """m-point Gauss-Legendre rule on [-1,1] (exact for degree 2m-1): the quadrature
+    of every integral here and the nodes of the GL basis (Sec. 2.2.1, 6.4)."""
     return npleg.leggauss(m)
 
 
 def lagrange_values(nodes, x):
-    """V[i, k] = l_i(x_k) for the Lagrange basis on ``nodes`` (product formula)."""
+    """V[i, k] = l_i(x_k) for the Lagrange basis on ``nodes`` (product formula; the
+    tensor-product factors of the basis of Sec. 2.2.1)."""
     nodes = np.asarray(nodes, dtype=np.float64)
     x = np.atleast_1d(np.asarray(x, dtype=np.float64))
     n = len(nodes)
@@ -59,7 +63,8 @@ def lagrange_values(nodes, x):
 
 
 def lagrange_derivs(nodes, x):
-    """D[i, k] = l_i'(x_k): derivative of the product formula by the product rule,
+    """D[i, k] = l_i'(x_k) for the basis of Sec. 2.2.1: derivative of the product
+    formula by the product rule,
     l_i'(x) = sum_{k != i} 1/(x_i - x_k) prod_{m != i,k} (x - x_m)/(x_i - x_m)."""
     nodes = np.asarray(nodes, dtype=np.float64)
     x = np.atleast_1d(np.asarray(x, dtype=np.float64))
@@ -89,14 +94,16 @@ def basis_nodes(p, basis="gll"):
 
 
 def mass_1d(p, basis="gll"):
-    """Exact 1D mass matrix M[i,j] = int_{-1}^{1} l_i l_j (Gauss-Legendre, p+1 points)."""
+    """Exact 1D mass matrix M[i,j] = int_{-1}^{1} l_i l_j (not diagonal with GLL
+    nodes, Sec. 4.1 "Structure of block-matrices"; Gauss-Legendre, p+1 points)."""
     xg, wg = gauss_legendre(p + 1)
     V = lagrange_values(basis_nodes(p, basis), xg)
     return (V * wg) @ V.T
 
 
 def stiffness_1d(p, basis="gll"):
-    """Exact 1D stiffness matrix K[i,j] = int_{-1}^{1} l_i' l_j'."""
+    """Exact 1D stiffness matrix K[i,j] = int_{-1}^{1} l_i' l_j' (the 1D factor of the
+    volume term of Eq. weak_form_IP)."""
     xg, wg = gauss_legendre(p + 1)
     D = lagrange_derivs(basis_nodes(p, basis), xg)
     return (D * wg) @ D.T
@@ -104,14 +111,15 @@ def stiffness_1d(p, basis="gll"):
 
 def endpoint_values(p, basis="gll"):
     """(e0, ep): values of each basis function at xi = -1 and xi = +1 (unit
-    vectors for GLL, dense for GL)."""
+    vectors for GLL, dense for GL): the value projection of Eq. solution_projection."""
     x = basis_nodes(p, basis)
     V = lagrange_values(x, np.array([-1.0, 1.0]))
     return V[:, 0].copy(), V[:, 1].copy()
 
 
 def endpoint_derivs(p, basis="gll"):
-    """(d0, dp): derivatives d/dxi of each basis function at xi = -1 and xi = +1."""
+    """(d0, dp): derivatives d/dxi of each basis function at xi = -1 and xi = +1: the
+    derivative projection of Eq. gradient_projection."""
     x = basis_nodes(p, basis)
     D = lagrange_derivs(x, np.array([-1.0, 1.0]))
     return D[:, 0].copy(), D[:, 1].copy()

@@ -31,7 +31,9 @@ THETA = -1.0  # symmetric interior penalty in the paper's sign convention
 
 
 class Mesh:
-    """Uniform tensor-product mesh of the unit box with n[dir] cells along axis dir."""
+    """Uniform tensor-product mesh of the unit box with n[dir] cells along axis dir
+    (the axis-aligned Cartesian cells of Sec. 2.1, uniformly refined) and the
+    degree-p tensor-product DG space on it (Sec. 2.2.1)."""
 
     def __init__(self, n, p, penalty_p=None, basis="gll"):
         """penalty_p: degree whose penalty 2 p (p+1) / h the facets use (default p).
@@ -61,30 +63,36 @@ class Mesh:
         self.dp = [dp * (2.0 / h) for h in self.h]         # physical d/dx at the high end
 
     def gamma(self, direction):
-        """Penalty gamma_F = 2 p (p+1) / h for a facet normal to ``direction``
+        """Penalty gamma_F = 2 p (p+1) / h for a facet normal to ``direction`` (Sec. 2.3.1)
         (p = penalty_p)."""
         return 2.0 * self.penalty_p * (self.penalty_p + 1) / self.h[direction]
 
     # axis bookkeeping of the grid view
     def cell_axis(self, direction):
+        """Array axis of the cells along ``direction`` (storage layout, no passage)."""
         return self.d - 1 - direction
 
     def node_axis(self, direction):
+        """Array axis of the cell-local nodes along ``direction`` (storage layout)."""
         return 2 * self.d - 1 - direction
 
     def grid(self, u):
+        """DoF vector as the array [cells (z, y, x)][nodes (z, y, x)] (storage layout)."""
         return np.asarray(u, dtype=np.float64).reshape(self.n[::-1] + (self.q,) * self.d)
 
     def flat(self, U):
+        """Inverse of ``grid``: [cell][local node] (storage layout)."""
         return U.reshape(self.ncell, self.nloc)
 
     def kappa_grid(self, kappa):
+        """Per-cell kappa as an array over the cells (kappa = 1 when None)."""
         if kappa is None:
             return np.ones(self.n[::-1])
         return np.asarray(kappa, dtype=np.float64).reshape(self.n[::-1])
 
     def node_coords(self):
-        """Physical coordinates of every DoF, shape (ndof, d)."""
+        """Physical coordinates of every DoF, shape (ndof, d): the nodes of Sec. 2.2.1
+        mapped to each cell."""
         xi01 = (self.nodes + 1.0) / 2.0
         out = np.zeros((self.ncell, self.nloc, self.d))
         cells = np.indices(self.n[::-1]).reshape(self.d, -1)[::-1]   # (ix, iy, iz) per cell
@@ -101,7 +109,8 @@ def _sl(nd, ax, s):
 
 
 def apply_1d(A, U, ax):
-    """Apply the 1D matrix A (rows: output index, cols: input index) along axis ax."""
+    """Apply the 1D matrix A (rows: output index, cols: input index) along axis ax
+    (one factor of a tensor-product operator, Sec. 4.1 "Structure of block-matrices")."""
     return np.moveaxis(np.tensordot(A, U, axes=([1], [ax])), 0, ax)
 
 
@@ -142,7 +151,8 @@ def _basis_tables(mesh):
 
 
 def local_volume_matrix(mesh):
-    """(grad phi_b, grad phi_a)_K for kappa = 1 by d-dimensional Gauss quadrature."""
+    """(grad phi_b, grad phi_a)_K for kappa = 1 by d-dimensional Gauss quadrature: the
+    volume term of Eq. weak_form_IP (Sec. 2.3.1)."""
     d, q = mesh.d, mesh.q
     xg, wg, V, D, _, _ = _basis_tables(mesh)
     ng = len(xg)
@@ -169,7 +179,8 @@ def local_volume_matrix(mesh):
 
 def local_facet_tables(mesh, direction):
     """Values and normal (+axis) derivatives of all cell basis functions on a facet
-    normal to ``direction``, at the facet's tangential Gauss points.
+    normal to ``direction``, at the facet's tangential Gauss points (the facet
+    integrals of Eq. weak_form_IP_facets, Sec. 4.1).
 
     Returns (W, val_lo, der_lo, val_hi, der_hi): the facet quadrature weights and,
     for the cell face at xi_dir = -1 (lo) and +1 (hi), arrays (nloc, npts)."""
@@ -194,7 +205,8 @@ def local_facet_tables(mesh, direction):
 
 
 def assemble(mesh, kappa=None):
-    """Assemble A (scipy CSR, ndof x ndof) from the bilinear form by quadrature.
+    """Assemble A (scipy CSR, ndof x ndof) from the bilinear form Eq. weak_form_IP by
+    quadrature (its matrix, Sec. 2.3.2).
 
     Rows are test functions, columns trial functions. Cells and facets are
     visited one by one; each facet contributes its four (interior) or one
@@ -205,6 +217,7 @@ def assemble(mesh, kappa=None):
     rows, cols, vals = [], [], []
 
     def add(cr, cc, blk):
+        """Scatter one coupling block into the COO lists."""
         r = cr * nl + np.arange(nl)
         c = cc * nl + np.arange(nl)
         rr, cc2 = np.meshgrid(r, c, indexing='ij')
@@ -300,7 +313,8 @@ def project(mesh, U):
 
 
 def facet_kappa(mesh, kappa_grid, direction):
-    """kappa_F per facet of ``direction`` (harmonic mean inside, kappa_K on the boundary),
+    """kappa_F per facet of ``direction`` (harmonic mean inside, kappa_K on the boundary;
+    the coefficient extension of Eq. weak_form_IP read for cellwise kappa, Sec. 2.3.1),
     stacked along the cell axis, broadcastable against the face fields."""
     ca = mesh.cell_axis(direction)
     nd = mesh.n[direction]
@@ -351,7 +365,8 @@ def numerical_flux(mesh, proj, own_only=False):
 
 
 def volume_term(mesh, U, kappa_grid):
-    """kappa_K (grad u, grad v)_K for all cells: sum over directions of the 1D
+    """kappa_K (grad u, grad v)_K for all cells (the cell term of Eq. cell_equation,
+    Alg. 2 stage 3): sum over directions of the 1D
     stiffness along that direction and 1D masses along the others."""
     Y = np.zeros_like(U)
     for direction in range(mesh.d):
@@ -415,7 +430,7 @@ def apply(mesh, u, kappa=None, own_only=False):
 
 
 def residual(mesh, u, b, kappa=None):
-    """r = b - A u."""
+    """r = b - A u (the residual of Eq. block-Jacobi-IP, Sec. 2.3.3)."""
     return np.asarray(b, dtype=np.float64).reshape(-1) - apply(mesh, u, kappa)
 
 
@@ -452,6 +467,7 @@ class BlockJacobi:
         self.Binv = np.linalg.inv(self.B)
 
     def apply_inverse(self, r):
+        """A_KK^-1 r cell by cell (the block inverse of Eq. block-Jacobi-IP)."""
         R = np.asarray(r).reshape(self.mesh.ncell, self.mesh.nloc)
         return np.einsum('cij,cj->ci', self.Binv, R).reshape(-1)
 
@@ -483,7 +499,8 @@ class BlockJacobi:
 # ---------------------------------------------------------------------------
 
 def load_vector(mesh, f, nquad=None):
-    """b_i = (f, phi_i) with (p+2)^d Gauss-Legendre points per cell. ``f`` takes
+    """b_i = (f, phi_i) (right-hand side of Eq. weak_form_IP, Sec. 2.3.1) with (p+2)^d
+    Gauss-Legendre points per cell. ``f`` takes
     d coordinate arrays and returns values."""
     m = mesh.q + 1 if nquad is None else nquad
     xg, wg = refelem.gauss_legendre(m)
@@ -513,7 +530,8 @@ def load_vector(mesh, f, nquad=None):
 
 
 def l2_error(mesh, u, uex, nquad=None):
-    """|| u_h - u_exact ||_{L2(Omega)} with (p+3)^d Gauss points per cell."""
+    """|| u_h - u_exact ||_{L2(Omega)} with (p+3)^d Gauss points per cell (the error
+    measure of Sec. 6.1)."""
     m = mesh.q + 2 if nquad is None else nquad
     xg, wg = refelem.gauss_legendre(m)
     V = refelem.lagrange_values(mesh.nodes, xg)                 # (q, m)
