@@ -205,7 +205,8 @@ int dgmg_destroy(dgmg_ctx *ctx);
 int dgmg_info(const dgmg_ctx *ctx, dgmg_info_t *info);
 
 /* The 1D node coordinates on [-1,1] of ctx's basis (GLL, or GL with
- * opts.basis = DGMG_BASIS_GL): HOST array of q doubles, ascending. */
+ * opts.basis = DGMG_BASIS_GL; Sec. 2.2.1, 6.4): HOST array of q doubles,
+ * ascending. */
 int dgmg_gll_nodes(const dgmg_ctx *ctx, double *nodes_host);
 
 /*
@@ -257,7 +258,8 @@ int dgmg_smooth(dgmg_ctx *ctx, double *u, const double *b, int nsteps, void *str
 int dgmg_vcycle(dgmg_ctx *ctx, const double *r, double *e, void *stream);
 
 /*
- * Solve A x = b with conjugate gradients preconditioned by dgmg_vcycle,
+ * Solve A x = b with conjugate gradients preconditioned by dgmg_vcycle (one
+ * multigrid cycle as the preconditioner P^-1, Sec. 5.1 "Exit criterion"),
  * starting from the x passed in. DGMG_OUTER_PCG: FP64 residual, update and dot
  * products every iteration (flexible Polak-Ribiere form with the FP32 V-cycle).
  * DGMG_OUTER_RELIABLE (mixed precision): the CG recurrences run in FP32 with
@@ -267,7 +269,7 @@ int dgmg_vcycle(dgmg_ctx *ctx, const double *r, double *e, void *stream);
  * coarsest solve stay FP64). Stops when ||b - A x||_2 <= rtol ||b||_2 (PCG: on
  * the recursive residual, then verified), reports the recomputed residual in
  * stats (HOST struct, may be NULL). DGMG_OUTER_MGMULT / _PREC run the stationary
- * iteration instead (iterations = cycles; prec_residual = ||x_k - x_(k-1)|| /
+ * iteration of Alg. 7 instead (iterations = cycles; prec_residual = ||x_k - x_(k-1)|| /
  * ||x_1 - x_0|| of the last cycle; rel_residual the true residual of the last
  * cycle). Blocks until done (it reads one scalar per
  * iteration). Returns DGMG_ENOTCONVERGED after maxit iterations,
@@ -279,8 +281,8 @@ int dgmg_vcycle(dgmg_ctx *ctx, const double *r, double *e, void *stream);
 int dgmg_solve(dgmg_ctx *ctx, const double *b, double *x, dgmg_stats *stats, void *stream);
 
 /*
- * dgmg_solve with HOST vectors: copies b and x (initial guess) to the ctx's
- * device buffers, solves, copies x back. b_host, x_host: ndof doubles each
+ * dgmg_solve (same method) with HOST vectors: copies b and x (initial guess)
+ * to the ctx's device buffers, solves, copies x back. b_host, x_host: ndof doubles each
  * (pinned memory gives the fastest copies). Blocks until x_host is written.
  */
 int dgmg_solve_host(dgmg_ctx *ctx, const double *b_host, double *x_host, dgmg_stats *stats,
@@ -296,6 +298,7 @@ int dgmg_quad_points(dgmg_ctx *ctx, double *xq, void *stream);
 int dgmg_load_vector(dgmg_ctx *ctx, const double *fq, double *b, void *stream);
 
 /*
+ * Sizing for the server's admission (no counterpart in the paper).
  * Device bytes dgmg_create would hold for this problem (exact byte count of its
  * allocations, before allocator rounding). HOST output.
  */
@@ -304,6 +307,8 @@ int dgmg_estimate_bytes(const dgmg_mesh *mesh, int p, const dgmg_opts *opts, siz
 /* ---- serving: continuous batching of independent solves ---- */
 
 /*
+ * Serving (the paper has no counterpart: independent solves of the method,
+ * as dgmg_solve, scheduled together).
  * Start a solve server on the current device: at most `max_active` solves run
  * at once (each on its own stream, advanced one CG iteration at a time by a
  * scheduler thread, so their kernels overlap), and the hierarchies it keeps
@@ -362,6 +367,8 @@ typedef struct {
 } dgmg_batch_info_t;
 
 /*
+ * Batching (the paper has no counterpart: independent problems, each solved
+ * as dgmg_solve, sharing launches).
  * Build `count` independent problems (meshes[i], degree p[i] in 1..6,
  * kappa[i]: HOST array of the mesh's ncell positive values or NULL = 1; kappa
  * itself may be NULL) for batched solving: each problem gets its own hierarchy
@@ -447,14 +454,14 @@ int dgmg_residual_restrict_noalloc(dgmg_ctx *ctx, const double *u, const double 
 int dgmg_cg_smooth(dgmg_ctx *ctx, int level, double *u, const double *b, int nsteps,
                    void *stream);
 
-/* Q1 level `level`: r = b - A_l u. */
+/* Q1 level `level`: r = b - A_l u (A_l the Galerkin operator, Sec. 2.4, 5.2). */
 int dgmg_cg_residual(dgmg_ctx *ctx, int level, const double *u, const double *b, double *r,
                      void *stream);
 
 /* h-restriction rc = P_h^T rf from level `level` to level+1 (Sec. 5.2). */
 int dgmg_h_restrict(dgmg_ctx *ctx, int level, const double *rf, double *rc, void *stream);
 
-/* h-prolongation uf += P_h ec from level+1 to level `level`. */
+/* h-prolongation uf += P_h ec from level+1 to level `level` (Sec. 5.2). */
 int dgmg_h_prolong(dgmg_ctx *ctx, int level, const double *ec, double *uf, void *stream);
 
 /* Coarsest-level solve e = A_c^{-1} r (dense, FP64; Alg. 6 coarse solve). */
