@@ -1,4 +1,7 @@
 // Batched solves: many independent problems share one kernel launch per stage.
+// Each problem is solved by the method of dgmg_solve (the hp cycle of Sec. 5.1
+// and 5.2 with the single-touch smoothing step of Alg. 4); batching itself has
+// no counterpart in the paper.
 //
 // dgmg_batch_create builds one ordinary hierarchy per problem (all of the
 // set-up is the single-problem code), then lays the problems out for batched

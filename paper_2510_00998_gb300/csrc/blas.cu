@@ -1,7 +1,9 @@
 // FP64 vector kernels of the outer conjugate-gradient loop: deterministic
 // two-stage dot products (fixed grid, fixed reduction order), the CG updates
 // with step lengths read from device memory, precision casts, and the
-// right-hand-side quadrature (b_i = (f, phi_i)).
+// right-hand-side quadrature (b_i = (f, phi_i), the right-hand side of
+// Eq. weak_form_IP). The CG loop uses one multigrid cycle as its preconditioner
+// (P^-1 of Sec. 5.1 "Exit criterion").
 #include <algorithm>
 
 #include "internal.h"

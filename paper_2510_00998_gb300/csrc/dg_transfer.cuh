@@ -1,4 +1,5 @@
-// Transfers between the DG levels of a gradual p-hierarchy (degree p_f on the
+// Transfers between the DG levels of a gradual p-hierarchy (the nested DG spaces
+// the outlook of Sec. 6.3 proposes; degree p_f on the
 // same mesh as degree p_c = p_f - 1): the cellwise injection of the coarse
 // polynomial space, P = I (x) I (x) I with I[i][j] = l_j^c(x_i^f) (the coarse
 // Lagrange basis at the fine nodes), and its transpose for the restriction of

@@ -1,4 +1,6 @@
-// Residual + p-restriction that allocates nothing at call time.
+// Residual + p-restriction (the residual traversal of Alg. 6 with the
+// restriction fused in, Sec. 5.1 "Restriction") that allocates nothing at call
+// time; as an interface variant it has no counterpart in the paper.
 //
 // Who needs it: code that runs where device allocation is not allowed or not
 // available -- real-time or embedded loops that forbid allocation after

@@ -1,4 +1,5 @@
-// Solve server: continuous batching of independent solves on one GPU.
+// Solve server: continuous batching of independent solves on one GPU (each
+// solved as dgmg_solve; serving has no counterpart in the paper).
 //
 // Requests (mesh, degree, kappa, device b and x) are queued by dgmg_submit and
 // admitted by a scheduler thread as soon as an execution slot is free and the
