@@ -440,7 +440,7 @@ int dgmg_residual_restrict(dgmg_ctx *ctx, const double *u, const double *b,
  * meshes needing more (more than 262,144 hexahedra or 524,288 quadrilaterals)
  * are rejected with DGMG_EINVAL. The first call on a device looks up that
  * array's device address (a one-time set-up per device, made with that device
- * current); make that first call before any stream capture. All calls share
+ * current). All calls share
  * the array: calls whose GPU work overlaps in time (other streams, other
  * threads, other contexts on the same device) race and must be serialised
  * by the caller. Every call overwrites the sums it reads, so no clearing is
