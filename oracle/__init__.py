@@ -23,7 +23,8 @@ Modules
   traffic   the memory-access model of Sec. 4.1 (Table 1)
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test in
-``tests/test_oracle_*.py`` except ``hpmg.mgmult`` cycle counts, which are
-"parity unpinned" (the paper does not state omega, nu or the penalty it used for
-Tables 3-4; only a ballpark comparison is possible).
+``tests/test_oracle_*.py``, ``hpmg.mgmult`` included (its iterates against the
+dense cycle matrix, its exit rules against the norms of those iterates). Its
+cycle counts against Tables 3-5 are a comparison under a reading, not a pin: the
+paper does not state omega, nu or the penalty it used there.
 """

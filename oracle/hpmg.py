@@ -17,8 +17,9 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 * Coarsest level: dense Cholesky solve (FP64).
 * V(nu_pre, nu_post) cycle used as preconditioner of FP64 CG, and the paper's
   MGMult (Alg. 7: nu pre-smoothing steps, no post-smoothing, one h-V-cycle for
-  the coarse correction, preconditioned-residual exit). MGMult cycle counts are
-  "parity unpinned": the paper does not state omega, nu or gamma for Tables 3-4.
+  the coarse correction, preconditioned-residual exit). The MGMult iteration is
+  pinned against its dense cycle matrix; its cycle counts against Tables 3-5
+  rest on a reading of omega, nu and gamma, which the paper does not state.
 """
 import numpy as np
 import scipy.linalg as sla
@@ -333,8 +334,10 @@ def mgmult(hier, b, u0=None, eps=1e-7, maxit=500, residual_kind='unprec'):
     """Alg. 7 (MGMult): nu block-Jacobi steps, coarse-grid correction (Alg. 6,
     one h-V-cycle), until the chosen relative residual drops below eps.
     residual_kind 'unprec': ||b - A u|| / ||b - A u_0||; 'prec':
-    ||u - u_old|| / ||u_1 - u_0||. Returns (u, cycles). Parity unpinned
-    against the paper's Tables 3-4."""
+    ||u - u_old|| / ||u_1 - u_0||. Returns (u, cycles). The iterates are pinned
+    against the dense cycle matrix and the exit rules against the norms of those
+    iterates (tests); the cycle counts of Tables 3-5 depend on omega, nu and the
+    penalty, which the paper does not state (a reading, not a pin)."""
     mesh = hier.mesh
     b = np.asarray(b, dtype=np.float64).reshape(-1)
     u = np.zeros(mesh.ndof) if u0 is None else np.array(u0, dtype=np.float64).reshape(-1)

@@ -245,7 +245,8 @@ def test_table5_cycle_counts_match_oracle(dgmg, n, p):
 
 
 def test_table5_shape(dgmg):
-    """Parity unpinned (omega, nu and the penalty of Tables 3-5 are not stated;
+    """A comparison under a reading, not a pin (omega, nu and the penalty of
+    Tables 3-5 are not stated;
     nu = 4, omega = 0.8 is the reading that reproduces them best): on 9^2, 27^2,
     81^2 and p = 2..4 the GL cycle counts lie between 0.7x the count of Table 5
     and one cycle above it, and, as Sec. 6.4 reports, stay close to the GLL

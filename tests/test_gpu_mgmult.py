@@ -85,7 +85,8 @@ def test_mgmult_cycle_counts_match_oracle(dgmg, n, p):
 
 @pytest.mark.gpu
 def test_mgmult_tables_3_4_shape(dgmg):
-    """Parity unpinned (the paper states neither omega, nu nor the penalty for
+    """A comparison under a reading, not a pin (the paper states neither
+    omega, nu nor the penalty for
     Tables 3-4): on 9^2 ... 243^2 with factor-3 coarsening, nu = 4 and omega = 0.8
     (the reading that reproduces the printed tables best) the cycle counts are
     h-robust (unpreconditioned: within 1.5x across the meshes; preconditioned: not

@@ -168,7 +168,8 @@ def test_manufactured_solution_rate(d, p, ns):
 
 
 def test_mgmult_cycles_ballpark_tables_3_4():
-    """Parity unpinned: the paper does not state omega, nu or gamma for Tables 3-4.
+    """A comparison under a reading, not a pin (the iteration itself is pinned in
+    test_oracle_mgmult.py): the paper does not state omega, nu or gamma for Tables 3-4.
     With nu = 4, omega = 0.8 and factor-3 coarsening the oracle's MGMult needs
     between 0.7x the printed cycle counts and one cycle more."""
     rows = np.loadtxt(os.path.join(GOLDEN, "table3_4_cycles.txt"))

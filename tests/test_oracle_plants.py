@@ -132,3 +132,12 @@ def test_technique4_wrong_centre_cell(monkeypatch):
     orig = sipg.block_diagonal
     monkeypatch.setattr(sipg, "block_diagonal", lambda mesh, kappa=None: np.roll(orig(mesh, kappa), 1, axis=0))
     _fails(S.test_interior_only_block_is_an_interior_cells_assembled_block, (3, 4), 3)
+
+
+def test_mgmult_lost_smoothing_step(monkeypatch):
+    # MGMult (Alg. 7) with one block-Jacobi step per cycle lost
+    import test_oracle_mgmult as G
+    orig = sipg.BlockJacobi.step_alg2
+    monkeypatch.setattr(sipg.BlockJacobi, "step_alg2",
+                        lambda self, u, b, omega, nsteps=1: orig(self, u, b, omega, max(nsteps - 1, 0)))
+    _fails(G.test_mgmult_iterates_follow_the_dense_cycle, (6, 5), 2, 2)
